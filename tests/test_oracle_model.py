@@ -1,0 +1,230 @@
+"""Pins of the oracle's TensorNet energy, forces and weight gradients:
+central finite differences, an autograd witness, the invariances the model
+fixes (Sec. 2.1.1: O(3) equivariance; translation, permutation and periodic
+image invariance), zero net force, cutoff continuity and the isolated-atom
+closed form."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.neighbors import neighbor_pairs
+from oracle.tensornet import TensorNet
+from paper_2402_17660_gb300 import synth
+
+from . import torch_witness
+
+SMALL = synth.ModelShape(F=16, K=8, L=2)
+FULL = synth.ModelShape()
+
+
+def _model(shape=SMALL, seed=0):
+    W = synth.init_weights(shape, seed)
+    return W, TensorNet(W, F=shape.F, K=shape.K, L=shape.L)
+
+
+def _pbc_small(seed=0, n=30, L=10.5):
+    """A periodic box just over 2 cutoffs wide at low density."""
+    rng = np.random.default_rng(seed)
+    s = synth.random_cluster(n, seed=seed, side=L, min_dist=1.2)
+    pos = s.pos.astype(np.float64) + rng.uniform(-L, L, (n, 3)).round() * 0  # inside the box
+    box = (np.eye(3) * L)[None].astype(np.float32)
+    return s.z, pos.astype(np.float32), s.batch, box
+
+
+def _fd_forces(m, z, pos, batch, box, h=1e-5):
+    pos = pos.astype(np.float64)
+    fd = np.zeros_like(pos)
+    for a in range(len(pos)):
+        for k in range(3):
+            pp = pos.copy()
+            pp[a, k] += h
+            pm = pos.copy()
+            pm[a, k] -= h
+            fd[a, k] = -(m.forward(z, pp, batch, box)[0].sum() - m.forward(z, pm, batch, box)[0].sum()) / (2 * h)
+    return fd
+
+
+def _rms(F):
+    return np.sqrt(np.mean(np.sum(F * F, axis=1)))
+
+
+@pytest.mark.parametrize("case", ["cluster", "pbc"])
+def test_forces_match_finite_differences(case):
+    W, m = _model()
+    if case == "cluster":
+        s = synth.random_cluster(10, seed=5, side=4.0)
+        z, pos, batch, box = s.z, s.pos, s.batch, None
+    else:
+        z, pos, batch, box = _pbc_small(1, n=12)
+    _, _, F, _ = m.energy_forces(z, pos, batch, box)
+    fd = _fd_forces(m, z, pos, batch, box)
+    assert np.max(np.abs(F - fd)) <= 1e-7 * max(_rms(F), 1.0)
+
+
+def test_forces_match_finite_differences_full_width():
+    W, m = _model(FULL)
+    s = synth.random_cluster(6, seed=9, side=3.0)
+    _, _, F, _ = m.energy_forces(s.z, s.pos, s.batch, None)
+    fd = _fd_forces(m, s.z, s.pos, s.batch, None)
+    assert np.max(np.abs(F - fd)) <= 1e-7 * max(_rms(F), 1.0)
+
+
+def test_weight_gradients_match_directional_fd():
+    W, m = _model()
+    s = synth.random_cluster(10, seed=6, side=4.0)
+    pos = s.pos.astype(np.float64)
+    _, _, _, G = m.energy_forces(s.z, pos, s.batch, None, want_weights=True)
+    rng = np.random.default_rng(0)
+    h = 1e-5
+    for name in W:
+        v = rng.standard_normal(W[name].shape)
+        Wp = {k: np.asarray(x, np.float64).copy() for k, x in W.items()}
+        Wm = {k: x.copy() for k, x in Wp.items()}
+        Wp[name] = Wp[name] + h * v
+        Wm[name] = Wm[name] - h * v
+        ep = TensorNet(Wp, F=16, K=8, L=2).forward(s.z, pos, s.batch, None)[0][0]
+        em = TensorNet(Wm, F=16, K=8, L=2).forward(s.z, pos, s.batch, None)[0][0]
+        fd = (ep - em) / (2 * h)
+        an = float(np.sum(G[name] * v))
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-2), name
+
+
+@pytest.mark.parametrize("case", ["cluster", "pbc", "batch"])
+def test_reverse_pass_matches_autograd_witness(case):
+    W, m = _model()
+    if case == "cluster":
+        s = synth.random_cluster(14, seed=7, side=4.5)
+        z, pos, batch, box = s.z, s.pos, s.batch, None
+    elif case == "pbc":
+        z, pos, batch, box = _pbc_small(2, n=20)
+    else:
+        s = synth.molecule_batch(3, nmin=5, nmax=9, seed=4)
+        z, pos, batch, box = s.z, s.pos, s.batch, None
+    i, j = neighbor_pairs(pos, batch, box, 5.0)
+    seed = np.linspace(0.5, 1.5, int(batch.max()) + 1)
+    Es, _, c = m.forward(z, pos, batch, box, pairs=(i, j))
+    gpos, G = m.backward(c, seed=seed)
+    P = {k: torch.tensor(np.asarray(v, np.float64), requires_grad=True) for k, v in W.items()}
+    X = torch.tensor(pos.astype(np.float64), requires_grad=True)
+    bt = None if box is None else torch.tensor(box.astype(np.float64))
+    Et = torch_witness.energy(P, torch.tensor(z).long(), X, torch.tensor(batch).long(), bt,
+                              torch.tensor(i), torch.tensor(j), F=16, K=8, L=2)
+    assert np.allclose(Et.detach().numpy(), Es, rtol=1e-12, atol=1e-12)
+    (Et * torch.tensor(seed)).sum().backward()
+    assert np.allclose(gpos, X.grad.numpy(), rtol=1e-9, atol=1e-11)
+    for k in W:
+        assert np.allclose(G[k], P[k].grad.numpy(), rtol=1e-9, atol=1e-11), k
+
+
+def _random_orthogonal(seed, reflect):
+    rng = np.random.default_rng(seed)
+    Q, R = np.linalg.qr(rng.standard_normal((3, 3)))
+    Q = Q * np.sign(np.diag(R))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] *= -1
+    if reflect:
+        Q = Q @ np.diag([1.0, 1.0, -1.0])
+    return Q
+
+
+@pytest.mark.parametrize("reflect", [False, True])
+def test_rotation_reflection_invariance_and_force_equivariance(reflect):
+    W, m = _model(FULL)
+    s = synth.random_cluster(20, seed=8)
+    pos = s.pos.astype(np.float64)
+    E0, _, F0, _ = m.energy_forces(s.z, pos, s.batch, None)
+    Q = _random_orthogonal(3, reflect)
+    E1, _, F1, _ = m.energy_forces(s.z, pos @ Q.T, s.batch, None)
+    assert abs(E1[0] - E0[0]) <= 1e-12 * max(1.0, abs(E0[0]))
+    assert np.allclose(F1, F0 @ Q.T, atol=1e-11)
+
+
+def test_translation_permutation_and_zero_net_force():
+    W, m = _model()
+    s = synth.random_cluster(24, seed=10)
+    pos = s.pos.astype(np.float64)
+    E0, Ei0, F0, _ = m.energy_forces(s.z, pos, s.batch, None)
+    assert np.allclose(F0.sum(0), 0.0, atol=1e-12)
+    E1, _, F1, _ = m.energy_forces(s.z, pos + np.array([3.1, -7.2, 0.4]), s.batch, None)
+    assert abs(E1[0] - E0[0]) < 1e-12 * max(1.0, abs(E0[0]))
+    perm = np.random.default_rng(1).permutation(len(pos))
+    E2, Ei2, F2, _ = m.energy_forces(s.z[perm], pos[perm], s.batch, None)
+    assert abs(E2[0] - E0[0]) < 1e-12 * max(1.0, abs(E0[0]))
+    assert np.allclose(F2, F0[perm], atol=1e-12)
+    assert np.allclose(Ei2, Ei0[perm], atol=1e-12)
+
+
+def test_periodic_image_shift_invariance():
+    W, m = _model()
+    z, pos, batch, box = _pbc_small(3, n=24)
+    pos = pos.astype(np.float64)
+    E0, _, F0, _ = m.energy_forces(z, pos, batch, box)
+    assert np.allclose(F0.sum(0), 0.0, atol=1e-12)
+    shifted = pos.copy()
+    shifted[::3] += np.array([10.5, -21.0, 31.5])        # lattice vectors of the box
+    E1, _, F1, _ = m.energy_forces(z, shifted, batch, box)
+    assert abs(E1[0] - E0[0]) < 1e-12 * max(1.0, abs(E0[0]))
+    assert np.allclose(F1, F0, atol=1e-12)
+
+
+def test_batch_equals_separate_systems():
+    W, m = _model()
+    s = synth.molecule_batch(4, nmin=6, nmax=12, seed=5)
+    Es, Ei, F, _ = m.energy_forces(s.z, s.pos, s.batch, None)
+    for k in range(4):
+        sel = s.batch == k
+        Ek, _, Fk, _ = m.energy_forces(s.z[sel], s.pos[sel], np.zeros(sel.sum(), np.int32), None)
+        assert abs(Ek[0] - Es[k]) < 1e-12 * max(1.0, abs(Es[k]))
+        assert np.allclose(Fk, F[sel], atol=1e-12)
+
+
+def test_isolated_atoms_reduce_to_output_mlp():
+    """Atoms farther apart than the cutoff have zero tensor features, so each
+    atom's energy is the output head applied to the LayerNorm shift alone:
+    an ordinary MLP (evaluated here with torch.nn layers)."""
+    W, m = _model()
+    pos = np.array([[0.0, 0, 0], [6.0, 0, 0], [0, 12.0, 0]])
+    z = np.array([1, 6, 8], np.int32)
+    Es, Ei, F, _ = m.energy_forces(z, pos, np.zeros(3, np.int32), None)
+    assert np.all(F == 0)
+    F_ = SMALL.F
+    net = torch.nn.Sequential(torch.nn.Linear(3 * F_, F_), torch.nn.SiLU(),
+                              torch.nn.Linear(F_, F_ // 2), torch.nn.SiLU(),
+                              torch.nn.Linear(F_ // 2, 1)).double()
+    with torch.no_grad():
+        for lin, wn, bn in ((net[0], "out_w", "out_b"), (net[2], "head1_w", "head1_b"),
+                            (net[4], "head2_w", "head2_b")):
+            lin.weight.copy_(torch.tensor(W[wn].astype(np.float64)))
+            lin.bias.copy_(torch.tensor(W[bn].astype(np.float64)))
+        ref = net(torch.tensor(W["out_ln_b"].astype(np.float64))).item()
+    assert np.allclose(Ei, ref, atol=1e-13)
+
+
+def test_cutoff_continuity():
+    """A pair at d = rc - eps differs from the isolated pair by O(eps^4):
+    phi(rc - eps) = O(eps^2) multiplies every tensor feature of the pair, and
+    the energy sees features only through squared norms."""
+    W, m = _model()
+    z = np.array([6, 8], np.int32)
+    b = np.zeros(2, np.int32)
+    far = m.forward(z, np.array([[0.0, 0, 0], [20.0, 0, 0]]), b, None)[0][0]
+    dE = []
+    for eps in (4e-2, 2e-2, 1e-2):
+        dE.append(m.forward(z, np.array([[0.0, 0, 0], [5.0 - eps, 0, 0]]), b, None)[0][0] - far)
+    assert abs(dE[0]) > 0
+    assert abs(dE[1] / dE[0] - 1 / 16) < 0.005 and abs(dE[2] / dE[1] - 1 / 16) < 0.005
+
+
+def test_zero_layer_model_runs_and_is_invariant():
+    shape = synth.ModelShape(F=16, K=8, L=0)
+    W = synth.init_weights(shape, 1)
+    m = TensorNet(W, F=16, K=8, L=0)
+    s = synth.random_cluster(12, seed=12)
+    pos = s.pos.astype(np.float64)
+    E0, _, F0, _ = m.energy_forces(s.z, pos, s.batch, None)
+    Q = _random_orthogonal(5, True)
+    E1, _, F1, _ = m.energy_forces(s.z, pos @ Q.T, s.batch, None)
+    assert abs(E1[0] - E0[0]) < 1e-12 * max(1, abs(E0[0]))
+    assert np.allclose(F1, F0 @ Q.T, atol=1e-12)
+    fd = _fd_forces(m, s.z, pos, s.batch, None)
+    assert np.max(np.abs(F0 - fd)) <= 1e-7 * max(_rms(F0), 1.0)
