@@ -1,0 +1,192 @@
+/*
+ * tnet.h - C ABI of libtnet: TensorNet energy and forces on one GB300 (sm_103a).
+ *
+ * The library computes what TorchMD-Net 2.0 (arXiv 2402.17660) describes as a
+ * neural network potential: atomic positions R and embedding indices Z go in,
+ * a per-sample scalar (the potential energy) and its negative gradient with
+ * respect to the positions (the atomic forces) come out (Sec. 2, Background;
+ * Fig. 1).  The representation model is TensorNet (Sec. 2.1.1), an
+ * O(3)-equivariant message passing network on rank-2 Cartesian tensors, with
+ * the hyperparameters of the paper's training example (Sec. 2.4, Table S4).
+ * The graph comes from a periodic cell-list neighbor search (Sec. 2.5.1).
+ *
+ * Conventions shared by every entry point
+ *   - Every pointer argument is a DEVICE pointer unless its comment says HOST.
+ *     The caller owns all memory (inputs, outputs and the workspace handed to
+ *     tnet_create); the library never allocates device memory.
+ *   - Calls are ordered on the given CUDA stream and return as soon as the
+ *     work is enqueued; they do not synchronise the host.  They issue no
+ *     host<->device copies, so tnet_neighbors and tnet_energy_forces can be
+ *     captured into a CUDA graph.
+ *   - The int return value reports synchronous argument errors only (a
+ *     tnet_status code).  Errors found on the device (pair capacity
+ *     exceeded, box too small, bad atomic number, non-finite positions) are
+ *     written to *status_dev (int32, device) with the first error winning;
+ *     the caller zeroes it before the call, synchronises and reads it after.
+ *   - Units: positions and box in Angstrom, energies in the model's unit
+ *     (treated as eV by tnet_md_step), time in fs, mass in amu.
+ *   - Arrays are C-contiguous; pos is [N][3] float32 (x, y, z per atom).
+ *   - A context is not thread-safe: calls that share a context must be
+ *     ordered on one stream.
+ */
+#ifndef TNET_H
+#define TNET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL means the legacy default stream. */
+typedef struct CUstream_st *tnet_stream_t;
+
+typedef struct tnet_ctx tnet_ctx;
+
+/* Model shape.  F: embedding dimension (channels), K: number of expnorm
+ * radial basis functions, L: number of interaction layers, max_z: rows of
+ * the atomic-number embedding table, cutoff_upper/lower: the cosine cutoff
+ * interval in Angstrom (Sec. 2.4: embedding_dimension 128, num_layers 2,
+ * num_rbf 32, max_z 100, cutoff 0..5 A).  precision: 0 = FP32 everywhere,
+ * 1 = BF16 tensor-core GEMMs with FP32 accumulation for the dense
+ * contractions (geometry, basis and scatter-adds stay FP32; the per-system
+ * energy is reduced in FP64 in both modes).
+ * Limits: F a multiple of 64 in [64, 512], K a multiple of 8 in [8, 64],
+ * 0 <= L <= 8, 1 <= max_z <= 128, 0 <= cutoff_lower < cutoff_upper. */
+typedef struct {
+    int F, K, L, max_z;
+    float cutoff_upper, cutoff_lower;
+    int precision;
+} tnet_model_desc;
+
+typedef enum {
+    TNET_OK = 0,
+    TNET_ERR_ARG = 1,         /* bad argument (host) or bad batch vector (device) */
+    TNET_ERR_CAPACITY = 2,    /* more pairs than the caller's capacity (device) */
+    TNET_ERR_BOX = 3,         /* box not lower-triangular or narrower than 2*cutoff */
+    TNET_ERR_NAN = 4,         /* non-finite position (device) */
+    TNET_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    TNET_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    TNET_ERR_WORKSPACE = 7,   /* workspace too small or misaligned */
+    TNET_ERR_Z = 8,           /* atomic number outside [0, max_z) (device) */
+    TNET_ERR_UNSUPPORTED = 9, /* valid request this build does not implement */
+    TNET_ERR_SKIN = 10        /* MD: an atom moved more than skin/2 between rebuilds */
+} tnet_status;
+
+const char *tnet_status_string(int status);
+
+/* Number of float32 values in the weight blob for this shape, or -1 for an
+ * invalid shape.  Blob layout: the parameters below, each C-contiguous
+ * float32, concatenated in this order with no padding.  Linear weights are
+ * stored (out, in) so that y = W x + b; stacks [3] are indexed
+ * p = 0 (I), 1 (A), 2 (S).
+ *   emb        [max_z][F]       atomic-number embedding
+ *   emb2_w     [F][2F], emb2_b [F]     pair embedding W_e [emb(z_i); emb(z_j)] + b_e
+ *   dproj_w    [3][F][K], dproj_b [3][F]   radial projections f^p = W^p e(d) + b^p
+ *   emb_ln_g   [F], emb_ln_b [F]           LayerNorm of the embedding norms
+ *   emb_mlp1_w [2F][F], emb_mlp1_b [2F]
+ *   emb_mlp2_w [3F][2F], emb_mlp2_b [3F]   per-atom scalar MLP (SiLU after each)
+ *   emb_mix_w  [3][F][F]                   channel mixing of I, A, S (no bias)
+ *   for l in 0..L-1:
+ *     l{l}_mlp1_w [F][K],   l{l}_mlp1_b [F]
+ *     l{l}_mlp2_w [2F][F],  l{l}_mlp2_b [2F]
+ *     l{l}_mlp3_w [3F][2F], l{l}_mlp3_b [3F]  edge radial MLP (SiLU after each)
+ *     l{l}_mix1_w [3][F][F]                   mixing before the messages
+ *     l{l}_mix2_w [3][F][F]                   mixing after the tensor products
+ *   out_ln_g   [3F], out_ln_b [3F]
+ *   out_w      [F][3F], out_b [F]
+ *   head1_w    [F/2][F], head1_b [F/2]
+ *   head2_w    [1][F/2], head2_b [1]
+ * Per-edge and per-atom 3F vectors are split channel-major: index c*3 + p. */
+int64_t tnet_weights_count(const tnet_model_desc *desc);
+
+/* Bytes of device workspace tnet_create needs for these limits (or -1 for
+ * invalid arguments).  max_atoms: most atoms per call, max_systems: most
+ * systems per call, max_pairs: the directed-pair capacity the caller will
+ * pass to tnet_neighbors (also the most pairs tnet_energy_forces accepts). */
+int64_t tnet_workspace_bytes(const tnet_model_desc *desc, int max_atoms, int max_systems,
+                             int64_t max_pairs);
+
+/* Create a context bound to the current CUDA device.  workspace: device
+ * memory of at least tnet_workspace_bytes(...) bytes, 256-byte aligned,
+ * owned by the caller and kept alive (and not used by anything else) until
+ * tnet_destroy.  *out receives a host-side handle. */
+int tnet_create(tnet_ctx **out, const tnet_model_desc *desc, int max_atoms, int max_systems,
+                int64_t max_pairs, void *workspace, size_t workspace_bytes);
+int tnet_destroy(tnet_ctx *ctx);
+
+/* Neighbor search (Sec. 2.5.1): all ordered pairs (i, j), i != j, of atoms in
+ * the same system with |r_i - r_j| < cutoff, where with periodic boundaries
+ * the distance is that of the nearest image.  One cell list per system
+ * (cells never mix systems); each system's cells are at least `cutoff`
+ * wide, so a system smaller than two cutoffs is searched all-pairs.
+ *   n_atoms, n_systems  counts (1 <= n_systems <= n_atoms is not required:
+ *                       systems may be empty)
+ *   pos      [N][3] float32
+ *   batch    [N] int32 system index of each atom, non-decreasing, in
+ *            [0, n_systems); NULL means every atom is in system 0
+ *   box      [S][3][3] float32, rows a, b, c of each system's box, lower-
+ *            triangular (a = (ax,0,0), b = (bx,by,0)); only rectangular
+ *            boxes (diagonal) are implemented; NULL means no periodicity.
+ *            Each perpendicular width must be >= 2*cutoff (else BOX).
+ *   cutoff   Angstrom (> 0); a pair is kept when d < cutoff
+ * Output (receiver-sorted CSR; within a row, columns ascend):
+ *   row_ptr  [N+1] int32   row_ptr[0] = 0, row i holds the j of pairs (i, j)
+ *   col      [cap] int32
+ *   n_pairs_dev  [1] int64 number of pairs found (also when > cap)
+ * If the pairs exceed cap, status CAPACITY is set, row_ptr still holds the
+ * exact row offsets, col is filled only below cap, and the caller must
+ * enlarge col to *n_pairs_dev and call again.  cap must not exceed the
+ * context's max_pairs. */
+int tnet_neighbors(tnet_ctx *ctx, int n_atoms, int n_systems, const float *pos,
+                   const int32_t *batch, const float *box, float cutoff, int32_t *row_ptr,
+                   int32_t *col, int64_t cap, int64_t *n_pairs_dev, int32_t *status_dev,
+                   tnet_stream_t stream);
+
+/* Energy and forces (Sec. 2, Fig. 1; TensorNet Sec. 2.1.1): per-system
+ * energies E_s = sum over atoms of the system of the per-atom output, and
+ * forces F_i = -dE/dr_i computed by a hand-written reverse pass.
+ *   weights  flat blob, tnet_weights_count floats (layout above)
+ *   z [N] int32 atomic numbers in [0, max_z); pos, batch, box as in
+ *   tnet_neighbors; row_ptr/col: a symmetric pair list from tnet_neighbors
+ *   built with a cutoff >= cutoff_upper (pairs at d >= cutoff_upper
+ *   contribute nothing, so a list with a skin is valid)
+ *   energy_seed [S] float32 or NULL: forces and weight gradients are those of
+ *            sum_s seed_s E_s (NULL: all ones)
+ *   energy   [S] float64 output
+ *   forces   [N][3] float32 output, or NULL to skip the reverse pass
+ *   grad_weights  [tnet_weights_count] float32 output (overwritten) or NULL.
+ * Results do not depend on the order of columns within a row beyond float
+ * rounding; with the CSR of tnet_neighbors they are deterministic. */
+int tnet_energy_forces(tnet_ctx *ctx, const float *weights, int n_atoms, int n_systems,
+                       const int32_t *z, const float *pos, const int32_t *batch,
+                       const float *box, const int32_t *row_ptr, const int32_t *col,
+                       const float *energy_seed, double *energy, float *forces,
+                       float *grad_weights, int32_t *status_dev, tnet_stream_t stream);
+
+/* Molecular dynamics (the paper's MD use, Sec. 3 "Molecular Simulations";
+ * one step = one energy evaluation plus one force backward pass): n_steps
+ * velocity-Verlet steps of one system with time step dt_fs:
+ *   v += dt/2 F/m; x += dt v; [every rebuild_every steps: neighbor list at
+ *   cutoff_upper + skin]; F = forces(x); v += dt/2 F/m.
+ * Forces in eV/A and masses in amu are converted with
+ * 1 eV/(A amu) = 9.64853321e-3 A/fs^2.
+ *   inv_mass [N] float32 1/m in 1/amu; pos, vel [N][3] float32 updated in
+ *   place (vel in A/fs); box [1][3][3] or NULL
+ *   e_kin, e_pot [n_steps] float64 outputs: kinetic and potential energy
+ *   after each step
+ * The steps run as replays of a CUDA graph of rebuild_every steps that the
+ * context captures on first use and re-captures when a pointer, count or
+ * parameter changes.  If an atom moves more than skin/2 between rebuilds,
+ * status SKIN is set (results of that interval are not trustworthy).
+ * Requires max_pairs >= the pairs within cutoff_upper + skin. */
+int tnet_md_step(tnet_ctx *ctx, const float *weights, int n_atoms, const int32_t *z,
+                 const float *inv_mass, float *pos, float *vel, const float *box, float dt_fs,
+                 float skin, int rebuild_every, int n_steps, double *e_kin, double *e_pot,
+                 int32_t *status_dev, tnet_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNET_H */

@@ -1,0 +1,253 @@
+// C ABI entry points, context and workspace layout, and the MD step.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "internal.cuh"
+
+namespace tnet {
+
+int validate_desc(const tnet_model_desc *d) {
+    if (!d) return TNET_ERR_ARG;
+    if (d->F < 64 || d->F > 512 || d->F % 64) return TNET_ERR_ARG;
+    if (d->K < 8 || d->K > 64 || d->K % 8) return TNET_ERR_ARG;
+    if (d->L < 0 || d->L > 8) return TNET_ERR_ARG;
+    if (d->max_z < 1 || d->max_z > 128) return TNET_ERR_ARG;
+    if (!(d->cutoff_upper > d->cutoff_lower) || d->cutoff_lower < 0.f) return TNET_ERR_ARG;
+    if (d->precision != 0 && d->precision != 1) return TNET_ERR_ARG;
+    return TNET_OK;
+}
+
+int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
+    if (validate_desc(d) || N < 1 || S < 1 || E < 0) return TNET_ERR_ARG;
+    size_t off = 0;
+    auto take = [&](int64_t bytes) {
+        const size_t o = off;
+        off += ((size_t)(bytes > 0 ? bytes : 0) + 255) & ~(size_t)255;
+        return o;
+    };
+    const int64_t F = d->F, K = d->K, NL = d->L, Z = d->max_z;
+    const int64_t n9 = 9LL * N * F;
+    const int64_t cells = 2LL * N + 8LL * S + 64;
+    const int64_t U = E / 2 + 1;
+    const int64_t f = 4, i = 4;
+    L->node9 = n9;
+    L->cells = cells;
+    L->maxU = U;
+    int64_t big = N + 1;
+    if (cells + 1 > big) big = cells + 1;
+    if (S + 1 > big) big = S + 1;
+    // neighbor search
+    L->sys_start = take(i * S);
+    L->sys_end = take(i * S);
+    L->sysinfo = take(sizeof(SysInfo) * S);
+    L->sys_ncell = take(i * (S + 1));
+    L->cell_count = take(i * (cells + 1));
+    L->cell_start = take(i * (cells + 1));
+    L->cell_fill = take(i * cells);
+    L->cell_of = take(i * N);
+    L->sorted = take(i * N);
+    L->spos = take(16LL * N);
+    L->rowcnt = take(i * (N + 1));
+    L->scan_tmp = take(i * (big / 4096 + 16));
+    // graph prep
+    L->rev = take(i * E);
+    L->pair_of = take(i * E);
+    L->uedge = take(8 * U);
+    L->ucnt = take(i * (N + 1));
+    L->nu = take(i * 4);
+    // node buffers
+    L->Ta = take(f * Z * F);
+    L->Tb = take(f * Z * F);
+    L->Xraw = take(f * n9);
+    L->Uemb = take(f * n9);
+    L->n0 = take(f * N * F);
+    L->as1 = take(f * N * 2 * F);
+    L->hs1 = take(f * N * 2 * F);
+    L->as2 = take(f * N * 3 * F);
+    L->s = take(f * N * 3 * F);
+    L->ln0 = take(8LL * N);
+    L->Xin = take(f * n9 * (NL > 0 ? NL : 1));
+    L->qn = take(f * N * F * NL);
+    L->Xn = take(f * n9 * NL);
+    L->Y = take(f * n9 * NL);
+    L->M = take(f * n9 * NL);
+    L->Tn = take(f * n9 * NL);
+    L->dX = take(f * n9 * NL);
+    L->Xfin = take(f * n9);
+    L->h = take(f * N * 3 * F);
+    L->hn = take(f * N * 3 * F);
+    L->lno = take(8LL * N);
+    L->ao = take(f * N * F);
+    L->o = take(f * N * F);
+    L->at = take(f * N * F / 2);
+    L->t = take(f * N * F / 2);
+    L->Ei = take(f * N);
+    // edge MLP
+    L->eu = take(f * U * K);
+    L->phiu = take(f * U);
+    L->a1 = take(f * U * F);
+    L->h1 = take(f * U * F);
+    L->a2 = take(f * U * 2 * F);
+    L->h2 = take(f * U * 2 * F);
+    L->a3 = take(f * U * 3 * F);
+    L->g = take(f * U * 3 * F);
+    // reverse pass
+    L->gXa = take(f * n9);
+    L->gXb = take(f * n9);
+    L->gdX = take(f * n9);
+    L->gTn = take(f * n9);
+    L->gM = take(f * n9);
+    L->gY = take(f * n9);
+    L->gat = take(f * N * F / 2);
+    L->gao = take(f * N * F);
+    L->ghn = take(f * N * 3 * F);
+    L->gh = take(f * N * 3 * F);
+    L->gU = take(f * n9);
+    L->gas2 = take(f * N * 3 * F);
+    L->gas1 = take(f * N * 2 * F);
+    L->gn0 = take(f * N * F);
+    L->gq0 = take(f * N * F);
+    L->gg = take(f * U * 3 * F);
+    L->ga2 = take(f * U * 2 * F);
+    L->ga1 = take(f * U * F);
+    L->ge = take(f * U * K);
+    L->gphiu = take(f * U);
+    L->gvec = take(f * 3 * E);
+    // MD
+    L->md_row_ptr = take(i * (N + 1));
+    L->md_col = take(i * E);
+    L->md_npairs = take(8);
+    L->md_forces = take(f * 3 * N);
+    L->md_energy = take(8);
+    L->md_pos_ref = take(f * 3 * N);
+    L->md_step = take(i * 4);
+    L->total = off;
+    return TNET_OK;
+}
+
+}  // namespace tnet
+
+using namespace tnet;
+
+extern "C" {
+
+const char *tnet_status_string(int s) {
+    switch (s) {
+        case TNET_OK: return "ok";
+        case TNET_ERR_ARG: return "invalid argument";
+        case TNET_ERR_CAPACITY: return "pair capacity exceeded";
+        case TNET_ERR_BOX: return "box not lower-triangular or narrower than twice the cutoff";
+        case TNET_ERR_NAN: return "non-finite position";
+        case TNET_ERR_CUDA: return "CUDA runtime error";
+        case TNET_ERR_TIMEOUT: return "device wait timed out";
+        case TNET_ERR_WORKSPACE: return "workspace too small or misaligned";
+        case TNET_ERR_Z: return "atomic number out of range";
+        case TNET_ERR_UNSUPPORTED: return "not supported by this build";
+        case TNET_ERR_SKIN: return "an atom moved more than skin/2 between neighbor-list rebuilds";
+        default: return "unknown status";
+    }
+}
+
+int64_t tnet_weights_count(const tnet_model_desc *d) {
+    if (validate_desc(d)) return -1;
+    return weight_offsets(d, nullptr, nullptr);
+}
+
+int64_t tnet_workspace_bytes(const tnet_model_desc *d, int max_atoms, int max_systems, int64_t max_pairs) {
+    Layout L;
+    if (build_layout(d, max_atoms, max_systems, max_pairs, &L)) return -1;
+    return (int64_t)L.total;
+}
+
+int tnet_create(tnet_ctx **out, const tnet_model_desc *d, int max_atoms, int max_systems,
+                int64_t max_pairs, void *workspace, size_t workspace_bytes) {
+    if (!out) return TNET_ERR_ARG;
+    *out = nullptr;
+    Layout L;
+    int rc = build_layout(d, max_atoms, max_systems, max_pairs, &L);
+    if (rc) return rc;
+    if (max_pairs > 0x7fffffffLL || max_atoms > (1 << 28)) return TNET_ERR_ARG;
+    if (!workspace || ((uintptr_t)workspace & 255) || workspace_bytes < L.total) return TNET_ERR_WORKSPACE;
+    tnet_ctx *c = (tnet_ctx *)calloc(1, sizeof(tnet_ctx));
+    if (!c) return TNET_ERR_ARG;
+    c->d = *d;
+    c->max_atoms = max_atoms;
+    c->max_systems = max_systems;
+    c->max_pairs = max_pairs;
+    c->ws = (char *)workspace;
+    c->ws_bytes = workspace_bytes;
+    c->lay = L;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        free(c);
+        return TNET_ERR_CUDA;
+    }
+    RadialParams &rp = c->rp;
+    rp.rc = d->cutoff_upper;
+    rp.rl = d->cutoff_lower;
+    rp.K = d->K;
+    const double start = exp(-(double)(d->cutoff_upper - d->cutoff_lower));
+    rp.alpha = (float)(5.0 / (double)(d->cutoff_upper - d->cutoff_lower));
+    rp.beta = (float)pow((2.0 / d->K) * (1.0 - start), -2.0);
+    rp.mu0 = (float)start;
+    rp.dmu = (float)((1.0 - start) / (d->K - 1));
+    rc = tnet_kernel_setup(c);
+    if (rc) {
+        free(c);
+        return rc;
+    }
+    *out = c;
+    return TNET_OK;
+}
+
+int tnet_destroy(tnet_ctx *c) {
+    if (!c) return TNET_ERR_ARG;
+    if (c->md_exec) cudaGraphExecDestroy(c->md_exec);
+    free(c);
+    return TNET_OK;
+}
+
+static int check_common(tnet_ctx *c, int N, int S, const float *pos, int32_t *status) {
+    if (!c || !pos || !status) return TNET_ERR_ARG;
+    if (N < 1 || N > c->max_atoms || S < 1 || S > c->max_systems) return TNET_ERR_ARG;
+    return TNET_OK;
+}
+
+int tnet_neighbors(tnet_ctx *c, int N, int S, const float *pos, const int32_t *batch, const float *box,
+                   float cutoff, int32_t *row_ptr, int32_t *col, int64_t cap, int64_t *n_pairs_dev,
+                   int32_t *status, tnet_stream_t stream) {
+    int rc = check_common(c, N, S, pos, status);
+    if (rc) return rc;
+    if (!row_ptr || !n_pairs_dev || (cap > 0 && !col)) return TNET_ERR_ARG;
+    if (cap < 0 || cap > c->max_pairs || !(cutoff > 0.f) || !isfinite(cutoff)) return TNET_ERR_ARG;
+    if (S > 1 && !batch) return TNET_ERR_ARG;
+    return neighbors_impl(c, N, S, pos, batch, box, cutoff, row_ptr, col, cap, n_pairs_dev, status,
+                          (cudaStream_t)stream);
+}
+
+int tnet_energy_forces(tnet_ctx *c, const float *w, int N, int S, const int32_t *z, const float *pos,
+                       const int32_t *batch, const float *box, const int32_t *row_ptr,
+                       const int32_t *col, const float *seed, double *energy, float *forces,
+                       float *grad_w, int32_t *status, tnet_stream_t stream) {
+    int rc = check_common(c, N, S, pos, status);
+    if (rc) return rc;
+    if (!w || !z || !row_ptr || !col || !energy) return TNET_ERR_ARG;
+    if (S > 1 && !batch) return TNET_ERR_ARG;
+    return energy_forces_impl(c, w, N, S, z, pos, batch, box, row_ptr, col, seed, energy, forces, grad_w,
+                              status, (cudaStream_t)stream);
+}
+
+int tnet_md_step(tnet_ctx *c, const float *w, int N, const int32_t *z, const float *inv_mass, float *pos,
+                 float *vel, const float *box, float dt, float skin, int rebuild_every, int n_steps,
+                 double *e_kin, double *e_pot, int32_t *status, tnet_stream_t stream) {
+    int rc = check_common(c, N, 1, pos, status);
+    if (rc) return rc;
+    if (!w || !z || !inv_mass || !vel || !e_kin || !e_pot) return TNET_ERR_ARG;
+    if (!(dt > 0.f) || !(skin >= 0.f) || rebuild_every < 1 || n_steps < 0) return TNET_ERR_ARG;
+    return md_impl(c, w, N, z, inv_mass, pos, vel, box, dt, skin, rebuild_every, n_steps, e_kin, e_pot,
+                   status, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,288 @@
+// Internal definitions shared by the libtnet CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/tnet.h"
+
+#define TNET_CUDA_TRY(expr)                                                         \
+    do {                                                                            \
+        cudaError_t e_ = (expr);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            fprintf(stderr, "libtnet: %s failed: %s (%s:%d)\n", #expr,              \
+                    cudaGetErrorString(e_), __FILE__, __LINE__);                    \
+            return TNET_ERR_CUDA;                                                   \
+        }                                                                           \
+    } while (0)
+
+#define TNET_LAUNCH_CHECK() TNET_CUDA_TRY(cudaGetLastError())
+
+namespace tnet {
+
+constexpr int kMaxCellsPerAtom = 2;   // cell budget: 2 cells per atom + 8 per system + 64
+constexpr int kMaxRowSorted = 1024;   // longest CSR row sorted in shared memory
+
+// First device-detected error wins.
+__device__ __forceinline__ void set_status(int32_t *st, int code) {
+    if (st) atomicCAS(st, 0, code);
+}
+
+// Per-system cell grid (one cell list per system; cells never mix systems).
+struct SysInfo {
+    float origin[3];    // lower corner of the grid
+    float inv_cell[3];  // 1 / cell width along x, y, z
+    float L[3];         // periodic box lengths (rectangular); 0 when not periodic
+    int nc[3];          // cells along x, y, z (>= 1)
+    int cell_off;       // first global cell index of this system
+    int pbc;            // 1 if periodic
+    int pad[2];
+};
+
+// ---------------------------------------------------------------------------
+// Compact rank-2 tensor coordinates.  A 3x3 feature X = i*Id + [a]_x + S is
+// stored as 9 coordinates v = (i, ax, ay, az, sxx, syy, sxy, sxz, syz) with
+// S symmetric-traceless (szz = -sxx - syy) and [a]_x the skew matrix with
+// [a]_x w = a x w.  The I/A/S parts are coordinate groups {0}, {1,2,3},
+// {4..8}; channel mixing acts on every coordinate alike.
+//
+// Memory layout of a node tensor buffer for N atoms and F channels: three
+// row planes of F floats, I rows [0,N) (row n), A rows [N,4N) (row N+3n+k),
+// S rows [4N,9N) (row 4N+5n+k).  A class-p mixing is one GEMM over a
+// contiguous block of rows.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t crow(int n, int k, int N) {
+    return k == 0 ? (int64_t)n : (k < 4 ? (int64_t)N + 3LL * n + (k - 1) : 4LL * N + 5LL * n + (k - 4));
+}
+
+__device__ __forceinline__ void load_coords(const float *__restrict__ T, int n, int c, int N, int F,
+                                            float v[9]) {
+    const float *pI = T + (int64_t)n * F + c;
+    const float *pA = T + ((int64_t)N + 3LL * n) * F + c;
+    const float *pS = T + (4LL * N + 5LL * n) * F + c;
+    v[0] = pI[0];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[1 + k] = pA[(int64_t)k * F];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[4 + k] = pS[(int64_t)k * F];
+}
+
+__device__ __forceinline__ void store_coords(float *__restrict__ T, int n, int c, int N, int F,
+                                             const float v[9]) {
+    float *pI = T + (int64_t)n * F + c;
+    float *pA = T + ((int64_t)N + 3LL * n) * F + c;
+    float *pS = T + (4LL * N + 5LL * n) * F + c;
+    pI[0] = v[0];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) pA[(int64_t)k * F] = v[1 + k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) pS[(int64_t)k * F] = v[4 + k];
+}
+
+// coordinates -> row-major 3x3
+__device__ __forceinline__ void expand(const float v[9], float m[9]) {
+    const float i = v[0], ax = v[1], ay = v[2], az = v[3];
+    const float sxx = v[4], syy = v[5], sxy = v[6], sxz = v[7], syz = v[8];
+    m[0] = i + sxx; m[1] = sxy - az; m[2] = sxz + ay;
+    m[3] = sxy + az; m[4] = i + syy; m[5] = syz - ax;
+    m[6] = sxz - ay; m[7] = syz + ax; m[8] = i - sxx - syy;
+}
+
+// row-major 3x3 -> coordinates of its I, A, S parts
+__device__ __forceinline__ void decomp(const float m[9], float v[9]) {
+    const float i = (m[0] + m[4] + m[8]) * (1.0f / 3.0f);
+    v[0] = i;
+    v[1] = 0.5f * (m[7] - m[5]);
+    v[2] = 0.5f * (m[2] - m[6]);
+    v[3] = 0.5f * (m[3] - m[1]);
+    v[4] = m[0] - i;
+    v[5] = m[4] - i;
+    v[6] = 0.5f * (m[1] + m[3]);
+    v[7] = 0.5f * (m[2] + m[6]);
+    v[8] = 0.5f * (m[5] + m[7]);
+}
+
+// gradient w.r.t. coordinates of f(expand(v)) given G = df/dm (transpose of expand)
+__device__ __forceinline__ void expand_T(const float G[9], float g[9]) {
+    g[0] = G[0] + G[4] + G[8];
+    g[1] = G[7] - G[5];
+    g[2] = G[2] - G[6];
+    g[3] = G[3] - G[1];
+    g[4] = G[0] - G[8];
+    g[5] = G[4] - G[8];
+    g[6] = G[1] + G[3];
+    g[7] = G[2] + G[6];
+    g[8] = G[5] + G[7];
+}
+
+// gradient w.r.t. the matrix of f(decomp(m)) given g = df/dv (transpose of decomp)
+__device__ __forceinline__ void decomp_T(const float g[9], float G[9]) {
+    const float dg = (g[0] - g[4] - g[5]) * (1.0f / 3.0f);
+    G[0] = dg + g[4];
+    G[4] = dg + g[5];
+    G[8] = dg;
+    G[1] = 0.5f * (g[6] - g[3]);
+    G[3] = 0.5f * (g[6] + g[3]);
+    G[2] = 0.5f * (g[7] + g[2]);
+    G[6] = 0.5f * (g[7] - g[2]);
+    G[5] = 0.5f * (g[8] - g[1]);
+    G[7] = 0.5f * (g[8] + g[1]);
+}
+
+// squared Frobenius norm of expand(v)
+__device__ __forceinline__ float cnorm(const float v[9]) {
+    const float sxx = v[4], syy = v[5], szz = -(v[4] + v[5]);
+    return 3.0f * v[0] * v[0] + 2.0f * (v[1] * v[1] + v[2] * v[2] + v[3] * v[3]) + sxx * sxx +
+           syy * syy + szz * szz + 2.0f * (v[6] * v[6] + v[7] * v[7] + v[8] * v[8]);
+}
+
+// d cnorm / d v
+__device__ __forceinline__ void cnorm_grad(const float v[9], float g[9]) {
+    g[0] = 6.0f * v[0];
+    g[1] = 4.0f * v[1];
+    g[2] = 4.0f * v[2];
+    g[3] = 4.0f * v[3];
+    g[4] = 4.0f * v[4] + 2.0f * v[5];
+    g[5] = 4.0f * v[5] + 2.0f * v[4];
+    g[6] = 4.0f * v[6];
+    g[7] = 4.0f * v[7];
+    g[8] = 4.0f * v[8];
+}
+
+// C = A B (row-major 3x3)
+__device__ __forceinline__ void mm3(const float A[9], const float B[9], float C[9]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            C[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+}
+
+// C = A^T B
+__device__ __forceinline__ void mm3_tn(const float A[9], const float B[9], float C[9]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            C[3 * r + c] = A[r] * B[c] + A[3 + r] * B[3 + c] + A[6 + r] * B[6 + c];
+}
+
+// C = A B^T
+__device__ __forceinline__ void mm3_nt(const float A[9], const float B[9], float C[9]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            C[3 * r + c] = A[3 * r] * B[3 * c] + A[3 * r + 1] * B[3 * c + 1] + A[3 * r + 2] * B[3 * c + 2];
+}
+
+__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + expf(-x)); }
+__device__ __forceinline__ float silu_grad_f(float x) {
+    const float s = 1.0f / (1.0f + expf(-x));
+    return s * (1.0f + x * (1.0f - s));
+}
+
+// ------------------------------------------------------------- geometry ---
+// Nearest periodic image of a pair vector for a rectangular box; L = 0 along
+// an axis means that axis is not periodic.
+__device__ __forceinline__ void mic(float &x, float &y, float &z, const SysInfo &s) {
+    if (s.pbc) {
+        x -= s.L[0] * rintf(x / s.L[0]);
+        y -= s.L[1] * rintf(y / s.L[1]);
+        z -= s.L[2] * rintf(z / s.L[2]);
+    }
+}
+
+// Radial part of the model: cosine cutoff phi(d), expnorm basis e_k(d) and
+// their derivatives.  Parameters precomputed on the host.
+struct RadialParams {
+    float rc, rl;       // cutoff_upper, cutoff_lower
+    float alpha, beta;  // expnorm decay and width
+    float mu0, dmu;     // centres mu_k = mu0 + k * dmu
+    int K;
+};
+
+__device__ __forceinline__ float cutoff_phi(float d, const RadialParams &p) {
+    return d < p.rc ? 0.5f * (cospif(d / p.rc) + 1.0f) : 0.0f;
+}
+__device__ __forceinline__ float cutoff_dphi(float d, const RadialParams &p) {
+    return d < p.rc ? -0.5f * 3.14159265358979f / p.rc * sinpif(d / p.rc) : 0.0f;
+}
+// k-th basis value (including the phi factor) and its d-derivative
+__device__ __forceinline__ void expnorm_k(float d, int k, const RadialParams &p, float phi, float dphi,
+                                          float &e, float &de) {
+    const float ex = expf(p.alpha * (p.rl - d));
+    const float t = ex - (p.mu0 + k * p.dmu);
+    const float rho = expf(-p.beta * t * t);
+    e = phi * rho;
+    de = dphi * rho + phi * rho * (2.0f * p.beta * t * p.alpha * ex);
+}
+
+// ------------------------------------------------------------ workspace ---
+struct Layout {
+    // neighbor search
+    size_t sys_start, sys_end, sysinfo, sys_ncell, cell_count, cell_start, cell_fill, cell_of,
+        sorted, spos, rowcnt, scan_tmp;
+    // energy / forces: graph bookkeeping
+    size_t rev, pair_of, uedge, ucnt, nu;
+    // node buffers
+    size_t Ta, Tb, Xraw, Uemb, n0, as1, hs1, as2, s, ln0;
+    size_t Xin, qn, Xn, Y, M, Tn, dX;  // per layer (stride given below)
+    size_t Xfin, h, hn, lno, ao, o, at, t, Ei;
+    // edge MLP (undirected active edges)
+    size_t eu, phiu, a1, h1, a2, h2, a3, g;
+    // backward
+    size_t gXa, gXb, gdX, gTn, gM, gY, gat, gao, ghn, gh, gU, gas2, gas1, gn0, gq0, gg, ga2, ga1, ge,
+        gphiu, gvec;
+    // MD
+    size_t md_row_ptr, md_col, md_npairs, md_forces, md_energy, md_pos_ref, md_step;
+    size_t total;
+    int64_t node9;  // floats of one [9N][F] buffer
+    int64_t cells;  // cell capacity
+    int64_t maxU;   // undirected-edge capacity
+};
+
+}  // namespace tnet
+
+struct tnet_ctx {
+    tnet_model_desc d;
+    int max_atoms, max_systems;
+    int64_t max_pairs;
+    char *ws;
+    size_t ws_bytes;
+    tnet::Layout lay;
+    tnet::RadialParams rp;
+    int device, num_sms;
+    // CUDA graph cache for tnet_md_step
+    cudaGraphExec_t md_exec;
+    const void *md_key[8];
+    int64_t md_keyi[6];
+    float md_keyf[3];
+};
+
+namespace tnet {
+int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L);
+int validate_desc(const tnet_model_desc *d);
+template <class T>
+__host__ inline T *wsp(tnet_ctx *c, size_t off) {
+    return reinterpret_cast<T *>(c->ws + off);
+}
+int scan_exclusive_i32(const int32_t *in, int32_t *out, int n, int32_t *tmp, int32_t *total_dev,
+                       int64_t *total64_dev, cudaStream_t st);
+int tnet_kernel_setup(tnet_ctx *c);
+int sys_bounds(const int32_t *batch, int N, int S, int32_t *sys_start, int32_t *sys_end,
+               int32_t *status, cudaStream_t st);
+int64_t weight_offsets(const tnet_model_desc *d, const float *base, struct Weights *w);
+int neighbors_impl(tnet_ctx *ctx, int n_atoms, int n_systems, const float *pos, const int32_t *batch,
+                   const float *box, float cutoff, int32_t *row_ptr, int32_t *col, int64_t cap,
+                   int64_t *n_pairs_dev, int32_t *status_dev, cudaStream_t st);
+int energy_forces_impl(tnet_ctx *ctx, const float *w, int n_atoms, int n_systems, const int32_t *z,
+                       const float *pos, const int32_t *batch, const float *box,
+                       const int32_t *row_ptr, const int32_t *col, const float *seed,
+                       double *energy, float *forces, float *grad_w, int32_t *status_dev,
+                       cudaStream_t st);
+int md_impl(tnet_ctx *ctx, const float *w, int n_atoms, const int32_t *z, const float *inv_mass,
+            float *pos, float *vel, const float *box, float dt, float skin, int rebuild_every,
+            int n_steps, double *e_kin, double *e_pot, int32_t *status_dev, cudaStream_t st);
+}  // namespace tnet

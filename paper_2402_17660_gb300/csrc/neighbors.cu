@@ -1,0 +1,451 @@
+// Cell-list neighbor search (Sec. 2.5.1) and device-wide exclusive scans.
+//
+// Differences from the paper's engine, by design: one cell list per system
+// (cells keyed by (system, cell)) instead of a single list for the whole
+// batch, so systems never test each other's atoms (the paper notes its
+// shared list degrades with batch size); the output is a receiver-sorted
+// CSR with ascending columns and an exact count instead of a -1 padded pair
+// list; overflow is reported in a device status word with the needed size.
+#include "internal.cuh"
+
+namespace tnet {
+
+// ------------------------------------------------------------------ scan ---
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *total, int32_t *smem) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t w = lane < (int)(blockDim.x >> 5) ? smem[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        smem[lane] = w;  // inclusive warp prefix
+    }
+    __syncthreads();
+    const int32_t warp_excl = wid ? smem[wid - 1] : 0;
+    *total = smem[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_excl + x - v;
+}
+
+__global__ void k_scan_tiles(const int32_t *__restrict__ in, int32_t *__restrict__ out, int n,
+                             int32_t *__restrict__ tile_sums) {
+    __shared__ int32_t sm[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    int32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : 0;
+        sum += v[k];
+    }
+    int32_t total;
+    int32_t run = block_exclusive_scan(sum, &total, sm);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// single block: exclusive scan of the tile sums (nt <= kScanTile)
+__global__ void k_scan_top(int32_t *__restrict__ tile_sums, int nt, int32_t *__restrict__ grand) {
+    __shared__ int32_t sm[32];
+    const int base = threadIdx.x * kScanItems;
+    int32_t v[kScanItems];
+    int32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < nt) ? tile_sums[base + k] : 0;
+        sum += v[k];
+    }
+    int32_t total;
+    int32_t run = block_exclusive_scan(sum, &total, sm);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < nt) tile_sums[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) *grand = total;
+}
+
+__global__ void k_scan_add(int32_t *__restrict__ out, int n, const int32_t *__restrict__ tile_sums,
+                           const int32_t *__restrict__ grand, int32_t *__restrict__ total_dev,
+                           int64_t *__restrict__ total64_dev) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += tile_sums[i / kScanTile];
+    if (i == 0) {
+        out[n] = *grand;
+        if (total_dev) *total_dev = *grand;
+        if (total64_dev) *total64_dev = *grand;
+    }
+}
+
+// out[0..n] = exclusive scan of in[0..n), out[n] = total.  tmp needs
+// ceil(n / 4096) + 1 ints.  n <= 4096 * 4096.
+int scan_exclusive_i32(const int32_t *in, int32_t *out, int n, int32_t *tmp, int32_t *total_dev,
+                       int64_t *total64_dev, cudaStream_t st) {
+    const int nt = (n + kScanTile - 1) / kScanTile;
+    if (nt > kScanTile) return TNET_ERR_ARG;
+    const int ntl = nt > 0 ? nt : 1;
+    if (n > 0) k_scan_tiles<<<nt, kScanThreads, 0, st>>>(in, out, n, tmp);
+    else TNET_CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(int32_t), st));
+    k_scan_top<<<1, kScanThreads, 0, st>>>(tmp, ntl, tmp + ntl);
+    k_scan_add<<<(n + 255) / 256 + 1, 256, 0, st>>>(out, n, tmp, tmp + ntl, total_dev, total64_dev);
+    TNET_LAUNCH_CHECK();
+    return TNET_OK;
+}
+
+// --------------------------------------------------------------- systems ---
+__global__ void k_sys_bounds(const int32_t *__restrict__ batch, int N, int S,
+                             int32_t *__restrict__ sys_start, int32_t *__restrict__ sys_end,
+                             int32_t *status) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int b = batch ? batch[n] : 0;
+    if (b < 0 || b >= S) {
+        set_status(status, TNET_ERR_ARG);
+        return;
+    }
+    const int bp = (n > 0) ? (batch ? batch[n - 1] : 0) : -1;
+    const int bn = (n + 1 < N) ? (batch ? batch[n + 1] : 0) : S;
+    if (bp > b) set_status(status, TNET_ERR_ARG);  // not sorted
+    if (bp != b) sys_start[b] = n;
+    if (bn != b) sys_end[b] = n + 1;
+}
+
+int sys_bounds(const int32_t *batch, int N, int S, int32_t *sys_start, int32_t *sys_end,
+               int32_t *status, cudaStream_t st) {
+    k_sys_bounds<<<(N + 255) / 256, 256, 0, st>>>(batch, N, S, sys_start, sys_end, status);
+    TNET_LAUNCH_CHECK();
+    return TNET_OK;
+}
+
+// One block per system: bounding box, finiteness, box checks and cell grid.
+__global__ void k_sys_setup(const float *__restrict__ pos, const float *__restrict__ box, float cutoff,
+                            const int32_t *__restrict__ sys_start, const int32_t *__restrict__ sys_end,
+                            SysInfo *__restrict__ info, int32_t *__restrict__ ncell, int32_t *status) {
+    const int s = blockIdx.x;
+    const int a0 = sys_start[s], a1 = sys_end[s];
+    float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+    int bad = 0;
+    for (int n = a0 + threadIdx.x; n < a1; n += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float x = pos[3LL * n + k];
+            if (!isfinite(x)) bad = 1;
+            lo[k] = fminf(lo[k], x);
+            hi[k] = fmaxf(hi[k], x);
+        }
+    }
+    __shared__ float slo[3][32], shi[3][32];
+    __shared__ int sbad;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    if (bad) atomicOr(&sbad, 1);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float l = lo[k], h = hi[k];
+        for (int o = 16; o; o >>= 1) {
+            l = fminf(l, __shfl_xor_sync(0xffffffffu, l, o));
+            h = fmaxf(h, __shfl_xor_sync(0xffffffffu, h, o));
+        }
+        if (lane == 0) {
+            slo[k][wid] = l;
+            shi[k][wid] = h;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const int nw = blockDim.x >> 5;
+    for (int k = 0; k < 3; ++k) {
+        for (int w = 1; w < nw; ++w) {
+            slo[k][0] = fminf(slo[k][0], slo[k][w]);
+            shi[k][0] = fmaxf(shi[k][0], shi[k][w]);
+        }
+    }
+    SysInfo si;
+    const int na = a1 - a0;
+    if (sbad) set_status(status, TNET_ERR_NAN);
+    if (box) {
+        const float *B = box + 9LL * s;
+        si.pbc = 1;
+        if (B[1] != 0.f || B[2] != 0.f || B[5] != 0.f || B[3] != 0.f || B[6] != 0.f || B[7] != 0.f) {
+            // only rectangular boxes are implemented (lower-triangular input
+            // with non-zero b_x, c_x or c_y is a triclinic box)
+            set_status(status, (B[1] != 0.f || B[2] != 0.f || B[5] != 0.f) ? TNET_ERR_BOX
+                                                                         : TNET_ERR_UNSUPPORTED);
+        }
+        for (int k = 0; k < 3; ++k) {
+            const float L = B[4 * k];
+            if (!(L >= 2.0f * cutoff)) set_status(status, TNET_ERR_BOX);
+            si.L[k] = L;
+            si.origin[k] = 0.f;
+            int nc = (L > 0.f) ? (int)floorf(L / cutoff) : 1;
+            si.nc[k] = nc < 1 ? 1 : nc;
+        }
+    } else {
+        si.pbc = 0;
+        for (int k = 0; k < 3; ++k) {
+            si.L[k] = 0.f;
+            const float ext = na > 0 ? (shi[k][0] - slo[k][0]) : 0.f;
+            si.origin[k] = na > 0 ? slo[k][0] : 0.f;
+            int nc = (ext > 0.f && isfinite(ext)) ? (int)floorf(ext / cutoff) : 1;
+            si.nc[k] = nc < 1 ? 1 : (nc > 1024 ? 1024 : nc);
+        }
+    }
+    // keep the grid no finer than ~2 cells per atom (cells only get wider)
+    const int64_t budget = 2LL * na + 8;
+    while ((int64_t)si.nc[0] * si.nc[1] * si.nc[2] > budget) {
+        int k = 0;
+        if (si.nc[1] > si.nc[k]) k = 1;
+        if (si.nc[2] > si.nc[k]) k = 2;
+        si.nc[k] = si.nc[k] / 2 > 1 ? si.nc[k] / 2 : 1;
+    }
+    for (int k = 0; k < 3; ++k) {
+        const float width = si.pbc ? si.L[k] : (na > 0 ? shi[k][0] - slo[k][0] : 0.f);
+        si.inv_cell[k] = width > 0.f ? si.nc[k] / width : 0.f;
+    }
+    si.cell_off = 0;
+    si.pad[0] = si.pad[1] = 0;
+    info[s] = si;
+    ncell[s] = na > 0 ? si.nc[0] * si.nc[1] * si.nc[2] : 0;
+}
+
+__device__ __forceinline__ int axis_cell(float x, int k, const SysInfo &s) {
+    float u = x - s.origin[k];
+    if (s.pbc) u -= s.L[k] * floorf(u / s.L[k]);
+    int c = (int)floorf(u * s.inv_cell[k]);
+    c = c < 0 ? 0 : c;
+    return c >= s.nc[k] ? s.nc[k] - 1 : c;
+}
+
+__global__ void k_bin(const float *__restrict__ pos, const int32_t *__restrict__ batch, int N,
+                      const SysInfo *__restrict__ info, const int32_t *__restrict__ cell_off,
+                      int32_t *__restrict__ cell_of, int32_t *__restrict__ cell_count, int64_t cells) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int b = batch ? batch[n] : 0;
+    const SysInfo s = info[b];
+    const int cx = axis_cell(pos[3LL * n], 0, s), cy = axis_cell(pos[3LL * n + 1], 1, s),
+              cz = axis_cell(pos[3LL * n + 2], 2, s);
+    int64_t c = cell_off[b] + ((int64_t)cx * s.nc[1] + cy) * s.nc[2] + cz;
+    if (c >= cells) c = cells - 1;  // unreachable when the budget holds
+    cell_of[n] = (int32_t)c;
+    atomicAdd(&cell_count[c], 1);
+}
+
+__global__ void k_scatter(const float *__restrict__ pos, int N, const int32_t *__restrict__ cell_of,
+                          const int32_t *__restrict__ cell_start, int32_t *__restrict__ cell_fill,
+                          int32_t *__restrict__ sorted, float4 *__restrict__ spos) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int c = cell_of[n];
+    const int slot = cell_start[c] + atomicAdd(&cell_fill[c], 1);
+    sorted[slot] = n;
+    spos[slot] = make_float4(pos[3LL * n], pos[3LL * n + 1], pos[3LL * n + 2], __int_as_float(n));
+}
+
+// distinct neighbour cells of cell c along one axis (wrapping when periodic)
+__device__ __forceinline__ int axis_neighbors(int c, int nc, int pbc, int out[3]) {
+    if (nc <= 3) {
+        for (int k = 0; k < nc; ++k) out[k] = k;
+        return nc;
+    }
+    int m = 0;
+    for (int o = -1; o <= 1; ++o) {
+        int x = c + o;
+        if (pbc) x = (x + nc) % nc;
+        else if (x < 0 || x >= nc) continue;
+        out[m++] = x;
+    }
+    return m;
+}
+
+// Visits every candidate j of atom i (same system, neighbouring cells) with
+// one warp; `fn(j, ok)` is called by all lanes in lock-step.
+template <class Fn>
+__device__ __forceinline__ void for_candidates(int i, const float *__restrict__ pos,
+                                               const int32_t *__restrict__ batch,
+                                               const SysInfo *__restrict__ info,
+                                               const int32_t *__restrict__ cell_off,
+                                               const int32_t *__restrict__ cell_start,
+                                               const float4 *__restrict__ spos, float rc2, Fn fn) {
+    const int lane = threadIdx.x & 31;
+    const int b = batch ? batch[i] : 0;
+    const SysInfo s = info[b];
+    const float xi = pos[3LL * i], yi = pos[3LL * i + 1], zi = pos[3LL * i + 2];
+    const int cx = axis_cell(xi, 0, s), cy = axis_cell(yi, 1, s), cz = axis_cell(zi, 2, s);
+    int nx[3], ny[3], nz[3];
+    const int mx = axis_neighbors(cx, s.nc[0], s.pbc, nx);
+    const int my = axis_neighbors(cy, s.nc[1], s.pbc, ny);
+    const int mz = axis_neighbors(cz, s.nc[2], s.pbc, nz);
+    const int off = cell_off[b];
+    for (int a = 0; a < mx; ++a)
+        for (int bb = 0; bb < my; ++bb)
+            for (int cc = 0; cc < mz; ++cc) {
+                const int cell = off + (nx[a] * s.nc[1] + ny[bb]) * s.nc[2] + nz[cc];
+                const int p0 = cell_start[cell], p1 = cell_start[cell + 1];
+                for (int p = p0; p < p1; p += 32) {
+                    bool ok = false;
+                    int j = -1;
+                    if (p + lane < p1) {
+                        const float4 q = spos[p + lane];
+                        j = __float_as_int(q.w);
+                        float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+                        mic(dx, dy, dz, s);
+                        const float d2 = dx * dx + dy * dy + dz * dz;
+                        ok = (j != i) && (d2 < rc2);
+                    }
+                    fn(j, ok);
+                }
+            }
+}
+
+__global__ void k_pair_count(const float *__restrict__ pos, const int32_t *__restrict__ batch, int N,
+                             const SysInfo *__restrict__ info, const int32_t *__restrict__ cell_off,
+                             const int32_t *__restrict__ cell_start, const float4 *__restrict__ spos,
+                             float rc2, int32_t *__restrict__ rowcnt) {
+    const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (i >= N) return;
+    int cnt = 0;
+    for_candidates(i, pos, batch, info, cell_off, cell_start, spos, rc2, [&](int j, bool ok) {
+        cnt += __popc(__ballot_sync(0xffffffffu, ok));
+    });
+    if ((threadIdx.x & 31) == 0) rowcnt[i] = cnt;
+}
+
+__global__ void k_cap_check(const int64_t *__restrict__ n_pairs, int64_t cap, int32_t *status) {
+    if (*n_pairs > cap) set_status(status, TNET_ERR_CAPACITY);
+}
+
+constexpr int kFillWarps = 4;
+
+__global__ void __launch_bounds__(kFillWarps * 32)
+k_pair_fill(const float *__restrict__ pos, const int32_t *__restrict__ batch, int N,
+            const SysInfo *__restrict__ info, const int32_t *__restrict__ cell_off,
+            const int32_t *__restrict__ cell_start, const float4 *__restrict__ spos, float rc2,
+            const int32_t *__restrict__ row_ptr, int32_t *__restrict__ col, int64_t cap) {
+    __shared__ int32_t buf[kFillWarps][kMaxRowSorted];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kFillWarps + w;
+    if (i >= N) return;
+    const int64_t r0 = row_ptr[i];
+    const int rlen = row_ptr[i + 1] - row_ptr[i];
+    int32_t *sb = buf[w];
+    const bool in_smem = rlen <= kMaxRowSorted;
+    int cnt = 0;
+    for_candidates(i, pos, batch, info, cell_off, cell_start, spos, rc2, [&](int j, bool ok) {
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        const int slot = cnt + __popc(m & ((1u << lane) - 1u));
+        if (ok) {
+            if (in_smem) sb[slot] = j;
+            else if (r0 + slot < cap) col[r0 + slot] = j;
+        }
+        cnt += __popc(m);
+    });
+    __syncwarp();
+    if (in_smem) {
+        int P = 1;
+        while (P < cnt) P <<= 1;
+        for (int k = cnt + lane; k < P; k += 32) sb[k] = 0x7fffffff;
+        __syncwarp();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                for (int t = lane; t < P; t += 32) {
+                    const int u = t ^ jj;
+                    if (u > t) {
+                        const int32_t a = sb[t], b = sb[u];
+                        const bool up = (t & k) == 0;
+                        if ((a > b) == up) {
+                            sb[t] = b;
+                            sb[u] = a;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int k = lane; k < cnt; k += 32)
+            if (r0 + k < cap) col[r0 + k] = sb[k];
+    } else if (lane == 0 && r0 + cnt <= cap) {
+        // pathological row: sort in place in global memory
+        for (int a = 1; a < cnt; ++a) {
+            const int32_t v = col[r0 + a];
+            int b = a - 1;
+            while (b >= 0 && col[r0 + b] > v) {
+                col[r0 + b + 1] = col[r0 + b];
+                --b;
+            }
+            col[r0 + b + 1] = v;
+        }
+    }
+}
+
+int neighbors_impl(tnet_ctx *ctx, int N, int S, const float *pos, const int32_t *batch,
+                   const float *box, float cutoff, int32_t *row_ptr, int32_t *col, int64_t cap,
+                   int64_t *n_pairs_dev, int32_t *status, cudaStream_t st) {
+    const Layout &L = ctx->lay;
+    int32_t *sys_start = wsp<int32_t>(ctx, L.sys_start), *sys_end = wsp<int32_t>(ctx, L.sys_end);
+    SysInfo *info = wsp<SysInfo>(ctx, L.sysinfo);
+    int32_t *ncell = wsp<int32_t>(ctx, L.sys_ncell);
+    int32_t *cell_count = wsp<int32_t>(ctx, L.cell_count), *cell_start = wsp<int32_t>(ctx, L.cell_start);
+    int32_t *cell_fill = wsp<int32_t>(ctx, L.cell_fill), *cell_of = wsp<int32_t>(ctx, L.cell_of);
+    int32_t *sorted = wsp<int32_t>(ctx, L.sorted), *rowcnt = wsp<int32_t>(ctx, L.rowcnt);
+    int32_t *tmp = wsp<int32_t>(ctx, L.scan_tmp);
+    float4 *spos = wsp<float4>(ctx, L.spos);
+    const int cells = (int)L.cells;
+
+    TNET_CUDA_TRY(cudaMemsetAsync(sys_start, 0, sizeof(int32_t) * S, st));
+    TNET_CUDA_TRY(cudaMemsetAsync(sys_end, 0, sizeof(int32_t) * S, st));
+    TNET_CUDA_TRY(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * (cells + 1), st));
+    TNET_CUDA_TRY(cudaMemsetAsync(cell_fill, 0, sizeof(int32_t) * cells, st));
+    if (N > 0) {
+        k_sys_bounds<<<(N + 255) / 256, 256, 0, st>>>(batch, N, S, sys_start, sys_end, status);
+        TNET_LAUNCH_CHECK();
+    }
+    k_sys_setup<<<S, 256, 0, st>>>(pos, box, cutoff, sys_start, sys_end, info, ncell, status);
+    TNET_LAUNCH_CHECK();
+    int rc = scan_exclusive_i32(ncell, ncell, S, tmp, nullptr, nullptr, st);
+    if (rc) return rc;
+    if (N > 0) {
+        k_bin<<<(N + 255) / 256, 256, 0, st>>>(pos, batch, N, info, ncell, cell_of, cell_count, cells);
+        TNET_LAUNCH_CHECK();
+    }
+    rc = scan_exclusive_i32(cell_count, cell_start, cells, tmp, nullptr, nullptr, st);
+    if (rc) return rc;
+    if (N > 0) {
+        k_scatter<<<(N + 255) / 256, 256, 0, st>>>(pos, N, cell_of, cell_start, cell_fill, sorted, spos);
+        TNET_LAUNCH_CHECK();
+        k_pair_count<<<(int)(((int64_t)N * 32 + 255) / 256), 256, 0, st>>>(
+            pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, rowcnt);
+        TNET_LAUNCH_CHECK();
+    }
+    rc = scan_exclusive_i32(rowcnt, row_ptr, N, tmp, nullptr, n_pairs_dev, st);
+    if (rc) return rc;
+    k_cap_check<<<1, 1, 0, st>>>(n_pairs_dev, cap, status);
+    TNET_LAUNCH_CHECK();
+    if (N > 0) {
+        k_pair_fill<<<(N + kFillWarps - 1) / kFillWarps, kFillWarps * 32, 0, st>>>(
+            pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, row_ptr, col, cap);
+        TNET_LAUNCH_CHECK();
+    }
+    return TNET_OK;
+}
+
+}  // namespace tnet

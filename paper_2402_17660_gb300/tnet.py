@@ -1,0 +1,194 @@
+"""PyTorch-facing API of libtnet: device memory, streams and autograd glue.
+
+Every step of the computation runs in libtnet's CUDA kernels; this module
+only allocates tensors, packs the weight blob in the layout of
+include/tnet.h and passes pointers and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _lib
+
+# Parameter order of the weight blob (include/tnet.h).
+def blob_layout(F: int, K: int, L: int, max_z: int) -> list[tuple[str, tuple[int, ...]]]:
+    out = [("emb", (max_z, F)), ("emb2_w", (F, 2 * F)), ("emb2_b", (F,)),
+           ("dproj_w", (3, F, K)), ("dproj_b", (3, F)), ("emb_ln_g", (F,)), ("emb_ln_b", (F,)),
+           ("emb_mlp1_w", (2 * F, F)), ("emb_mlp1_b", (2 * F,)),
+           ("emb_mlp2_w", (3 * F, 2 * F)), ("emb_mlp2_b", (3 * F,)), ("emb_mix_w", (3, F, F))]
+    for l in range(L):
+        out += [(f"l{l}_mlp1_w", (F, K)), (f"l{l}_mlp1_b", (F,)),
+                (f"l{l}_mlp2_w", (2 * F, F)), (f"l{l}_mlp2_b", (2 * F,)),
+                (f"l{l}_mlp3_w", (3 * F, 2 * F)), (f"l{l}_mlp3_b", (3 * F,)),
+                (f"l{l}_mix1_w", (3, F, F)), (f"l{l}_mix2_w", (3, F, F))]
+    out += [("out_ln_g", (3 * F,)), ("out_ln_b", (3 * F,)), ("out_w", (F, 3 * F)), ("out_b", (F,)),
+            ("head1_w", (F // 2, F)), ("head1_b", (F // 2,)), ("head2_w", (1, F // 2)), ("head2_b", (1,))]
+    return out
+
+
+def pack_weights(weights: dict, F: int, K: int, L: int, max_z: int) -> np.ndarray:
+    parts = []
+    for name, shp in blob_layout(F, K, L, max_z):
+        a = np.asarray(weights[name], dtype=np.float32)
+        if a.shape != shp:
+            raise ValueError(f"{name}: shape {a.shape}, expected {shp}")
+        parts.append(a.ravel())
+    return np.concatenate(parts)
+
+
+def unpack_weights(blob, F: int, K: int, L: int, max_z: int) -> dict:
+    blob = np.asarray(blob)
+    out, o = {}, 0
+    for name, shp in blob_layout(F, K, L, max_z):
+        n = int(np.prod(shp))
+        out[name] = blob[o:o + n].reshape(shp)
+        o += n
+    return out
+
+
+def _p(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+@dataclasses.dataclass
+class NeighborList:
+    row_ptr: torch.Tensor   # [N+1] int32
+    col: torch.Tensor       # [cap] int32
+    n_pairs: torch.Tensor   # [1] int64 (device)
+    cutoff: float
+
+
+class TensorNet:
+    """One libtnet context: model shape, limits and its device workspace."""
+
+    def __init__(self, weights: dict, F=128, K=32, L=2, max_z=100, cutoff_upper=5.0, cutoff_lower=0.0,
+                 max_atoms=1024, max_systems=1, max_pairs=65536, precision=0, device="cuda"):
+        self.lib = _lib.load()
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise RuntimeError("libtnet runs on CUDA devices only")
+        self.F, self.K, self.L, self.max_z = F, K, L, max_z
+        self.cutoff = float(cutoff_upper)
+        self.desc = _lib.ModelDesc(F, K, L, max_z, cutoff_upper, cutoff_lower, precision)
+        self.max_atoms, self.max_systems, self.max_pairs = int(max_atoms), int(max_systems), int(max_pairs)
+        nbytes = self.lib.tnet_workspace_bytes(ctypes.byref(self.desc), self.max_atoms, self.max_systems,
+                                               self.max_pairs)
+        if nbytes < 0:
+            raise ValueError("invalid model shape or limits")
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=self.device)
+            base = self.workspace.data_ptr()
+            aligned = (base + 255) & ~255
+            self.ctx = ctypes.c_void_p()
+            _lib.check(self.lib.tnet_create(ctypes.byref(self.ctx), ctypes.byref(self.desc), self.max_atoms,
+                                            self.max_systems, self.max_pairs, ctypes.c_void_p(aligned),
+                                            int(nbytes)), "tnet_create")
+        self.n_weights = int(self.lib.tnet_weights_count(ctypes.byref(self.desc)))
+        self.set_weights(weights)
+        self.status = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx is not None and ctx.value:
+            self.lib.tnet_destroy(ctx)
+            self.ctx = None
+
+    def set_weights(self, weights) -> None:
+        if isinstance(weights, torch.Tensor):
+            w = weights.detach().to(self.device, torch.float32).contiguous()
+        else:
+            w = torch.from_numpy(pack_weights(weights, self.F, self.K, self.L, self.max_z)).to(self.device)
+        if w.numel() != self.n_weights:
+            raise ValueError("weight blob size mismatch")
+        self.weights = w
+
+    # -------------------------------------------------------------- status
+    def reset_status(self):
+        self.status.zero_()
+
+    def check_status(self, where="libtnet"):
+        code = int(self.status.item())
+        if code:
+            raise _lib.TnetError(code, where)
+
+    # ----------------------------------------------------------- neighbors
+    def neighbors(self, pos, batch=None, box=None, n_systems=1, cutoff=None, cap=None,
+                  out: NeighborList | None = None) -> NeighborList:
+        N = pos.shape[0]
+        cutoff = self.cutoff if cutoff is None else float(cutoff)
+        cap = self.max_pairs if cap is None else int(cap)
+        if out is None:
+            out = NeighborList(torch.empty(N + 1, dtype=torch.int32, device=self.device),
+                               torch.empty(max(cap, 1), dtype=torch.int32, device=self.device),
+                               torch.zeros(1, dtype=torch.int64, device=self.device), cutoff)
+        _lib.check(self.lib.tnet_neighbors(self.ctx, N, n_systems, _p(pos), _p(batch), _p(box),
+                                           ctypes.c_float(cutoff), _p(out.row_ptr), _p(out.col), cap,
+                                           _p(out.n_pairs), _p(self.status), _stream(self.device)),
+                   "tnet_neighbors")
+        return out
+
+    # ------------------------------------------------------- energy/forces
+    def energy_forces(self, z, pos, nl: NeighborList, batch=None, box=None, n_systems=1, forces=True,
+                      grad_weights=False, seed=None, out=None):
+        N = pos.shape[0]
+        if out is None:
+            E = torch.empty(n_systems, dtype=torch.float64, device=self.device)
+            Fo = torch.empty((N, 3), dtype=torch.float32, device=self.device) if forces else None
+            G = torch.empty(self.n_weights, dtype=torch.float32, device=self.device) if grad_weights else None
+        else:
+            E, Fo, G = out
+        _lib.check(self.lib.tnet_energy_forces(self.ctx, _p(self.weights), N, n_systems, _p(z), _p(pos),
+                                               _p(batch), _p(box), _p(nl.row_ptr), _p(nl.col), _p(seed),
+                                               _p(E), _p(Fo), _p(G), _p(self.status), _stream(self.device)),
+                   "tnet_energy_forces")
+        return E, Fo, G
+
+    # ----------------------------------------------------------------- MD
+    def md(self, z, inv_mass, pos, vel, box, dt, skin, rebuild_every, n_steps, e_kin=None, e_pot=None):
+        N = pos.shape[0]
+        e_kin = torch.empty(n_steps, dtype=torch.float64, device=self.device) if e_kin is None else e_kin
+        e_pot = torch.empty(n_steps, dtype=torch.float64, device=self.device) if e_pot is None else e_pot
+        _lib.check(self.lib.tnet_md_step(self.ctx, _p(self.weights), N, _p(z), _p(inv_mass), _p(pos), _p(vel),
+                                         _p(box), ctypes.c_float(dt), ctypes.c_float(skin), int(rebuild_every),
+                                         int(n_steps), _p(e_kin), _p(e_pot), _p(self.status),
+                                         _stream(self.device)), "tnet_md_step")
+        return e_kin, e_pot
+
+
+class EnergyFn(torch.autograd.Function):
+    """E_s(pos, weights) with gradients from libtnet's reverse pass.
+
+    forward(pos, weights, model, z, nl, batch, box, n_systems) -> E [S] f64.
+    d/dpos = -forces scaled per system by the incoming gradient; d/dweights
+    comes from a second reverse pass seeded with the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, pos, weights, model: TensorNet, z, nl, batch, box, n_systems):
+        model.set_weights(weights)
+        E, Fo, _ = model.energy_forces(z, pos.detach(), nl, batch, box, n_systems, forces=True)
+        ctx.model, ctx.args = model, (z, nl, batch, box, n_systems)
+        ctx.save_for_backward(pos, weights, Fo)
+        return E
+
+    @staticmethod
+    def backward(ctx, gE):
+        pos, weights, Fo = ctx.saved_tensors
+        z, nl, batch, box, n_systems = ctx.args
+        model = ctx.model
+        gpos = gw = None
+        if ctx.needs_input_grad[0]:
+            scale = gE.to(torch.float32)[batch.long()] if batch is not None else gE.to(torch.float32)[0]
+            gpos = -Fo * (scale[:, None] if batch is not None else scale)
+        if ctx.needs_input_grad[1]:
+            model.set_weights(weights)
+            _, _, gw = model.energy_forces(z, pos.detach(), nl, batch, box, n_systems, forces=True,
+                                           grad_weights=True, seed=gE.to(torch.float32).contiguous())
+        return gpos, gw, None, None, None, None, None, None

@@ -1,0 +1,75 @@
+"""Host-side checks of the C-ABI library (no GPU needed): the library loads,
+exports every function include/tnet.h declares, reports shapes and workspace
+sizes, and the Python blob layout agrees with the header and the
+generators."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2402_17660_gb300 import _lib, synth, tnet
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _lib.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _lib.header_functions()
+    assert {"tnet_neighbors", "tnet_energy_forces", "tnet_md_step", "tnet_create"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.SIGNATURES)
+
+
+def test_weights_count_matches_layouts(lib):
+    for F, K, L in ((128, 32, 2), (64, 8, 0), (128, 32, 1), (256, 64, 3)):
+        d = _lib.ModelDesc(F, K, L, 100, 5.0, 0.0, 0)
+        n = lib.tnet_weights_count(ctypes.byref(d))
+        spec = synth.param_spec(synth.ModelShape(F=F, K=K, L=L))
+        assert n == sum(int(np.prod(s)) for _, s in spec)
+        assert [(a, tuple(b)) for a, b in tnet.blob_layout(F, K, L, 100)] == [(a, tuple(b)) for a, b in spec]
+
+
+def test_invalid_shapes_rejected(lib):
+    for bad in ((100, 32, 2), (128, 7, 2), (128, 32, 9), (128, 32, -1)):
+        d = _lib.ModelDesc(*bad, 100, 5.0, 0.0, 0)
+        assert lib.tnet_weights_count(ctypes.byref(d)) == -1
+    d = _lib.ModelDesc(128, 32, 2, 100, 5.0, 6.0, 0)
+    assert lib.tnet_weights_count(ctypes.byref(d)) == -1
+
+
+def test_workspace_bytes(lib):
+    d = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0)
+    a = lib.tnet_workspace_bytes(ctypes.byref(d), 1000, 1, 100000)
+    b = lib.tnet_workspace_bytes(ctypes.byref(d), 2000, 1, 200000)
+    assert 0 < a < b
+    assert lib.tnet_workspace_bytes(ctypes.byref(d), 0, 1, 10) == -1
+
+
+def test_create_rejects_bad_workspace(lib):
+    d = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0)
+    ctx = ctypes.c_void_p()
+    rc = lib.tnet_create(ctypes.byref(ctx), ctypes.byref(d), 100, 1, 1000, None, 0)
+    assert rc == 7 and not ctx.value
+    rc = lib.tnet_create(ctypes.byref(ctx), ctypes.byref(d), 100, 1, 1000, ctypes.c_void_p(0x1001), 1 << 40)
+    assert rc == 7
+
+
+def test_null_context_rejected(lib):
+    assert lib.tnet_neighbors(None, 10, 1, None, None, None, ctypes.c_float(5.0), None, None, 0, None,
+                              None, None) == 1
+    assert lib.tnet_energy_forces(None, None, 1, 1, None, None, None, None, None, None, None, None, None,
+                                  None, None, None) == 1
+    assert lib.tnet_md_step(None, None, 1, None, None, None, None, None, ctypes.c_float(0.5),
+                            ctypes.c_float(1.0), 20, 10, None, None, None, None) == 1
+    assert lib.tnet_status_string(2).decode() == "pair capacity exceeded"
+
+
+def test_pack_unpack_roundtrip():
+    W = synth.init_weights(synth.ModelShape(F=64, K=8, L=1), seed=3)
+    blob = tnet.pack_weights(W, 64, 8, 1, 100)
+    back = tnet.unpack_weights(blob, 64, 8, 1, 100)
+    for k in W:
+        assert np.array_equal(back[k], W[k])

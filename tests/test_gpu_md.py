@@ -1,0 +1,84 @@
+"""GPU checks of tnet_md_step: one step equals a hand-assembled velocity
+Verlet step built from tnet_energy_forces, graph replays equal the eager
+path bit for bit, and the total energy is conserved over a short run."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2402_17660_gb300 import synth
+
+from .gpu_helpers import DEV, gpu_energy_forces, gpu_pairs, make_model, to_dev
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
+
+W = synth.init_weights(synth.ModelShape(), seed=0)
+ACC = synth.EV_PER_AMU_A2_FS2
+
+
+def _state(sys):
+    z, pos, _, box = to_dev(sys)
+    vel = torch.from_numpy(synth.maxwell_boltzmann(sys, 300.0, seed=1)).to(DEV)
+    inv_m = torch.from_numpy(1.0 / sys.masses()).to(DEV)
+    return z, pos, vel, inv_m, box
+
+
+def test_one_step_matches_velocity_verlet():
+    s = synth.workload("water3000")
+    m = make_model(W, s, max_pairs=300000)
+    z, pos, vel, inv_m, box = _state(s)
+    dt = 0.5
+    E0, F0 = gpu_energy_forces(m, s)
+    p1, v1 = pos.clone(), vel.clone()
+    m.reset_status()
+    ek, ep = m.md(z, inv_m, p1, v1, box, dt, 1.0, 20, 1)
+    torch.cuda.synchronize()
+    m.check_status("md")
+    F0t = torch.from_numpy(F0).to(DEV)
+    vh = vel + 0.5 * dt * ACC * F0t * inv_m[:, None]
+    x1 = pos + dt * vh
+    assert torch.allclose(p1, x1, rtol=0, atol=1e-5)
+    s1 = synth.System(s.name, s.z, x1.cpu().numpy(), s.batch, s.box, 1)
+    E1, F1 = gpu_energy_forces(m, s1, nl=gpu_pairs(m, s1, cutoff=6.0))
+    v_ref = vh + 0.5 * dt * ACC * torch.from_numpy(F1).to(DEV) * inv_m[:, None]
+    assert torch.allclose(v1, v_ref, rtol=0, atol=1e-5)
+    assert abs(ep[0].item() - E1[0]) <= 1e-5 * abs(E1[0]) + 1e-3
+    ke = 0.5 * np.sum(np.sum(v1.cpu().numpy().astype(np.float64) ** 2, 1) / (1.0 / s.masses())) / ACC
+    assert abs(ek[0].item() - ke) <= 1e-6 * ke
+
+
+def test_graph_replay_equals_eager():
+    s = synth.workload("water3000")
+    m = make_model(W, s, max_pairs=300000)
+    z, pos, vel, inv_m, box = _state(s)
+    pa, va = pos.clone(), vel.clone()
+    pb, vb = pos.clone(), vel.clone()
+    m.reset_status()
+    eka, epa = m.md(z, inv_m, pa, va, box, 0.5, 1.0, 10, 20)   # two graph replays
+    ekb, epb = m.md(z, inv_m, pb, vb, box, 0.5, 1.0, 10, 5)    # eager path (5 < 10)
+    ekb2, epb2 = m.md(z, inv_m, pb, vb, box, 0.5, 1.0, 10, 5)
+    torch.cuda.synchronize()
+    m.check_status("md")
+    # the eager run rebuilt at steps 0 and 5 of each call; compare with a
+    # replayed run that rebuilds at the same steps instead
+    pc, vc = pos.clone(), vel.clone()
+    ekc, epc = m.md(z, inv_m, pc, vc, box, 0.5, 1.0, 5, 10)     # graph of 5 steps, replayed twice
+    torch.cuda.synchronize()
+    assert torch.equal(pc, pb) and torch.equal(vc, vb)
+    assert torch.equal(epc[:5], epb) and torch.equal(epc[5:], epb2)
+    assert np.isfinite(epa.cpu().numpy()).all() and np.isfinite(eka.cpu().numpy()).all()
+
+
+def test_energy_conservation_short_run():
+    s = synth.workload("water3000")
+    m = make_model(W, s, max_pairs=300000)
+    z, pos, vel, inv_m, box = _state(s)
+    m.reset_status()
+    ek, ep = m.md(z, inv_m, pos, vel, box, 0.25, 1.0, 20, 200)
+    torch.cuda.synchronize()
+    m.check_status("md")
+    et = (ek + ep).cpu().numpy()
+    ke = ek.cpu().numpy()
+    drift = abs(et[-1] - et[0]) / s.n_atoms
+    fluct = np.std(ke) / s.n_atoms
+    print(f"E_tot drift per atom over 50 fs: {drift:.3e} eV; KE fluctuation per atom {fluct:.3e} eV")
+    assert drift < max(0.05 * np.std(ke), 1e-3 * s.n_atoms) / s.n_atoms

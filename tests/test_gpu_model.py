@@ -1,0 +1,176 @@
+"""GPU parity of tnet_energy_forces against the FP64 oracle: energies within
+1e-5 relative (|dE_s| <= 1e-5 max(|E_s|, sum_i |E_i|)) and forces within
+1e-4 of the RMS force, on seeded inputs; at full size, the invariances the
+model fixes and a finite-difference check of the forces."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.neighbors import neighbor_pairs
+from paper_2402_17660_gb300 import synth
+from paper_2402_17660_gb300.tnet import EnergyFn
+
+from .gpu_helpers import (DEV, E_TOL, F_TOL, RC, energy_errors, force_error, gpu_energy_forces, gpu_pairs,
+                          make_model, margin_ok, oracle_energy_forces, to_dev)
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
+
+SHAPE = synth.ModelShape()
+W = synth.init_weights(SHAPE, seed=0)
+
+
+def _compare(sys, shape=SHAPE, weights=W, seed=None):
+    m = make_model(weights, sys, shape=shape)
+    E, F = gpu_energy_forces(m, sys, seed=seed)
+    Es, Ei, Fo = oracle_energy_forces(weights, sys, shape, seed=seed)
+    e_err = energy_errors(E, Es, Ei, sys.batch)
+    f_err = force_error(F, Fo)
+    print(f"{sys.name}: N={sys.n_atoms} max rel energy err {e_err.max():.2e}, rel RMS force err {f_err:.2e}")
+    assert np.all(e_err <= E_TOL), e_err
+    assert f_err <= F_TOL, f_err
+    return m, E, F
+
+
+def _cluster(n, seed0=200):
+    for s in range(seed0, seed0 + 50):
+        c = synth.random_cluster(n, seed=s, side=None if n > 3 else 4.0)
+        if margin_ok(c):
+            return c
+    raise RuntimeError
+
+
+@pytest.mark.parametrize("n", [2, 3, 8, 64])
+def test_small_clusters(n):
+    _compare(_cluster(n))
+
+
+def test_isolated_atom_and_far_pair():
+    s = synth.System("sparse", np.array([1, 6, 8, 7], np.int32),
+                     np.array([[0, 0, 0], [20, 0, 0], [20, 4.2, 0], [0, 0, 30]], np.float32),
+                     np.zeros(4, np.int32), None, 1)
+    _compare(s)
+
+
+def test_periodic_small_box():
+    for seed in range(300, 340):
+        c = synth.random_cluster(30, seed=seed, side=10.5, min_dist=1.2)
+        c.box = (np.eye(3) * 10.5)[None].astype(np.float32)
+        if margin_ok(c):
+            break
+    _compare(c)
+
+
+def test_molecule32():
+    _compare(synth.workload("molecule32"))
+
+
+def test_batch_of_molecules_uneven_sizes():
+    s = synth.molecule_batch(48, seed=2)
+    _compare(s)
+
+
+def test_energy_seed_weights_forces():
+    s = synth.molecule_batch(5, nmin=8, nmax=30, seed=9)
+    seed = np.array([0.5, -1.0, 2.0, 0.0, 1.5])
+    _compare(s, seed=seed)
+
+
+@pytest.mark.parametrize("L", [0, 1, 3])
+def test_other_layer_counts(L):
+    shape = synth.ModelShape(L=L)
+    _compare(_cluster(40, 400), shape=shape, weights=synth.init_weights(shape, seed=1))
+
+
+def test_water3000():
+    _compare(synth.workload("water3000"))
+
+
+def test_skin_list_gives_identical_results():
+    s = synth.water_box(10, 31.04, seed=1, radii=(5.0, 6.0))
+    m = make_model(W, s, max_pairs=400000)
+    E1, F1 = gpu_energy_forces(m, s, nl=gpu_pairs(m, s, cutoff=5.0))
+    E2, F2 = gpu_energy_forces(m, s, nl=gpu_pairs(m, s, cutoff=6.0))
+    assert np.array_equal(E1, E2) and np.array_equal(F1, F2)
+
+
+def test_deterministic():
+    s = synth.workload("water3000")
+    m = make_model(W, s)
+    nl = gpu_pairs(m, s)
+    E1, F1 = gpu_energy_forces(m, s, nl=nl)
+    E2, F2 = gpu_energy_forces(m, s, nl=nl)
+    assert np.array_equal(E1, E2) and np.array_equal(F1, F2)
+
+
+def test_bad_atomic_number_flagged():
+    s = _cluster(8)
+    s.z[3] = 120
+    m = make_model(W, s)
+    z, pos, batch, box = to_dev(s)
+    nl = gpu_pairs(m, s)
+    m.reset_status()
+    m.energy_forces(z, pos, nl)
+    torch.cuda.synchronize()
+    assert int(m.status.item()) == 8
+
+
+def test_autograd_function_positions():
+    s = _cluster(16, 500)
+    m = make_model(W, s)
+    z, pos, batch, box = to_dev(s)
+    nl = gpu_pairs(m, s)
+    p = pos.clone().requires_grad_(True)
+    E = EnergyFn.apply(p, m.weights, m, z, nl, None, None, 1)
+    (3.0 * E.sum()).backward()
+    _, Fo = gpu_energy_forces(m, s, nl=nl)
+    assert torch.allclose(p.grad.cpu(), torch.from_numpy(-3.0 * Fo), rtol=0, atol=1e-6)
+
+
+# ------------------------------------------------------------ full size ---
+def _axis_permuted(sys, perm):
+    s = synth.System(sys.name + "perm", sys.z.copy(), np.ascontiguousarray(sys.pos[:, perm]), sys.batch.copy(),
+                     None if sys.box is None else sys.box.copy(), sys.n_systems)
+    return s
+
+
+@pytest.mark.parametrize("name", ["solvated24k", "water96k"])
+def test_full_size_invariances(name):
+    s = synth.workload(name)
+    m = make_model(W, s, max_pairs=70 * s.n_atoms)
+    E0, F0 = gpu_energy_forces(m, s)
+    rmsF = np.sqrt(np.mean(np.sum(F0 ** 2, 1)))
+    # net force vanishes (E depends only on pair vectors)
+    assert np.linalg.norm(F0.astype(np.float64).sum(0)) <= 1e-5 * rmsF * s.n_atoms
+    # cubic box: permuting the axes is a symmetry (E invariant, F permuted)
+    perm = [1, 2, 0]
+    E1, F1 = gpu_energy_forces(m, _axis_permuted(s, perm))
+    scale = np.abs(E0).max()
+    assert abs(E1[0] - E0[0]) <= 1e-5 * max(scale, 1.0)
+    assert force_error(F1, F0[:, perm]) <= F_TOL
+    # lattice shifts of a third of the atoms leave everything unchanged
+    sh = synth.System(s.name, s.z, s.pos.copy(), s.batch, s.box, 1)
+    L = float(s.box[0, 0, 0])
+    sh.pos[::3] += np.array([L, -L, 2 * L], np.float32)
+    E2, F2 = gpu_energy_forces(m, sh)
+    assert abs(E2[0] - E0[0]) <= 1e-5 * max(scale, 1.0)
+    assert force_error(F2, F0) <= F_TOL
+
+
+@pytest.mark.parametrize("name", ["water3000", "solvated24k"])
+def test_full_size_directional_finite_difference(name):
+    """dE/dh along a random displacement field equals -sum F . v (energy
+    reduced in FP64 on the GPU; positions displaced by +-h)."""
+    s = synth.workload(name)
+    m = make_model(W, s, max_pairs=100 * s.n_atoms)
+    E0, F0 = gpu_energy_forces(m, s)
+    v = np.random.default_rng(0).standard_normal(s.pos.shape)
+    h = 2e-3
+    sp = synth.System(s.name, s.z, (s.pos + h * v).astype(np.float32), s.batch, s.box, 1)
+    sm = synth.System(s.name, s.z, (s.pos - h * v).astype(np.float32), s.batch, s.box, 1)
+    dp = (sp.pos.astype(np.float64) - sm.pos.astype(np.float64))   # the displacement actually applied
+    Ep, _ = gpu_energy_forces(m, sp, nl=gpu_pairs(m, sp, cutoff=6.0))
+    Em, _ = gpu_energy_forces(m, sm, nl=gpu_pairs(m, sm, cutoff=6.0))
+    fd = Ep[0] - Em[0]
+    an = -np.sum(F0.astype(np.float64) * dp)
+    print(f"{name}: FD {fd:.6e} analytic {an:.6e}")
+    assert abs(fd - an) <= 2e-3 * abs(an)

@@ -1,0 +1,154 @@
+"""GPU parity of tnet_neighbors against the oracle's brute-force pairs: the
+pair set must match exactly (rows sorted, columns ascending), plus the
+device-side error paths (capacity, box, NaN)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.neighbors import neighbor_pairs, neighbor_rows
+from paper_2402_17660_gb300 import synth
+
+from .gpu_helpers import RC, csr_to_pairs, gpu_pairs, make_model, margin_ok
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
+
+W = synth.init_weights(synth.ModelShape(), seed=0)
+
+
+def _check_exact(sys, cutoff=RC, cap=None):
+    m = make_model(W, sys, max_pairs=None, cutoff=cutoff)
+    nl = gpu_pairs(m, sys, cutoff=cutoff, cap=cap)
+    assert int(m.status.item()) == 0
+    gi, gj = csr_to_pairs(nl)
+    oi, oj = neighbor_pairs(sys.pos, sys.batch, sys.box, cutoff)
+    assert int(nl.n_pairs.item()) == len(oi)
+    assert np.array_equal(gi, oi) and np.array_equal(gj, oj)
+    return nl
+
+
+def _pbc_case(seed, n=40, L=(10.5, 11.0, 12.25)):
+    rng = np.random.default_rng(seed)
+    L = np.array(L)
+    pos = rng.uniform(-0.5, 1.5, (n, 3)) * L
+    pos[0] = [0.0, 0.0, 0.0]
+    pos[1] = L - 1e-3
+    pos[2] = [L[0], 0.5 * L[1], 0.0]
+    pos[3] = [-L[0] + 0.7, -2 * L[1] + 0.3, 3 * L[2] + 0.2]
+    s = synth.System(f"pbc{seed}", rng.choice([1, 6, 7, 8], n).astype(np.int32), pos.astype(np.float32),
+                     np.zeros(n, np.int32), np.diag(L)[None].astype(np.float32), 1)
+    return s
+
+
+@pytest.mark.parametrize("n", [2, 3, 8, 64, 300])
+def test_clusters_exact(n):
+    seed = 0
+    while True:
+        s = synth.random_cluster(n, seed=100 + seed, side=None if n > 3 else 4.0)
+        if margin_ok(s):
+            break
+        seed += 1
+    _check_exact(s)
+
+
+def test_pbc_edge_cases_exact():
+    done = 0
+    for seed in range(40):
+        s = _pbc_case(seed)
+        if not margin_ok(s):
+            continue
+        _check_exact(s)
+        done += 1
+        if done == 4:
+            break
+    assert done == 4
+
+
+def test_batched_boxes_exact():
+    parts = []
+    for s in range(60):
+        c = _pbc_case(s, n=25, L=(10.5 + 0.25 * (s % 4), 10.6, 11.0))
+        if margin_ok(c):
+            parts.append(c)
+        if len(parts) == 3:
+            break
+    sys = synth.System("pbcbatch", np.concatenate([p.z for p in parts]), np.concatenate([p.pos for p in parts]),
+                       np.concatenate([np.full(25, k, np.int32) for k in range(3)]),
+                       np.concatenate([p.box for p in parts]), 3)
+    _check_exact(sys)
+
+
+@pytest.mark.parametrize("name", ["molecule32", "water3000", "batch512"])
+def test_workloads_exact(name):
+    _check_exact(synth.workload(name))
+
+
+def test_skin_cutoff_exact():
+    s = synth.water_box(10, 31.04, seed=1, radii=(5.0, 6.0))
+    _check_exact(s, cutoff=6.0)
+
+
+@pytest.mark.parametrize("name", ["solvated24k", "water96k"])
+def test_large_sampled_rows(name):
+    s = synth.workload(name)
+    m = make_model(W, s, max_pairs=120 * s.n_atoms)
+    nl = gpu_pairs(m, s)
+    assert int(m.status.item()) == 0
+    gi, gj = csr_to_pairs(nl)
+    rp = nl.row_ptr.cpu().numpy()
+    rows = np.random.default_rng(0).choice(s.n_atoms, 256, replace=False)
+    ref = neighbor_rows(s.pos, s.batch, s.box, RC, rows)
+    for a, r in zip(rows, ref):
+        assert np.array_equal(gj[rp[a]:rp[a + 1]], r), a
+    # whole-list properties: no self pairs, symmetric, rows ascending
+    assert np.all(gi != gj)
+    key = gi * s.n_atoms + gj
+    assert np.all(np.diff(key) > 0)
+    rkey = np.sort(gj * s.n_atoms + gi)
+    assert np.array_equal(rkey, key)
+
+
+def test_capacity_overflow_reports_needed_size():
+    s = synth.workload("water3000")
+    oi, _ = neighbor_pairs(s.pos, s.batch, s.box, RC)
+    m = make_model(W, s, max_pairs=len(oi) + 100)
+    cap = len(oi) // 2
+    nl = gpu_pairs(m, s, cap=cap)
+    assert int(m.status.item()) == 2
+    assert int(nl.n_pairs.item()) == len(oi)
+    counts = np.bincount(oi, minlength=s.n_atoms)
+    assert np.array_equal(np.diff(nl.row_ptr.cpu().numpy()), counts)
+
+
+def test_box_too_small_and_nan_flagged():
+    s = synth.random_cluster(20, seed=1)
+    s.box = (np.eye(3) * 9.0)[None].astype(np.float32)
+    m = make_model(W, s, max_pairs=1000)
+    gpu_pairs(m, s)
+    assert int(m.status.item()) == 3
+    s2 = synth.random_cluster(20, seed=2)
+    s2.pos[5, 1] = np.nan
+    m2 = make_model(W, synth.random_cluster(20, seed=2), max_pairs=1000)
+    gpu_pairs(m2, s2)
+    assert int(m2.status.item()) == 4
+
+
+def test_deterministic_and_graph_capturable():
+    s = synth.workload("water3000")
+    m = make_model(W, s)
+    a = gpu_pairs(m, s)
+    ga = a.col.clone()
+    from .gpu_helpers import to_dev
+    _, pos, _, box = to_dev(s)
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        m.reset_status()
+        out = m.neighbors(pos, None, box)          # warm-up on the side stream
+        stream.synchronize()
+        with torch.cuda.graph(g, stream=stream):
+            out = m.neighbors(pos, None, box, out=out)
+    out.col.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    n = int(a.n_pairs.item())
+    assert torch.equal(out.col[:n], ga[:n])
