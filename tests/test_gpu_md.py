@@ -11,7 +11,7 @@ from .gpu_helpers import DEV, gpu_energy_forces, gpu_pairs, make_model, to_dev
 
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
 
-W = synth.init_weights(synth.ModelShape(), seed=0)
+W = synth.md_weights(synth.ModelShape(), seed=0)
 ACC = synth.EV_PER_AMU_A2_FS2
 
 
