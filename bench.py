@@ -1,0 +1,436 @@
+#!/usr/bin/env python
+"""TensorNet energy+force benchmark on GB300.
+
+One step = one pass of the whole hot path over the workload: cell-list
+neighbor search, TensorNet energy (per system, FP64 reduction) and forces
+through the hand-written reverse pass.  The step is captured once in a CUDA
+graph and replayed; L2 is flushed (a 256 MB write) before every timed step
+and the flush is outside the timed events.
+
+Prints ONE JSON line (rank 0).  Metric: energy+force evaluations/s of the
+whole job (replicas across ranks; the workload does not shard).
+--impl reference times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TensorNet energy+force evals/s and ns/day vs atoms; % of HBM/tensor roofline"
+UNIT = "evals/s"
+FS_PER_STEP = 0.5            # MD time step used for the ns/day figure
+FP32_LANES_PER_SM = 128      # FP32 FMA lanes per SM (4 partitions x 32)
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water3000")
+    ap.add_argument("--precision", default="fp32", choices=["fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ utils ---
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_workload(name):
+    from paper_2402_17660_gb300 import synth
+    return synth.workload(name)
+
+
+def carve_cluster(sys_, n_target, seed=0):
+    """Atoms (whole molecules of 3 for water boxes) nearest the box centre,
+    unwrapped into one non-periodic cluster: a bounded oracle sample."""
+    from paper_2402_17660_gb300 import synth
+    pos = sys_.pos.astype(np.float64)
+    if sys_.box is not None:
+        L = np.diag(sys_.box[0]).astype(np.float64)
+        c = L / 2
+        d = pos - c
+        d -= L * np.round(d / L)
+        pos = c + d
+    else:
+        c = pos.mean(0)
+    r = np.linalg.norm(pos - c, axis=1)
+    idx = np.sort(np.argsort(r)[:n_target])
+    return synth.System(sys_.name + f"_sample{n_target}", sys_.z[idx], pos[idx].astype(np.float32),
+                        np.zeros(len(idx), np.int32), None, 1)
+
+
+def oracle_eval_seconds(sys_, W, reps=1):
+    from oracle.neighbors import neighbor_pairs
+    from oracle.tensornet import TensorNet as Oracle
+    o = Oracle(W)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        pr = neighbor_pairs(sys_.pos, sys_.batch, sys_.box, 5.0)
+        o.energy_forces(sys_.z, sys_.pos, sys_.batch, sys_.box, pairs=pr, n_systems=sys_.n_systems)
+    return (time.perf_counter() - t0) / reps
+
+
+def cpu_baseline(sys_, W):
+    """The oracle as it stands on the host cores, on a bounded sample."""
+    if sys_.n_atoms <= 3000:
+        t = oracle_eval_seconds(sys_, W)
+        return {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                "sample": f"one full FP64 oracle energy+force evaluation of {sys_.name} "
+                          f"(brute-force pairs + forward + analytic reverse pass), {t:.1f} s"}
+    n = 1500
+    sample = carve_cluster(sys_, n)
+    t = oracle_eval_seconds(sample, W)
+    scale = n / sys_.n_atoms
+    return {"value": scale / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 oracle energy+force on a {n}-atom cluster carved from {sys_.name} "
+                      f"({t:.1f} s), evals/s scaled by {n}/{sys_.n_atoms} atoms"}
+
+
+def workload_config(sys_, n_pairs, args, graph=True):
+    return {"workload": sys_.name, "n_atoms": sys_.n_atoms, "n_systems": sys_.n_systems,
+            "periodic": sys_.box is not None, "directed_pairs": int(n_pairs), "cutoff_A": 5.0,
+            "layers": 2, "channels": 128, "rbf": 32, "precision": args.precision,
+            "step": "neighbor search + energy + forces", "cuda_graph": graph,
+            "l2": "flushed (256 MB write) before every timed step"}
+
+
+# ------------------------------------------------------------- reference ---
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2402_17660_gb300 import synth
+    sys_ = load_workload(args.workload)
+    W = synth.init_weights(synth.ModelShape(), seed=0)
+    n = min(300, sys_.n_atoms)
+    sample = carve_cluster(sys_, n)
+    scale = n / sys_.n_atoms
+    for _ in range(args.warmup):
+        oracle_eval_seconds(sample, W)
+    ts = [oracle_eval_seconds(sample, W) for _ in range(args.steps)]
+    per_step = sum(ts) / len(ts)
+    value = scale / per_step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step / scale * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": sys_.name, "n_atoms": sys_.n_atoms,
+                                            "sample": f"{n}-atom cluster carved from {sys_.name}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"FP64 oracle energy+force on a {n}-atom cluster carved from "
+                                       f"{sys_.name}, evals/s scaled by {n}/{sys_.n_atoms} atoms"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ ours ---
+STAGE_WORK = {
+    # stage tag -> function(nu, N, E, F, K) giving (kind, algorithmic amount per stage instance)
+    "mlp1": lambda nu, N, E, F, K: ("flop", 2.0 * nu * K * F),
+    "mlp2": lambda nu, N, E, F, K: ("flop", 2.0 * nu * F * 2 * F),
+    "mlp3": lambda nu, N, E, F, K: ("flop", 2.0 * nu * 2 * F * 3 * F),
+    "mlp3_bwd": lambda nu, N, E, F, K: ("flop", 2.0 * nu * 3 * F * 2 * F),
+    "mlp2_bwd": lambda nu, N, E, F, K: ("flop", 2.0 * nu * 2 * F * F),
+    "mlp1_bwd": lambda nu, N, E, F, K: ("flop", 2.0 * nu * F * K),
+    # message gather: read Y and the per-pair filters once, write M once, read the CSR
+    "message": lambda nu, N, E, F, K: ("bytes", 4.0 * (2 * 9 * N * F + 3 * F * nu) + 8.0 * E),
+    "message_bwd": lambda nu, N, E, F, K: ("bytes", 4.0 * (4 * 9 * N * F + 2 * 3 * F * nu) + 8.0 * E),
+}
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    from paper_2402_17660_gb300 import _lib, synth
+    from paper_2402_17660_gb300.tnet import TensorNet
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    sys_ = load_workload(args.workload)
+    shape = synth.ModelShape()
+    W = synth.init_weights(shape, seed=0)
+    N = sys_.n_atoms
+    cap = int(75 * N) + 1024
+    m = TensorNet(W, max_atoms=N, max_systems=sys_.n_systems, max_pairs=cap, device=dev)
+    lib = m.lib
+    z = torch.from_numpy(sys_.z).to(dev)
+    pos = torch.from_numpy(sys_.pos).to(dev)
+    batch = torch.from_numpy(sys_.batch).to(dev) if sys_.n_systems > 1 else None
+    box = torch.from_numpy(sys_.box).to(dev) if sys_.box is not None else None
+    S = sys_.n_systems
+
+    # eager first call: allocate outputs, check status, learn the pair count
+    m.reset_status()
+    nl = m.neighbors(pos, batch, box, S)
+    E = torch.empty(S, dtype=torch.float64, device=dev)
+    Fo = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    m.energy_forces(z, pos, nl, batch, box, S, out=(E, Fo, None))
+    torch.cuda.synchronize()
+    m.check_status("bench warm-up")
+    n_pairs = int(nl.n_pairs.item())
+    nu = n_pairs // 2
+
+    def step():
+        m.neighbors(pos, batch, box, S, out=nl)
+        m.energy_forces(z, pos, nl, batch, box, S, out=(E, Fo, None))
+
+    # capture the step in a CUDA graph (and count the kernels it launches)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    c0 = lib.tnet_launch_count()
+    with torch.cuda.graph(g):
+        step()
+    launches_per_step = int(lib.tnet_launch_count() - c0)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    for _ in range(args.warmup):
+        flush.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+
+    # ---- timed region
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record()
+        g.replay()
+        ends[k].record()
+    torch.cuda.synchronize()
+    barrier(world)
+    ck = clocks.stop() if rank == 0 else None
+    times = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = allmax(sum(times), world)
+    m.reset_status()
+    g.replay()
+    torch.cuda.synchronize()
+    m.check_status("bench timed steps")
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ---- live per-stage timing (eager steps with the library's event profiler)
+    F_ = shape.F
+    lib.tnet_profile(m.ctx, 1)
+    for _ in range(args.profile_steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ntag = 32
+    ms = (ctypes.c_float * ntag)()
+    cnt = (ctypes.c_int64 * ntag)()
+    lib.tnet_profile_read(m.ctx, ntag, ms, cnt)
+    lib.tnet_profile(m.ctx, 0)
+    stages = {}
+    for t in range(ntag):
+        name = lib.tnet_profile_tag(t)
+        if name is None:
+            break
+        if cnt[t]:
+            stages[name.decode()] = {"ms_per_step": ms[t] / args.profile_steps, "instances": int(cnt[t])}
+    top = max(stages, key=lambda k: stages[k]["ms_per_step"])
+    roofline = None
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
+    work_tags = [k for k in sorted(stages, key=lambda k: -stages[k]["ms_per_step"]) if k in STAGE_WORK]
+    if work_tags:
+        tag = work_tags[0]
+        kind, amount = STAGE_WORK[tag](nu, N, n_pairs, F_, shape.K)
+        per_launch_ms = stages[tag]["ms_per_step"] * args.profile_steps / stages[tag]["instances"]
+        traffic = None
+        tpath = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tpath):
+            tr = json.load(open(tpath)).get(f"{args.workload}:{tag}")
+            if tr and tr.get("kernel_rev") == kernel_revision():
+                traffic = tr["bytes_per_launch"]
+        if kind == "flop":
+            ach = amount / (per_launch_ms * 1e-3) / 1e12
+            roofline = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": ach / fp32_peak, "traffic": traffic, "kernel": tag,
+                        "peak_note": "FP32 FFMA peak 152 SM x 128 lanes x 2 x 2070 MHz (derived)",
+                        "algorithmic_per_launch": amount, "launch_ms": per_launch_ms}
+        else:
+            ach = amount / (per_launch_ms * 1e-3) / 1e9
+            roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                        "traffic": traffic, "kernel": tag, "peak_note": "of measured (MEASURED_PEAKS.json)",
+                        "algorithmic_per_launch": amount, "launch_ms": per_launch_ms}
+
+    # ---- end to end through the public API with host buffers
+    pos_h = torch.from_numpy(sys_.pos).pin_memory()
+    E_h = torch.empty(S, dtype=torch.float64).pin_memory()
+    F_h = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+    pos_d = torch.empty_like(pos)
+
+    def e2e_step():
+        pos_d.copy_(pos_h, non_blocking=True)
+        m.neighbors(pos_d, batch, box, S, out=nl)
+        m.energy_forces(z, pos_d, nl, batch, box, S, out=(E, Fo, None))
+        E_h.copy_(E, non_blocking=True)
+        F_h.copy_(Fo, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = allmax(e0.elapsed_time(e1), world)
+    e2e = {"value": world * args.steps / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(pos_h.numel() * 4), "d2h_bytes_per_step": int(E_h.numel() * 8 + F_h.numel() * 4),
+           "path": "TensorNet.neighbors + TensorNet.energy_forces (eager) with pinned host positions in "
+                   "and energy + forces out"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(sys_, n_pairs, args),
+            "ns_per_day_at_0.5fs": value / world * 86400 * FS_PER_STEP * 1e-6,
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
+            "stages_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in
+                                   sorted(stages.items(), key=lambda kv: -kv[1]["ms_per_step"])},
+            "clocks": ck, "parallelism": f"replicas x{world}"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sys_, W)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_revision() -> str:
+    """Hash of the CUDA sources; a stored ncu traffic figure is used only
+    while the kernels it was measured on are unchanged."""
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2402_17660_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

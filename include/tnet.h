@@ -186,6 +186,23 @@ int tnet_md_step(tnet_ctx *ctx, const float *weights, int n_atoms, const int32_t
                  float skin, int rebuild_every, int n_steps, double *e_kin, double *e_pot,
                  int32_t *status_dev, tnet_stream_t stream);
 
+/* ---- instrumentation (no counterpart in the paper; used by the benchmark) */
+
+/* Number of CUDA kernels the library has enqueued in this process (all
+ * contexts, host-side count; a launch captured into a graph counts once, at
+ * capture time). */
+int64_t tnet_launch_count(void);
+
+/* Stage profiler.  tnet_profile(ctx, 1) clears and starts recording CUDA
+ * events around each stage of later calls on this context (not while the
+ * stream is being captured); tnet_profile(ctx, 0) stops.  tnet_profile_read
+ * synchronises on the recorded events and returns, for tags 0..ntags-1,
+ * the summed milliseconds and the number of recorded stage instances.
+ * tnet_profile_tag(t) names tag t, or returns NULL past the last tag. */
+int tnet_profile(tnet_ctx *ctx, int enable);
+int tnet_profile_read(tnet_ctx *ctx, int ntags, float *ms, int64_t *count);
+const char *tnet_profile_tag(int tag);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,10 @@ SIGNATURES = {
                                   _vp, _vp, _vp]),
     "tnet_md_step": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _f32, _f32, _i32, _i32, _vp, _vp,
                             _vp, _vp]),
+    "tnet_launch_count": (_i64, []),
+    "tnet_profile": (_i32, [_vp, _i32]),
+    "tnet_profile_read": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_i64)]),
+    "tnet_profile_tag": (ctypes.c_char_p, [_i32]),
 }
 
 STATUS = {0: "OK", 1: "ARG", 2: "CAPACITY", 3: "BOX", 4: "NAN", 5: "CUDA", 6: "TIMEOUT",

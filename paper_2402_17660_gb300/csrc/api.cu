@@ -3,6 +3,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace tnet {
@@ -126,9 +128,36 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     return TNET_OK;
 }
 
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ProfSeq::ProfSeq(tnet_ctx *ctx, cudaStream_t s) : c(ctx), st(s), slot(-1), active(false) {
+    if (!c || !c->prof_on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    active = true;
+}
+void ProfSeq::mark(int tag) {
+    if (!active) return;
+    if (slot >= 0) {
+        cudaEventRecord(c->prof_ev[2 * slot + 1], st);
+        slot = -1;
+    }
+    if (tag >= 0 && c->prof_n < c->prof_cap) {
+        slot = c->prof_n++;
+        c->prof_tag[slot] = tag;
+        cudaEventRecord(c->prof_ev[2 * slot], st);
+    }
+}
+
 }  // namespace tnet
 
 using namespace tnet;
+
+static const char *kTagNames[P_NTAGS] = {
+    "neighbors", "graph_prep", "emb_edges", "emb_node", "mlp1", "mlp2", "mlp3", "message",
+    "node_mix", "node_elem", "output", "output_bwd", "node_bwd", "message_bwd", "mlp_elem_bwd",
+    "mlp3_bwd", "mlp2_bwd", "mlp1_bwd", "emb_node_bwd", "emb_edges_bwd", "forces"};
 
 extern "C" {
 
@@ -205,7 +234,50 @@ int tnet_create(tnet_ctx **out, const tnet_model_desc *d, int max_atoms, int max
 int tnet_destroy(tnet_ctx *c) {
     if (!c) return TNET_ERR_ARG;
     if (c->md_exec) cudaGraphExecDestroy(c->md_exec);
+    if (c->prof_ev) {
+        for (int k = 0; k < 2 * c->prof_cap; ++k) cudaEventDestroy(c->prof_ev[k]);
+        free(c->prof_ev);
+        free(c->prof_tag);
+    }
     free(c);
+    return TNET_OK;
+}
+
+int64_t tnet_launch_count(void) { return g_launches.load(); }
+
+const char *tnet_profile_tag(int tag) { return (tag >= 0 && tag < P_NTAGS) ? kTagNames[tag] : nullptr; }
+
+int tnet_profile(tnet_ctx *c, int enable) {
+    if (!c) return TNET_ERR_ARG;
+    if (enable && !c->prof_ev) {
+        const int cap = 4096;
+        c->prof_ev = (cudaEvent_t *)calloc(2 * cap, sizeof(cudaEvent_t));
+        c->prof_tag = (int *)calloc(cap, sizeof(int));
+        if (!c->prof_ev || !c->prof_tag) return TNET_ERR_ARG;
+        for (int k = 0; k < 2 * cap; ++k) TNET_CUDA_TRY(cudaEventCreate(&c->prof_ev[k]));
+        c->prof_cap = cap;
+    }
+    c->prof_on = enable ? 1 : 0;
+    c->prof_n = 0;
+    return TNET_OK;
+}
+
+int tnet_profile_read(tnet_ctx *c, int ntags, float *ms, int64_t *count) {
+    if (!c || ntags < 0 || !ms || !count) return TNET_ERR_ARG;
+    for (int t = 0; t < ntags; ++t) {
+        ms[t] = 0.f;
+        count[t] = 0;
+    }
+    for (int k = 0; k < c->prof_n; ++k) {
+        TNET_CUDA_TRY(cudaEventSynchronize(c->prof_ev[2 * k + 1]));
+        float e = 0.f;
+        TNET_CUDA_TRY(cudaEventElapsedTime(&e, c->prof_ev[2 * k], c->prof_ev[2 * k + 1]));
+        const int t = c->prof_tag[k];
+        if (t < ntags) {
+            ms[t] += e;
+            count[t] += 1;
+        }
+    }
     return TNET_OK;
 }
 

@@ -222,6 +222,7 @@ inline int sgemm(const GemmShape &P, const Epi &epi, int num_sms, cudaStream_t s
     if (tiles < grid) grid = tiles;
     dim3 g((unsigned)grid, 1, P.nclass);
     k_sgemm<TA, TB, Epi><<<g, GTHREADS, 0, st>>>(P, epi);
+    count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
 }

@@ -245,6 +245,18 @@ struct Layout {
 
 }  // namespace tnet
 
+namespace tnet {
+// Host-side count of kernels enqueued by the library (all contexts).
+void count_launch();
+
+// Stages timed by the optional CUDA-event profiler (tnet_profile).
+enum ProfTag {
+    P_NBR = 0, P_PREP, P_EMB_EDGE, P_EMB_NODE, P_MLP1, P_MLP2, P_MLP3, P_MESSAGE, P_NODE_MIX,
+    P_NODE_ELEM, P_OUTPUT, P_OUT_BWD, P_NODE_BWD, P_MSG_BWD, P_MLP_ELEM_BWD, P_MLP3_BWD, P_MLP2_BWD,
+    P_MLP1_BWD, P_EMB_NODE_BWD, P_EMB_EDGE_BWD, P_FORCES, P_NTAGS
+};
+}  // namespace tnet
+
 struct tnet_ctx {
     tnet_model_desc d;
     int max_atoms, max_systems;
@@ -254,6 +266,10 @@ struct tnet_ctx {
     tnet::Layout lay;
     tnet::RadialParams rp;
     int device, num_sms;
+    // optional stage profiler
+    int prof_on, prof_n, prof_cap;
+    cudaEvent_t *prof_ev;
+    int *prof_tag;
     // CUDA graph cache for tnet_md_step
     cudaGraphExec_t md_exec;
     const void *md_key[8];
@@ -262,6 +278,18 @@ struct tnet_ctx {
 };
 
 namespace tnet {
+// Sequential stage markers: mark(tag) closes the open stage and opens the
+// next one; CUDA events are recorded only when profiling is on and the
+// stream is not being captured.
+struct ProfSeq {
+    tnet_ctx *c;
+    cudaStream_t st;
+    int slot;
+    bool active;
+    ProfSeq(tnet_ctx *ctx, cudaStream_t s);
+    void mark(int tag);
+    ~ProfSeq() { mark(-1); }
+};
 int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L);
 int validate_desc(const tnet_model_desc *d);
 template <class T>

@@ -85,6 +85,7 @@ int enqueue_rebuild(tnet_ctx *c, const MdArgs &a, cudaStream_t st) {
                             st);
     if (rc) return rc;
     k_copy<<<(3 * a.N + 255) / 256, 256, 0, st>>>(wsp<float>(c, L.md_pos_ref), a.pos, 3LL * a.N);
+    count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
 }
@@ -101,9 +102,11 @@ int enqueue_step(tnet_ctx *c, const MdArgs &a, bool rebuild, cudaStream_t st) {
     float *F = wsp<float>(c, L.md_forces);
     const int nb3 = (3 * a.N + 255) / 256, nb = (a.N + 255) / 256;
     k_half_kick<<<nb3, 256, 0, st>>>(a.vel, F, a.inv_m, a.N, 0.5f * a.dt);
+    count_launch();
     const float lim = 0.5f * a.skin;
     k_drift<<<nb, 256, 0, st>>>(a.pos, a.vel, a.N, a.dt, wsp<float>(c, L.md_pos_ref), a.box, lim * lim,
                                 a.status);
+    count_launch();
     TNET_LAUNCH_CHECK();
     if (rebuild) {
         int rc = enqueue_rebuild(c, a, st);
@@ -112,8 +115,10 @@ int enqueue_step(tnet_ctx *c, const MdArgs &a, bool rebuild, cudaStream_t st) {
     int rc = enqueue_forces(c, a, st);
     if (rc) return rc;
     k_half_kick<<<nb3, 256, 0, st>>>(a.vel, F, a.inv_m, a.N, 0.5f * a.dt);
+    count_launch();
     k_record<<<1, 1024, 0, st>>>(a.vel, a.inv_m, a.N, wsp<double>(c, L.md_energy), a.e_kin, a.e_pot,
                                  wsp<int32_t>(c, L.md_step));
+    count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
 }

@@ -884,27 +884,25 @@ __global__ void k_emb_edges_bwd(const float *__restrict__ pos, const float *__re
     }
 }
 
-// F_i = -sum_{e in row i} (gvec[e] - gvec[rev[e]]) (one warp per atom)
+// F_i = -sum_{e in row i} (gvec[e] - gvec[rev[e]]) over the active edges of
+// the row, summed in row order by one thread per atom so the result does not
+// depend on inactive (skin) entries of the list.
 __global__ void k_forces(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ rev,
-                         const float *__restrict__ gvec, int N, float *__restrict__ forces) {
-    const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+                         const int32_t *__restrict__ pair_of, const float *__restrict__ gvec, int N,
+                         float *__restrict__ forces) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int lane = threadIdx.x & 31;
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    for (int e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
+    for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        if (pair_of[e] < 0) continue;
         const int r = rev[e];
         fx += gvec[3LL * e] - gvec[3LL * r];
         fy += gvec[3LL * e + 1] - gvec[3LL * r + 1];
         fz += gvec[3LL * e + 2] - gvec[3LL * r + 2];
     }
-    fx = warp_sum(fx);
-    fy = warp_sum(fy);
-    fz = warp_sum(fz);
-    if (lane == 0) {
-        forces[3LL * i] = -fx;
-        forces[3LL * i + 1] = -fy;
-        forces[3LL * i + 2] = -fz;
-    }
+    forces[3LL * i] = -fx;
+    forces[3LL * i + 1] = -fy;
+    forces[3LL * i + 2] = -fz;
 }
 
 // Opt the kernels with large dynamic shared memory into it (once per context).
@@ -956,27 +954,36 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     const int warps_grid = (int)(((int64_t)N * 32 + 255) / 256);
 
     // ---- graph prep
+    ProfSeq pf(ctx, st);
+    pf.mark(P_PREP);
     TNET_CUDA_TRY(cudaMemsetAsync(sys_start, 0, sizeof(int32_t) * S, st));
     TNET_CUDA_TRY(cudaMemsetAsync(sys_end, 0, sizeof(int32_t) * S, st));
     if (N > 0) TRY(sys_bounds(batch, N, S, sys_start, sys_end, status, st));
     if (N > 0) {
         k_rev<<<warps_grid, 256, 0, st>>>(row_ptr, col, N, rev, status);
+        count_launch();
         k_upper_count<<<warps_grid, 256, 0, st>>>(pos, box, batch, row_ptr, col, N, rp.rc, ucnt);
+        count_launch();
         TNET_LAUNCH_CHECK();
     }
     TRY(scan_exclusive_i32(ucnt, ucnt, N, i32(Lw.scan_tmp), nu, nullptr, st));
     if (N > 0) {
         k_upper_assign<<<warps_grid, 256, 0, st>>>(pos, box, batch, row_ptr, col, N, rp.rc, ucnt,
                                                    pair_of, uij);
+        count_launch();
         k_lower_assign<<<warps_grid, 256, 0, st>>>(row_ptr, col, rev, N, pair_of);
+        count_launch();
         TNET_LAUNCH_CHECK();
     }
     float *eu = f32(Lw.eu), *phiu = f32(Lw.phiu);
     k_edge_rbf<<<sms * 8, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu);
+    count_launch();
     k_elem_tables<<<d.max_z, F, 0, st>>>(W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
+    count_launch();
     TNET_LAUNCH_CHECK();
 
     // ---- embedding
+    pf.mark(P_EMB_EDGE);
     float *Xraw = f32(Lw.Xraw), *Uemb = f32(Lw.Uemb), *n0 = f32(Lw.n0), *as1 = f32(Lw.as1),
           *hs1 = f32(Lw.hs1), *as2 = f32(Lw.as2), *s = f32(Lw.s);
     float2 *ln0 = wsp<float2>(ctx, Lw.ln0);
@@ -985,9 +992,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     if (N > 0) {
         k_emb_edges<<<emb_blocks, F, emb_smem, st>>>(pos, box, batch, z, row_ptr, col, N, F, d.max_z, rp,
                                                      W.dproj_w, W.dproj_b, Ta, Tb, Xraw, status);
+        count_launch();
         k_norm_ln<<<N, F, 0, st>>>(Xraw, N, F, W.emb_ln_g, W.emb_ln_b, n0, ln0);
+        count_launch();
         TNET_LAUNCH_CHECK();
     }
+    pf.mark(P_EMB_NODE);
     TRY(sgemm<false, true>(gshape(N, 2 * F, F, n0, F, W.emb_mlp1_w, F),
                            EpiBiasAct{W.emb_mlp1_b, as1, 2 * F, hs1, 2 * F, 1, nullptr}, sms, st));
     TRY(sgemm<false, true>(gshape(N, 3 * F, 2 * F, hs1, 2 * F, W.emb_mlp2_w, 2 * F),
@@ -995,6 +1005,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     TRY(sgemm<false, true>(gshape_classes(N, F, Xraw, W.emb_mix_w), EpiStore{Uemb, F, 0}, sms, st));
     float *X = f32(Lw.Xin);  // layer 0 input
     k_emb_scale<<<grid_for((int64_t)N * F, 256, sms), 256, 0, st>>>(Uemb, s, N, F, X);
+    count_launch();
     TNET_LAUNCH_CHECK();
 
     // ---- interaction layers
@@ -1002,12 +1013,15 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
           *gbuf = f32(Lw.g);
     auto edge_mlp = [&](int l) -> int {
         const LayerW &Lr = W.layer[l];
+        pf.mark(P_MLP1);
         GemmShape p1 = gshape(maxU, F, K, eu, K, Lr.mlp1_w, K);
         p1.rows_dev = nu;
         TRY(sgemm<false, true>(p1, EpiBiasAct{Lr.mlp1_b, a1, F, h1, F, 1, nullptr}, sms, st));
+        pf.mark(P_MLP2);
         GemmShape p2 = gshape(maxU, 2 * F, F, h1, F, Lr.mlp2_w, F);
         p2.rows_dev = nu;
         TRY(sgemm<false, true>(p2, EpiBiasAct{Lr.mlp2_b, a2, 2 * F, h2, 2 * F, 1, nullptr}, sms, st));
+        pf.mark(P_MLP3);
         GemmShape p3 = gshape(maxU, 3 * F, 2 * F, h2, 2 * F, Lr.mlp3_w, 2 * F);
         p3.rows_dev = nu;
         TRY(sgemm<false, true>(p3, EpiBiasAct{Lr.mlp3_b, a3, 3 * F, gbuf, 3 * F, 1, phiu}, sms, st));
@@ -1020,45 +1034,64 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         float *Y = f32(Lw.Y) + l * n9, *M = f32(Lw.M) + l * n9, *Tn = f32(Lw.Tn) + l * n9,
               *dX = f32(Lw.dX) + l * n9;
         float *Xnext = (l + 1 < NL) ? X + (l + 1) * n9 : f32(Lw.Xfin);
+        pf.mark(P_NODE_ELEM);
         k_node_norm<<<ew, 256, 0, st>>>(Xl, N, F, qn, Xn);
+        count_launch();
         TNET_LAUNCH_CHECK();
+        pf.mark(P_NODE_MIX);
         TRY(sgemm<false, true>(gshape_classes(N, F, Xn, W.layer[l].mix1_w), EpiStore{Y, F, 0}, sms, st));
         TRY(edge_mlp(l));
+        pf.mark(P_MESSAGE);
         k_message<<<atom_blocks, F, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, N, F, M);
+        count_launch();
+        pf.mark(P_NODE_ELEM);
         k_node_update<<<ew, 256, 0, st>>>(Y, M, N, F, Tn);
+        count_launch();
         TNET_LAUNCH_CHECK();
+        pf.mark(P_NODE_MIX);
         TRY(sgemm<false, true>(gshape_classes(N, F, Tn, W.layer[l].mix2_w), EpiStore{dX, F, 0}, sms, st));
+        pf.mark(P_NODE_ELEM);
         k_residual<<<ew, 256, 0, st>>>(Xn, dX, N, F, Xnext);
+        count_launch();
         TNET_LAUNCH_CHECK();
     }
     float *Xfin = NL > 0 ? f32(Lw.Xfin) : X;
 
     // ---- output model
+    pf.mark(P_OUTPUT);
     float *h = f32(Lw.h), *hn = f32(Lw.hn), *ao = f32(Lw.ao), *o = f32(Lw.o), *at = f32(Lw.at),
           *t = f32(Lw.t), *Ei = f32(Lw.Ei);
     float2 *lno = wsp<float2>(ctx, Lw.lno);
     if (N > 0) {
         k_out_norms<<<N, F, 0, st>>>(Xfin, N, F, W.out_ln_g, W.out_ln_b, h, hn, lno);
+        count_launch();
         TNET_LAUNCH_CHECK();
     }
     TRY(sgemm<false, true>(gshape(N, F, 3 * F, hn, 3 * F, W.out_w, 3 * F),
                            EpiBiasAct{W.out_b, ao, F, o, F, 1, nullptr}, sms, st));
     TRY(sgemm<false, true>(gshape(N, H, F, o, F, W.head1_w, F),
                            EpiBiasAct{W.head1_b, at, H, t, H, 1, nullptr}, sms, st));
-    if (N > 0) k_head<<<warps_grid, 256, 0, st>>>(t, N, H, W.head2_w, W.head2_b, Ei);
+    if (N > 0) {
+        k_head<<<warps_grid, 256, 0, st>>>(t, N, H, W.head2_w, W.head2_b, Ei);
+        count_launch();
+    }
     k_energy<<<S, 256, 0, st>>>(Ei, sys_start, sys_end, energy);
+    count_launch();
     TNET_LAUNCH_CHECK();
     if (!forces || N == 0) return TNET_OK;
 
     // ---- reverse pass
+    pf.mark(P_OUT_BWD);
     float *gat = f32(Lw.gat), *gao = f32(Lw.gao), *ghn = f32(Lw.ghn);
     float *gX = f32(Lw.gXa), *gdX = f32(Lw.gdX), *gTn = f32(Lw.gTn), *gM = f32(Lw.gM), *gY = f32(Lw.gY);
     float *gg = f32(Lw.gg), *ga2 = f32(Lw.ga2), *ga1 = f32(Lw.ga1), *ge = f32(Lw.ge), *gphiu = f32(Lw.gphiu);
     k_head_bwd<<<grid_for((int64_t)N * H, 256, sms), 256, 0, st>>>(at, N, H, W.head2_w, seed, batch, gat);
+    count_launch();
     TNET_LAUNCH_CHECK();
     TRY(sgemm<false, false>(gshape(N, F, H, gat, H, W.head1_w, F), EpiGradAct{ao, F, gao, F, 0}, sms, st));
     TRY(sgemm<false, false>(gshape(N, 3 * F, F, gao, F, W.out_w, 3 * F), EpiStore{ghn, 3 * F, 0}, sms, st));
     k_out_norms_bwd<<<N, F, 0, st>>>(Xfin, h, ghn, lno, W.out_ln_g, N, F, gX);
+    count_launch();
     TNET_LAUNCH_CHECK();
     if (NL > 0) TNET_CUDA_TRY(cudaMemsetAsync(gphiu, 0, sizeof(float) * maxU, st));
     for (int l = NL - 1; l >= 0; --l) {
@@ -1066,45 +1099,64 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         float *Xl = X + l * n9, *Xn = f32(Lw.Xn) + l * n9, *qn = f32(Lw.qn) + (int64_t)l * N * F;
         float *Y = f32(Lw.Y) + l * n9, *M = f32(Lw.M) + l * n9, *dX = f32(Lw.dX) + l * n9;
         (void)Xn;
+        pf.mark(P_NODE_BWD);
         k_residual_bwd<<<ew, 256, 0, st>>>(gX, dX, N, F, gdX);
+        count_launch();
         TNET_LAUNCH_CHECK();
         TRY(sgemm<false, false>(gshape_classes(N, F, gdX, Lr.mix2_w), EpiStore{gTn, F, 0}, sms, st));
         k_T_bwd<<<ew, 256, 0, st>>>(Y, M, gTn, N, F, gY, gM);
+        count_launch();
         TNET_LAUNCH_CHECK();
         TRY(edge_mlp(l));  // recompute a1, h1, a2, h2, a3, g of this layer
+        pf.mark(P_MSG_BWD);
         k_message_bwd<<<atom_blocks, F, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, gM, N, F, gY, gg);
+        count_launch();
+        pf.mark(P_MLP_ELEM_BWD);
         k_mlp3_bwd<<<sms * 8, 256, 0, st>>>(gg, a3, phiu, nu, 3 * F, gphiu);
+        count_launch();
         TNET_LAUNCH_CHECK();
+        pf.mark(P_MLP3_BWD);
         GemmShape q3 = gshape(maxU, 2 * F, 3 * F, gg, 3 * F, Lr.mlp3_w, 2 * F);
         q3.rows_dev = nu;
         TRY(sgemm<false, false>(q3, EpiGradAct{a2, 2 * F, ga2, 2 * F, 0}, sms, st));
+        pf.mark(P_MLP2_BWD);
         GemmShape q2 = gshape(maxU, F, 2 * F, ga2, 2 * F, Lr.mlp2_w, F);
         q2.rows_dev = nu;
         TRY(sgemm<false, false>(q2, EpiGradAct{a1, F, ga1, F, 0}, sms, st));
+        pf.mark(P_MLP1_BWD);
         GemmShape q1 = gshape(maxU, K, F, ga1, F, Lr.mlp1_w, K);
         q1.rows_dev = nu;
         TRY(sgemm<false, false>(q1, EpiStore{ge, K, l != NL - 1}, sms, st));
+        pf.mark(P_NODE_BWD);
         TRY(sgemm<false, false>(gshape_classes(N, F, gY, Lr.mix1_w), EpiStore{gX, F, 1}, sms, st));
         k_node_norm_bwd<<<ew, 256, 0, st>>>(Xl, qn, N, F, gX);
+        count_launch();
         TNET_LAUNCH_CHECK();
     }
     // embedding adjoint: gX now holds dE/dX0
+    pf.mark(P_EMB_NODE_BWD);
     float *gU = f32(Lw.gU), *gas2 = f32(Lw.gas2), *gas1 = f32(Lw.gas1), *gn0 = f32(Lw.gn0);
     float *gXraw = gdX;
     k_emb_scale_bwd<<<ew, 256, 0, st>>>(gX, Uemb, s, as2, N, F, gU, gas2);
+    count_launch();
     TNET_LAUNCH_CHECK();
     TRY(sgemm<false, false>(gshape(N, 2 * F, 3 * F, gas2, 3 * F, W.emb_mlp2_w, 2 * F),
                             EpiGradAct{as1, 2 * F, gas1, 2 * F, 0}, sms, st));
     TRY(sgemm<false, false>(gshape(N, F, 2 * F, gas1, 2 * F, W.emb_mlp1_w, F), EpiStore{gn0, F, 0}, sms, st));
     TRY(sgemm<false, false>(gshape_classes(N, F, gU, W.emb_mix_w), EpiStore{gXraw, F, 0}, sms, st));
     k_ln0_bwd<<<N, F, 0, st>>>(Xraw, gn0, ln0, W.emb_ln_g, N, F, gXraw);
+    count_launch();
     TNET_LAUNCH_CHECK();
+    pf.mark(P_EMB_EDGE_BWD);
     float *gvec = f32(Lw.gvec);
     const size_t bwd_smem = sizeof(float) * (3 * F * (K + 1) + 2 * kEG * K + kEG * 3 * F);
     k_emb_edges_bwd<<<emb_blocks, F, bwd_smem, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, F,
                                                      d.max_z, rp, W.dproj_w, W.dproj_b, Ta, Tb, gXraw,
                                                      ge, gphiu, NL > 0, gvec);
-    k_forces<<<warps_grid, 256, 0, st>>>(row_ptr, rev, gvec, N, forces);
+    count_launch();
+    pf.mark(P_FORCES);
+    k_forces<<<(N + 127) / 128, 128, 0, st>>>(row_ptr, rev, pair_of, gvec, N, forces);
+    count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
 }

@@ -102,10 +102,15 @@ int scan_exclusive_i32(const int32_t *in, int32_t *out, int n, int32_t *tmp, int
     const int nt = (n + kScanTile - 1) / kScanTile;
     if (nt > kScanTile) return TNET_ERR_ARG;
     const int ntl = nt > 0 ? nt : 1;
-    if (n > 0) k_scan_tiles<<<nt, kScanThreads, 0, st>>>(in, out, n, tmp);
+    if (n > 0) {
+        k_scan_tiles<<<nt, kScanThreads, 0, st>>>(in, out, n, tmp);
+        count_launch();
+    }
     else TNET_CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(int32_t), st));
     k_scan_top<<<1, kScanThreads, 0, st>>>(tmp, ntl, tmp + ntl);
+    count_launch();
     k_scan_add<<<(n + 255) / 256 + 1, 256, 0, st>>>(out, n, tmp, tmp + ntl, total_dev, total64_dev);
+    count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
 }
@@ -131,6 +136,7 @@ __global__ void k_sys_bounds(const int32_t *__restrict__ batch, int N, int S,
 int sys_bounds(const int32_t *batch, int N, int S, int32_t *sys_start, int32_t *sys_end,
                int32_t *status, cudaStream_t st) {
     k_sys_bounds<<<(N + 255) / 256, 256, 0, st>>>(batch, N, S, sys_start, sys_end, status);
+    count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
 }
@@ -410,6 +416,8 @@ int neighbors_impl(tnet_ctx *ctx, int N, int S, const float *pos, const int32_t 
     int32_t *tmp = wsp<int32_t>(ctx, L.scan_tmp);
     float4 *spos = wsp<float4>(ctx, L.spos);
     const int cells = (int)L.cells;
+    ProfSeq pf(ctx, st);
+    pf.mark(P_NBR);
 
     TNET_CUDA_TRY(cudaMemsetAsync(sys_start, 0, sizeof(int32_t) * S, st));
     TNET_CUDA_TRY(cudaMemsetAsync(sys_end, 0, sizeof(int32_t) * S, st));
@@ -417,32 +425,39 @@ int neighbors_impl(tnet_ctx *ctx, int N, int S, const float *pos, const int32_t 
     TNET_CUDA_TRY(cudaMemsetAsync(cell_fill, 0, sizeof(int32_t) * cells, st));
     if (N > 0) {
         k_sys_bounds<<<(N + 255) / 256, 256, 0, st>>>(batch, N, S, sys_start, sys_end, status);
+        count_launch();
         TNET_LAUNCH_CHECK();
     }
     k_sys_setup<<<S, 256, 0, st>>>(pos, box, cutoff, sys_start, sys_end, info, ncell, status);
+    count_launch();
     TNET_LAUNCH_CHECK();
     int rc = scan_exclusive_i32(ncell, ncell, S, tmp, nullptr, nullptr, st);
     if (rc) return rc;
     if (N > 0) {
         k_bin<<<(N + 255) / 256, 256, 0, st>>>(pos, batch, N, info, ncell, cell_of, cell_count, cells);
+        count_launch();
         TNET_LAUNCH_CHECK();
     }
     rc = scan_exclusive_i32(cell_count, cell_start, cells, tmp, nullptr, nullptr, st);
     if (rc) return rc;
     if (N > 0) {
         k_scatter<<<(N + 255) / 256, 256, 0, st>>>(pos, N, cell_of, cell_start, cell_fill, sorted, spos);
+        count_launch();
         TNET_LAUNCH_CHECK();
         k_pair_count<<<(int)(((int64_t)N * 32 + 255) / 256), 256, 0, st>>>(
             pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, rowcnt);
+        count_launch();
         TNET_LAUNCH_CHECK();
     }
     rc = scan_exclusive_i32(rowcnt, row_ptr, N, tmp, nullptr, n_pairs_dev, st);
     if (rc) return rc;
     k_cap_check<<<1, 1, 0, st>>>(n_pairs_dev, cap, status);
+    count_launch();
     TNET_LAUNCH_CHECK();
     if (N > 0) {
         k_pair_fill<<<(N + kFillWarps - 1) / kFillWarps, kFillWarps * 32, 0, st>>>(
             pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, row_ptr, col, cap);
+        count_launch();
         TNET_LAUNCH_CHECK();
     }
     return TNET_OK;
