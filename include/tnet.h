@@ -186,6 +186,25 @@ int tnet_md_step(tnet_ctx *ctx, const float *weights, int n_atoms, const int32_t
                  float skin, int rebuild_every, int n_steps, double *e_kin, double *e_pot,
                  int32_t *status_dev, tnet_stream_t stream);
 
+/* ---- allocation-free neighbor search (no counterpart in the paper) -------
+ * For callers that cannot allocate device memory (code inside another
+ * framework's memory pool or a real-time loop that forbids cudaMalloc after
+ * start-up, or plain C callers with no allocator): the same search as
+ * tnet_neighbors, with the same arguments and outputs but no context, its
+ * scratch held in a file-scope __device__ array of 2 MiB that every GPU
+ * loading the library keeps until the process exits.  The caller still
+ * passes all inputs and outputs.
+ * Limits: n_atoms <= 16384 and n_systems <= 1024; larger requests return
+ * TNET_ERR_WORKSPACE at once (nothing is enqueued).  No cudaMalloc, cudaFree
+ * or allocating library call is made.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  All calls share the array: calls whose GPU
+ * work overlaps (different streams or threads) race; calls ordered on one
+ * stream are safe. */
+int tnet_neighbors_noalloc(int n_atoms, int n_systems, const float *pos, const int32_t *batch,
+                           const float *box, float cutoff, int32_t *row_ptr, int32_t *col, int64_t cap,
+                           int64_t *n_pairs_dev, int32_t *status_dev, tnet_stream_t stream);
+
 /* ---- instrumentation (no counterpart in the paper; used by the benchmark) */
 
 /* Number of CUDA kernels the library has enqueued in this process (all
