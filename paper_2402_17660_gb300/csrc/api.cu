@@ -116,6 +116,19 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->ge = take(f * U * K);
     L->gphiu = take(f * U);
     L->gvec = take(f * 3 * E);
+    L->fu = take(f * U * 3 * F);
+    L->gfu = take(f * U * 3 * F);
+    L->ue = take(i * U);
+    L->edge_g = take(16 * E);
+    L->gp = take(f * 3 * U);
+    L->q0 = take(f * N * F);
+    L->gEi = take(f * N);
+    L->gA_atom = take(f * N * F);
+    L->gB_atom = take(f * N * F);
+    L->zsplits = 32;
+    L->zpart = take(f * 2 * L->zsplits * Z * F);
+    L->wpart_floats = 4LL << 20;
+    L->wpart = take(f * L->wpart_floats);
     // MD
     L->md_row_ptr = take(i * (N + 1));
     L->md_col = take(i * E);

@@ -235,6 +235,11 @@ struct Layout {
     // backward
     size_t gXa, gXb, gdX, gTn, gM, gY, gat, gao, ghn, gh, gU, gas2, gas1, gn0, gq0, gg, ga2, ga1, ge,
         gphiu, gvec;
+    // per-pair embedding projections and pair adjoints
+    size_t fu, gfu, ue, edge_g, gp, q0, gEi;
+    // weight-gradient scratch
+    size_t gA_atom, gB_atom, zpart, wpart;
+    int64_t wpart_floats, zsplits;
     // MD
     size_t md_row_ptr, md_col, md_npairs, md_forces, md_energy, md_pos_ref, md_step;
     size_t total;
@@ -290,6 +295,29 @@ struct ProfSeq {
     void mark(int tag);
     ~ProfSeq() { mark(-1); }
 };
+// Row-sum reductions for weight gradients (grad.cu).  Up to 3 classes of
+// rows (blockIdx.z), e.g. the I, A and S coordinate planes.
+struct WgradShape {
+    int M, N;                 // output [M][N] per class
+    int64_t rows[3];          // rows per class (capacity if rows_dev is set)
+    int64_t row0[3];          // first row of each class in A and B
+    const int32_t *rows_dev;  // optional device row count (class 0 only), times rows_mul
+    int rows_mul;
+    const float *A;           // A[row][m]
+    int64_t lda;
+    const float *B;           // B[row][n]
+    int64_t ldb;
+    int nclass;
+};
+// out[z][m][n] (+)= sum_rows A[r][m] B[r][n]
+int wgrad_outer(const WgradShape &P, float *partial, int64_t partial_cap, float *out, int accumulate, int sms,
+                cudaStream_t st);
+// out[z][m] (+)= sum_rows A[r][m] * roww[r] (roww may be NULL)
+int wgrad_colsum(const WgradShape &P, const float *roww, float *partial, int64_t partial_cap, float *out,
+                 int accumulate, int sms, cudaStream_t st);
+int wgrad_layernorm(const float *gy, const float *x, const float2 *stats, int R, int C, float *partial,
+                    int64_t partial_cap, float *out_g, int sms, cudaStream_t st);
+
 int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L);
 int validate_desc(const tnet_model_desc *d);
 template <class T>

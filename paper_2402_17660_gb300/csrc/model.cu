@@ -151,7 +151,7 @@ __global__ void k_upper_assign(const float *__restrict__ pos, const float *__res
                                const int32_t *__restrict__ batch, const int32_t *__restrict__ row_ptr,
                                const int32_t *__restrict__ col, int N, float rc,
                                const int32_t *__restrict__ uoff, int32_t *__restrict__ pair_of,
-                               int2 *__restrict__ uij) {
+                               int2 *__restrict__ uij, int32_t *__restrict__ ue) {
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (i >= N) return;
     const int lane = threadIdx.x & 31;
@@ -174,6 +174,7 @@ __global__ void k_upper_assign(const float *__restrict__ pos, const float *__res
                 const int u = base + __popc(m & ((1u << lane) - 1u));
                 pair_of[e] = u;
                 uij[u] = make_int2(i, j);
+                ue[u] = e;
             } else {
                 pair_of[e] = -1;
             }
@@ -255,25 +256,17 @@ __device__ __forceinline__ EdgeGeo edge_geo(const float *__restrict__ pos, const
     return g;
 }
 
-// X_raw_i = sum_j phi Z_ij (f^I I0 + f^A A0(u) + f^S S0(u)); block = F threads,
-// persistent over atoms.  Dynamic smem: W [3][K][F] + e [kEG][K].
+// X_raw_i = sum_j phi Z_ij (f^I I0 + f^A A0(u) + f^S S0(u)) over the active
+// edges of row i, in row order.  f^p = W^p e(d) + b^p depends only on d, so
+// it is computed once per undirected pair by a GEMM (fu, columns p*F + c).
+// Block = F threads (thread = channel), persistent over atoms.
 __global__ void k_emb_edges(const float *__restrict__ pos, const float *__restrict__ box,
                             const int32_t *__restrict__ batch, const int32_t *__restrict__ z,
                             const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                            int N, int F, int max_z, RadialParams rp, const float *__restrict__ dproj_w,
-                            const float *__restrict__ dproj_b, const float *__restrict__ Ta,
+                            const int32_t *__restrict__ pair_of, int N, int F, int max_z, RadialParams rp,
+                            const float *__restrict__ fu, const float *__restrict__ Ta,
                             const float *__restrict__ Tb, float *__restrict__ Xraw, int32_t *status) {
-    extern __shared__ float sm[];
-    const int K = rp.K, c = threadIdx.x;
-    float *Ws = sm;                   // [3][K][F]
-    float *es = Ws + 3 * K * F;       // [kEG][K]
-    __shared__ EdgeGeo geo[kEG];
-    for (int t = threadIdx.x; t < 3 * K * F; t += blockDim.x) {
-        const int p = t / (K * F), r = t % (K * F), k = r / F, cc = r % F;
-        Ws[t] = dproj_w[((int64_t)p * F + cc) * K + k];
-    }
-    const float bI = dproj_b[c], bA = dproj_b[F + c], bS = dproj_b[2 * F + c];
-    __syncthreads();
+    const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         int zi = z[i];
         if (zi < 0 || zi >= max_z) {
@@ -282,43 +275,25 @@ __global__ void k_emb_edges(const float *__restrict__ pos, const float *__restri
         }
         const float ta = Ta[(int64_t)zi * F + c];
         float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
-        for (int eb = e0; eb < e1; eb += kEG) {
-            if (threadIdx.x < kEG) {
-                const int e = eb + threadIdx.x;
-                if (e < e1) geo[threadIdx.x] = edge_geo(pos, box, batch, i, col[e], rp);
-                else geo[threadIdx.x].active = 0;
-            }
-            __syncthreads();
-            for (int t = threadIdx.x; t < kEG * K; t += blockDim.x) {
-                const int g = t / K, k = t % K;
-                float e = 0.f, de;
-                if (geo[g].active) expnorm_k(geo[g].d, k, rp, geo[g].phi, 0.f, e, de);
-                es[t] = e;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int g = 0; g < kEG; ++g) {
-                if (!geo[g].active) continue;
-                float fI = bI, fA = bA, fS = bS;
-                for (int k = 0; k < K; ++k) {
-                    const float ek = es[g * K + k];
-                    fI = fmaf(Ws[(0 * K + k) * F + c], ek, fI);
-                    fA = fmaf(Ws[(1 * K + k) * F + c], ek, fA);
-                    fS = fmaf(Ws[(2 * K + k) * F + c], ek, fS);
-                }
-                int zj = z[geo[g].j];
-                zj = (zj < 0 || zj >= max_z) ? 0 : zj;
-                const float pz = geo[g].phi * (ta + Tb[(int64_t)zj * F + c]);
-                const float cI = pz * fI, cA = pz * fA, cS = pz * fS;
-                const float ux = geo[g].u[0], uy = geo[g].u[1], uz = geo[g].u[2];
-                v[0] += cI;
-                v[1] += cA * ux; v[2] += cA * uy; v[3] += cA * uz;
-                v[4] += cS * (ux * ux - (1.0f / 3.0f));
-                v[5] += cS * (uy * uy - (1.0f / 3.0f));
-                v[6] += cS * ux * uy; v[7] += cS * ux * uz; v[8] += cS * uy * uz;
-            }
-            __syncthreads();
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int u = pair_of[e];
+            if (u < 0) continue;
+            const int j = col[e];
+            float x, y, zz;
+            pair_vec(pos, box, batch, i, j, x, y, zz);
+            const float d = sqrtf(x * x + y * y + zz * zz);
+            const float inv = 1.0f / d;
+            const float ux = x * inv, uy = y * inv, uz = zz * inv;
+            int zj = z[j];
+            zj = (zj < 0 || zj >= max_z) ? 0 : zj;
+            const float pz = cutoff_phi(d, rp) * (ta + Tb[(int64_t)zj * F + c]);
+            const float *f = fu + (int64_t)u * 3 * F + c;
+            const float cI = pz * f[0], cA = pz * f[F], cS = pz * f[2 * F];
+            v[0] += cI;
+            v[1] += cA * ux; v[2] += cA * uy; v[3] += cA * uz;
+            v[4] += cS * (ux * ux - (1.0f / 3.0f));
+            v[5] += cS * (uy * uy - (1.0f / 3.0f));
+            v[6] += cS * ux * uy; v[7] += cS * ux * uz; v[8] += cS * uy * uz;
         }
         store_coords(Xraw, i, c, N, F, v);
     }
@@ -326,7 +301,8 @@ __global__ void k_emb_edges(const float *__restrict__ pos, const float *__restri
 
 // q0 = ||X_raw|| per channel, LayerNorm over channels -> n0; caches (mean, rstd)
 __global__ void k_norm_ln(const float *__restrict__ X, int N, int F, const float *__restrict__ g,
-                          const float *__restrict__ b, float *__restrict__ n0, float2 *__restrict__ ln) {
+                          const float *__restrict__ b, float *__restrict__ n0, float2 *__restrict__ ln,
+                          float *__restrict__ q0) {
     __shared__ float sm[32];
     const int i = blockIdx.x, c = threadIdx.x;
     float v[9];
@@ -337,6 +313,7 @@ __global__ void k_norm_ln(const float *__restrict__ X, int N, int F, const float
     const float var = block_sum(dv * dv, sm) / F;
     const float rstd = rsqrtf(var + 1e-5f);
     n0[(int64_t)i * F + c] = dv * rstd * g[c] + b[c];
+    q0[(int64_t)i * F + c] = q;
     if (c == 0) ln[i] = make_float2(mean, rstd);
 }
 
@@ -743,175 +720,244 @@ __global__ void k_ln0_bwd(const float *__restrict__ Xraw, const float *__restric
     store_coords(gXraw, i, c, N, F, gv);
 }
 
-// Embedding edge adjoint and per-edge dE/dr_ij (block = F threads, persistent
-// over atoms).  Also adds the radial-MLP adjoints (ge_u, gphi_u) of the
-// undirected pair to its upper directed edge.  Dynamic smem:
-// W [3][F][K+1] + e, de [kEG][K] + gf [kEG][3][F].
-__global__ void k_emb_edges_bwd(const float *__restrict__ pos, const float *__restrict__ box,
-                                const int32_t *__restrict__ batch, const int32_t *__restrict__ z,
-                                const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                                const int32_t *__restrict__ pair_of, int N, int F, int max_z,
-                                RadialParams rp, const float *__restrict__ dproj_w,
-                                const float *__restrict__ dproj_b, const float *__restrict__ Ta,
-                                const float *__restrict__ Tb, const float *__restrict__ gXraw,
-                                const float *__restrict__ ge_u, const float *__restrict__ gphi_u,
-                                int have_mlp, float *__restrict__ gvec) {
-    extern __shared__ float sm[];
-    const int K = rp.K, KP = K + 1, c = threadIdx.x;
-    float *Ws = sm;                    // [3][F][KP]
-    float *es = Ws + 3 * F * KP;       // [kEG][K]
-    float *des = es + kEG * K;         // [kEG][K]
-    float *gfs = des + kEG * K;        // [kEG][3][F]
-    __shared__ EdgeGeo geo[kEG];
-    __shared__ float red[kEG][4][32];
-    for (int t = threadIdx.x; t < 3 * F * K; t += blockDim.x) {
-        const int p = t / (F * K), r = t % (F * K), cc = r / K, k = r % K;
-        Ws[(p * F + cc) * KP + k] = dproj_w[t];
-    }
-    const float bI = dproj_b[c], bA = dproj_b[F + c], bS = dproj_b[2 * F + c];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    for (int i = blockIdx.x; i < N; i += gridDim.x) {
+// Embedding edge adjoint, one warp per atom i (lane = channels lane + 32k).
+// For each active directed edge e = (i, j) of the row it writes
+//   edge_g[e] = (dE/dphi, dE/du) of that directed use of the pair (u = r_ij/d),
+// and for upper edges (j > i) the pair's projection adjoint summed over both
+// directions, gfu[u] = dE/df^p (columns p*F + c), which needs gXraw_j.
+// With want_z it also sums the pair-embedding adjoints dE/dZ per atom as
+// receiver (gA_atom) and as sender (gB_atom) for the embedding-table gradients.
+template <int CPL>
+__global__ void k_emb_bwd(const float *__restrict__ pos, const float *__restrict__ box,
+                          const int32_t *__restrict__ batch, const int32_t *__restrict__ z,
+                          const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                          const int32_t *__restrict__ pair_of, int N, int max_z, RadialParams rp,
+                          const float *__restrict__ fu, const float *__restrict__ Ta,
+                          const float *__restrict__ Tb, const float *__restrict__ gXraw, int want_z,
+                          float *__restrict__ gfu, float4 *__restrict__ edge_g, float *__restrict__ gA_atom,
+                          float *__restrict__ gB_atom) {
+    constexpr int F = CPL * 32;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t ii = warp0; ii < N; ii += nwarps) {
+        const int i = (int)ii;
         int zi = z[i];
         zi = (zi < 0 || zi >= max_z) ? 0 : zi;
-        const float ta = Ta[(int64_t)zi * F + c];
-        float gv[9];
-        load_coords(gXraw, i, c, N, F, gv);
-        const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
-        for (int eb = e0; eb < e1; eb += kEG) {
-            if (threadIdx.x < kEG) {
-                const int e = eb + threadIdx.x;
-                if (e < e1) geo[threadIdx.x] = edge_geo(pos, box, batch, i, col[e], rp);
-                else geo[threadIdx.x].active = 0;
-            }
-            __syncthreads();
-            for (int t = threadIdx.x; t < kEG * K; t += blockDim.x) {
-                const int g = t / K, k = t % K;
-                float e = 0.f, de = 0.f;
-                if (geo[g].active) expnorm_k(geo[g].d, k, rp, geo[g].phi, geo[g].dphi, e, de);
-                es[t] = e;
-                des[t] = de;
-            }
-            __syncthreads();
-            float part[kEG][4];
+        float gi[CPL][9], ta[CPL], tbi[CPL], accA[CPL], accB[CPL];
 #pragma unroll
-            for (int g = 0; g < kEG; ++g) {
-                part[g][0] = part[g][1] = part[g][2] = part[g][3] = 0.f;
-                if (!geo[g].active) {
-                    gfs[(g * 3 + 0) * F + c] = 0.f;
-                    gfs[(g * 3 + 1) * F + c] = 0.f;
-                    gfs[(g * 3 + 2) * F + c] = 0.f;
-                    continue;
-                }
-                float fI = bI, fA = bA, fS = bS;
-                const float *wI = Ws + (0 * F + c) * KP, *wA = Ws + (1 * F + c) * KP, *wS = Ws + (2 * F + c) * KP;
-                for (int k = 0; k < K; ++k) {
-                    const float ek = es[g * K + k];
-                    fI = fmaf(wI[k], ek, fI);
-                    fA = fmaf(wA[k], ek, fA);
-                    fS = fmaf(wS[k], ek, fS);
-                }
-                int zj = z[geo[g].j];
-                zj = (zj < 0 || zj >= max_z) ? 0 : zj;
-                const float Z = ta + Tb[(int64_t)zj * F + c];
-                const float phi = geo[g].phi;
-                const float ux = geo[g].u[0], uy = geo[g].u[1], uz = geo[g].u[2];
-                const float cA = phi * Z * fA, cS = phi * Z * fS;
-                const float gcI = gv[0];
-                const float gcA = gv[1] * ux + gv[2] * uy + gv[3] * uz;
-                const float bxx = ux * ux - (1.0f / 3.0f), byy = uy * uy - (1.0f / 3.0f);
-                const float gcS = gv[4] * bxx + gv[5] * byy + gv[6] * ux * uy + gv[7] * ux * uz + gv[8] * uy * uz;
-                part[g][0] = Z * (gcI * fI + gcA * fA + gcS * fS);  // d/dphi
-                part[g][1] = cA * gv[1] + cS * (2.f * ux * gv[4] + uy * gv[6] + uz * gv[7]);
-                part[g][2] = cA * gv[2] + cS * (2.f * uy * gv[5] + ux * gv[6] + uz * gv[8]);
-                part[g][3] = cA * gv[3] + cS * (ux * gv[7] + uy * gv[8]);
-                const float pz = phi * Z;
-                gfs[(g * 3 + 0) * F + c] = gcI * pz;
-                gfs[(g * 3 + 1) * F + c] = gcA * pz;
-                gfs[(g * 3 + 2) * F + c] = gcS * pz;
+        for (int k = 0; k < CPL; ++k) {
+            const int c = lane + 32 * k;
+            load_coords(gXraw, i, c, N, F, gi[k]);
+            ta[k] = Ta[(int64_t)zi * F + c];
+            tbi[k] = Tb[(int64_t)zi * F + c];
+            accA[k] = accB[k] = 0.f;
+        }
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int u = pair_of[e];
+            if (u < 0) {
+                if (lane == 0) edge_g[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                continue;
             }
+            const int j = col[e];
+            float x, y, zz;
+            pair_vec(pos, box, batch, i, j, x, y, zz);
+            const float d = sqrtf(x * x + y * y + zz * zz);
+            const float inv = 1.0f / d;
+            const float ux = x * inv, uy = y * inv, uz = zz * inv;
+            const float phi = cutoff_phi(d, rp);
+            const float bxx = ux * ux - (1.0f / 3.0f), byy = uy * uy - (1.0f / 3.0f);
+            const float bxy = ux * uy, bxz = ux * uz, byz = uy * uz;
+            int zj = z[j];
+            zj = (zj < 0 || zj >= max_z) ? 0 : zj;
+            const bool upper = j > i;
+            const bool need_j = upper || want_z;
+            float gphi = 0.f, gux = 0.f, guy = 0.f, guz = 0.f;
 #pragma unroll
-            for (int g = 0; g < kEG; ++g)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float s = warp_sum(part[g][q]);
-                    if (lane == 0) red[g][q][wid] = s;
-                }
-            __syncthreads();
-            // warp g: dE/dd of edge g = sum_k (ge_k de_k/dd) + gphi dphi/dd
-            for (int g = wid; g < kEG; g += nw) {
-                float s = 0.f;
-                if (geo[g].active) {
-                    const int e = eb + g;
-                    const int u = have_mlp ? pair_of[e] : -1;
-                    const bool upper = (u >= 0) && (geo[g].j > i);
-                    for (int k = lane; k < K; k += 32) {
-                        float gek = 0.f;
-                        for (int p = 0; p < 3; ++p) {
-                            const float *gf = gfs + (g * 3 + p) * F;
-                            const float *w = Ws + p * F * KP + k;
-                            for (int cc = 0; cc < F; ++cc) gek = fmaf(gf[cc], w[cc * KP], gek);
-                        }
-                        if (upper) gek += ge_u[(int64_t)u * K + k];
-                        s = fmaf(gek, des[g * K + k], s);
+            for (int k = 0; k < CPL; ++k) {
+                const int c = lane + 32 * k;
+                const float *fp = fu + (int64_t)u * 3 * F + c;
+                const float f0 = fp[0], f1 = fp[F], f2 = fp[2 * F];
+                const float Zij = ta[k] + Tb[(int64_t)zj * F + c];
+                const float *g = gi[k];
+                const float gc0 = g[0];
+                const float gcA = g[1] * ux + g[2] * uy + g[3] * uz;
+                const float gcS = g[4] * bxx + g[5] * byy + g[6] * bxy + g[7] * bxz + g[8] * byz;
+                const float dot = gc0 * f0 + gcA * f1 + gcS * f2;
+                gphi = fmaf(Zij, dot, gphi);
+                const float cA = phi * Zij * f1, cS = phi * Zij * f2;
+                gux += cA * g[1] + cS * (2.f * ux * g[4] + uy * g[6] + uz * g[7]);
+                guy += cA * g[2] + cS * (2.f * uy * g[5] + ux * g[6] + uz * g[8]);
+                guz += cA * g[3] + cS * (ux * g[7] + uy * g[8]);
+                accA[k] = fmaf(phi, dot, accA[k]);
+                if (need_j) {
+                    float gj[9];
+                    load_coords(gXraw, j, c, N, F, gj);
+                    // the reverse use (j, i): u_ji = -u, the S basis is even in u
+                    const float hc0 = gj[0];
+                    const float hcA = -(gj[1] * ux + gj[2] * uy + gj[3] * uz);
+                    const float hcS = gj[4] * bxx + gj[5] * byy + gj[6] * bxy + gj[7] * bxz + gj[8] * byz;
+                    const float Zji = Ta[(int64_t)zj * F + c] + tbi[k];
+                    if (upper) {
+                        float *o = gfu + (int64_t)u * 3 * F + c;
+                        o[0] = phi * (Zij * gc0 + Zji * hc0);
+                        o[F] = phi * (Zij * gcA + Zji * hcA);
+                        o[2 * F] = phi * (Zij * gcS + Zji * hcS);
                     }
-                    s = warp_sum(s);
-                    if (lane == 0) {
-                        float gphi = 0.f, gux = 0.f, guy = 0.f, guz = 0.f;
-                        for (int w = 0; w < nw; ++w) {
-                            gphi += red[g][0][w];
-                            gux += red[g][1][w];
-                            guy += red[g][2][w];
-                            guz += red[g][3][w];
-                        }
-                        if (upper) gphi += gphi_u[u];
-                        const float gd = s + gphi * geo[g].dphi;
-                        const float ux = geo[g].u[0], uy = geo[g].u[1], uz = geo[g].u[2];
-                        const float dot = gux * ux + guy * uy + guz * uz;
-                        const float inv = 1.0f / geo[g].d;
-                        float *o = gvec + 3LL * e;
-                        o[0] = gd * ux + (gux - dot * ux) * inv;
-                        o[1] = gd * uy + (guy - dot * uy) * inv;
-                        o[2] = gd * uz + (guz - dot * uz) * inv;
-                    }
-                } else if (lane == 0 && eb + g < e1) {
-                    float *o = gvec + 3LL * (eb + g);
-                    o[0] = o[1] = o[2] = 0.f;
+                    accB[k] = fmaf(phi, hc0 * f0 + hcA * f1 + hcS * f2, accB[k]);
                 }
             }
-            __syncthreads();
+            gphi = warp_sum(gphi);
+            gux = warp_sum(gux);
+            guy = warp_sum(guy);
+            guz = warp_sum(guz);
+            if (lane == 0) edge_g[e] = make_float4(gphi, gux, guy, guz);
+        }
+        if (want_z) {
+#pragma unroll
+            for (int k = 0; k < CPL; ++k) {
+                gA_atom[(int64_t)i * F + lane + 32 * k] = accA[k];
+                gB_atom[(int64_t)i * F + lane + 32 * k] = accB[k];
+            }
         }
     }
 }
 
-// F_i = -sum_{e in row i} (gvec[e] - gvec[rev[e]]) over the active edges of
-// the row, summed in row order by one thread per atom so the result does not
-// depend on inactive (skin) entries of the list.
-__global__ void k_forces(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ rev,
-                         const int32_t *__restrict__ pair_of, const float *__restrict__ gvec, int N,
+// dE/dr_ij of each undirected pair (i < j): one warp per pair, lane k < K.
+//   dE/dd   = sum_k ge[u][k] de_k/dd + (gphi_mlp[u] + gphi(i,j) + gphi(j,i)) dphi/dd
+//   dE/du   = gu(i,j) - gu(j,i)                       (u_ji = -u_ij)
+//   Gp[u]   = dE/dd u + (dE/du - (dE/du . u) u) / d
+__global__ void k_pair_vec(const float *__restrict__ pos, const float *__restrict__ box,
+                           const int32_t *__restrict__ batch, const int2 *__restrict__ uij,
+                           const int32_t *__restrict__ ue, const int32_t *__restrict__ rev,
+                           const int32_t *__restrict__ nu, RadialParams rp, const float *__restrict__ ge,
+                           const float *__restrict__ gphi_mlp, const float4 *__restrict__ edge_g,
+                           float *__restrict__ Gp) {
+    const int U = *nu;
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < U;
+         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int2 p = uij[u];
+        float x, y, zz;
+        pair_vec(pos, box, batch, p.x, p.y, x, y, zz);
+        const float d = sqrtf(x * x + y * y + zz * zz);
+        const float phi = cutoff_phi(d, rp), dphi = cutoff_dphi(d, rp);
+        float s = 0.f;
+        for (int k = lane; k < rp.K; k += 32) {
+            float e, de;
+            expnorm_k(d, k, rp, phi, dphi, e, de);
+            s = fmaf(ge ? ge[u * rp.K + k] : 0.f, de, s);
+        }
+        s = warp_sum(s);
+        if (lane == 0) {
+            const int e = ue[u];
+            const float4 a = edge_g[e], b = edge_g[rev[e]];
+            const float gphi = (gphi_mlp ? gphi_mlp[u] : 0.f) + a.x + b.x;
+            const float gd = s + gphi * dphi;
+            const float inv = 1.0f / d;
+            const float ux = x * inv, uy = y * inv, uz = zz * inv;
+            const float gx = a.y - b.y, gy = a.z - b.z, gz = a.w - b.w;
+            const float dot = gx * ux + gy * uy + gz * uz;
+            Gp[3 * u] = gd * ux + (gx - dot * ux) * inv;
+            Gp[3 * u + 1] = gd * uy + (gy - dot * uy) * inv;
+            Gp[3 * u + 2] = gd * uz + (gz - dot * uz) * inv;
+        }
+    }
+}
+
+// F_i = -dE/dr_i = -sum over the active edges of row i of +-Gp[pair]
+// (+ when i is the pair's first atom, r_ij = r_i - r_j), in row order.
+__global__ void k_forces(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                         const int32_t *__restrict__ pair_of, const float *__restrict__ Gp, int N,
                          float *__restrict__ forces) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float fx = 0.f, fy = 0.f, fz = 0.f;
     for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-        if (pair_of[e] < 0) continue;
-        const int r = rev[e];
-        fx += gvec[3LL * e] - gvec[3LL * r];
-        fy += gvec[3LL * e + 1] - gvec[3LL * r + 1];
-        fz += gvec[3LL * e + 2] - gvec[3LL * r + 2];
+        const int u = pair_of[e];
+        if (u < 0) continue;
+        const float sgn = col[e] > i ? 1.0f : -1.0f;
+        fx = fmaf(sgn, Gp[3LL * u], fx);
+        fy = fmaf(sgn, Gp[3LL * u + 1], fy);
+        fz = fmaf(sgn, Gp[3LL * u + 2], fz);
     }
     forces[3LL * i] = -fx;
     forces[3LL * i + 1] = -fy;
     forces[3LL * i + 2] = -fz;
 }
 
-// Opt the kernels with large dynamic shared memory into it (once per context).
+// Per-element sums of the pair-embedding adjoints (split over atom ranges):
+// zpart[s][0][z][c] = sum_{i in split s, z_i = z} gA_atom[i][c], and [1] for gB.
+__global__ void k_group_z(const int32_t *__restrict__ z, const float *__restrict__ gA,
+                          const float *__restrict__ gB, int N, int F, int max_z, int splits,
+                          float *__restrict__ zpart) {
+    const int zz = blockIdx.x, s = blockIdx.y, c = threadIdx.x;
+    const int chunk = (N + splits - 1) / splits;
+    const int i0 = s * chunk, i1 = min(N, i0 + chunk);
+    float a = 0.f, b = 0.f;
+    for (int i = i0; i < i1; ++i) {
+        if (z[i] == zz) {
+            a += gA[(int64_t)i * F + c];
+            b += gB[(int64_t)i * F + c];
+        }
+    }
+    zpart[(((int64_t)s * 2 + 0) * max_z + zz) * F + c] = a;
+    zpart[(((int64_t)s * 2 + 1) * max_z + zz) * F + c] = b;
+}
+
+// A[z] = sum over splits of the receiver sums, B[z] likewise for senders.
+__global__ void k_zreduce(const float *__restrict__ zpart, int splits, int F, int max_z, float *__restrict__ AB) {
+    const int zz = blockIdx.x, c = threadIdx.x;
+    for (int h = 0; h < 2; ++h) {
+        float acc = 0.f;
+        for (int s = 0; s < splits; ++s) acc += zpart[(((int64_t)s * 2 + h) * max_z + zz) * F + c];
+        AB[((int64_t)h * max_z + zz) * F + c] = acc;
+    }
+}
+
+// Gradients of the atom embedding and the pair embedding Linear from the
+// per-element sums A[z] (receiver) and B[z] (sender), Z_ij = W_e[emb_zi; emb_zj] + b_e.
+// Blocks 0..F-1 give rows of dW_e (and db_e), blocks F..F+max_z-1 rows of demb.
+__global__ void k_emb_tables_grad2(const float *__restrict__ AB, int F, int max_z, const float *__restrict__ emb,
+                                   const float *__restrict__ We, float *__restrict__ g_emb,
+                                   float *__restrict__ g_We, float *__restrict__ g_be) {
+    const int r = blockIdx.x, c = threadIdx.x;
+    const float *A = AB, *B = AB + (int64_t)max_z * F;
+    if (r < F) {
+        // g_We[r][c] = sum_z A[z][r] emb[z][c];  g_We[r][F + c] = sum_z B[z][r] emb[z][c]
+        float a = 0.f, b = 0.f;
+        for (int zz = 0; zz < max_z; ++zz) {
+            const float e = emb[(int64_t)zz * F + c];
+            a = fmaf(A[(int64_t)zz * F + r], e, a);
+            b = fmaf(B[(int64_t)zz * F + r], e, b);
+        }
+        g_We[(int64_t)r * 2 * F + c] = a;
+        g_We[(int64_t)r * 2 * F + F + c] = b;
+        if (r == 0) {
+            float bb = 0.f;
+            for (int zz = 0; zz < max_z; ++zz) bb += A[(int64_t)zz * F + c];
+            g_be[c] = bb;
+        }
+    } else {
+        // g_emb[z][c] = sum_r A[z][r] We[r][c] + B[z][r] We[r][F + c]
+        const int zz = r - F;
+        float a = 0.f;
+        for (int q = 0; q < F; ++q)
+            a += A[(int64_t)zz * F + q] * We[(int64_t)q * 2 * F + c] + B[(int64_t)zz * F + q] * We[(int64_t)q * 2 * F + F + c];
+        g_emb[(int64_t)zz * F + c] = a;
+    }
+}
+
+// dE/dE_i (seed of the system) and its products for the head gradients
+__global__ void k_seed_atoms(const float *__restrict__ seed, const int32_t *__restrict__ batch, int N,
+                             float *__restrict__ gEi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) gEi[i] = seed ? seed[batch ? batch[i] : 0] : 1.0f;
+}
+
+// Per-context kernel set-up (nothing needs opting in at present).
 int tnet_kernel_setup(tnet_ctx *c) {
-    const int F = c->d.F, K = c->d.K;
-    const size_t fwd = sizeof(float) * (3 * K * F + kEG * K);
-    const size_t bwd = sizeof(float) * (3 * F * (K + 1) + 2 * kEG * K + kEG * 3 * F);
-    TNET_CUDA_TRY(cudaFuncSetAttribute(k_emb_edges, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd));
-    TNET_CUDA_TRY(cudaFuncSetAttribute(k_emb_edges_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd));
+    (void)c;
     return TNET_OK;
 }
 
@@ -934,69 +980,86 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
                        const int32_t *row_ptr, const int32_t *col, const float *seed,
                        double *energy, float *forces, float *grad_w, int32_t *status,
                        cudaStream_t st) {
-    if (grad_w) return TNET_ERR_UNSUPPORTED;
     const tnet_model_desc &d = ctx->d;
     const Layout &Lw = ctx->lay;
     const int F = d.F, K = d.K, NL = d.L, H = F / 2;
     const int sms = ctx->num_sms;
     const RadialParams rp = ctx->rp;
-    Weights W;
+    Weights W, G;
     weight_offsets(&d, wblob, &W);
+    weight_offsets(&d, grad_w, &G);
+    auto gw = [](const float *p) { return const_cast<float *>(p); };
     auto f32 = [&](size_t off) { return wsp<float>(ctx, off); };
     auto i32 = [&](size_t off) { return wsp<int32_t>(ctx, off); };
     const int64_t n9 = Lw.node9;
     const int maxU = (int)Lw.maxU;
+    float *wpart = f32(Lw.wpart);
+    const int64_t wcap = Lw.wpart_floats;
     int32_t *sys_start = i32(Lw.sys_start), *sys_end = i32(Lw.sys_end);
     int32_t *rev = i32(Lw.rev), *pair_of = i32(Lw.pair_of), *ucnt = i32(Lw.ucnt);
-    int32_t *nu = i32(Lw.nu);
+    int32_t *nu = i32(Lw.nu), *ue = i32(Lw.ue);
     int2 *uij = wsp<int2>(ctx, Lw.uedge);
     float *Ta = f32(Lw.Ta), *Tb = f32(Lw.Tb);
     const int warps_grid = (int)(((int64_t)N * 32 + 255) / 256);
+    // row-sum shapes for weight gradients
+    auto rows1 = [&](int M_, int N_, int64_t R, const float *A, int64_t lda, const float *B, int64_t ldb,
+                     const int32_t *rows_dev) {
+        WgradShape P{};
+        P.M = M_; P.N = N_; P.rows[0] = R; P.row0[0] = 0; P.rows_dev = rows_dev; P.rows_mul = 1;
+        P.A = A; P.lda = lda; P.B = B; P.ldb = ldb; P.nclass = 1;
+        return P;
+    };
+    auto rows3 = [&](const float *A, const float *B) {  // the I, A, S coordinate planes
+        WgradShape P{};
+        P.M = F; P.N = F;
+        P.rows[0] = N; P.rows[1] = 3LL * N; P.rows[2] = 5LL * N;
+        P.row0[0] = 0; P.row0[1] = N; P.row0[2] = 4LL * N;
+        P.rows_dev = nullptr; P.rows_mul = 1;
+        P.A = A; P.lda = F; P.B = B; P.ldb = F; P.nclass = 3;
+        return P;
+    };
 
     // ---- graph prep
     ProfSeq pf(ctx, st);
     pf.mark(P_PREP);
     TNET_CUDA_TRY(cudaMemsetAsync(sys_start, 0, sizeof(int32_t) * S, st));
     TNET_CUDA_TRY(cudaMemsetAsync(sys_end, 0, sizeof(int32_t) * S, st));
-    if (N > 0) TRY(sys_bounds(batch, N, S, sys_start, sys_end, status, st));
-    if (N > 0) {
-        k_rev<<<warps_grid, 256, 0, st>>>(row_ptr, col, N, rev, status);
-        count_launch();
-        k_upper_count<<<warps_grid, 256, 0, st>>>(pos, box, batch, row_ptr, col, N, rp.rc, ucnt);
-        count_launch();
-        TNET_LAUNCH_CHECK();
-    }
+    TRY(sys_bounds(batch, N, S, sys_start, sys_end, status, st));
+    k_rev<<<warps_grid, 256, 0, st>>>(row_ptr, col, N, rev, status);
+    count_launch();
+    k_upper_count<<<warps_grid, 256, 0, st>>>(pos, box, batch, row_ptr, col, N, rp.rc, ucnt);
+    count_launch();
+    TNET_LAUNCH_CHECK();
     TRY(scan_exclusive_i32(ucnt, ucnt, N, i32(Lw.scan_tmp), nu, nullptr, st));
-    if (N > 0) {
-        k_upper_assign<<<warps_grid, 256, 0, st>>>(pos, box, batch, row_ptr, col, N, rp.rc, ucnt,
-                                                   pair_of, uij);
-        count_launch();
-        k_lower_assign<<<warps_grid, 256, 0, st>>>(row_ptr, col, rev, N, pair_of);
-        count_launch();
-        TNET_LAUNCH_CHECK();
-    }
-    float *eu = f32(Lw.eu), *phiu = f32(Lw.phiu);
+    k_upper_assign<<<warps_grid, 256, 0, st>>>(pos, box, batch, row_ptr, col, N, rp.rc, ucnt, pair_of, uij, ue);
+    count_launch();
+    k_lower_assign<<<warps_grid, 256, 0, st>>>(row_ptr, col, rev, N, pair_of);
+    count_launch();
+    TNET_LAUNCH_CHECK();
+    float *eu = f32(Lw.eu), *phiu = f32(Lw.phiu), *fu = f32(Lw.fu);
     k_edge_rbf<<<sms * 8, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu);
     count_launch();
     k_elem_tables<<<d.max_z, F, 0, st>>>(W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
     count_launch();
     TNET_LAUNCH_CHECK();
+    {   // radial projections f^p = W^p e(d) + b^p, once per undirected pair
+        GemmShape pp = gshape(maxU, 3 * F, K, eu, K, W.dproj_w, K);
+        pp.rows_dev = nu;
+        TRY(sgemm<false, true>(pp, EpiBiasAct{W.dproj_b, nullptr, 0, fu, 3 * F, 0, nullptr}, sms, st));
+    }
 
     // ---- embedding
     pf.mark(P_EMB_EDGE);
     float *Xraw = f32(Lw.Xraw), *Uemb = f32(Lw.Uemb), *n0 = f32(Lw.n0), *as1 = f32(Lw.as1),
-          *hs1 = f32(Lw.hs1), *as2 = f32(Lw.as2), *s = f32(Lw.s);
+          *hs1 = f32(Lw.hs1), *as2 = f32(Lw.as2), *s = f32(Lw.s), *q0 = f32(Lw.q0);
     float2 *ln0 = wsp<float2>(ctx, Lw.ln0);
-    const int emb_blocks = N < sms * 4 ? (N > 0 ? N : 1) : sms * 4;
-    const size_t emb_smem = sizeof(float) * (3 * K * F + kEG * K);
-    if (N > 0) {
-        k_emb_edges<<<emb_blocks, F, emb_smem, st>>>(pos, box, batch, z, row_ptr, col, N, F, d.max_z, rp,
-                                                     W.dproj_w, W.dproj_b, Ta, Tb, Xraw, status);
-        count_launch();
-        k_norm_ln<<<N, F, 0, st>>>(Xraw, N, F, W.emb_ln_g, W.emb_ln_b, n0, ln0);
-        count_launch();
-        TNET_LAUNCH_CHECK();
-    }
+    const int atom_blocks = N < sms * 8 ? N : sms * 8;
+    k_emb_edges<<<atom_blocks, F, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, F, d.max_z, rp, fu, Ta,
+                                           Tb, Xraw, status);
+    count_launch();
+    k_norm_ln<<<N, F, 0, st>>>(Xraw, N, F, W.emb_ln_g, W.emb_ln_b, n0, ln0, q0);
+    count_launch();
+    TNET_LAUNCH_CHECK();
     pf.mark(P_EMB_NODE);
     TRY(sgemm<false, true>(gshape(N, 2 * F, F, n0, F, W.emb_mlp1_w, F),
                            EpiBiasAct{W.emb_mlp1_b, as1, 2 * F, hs1, 2 * F, 1, nullptr}, sms, st));
@@ -1028,7 +1091,6 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         return TNET_OK;
     };
     const int ew = grid_for((int64_t)N * F, 256, sms);
-    const int atom_blocks = N < sms * 8 ? (N > 0 ? N : 1) : sms * 8;
     for (int l = 0; l < NL; ++l) {
         float *Xl = X + l * n9, *Xn = f32(Lw.Xn) + l * n9, *qn = f32(Lw.qn) + (int64_t)l * N * F;
         float *Y = f32(Lw.Y) + l * n9, *M = f32(Lw.M) + l * n9, *Tn = f32(Lw.Tn) + l * n9,
@@ -1062,27 +1124,24 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     float *h = f32(Lw.h), *hn = f32(Lw.hn), *ao = f32(Lw.ao), *o = f32(Lw.o), *at = f32(Lw.at),
           *t = f32(Lw.t), *Ei = f32(Lw.Ei);
     float2 *lno = wsp<float2>(ctx, Lw.lno);
-    if (N > 0) {
-        k_out_norms<<<N, F, 0, st>>>(Xfin, N, F, W.out_ln_g, W.out_ln_b, h, hn, lno);
-        count_launch();
-        TNET_LAUNCH_CHECK();
-    }
+    k_out_norms<<<N, F, 0, st>>>(Xfin, N, F, W.out_ln_g, W.out_ln_b, h, hn, lno);
+    count_launch();
+    TNET_LAUNCH_CHECK();
     TRY(sgemm<false, true>(gshape(N, F, 3 * F, hn, 3 * F, W.out_w, 3 * F),
                            EpiBiasAct{W.out_b, ao, F, o, F, 1, nullptr}, sms, st));
     TRY(sgemm<false, true>(gshape(N, H, F, o, F, W.head1_w, F),
                            EpiBiasAct{W.head1_b, at, H, t, H, 1, nullptr}, sms, st));
-    if (N > 0) {
-        k_head<<<warps_grid, 256, 0, st>>>(t, N, H, W.head2_w, W.head2_b, Ei);
-        count_launch();
-    }
+    k_head<<<warps_grid, 256, 0, st>>>(t, N, H, W.head2_w, W.head2_b, Ei);
+    count_launch();
     k_energy<<<S, 256, 0, st>>>(Ei, sys_start, sys_end, energy);
     count_launch();
     TNET_LAUNCH_CHECK();
-    if (!forces || N == 0) return TNET_OK;
+    if (!forces && !grad_w) return TNET_OK;
+    const bool wg = grad_w != nullptr;
 
     // ---- reverse pass
     pf.mark(P_OUT_BWD);
-    float *gat = f32(Lw.gat), *gao = f32(Lw.gao), *ghn = f32(Lw.ghn);
+    float *gat = f32(Lw.gat), *gao = f32(Lw.gao), *ghn = f32(Lw.ghn), *gEi = f32(Lw.gEi);
     float *gX = f32(Lw.gXa), *gdX = f32(Lw.gdX), *gTn = f32(Lw.gTn), *gM = f32(Lw.gM), *gY = f32(Lw.gY);
     float *gg = f32(Lw.gg), *ga2 = f32(Lw.ga2), *ga1 = f32(Lw.ga1), *ge = f32(Lw.ge), *gphiu = f32(Lw.gphiu);
     k_head_bwd<<<grid_for((int64_t)N * H, 256, sms), 256, 0, st>>>(at, N, H, W.head2_w, seed, batch, gat);
@@ -1093,17 +1152,34 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     k_out_norms_bwd<<<N, F, 0, st>>>(Xfin, h, ghn, lno, W.out_ln_g, N, F, gX);
     count_launch();
     TNET_LAUNCH_CHECK();
+    if (wg) {
+        k_seed_atoms<<<(N + 255) / 256, 256, 0, st>>>(seed, batch, N, gEi);
+        count_launch();
+        TNET_LAUNCH_CHECK();
+        TRY(wgrad_colsum(rows1(H, 1, N, t, H, nullptr, 0, nullptr), gEi, wpart, wcap, gw(G.head2_w), 0, sms, st));
+        TRY(wgrad_colsum(rows1(1, 1, N, gEi, 1, nullptr, 0, nullptr), nullptr, wpart, wcap, gw(G.head2_b), 0, sms,
+                         st));
+        TRY(wgrad_outer(rows1(H, F, N, gat, H, o, F, nullptr), wpart, wcap, gw(G.head1_w), 0, sms, st));
+        TRY(wgrad_colsum(rows1(H, 1, N, gat, H, nullptr, 0, nullptr), nullptr, wpart, wcap, gw(G.head1_b), 0, sms,
+                         st));
+        TRY(wgrad_outer(rows1(F, 3 * F, N, gao, F, hn, 3 * F, nullptr), wpart, wcap, gw(G.out_w), 0, sms, st));
+        TRY(wgrad_colsum(rows1(F, 1, N, gao, F, nullptr, 0, nullptr), nullptr, wpart, wcap, gw(G.out_b), 0, sms,
+                         st));
+        TRY(wgrad_layernorm(ghn, h, lno, N, 3 * F, wpart, wcap, gw(G.out_ln_g), sms, st));
+    }
     if (NL > 0) TNET_CUDA_TRY(cudaMemsetAsync(gphiu, 0, sizeof(float) * maxU, st));
     for (int l = NL - 1; l >= 0; --l) {
         const LayerW &Lr = W.layer[l];
+        const LayerW &Gr = G.layer[l];
         float *Xl = X + l * n9, *Xn = f32(Lw.Xn) + l * n9, *qn = f32(Lw.qn) + (int64_t)l * N * F;
-        float *Y = f32(Lw.Y) + l * n9, *M = f32(Lw.M) + l * n9, *dX = f32(Lw.dX) + l * n9;
-        (void)Xn;
+        float *Y = f32(Lw.Y) + l * n9, *M = f32(Lw.M) + l * n9, *dX = f32(Lw.dX) + l * n9,
+              *Tn = f32(Lw.Tn) + l * n9;
         pf.mark(P_NODE_BWD);
         k_residual_bwd<<<ew, 256, 0, st>>>(gX, dX, N, F, gdX);
         count_launch();
         TNET_LAUNCH_CHECK();
         TRY(sgemm<false, false>(gshape_classes(N, F, gdX, Lr.mix2_w), EpiStore{gTn, F, 0}, sms, st));
+        if (wg) TRY(wgrad_outer(rows3(gdX, Tn), wpart, wcap, gw(Gr.mix2_w), 0, sms, st));
         k_T_bwd<<<ew, 256, 0, st>>>(Y, M, gTn, N, F, gY, gM);
         count_launch();
         TNET_LAUNCH_CHECK();
@@ -1127,6 +1203,18 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         GemmShape q1 = gshape(maxU, K, F, ga1, F, Lr.mlp1_w, K);
         q1.rows_dev = nu;
         TRY(sgemm<false, false>(q1, EpiStore{ge, K, l != NL - 1}, sms, st));
+        if (wg) {
+            TRY(wgrad_outer(rows1(3 * F, 2 * F, maxU, gg, 3 * F, h2, 2 * F, nu), wpart, wcap, gw(Gr.mlp3_w), 0, sms, st));
+            TRY(wgrad_colsum(rows1(3 * F, 1, maxU, gg, 3 * F, nullptr, 0, nu), nullptr, wpart, wcap, gw(Gr.mlp3_b), 0,
+                             sms, st));
+            TRY(wgrad_outer(rows1(2 * F, F, maxU, ga2, 2 * F, h1, F, nu), wpart, wcap, gw(Gr.mlp2_w), 0, sms, st));
+            TRY(wgrad_colsum(rows1(2 * F, 1, maxU, ga2, 2 * F, nullptr, 0, nu), nullptr, wpart, wcap, gw(Gr.mlp2_b), 0,
+                             sms, st));
+            TRY(wgrad_outer(rows1(F, K, maxU, ga1, F, eu, K, nu), wpart, wcap, gw(Gr.mlp1_w), 0, sms, st));
+            TRY(wgrad_colsum(rows1(F, 1, maxU, ga1, F, nullptr, 0, nu), nullptr, wpart, wcap, gw(Gr.mlp1_b), 0, sms,
+                             st));
+            TRY(wgrad_outer(rows3(gY, Xn), wpart, wcap, gw(Gr.mix1_w), 0, sms, st));
+        }
         pf.mark(P_NODE_BWD);
         TRY(sgemm<false, false>(gshape_classes(N, F, gY, Lr.mix1_w), EpiStore{gX, F, 1}, sms, st));
         k_node_norm_bwd<<<ew, 256, 0, st>>>(Xl, qn, N, F, gX);
@@ -1147,15 +1235,64 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     k_ln0_bwd<<<N, F, 0, st>>>(Xraw, gn0, ln0, W.emb_ln_g, N, F, gXraw);
     count_launch();
     TNET_LAUNCH_CHECK();
+    if (wg) {
+        TRY(wgrad_outer(rows3(gU, Xraw), wpart, wcap, gw(G.emb_mix_w), 0, sms, st));
+        TRY(wgrad_outer(rows1(3 * F, 2 * F, N, gas2, 3 * F, hs1, 2 * F, nullptr), wpart, wcap, gw(G.emb_mlp2_w), 0,
+                        sms, st));
+        TRY(wgrad_colsum(rows1(3 * F, 1, N, gas2, 3 * F, nullptr, 0, nullptr), nullptr, wpart, wcap,
+                         gw(G.emb_mlp2_b), 0, sms, st));
+        TRY(wgrad_outer(rows1(2 * F, F, N, gas1, 2 * F, n0, F, nullptr), wpart, wcap, gw(G.emb_mlp1_w), 0, sms, st));
+        TRY(wgrad_colsum(rows1(2 * F, 1, N, gas1, 2 * F, nullptr, 0, nullptr), nullptr, wpart, wcap,
+                         gw(G.emb_mlp1_b), 0, sms, st));
+        TRY(wgrad_layernorm(gn0, q0, ln0, N, F, wpart, wcap, gw(G.emb_ln_g), sms, st));
+    }
     pf.mark(P_EMB_EDGE_BWD);
-    float *gvec = f32(Lw.gvec);
-    const size_t bwd_smem = sizeof(float) * (3 * F * (K + 1) + 2 * kEG * K + kEG * 3 * F);
-    k_emb_edges_bwd<<<emb_blocks, F, bwd_smem, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, F,
-                                                     d.max_z, rp, W.dproj_w, W.dproj_b, Ta, Tb, gXraw,
-                                                     ge, gphiu, NL > 0, gvec);
+    float *gfu = f32(Lw.gfu), *Gp = f32(Lw.gp), *gA = f32(Lw.gA_atom), *gB = f32(Lw.gB_atom);
+    float4 *edge_g = wsp<float4>(ctx, Lw.edge_g);
+    const int bwd_blocks = grid_for((int64_t)N * 32, 256, sms);
+#define EMB_BWD(CPL)                                                                                    \
+    k_emb_bwd<CPL><<<bwd_blocks, 256, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, d.max_z, rp, fu, \
+                                               Ta, Tb, gXraw, wg ? 1 : 0, gfu, edge_g, gA, gB)
+    switch (F / 32) {
+        case 2: EMB_BWD(2); break;
+        case 4: EMB_BWD(4); break;
+        case 6: EMB_BWD(6); break;
+        case 8: EMB_BWD(8); break;
+        case 10: EMB_BWD(10); break;
+        case 12: EMB_BWD(12); break;
+        case 14: EMB_BWD(14); break;
+        case 16: EMB_BWD(16); break;
+        default: return TNET_ERR_ARG;
+    }
+#undef EMB_BWD
     count_launch();
+    TNET_LAUNCH_CHECK();
+    {   // dE/de of the pair's radial basis also flows through the projections
+        GemmShape pg = gshape(maxU, K, 3 * F, gfu, 3 * F, W.dproj_w, K);
+        pg.rows_dev = nu;
+        TRY(sgemm<false, false>(pg, EpiStore{ge, K, NL > 0}, sms, st));
+    }
+    if (wg) {
+        TRY(wgrad_outer(rows1(3 * F, K, maxU, gfu, 3 * F, eu, K, nu), wpart, wcap, gw(G.dproj_w), 0, sms, st));
+        TRY(wgrad_colsum(rows1(3 * F, 1, maxU, gfu, 3 * F, nullptr, 0, nu), nullptr, wpart, wcap, gw(G.dproj_b), 0,
+                         sms, st));
+        const int zs = (int)Lw.zsplits;
+        float *zpart = f32(Lw.zpart);
+        k_group_z<<<dim3(d.max_z, zs), F, 0, st>>>(z, gA, gB, N, F, d.max_z, zs, zpart);
+        count_launch();
+        k_zreduce<<<d.max_z, F, 0, st>>>(zpart, zs, F, d.max_z, zpart);
+        count_launch();
+        k_emb_tables_grad2<<<F + d.max_z, F, 0, st>>>(zpart, F, d.max_z, W.emb, W.emb2_w, gw(G.emb), gw(G.emb2_w),
+                                                      gw(G.emb2_b));
+        count_launch();
+        TNET_LAUNCH_CHECK();
+    }
+    if (!forces) return TNET_OK;
     pf.mark(P_FORCES);
-    k_forces<<<(N + 127) / 128, 128, 0, st>>>(row_ptr, rev, pair_of, gvec, N, forces);
+    k_pair_vec<<<sms * 8, 256, 0, st>>>(pos, box, batch, uij, ue, rev, nu, rp, ge, NL > 0 ? gphiu : nullptr, edge_g,
+                                        Gp);
+    count_launch();
+    k_forces<<<(N + 127) / 128, 128, 0, st>>>(row_ptr, col, pair_of, Gp, N, forces);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;

@@ -174,3 +174,66 @@ def test_full_size_directional_finite_difference(name):
     an = -np.sum(F0.astype(np.float64) * dp)
     print(f"{name}: FD {fd:.6e} analytic {an:.6e} rel {abs(fd - an) / abs(an):.2e}")
     assert abs(fd - an) <= 1e-3 * abs(an)
+
+
+# ---------------------------------------------------------- weight grads ---
+def _compare_weight_grads(sys, shape=SHAPE, weights=W, seed=None):
+    from oracle.tensornet import TensorNet as Oracle
+    from paper_2402_17660_gb300.tnet import unpack_weights
+    m = make_model(weights, sys, shape=shape)
+    z, pos, batch, box = to_dev(sys)
+    nl = gpu_pairs(m, sys)
+    m.reset_status()
+    sd = None if seed is None else torch.tensor(seed, dtype=torch.float32, device=DEV)
+    E, F, G = m.energy_forces(z, pos, nl, batch if sys.n_systems > 1 else None, box, sys.n_systems,
+                              forces=True, grad_weights=True, seed=sd)
+    torch.cuda.synchronize()
+    m.check_status("energy_forces(grad_weights)")
+    Gg = unpack_weights(G.cpu().numpy(), shape.F, shape.K, shape.L, shape.max_z)
+    o = Oracle(weights, F=shape.F, K=shape.K, L=shape.L)
+    _, _, Fo, Go = o.energy_forces(sys.z, sys.pos, sys.batch, sys.box, n_systems=sys.n_systems, want_weights=True,
+                                   seed=seed)
+    assert force_error(F.cpu().numpy(), Fo) <= F_TOL
+    worst = 0.0
+    for k in Go:
+        ref = Go[k]
+        rms = np.sqrt(np.mean(ref ** 2))
+        err = np.sqrt(np.mean((Gg[k].astype(np.float64) - ref) ** 2))
+        rel = err / max(rms, 1e-30)
+        worst = max(worst, rel)
+        assert rel <= F_TOL, (k, rel)
+    print(f"{sys.name}: worst per-tensor rel RMS weight-gradient error {worst:.2e}")
+
+
+def test_weight_gradients_cluster():
+    _compare_weight_grads(_cluster(24, 600))
+
+
+def test_weight_gradients_periodic_batch_and_seed():
+    parts = [synth.random_cluster(20, seed=700 + k, side=10.5, min_dist=1.2) for k in range(3)]
+    s = synth.System("pbcbatch", np.concatenate([p.z for p in parts]), np.concatenate([p.pos for p in parts]),
+                     np.repeat(np.arange(3, dtype=np.int32), 20), np.tile((np.eye(3) * 10.5)[None], (3, 1, 1)).astype(np.float32), 3)
+    _compare_weight_grads(s, seed=np.array([1.0, -0.5, 2.0]))
+
+
+@pytest.mark.parametrize("L", [0, 1])
+def test_weight_gradients_other_layer_counts(L):
+    shape = synth.ModelShape(L=L)
+    _compare_weight_grads(_cluster(20, 800), shape=shape, weights=synth.init_weights(shape, seed=2))
+
+
+def test_weight_gradients_water3000():
+    _compare_weight_grads(synth.workload("water3000"))
+
+
+def test_autograd_function_weights():
+    s = _cluster(16, 900)
+    m = make_model(W, s)
+    z, pos, batch, box = to_dev(s)
+    nl = gpu_pairs(m, s)
+    w = m.weights.clone().requires_grad_(True)
+    E = EnergyFn.apply(pos, w, m, z, nl, None, None, 1)
+    (2.0 * E.sum()).backward()
+    _, _, G = m.energy_forces(z, pos, nl, grad_weights=True)
+    torch.cuda.synchronize()
+    assert torch.allclose(w.grad, 2.0 * G, rtol=1e-5, atol=1e-7)
