@@ -205,6 +205,15 @@ int tnet_neighbors_noalloc(int n_atoms, int n_systems, const float *pos, const i
                            const float *box, float cutoff, int32_t *row_ptr, int32_t *col, int64_t cap,
                            int64_t *n_pairs_dev, int32_t *status_dev, tnet_stream_t stream);
 
+/* ---- testing (no counterpart in the paper) --------------------------------
+ * C[M][N] = A[M][K] * B[N][K]^T on the tensor cores (tcgen05, BF16 inputs,
+ * FP32 accumulation), the GEMM engine of the BF16 precision mode, exposed so
+ * that tests can check it against a library matmul.  A, B bf16 K-major
+ * device arrays, C float32 [M][N]; K a multiple of 8, N a multiple of 4 and
+ * <= 512.  Bounded in-kernel waits report TNET_ERR_TIMEOUT in *status_dev. */
+int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void *B, float *C, int32_t *status_dev,
+                       tnet_stream_t stream);
+
 /* ---- instrumentation (no counterpart in the paper; used by the benchmark) */
 
 /* Number of CUDA kernels the library has enqueued in this process (all

@@ -34,6 +34,7 @@ SIGNATURES = {
     "tnet_md_step": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _f32, _f32, _i32, _i32, _vp, _vp,
                             _vp, _vp]),
     "tnet_neighbors_noalloc": (_i32, [_i32, _i32, _vp, _vp, _vp, _f32, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "tnet_debug_tc_gemm": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "tnet_launch_count": (_i64, []),
     "tnet_profile": (_i32, [_vp, _i32]),
     "tnet_profile_read": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_i64)]),

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtnet.so")
-SOURCES = ["neighbors.cu", "model.cu", "grad.cu", "api.cu", "md.cu", "noalloc.cu"]
+SOURCES = ["neighbors.cu", "model.cu", "grad.cu", "tc_gemm.cu", "api.cu", "md.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

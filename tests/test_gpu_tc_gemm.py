@@ -1,0 +1,39 @@
+"""The tcgen05 tensor-core GEMM (TMA + TMEM, BF16 inputs, FP32 accumulation)
+against torch's matmul of the same BF16 operands in FP32, through the C ABI,
+on ragged shapes (M not a multiple of the 128-row tile, K narrower than one
+64-wide k-block, N split over two 192-wide tiles)."""
+import ctypes
+
+import pytest
+import torch
+
+from paper_2402_17660_gb300 import _lib
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
+
+
+def _run(M, N, K, seed=0):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lib = _lib.load()
+    rc = lib.tnet_debug_tc_gemm(M, N, K, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(st.data_ptr()),
+                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = A.double() @ B.double().T
+    err = (C.double() - ref).abs().max().item()
+    scale = ref.abs().max().item()
+    return err, scale
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (1, 32, 32), (300, 128, 32), (1000, 256, 128),
+                                   (777, 384, 256), (129, 64, 384), (4096, 384, 256), (5000, 32, 128)])
+def test_tc_gemm_matches_matmul(M, N, K):
+    err, scale = _run(M, N, K)
+    # exact BF16 products, FP32 accumulation over K terms
+    assert err <= 1e-5 * scale * max(1.0, (K / 64) ** 0.5), (err, scale)
