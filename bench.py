@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water3000")
-    ap.add_argument("--precision", default="fp32", choices=["fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=3)
     return ap.parse_args()
@@ -158,31 +158,32 @@ def carve_cluster(sys_, n_target, seed=0):
                         np.zeros(len(idx), np.int32), None, 1)
 
 
-def oracle_eval_seconds(sys_, W, reps=1):
+def oracle_eval_seconds(sys_, W, reps=1, want=False):
     from oracle.neighbors import neighbor_pairs
     from oracle.tensornet import TensorNet as Oracle
     o = Oracle(W)
     t0 = time.perf_counter()
     for _ in range(reps):
         pr = neighbor_pairs(sys_.pos, sys_.batch, sys_.box, 5.0)
-        o.energy_forces(sys_.z, sys_.pos, sys_.batch, sys_.box, pairs=pr, n_systems=sys_.n_systems)
-    return (time.perf_counter() - t0) / reps
+        Es, Ei, Fr, _ = o.energy_forces(sys_.z, sys_.pos, sys_.batch, sys_.box, pairs=pr, n_systems=sys_.n_systems)
+    t = (time.perf_counter() - t0) / reps
+    return (t, (Es, Ei, Fr)) if want else t
 
 
 def cpu_baseline(sys_, W):
     """The oracle as it stands on the host cores, on a bounded sample."""
     if sys_.n_atoms <= 3000:
-        t = oracle_eval_seconds(sys_, W)
+        t, ref = oracle_eval_seconds(sys_, W, want=True)
         return {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                 "sample": f"one full FP64 oracle energy+force evaluation of {sys_.name} "
-                          f"(brute-force pairs + forward + analytic reverse pass), {t:.1f} s"}
+                          f"(brute-force pairs + forward + analytic reverse pass), {t:.1f} s"}, ref
     n = 1500
     sample = carve_cluster(sys_, n)
     t = oracle_eval_seconds(sample, W)
     scale = n / sys_.n_atoms
     return {"value": scale / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"FP64 oracle energy+force on a {n}-atom cluster carved from {sys_.name} "
-                      f"({t:.1f} s), evals/s scaled by {n}/{sys_.n_atoms} atoms"}
+                      f"({t:.1f} s), evals/s scaled by {n}/{sys_.n_atoms} atoms"}, None
 
 
 def workload_config(sys_, n_pairs, args, graph=True):
@@ -250,7 +251,8 @@ def run_ours(args):
     W = synth.init_weights(shape, seed=0)
     N = sys_.n_atoms
     cap = int(75 * N) + 1024
-    m = TensorNet(W, max_atoms=N, max_systems=sys_.n_systems, max_pairs=cap, device=dev)
+    prec = 1 if args.precision == "bf16" else 0
+    m = TensorNet(W, max_atoms=N, max_systems=sys_.n_systems, max_pairs=cap, precision=prec, device=dev)
     lib = m.lib
     z = torch.from_numpy(sys_.z).to(dev)
     pos = torch.from_numpy(sys_.pos).to(dev)
@@ -394,17 +396,40 @@ def run_ours(args):
            "path": "TensorNet.neighbors + TensorNet.energy_forces (eager) with pinned host positions in "
                    "and energy + forces out"}
 
+    # accuracy of this run's result: against the FP32 path on the same GPU, and
+    # (below, with the CPU baseline) against the FP64 oracle
+    m.energy_forces(z, pos, nl, batch, box, S, out=(E, Fo, None))
+    torch.cuda.synchronize()
+    E_run, F_run = E.cpu().numpy().copy(), Fo.cpu().numpy().astype(np.float64)
+    accuracy = {}
+    if prec:
+        m32 = TensorNet(W, max_atoms=N, max_systems=S, max_pairs=cap, precision=0, device=dev)
+        nl32 = m32.neighbors(pos, batch, box, S)
+        E32, F32, _ = m32.energy_forces(z, pos, nl32, batch, box, S)
+        torch.cuda.synchronize()
+        F32 = F32.cpu().numpy().astype(np.float64)
+        accuracy["vs_fp32_gpu"] = {
+            "energy_rel": float(np.max(np.abs(E_run - E32.cpu().numpy()) / np.maximum(np.abs(E32.cpu().numpy()), 1e-30))),
+            "force_rel_rms": float(np.sqrt(np.mean(np.sum((F_run - F32) ** 2, 1)) / np.mean(np.sum(F32 ** 2, 1))))}
+        del m32
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 GEMM / f32" if prec else "f32",
+            "data": "synthetic",
             "config": workload_config(sys_, n_pairs, args),
             "ns_per_day_at_0.5fs": value / world * 86400 * FS_PER_STEP * 1e-6,
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
             "stages_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in
                                    sorted(stages.items(), key=lambda kv: -kv[1]["ms_per_step"])},
-            "clocks": ck, "parallelism": f"replicas x{world}"}
+            "clocks": ck, "parallelism": f"replicas x{world}", "accuracy": accuracy}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sys_, W)
+        line["cpu_baseline"], ref = cpu_baseline(sys_, W)
+        if ref is not None:
+            Es, Ei, Fr = ref
+            scale = np.maximum(np.abs(Es), np.bincount(sys_.batch, weights=np.abs(Ei), minlength=len(Es)))
+            accuracy["vs_fp64_oracle"] = {
+                "energy_rel": float(np.max(np.abs(E_run - Es) / scale)),
+                "force_rel_rms": float(np.sqrt(np.mean(np.sum((F_run - Fr) ** 2, 1)) / np.mean(np.sum(Fr ** 2, 1))))}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

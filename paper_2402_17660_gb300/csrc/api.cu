@@ -129,6 +129,26 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->zpart = take(f * 2 * L->zsplits * Z * F);
     L->wpart_floats = 4LL << 20;
     L->wpart = take(f * L->wpart_floats);
+    // BF16 copies (only with precision 1): weights forward + transposed, one
+    // node-tensor operand, and the per-pair radial-MLP operands
+    const int64_t bfp = d->precision == 1 ? 1 : 0, b2 = 2;
+    int64_t nw = 0;
+    {
+        nw += Z * F + F * 2 * F + F + 3 * F * K + 3 * F + 2 * F + 2 * F * F + 2 * F + 3 * F * 2 * F + 3 * F +
+              3 * F * F;
+        nw += NL * (F * K + F + 2 * F * F + 2 * F + 3 * F * 2 * F + 3 * F + 6 * F * F);
+        nw += 6 * F + F * 3 * F + F + F / 2 * F + F / 2 + F / 2 + 1;
+    }
+    L->wbf_elems = 2 * nw;
+    L->wbf = take(bfp * b2 * L->wbf_elems);
+    L->nbf = take(bfp * b2 * n9);
+    L->eu_bf = take(bfp * b2 * U * K);
+    L->h1_bf = take(bfp * b2 * U * F);
+    L->h2_bf = take(bfp * b2 * U * 2 * F);
+    L->ga3_bf = take(bfp * b2 * U * 3 * F);
+    L->ga2_bf = take(bfp * b2 * U * 2 * F);
+    L->ga1_bf = take(bfp * b2 * U * F);
+    L->gfu_bf = take(bfp * b2 * U * 3 * F);
     // MD
     L->md_row_ptr = take(i * (N + 1));
     L->md_col = take(i * E);

@@ -13,6 +13,8 @@
 // inside a CUDA graph when the true count is only known on the device.
 // Tiles are visited by a persistent grid-stride loop.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace tnet {
@@ -34,6 +36,15 @@ struct GemmShape {
 
 // --------------------------------------------------------------- epilogues
 // Each epilogue receives 4 consecutive columns (n..n+3, all < N) of row m.
+// Optional BF16 copies feed the tensor-core GEMMs of the BF16 mode.
+__device__ __forceinline__ void store_bf16x4(__nv_bfloat16 *p, const float o[4]) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]), b = __floats2bfloat162_rn(o[2], o[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t *>(&a);
+    u.y = *reinterpret_cast<uint32_t *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+
 struct EpiStore {  // C = v (+ C when accumulate)
     float *C;
     int64_t ldc;
@@ -49,7 +60,7 @@ struct EpiStore {  // C = v (+ C when accumulate)
     }
 };
 
-struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m]
+struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m] (+ bf16 copy)
     const float *bias;
     float *pre;
     int64_t ldp;
@@ -57,6 +68,8 @@ struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m]
     int64_t ldo;
     int silu;
     const float *rowscale;
+    __nv_bfloat16 *out_bf;
+    int64_t ldob;
     __device__ void operator()(int z, int64_t m, int n, const float v[4]) const {
         float a[4], o[4];
         const float rs = rowscale ? rowscale[m] : 1.0f;
@@ -67,15 +80,18 @@ struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m]
         }
         if (pre) *reinterpret_cast<float4 *>(pre + m * ldp + n) = make_float4(a[0], a[1], a[2], a[3]);
         if (out) *reinterpret_cast<float4 *>(out + m * ldo + n) = make_float4(o[0], o[1], o[2], o[3]);
+        if (out_bf) store_bf16x4(out_bf + m * ldob + n, o);
     }
 };
 
-struct EpiGradAct {  // out = v * silu'(pre)  (+ out when accumulate)
+struct EpiGradAct {  // out = v * silu'(pre)  (+ out when accumulate) (+ bf16 copy)
     const float *pre;
     int64_t ldp;
     float *out;
     int64_t ldo;
     int accumulate;
+    __nv_bfloat16 *out_bf;
+    int64_t ldob;
     __device__ void operator()(int z, int64_t m, int n, const float v[4]) const {
         const float4 a = *reinterpret_cast<const float4 *>(pre + m * ldp + n);
         float o[4] = {v[0] * silu_grad_f(a.x), v[1] * silu_grad_f(a.y), v[2] * silu_grad_f(a.z),
@@ -86,6 +102,7 @@ struct EpiGradAct {  // out = v * silu'(pre)  (+ out when accumulate)
             o[0] += c.x; o[1] += c.y; o[2] += c.z; o[3] += c.w;
         }
         *p = make_float4(o[0], o[1], o[2], o[3]);
+        if (out_bf) store_bf16x4(out_bf + m * ldob + n, o);
     }
 };
 

@@ -1,6 +1,7 @@
 // Internal definitions shared by the libtnet CUDA sources.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -78,6 +79,17 @@ __device__ __forceinline__ void store_coords(float *__restrict__ T, int n, int c
     for (int k = 0; k < 3; ++k) pA[(int64_t)k * F] = v[1 + k];
 #pragma unroll
     for (int k = 0; k < 5; ++k) pS[(int64_t)k * F] = v[4 + k];
+}
+
+// optional BF16 copy of a node tensor (operand of the BF16 tensor-core mixing)
+__device__ __forceinline__ void store_coords_bf(__nv_bfloat16 *__restrict__ T, int n, int c, int N, int F,
+                                                const float v[9]) {
+    if (!T) return;
+    T[(int64_t)n * F + c] = __float2bfloat16_rn(v[0]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) T[((int64_t)N + 3LL * n + k) * F + c] = __float2bfloat16_rn(v[1 + k]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) T[(4LL * N + 5LL * n + k) * F + c] = __float2bfloat16_rn(v[4 + k]);
 }
 
 // coordinates -> row-major 3x3
@@ -239,6 +251,9 @@ struct Layout {
     size_t fu, gfu, ue, edge_g, gp, q0, gEi;
     // weight-gradient scratch
     size_t gA_atom, gB_atom, zpart, wpart;
+    // BF16 mode: operand copies for the tensor-core GEMMs
+    size_t wbf, nbf, eu_bf, h1_bf, h2_bf, ga3_bf, ga2_bf, ga1_bf, gfu_bf;
+    int64_t wbf_elems;
     int64_t wpart_floats, zsplits;
     // MD
     size_t md_row_ptr, md_col, md_npairs, md_forces, md_energy, md_pos_ref, md_step;

@@ -17,6 +17,7 @@
 //                per atom from its row and the reverse edges (no atomics).
 #include "gemm.cuh"
 #include "internal.cuh"
+#include "tc_gemm.cuh"
 
 namespace tnet {
 
@@ -198,7 +199,7 @@ __global__ void k_lower_assign(const int32_t *__restrict__ row_ptr, const int32_
 __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restrict__ box,
                            const int32_t *__restrict__ batch, const int2 *__restrict__ uij,
                            const int32_t *__restrict__ nu, int maxU, RadialParams rp,
-                           float *__restrict__ eu, float *__restrict__ phiu) {
+                           float *__restrict__ eu, float *__restrict__ phiu, __nv_bfloat16 *__restrict__ eu_bf) {
     const int U = *nu;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)U * rp.K;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -211,6 +212,7 @@ __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restric
         float e, de;
         expnorm_k(d, k, rp, phi, 0.f, e, de);
         eu[t] = e;
+        if (eu_bf) eu_bf[t] = __float2bfloat16_rn(e);
         if (k == 0) phiu[u] = phi;
     }
 }
@@ -265,7 +267,8 @@ __global__ void k_emb_edges(const float *__restrict__ pos, const float *__restri
                             const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                             const int32_t *__restrict__ pair_of, int N, int F, int max_z, RadialParams rp,
                             const float *__restrict__ fu, const float *__restrict__ Ta,
-                            const float *__restrict__ Tb, float *__restrict__ Xraw, int32_t *status) {
+                            const float *__restrict__ Tb, float *__restrict__ Xraw, int32_t *status,
+                            __nv_bfloat16 *__restrict__ Xraw_bf) {
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         int zi = z[i];
@@ -296,6 +299,7 @@ __global__ void k_emb_edges(const float *__restrict__ pos, const float *__restri
             v[6] += cS * ux * uy; v[7] += cS * ux * uz; v[8] += cS * uy * uz;
         }
         store_coords(Xraw, i, c, N, F, v);
+        store_coords_bf(Xraw_bf, i, c, N, F, v);
     }
 }
 
@@ -338,7 +342,7 @@ __global__ void k_emb_scale(const float *__restrict__ U, const float *__restrict
 // ----------------------------------------------------- interaction ---
 // Xn = X / (||X|| + 1)
 __global__ void k_node_norm(const float *__restrict__ X, int N, int F, float *__restrict__ qn,
-                            float *__restrict__ Xn) {
+                            float *__restrict__ Xn, __nv_bfloat16 *__restrict__ Xn_bf) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -350,6 +354,7 @@ __global__ void k_node_norm(const float *__restrict__ X, int N, int F, float *__
 #pragma unroll
         for (int k = 0; k < 9; ++k) v[k] *= r;
         store_coords(Xn, i, c, N, F, v);
+        store_coords_bf(Xn_bf, i, c, N, F, v);
     }
 }
 
@@ -380,7 +385,7 @@ __global__ void k_message(const int32_t *__restrict__ row_ptr, const int32_t *__
 
 // T = Y M + M Y; Tn = decomp(T) / (||T|| + 1)
 __global__ void k_node_update(const float *__restrict__ Y, const float *__restrict__ M, int N, int F,
-                              float *__restrict__ Tn) {
+                              float *__restrict__ Tn, __nv_bfloat16 *__restrict__ Tn_bf) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -398,6 +403,7 @@ __global__ void k_node_update(const float *__restrict__ Y, const float *__restri
 #pragma unroll
         for (int k = 0; k < 9; ++k) tc[k] *= r;
         store_coords(Tn, i, c, N, F, tc);
+        store_coords_bf(Tn_bf, i, c, N, F, tc);
     }
 }
 
@@ -522,7 +528,7 @@ __global__ void k_out_norms_bwd(const float *__restrict__ X, const float *__rest
 
 // X_out = Xn + dX + dX dX:  g_dX = g + expand^T(G Q^T + Q^T G), G = decomp^T(g)
 __global__ void k_residual_bwd(const float *__restrict__ gX, const float *__restrict__ dX, int N, int F,
-                               float *__restrict__ gdX) {
+                               float *__restrict__ gdX, __nv_bfloat16 *__restrict__ gdX_bf) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -539,6 +545,7 @@ __global__ void k_residual_bwd(const float *__restrict__ gX, const float *__rest
 #pragma unroll
         for (int k = 0; k < 9; ++k) g[k] += gq[k];
         store_coords(gdX, i, c, N, F, g);
+        store_coords_bf(gdX_bf, i, c, N, F, g);
     }
 }
 
@@ -593,7 +600,7 @@ __global__ void k_T_bwd(const float *__restrict__ Y, const float *__restrict__ M
 __global__ void k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                               const int32_t *__restrict__ pair_of, const float *__restrict__ gU,
                               const float *__restrict__ Y, const float *__restrict__ gM, int N, int F,
-                              float *__restrict__ gY, float *__restrict__ gg) {
+                              float *__restrict__ gY, float *__restrict__ gg, __nv_bfloat16 *__restrict__ gY_bf) {
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         float yi[9], gmi[9], acc[9];
@@ -626,13 +633,14 @@ __global__ void k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t
             }
         }
         store_coords(gY, i, c, N, F, acc);
+        store_coords_bf(gY_bf, i, c, N, F, acc);
     }
 }
 
 // g = phi * silu(a3):  ga3 = gg * phi * silu'(a3) (in place), gphi += <gg, silu(a3)>
 __global__ void k_mlp3_bwd(float *__restrict__ gg, const float *__restrict__ a3,
                            const float *__restrict__ phiu, const int32_t *__restrict__ nu, int W,
-                           float *__restrict__ gphi) {
+                           float *__restrict__ gphi, __nv_bfloat16 *__restrict__ ga3_bf) {
     const int U = *nu;
     const int lane = threadIdx.x & 31;
     for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < U;
@@ -643,7 +651,9 @@ __global__ void k_mlp3_bwd(float *__restrict__ gg, const float *__restrict__ a3,
             const int64_t o = u * W + n;
             const float a = a3[o], gv = gg[o];
             s = fmaf(gv, silu_f(a), s);
-            gg[o] = gv * phi * silu_grad_f(a);
+            const float ga = gv * phi * silu_grad_f(a);
+            gg[o] = ga;
+            if (ga3_bf) ga3_bf[o] = __float2bfloat16_rn(ga);
         }
         s = warp_sum(s);
         if (lane == 0) gphi[u] += s;
@@ -674,7 +684,7 @@ __global__ void k_node_norm_bwd(const float *__restrict__ X, const float *__rest
 // X0 = s_p * U:  gU = s_p gX0; gas2 = <gX0, U>_p * silu'(as2)
 __global__ void k_emb_scale_bwd(const float *__restrict__ gX0, const float *__restrict__ U,
                                 const float *__restrict__ s, const float *__restrict__ as2, int N, int F,
-                                float *__restrict__ gU, float *__restrict__ gas2) {
+                                float *__restrict__ gU, float *__restrict__ gas2, __nv_bfloat16 *__restrict__ gU_bf) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -693,6 +703,7 @@ __global__ void k_emb_scale_bwd(const float *__restrict__ gX0, const float *__re
 #pragma unroll
         for (int k = 4; k < 9; ++k) g[k] *= si[2];
         store_coords(gU, i, c, N, F, g);
+        store_coords_bf(gU_bf, i, c, N, F, g);
 #pragma unroll
         for (int p = 0; p < 3; ++p) gas2[t * 3 + p] = gs[p] * silu_grad_f(as2[t * 3 + p]);
     }
@@ -735,7 +746,7 @@ __global__ void k_emb_bwd(const float *__restrict__ pos, const float *__restrict
                           const float *__restrict__ fu, const float *__restrict__ Ta,
                           const float *__restrict__ Tb, const float *__restrict__ gXraw, int want_z,
                           float *__restrict__ gfu, float4 *__restrict__ edge_g, float *__restrict__ gA_atom,
-                          float *__restrict__ gB_atom) {
+                          float *__restrict__ gB_atom, __nv_bfloat16 *__restrict__ gfu_bf) {
     constexpr int F = CPL * 32;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -800,9 +811,18 @@ __global__ void k_emb_bwd(const float *__restrict__ pos, const float *__restrict
                     const float Zji = Ta[(int64_t)zj * F + c] + tbi[k];
                     if (upper) {
                         float *o = gfu + (int64_t)u * 3 * F + c;
-                        o[0] = phi * (Zij * gc0 + Zji * hc0);
-                        o[F] = phi * (Zij * gcA + Zji * hcA);
-                        o[2 * F] = phi * (Zij * gcS + Zji * hcS);
+                        const float o0 = phi * (Zij * gc0 + Zji * hc0);
+                        const float o1 = phi * (Zij * gcA + Zji * hcA);
+                        const float o2 = phi * (Zij * gcS + Zji * hcS);
+                        o[0] = o0;
+                        o[F] = o1;
+                        o[2 * F] = o2;
+                        if (gfu_bf) {
+                            __nv_bfloat16 *ob = gfu_bf + (int64_t)u * 3 * F + c;
+                            ob[0] = __float2bfloat16_rn(o0);
+                            ob[F] = __float2bfloat16_rn(o1);
+                            ob[2 * F] = __float2bfloat16_rn(o2);
+                        }
                     }
                     accB[k] = fmaf(phi, hc0 * f0 + hcA * f1 + hcS * f2, accB[k]);
                 }
@@ -955,10 +975,43 @@ __global__ void k_seed_atoms(const float *__restrict__ seed, const int32_t *__re
     if (i < N) gEi[i] = seed ? seed[batch ? batch[i] : 0] : 1.0f;
 }
 
+// BF16 copies of the GEMM weights for the tensor-core mode: job j converts
+// a [rows][cols] float matrix, transposed when tr[j] (backward operands).
+constexpr int kMaxCvtJobs = 128;
+struct CvtJobs {
+    const float *src[kMaxCvtJobs];
+    __nv_bfloat16 *dst[kMaxCvtJobs];
+    int rows[kMaxCvtJobs], cols[kMaxCvtJobs], tr[kMaxCvtJobs];
+    int n;
+};
+__global__ void k_cvt_weights(const __grid_constant__ CvtJobs J) {
+    const int j = blockIdx.y;
+    if (j >= J.n) return;
+    const int R = J.rows[j], C = J.cols[j];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < R * C; t += gridDim.x * blockDim.x) {
+        const int r = t / C, c = t % C;
+        const __nv_bfloat16 v = __float2bfloat16_rn(J.src[j][t]);
+        J.dst[j][J.tr[j] ? (int64_t)c * R + r : (int64_t)t] = v;
+    }
+}
+
 // Per-context kernel set-up (nothing needs opting in at present).
 int tnet_kernel_setup(tnet_ctx *c) {
     (void)c;
     return TNET_OK;
+}
+
+// Tensor-core GEMM with the column tile chosen from N.
+template <class Epi>
+int tc_any(const tc::TcShape &P, const __nv_bfloat16 *A, int64_t a_rows, int64_t lda, const __nv_bfloat16 *B,
+           int64_t b_rows, int64_t ldb, const Epi &epi, int32_t *status, cudaStream_t st) {
+    if (P.N <= 32) return tc::tc_gemm<32>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
+    if (P.N <= 64) return tc::tc_gemm<64>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
+    if (P.N <= 128) return tc::tc_gemm<128>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
+    if (P.N % 256 == 0) return tc::tc_gemm<256>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
+    if (P.N % 192 == 0) return tc::tc_gemm<192>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
+    if (P.N % 128 == 0) return tc::tc_gemm<128>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
+    return TNET_ERR_ARG;
 }
 
 // ============================================================ driver ===
@@ -1019,9 +1072,63 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         return P;
     };
 
+    // ---- BF16 tensor-core mode: operand buffers and weight copies
+    const bool bf = d.precision == 1;
+    auto bfp = [&](size_t off) { return bf ? wsp<__nv_bfloat16>(ctx, off) : (__nv_bfloat16 *)nullptr; };
+    __nv_bfloat16 *nbf = bfp(Lw.nbf), *eu_bf = bfp(Lw.eu_bf), *h1_bf = bfp(Lw.h1_bf), *h2_bf = bfp(Lw.h2_bf),
+                  *ga3_bf = bfp(Lw.ga3_bf), *ga2_bf = bfp(Lw.ga2_bf), *ga1_bf = bfp(Lw.ga1_bf),
+                  *gfu_bf = bfp(Lw.gfu_bf);
+    struct LayerB {
+        __nv_bfloat16 *mlp1, *mlp2, *mlp3, *mlp1T, *mlp2T, *mlp3T, *mix1, *mix1T, *mix2, *mix2T;
+    } lb[8] = {};
+    __nv_bfloat16 *dproj_b16 = nullptr, *dprojT_b16 = nullptr, *emix_b16 = nullptr, *emixT_b16 = nullptr;
+
     // ---- graph prep
     ProfSeq pf(ctx, st);
     pf.mark(P_PREP);
+    if (bf) {
+        CvtJobs J;
+        J.n = 0;
+        __nv_bfloat16 *wb = wsp<__nv_bfloat16>(ctx, Lw.wbf);
+        int64_t woff = 0;
+        auto job = [&](const float *src, int rows, int cols, int tr) {
+            __nv_bfloat16 *dst = wb + woff;
+            woff += (int64_t)rows * cols;
+            woff = (woff + 127) & ~(int64_t)127;
+            J.src[J.n] = src; J.dst[J.n] = dst; J.rows[J.n] = rows; J.cols[J.n] = cols; J.tr[J.n] = tr;
+            ++J.n;
+            return dst;
+        };
+        auto job_classes_T = [&](const float *src) {  // [3][F][F] -> per-class transposes
+            __nv_bfloat16 *first = nullptr;
+            for (int q = 0; q < 3; ++q) {
+                __nv_bfloat16 *p = job(src + (int64_t)q * F * F, F, F, 1);
+                if (!q) first = p;
+            }
+            return first;
+        };
+        dproj_b16 = job(W.dproj_w, 3 * F, K, 0);
+        dprojT_b16 = job(W.dproj_w, 3 * F, K, 1);
+        emix_b16 = job(W.emb_mix_w, 3 * F, F, 0);
+        emixT_b16 = job_classes_T(W.emb_mix_w);
+        for (int l = 0; l < NL; ++l) {
+            const LayerW &Lr = W.layer[l];
+            lb[l].mlp1 = job(Lr.mlp1_w, F, K, 0);
+            lb[l].mlp2 = job(Lr.mlp2_w, 2 * F, F, 0);
+            lb[l].mlp3 = job(Lr.mlp3_w, 3 * F, 2 * F, 0);
+            lb[l].mlp1T = job(Lr.mlp1_w, F, K, 1);
+            lb[l].mlp2T = job(Lr.mlp2_w, 2 * F, F, 1);
+            lb[l].mlp3T = job(Lr.mlp3_w, 3 * F, 2 * F, 1);
+            lb[l].mix1 = job(Lr.mix1_w, 3 * F, F, 0);
+            lb[l].mix1T = job_classes_T(Lr.mix1_w);
+            lb[l].mix2 = job(Lr.mix2_w, 3 * F, F, 0);
+            lb[l].mix2T = job_classes_T(Lr.mix2_w);
+        }
+        if (woff > Lw.wbf_elems || J.n > kMaxCvtJobs) return TNET_ERR_WORKSPACE;
+        k_cvt_weights<<<dim3(64, J.n), 256, 0, st>>>(J);
+        count_launch();
+        TNET_LAUNCH_CHECK();
+    }
     TNET_CUDA_TRY(cudaMemsetAsync(sys_start, 0, sizeof(int32_t) * S, st));
     TNET_CUDA_TRY(cudaMemsetAsync(sys_end, 0, sizeof(int32_t) * S, st));
     TRY(sys_bounds(batch, N, S, sys_start, sys_end, status, st));
@@ -1037,15 +1144,22 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     float *eu = f32(Lw.eu), *phiu = f32(Lw.phiu), *fu = f32(Lw.fu);
-    k_edge_rbf<<<sms * 8, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu);
+    k_edge_rbf<<<sms * 8, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu, eu_bf);
     count_launch();
     k_elem_tables<<<d.max_z, F, 0, st>>>(W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
     count_launch();
     TNET_LAUNCH_CHECK();
     {   // radial projections f^p = W^p e(d) + b^p, once per undirected pair
-        GemmShape pp = gshape(maxU, 3 * F, K, eu, K, W.dproj_w, K);
-        pp.rows_dev = nu;
-        TRY(sgemm<false, true>(pp, EpiBiasAct{W.dproj_b, nullptr, 0, fu, 3 * F, 0, nullptr}, sms, st));
+        const EpiBiasAct ep{W.dproj_b, nullptr, 0, fu, 3 * F, 0, nullptr};
+        if (bf) {
+            tc::TcShape tp = tc::tshape(maxU, 3 * F, K);
+            tp.rows_dev = nu;
+            TRY(tc_any(tp, eu_bf, maxU, K, dproj_b16, 3 * F, K, ep, status, st));
+        } else {
+            GemmShape pp = gshape(maxU, 3 * F, K, eu, K, W.dproj_w, K);
+            pp.rows_dev = nu;
+            TRY(sgemm<false, true>(pp, ep, sms, st));
+        }
     }
 
     // ---- embedding
@@ -1055,7 +1169,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     float2 *ln0 = wsp<float2>(ctx, Lw.ln0);
     const int atom_blocks = N < sms * 8 ? N : sms * 8;
     k_emb_edges<<<atom_blocks, F, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, F, d.max_z, rp, fu, Ta,
-                                           Tb, Xraw, status);
+                                           Tb, Xraw, status, nbf);
     count_launch();
     k_norm_ln<<<N, F, 0, st>>>(Xraw, N, F, W.emb_ln_g, W.emb_ln_b, n0, ln0, q0);
     count_launch();
@@ -1065,7 +1179,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
                            EpiBiasAct{W.emb_mlp1_b, as1, 2 * F, hs1, 2 * F, 1, nullptr}, sms, st));
     TRY(sgemm<false, true>(gshape(N, 3 * F, 2 * F, hs1, 2 * F, W.emb_mlp2_w, 2 * F),
                            EpiBiasAct{W.emb_mlp2_b, as2, 3 * F, s, 3 * F, 1, nullptr}, sms, st));
-    TRY(sgemm<false, true>(gshape_classes(N, F, Xraw, W.emb_mix_w), EpiStore{Uemb, F, 0}, sms, st));
+    if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, emix_b16, 3 * F, F, EpiStore{Uemb, F, 0}, status, st));
+    else TRY(sgemm<false, true>(gshape_classes(N, F, Xraw, W.emb_mix_w), EpiStore{Uemb, F, 0}, sms, st));
     float *X = f32(Lw.Xin);  // layer 0 input
     k_emb_scale<<<grid_for((int64_t)N * F, 256, sms), 256, 0, st>>>(Uemb, s, N, F, X);
     count_launch();
@@ -1076,18 +1191,32 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
           *gbuf = f32(Lw.g);
     auto edge_mlp = [&](int l) -> int {
         const LayerW &Lr = W.layer[l];
+        const EpiBiasAct e1{Lr.mlp1_b, a1, F, h1, F, 1, nullptr, h1_bf, F};
+        const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, h2, 2 * F, 1, nullptr, h2_bf, 2 * F};
+        const EpiBiasAct e3{Lr.mlp3_b, a3, 3 * F, gbuf, 3 * F, 1, phiu};
+        if (bf) {
+            tc::TcShape t1 = tc::tshape(maxU, F, K), t2 = tc::tshape(maxU, 2 * F, F), t3 = tc::tshape(maxU, 3 * F, 2 * F);
+            t1.rows_dev = t2.rows_dev = t3.rows_dev = nu;
+            pf.mark(P_MLP1);
+            TRY(tc_any(t1, eu_bf, maxU, K, lb[l].mlp1, F, K, e1, status, st));
+            pf.mark(P_MLP2);
+            TRY(tc_any(t2, h1_bf, maxU, F, lb[l].mlp2, 2 * F, F, e2, status, st));
+            pf.mark(P_MLP3);
+            TRY(tc_any(t3, h2_bf, maxU, 2 * F, lb[l].mlp3, 3 * F, 2 * F, e3, status, st));
+            return TNET_OK;
+        }
         pf.mark(P_MLP1);
         GemmShape p1 = gshape(maxU, F, K, eu, K, Lr.mlp1_w, K);
         p1.rows_dev = nu;
-        TRY(sgemm<false, true>(p1, EpiBiasAct{Lr.mlp1_b, a1, F, h1, F, 1, nullptr}, sms, st));
+        TRY(sgemm<false, true>(p1, e1, sms, st));
         pf.mark(P_MLP2);
         GemmShape p2 = gshape(maxU, 2 * F, F, h1, F, Lr.mlp2_w, F);
         p2.rows_dev = nu;
-        TRY(sgemm<false, true>(p2, EpiBiasAct{Lr.mlp2_b, a2, 2 * F, h2, 2 * F, 1, nullptr}, sms, st));
+        TRY(sgemm<false, true>(p2, e2, sms, st));
         pf.mark(P_MLP3);
         GemmShape p3 = gshape(maxU, 3 * F, 2 * F, h2, 2 * F, Lr.mlp3_w, 2 * F);
         p3.rows_dev = nu;
-        TRY(sgemm<false, true>(p3, EpiBiasAct{Lr.mlp3_b, a3, 3 * F, gbuf, 3 * F, 1, phiu}, sms, st));
+        TRY(sgemm<false, true>(p3, e3, sms, st));
         return TNET_OK;
     };
     const int ew = grid_for((int64_t)N * F, 256, sms);
@@ -1097,21 +1226,23 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
               *dX = f32(Lw.dX) + l * n9;
         float *Xnext = (l + 1 < NL) ? X + (l + 1) * n9 : f32(Lw.Xfin);
         pf.mark(P_NODE_ELEM);
-        k_node_norm<<<ew, 256, 0, st>>>(Xl, N, F, qn, Xn);
+        k_node_norm<<<ew, 256, 0, st>>>(Xl, N, F, qn, Xn, nbf);
         count_launch();
         TNET_LAUNCH_CHECK();
         pf.mark(P_NODE_MIX);
-        TRY(sgemm<false, true>(gshape_classes(N, F, Xn, W.layer[l].mix1_w), EpiStore{Y, F, 0}, sms, st));
+        if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix1, 3 * F, F, EpiStore{Y, F, 0}, status, st));
+        else TRY(sgemm<false, true>(gshape_classes(N, F, Xn, W.layer[l].mix1_w), EpiStore{Y, F, 0}, sms, st));
         TRY(edge_mlp(l));
         pf.mark(P_MESSAGE);
         k_message<<<atom_blocks, F, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, N, F, M);
         count_launch();
         pf.mark(P_NODE_ELEM);
-        k_node_update<<<ew, 256, 0, st>>>(Y, M, N, F, Tn);
+        k_node_update<<<ew, 256, 0, st>>>(Y, M, N, F, Tn, nbf);
         count_launch();
         TNET_LAUNCH_CHECK();
         pf.mark(P_NODE_MIX);
-        TRY(sgemm<false, true>(gshape_classes(N, F, Tn, W.layer[l].mix2_w), EpiStore{dX, F, 0}, sms, st));
+        if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix2, 3 * F, F, EpiStore{dX, F, 0}, status, st));
+        else TRY(sgemm<false, true>(gshape_classes(N, F, Tn, W.layer[l].mix2_w), EpiStore{dX, F, 0}, sms, st));
         pf.mark(P_NODE_ELEM);
         k_residual<<<ew, 256, 0, st>>>(Xn, dX, N, F, Xnext);
         count_launch();
@@ -1175,34 +1306,49 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         float *Y = f32(Lw.Y) + l * n9, *M = f32(Lw.M) + l * n9, *dX = f32(Lw.dX) + l * n9,
               *Tn = f32(Lw.Tn) + l * n9;
         pf.mark(P_NODE_BWD);
-        k_residual_bwd<<<ew, 256, 0, st>>>(gX, dX, N, F, gdX);
+        k_residual_bwd<<<ew, 256, 0, st>>>(gX, dX, N, F, gdX, nbf);
         count_launch();
         TNET_LAUNCH_CHECK();
-        TRY(sgemm<false, false>(gshape_classes(N, F, gdX, Lr.mix2_w), EpiStore{gTn, F, 0}, sms, st));
+        if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix2T, 3 * F, F, EpiStore{gTn, F, 0}, status, st));
+        else TRY(sgemm<false, false>(gshape_classes(N, F, gdX, Lr.mix2_w), EpiStore{gTn, F, 0}, sms, st));
         if (wg) TRY(wgrad_outer(rows3(gdX, Tn), wpart, wcap, gw(Gr.mix2_w), 0, sms, st));
         k_T_bwd<<<ew, 256, 0, st>>>(Y, M, gTn, N, F, gY, gM);
         count_launch();
         TNET_LAUNCH_CHECK();
         TRY(edge_mlp(l));  // recompute a1, h1, a2, h2, a3, g of this layer
         pf.mark(P_MSG_BWD);
-        k_message_bwd<<<atom_blocks, F, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, gM, N, F, gY, gg);
+        k_message_bwd<<<atom_blocks, F, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, gM, N, F, gY, gg, nbf);
         count_launch();
         pf.mark(P_MLP_ELEM_BWD);
-        k_mlp3_bwd<<<sms * 8, 256, 0, st>>>(gg, a3, phiu, nu, 3 * F, gphiu);
+        k_mlp3_bwd<<<sms * 8, 256, 0, st>>>(gg, a3, phiu, nu, 3 * F, gphiu, ga3_bf);
         count_launch();
         TNET_LAUNCH_CHECK();
-        pf.mark(P_MLP3_BWD);
-        GemmShape q3 = gshape(maxU, 2 * F, 3 * F, gg, 3 * F, Lr.mlp3_w, 2 * F);
-        q3.rows_dev = nu;
-        TRY(sgemm<false, false>(q3, EpiGradAct{a2, 2 * F, ga2, 2 * F, 0}, sms, st));
-        pf.mark(P_MLP2_BWD);
-        GemmShape q2 = gshape(maxU, F, 2 * F, ga2, 2 * F, Lr.mlp2_w, F);
-        q2.rows_dev = nu;
-        TRY(sgemm<false, false>(q2, EpiGradAct{a1, F, ga1, F, 0}, sms, st));
-        pf.mark(P_MLP1_BWD);
-        GemmShape q1 = gshape(maxU, K, F, ga1, F, Lr.mlp1_w, K);
-        q1.rows_dev = nu;
-        TRY(sgemm<false, false>(q1, EpiStore{ge, K, l != NL - 1}, sms, st));
+        const EpiGradAct g3{a2, 2 * F, ga2, 2 * F, 0, ga2_bf, 2 * F};
+        const EpiGradAct g2{a1, F, ga1, F, 0, ga1_bf, F};
+        const EpiStore g1{ge, K, l != NL - 1};
+        if (bf) {
+            tc::TcShape t3 = tc::tshape(maxU, 2 * F, 3 * F), t2 = tc::tshape(maxU, F, 2 * F), t1 = tc::tshape(maxU, K, F);
+            t1.rows_dev = t2.rows_dev = t3.rows_dev = nu;
+            pf.mark(P_MLP3_BWD);
+            TRY(tc_any(t3, ga3_bf, maxU, 3 * F, lb[l].mlp3T, 2 * F, 3 * F, g3, status, st));
+            pf.mark(P_MLP2_BWD);
+            TRY(tc_any(t2, ga2_bf, maxU, 2 * F, lb[l].mlp2T, F, 2 * F, g2, status, st));
+            pf.mark(P_MLP1_BWD);
+            TRY(tc_any(t1, ga1_bf, maxU, F, lb[l].mlp1T, K, F, g1, status, st));
+        } else {
+            pf.mark(P_MLP3_BWD);
+            GemmShape q3 = gshape(maxU, 2 * F, 3 * F, gg, 3 * F, Lr.mlp3_w, 2 * F);
+            q3.rows_dev = nu;
+            TRY(sgemm<false, false>(q3, g3, sms, st));
+            pf.mark(P_MLP2_BWD);
+            GemmShape q2 = gshape(maxU, F, 2 * F, ga2, 2 * F, Lr.mlp2_w, F);
+            q2.rows_dev = nu;
+            TRY(sgemm<false, false>(q2, g2, sms, st));
+            pf.mark(P_MLP1_BWD);
+            GemmShape q1 = gshape(maxU, K, F, ga1, F, Lr.mlp1_w, K);
+            q1.rows_dev = nu;
+            TRY(sgemm<false, false>(q1, g1, sms, st));
+        }
         if (wg) {
             TRY(wgrad_outer(rows1(3 * F, 2 * F, maxU, gg, 3 * F, h2, 2 * F, nu), wpart, wcap, gw(Gr.mlp3_w), 0, sms, st));
             TRY(wgrad_colsum(rows1(3 * F, 1, maxU, gg, 3 * F, nullptr, 0, nu), nullptr, wpart, wcap, gw(Gr.mlp3_b), 0,
@@ -1216,7 +1362,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             TRY(wgrad_outer(rows3(gY, Xn), wpart, wcap, gw(Gr.mix1_w), 0, sms, st));
         }
         pf.mark(P_NODE_BWD);
-        TRY(sgemm<false, false>(gshape_classes(N, F, gY, Lr.mix1_w), EpiStore{gX, F, 1}, sms, st));
+        if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix1T, 3 * F, F, EpiStore{gX, F, 1}, status, st));
+        else TRY(sgemm<false, false>(gshape_classes(N, F, gY, Lr.mix1_w), EpiStore{gX, F, 1}, sms, st));
         k_node_norm_bwd<<<ew, 256, 0, st>>>(Xl, qn, N, F, gX);
         count_launch();
         TNET_LAUNCH_CHECK();
@@ -1225,13 +1372,14 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     pf.mark(P_EMB_NODE_BWD);
     float *gU = f32(Lw.gU), *gas2 = f32(Lw.gas2), *gas1 = f32(Lw.gas1), *gn0 = f32(Lw.gn0);
     float *gXraw = gdX;
-    k_emb_scale_bwd<<<ew, 256, 0, st>>>(gX, Uemb, s, as2, N, F, gU, gas2);
+    k_emb_scale_bwd<<<ew, 256, 0, st>>>(gX, Uemb, s, as2, N, F, gU, gas2, nbf);
     count_launch();
     TNET_LAUNCH_CHECK();
     TRY(sgemm<false, false>(gshape(N, 2 * F, 3 * F, gas2, 3 * F, W.emb_mlp2_w, 2 * F),
                             EpiGradAct{as1, 2 * F, gas1, 2 * F, 0}, sms, st));
     TRY(sgemm<false, false>(gshape(N, F, 2 * F, gas1, 2 * F, W.emb_mlp1_w, F), EpiStore{gn0, F, 0}, sms, st));
-    TRY(sgemm<false, false>(gshape_classes(N, F, gU, W.emb_mix_w), EpiStore{gXraw, F, 0}, sms, st));
+    if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, emixT_b16, 3 * F, F, EpiStore{gXraw, F, 0}, status, st));
+    else TRY(sgemm<false, false>(gshape_classes(N, F, gU, W.emb_mix_w), EpiStore{gXraw, F, 0}, sms, st));
     k_ln0_bwd<<<N, F, 0, st>>>(Xraw, gn0, ln0, W.emb_ln_g, N, F, gXraw);
     count_launch();
     TNET_LAUNCH_CHECK();
@@ -1252,7 +1400,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     const int bwd_blocks = grid_for((int64_t)N * 32, 256, sms);
 #define EMB_BWD(CPL)                                                                                    \
     k_emb_bwd<CPL><<<bwd_blocks, 256, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, d.max_z, rp, fu, \
-                                               Ta, Tb, gXraw, wg ? 1 : 0, gfu, edge_g, gA, gB)
+                                               Ta, Tb, gXraw, wg ? 1 : 0, gfu, edge_g, gA, gB, gfu_bf)
     switch (F / 32) {
         case 2: EMB_BWD(2); break;
         case 4: EMB_BWD(4); break;
@@ -1268,9 +1416,15 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     {   // dE/de of the pair's radial basis also flows through the projections
-        GemmShape pg = gshape(maxU, K, 3 * F, gfu, 3 * F, W.dproj_w, K);
-        pg.rows_dev = nu;
-        TRY(sgemm<false, false>(pg, EpiStore{ge, K, NL > 0}, sms, st));
+        if (bf) {
+            tc::TcShape tg = tc::tshape(maxU, K, 3 * F);
+            tg.rows_dev = nu;
+            TRY(tc_any(tg, gfu_bf, maxU, 3 * F, dprojT_b16, K, 3 * F, EpiStore{ge, K, NL > 0}, status, st));
+        } else {
+            GemmShape pg = gshape(maxU, K, 3 * F, gfu, 3 * F, W.dproj_w, K);
+            pg.rows_dev = nu;
+            TRY(sgemm<false, false>(pg, EpiStore{ge, K, NL > 0}, sms, st));
+        }
     }
     if (wg) {
         TRY(wgrad_outer(rows1(3 * F, K, maxU, gfu, 3 * F, eu, K, nu), wpart, wcap, gw(G.dproj_w), 0, sms, st));

@@ -237,3 +237,51 @@ def test_autograd_function_weights():
     _, _, G = m.energy_forces(z, pos, nl, grad_weights=True)
     torch.cuda.synchronize()
     assert torch.allclose(w.grad, 2.0 * G, rtol=1e-5, atol=1e-7)
+
+
+# --------------------------------------------------------------- BF16 mode ---
+BF16_F_TOL = 1e-2   # BF16 tensor-core GEMMs: RMS force error <= 1e-2 of the RMS force
+
+
+def _make_bf16(sys, weights=W, shape=SHAPE, max_pairs=None):
+    from paper_2402_17660_gb300.tnet import TensorNet
+    m32 = make_model(weights, sys, shape=shape, max_pairs=max_pairs)
+    return TensorNet(weights, F=shape.F, K=shape.K, L=shape.L, max_z=shape.max_z, max_atoms=sys.n_atoms,
+                     max_systems=sys.n_systems, max_pairs=m32.max_pairs, precision=1, device=DEV), m32
+
+
+@pytest.mark.parametrize("name", ["molecule32", "water3000"])
+def test_bf16_mode_against_oracle(name):
+    s = synth.workload(name)
+    mb, m32 = _make_bf16(s)
+    Eb, Fb = gpu_energy_forces(mb, s)
+    E32, F32 = gpu_energy_forces(m32, s)
+    Es, Ei, Fo = oracle_energy_forces(W, s)
+    e_err = energy_errors(Eb, Es, Ei, s.batch).max()
+    f_err = force_error(Fb, Fo)
+    f_err32 = force_error(Fb, F32)
+    print(f"{name} BF16: rel energy err {e_err:.2e}, rel RMS force err vs oracle {f_err:.2e}, vs FP32 {f_err32:.2e}")
+    assert f_err <= BF16_F_TOL and f_err32 <= BF16_F_TOL
+    assert e_err <= 1e-2
+
+
+def test_bf16_mode_batch_and_weight_grads():
+    from paper_2402_17660_gb300.tnet import unpack_weights
+    s = synth.molecule_batch(40, seed=3)
+    mb, m32 = _make_bf16(s)
+    Eb, Fb = gpu_energy_forces(mb, s)
+    E32, F32 = gpu_energy_forces(m32, s)
+    assert force_error(Fb, F32) <= BF16_F_TOL
+    z, pos, batch, box = to_dev(s)
+    outs = []
+    for m in (mb, m32):
+        nl = gpu_pairs(m, s)
+        m.reset_status()
+        _, _, G = m.energy_forces(z, pos, nl, batch, box, s.n_systems, grad_weights=True)
+        torch.cuda.synchronize()
+        m.check_status("bf16 grads")
+        outs.append(unpack_weights(G.cpu().numpy(), 128, 32, 2, 100))
+    worst = max(np.sqrt(np.mean((outs[0][k] - outs[1][k]) ** 2)) / max(np.sqrt(np.mean(outs[1][k] ** 2)), 1e-30)
+                for k in outs[1])
+    print(f"BF16 vs FP32 worst per-tensor weight-gradient rel RMS diff {worst:.2e}")
+    assert worst <= 5e-2
