@@ -1075,13 +1075,13 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     // ---- BF16 tensor-core mode: operand buffers and weight copies
     const bool bf = d.precision == 1;
     auto bfp = [&](size_t off) { return bf ? wsp<__nv_bfloat16>(ctx, off) : (__nv_bfloat16 *)nullptr; };
-    __nv_bfloat16 *nbf = bfp(Lw.nbf), *eu_bf = bfp(Lw.eu_bf), *h1_bf = bfp(Lw.h1_bf), *h2_bf = bfp(Lw.h2_bf),
-                  *ga3_bf = bfp(Lw.ga3_bf), *ga2_bf = bfp(Lw.ga2_bf), *ga1_bf = bfp(Lw.ga1_bf),
-                  *gfu_bf = bfp(Lw.gfu_bf);
+    // (the num_rbf-wide operands e(d) and dE/df stay FP32, so no bf16 copies)
+    __nv_bfloat16 *nbf = bfp(Lw.nbf), *eu_bf = nullptr, *h1_bf = bfp(Lw.h1_bf), *h2_bf = bfp(Lw.h2_bf),
+                  *ga3_bf = bfp(Lw.ga3_bf), *ga2_bf = bfp(Lw.ga2_bf), *ga1_bf = nullptr, *gfu_bf = nullptr;
     struct LayerB {
-        __nv_bfloat16 *mlp1, *mlp2, *mlp3, *mlp1T, *mlp2T, *mlp3T, *mix1, *mix1T, *mix2, *mix2T;
+        __nv_bfloat16 *mlp2, *mlp3, *mlp2T, *mlp3T, *mix1, *mix1T, *mix2, *mix2T;
     } lb[8] = {};
-    __nv_bfloat16 *dproj_b16 = nullptr, *dprojT_b16 = nullptr, *emix_b16 = nullptr, *emixT_b16 = nullptr;
+    __nv_bfloat16 *emix_b16 = nullptr, *emixT_b16 = nullptr;
 
     // ---- graph prep
     ProfSeq pf(ctx, st);
@@ -1107,16 +1107,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             }
             return first;
         };
-        dproj_b16 = job(W.dproj_w, 3 * F, K, 0);
-        dprojT_b16 = job(W.dproj_w, 3 * F, K, 1);
         emix_b16 = job(W.emb_mix_w, 3 * F, F, 0);
         emixT_b16 = job_classes_T(W.emb_mix_w);
         for (int l = 0; l < NL; ++l) {
             const LayerW &Lr = W.layer[l];
-            lb[l].mlp1 = job(Lr.mlp1_w, F, K, 0);
             lb[l].mlp2 = job(Lr.mlp2_w, 2 * F, F, 0);
             lb[l].mlp3 = job(Lr.mlp3_w, 3 * F, 2 * F, 0);
-            lb[l].mlp1T = job(Lr.mlp1_w, F, K, 1);
             lb[l].mlp2T = job(Lr.mlp2_w, 2 * F, F, 1);
             lb[l].mlp3T = job(Lr.mlp3_w, 3 * F, 2 * F, 1);
             lb[l].mix1 = job(Lr.mix1_w, 3 * F, F, 0);
@@ -1150,16 +1146,13 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     {   // radial projections f^p = W^p e(d) + b^p, once per undirected pair
+        // FP32 in both modes: K = num_rbf is small, and rounding the narrow
+        // expnorm basis values to bf16 costs more force accuracy than any
+        // other operand
         const EpiBiasAct ep{W.dproj_b, nullptr, 0, fu, 3 * F, 0, nullptr};
-        if (bf) {
-            tc::TcShape tp = tc::tshape(maxU, 3 * F, K);
-            tp.rows_dev = nu;
-            TRY(tc_any(tp, eu_bf, maxU, K, dproj_b16, 3 * F, K, ep, status, st));
-        } else {
-            GemmShape pp = gshape(maxU, 3 * F, K, eu, K, W.dproj_w, K);
-            pp.rows_dev = nu;
-            TRY(sgemm<false, true>(pp, ep, sms, st));
-        }
+        GemmShape pp = gshape(maxU, 3 * F, K, eu, K, W.dproj_w, K);
+        pp.rows_dev = nu;
+        TRY(sgemm<false, true>(pp, ep, sms, st));
     }
 
     // ---- embedding
@@ -1195,10 +1188,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, h2, 2 * F, 1, nullptr, h2_bf, 2 * F};
         const EpiBiasAct e3{Lr.mlp3_b, a3, 3 * F, gbuf, 3 * F, 1, phiu};
         if (bf) {
-            tc::TcShape t1 = tc::tshape(maxU, F, K), t2 = tc::tshape(maxU, 2 * F, F), t3 = tc::tshape(maxU, 3 * F, 2 * F);
-            t1.rows_dev = t2.rows_dev = t3.rows_dev = nu;
-            pf.mark(P_MLP1);
-            TRY(tc_any(t1, eu_bf, maxU, K, lb[l].mlp1, F, K, e1, status, st));
+            tc::TcShape t2 = tc::tshape(maxU, 2 * F, F), t3 = tc::tshape(maxU, 3 * F, 2 * F);
+            t2.rows_dev = t3.rows_dev = nu;
+            pf.mark(P_MLP1);  // K = num_rbf: FP32 (see the projections above)
+            GemmShape p1 = gshape(maxU, F, K, eu, K, Lr.mlp1_w, K);
+            p1.rows_dev = nu;
+            TRY(sgemm<false, true>(p1, e1, sms, st));
             pf.mark(P_MLP2);
             TRY(tc_any(t2, h1_bf, maxU, F, lb[l].mlp2, 2 * F, F, e2, status, st));
             pf.mark(P_MLP3);
@@ -1327,14 +1322,16 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         const EpiGradAct g2{a1, F, ga1, F, 0, ga1_bf, F};
         const EpiStore g1{ge, K, l != NL - 1};
         if (bf) {
-            tc::TcShape t3 = tc::tshape(maxU, 2 * F, 3 * F), t2 = tc::tshape(maxU, F, 2 * F), t1 = tc::tshape(maxU, K, F);
-            t1.rows_dev = t2.rows_dev = t3.rows_dev = nu;
+            tc::TcShape t3 = tc::tshape(maxU, 2 * F, 3 * F), t2 = tc::tshape(maxU, F, 2 * F);
+            t2.rows_dev = t3.rows_dev = nu;
             pf.mark(P_MLP3_BWD);
             TRY(tc_any(t3, ga3_bf, maxU, 3 * F, lb[l].mlp3T, 2 * F, 3 * F, g3, status, st));
             pf.mark(P_MLP2_BWD);
             TRY(tc_any(t2, ga2_bf, maxU, 2 * F, lb[l].mlp2T, F, 2 * F, g2, status, st));
-            pf.mark(P_MLP1_BWD);
-            TRY(tc_any(t1, ga1_bf, maxU, F, lb[l].mlp1T, K, F, g1, status, st));
+            pf.mark(P_MLP1_BWD);  // N = num_rbf: FP32 SIMT
+            GemmShape q1 = gshape(maxU, K, F, ga1, F, Lr.mlp1_w, K);
+            q1.rows_dev = nu;
+            TRY(sgemm<false, false>(q1, g1, sms, st));
         } else {
             pf.mark(P_MLP3_BWD);
             GemmShape q3 = gshape(maxU, 2 * F, 3 * F, gg, 3 * F, Lr.mlp3_w, 2 * F);
@@ -1416,15 +1413,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     {   // dE/de of the pair's radial basis also flows through the projections
-        if (bf) {
-            tc::TcShape tg = tc::tshape(maxU, K, 3 * F);
-            tg.rows_dev = nu;
-            TRY(tc_any(tg, gfu_bf, maxU, 3 * F, dprojT_b16, K, 3 * F, EpiStore{ge, K, NL > 0}, status, st));
-        } else {
-            GemmShape pg = gshape(maxU, K, 3 * F, gfu, 3 * F, W.dproj_w, K);
-            pg.rows_dev = nu;
-            TRY(sgemm<false, false>(pg, EpiStore{ge, K, NL > 0}, sms, st));
-        }
+        GemmShape pg = gshape(maxU, K, 3 * F, gfu, 3 * F, W.dproj_w, K);
+        pg.rows_dev = nu;
+        TRY(sgemm<false, false>(pg, EpiStore{ge, K, NL > 0}, sms, st));
     }
     if (wg) {
         TRY(wgrad_outer(rows1(3 * F, K, maxU, gfu, 3 * F, eu, K, nu), wpart, wcap, gw(G.dproj_w), 0, sms, st));

@@ -6,12 +6,15 @@
 //   C[m][n] = epi( sum_k A[m][k] B[n][k] ),  A [rows][lda], B [rows][ldb] bf16,
 //   both K-major (row-major with K contiguous).
 //
-// One CTA computes one 128 x BN output tile.  Warp 0 issues TMA loads into a
-// 4-stage ring, warp 1 owns TMEM and issues the MMAs (K = 16 per instruction,
-// four per 64-wide k-block), warps 2..5 drain TMEM (warp w reads lanes
-// 32*(w%4) .. +31) and run the epilogue.  Every mbarrier wait is bounded; on
-// expiry the kernel records TNET_ERR_TIMEOUT, waits (bounded) for its own
-// copies in flight, frees TMEM and returns.
+// Persistent CTAs walk 128 x BN output tiles.  Warp 0 issues TMA loads into a
+// 4-stage shared-memory ring, warp 1 owns TMEM and issues the MMAs (K = 16
+// per instruction, four per 64-wide k-block) into one of two accumulators,
+// so the epilogue of a tile overlaps the MMAs of the next.  Eight epilogue
+// warps drain TMEM (warp w reads lanes 32*(w%4) .. +31, half of the tile's
+// columns each) and run the fused epilogue.  Every mbarrier wait is bounded;
+// on expiry the kernel records TNET_ERR_TIMEOUT, the other roles stop, the
+// producer waits (bounded) for its own copies in flight, TMEM is freed and
+// the kernel returns.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -21,7 +24,7 @@
 namespace tnet {
 namespace tc {
 
-constexpr int BM = 128, BK = 64, STAGES = 4, THREADS = 192;
+constexpr int BM = 128, BK = 64, STAGES = 4, EPI_WARPS = 8, THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 struct TcShape {
@@ -43,10 +46,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-// bounded wait on the given phase parity; false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// bounded wait on the given phase parity; false when the limit ran out or
+// (when given) the CTA's abort flag was raised
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag = nullptr) {
     const uint32_t addr = smem_u32(bar);
     for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        if (abort_flag && (it & 1023u) == 1023u && *abort_flag) return false;
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -123,8 +131,26 @@ template <int BN>
 struct TileCfg {
     static constexpr uint32_t A_BYTES = BM * BK * 2;
     static constexpr uint32_t B_BYTES = BN * BK * 2;
-    static constexpr uint32_t TMEM_COLS = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+    static constexpr uint32_t TMEM_COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
     static constexpr size_t SMEM = 1024 + STAGES * (size_t)(A_BYTES + B_BYTES) + 256;
+};
+
+// Tile index -> (class, first row, first column); false past the last tile.
+struct TileIter {
+    int tilesN, nclass, mt[3];
+    __device__ bool get(int t, int &z, int &m0, int &n0, int BN_) const {
+        for (int c = 0; c < nclass; ++c) {
+            const int cnt = mt[c] * tilesN;
+            if (t < cnt) {
+                z = c;
+                m0 = (t / tilesN) * BM;
+                n0 = (t % tilesN) * BN_;
+                return true;
+            }
+            t -= cnt;
+        }
+        return false;
+    }
 };
 
 template <int BN, class Epi>
@@ -138,19 +164,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint8_t *sB = smem + STAGES * C::A_BYTES;
     uint64_t *full = (uint64_t *)(sB + STAGES * C::B_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *done = empty + STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *acc_empty = acc_full + 2;
+    uint32_t *tmem_slot = (uint32_t *)(acc_empty + 2);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
-    const int z = blockIdx.z;
-    int M = P.M[z];
-    if (z == 0 && P.rows_dev) {
+    // rows per class (class 0 may be bounded by a device-side count)
+    int Mz[3];
+    for (int c = 0; c < 3; ++c) Mz[c] = c < P.nclass ? P.M[c] : 0;
+    if (P.rows_dev) {
         const int md = *P.rows_dev * P.rows_mul;
-        M = md < M ? md : M;
+        Mz[0] = md < Mz[0] ? md : Mz[0];
     }
-    const int m0 = blockIdx.x * BM;
-    if (m0 >= M) return;  // whole CTA leaves before touching TMEM
-    const int n0 = blockIdx.y * BN;
+    TileIter it;
+    it.tilesN = (P.N + BN - 1) / BN;
+    it.nclass = P.nclass;
+    for (int c = 0; c < 3; ++c) it.mt[c] = (Mz[c] + BM - 1) / BM;
     const int nk = (P.K + BK - 1) / BK;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -159,7 +188,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], EPI_WARPS);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -171,58 +203,82 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
-            int issued = 0;
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % STAGES;
-                if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
-                    set_status(status, TNET_ERR_TIMEOUT);
-                    *abort_flag = 1;
-                    break;
+            int kg = 0;
+            int z, m0, n0;
+            for (int t = blockIdx.x; it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x) {
+                for (int kb = 0; kb < nk; ++kb, ++kg) {
+                    const int s = kg % STAGES;
+                    if (kg >= STAGES && !mbar_wait(&empty[s], ((kg / STAGES) - 1) & 1, abort_flag)) {
+                        set_status(status, TNET_ERR_TIMEOUT);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    mbar_expect_tx(&full[s], C::A_BYTES + C::B_BYTES);
+                    tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * BK, (int)(P.row0[z] + m0), &full[s]);
+                    tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * BK, (int)(P.brow0[z] + n0), &full[s]);
                 }
-                mbar_expect_tx(&full[s], C::A_BYTES + C::B_BYTES);
-                tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * BK, (int)(P.row0[z] + m0), &full[s]);
-                tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * BK, (int)(P.brow0[z] + n0), &full[s]);
-                issued = kb + 1;
             }
-            for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-                mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);  // own copies have landed
+            for (int k = kg > STAGES ? kg - STAGES : 0; k < kg; ++k)
+                mbar_wait(&full[k % STAGES], (k / STAGES) & 1);  // own copies have landed
         }
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
             const uint32_t idesc = idesc_bf16(BM, BN);
-            bool ok = true;
-            for (int kb = 0; kb < nk; ++kb) {
-                const int s = kb % STAGES;
-                if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
-                    ok = false;
+            int kg = 0, lt = 0;
+            int z, m0, n0;
+            for (int t = blockIdx.x; it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x, ++lt) {
+                const int buf = lt & 1;
+                if (lt >= 2 && !mbar_wait(&acc_empty[buf], ((lt >> 1) - 1) & 1, abort_flag)) {
+                    set_status(status, TNET_ERR_TIMEOUT);
+                    *abort_flag = 1;
                     break;
                 }
                 fence_after();
-                const uint32_t a0 = smem_u32(sA + s * C::A_BYTES), b0 = smem_u32(sB + s * C::B_BYTES);
+                const uint32_t d = tmem + (uint32_t)(buf * BN);
+                bool ok = true;
+                for (int kb = 0; kb < nk; ++kb, ++kg) {
+                    const int s = kg % STAGES;
+                    if (!mbar_wait(&full[s], (kg / STAGES) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t a0 = smem_u32(sA + s * C::A_BYTES), b0 = smem_u32(sB + s * C::B_BYTES);
 #pragma unroll
-                for (int k = 0; k < BK / 16; ++k)
-                    umma_bf16(tmem, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc,
-                              (kb > 0 || k > 0) ? 1u : 0u);
-                umma_commit(&empty[s]);
+                    for (int k = 0; k < BK / 16; ++k)
+                        umma_bf16(d, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc,
+                                  (kb > 0 || k > 0) ? 1u : 0u);
+                    umma_commit(&empty[s]);
+                }
+                if (!ok) {
+                    set_status(status, TNET_ERR_TIMEOUT);
+                    *abort_flag = 1;
+                    break;
+                }
+                umma_commit(&acc_full[buf]);
             }
-            if (!ok) {
+        }
+    } else {  // epilogue warps 2..9
+        const int q = warp & 3;                  // TMEM lane quadrant this warp may read
+        const int half = (warp - 2) >> 2;        // which half of the tile's columns
+        const int c_begin = half * (BN / 2), c_end = c_begin + BN / 2;
+        int lt = 0;
+        int z, m0, n0;
+        for (int t = blockIdx.x; it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            if (!mbar_wait(&acc_full[buf], (lt >> 1) & 1, abort_flag)) {
                 set_status(status, TNET_ERR_TIMEOUT);
                 *abort_flag = 1;
+                break;
             }
-            umma_commit(done);
-        }
-    } else {  // epilogue warps 2..5
-        const int q = warp & 3;
-        const bool ok = mbar_wait(done, 0);
-        fence_after();
-        if (!ok) set_status(status, TNET_ERR_TIMEOUT);
-        if (ok && !*abort_flag) {
+            fence_after();
             const int row = m0 + 32 * q + lane;
+            const int Mrow = Mz[z];
 #pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 16) {
+            for (int c0 = c_begin; c0 < c_end; c0 += 16) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-                if (row < M) {
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0), v);
+                if (row < Mrow) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const int n = n0 + c0 + 4 * j;
@@ -230,6 +286,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                 }
             }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
         }
     }
     fence_before();
@@ -270,8 +329,17 @@ int tc_gemm(const TcShape &P, const __nv_bfloat16 *A, int64_t a_rows, int64_t ld
                                            (int)C::SMEM));
         attr_set = true;
     }
-    dim3 g((maxM + BM - 1) / BM, (P.N + BN - 1) / BN, P.nclass);
-    k_tc_gemm<BN, Epi><<<g, THREADS, C::SMEM, st>>>(ma, mb, P, epi, status);
+    int64_t tiles = 0;
+    for (int z = 0; z < P.nclass; ++z) tiles += (int64_t)((P.M[z] + BM - 1) / BM) * ((P.N + BN - 1) / BN);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    k_tc_gemm<BN, Epi><<<grid, THREADS, C::SMEM, st>>>(ma, mb, P, epi, status);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
