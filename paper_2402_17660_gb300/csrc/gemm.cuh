@@ -35,7 +35,8 @@ struct GemmShape {
 };
 
 // --------------------------------------------------------------- epilogues
-// Each epilogue receives 4 consecutive columns (n..n+3, all < N) of row m.
+// Each epilogue receives 4 consecutive columns (n..n+3, all < N) of row m by
+// value (a pointer would force the accumulator fragment into local memory).
 // Optional BF16 copies feed the tensor-core GEMMs of the BF16 mode.
 __device__ __forceinline__ void store_bf16x4(__nv_bfloat16 *p, const float o[4]) {
     __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]), b = __floats2bfloat162_rn(o[2], o[3]);
@@ -49,9 +50,8 @@ struct EpiStore {  // C = v (+ C when accumulate)
     float *C;
     int64_t ldc;
     int accumulate;
-    __device__ void operator()(int z, int64_t m, int n, const float v[4]) const {
+    __device__ void operator()(int z, int64_t m, int n, float4 o) const {
         float4 *p = reinterpret_cast<float4 *>(C + m * ldc + n);
-        float4 o = make_float4(v[0], v[1], v[2], v[3]);
         if (accumulate) {
             const float4 c = *p;
             o.x += c.x; o.y += c.y; o.z += c.z; o.w += c.w;
@@ -70,7 +70,8 @@ struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m] (+ bf1
     const float *rowscale;
     __nv_bfloat16 *out_bf;
     int64_t ldob;
-    __device__ void operator()(int z, int64_t m, int n, const float v[4]) const {
+    __device__ void operator()(int z, int64_t m, int n, float4 vv) const {
+        const float v[4] = {vv.x, vv.y, vv.z, vv.w};
         float a[4], o[4];
         const float rs = rowscale ? rowscale[m] : 1.0f;
 #pragma unroll
@@ -92,7 +93,8 @@ struct EpiGradAct {  // out = v * silu'(pre)  (+ out when accumulate) (+ bf16 co
     int accumulate;
     __nv_bfloat16 *out_bf;
     int64_t ldob;
-    __device__ void operator()(int z, int64_t m, int n, const float v[4]) const {
+    __device__ void operator()(int z, int64_t m, int n, float4 vv) const {
+        const float v[4] = {vv.x, vv.y, vv.z, vv.w};
         const float4 a = *reinterpret_cast<const float4 *>(pre + m * ldp + n);
         float o[4] = {v[0] * silu_grad_f(a.x), v[1] * silu_grad_f(a.y), v[2] * silu_grad_f(a.z),
                       v[3] * silu_grad_f(a.w)};
@@ -112,12 +114,13 @@ __global__ void __launch_bounds__(GTHREADS) k_sgemm(GemmShape P, Epi epi) {
     __shared__ __align__(16) float As[2][GBK][GBM];
     __shared__ __align__(16) float Bs[2][GBK][GBN];
     const int z = blockIdx.z;
-    int M = P.M[z];
+    // selects, not P.M[z]: a dynamically indexed parameter array is copied to local memory
+    int M = z == 0 ? P.M[0] : (z == 1 ? P.M[1] : P.M[2]);
     if (z == 0 && P.rows_dev) {
         const int md = *P.rows_dev * P.rows_mul;
         M = md < M ? md : M;
     }
-    const int64_t r0 = P.row0[z];
+    const int64_t r0 = z == 0 ? P.row0[0] : (z == 1 ? P.row0[1] : P.row0[2]);
     const float *A = P.A + (TA ? r0 : r0 * P.lda);
     const float *B = P.B + (int64_t)z * P.strideB;
     const int N = P.N, K = P.K;
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(GTHREADS) k_sgemm(GemmShape P, Epi epi) {
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int m = m0 + ty * 8 + i;
-                if (m < M) epi(z, r0 + m, n, acc[i]);
+                if (m < M) epi(z, r0 + m, n, make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]));
             }
         }
         __syncthreads();

@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(WTHREADS) k_wgrad(WgradShape P, int splits, in
     __shared__ __align__(16) float As[WBK][WBM];
     __shared__ __align__(16) float Bs[WBK][WBN];
     const int z = blockIdx.z, s = blockIdx.y;
-    int64_t R = P.rows[z];
+    int64_t R = z == 0 ? P.rows[0] : (z == 1 ? P.rows[1] : P.rows[2]);
     if (z == 0 && P.rows_dev) {
         const int64_t rd = (int64_t)(*P.rows_dev) * P.rows_mul;
         R = rd < R ? rd : R;
@@ -26,8 +26,9 @@ __global__ void __launch_bounds__(WTHREADS) k_wgrad(WgradShape P, int splits, in
     const int64_t r_begin = s * chunk;
     int64_t r_end = r_begin + chunk;
     if (r_end > R) r_end = R;
-    const float *A = P.A + P.row0[z] * P.lda;
-    const float *B = P.B + P.row0[z] * P.ldb;
+    const int64_t rz = z == 0 ? P.row0[0] : (z == 1 ? P.row0[1] : P.row0[2]);
+    const float *A = P.A + rz * P.lda;
+    const float *B = P.B + rz * P.ldb;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     float acc[4][4] = {};
     for (int64_t r0 = r_begin; r0 < r_end; r0 += WBK) {
@@ -74,7 +75,7 @@ __global__ void k_colsum(WgradShape P, int splits, int64_t chunk, const float *_
     const int z = blockIdx.z, s = blockIdx.y;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= P.M) return;
-    int64_t R = P.rows[z];
+    int64_t R = z == 0 ? P.rows[0] : (z == 1 ? P.rows[1] : P.rows[2]);
     if (z == 0 && P.rows_dev) {
         const int64_t rd = (int64_t)(*P.rows_dev) * P.rows_mul;
         R = rd < R ? rd : R;
@@ -82,7 +83,7 @@ __global__ void k_colsum(WgradShape P, int splits, int64_t chunk, const float *_
     const int64_t r_begin = s * chunk;
     int64_t r_end = r_begin + chunk;
     if (r_end > R) r_end = R;
-    const float *A = P.A + P.row0[z] * P.lda;
+    const float *A = P.A + (z == 0 ? P.row0[0] : (z == 1 ? P.row0[1] : P.row0[2])) * P.lda;
     float acc = 0.f;
     for (int64_t r = r_begin; r < r_end; ++r) acc += A[r * P.lda + m] * (roww ? roww[r] : 1.0f);
     partial[((int64_t)z * splits + s) * P.M + m] = acc;

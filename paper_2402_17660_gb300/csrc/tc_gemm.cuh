@@ -136,22 +136,21 @@ struct TileCfg {
 };
 
 // Tile index -> (class, first row, first column); false past the last tile.
+// Scalars and selects only: dynamically indexed arrays would live in local memory.
 struct TileIter {
-    int tilesN, nclass, mt[3];
-    __device__ bool get(int t, int &z, int &m0, int &n0, int BN_) const {
-        for (int c = 0; c < nclass; ++c) {
-            const int cnt = mt[c] * tilesN;
-            if (t < cnt) {
-                z = c;
-                m0 = (t / tilesN) * BM;
-                n0 = (t % tilesN) * BN_;
-                return true;
-            }
-            t -= cnt;
-        }
-        return false;
+    int tilesN, nclass, mt0, mt1, mt2;
+    __device__ __forceinline__ bool get(int t, int &z, int &m0, int &n0, int BN_) const {
+        const int c0 = mt0 * tilesN, c1 = mt1 * tilesN, c2 = mt2 * tilesN;
+        if (t < c0) z = 0;
+        else if (nclass > 1 && t < c0 + c1) { z = 1; t -= c0; }
+        else if (nclass > 2 && t < c0 + c1 + c2) { z = 2; t -= c0 + c1; }
+        else return false;
+        m0 = (t / tilesN) * BM;
+        n0 = (t % tilesN) * BN_;
+        return true;
     }
 };
+__device__ __forceinline__ int64_t sel3(int z, int64_t a, int64_t b, int64_t c) { return z == 0 ? a : (z == 1 ? b : c); }
 
 template <int BN, class Epi>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -170,16 +169,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     // rows per class (class 0 may be bounded by a device-side count)
-    int Mz[3];
-    for (int c = 0; c < 3; ++c) Mz[c] = c < P.nclass ? P.M[c] : 0;
+    int M0 = P.M[0];
+    const int M1 = P.nclass > 1 ? P.M[1] : 0, M2 = P.nclass > 2 ? P.M[2] : 0;
     if (P.rows_dev) {
         const int md = *P.rows_dev * P.rows_mul;
-        Mz[0] = md < Mz[0] ? md : Mz[0];
+        M0 = md < M0 ? md : M0;
     }
     TileIter it;
     it.tilesN = (P.N + BN - 1) / BN;
     it.nclass = P.nclass;
-    for (int c = 0; c < 3; ++c) it.mt[c] = (Mz[c] + BM - 1) / BM;
+    it.mt0 = (M0 + BM - 1) / BM;
+    it.mt1 = (M1 + BM - 1) / BM;
+    it.mt2 = (M2 + BM - 1) / BM;
     const int nk = (P.K + BK - 1) / BK;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -214,8 +215,10 @@ __global__ void __launch_bounds__(THREADS, 1)
                         break;
                     }
                     mbar_expect_tx(&full[s], C::A_BYTES + C::B_BYTES);
-                    tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * BK, (int)(P.row0[z] + m0), &full[s]);
-                    tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * BK, (int)(P.brow0[z] + n0), &full[s]);
+                    tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * BK, (int)(sel3(z, P.row0[0], P.row0[1], P.row0[2]) + m0),
+                                &full[s]);
+                    tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * BK,
+                                (int)(sel3(z, P.brow0[0], P.brow0[1], P.brow0[2]) + n0), &full[s]);
                 }
             }
             for (int k = kg > STAGES ? kg - STAGES : 0; k < kg; ++k)
@@ -273,7 +276,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             fence_after();
             const int row = m0 + 32 * q + lane;
-            const int Mrow = Mz[z];
+            const int Mrow = (int)sel3(z, M0, M1, M2);
+            const int64_t rbase = sel3(z, P.row0[0], P.row0[1], P.row0[2]);
 #pragma unroll 1
             for (int c0 = c_begin; c0 < c_end; c0 += 16) {
                 float v[16];
@@ -282,7 +286,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const int n = n0 + c0 + 4 * j;
-                        if (n < P.N) epi(z, P.row0[z] + row, n, &v[4 * j]);
+                        if (n < P.N)
+                            epi(z, rbase + row, n, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
                     }
                 }
             }
