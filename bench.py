@@ -225,18 +225,29 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours ---
-STAGE_WORK = {
-    # stage tag -> function(nu, N, E, F, K) giving (kind, algorithmic amount per stage instance)
-    "mlp1": lambda nu, N, E, F, K: ("flop", 2.0 * nu * K * F),
-    "mlp2": lambda nu, N, E, F, K: ("flop", 2.0 * nu * F * 2 * F),
-    "mlp3": lambda nu, N, E, F, K: ("flop", 2.0 * nu * 2 * F * 3 * F),
-    "mlp3_bwd": lambda nu, N, E, F, K: ("flop", 2.0 * nu * 3 * F * 2 * F),
-    "mlp2_bwd": lambda nu, N, E, F, K: ("flop", 2.0 * nu * 2 * F * F),
-    "mlp1_bwd": lambda nu, N, E, F, K: ("flop", 2.0 * nu * F * K),
-    # message gather: read Y and the per-pair filters once, write M once, read the CSR
-    "message": lambda nu, N, E, F, K: ("bytes", 4.0 * (2 * 9 * N * F + 3 * F * nu) + 8.0 * E),
-    "message_bwd": lambda nu, N, E, F, K: ("bytes", 4.0 * (4 * 9 * N * F + 2 * 3 * F * nu) + 8.0 * E),
-}
+def stage_work(tag, nu, N, E, F, K, bf16):
+    """Algorithmic work of one instance of a timed stage: (FLOP, bytes, engine).
+    Bytes count each operand read once and each result written once."""
+    f = 4.0
+    hb = 2.0 if bf16 else 4.0            # bytes per element of a GEMM input operand
+    if tag == "mlp1":
+        return 2.0 * nu * K * F, nu * (K * f + F * f + F * hb), "alu"
+    if tag == "mlp2":
+        return 2.0 * nu * F * 2 * F, nu * (F * hb + 2 * F * f + 2 * F * hb), "tensor" if bf16 else "alu"
+    if tag == "mlp3":
+        return 2.0 * nu * 2 * F * 3 * F, nu * (2 * F * hb + 2 * 3 * F * f), "tensor" if bf16 else "alu"
+    if tag == "mlp3_bwd":
+        return 2.0 * nu * 3 * F * 2 * F, nu * (3 * F * hb + 2 * F * f + 2 * F * f + (2 * F * 2 if bf16 else 0)), \
+            "tensor" if bf16 else "alu"
+    if tag == "mlp2_bwd":
+        return 2.0 * nu * 2 * F * F, nu * (2 * F * hb + F * f + F * f), "tensor" if bf16 else "alu"
+    if tag == "mlp1_bwd":
+        return 2.0 * nu * F * K, nu * (F * f + 2 * K * f), "alu"
+    if tag == "message":     # read Y and the pair filters once, write M once, read the CSR
+        return 2.0 * 9 * F * 2 * nu, f * (2 * 9 * N * F + 3 * F * nu) + 8.0 * E, "hbm"
+    if tag == "message_bwd":
+        return 4.0 * 9 * F * 2 * nu, f * (4 * 9 * N * F + 2 * 3 * F * nu) + 8.0 * E, "hbm"
+    return None
 
 
 def run_ours(args):
@@ -337,34 +348,40 @@ def run_ours(args):
             break
         if cnt[t]:
             stages[name.decode()] = {"ms_per_step": ms[t] / args.profile_steps, "instances": int(cnt[t])}
-    top = max(stages, key=lambda k: stages[k]["ms_per_step"])
     roofline = None
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
-    work_tags = [k for k in sorted(stages, key=lambda k: -stages[k]["ms_per_step"]) if k in STAGE_WORK]
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s, derived
+    bf = args.precision == "bf16"
+    work_tags = [k for k in sorted(stages, key=lambda k: -stages[k]["ms_per_step"])
+                 if stage_work(k, nu, N, n_pairs, F_, shape.K, bf) is not None]
     if work_tags:
         tag = work_tags[0]
-        kind, amount = STAGE_WORK[tag](nu, N, n_pairs, F_, shape.K)
+        flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, bf)
         per_launch_ms = stages[tag]["ms_per_step"] * args.profile_steps / stages[tag]["instances"]
         traffic = None
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tpath):
-            tr = json.load(open(tpath)).get(f"{args.workload}:{tag}")
+            tr = json.load(open(tpath)).get(f"{args.workload}:{args.precision}:{tag}")
             if tr and tr.get("kernel_rev") == kernel_revision():
                 traffic = tr["bytes_per_launch"]
-        if kind == "flop":
-            ach = amount / (per_launch_ms * 1e-3) / 1e12
-            roofline = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                        "frac": ach / fp32_peak, "traffic": traffic, "kernel": tag,
-                        "peak_note": "FP32 FFMA peak 152 SM x 128 lanes x 2 x 2070 MHz (derived)",
-                        "algorithmic_per_launch": amount, "launch_ms": per_launch_ms}
+        cpeak, cname, cnote = ((bf16_peak, "tensor", "of measured bf16 burst (MEASURED_PEAKS.json)")
+                               if engine == "tensor" else
+                               (fp32_peak, "alu", "FP32 FFMA peak 152 SM x 128 lanes x 2 x 2070 MHz (derived)"))
+        ridge = cpeak * 1e12 / (hbm * 1e9)            # FLOP per byte where the two roofs meet
+        if engine != "hbm" and flops / nbytes >= ridge:
+            ach = flops / (per_launch_ms * 1e-3) / 1e12
+            roofline = {"bound": cname, "achieved": ach, "peak": cpeak, "unit": "TFLOP/s", "frac": ach / cpeak,
+                        "peak_note": cnote}
         else:
-            ach = amount / (per_launch_ms * 1e-3) / 1e9
+            ach = nbytes / (per_launch_ms * 1e-3) / 1e9
             roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                        "traffic": traffic, "kernel": tag, "peak_note": "of measured (MEASURED_PEAKS.json)",
-                        "algorithmic_per_launch": amount, "launch_ms": per_launch_ms}
+                        "peak_note": "of measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
+        roofline.update({"traffic": traffic, "kernel": tag, "algorithmic_flop_per_launch": flops,
+                         "algorithmic_bytes_per_launch": nbytes, "launch_ms": per_launch_ms,
+                         "arithmetic_intensity": flops / nbytes})
 
     # ---- end to end through the public API with host buffers
     pos_h = torch.from_numpy(sys_.pos).pin_memory()

@@ -74,9 +74,11 @@ struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m] (+ bf1
         const float v[4] = {vv.x, vv.y, vv.z, vv.w};
         float a[4], o[4];
         const float rs = rowscale ? rowscale[m] : 1.0f;
+        const float4 b4 = bias ? *reinterpret_cast<const float4 *>(bias + n) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            a[q] = v[q] + (bias ? bias[n + q] : 0.0f);
+            a[q] = v[q] + bv[q];
             o[q] = (silu ? silu_f(a[q]) : a[q]) * rs;
         }
         if (pre) *reinterpret_cast<float4 *>(pre + m * ldp + n) = make_float4(a[0], a[1], a[2], a[3]);

@@ -189,9 +189,11 @@ __device__ __forceinline__ void mm3_nt(const float A[9], const float B[9], float
             C[3 * r + c] = A[3 * r] * B[3 * c] + A[3 * r + 1] * B[3 * c + 1] + A[3 * r + 2] * B[3 * c + 2];
 }
 
-__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + expf(-x)); }
+// SiLU and its derivative (fast-math exp and divide: a few ulp, far inside
+// the FP32 path's error budget)
+__device__ __forceinline__ float silu_f(float x) { return __fdividef(x, 1.0f + __expf(-x)); }
 __device__ __forceinline__ float silu_grad_f(float x) {
-    const float s = 1.0f / (1.0f + expf(-x));
+    const float s = __fdividef(1.0f, 1.0f + __expf(-x));
     return s * (1.0f + x * (1.0f - s));
 }
 

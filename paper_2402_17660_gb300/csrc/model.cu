@@ -1074,6 +1074,10 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
 
     // ---- BF16 tensor-core mode: operand buffers and weight copies
     const bool bf = d.precision == 1;
+    const bool wg = grad_w != nullptr;
+    // FP32 activations h1, h2 are read by the FP32 GEMMs and by the weight
+    // gradients; the BF16 GEMMs read only their bf16 copies
+    const bool keep_h = !bf || wg;
     auto bfp = [&](size_t off) { return bf ? wsp<__nv_bfloat16>(ctx, off) : (__nv_bfloat16 *)nullptr; };
     // (the num_rbf-wide operands e(d) and dE/df stay FP32, so no bf16 copies)
     __nv_bfloat16 *nbf = bfp(Lw.nbf), *eu_bf = nullptr, *h1_bf = bfp(Lw.h1_bf), *h2_bf = bfp(Lw.h2_bf),
@@ -1184,8 +1188,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
           *gbuf = f32(Lw.g);
     auto edge_mlp = [&](int l) -> int {
         const LayerW &Lr = W.layer[l];
-        const EpiBiasAct e1{Lr.mlp1_b, a1, F, h1, F, 1, nullptr, h1_bf, F};
-        const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, h2, 2 * F, 1, nullptr, h2_bf, 2 * F};
+        const EpiBiasAct e1{Lr.mlp1_b, a1, F, keep_h ? h1 : nullptr, F, 1, nullptr, h1_bf, F};
+        const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, keep_h ? h2 : nullptr, 2 * F, 1, nullptr, h2_bf, 2 * F};
         const EpiBiasAct e3{Lr.mlp3_b, a3, 3 * F, gbuf, 3 * F, 1, phiu};
         if (bf) {
             tc::TcShape t2 = tc::tshape(maxU, 2 * F, F), t3 = tc::tshape(maxU, 3 * F, 2 * F);
@@ -1263,7 +1267,6 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     if (!forces && !grad_w) return TNET_OK;
-    const bool wg = grad_w != nullptr;
 
     // ---- reverse pass
     pf.mark(P_OUT_BWD);

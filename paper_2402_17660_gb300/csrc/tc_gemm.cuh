@@ -9,9 +9,9 @@
 // Persistent CTAs walk 128 x BN output tiles.  Warp 0 issues TMA loads into a
 // 4-stage shared-memory ring, warp 1 owns TMEM and issues the MMAs (K = 16
 // per instruction, four per 64-wide k-block) into one of two accumulators,
-// so the epilogue of a tile overlaps the MMAs of the next.  Eight epilogue
-// warps drain TMEM (warp w reads lanes 32*(w%4) .. +31, half of the tile's
-// columns each) and run the fused epilogue.  Every mbarrier wait is bounded;
+// so the epilogue of a tile overlaps the MMAs of the next.  Sixteen epilogue
+// warps drain TMEM (warp w reads lanes 32*(w%4) .. +31, a quarter of the
+// tile's columns each) and run the fused epilogue.  Every mbarrier wait is bounded;
 // on expiry the kernel records TNET_ERR_TIMEOUT, the other roles stop, the
 // producer waits (bounded) for its own copies in flight, TMEM is freed and
 // the kernel returns.
@@ -24,7 +24,8 @@
 namespace tnet {
 namespace tc {
 
-constexpr int BM = 128, BK = 64, STAGES = 4, EPI_WARPS = 8, THREADS = 64 + 32 * EPI_WARPS;
+constexpr int BM = 128, BK = 64, EPI_WARPS = 16, THREADS = 64 + 32 * EPI_WARPS;
+constexpr int STG_LD = 20;  // floats per staged row (16 + pad, keeps float4 alignment)
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 struct TcShape {
@@ -129,10 +130,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 
 template <int BN>
 struct TileCfg {
+    static constexpr int STAGES = BN >= 192 ? 3 : 4;
     static constexpr uint32_t A_BYTES = BM * BK * 2;
     static constexpr uint32_t B_BYTES = BN * BK * 2;
     static constexpr uint32_t TMEM_COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
-    static constexpr size_t SMEM = 1024 + STAGES * (size_t)(A_BYTES + B_BYTES) + 256;
+    static constexpr uint32_t STAGE_BYTES = EPI_WARPS * 32 * STG_LD * 4;  // epilogue transpose buffers
+    static constexpr size_t SMEM = 1024 + STAGES * (size_t)(A_BYTES + B_BYTES) + 256 + STAGE_BYTES;
 };
 
 // Tile index -> (class, first row, first column); false past the last tile.
@@ -157,6 +160,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcShape P, Epi epi,
               int32_t *status) {
     using C = TileCfg<BN>;
+    constexpr int STAGES = C::STAGES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = smem;
@@ -167,6 +171,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t *acc_empty = acc_full + 2;
     uint32_t *tmem_slot = (uint32_t *)(acc_empty + 2);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    float *stage_all = (float *)(sB + STAGES * C::B_BYTES + 256);
 
     // rows per class (class 0 may be bounded by a device-side count)
     int M0 = P.M[0];
@@ -263,8 +268,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else {  // epilogue warps 2..9
         const int q = warp & 3;                  // TMEM lane quadrant this warp may read
-        const int half = (warp - 2) >> 2;        // which half of the tile's columns
-        const int c_begin = half * (BN / 2), c_end = c_begin + BN / 2;
+        // column slices of at least 16 (one tcgen05.ld.x16); warps past the last
+        // slice only take part in the accumulator hand-off
+        constexpr int NSLICE = (BN / 16) < (EPI_WARPS / 4) ? (BN / 16) : (EPI_WARPS / 4);
+        constexpr int CW = BN / NSLICE;
+        const int part = (warp - 2) >> 2;
+        const int c_begin = part < NSLICE ? part * CW : 0, c_end = part < NSLICE ? c_begin + CW : 0;
         int lt = 0;
         int z, m0, n0;
         for (int t = blockIdx.x; it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x, ++lt) {
@@ -275,21 +284,31 @@ __global__ void __launch_bounds__(THREADS, 1)
                 break;
             }
             fence_after();
-            const int row = m0 + 32 * q + lane;
             const int Mrow = (int)sel3(z, M0, M1, M2);
             const int64_t rbase = sel3(z, P.row0[0], P.row0[1], P.row0[2]);
+            // TMEM gives thread = row; a shared-memory transpose hands each lane
+            // 4 columns of 4 rows instead, so every store instruction of the
+            // warp writes 8 rows x 64 contiguous bytes
+            float *stg = stage_all + (warp - 2) * 32 * STG_LD;
+            const int rsub = lane >> 2, csub = (lane & 3) * 4;
 #pragma unroll 1
             for (int c0 = c_begin; c0 < c_end; c0 += 16) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0), v);
-                if (row < Mrow) {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int n = n0 + c0 + 4 * j;
-                        if (n < P.N)
-                            epi(z, rbase + row, n, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
-                    }
+                for (int j = 0; j < 4; ++j)
+                    *reinterpret_cast<float4 *>(stg + lane * STG_LD + 4 * j) =
+                        make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                __syncwarp();
+                const int n = n0 + c0 + csub;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int r = rsub + 8 * k;
+                    const int row = m0 + 32 * q + r;
+                    const float4 w = *reinterpret_cast<const float4 *>(stg + r * STG_LD + csub);
+                    if (row < Mrow && n < P.N) epi(z, rbase + row, n, w);
                 }
+                __syncwarp();
             }
             fence_before();
             __syncwarp();
