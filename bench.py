@@ -243,6 +243,12 @@ def stage_work(tag, nu, N, E, F, K, bf16):
         return 2.0 * nu * 2 * F * F, nu * (2 * F * hb + F * f + F * f), "tensor" if bf16 else "alu"
     if tag == "mlp1_bwd":
         return 2.0 * nu * F * K, nu * (F * f + 2 * K * f), "alu"
+    if tag == "emb_edges":   # read the pair projections once, write X_raw once
+        return 2.0 * 12 * F * 2 * nu, f * (3 * F * nu + 9 * N * F) + (2.0 * 9 * N * F if bf16 else 0), "hbm"
+    if tag == "emb_edges_bwd":  # read gX_raw and the projections, write their adjoint and 16 B per edge
+        return 2.0 * 40 * F * 2 * nu, f * (9 * N * F + 6 * F * nu) + 16.0 * E, "hbm"
+    if tag == "mlp_elem_bwd":   # read dE/dg and a3, write dE/da3 (+ bf16 copy)
+        return 6.0 * 3 * F * nu, nu * 3 * F * (3 * f + (2 if bf16 else 0)), "hbm"
     if tag == "message":     # read Y and the pair filters once, write M once, read the CSR
         return 2.0 * 9 * F * 2 * nu, f * (2 * 9 * N * F + 3 * F * nu) + 8.0 * E, "hbm"
     if tag == "message_bwd":

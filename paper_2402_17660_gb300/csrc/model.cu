@@ -21,6 +21,8 @@
 
 namespace tnet {
 
+constexpr int kMU = 4;  // edges whose loads are in flight together in the row kernels
+
 // ----------------------------------------------------------- weights ---
 struct LayerW {
     const float *mlp1_w, *mlp1_b, *mlp2_w, *mlp2_b, *mlp3_w, *mlp3_b, *mix1_w, *mix2_w;
@@ -261,7 +263,8 @@ __device__ __forceinline__ EdgeGeo edge_geo(const float *__restrict__ pos, const
 // X_raw_i = sum_j phi Z_ij (f^I I0 + f^A A0(u) + f^S S0(u)) over the active
 // edges of row i, in row order.  f^p = W^p e(d) + b^p depends only on d, so
 // it is computed once per undirected pair by a GEMM (fu, columns p*F + c).
-// Block = F threads (thread = channel), persistent over atoms.
+// Block = F threads (thread = channel), persistent over atoms; loads for kMU
+// edges are in flight together.
 __global__ void k_emb_edges(const float *__restrict__ pos, const float *__restrict__ box,
                             const int32_t *__restrict__ batch, const int32_t *__restrict__ z,
                             const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
@@ -278,25 +281,40 @@ __global__ void k_emb_edges(const float *__restrict__ pos, const float *__restri
         }
         const float ta = Ta[(int64_t)zi * F + c];
         float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            const int u = pair_of[e];
-            if (u < 0) continue;
-            const int j = col[e];
-            float x, y, zz;
-            pair_vec(pos, box, batch, i, j, x, y, zz);
-            const float d = sqrtf(x * x + y * y + zz * zz);
-            const float inv = 1.0f / d;
-            const float ux = x * inv, uy = y * inv, uz = zz * inv;
-            int zj = z[j];
-            zj = (zj < 0 || zj >= max_z) ? 0 : zj;
-            const float pz = cutoff_phi(d, rp) * (ta + Tb[(int64_t)zj * F + c]);
-            const float *f = fu + (int64_t)u * 3 * F + c;
-            const float cI = pz * f[0], cA = pz * f[F], cS = pz * f[2 * F];
-            v[0] += cI;
-            v[1] += cA * ux; v[2] += cA * uy; v[3] += cA * uz;
-            v[4] += cS * (ux * ux - (1.0f / 3.0f));
-            v[5] += cS * (uy * uy - (1.0f / 3.0f));
-            v[6] += cS * ux * uy; v[7] += cS * ux * uz; v[8] += cS * uy * uz;
+        const int e1 = row_ptr[i + 1];
+        for (int eb = row_ptr[i]; eb < e1; eb += kMU) {
+            int uu[kMU], jj[kMU];
+#pragma unroll
+            for (int k = 0; k < kMU; ++k) {
+                const int e = eb + k;
+                uu[k] = e < e1 ? pair_of[e] : -1;
+                jj[k] = e < e1 ? col[e] : 0;
+            }
+            float f[kMU][3], tb[kMU], r[kMU][3];
+#pragma unroll
+            for (int k = 0; k < kMU; ++k) {
+                if (uu[k] < 0) continue;
+                const float *fp = fu + (int64_t)uu[k] * 3 * F + c;
+                f[k][0] = fp[0]; f[k][1] = fp[F]; f[k][2] = fp[2 * F];
+                int zj = z[jj[k]];
+                zj = (zj < 0 || zj >= max_z) ? 0 : zj;
+                tb[k] = Tb[(int64_t)zj * F + c];
+                pair_vec(pos, box, batch, i, jj[k], r[k][0], r[k][1], r[k][2]);
+            }
+#pragma unroll
+            for (int k = 0; k < kMU; ++k) {
+                if (uu[k] < 0) continue;
+                const float d = sqrtf(r[k][0] * r[k][0] + r[k][1] * r[k][1] + r[k][2] * r[k][2]);
+                const float inv = 1.0f / d;
+                const float ux = r[k][0] * inv, uy = r[k][1] * inv, uz = r[k][2] * inv;
+                const float pz = cutoff_phi(d, rp) * (ta + tb[k]);
+                const float cI = pz * f[k][0], cA = pz * f[k][1], cS = pz * f[k][2];
+                v[0] += cI;
+                v[1] += cA * ux; v[2] += cA * uy; v[3] += cA * uz;
+                v[4] += cS * (ux * ux - (1.0f / 3.0f));
+                v[5] += cS * (uy * uy - (1.0f / 3.0f));
+                v[6] += cS * ux * uy; v[7] += cS * ux * uz; v[8] += cS * uy * uz;
+            }
         }
         store_coords(Xraw, i, c, N, F, v);
         store_coords_bf(Xraw_bf, i, c, N, F, v);
@@ -358,26 +376,41 @@ __global__ void k_node_norm(const float *__restrict__ X, int N, int F, float *__
     }
 }
 
-// M_i = sum_j g^p_ij Y^p_j over the row (block = F threads, one atom per block)
+// M_i = sum_j g^p_ij Y^p_j over the row (block = F threads, one atom per block).
+// Loads for kMU edges are issued before any of them is used (memory-level
+// parallelism); the sums still run in row order.
 __global__ void k_message(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                           const int32_t *__restrict__ pair_of, const float *__restrict__ gU,
                           const float *__restrict__ Y, int N, int F, float *__restrict__ M) {
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         float m[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            const int u = pair_of[e];
-            if (u < 0) continue;
-            const int j = col[e];
-            const float *g = gU + (int64_t)u * 3 * F + 3 * c;
-            const float gI = g[0], gA = g[1], gS = g[2];
-            float y[9];
-            load_coords(Y, j, c, N, F, y);
-            m[0] = fmaf(gI, y[0], m[0]);
+        const int e1 = row_ptr[i + 1];
+        for (int eb = row_ptr[i]; eb < e1; eb += kMU) {
+            int uu[kMU], jj[kMU];
 #pragma unroll
-            for (int k = 1; k < 4; ++k) m[k] = fmaf(gA, y[k], m[k]);
+            for (int k = 0; k < kMU; ++k) {
+                const int e = eb + k;
+                uu[k] = e < e1 ? pair_of[e] : -1;
+                jj[k] = e < e1 ? col[e] : 0;
+            }
+            float g[kMU][3], y[kMU][9];
 #pragma unroll
-            for (int k = 4; k < 9; ++k) m[k] = fmaf(gS, y[k], m[k]);
+            for (int k = 0; k < kMU; ++k) {
+                if (uu[k] < 0) continue;
+                const float *gp = gU + (int64_t)uu[k] * 3 * F + 3 * c;
+                g[k][0] = gp[0]; g[k][1] = gp[1]; g[k][2] = gp[2];
+                load_coords(Y, jj[k], c, N, F, y[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < kMU; ++k) {
+                if (uu[k] < 0) continue;
+                m[0] = fmaf(g[k][0], y[k][0], m[0]);
+#pragma unroll
+                for (int q = 1; q < 4; ++q) m[q] = fmaf(g[k][1], y[k][q], m[q]);
+#pragma unroll
+                for (int q = 4; q < 9; ++q) m[q] = fmaf(g[k][2], y[k][q], m[q]);
+            }
         }
         store_coords(M, i, c, N, F, m);
     }
@@ -597,6 +630,7 @@ __global__ void k_T_bwd(const float *__restrict__ Y, const float *__restrict__ M
 //   gY_i += sum_j g^p_ij gM_j                       (g_ij = g_ji)
 //   gg[u(i,j)] = <gM_i, Y^p_j> + <gM_j, Y^p_i>       for upper edges j > i
 // Each undirected entry is written once, by its upper edge: no atomics.
+// Loads for kMU edges are in flight together; sums run in row order.
 __global__ void k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                               const int32_t *__restrict__ pair_of, const float *__restrict__ gU,
                               const float *__restrict__ Y, const float *__restrict__ gM, int N, int F,
@@ -607,29 +641,43 @@ __global__ void k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t
         load_coords(Y, i, c, N, F, yi);
         load_coords(gM, i, c, N, F, gmi);
         load_coords(gY, i, c, N, F, acc);
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            const int u = pair_of[e];
-            if (u < 0) continue;
-            const int j = col[e];
-            float yj[9], gmj[9];
-            load_coords(gM, j, c, N, F, gmj);
-            const float *g = gU + (int64_t)u * 3 * F + 3 * c;
-            const float gI = g[0], gA = g[1], gS = g[2];
-            acc[0] = fmaf(gI, gmj[0], acc[0]);
+        const int e1 = row_ptr[i + 1];
+        for (int eb = row_ptr[i]; eb < e1; eb += kMU) {
+            int uu[kMU], jj[kMU];
 #pragma unroll
-            for (int k = 1; k < 4; ++k) acc[k] = fmaf(gA, gmj[k], acc[k]);
+            for (int k = 0; k < kMU; ++k) {
+                const int e = eb + k;
+                uu[k] = e < e1 ? pair_of[e] : -1;
+                jj[k] = e < e1 ? col[e] : 0;
+            }
+            float g[kMU][3], gmj[kMU][9];
 #pragma unroll
-            for (int k = 4; k < 9; ++k) acc[k] = fmaf(gS, gmj[k], acc[k]);
-            if (j > i) {
-                load_coords(Y, j, c, N, F, yj);
-                float sI = gmi[0] * yj[0] + gmj[0] * yi[0];
-                float sA = 0.f, sS = 0.f;
+            for (int k = 0; k < kMU; ++k) {
+                if (uu[k] < 0) continue;
+                const float *gp = gU + (int64_t)uu[k] * 3 * F + 3 * c;
+                g[k][0] = gp[0]; g[k][1] = gp[1]; g[k][2] = gp[2];
+                load_coords(gM, jj[k], c, N, F, gmj[k]);
+            }
 #pragma unroll
-                for (int k = 1; k < 4; ++k) sA += gmi[k] * yj[k] + gmj[k] * yi[k];
+            for (int k = 0; k < kMU; ++k) {
+                if (uu[k] < 0) continue;
+                acc[0] = fmaf(g[k][0], gmj[k][0], acc[0]);
 #pragma unroll
-                for (int k = 4; k < 9; ++k) sS += gmi[k] * yj[k] + gmj[k] * yi[k];
-                float *o = gg + (int64_t)u * 3 * F + 3 * c;
-                o[0] = sI; o[1] = sA; o[2] = sS;
+                for (int q = 1; q < 4; ++q) acc[q] = fmaf(g[k][1], gmj[k][q], acc[q]);
+#pragma unroll
+                for (int q = 4; q < 9; ++q) acc[q] = fmaf(g[k][2], gmj[k][q], acc[q]);
+                if (jj[k] > i) {
+                    float yj[9];
+                    load_coords(Y, jj[k], c, N, F, yj);
+                    float sI = gmi[0] * yj[0] + gmj[k][0] * yi[0];
+                    float sA = 0.f, sS = 0.f;
+#pragma unroll
+                    for (int q = 1; q < 4; ++q) sA += gmi[q] * yj[q] + gmj[k][q] * yi[q];
+#pragma unroll
+                    for (int q = 4; q < 9; ++q) sS += gmi[q] * yj[q] + gmj[k][q] * yi[q];
+                    float *o = gg + (int64_t)uu[k] * 3 * F + 3 * c;
+                    o[0] = sI; o[1] = sA; o[2] = sS;
+                }
             }
         }
         store_coords(gY, i, c, N, F, acc);
@@ -839,6 +887,99 @@ __global__ void k_emb_bwd(const float *__restrict__ pos, const float *__restrict
                 gA_atom[(int64_t)i * F + lane + 32 * k] = accA[k];
                 gB_atom[(int64_t)i * F + lane + 32 * k] = accB[k];
             }
+        }
+    }
+}
+
+// Embedding edge adjoint for forces only, one warp per undirected pair
+// (lane = channels lane + 32k): both directed uses of the pair at once,
+//   edge_g[e]      = (dE/dphi, dE/du) of the use (i, j), u = r_ij / d
+//   edge_g[rev e]  = the same for (j, i), u_ji = -u
+//   gfu[u]         = dE/df^p summed over both uses (columns p*F + c).
+// Pair-parallel, so small systems still fill the GPU.
+template <int CPL>
+__global__ void k_emb_bwd_pairs(const float *__restrict__ pos, const float *__restrict__ box,
+                                const int32_t *__restrict__ batch, const int32_t *__restrict__ z,
+                                const int2 *__restrict__ uij, const int32_t *__restrict__ ue,
+                                const int32_t *__restrict__ rev, const int32_t *__restrict__ nu, int N, int max_z,
+                                RadialParams rp, const float *__restrict__ fu, const float *__restrict__ Ta,
+                                const float *__restrict__ Tb, const float *__restrict__ gXraw,
+                                float *__restrict__ gfu, float4 *__restrict__ edge_g,
+                                __nv_bfloat16 *__restrict__ gfu_bf) {
+    constexpr int F = CPL * 32;
+    const int lane = threadIdx.x & 31;
+    const int U = *nu;
+    for (int64_t uu = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; uu < U;
+         uu += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int u = (int)uu;
+        const int2 p = uij[u];
+        const int i = p.x, j = p.y;
+        float x, y, zz;
+        pair_vec(pos, box, batch, i, j, x, y, zz);
+        const float d = sqrtf(x * x + y * y + zz * zz);
+        const float inv = 1.0f / d;
+        const float ux = x * inv, uy = y * inv, uz = zz * inv;
+        const float phi = cutoff_phi(d, rp);
+        const float bxx = ux * ux - (1.0f / 3.0f), byy = uy * uy - (1.0f / 3.0f);
+        const float bxy = ux * uy, bxz = ux * uz, byz = uy * uz;
+        int zi = z[i], zj = z[j];
+        zi = (zi < 0 || zi >= max_z) ? 0 : zi;
+        zj = (zj < 0 || zj >= max_z) ? 0 : zj;
+        float a_phi = 0.f, ax = 0.f, ay = 0.f, az = 0.f;   // use (i, j)
+        float b_phi = 0.f, bx = 0.f, by = 0.f, bz = 0.f;   // use (j, i), gradient w.r.t. u_ji
+#pragma unroll
+        for (int k = 0; k < CPL; ++k) {
+            const int c = lane + 32 * k;
+            const float *fp = fu + (int64_t)u * 3 * F + c;
+            const float f0 = fp[0], f1 = fp[F], f2 = fp[2 * F];
+            float gi[9], gj[9];
+            load_coords(gXraw, i, c, N, F, gi);
+            load_coords(gXraw, j, c, N, F, gj);
+            const float Zij = Ta[(int64_t)zi * F + c] + Tb[(int64_t)zj * F + c];
+            const float Zji = Ta[(int64_t)zj * F + c] + Tb[(int64_t)zi * F + c];
+            // use (i, j)
+            const float gc0 = gi[0];
+            const float gcA = gi[1] * ux + gi[2] * uy + gi[3] * uz;
+            const float gcS = gi[4] * bxx + gi[5] * byy + gi[6] * bxy + gi[7] * bxz + gi[8] * byz;
+            a_phi = fmaf(Zij, gc0 * f0 + gcA * f1 + gcS * f2, a_phi);
+            {
+                const float cA = phi * Zij * f1, cS = phi * Zij * f2;
+                ax += cA * gi[1] + cS * (2.f * ux * gi[4] + uy * gi[6] + uz * gi[7]);
+                ay += cA * gi[2] + cS * (2.f * uy * gi[5] + ux * gi[6] + uz * gi[8]);
+                az += cA * gi[3] + cS * (ux * gi[7] + uy * gi[8]);
+            }
+            // use (j, i): v = -u, the S basis is even in u
+            const float vx = -ux, vy = -uy, vz = -uz;
+            const float hc0 = gj[0];
+            const float hcA = gj[1] * vx + gj[2] * vy + gj[3] * vz;
+            const float hcS = gj[4] * bxx + gj[5] * byy + gj[6] * bxy + gj[7] * bxz + gj[8] * byz;
+            b_phi = fmaf(Zji, hc0 * f0 + hcA * f1 + hcS * f2, b_phi);
+            {
+                const float cA = phi * Zji * f1, cS = phi * Zji * f2;
+                bx += cA * gj[1] + cS * (2.f * vx * gj[4] + vy * gj[6] + vz * gj[7]);
+                by += cA * gj[2] + cS * (2.f * vy * gj[5] + vx * gj[6] + vz * gj[8]);
+                bz += cA * gj[3] + cS * (vx * gj[7] + vy * gj[8]);
+            }
+            const float o0 = phi * (Zij * gc0 + Zji * hc0);
+            const float o1 = phi * (Zij * gcA + Zji * hcA);
+            const float o2 = phi * (Zij * gcS + Zji * hcS);
+            float *o = gfu + (int64_t)u * 3 * F + c;
+            o[0] = o0;
+            o[F] = o1;
+            o[2 * F] = o2;
+            if (gfu_bf) {
+                __nv_bfloat16 *ob = gfu_bf + (int64_t)u * 3 * F + c;
+                ob[0] = __float2bfloat16_rn(o0);
+                ob[F] = __float2bfloat16_rn(o1);
+                ob[2 * F] = __float2bfloat16_rn(o2);
+            }
+        }
+        a_phi = warp_sum(a_phi); ax = warp_sum(ax); ay = warp_sum(ay); az = warp_sum(az);
+        b_phi = warp_sum(b_phi); bx = warp_sum(bx); by = warp_sum(by); bz = warp_sum(bz);
+        if (lane == 0) {
+            const int e = ue[u];
+            edge_g[e] = make_float4(a_phi, ax, ay, az);
+            edge_g[rev[e]] = make_float4(b_phi, bx, by, bz);
         }
     }
 }
@@ -1398,9 +1539,15 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     float *gfu = f32(Lw.gfu), *Gp = f32(Lw.gp), *gA = f32(Lw.gA_atom), *gB = f32(Lw.gB_atom);
     float4 *edge_g = wsp<float4>(ctx, Lw.edge_g);
     const int bwd_blocks = grid_for((int64_t)N * 32, 256, sms);
-#define EMB_BWD(CPL)                                                                                    \
-    k_emb_bwd<CPL><<<bwd_blocks, 256, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, d.max_z, rp, fu, \
-                                               Ta, Tb, gXraw, wg ? 1 : 0, gfu, edge_g, gA, gB, gfu_bf)
+    // weight gradients need per-atom sums of the pair-embedding adjoints
+    // (atom-parallel kernel); forces alone use the pair-parallel kernel
+#define EMB_BWD(CPL)                                                                                         \
+    if (wg)                                                                                                  \
+        k_emb_bwd<CPL><<<bwd_blocks, 256, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, d.max_z, rp, \
+                                                   fu, Ta, Tb, gXraw, 1, gfu, edge_g, gA, gB, gfu_bf);        \
+    else                                                                                                     \
+        k_emb_bwd_pairs<CPL><<<sms * 8, 256, 0, st>>>(pos, box, batch, z, uij, ue, rev, nu, N, d.max_z, rp, fu, \
+                                                      Ta, Tb, gXraw, gfu, edge_g, gfu_bf)
     switch (F / 32) {
         case 2: EMB_BWD(2); break;
         case 4: EMB_BWD(4); break;
