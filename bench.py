@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--md", type=int, default=0,
+                    help="also time this many velocity-Verlet steps (0.5 fs, 1 A skin, rebuild every 20)")
+    ap.add_argument("--per-molecule", action="store_true",
+                    help="for batched workloads, also time one eager call per molecule")
     return ap.parse_args()
 
 
@@ -68,6 +72,11 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def job_rate(units_per_rank, local_ms, world):
+    """Whole-job throughput: units of all ranks / the slowest rank's time."""
+    return world * units_per_rank / (allmax(local_ms, world) / 1e3)
 
 
 def allmax(x, world):
@@ -328,12 +337,12 @@ def run_ours(args):
     barrier(world)
     ck = clocks.stop() if rank == 0 else None
     times = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = allmax(sum(times), world)
+    value = job_rate(args.steps, sum(times), world)
+    total_ms = world * args.steps / value * 1e3
     m.reset_status()
     g.replay()
     torch.cuda.synchronize()
     m.check_status("bench timed steps")
-    value = world * args.steps / (total_ms / 1e3)
 
     # ---- live per-stage timing (eager steps with the library's event profiler)
     F_ = shape.F
@@ -453,12 +462,90 @@ def run_ours(args):
             accuracy["vs_fp64_oracle"] = {
                 "energy_rel": float(np.max(np.abs(E_run - Es) / scale)),
                 "force_rel_rms": float(np.sqrt(np.mean(np.sum((F_run - Fr) ** 2, 1)) / np.mean(np.sum(Fr ** 2, 1))))}
+    if args.per_molecule and S > 1:
+        line["per_molecule_launches"] = per_molecule(sys_, W, prec, dev, args)
+    if args.md > 0:
+        del g, m, nl
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        line["md"] = run_md(sys_, shape, prec, dev, args)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def per_molecule(sys_, W, prec, dev, args):
+    """The same batch evaluated with one eager neighbor + energy/force call
+    per molecule (the launch pattern the batched, graph-captured form
+    replaces)."""
+    import torch
+    from paper_2402_17660_gb300.tnet import TensorNet
+    starts = np.searchsorted(sys_.batch, np.arange(sys_.n_systems + 1))
+    nmax = int(np.max(np.diff(starts)))
+    m = TensorNet(W, max_atoms=nmax, max_systems=1, max_pairs=nmax * nmax + 64, precision=prec, device=dev)
+    mols = []
+    for s in range(sys_.n_systems):
+        a, b = starts[s], starts[s + 1]
+        mols.append((torch.from_numpy(sys_.z[a:b]).to(dev), torch.from_numpy(sys_.pos[a:b]).to(dev)))
+
+    def one_pass():
+        for zz, pp in mols:
+            nl = m.neighbors(pp)
+            m.energy_forces(zz, pp, nl)
+
+    one_pass()
+    torch.cuda.synchronize()
+    m.check_status("per-molecule pass")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, args.steps // 5)
+    t0 = time.perf_counter()
+    e0.record()
+    for _ in range(reps):
+        one_pass()
+    e1.record()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) / reps
+    gpu = e0.elapsed_time(e1) / 1e3 / reps
+    return {"value": 1.0 / max(wall, gpu), "unit": "batch evals/s", "molecules": sys_.n_systems,
+            "ms_per_batch": max(wall, gpu) * 1e3, "kernels_per_batch": None,
+            "note": "eager: one tnet_neighbors + tnet_energy_forces call per molecule, no graph"}
+
+
+def run_md(sys_, shape, prec, dev, args):
+    """Velocity Verlet through tnet_md_step (blocks of 20 steps replayed as
+    one CUDA graph): ns/day and total-energy drift."""
+    import torch
+    from paper_2402_17660_gb300 import synth
+    from paper_2402_17660_gb300.tnet import TensorNet
+    if sys_.n_systems != 1:
+        return {"skipped": "MD runs one system"}
+    Wmd = synth.md_weights(shape, seed=0)
+    N = sys_.n_atoms
+    m = TensorNet(Wmd, max_atoms=N, max_systems=1, max_pairs=int(100 * N) + 1024, precision=prec, device=dev)
+    z = torch.from_numpy(sys_.z).to(dev)
+    pos = torch.from_numpy(sys_.pos).to(dev).clone()
+    vel = torch.from_numpy(synth.maxwell_boltzmann(sys_, 300.0, seed=1)).to(dev)
+    inv_m = torch.from_numpy(1.0 / sys_.masses()).to(dev)
+    box = torch.from_numpy(sys_.box).to(dev) if sys_.box is not None else None
+    R, dt = 20, 0.5
+    n = max(R, (args.md // R) * R)
+    m.reset_status()
+    m.md(z, inv_m, pos, vel, box, dt, 1.0, R, 2 * R)           # warm-up, graph capture
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ek, ep = m.md(z, inv_m, pos, vel, box, dt, 1.0, R, n)
+    e1.record()
+    torch.cuda.synchronize()
+    status = int(m.status.item())
+    sec = e0.elapsed_time(e1) / 1e3
+    et = (ek + ep).cpu().numpy()
+    return {"steps": n, "dt_fs": dt, "rebuild_every": R, "skin_A": 1.0, "ns_per_day": n * dt * 1e-6 / sec * 86400,
+            "steps_per_s": n / sec, "drift_eV_per_atom_per_ps": float((et[-1] - et[0]) / N / (n * dt * 1e-3)),
+            "status": status, "weights": "random init, output layer scaled by 0.05"}
 
 
 def kernel_revision() -> str:
