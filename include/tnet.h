@@ -214,6 +214,19 @@ int tnet_neighbors_noalloc(int n_atoms, int n_systems, const float *pos, const i
 int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void *B, float *C, int32_t *status_dev,
                        tnet_stream_t stream);
 
+/* ---- tuning (no counterpart in the paper) ---------------------------------
+ * Launch-shape knobs of a context: grid sizes and GEMM column tiles.  Every
+ * value is valid on any input; the choice only changes speed.  Knob k takes
+ * one of tnet_tuning_candidates(k, ...) (the count is returned; values are
+ * written up to max).  tnet_set_tuning rejects values outside the candidate
+ * lists.  An autotuner times the candidates on a real input and sets the
+ * fastest (paper_2402_17660_gb300.tnet.autotune). */
+int tnet_tuning_knobs(void);
+const char *tnet_tuning_name(int knob);
+int tnet_tuning_candidates(int knob, int32_t *values, int max);
+int tnet_get_tuning(tnet_ctx *ctx, int32_t *knobs, int n);
+int tnet_set_tuning(tnet_ctx *ctx, const int32_t *knobs, int n);
+
 /* ---- instrumentation (no counterpart in the paper; used by the benchmark) */
 
 /* Number of CUDA kernels the library has enqueued in this process (all

@@ -35,6 +35,11 @@ SIGNATURES = {
                             _vp, _vp]),
     "tnet_neighbors_noalloc": (_i32, [_i32, _i32, _vp, _vp, _vp, _f32, _vp, _vp, _i64, _vp, _vp, _vp]),
     "tnet_debug_tc_gemm": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "tnet_tuning_knobs": (_i32, []),
+    "tnet_tuning_name": (ctypes.c_char_p, [_i32]),
+    "tnet_tuning_candidates": (_i32, [_i32, ctypes.POINTER(_i32), _i32]),
+    "tnet_get_tuning": (_i32, [_vp, ctypes.POINTER(_i32), _i32]),
+    "tnet_set_tuning": (_i32, [_vp, ctypes.POINTER(_i32), _i32]),
     "tnet_launch_count": (_i64, []),
     "tnet_profile": (_i32, [_vp, _i32]),
     "tnet_profile_read": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_i64)]),

@@ -187,6 +187,14 @@ void ProfSeq::mark(int tag) {
 
 using namespace tnet;
 
+// Candidate values of each tuning knob (TuneKnob) and the default's index.
+static const int kTuneCandidates[T_NKNOBS][4] = {{1, 2, 3, 4}, {192, 128, 0, 0}, {256, 128, 0, 0}, {4, 8, 16, 0},
+                                                 {4, 8, 16, 0}};
+static const int kTuneCount[T_NKNOBS] = {4, 2, 2, 3, 3};
+static const int kTuneDefault[T_NKNOBS] = {2, 0, 0, 1, 1};
+static const char *kTuneNames[T_NKNOBS] = {"gemm_ctas_per_sm", "tc_tile_n_3f", "tc_tile_n_2f", "row_blocks_per_sm",
+                                           "pair_blocks_per_sm"};
+
 static const char *kTagNames[P_NTAGS] = {
     "neighbors", "graph_prep", "emb_edges", "emb_node", "mlp1", "mlp2", "mlp3", "message",
     "node_mix", "node_elem", "output", "output_bwd", "node_bwd", "message_bwd", "mlp_elem_bwd",
@@ -255,6 +263,7 @@ int tnet_create(tnet_ctx **out, const tnet_model_desc *d, int max_atoms, int max
     rp.beta = (float)pow((2.0 / d->K) * (1.0 - start), -2.0);
     rp.mu0 = (float)start;
     rp.dmu = (float)((1.0 - start) / (d->K - 1));
+    for (int k = 0; k < T_NKNOBS; ++k) c->tune[k] = kTuneCandidates[k][kTuneDefault[k]];
     rc = tnet_kernel_setup(c);
     if (rc) {
         free(c);
@@ -277,6 +286,30 @@ int tnet_destroy(tnet_ctx *c) {
 }
 
 int64_t tnet_launch_count(void) { return g_launches.load(); }
+
+int tnet_tuning_knobs(void) { return T_NKNOBS; }
+const char *tnet_tuning_name(int knob) { return (knob >= 0 && knob < T_NKNOBS) ? kTuneNames[knob] : nullptr; }
+int tnet_tuning_candidates(int knob, int32_t *values, int max) {
+    if (knob < 0 || knob >= T_NKNOBS || !values) return -1;
+    const int n = kTuneCount[knob] < max ? kTuneCount[knob] : max;
+    for (int i = 0; i < n; ++i) values[i] = kTuneCandidates[knob][i];
+    return kTuneCount[knob];
+}
+int tnet_get_tuning(tnet_ctx *c, int32_t *knobs, int n) {
+    if (!c || !knobs || n < 0) return TNET_ERR_ARG;
+    for (int k = 0; k < n && k < T_NKNOBS; ++k) knobs[k] = c->tune[k];
+    return TNET_OK;
+}
+int tnet_set_tuning(tnet_ctx *c, const int32_t *knobs, int n) {
+    if (!c || !knobs || n < 0 || n > T_NKNOBS) return TNET_ERR_ARG;
+    for (int k = 0; k < n; ++k) {
+        bool ok = false;
+        for (int i = 0; i < kTuneCount[k]; ++i) ok |= kTuneCandidates[k][i] == knobs[k];
+        if (!ok) return TNET_ERR_ARG;
+    }
+    for (int k = 0; k < n; ++k) c->tune[k] = knobs[k];
+    return TNET_OK;
+}
 
 const char *tnet_profile_tag(int tag) { return (tag >= 0 && tag < P_NTAGS) ? kTagNames[tag] : nullptr; }
 

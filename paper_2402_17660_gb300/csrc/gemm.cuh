@@ -233,14 +233,15 @@ __global__ void __launch_bounds__(GTHREADS) k_sgemm(GemmShape P, Epi epi) {
 }
 
 // Host launcher.  grid: persistent, sized from the capacity.
+// max_ctas: size of the persistent grid (a tuning knob: SMs x CTAs per SM)
 template <bool TA, bool TB, class Epi>
-inline int sgemm(const GemmShape &P, const Epi &epi, int num_sms, cudaStream_t st) {
+inline int sgemm(const GemmShape &P, const Epi &epi, int max_ctas, cudaStream_t st) {
     int maxM = 0;
     for (int z = 0; z < P.nclass; ++z) maxM = P.M[z] > maxM ? P.M[z] : maxM;
     if (maxM <= 0 || P.N <= 0) return TNET_OK;
     if (P.K % GBK || P.N % 4) return TNET_ERR_ARG;
     const int64_t tiles = (int64_t)((maxM + GBM - 1) / GBM) * ((P.N + GBN - 1) / GBN);
-    int64_t grid = (int64_t)num_sms * 3;
+    int64_t grid = max_ctas > 0 ? max_ctas : 1;
     if (tiles < grid) grid = tiles;
     dim3 g((unsigned)grid, 1, P.nclass);
     k_sgemm<TA, TB, Epi><<<g, GTHREADS, 0, st>>>(P, epi);

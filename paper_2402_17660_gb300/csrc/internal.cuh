@@ -272,6 +272,11 @@ namespace tnet {
 void count_launch();
 
 // Stages timed by the optional CUDA-event profiler (tnet_profile).
+// Tuning knobs: 0 SIMT-GEMM CTAs per SM, 1 tcgen05 column tile for N = 3F,
+// 2 tcgen05 column tile for N = 2F, 3 row-kernel blocks per SM, 4 pair-kernel
+// blocks (256 threads) per SM.
+enum TuneKnob { T_GEMM_CTAS = 0, T_TC_BN_3F, T_TC_BN_2F, T_ROW_BLOCKS, T_PAIR_BLOCKS, T_NKNOBS };
+
 enum ProfTag {
     P_NBR = 0, P_PREP, P_EMB_EDGE, P_EMB_NODE, P_MLP1, P_MLP2, P_MLP3, P_MESSAGE, P_NODE_MIX,
     P_NODE_ELEM, P_OUTPUT, P_OUT_BWD, P_NODE_BWD, P_MSG_BWD, P_MLP_ELEM_BWD, P_MLP3_BWD, P_MLP2_BWD,
@@ -288,6 +293,8 @@ struct tnet_ctx {
     tnet::Layout lay;
     tnet::RadialParams rp;
     int device, num_sms;
+    // tuning knobs (tnet_set_tuning); see kTuneCandidates in api.cu
+    int tune[8];
     // optional stage profiler
     int prof_on, prof_n, prof_cap;
     cudaEvent_t *prof_ev;

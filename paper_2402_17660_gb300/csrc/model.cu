@@ -1145,7 +1145,10 @@ int tnet_kernel_setup(tnet_ctx *c) {
 // Tensor-core GEMM with the column tile chosen from N.
 template <class Epi>
 int tc_any(const tc::TcShape &P, const __nv_bfloat16 *A, int64_t a_rows, int64_t lda, const __nv_bfloat16 *B,
-           int64_t b_rows, int64_t ldb, const Epi &epi, int32_t *status, cudaStream_t st) {
+           int64_t b_rows, int64_t ldb, const Epi &epi, int32_t *status, cudaStream_t st, int bn = 0) {
+    if (bn == 128 && P.N % 128 == 0) return tc::tc_gemm<128>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
+    if (bn == 192 && P.N % 192 == 0) return tc::tc_gemm<192>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
+    if (bn == 256 && P.N % 256 == 0) return tc::tc_gemm<256>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
     if (P.N <= 32) return tc::tc_gemm<32>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
     if (P.N <= 64) return tc::tc_gemm<64>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
     if (P.N <= 128) return tc::tc_gemm<128>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
@@ -1179,6 +1182,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     const int F = d.F, K = d.K, NL = d.L, H = F / 2;
     const int sms = ctx->num_sms;
     const RadialParams rp = ctx->rp;
+    const int gctas = sms * ctx->tune[T_GEMM_CTAS];
+    const int bn3 = ctx->tune[T_TC_BN_3F], bn2 = ctx->tune[T_TC_BN_2F];
+    const int pair_grid = sms * ctx->tune[T_PAIR_BLOCKS];
     Weights W, G;
     weight_offsets(&d, wblob, &W);
     weight_offsets(&d, grad_w, &G);
@@ -1285,7 +1291,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     float *eu = f32(Lw.eu), *phiu = f32(Lw.phiu), *fu = f32(Lw.fu);
-    k_edge_rbf<<<sms * 8, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu, eu_bf);
+    k_edge_rbf<<<pair_grid, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu, eu_bf);
     count_launch();
     k_elem_tables<<<d.max_z, F, 0, st>>>(W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
     count_launch();
@@ -1297,7 +1303,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         const EpiBiasAct ep{W.dproj_b, nullptr, 0, fu, 3 * F, 0, nullptr};
         GemmShape pp = gshape(maxU, 3 * F, K, eu, K, W.dproj_w, K);
         pp.rows_dev = nu;
-        TRY(sgemm<false, true>(pp, ep, sms, st));
+        TRY(sgemm<false, true>(pp, ep, gctas, st));
     }
 
     // ---- embedding
@@ -1305,7 +1311,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     float *Xraw = f32(Lw.Xraw), *Uemb = f32(Lw.Uemb), *n0 = f32(Lw.n0), *as1 = f32(Lw.as1),
           *hs1 = f32(Lw.hs1), *as2 = f32(Lw.as2), *s = f32(Lw.s), *q0 = f32(Lw.q0);
     float2 *ln0 = wsp<float2>(ctx, Lw.ln0);
-    const int atom_blocks = N < sms * 8 ? N : sms * 8;
+    const int atom_blocks = N < sms * ctx->tune[T_ROW_BLOCKS] ? N : sms * ctx->tune[T_ROW_BLOCKS];
     k_emb_edges<<<atom_blocks, F, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, F, d.max_z, rp, fu, Ta,
                                            Tb, Xraw, status, nbf);
     count_launch();
@@ -1314,11 +1320,11 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     TNET_LAUNCH_CHECK();
     pf.mark(P_EMB_NODE);
     TRY(sgemm<false, true>(gshape(N, 2 * F, F, n0, F, W.emb_mlp1_w, F),
-                           EpiBiasAct{W.emb_mlp1_b, as1, 2 * F, hs1, 2 * F, 1, nullptr}, sms, st));
+                           EpiBiasAct{W.emb_mlp1_b, as1, 2 * F, hs1, 2 * F, 1, nullptr}, gctas, st));
     TRY(sgemm<false, true>(gshape(N, 3 * F, 2 * F, hs1, 2 * F, W.emb_mlp2_w, 2 * F),
-                           EpiBiasAct{W.emb_mlp2_b, as2, 3 * F, s, 3 * F, 1, nullptr}, sms, st));
+                           EpiBiasAct{W.emb_mlp2_b, as2, 3 * F, s, 3 * F, 1, nullptr}, gctas, st));
     if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, emix_b16, 3 * F, F, EpiStore{Uemb, F, 0}, status, st));
-    else TRY(sgemm<false, true>(gshape_classes(N, F, Xraw, W.emb_mix_w), EpiStore{Uemb, F, 0}, sms, st));
+    else TRY(sgemm<false, true>(gshape_classes(N, F, Xraw, W.emb_mix_w), EpiStore{Uemb, F, 0}, gctas, st));
     float *X = f32(Lw.Xin);  // layer 0 input
     k_emb_scale<<<grid_for((int64_t)N * F, 256, sms), 256, 0, st>>>(Uemb, s, N, F, X);
     count_launch();
@@ -1338,25 +1344,25 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             pf.mark(P_MLP1);  // K = num_rbf: FP32 (see the projections above)
             GemmShape p1 = gshape(maxU, F, K, eu, K, Lr.mlp1_w, K);
             p1.rows_dev = nu;
-            TRY(sgemm<false, true>(p1, e1, sms, st));
+            TRY(sgemm<false, true>(p1, e1, gctas, st));
             pf.mark(P_MLP2);
-            TRY(tc_any(t2, h1_bf, maxU, F, lb[l].mlp2, 2 * F, F, e2, status, st));
+            TRY(tc_any(t2, h1_bf, maxU, F, lb[l].mlp2, 2 * F, F, e2, status, st, bn2));
             pf.mark(P_MLP3);
-            TRY(tc_any(t3, h2_bf, maxU, 2 * F, lb[l].mlp3, 3 * F, 2 * F, e3, status, st));
+            TRY(tc_any(t3, h2_bf, maxU, 2 * F, lb[l].mlp3, 3 * F, 2 * F, e3, status, st, bn3));
             return TNET_OK;
         }
         pf.mark(P_MLP1);
         GemmShape p1 = gshape(maxU, F, K, eu, K, Lr.mlp1_w, K);
         p1.rows_dev = nu;
-        TRY(sgemm<false, true>(p1, e1, sms, st));
+        TRY(sgemm<false, true>(p1, e1, gctas, st));
         pf.mark(P_MLP2);
         GemmShape p2 = gshape(maxU, 2 * F, F, h1, F, Lr.mlp2_w, F);
         p2.rows_dev = nu;
-        TRY(sgemm<false, true>(p2, e2, sms, st));
+        TRY(sgemm<false, true>(p2, e2, gctas, st));
         pf.mark(P_MLP3);
         GemmShape p3 = gshape(maxU, 3 * F, 2 * F, h2, 2 * F, Lr.mlp3_w, 2 * F);
         p3.rows_dev = nu;
-        TRY(sgemm<false, true>(p3, e3, sms, st));
+        TRY(sgemm<false, true>(p3, e3, gctas, st));
         return TNET_OK;
     };
     const int ew = grid_for((int64_t)N * F, 256, sms);
@@ -1371,7 +1377,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         TNET_LAUNCH_CHECK();
         pf.mark(P_NODE_MIX);
         if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix1, 3 * F, F, EpiStore{Y, F, 0}, status, st));
-        else TRY(sgemm<false, true>(gshape_classes(N, F, Xn, W.layer[l].mix1_w), EpiStore{Y, F, 0}, sms, st));
+        else TRY(sgemm<false, true>(gshape_classes(N, F, Xn, W.layer[l].mix1_w), EpiStore{Y, F, 0}, gctas, st));
         TRY(edge_mlp(l));
         pf.mark(P_MESSAGE);
         k_message<<<atom_blocks, F, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, N, F, M);
@@ -1382,7 +1388,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         TNET_LAUNCH_CHECK();
         pf.mark(P_NODE_MIX);
         if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix2, 3 * F, F, EpiStore{dX, F, 0}, status, st));
-        else TRY(sgemm<false, true>(gshape_classes(N, F, Tn, W.layer[l].mix2_w), EpiStore{dX, F, 0}, sms, st));
+        else TRY(sgemm<false, true>(gshape_classes(N, F, Tn, W.layer[l].mix2_w), EpiStore{dX, F, 0}, gctas, st));
         pf.mark(P_NODE_ELEM);
         k_residual<<<ew, 256, 0, st>>>(Xn, dX, N, F, Xnext);
         count_launch();
@@ -1399,9 +1405,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     TRY(sgemm<false, true>(gshape(N, F, 3 * F, hn, 3 * F, W.out_w, 3 * F),
-                           EpiBiasAct{W.out_b, ao, F, o, F, 1, nullptr}, sms, st));
+                           EpiBiasAct{W.out_b, ao, F, o, F, 1, nullptr}, gctas, st));
     TRY(sgemm<false, true>(gshape(N, H, F, o, F, W.head1_w, F),
-                           EpiBiasAct{W.head1_b, at, H, t, H, 1, nullptr}, sms, st));
+                           EpiBiasAct{W.head1_b, at, H, t, H, 1, nullptr}, gctas, st));
     k_head<<<warps_grid, 256, 0, st>>>(t, N, H, W.head2_w, W.head2_b, Ei);
     count_launch();
     k_energy<<<S, 256, 0, st>>>(Ei, sys_start, sys_end, energy);
@@ -1417,8 +1423,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     k_head_bwd<<<grid_for((int64_t)N * H, 256, sms), 256, 0, st>>>(at, N, H, W.head2_w, seed, batch, gat);
     count_launch();
     TNET_LAUNCH_CHECK();
-    TRY(sgemm<false, false>(gshape(N, F, H, gat, H, W.head1_w, F), EpiGradAct{ao, F, gao, F, 0}, sms, st));
-    TRY(sgemm<false, false>(gshape(N, 3 * F, F, gao, F, W.out_w, 3 * F), EpiStore{ghn, 3 * F, 0}, sms, st));
+    TRY(sgemm<false, false>(gshape(N, F, H, gat, H, W.head1_w, F), EpiGradAct{ao, F, gao, F, 0}, gctas, st));
+    TRY(sgemm<false, false>(gshape(N, 3 * F, F, gao, F, W.out_w, 3 * F), EpiStore{ghn, 3 * F, 0}, gctas, st));
     k_out_norms_bwd<<<N, F, 0, st>>>(Xfin, h, ghn, lno, W.out_ln_g, N, F, gX);
     count_launch();
     TNET_LAUNCH_CHECK();
@@ -1449,7 +1455,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         count_launch();
         TNET_LAUNCH_CHECK();
         if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix2T, 3 * F, F, EpiStore{gTn, F, 0}, status, st));
-        else TRY(sgemm<false, false>(gshape_classes(N, F, gdX, Lr.mix2_w), EpiStore{gTn, F, 0}, sms, st));
+        else TRY(sgemm<false, false>(gshape_classes(N, F, gdX, Lr.mix2_w), EpiStore{gTn, F, 0}, gctas, st));
         if (wg) TRY(wgrad_outer(rows3(gdX, Tn), wpart, wcap, gw(Gr.mix2_w), 0, sms, st));
         k_T_bwd<<<ew, 256, 0, st>>>(Y, M, gTn, N, F, gY, gM);
         count_launch();
@@ -1459,7 +1465,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         k_message_bwd<<<atom_blocks, F, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, gM, N, F, gY, gg, nbf);
         count_launch();
         pf.mark(P_MLP_ELEM_BWD);
-        k_mlp3_bwd<<<sms * 8, 256, 0, st>>>(gg, a3, phiu, nu, 3 * F, gphiu, ga3_bf);
+        k_mlp3_bwd<<<pair_grid, 256, 0, st>>>(gg, a3, phiu, nu, 3 * F, gphiu, ga3_bf);
         count_launch();
         TNET_LAUNCH_CHECK();
         const EpiGradAct g3{a2, 2 * F, ga2, 2 * F, 0, ga2_bf, 2 * F};
@@ -1469,26 +1475,26 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             tc::TcShape t3 = tc::tshape(maxU, 2 * F, 3 * F), t2 = tc::tshape(maxU, F, 2 * F);
             t2.rows_dev = t3.rows_dev = nu;
             pf.mark(P_MLP3_BWD);
-            TRY(tc_any(t3, ga3_bf, maxU, 3 * F, lb[l].mlp3T, 2 * F, 3 * F, g3, status, st));
+            TRY(tc_any(t3, ga3_bf, maxU, 3 * F, lb[l].mlp3T, 2 * F, 3 * F, g3, status, st, bn2));
             pf.mark(P_MLP2_BWD);
             TRY(tc_any(t2, ga2_bf, maxU, 2 * F, lb[l].mlp2T, F, 2 * F, g2, status, st));
             pf.mark(P_MLP1_BWD);  // N = num_rbf: FP32 SIMT
             GemmShape q1 = gshape(maxU, K, F, ga1, F, Lr.mlp1_w, K);
             q1.rows_dev = nu;
-            TRY(sgemm<false, false>(q1, g1, sms, st));
+            TRY(sgemm<false, false>(q1, g1, gctas, st));
         } else {
             pf.mark(P_MLP3_BWD);
             GemmShape q3 = gshape(maxU, 2 * F, 3 * F, gg, 3 * F, Lr.mlp3_w, 2 * F);
             q3.rows_dev = nu;
-            TRY(sgemm<false, false>(q3, g3, sms, st));
+            TRY(sgemm<false, false>(q3, g3, gctas, st));
             pf.mark(P_MLP2_BWD);
             GemmShape q2 = gshape(maxU, F, 2 * F, ga2, 2 * F, Lr.mlp2_w, F);
             q2.rows_dev = nu;
-            TRY(sgemm<false, false>(q2, g2, sms, st));
+            TRY(sgemm<false, false>(q2, g2, gctas, st));
             pf.mark(P_MLP1_BWD);
             GemmShape q1 = gshape(maxU, K, F, ga1, F, Lr.mlp1_w, K);
             q1.rows_dev = nu;
-            TRY(sgemm<false, false>(q1, g1, sms, st));
+            TRY(sgemm<false, false>(q1, g1, gctas, st));
         }
         if (wg) {
             TRY(wgrad_outer(rows1(3 * F, 2 * F, maxU, gg, 3 * F, h2, 2 * F, nu), wpart, wcap, gw(Gr.mlp3_w), 0, sms, st));
@@ -1504,7 +1510,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         }
         pf.mark(P_NODE_BWD);
         if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix1T, 3 * F, F, EpiStore{gX, F, 1}, status, st));
-        else TRY(sgemm<false, false>(gshape_classes(N, F, gY, Lr.mix1_w), EpiStore{gX, F, 1}, sms, st));
+        else TRY(sgemm<false, false>(gshape_classes(N, F, gY, Lr.mix1_w), EpiStore{gX, F, 1}, gctas, st));
         k_node_norm_bwd<<<ew, 256, 0, st>>>(Xl, qn, N, F, gX);
         count_launch();
         TNET_LAUNCH_CHECK();
@@ -1517,10 +1523,10 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     TRY(sgemm<false, false>(gshape(N, 2 * F, 3 * F, gas2, 3 * F, W.emb_mlp2_w, 2 * F),
-                            EpiGradAct{as1, 2 * F, gas1, 2 * F, 0}, sms, st));
-    TRY(sgemm<false, false>(gshape(N, F, 2 * F, gas1, 2 * F, W.emb_mlp1_w, F), EpiStore{gn0, F, 0}, sms, st));
+                            EpiGradAct{as1, 2 * F, gas1, 2 * F, 0}, gctas, st));
+    TRY(sgemm<false, false>(gshape(N, F, 2 * F, gas1, 2 * F, W.emb_mlp1_w, F), EpiStore{gn0, F, 0}, gctas, st));
     if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, emixT_b16, 3 * F, F, EpiStore{gXraw, F, 0}, status, st));
-    else TRY(sgemm<false, false>(gshape_classes(N, F, gU, W.emb_mix_w), EpiStore{gXraw, F, 0}, sms, st));
+    else TRY(sgemm<false, false>(gshape_classes(N, F, gU, W.emb_mix_w), EpiStore{gXraw, F, 0}, gctas, st));
     k_ln0_bwd<<<N, F, 0, st>>>(Xraw, gn0, ln0, W.emb_ln_g, N, F, gXraw);
     count_launch();
     TNET_LAUNCH_CHECK();
@@ -1546,7 +1552,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         k_emb_bwd<CPL><<<bwd_blocks, 256, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, d.max_z, rp, \
                                                    fu, Ta, Tb, gXraw, 1, gfu, edge_g, gA, gB, gfu_bf);        \
     else                                                                                                     \
-        k_emb_bwd_pairs<CPL><<<sms * 8, 256, 0, st>>>(pos, box, batch, z, uij, ue, rev, nu, N, d.max_z, rp, fu, \
+        k_emb_bwd_pairs<CPL><<<pair_grid, 256, 0, st>>>(pos, box, batch, z, uij, ue, rev, nu, N, d.max_z, rp, fu, \
                                                       Ta, Tb, gXraw, gfu, edge_g, gfu_bf)
     switch (F / 32) {
         case 2: EMB_BWD(2); break;
@@ -1565,7 +1571,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     {   // dE/de of the pair's radial basis also flows through the projections
         GemmShape pg = gshape(maxU, K, 3 * F, gfu, 3 * F, W.dproj_w, K);
         pg.rows_dev = nu;
-        TRY(sgemm<false, false>(pg, EpiStore{ge, K, NL > 0}, sms, st));
+        TRY(sgemm<false, false>(pg, EpiStore{ge, K, NL > 0}, gctas, st));
     }
     if (wg) {
         TRY(wgrad_outer(rows1(3 * F, K, maxU, gfu, 3 * F, eu, K, nu), wpart, wcap, gw(G.dproj_w), 0, sms, st));
@@ -1584,7 +1590,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     }
     if (!forces) return TNET_OK;
     pf.mark(P_FORCES);
-    k_pair_vec<<<sms * 8, 256, 0, st>>>(pos, box, batch, uij, ue, rev, nu, rp, ge, NL > 0 ? gphiu : nullptr, edge_g,
+    k_pair_vec<<<pair_grid, 256, 0, st>>>(pos, box, batch, uij, ue, rev, nu, rp, ge, NL > 0 ? gphiu : nullptr, edge_g,
                                         Gp);
     count_launch();
     k_forces<<<(N + 127) / 128, 128, 0, st>>>(row_ptr, col, pair_of, Gp, N, forces);

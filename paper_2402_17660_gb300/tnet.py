@@ -8,6 +8,8 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import json
+import os
 
 import numpy as np
 import torch
@@ -110,6 +112,17 @@ class TensorNet:
             raise ValueError("weight blob size mismatch")
         self.weights = w
 
+    # -------------------------------------------------------------- tuning
+    def get_tuning(self) -> list[int]:
+        n = self.lib.tnet_tuning_knobs()
+        buf = (ctypes.c_int32 * n)()
+        _lib.check(self.lib.tnet_get_tuning(self.ctx, buf, n), "tnet_get_tuning")
+        return list(buf)
+
+    def set_tuning(self, knobs) -> None:
+        buf = (ctypes.c_int32 * len(knobs))(*knobs)
+        _lib.check(self.lib.tnet_set_tuning(self.ctx, buf, len(knobs)), "tnet_set_tuning")
+
     # -------------------------------------------------------------- status
     def reset_status(self):
         self.status.zero_()
@@ -192,3 +205,68 @@ class EnergyFn(torch.autograd.Function):
             _, _, gw = model.energy_forces(z, pos.detach(), nl, batch, box, n_systems, forces=True,
                                            grad_weights=True, seed=gE.to(torch.float32).contiguous())
         return gpos, gw, None, None, None, None, None, None
+
+
+# ------------------------------------------------------------------ autotuner
+TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune", "tuning.json")
+
+
+def tuning_knobs(lib=None) -> list[tuple[str, list[int]]]:
+    lib = lib or _lib.load()
+    out = []
+    for k in range(lib.tnet_tuning_knobs()):
+        buf = (ctypes.c_int32 * 8)()
+        n = lib.tnet_tuning_candidates(k, buf, 8)
+        out.append((lib.tnet_tuning_name(k).decode(), list(buf)[:n]))
+    return out
+
+
+def autotune(model: TensorNet, z, pos, nl: NeighborList, batch=None, box=None, n_systems=1, reps=3,
+             cache: str | None = TUNE_CACHE, force=False):
+    """Pick launch shapes by timing them on this input (coordinate descent
+    over the context's knobs, CUDA events around whole energy+force calls),
+    set them on the model and cache them as JSON keyed by GPU, precision,
+    shape and size.  Returns (knobs, {knob: {candidate: ms}})."""
+    dev = model.device
+    key = "|".join([torch.cuda.get_device_name(dev), f"p{model.desc.precision}", f"F{model.F}L{model.L}",
+                    f"N{pos.shape[0]}", f"S{n_systems}", f"E{int(nl.n_pairs.item()) // 1024}k"])
+    table = {}
+    if cache and os.path.exists(cache):
+        try:
+            table = json.load(open(cache))
+        except (OSError, ValueError):
+            table = {}
+    if not force and key in table:
+        model.set_tuning(table[key]["knobs"])
+        return table[key]["knobs"], table[key].get("timings", {})
+    E = torch.empty(n_systems, dtype=torch.float64, device=dev)
+    Fo = torch.empty((pos.shape[0], 3), dtype=torch.float32, device=dev)
+
+    def run_ms():
+        model.energy_forces(z, pos, nl, batch, box, n_systems, out=(E, Fo, None))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(reps):
+            model.energy_forces(z, pos, nl, batch, box, n_systems, out=(E, Fo, None))
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    knobs = model.get_tuning()
+    timings = {}
+    for k, (name, cands) in enumerate(tuning_knobs(model.lib)):
+        res = {}
+        for v in cands:
+            trial = list(knobs)
+            trial[k] = v
+            model.set_tuning(trial)
+            res[v] = run_ms()
+        knobs[k] = min(res, key=res.get)
+        timings[name] = {str(v): round(t, 4) for v, t in res.items()}
+    model.set_tuning(knobs)
+    if cache:
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        table[key] = {"knobs": knobs, "timings": timings}
+        with open(cache, "w") as f:
+            json.dump(table, f, indent=1)
+    return knobs, timings

@@ -73,3 +73,13 @@ def test_pack_unpack_roundtrip():
     back = tnet.unpack_weights(blob, 64, 8, 1, 100)
     for k in W:
         assert np.array_equal(back[k], W[k])
+
+
+def test_tuning_knobs_exported(lib):
+    from paper_2402_17660_gb300 import tnet
+    knobs = tnet.tuning_knobs(lib)
+    assert len(knobs) == lib.tnet_tuning_knobs() >= 4
+    for name, cands in knobs:
+        assert name and len(cands) >= 2 and all(c > 0 for c in cands)
+    assert lib.tnet_tuning_name(99) is None
+    assert lib.tnet_set_tuning(None, None, 0) == 1

@@ -285,3 +285,28 @@ def test_bf16_mode_batch_and_weight_grads():
                 for k in outs[1])
     print(f"BF16 vs FP32 worst per-tensor weight-gradient rel RMS diff {worst:.2e}")
     assert worst <= 5e-2
+
+
+def test_autotuner_knobs_change_speed_not_results(tmp_path):
+    from paper_2402_17660_gb300.tnet import autotune, tuning_knobs
+    s = synth.workload("water3000")
+    for prec in (0, 1):
+        from paper_2402_17660_gb300.tnet import TensorNet
+        m = TensorNet(W, max_atoms=s.n_atoms, max_systems=1, max_pairs=250000, precision=prec, device=DEV)
+        z, pos, batch, box = to_dev(s)
+        nl = gpu_pairs(m, s)
+        E0, F0 = gpu_energy_forces(m, s, nl=nl)
+        knobs, timings = autotune(m, z, pos, nl, None, box, 1, reps=1, cache=str(tmp_path / "t.json"))
+        assert len(timings) == len(tuning_knobs())
+        # every candidate of every knob gives the same result within rounding
+        for k, (name, cands) in enumerate(tuning_knobs()):
+            for v in cands:
+                trial = list(knobs)
+                trial[k] = v
+                m.set_tuning(trial)
+                E1, F1 = gpu_energy_forces(m, s, nl=nl)
+                assert abs(E1[0] - E0[0]) <= 1e-6 * abs(E0[0]), (name, v)
+                assert force_error(F1, F0) <= 1e-5, (name, v)
+        # the cache is read back
+        knobs2, _ = autotune(m, z, pos, nl, None, box, 1, cache=str(tmp_path / "t.json"))
+        assert knobs2 == knobs
