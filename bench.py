@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water3000")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32x3", "bf16"],
+                    help="fp32: SIMT FP32 GEMMs; tf32x3: FP32-accurate 3xTF32 tensor-core GEMMs; "
+                         "bf16: BF16 tensor-core GEMMs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--md", type=int, default=0,
@@ -283,7 +285,7 @@ def run_ours(args):
     W = synth.init_weights(shape, seed=0)
     N = sys_.n_atoms
     cap = int(75 * N) + 1024
-    prec = 1 if args.precision == "bf16" else 0
+    prec = {"fp32": 0, "bf16": 1, "tf32x3": 2}[args.precision]
     m = TensorNet(W, max_atoms=N, max_systems=sys_.n_systems, max_pairs=cap, precision=prec, device=dev)
     lib = m.lib
     z = torch.from_numpy(sys_.z).to(dev)
@@ -380,11 +382,16 @@ def run_ours(args):
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s, derived
     bf = args.precision == "bf16"
+    x3 = args.precision == "tf32x3"
     work_tags = [k for k in sorted(stages, key=lambda k: -stages[k]["ms_per_step"])
                  if stage_work(k, nu, N, n_pairs, F_, shape.K, bf) is not None]
     if work_tags:
         tag = work_tags[0]
         flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, bf)
+        if x3 and tag in ("mlp2", "mlp3", "mlp3_bwd", "mlp2_bwd"):
+            # 3xTF32: three TF32 MMAs per product; operands fp32 + fp32 residual
+            engine = "tensor_tf32"
+            nbytes = nbytes * 1.5
         per_launch_ms = stages[tag]["ms_per_step"] * args.profile_steps / stages[tag]["instances"]
         traffic = None
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
@@ -392,9 +399,14 @@ def run_ours(args):
             tr = json.load(open(tpath)).get(f"{args.workload}:{args.precision}:{tag}")
             if tr and tr.get("kernel_rev") == kernel_revision():
                 traffic = tr["bytes_per_launch"]
-        cpeak, cname, cnote = ((bf16_peak, "tensor", "of measured bf16 burst (MEASURED_PEAKS.json)")
-                               if engine == "tensor" else
-                               (fp32_peak, "alu", "FP32 FFMA peak 152 SM x 128 lanes x 2 x 2070 MHz (derived)"))
+        if engine == "tensor":
+            cpeak, cname, cnote = bf16_peak, "tensor", "of measured bf16 burst (MEASURED_PEAKS.json)"
+        elif engine == "tensor_tf32":
+            # useful FLOP against one third of the TF32 rate (nominal TF32 = bf16 / 2)
+            cpeak, cname = bf16_peak / 2 / 3, "tensor"
+            cnote = "measured bf16 burst x nominal TF32/BF16 ratio 1/2, divided by the 3 MMAs of 3xTF32"
+        else:
+            cpeak, cname, cnote = fp32_peak, "alu", "FP32 FFMA peak 152 SM x 128 lanes x 2 x 2070 MHz (derived)"
         ridge = cpeak * 1e12 / (hbm * 1e9)            # FLOP per byte where the two roofs meet
         if engine != "hbm" and flops / nbytes >= ridge:
             ach = flops / (per_launch_ms * 1e-3) / 1e12
@@ -444,7 +456,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     E_run, F_run = E.cpu().numpy().copy(), Fo.cpu().numpy().astype(np.float64)
     accuracy = {}
-    if prec:
+    if prec == 1:
         m32 = TensorNet(W, max_atoms=N, max_systems=S, max_pairs=cap, precision=0, device=dev)
         nl32 = m32.neighbors(pos, batch, box, S)
         E32, F32, _ = m32.energy_forces(z, pos, nl32, batch, box, S)
@@ -460,7 +472,8 @@ def run_ours(args):
         del m32
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 GEMM / f32" if prec else "f32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f32", 1: "bf16 GEMM / f32", 2: "f32 (3xTF32 tensor-core GEMM)"}[prec],
             "data": "synthetic",
             "config": workload_config(sys_, n_pairs, args),
             "ns_per_day_at_0.5fs": value / world * 86400 * FS_PER_STEP * 1e-6,

@@ -48,11 +48,15 @@ typedef struct tnet_ctx tnet_ctx;
  * radial basis functions, L: number of interaction layers, max_z: rows of
  * the atomic-number embedding table, cutoff_upper/lower: the cosine cutoff
  * interval in Angstrom (Sec. 2.4: embedding_dimension 128, num_layers 2,
- * num_rbf 32, max_z 100, cutoff 0..5 A).  precision: 0 = FP32 everywhere,
- * 1 = BF16 tensor-core GEMMs with FP32 accumulation for the dense
- * contractions (geometry, basis and scatter-adds stay FP32; the per-system
- * energy is reduced in FP64 in both modes).
+ * num_rbf 32, max_z 100, cutoff 0..5 A).  precision: 0 = FP32 everywhere
+ * (SIMT GEMMs); 1 = BF16 tensor-core GEMMs with FP32 accumulation for the
+ * 2F/3F-wide radial-MLP layers and the I/A/S channel mixing; 2 = the same
+ * GEMMs on the tensor cores in 3xTF32 (FP32 operands split into TF32 high
+ * and residual parts), FP32-level accuracy.  Geometry, radial basis, the
+ * num_rbf-wide layers and scatter-adds stay FP32 and the per-system energy
+ * is reduced in FP64 in every mode.
  * Limits: F a multiple of 64 in [64, 512], K a multiple of 8 in [8, 64],
+ * (precision 1 and 2 need F <= 256),
  * 0 <= L <= 8, 1 <= max_z <= 128, 0 <= cutoff_lower < cutoff_upper. */
 typedef struct {
     int F, K, L, max_z;
@@ -213,6 +217,11 @@ int tnet_neighbors_noalloc(int n_atoms, int n_systems, const float *pos, const i
  * <= 512.  Bounded in-kernel waits report TNET_ERR_TIMEOUT in *status_dev. */
 int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void *B, float *C, int32_t *status_dev,
                        tnet_stream_t stream);
+/* The same in 3xTF32: A [M][K], B [N][K] float32; A_lo, B_lo are caller
+ * scratch of the same sizes that receive the TF32 residuals; K a multiple of
+ * 4, N a multiple of 4 and <= 512. */
+int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const float *B, float *A_lo, float *B_lo, float *C,
+                           int32_t *status_dev, tnet_stream_t stream);
 
 /* ---- tuning (no counterpart in the paper) ---------------------------------
  * Launch-shape knobs of a context: grid sizes and GEMM column tiles.  Every

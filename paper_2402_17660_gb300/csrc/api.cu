@@ -16,7 +16,7 @@ int validate_desc(const tnet_model_desc *d) {
     if (d->L < 0 || d->L > 8) return TNET_ERR_ARG;
     if (d->max_z < 1 || d->max_z > 128) return TNET_ERR_ARG;
     if (!(d->cutoff_upper > d->cutoff_lower) || d->cutoff_lower < 0.f) return TNET_ERR_ARG;
-    if (d->precision != 0 && d->precision != 1) return TNET_ERR_ARG;
+    if (d->precision < 0 || d->precision > 2) return TNET_ERR_ARG;
     return TNET_OK;
 }
 
@@ -129,9 +129,11 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->zpart = take(f * 2 * L->zsplits * Z * F);
     L->wpart_floats = 4LL << 20;
     L->wpart = take(f * L->wpart_floats);
-    // BF16 copies (only with precision 1): weights forward + transposed, one
-    // node-tensor operand, and the per-pair radial-MLP operands
-    const int64_t bfp = d->precision == 1 ? 1 : 0, b2 = 2;
+    // tensor-core modes: weight operands (bf16 forward + transposed copies, or
+    // fp32 residuals + transposed high parts), one node-tensor operand copy and
+    // the per-pair radial-MLP operand copies (bf16 or fp32 TF32 residuals)
+    const int prec = d->precision;
+    const int64_t esz = prec == 1 ? 2 : (prec == 2 ? 4 : 0);
     int64_t nw = 0;
     {
         nw += Z * F + F * 2 * F + F + 3 * F * K + 3 * F + 2 * F + 2 * F * F + 2 * F + 3 * F * 2 * F + 3 * F +
@@ -139,16 +141,16 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
         nw += NL * (F * K + F + 2 * F * F + 2 * F + 3 * F * 2 * F + 3 * F + 6 * F * F);
         nw += 6 * F + F * 3 * F + F + F / 2 * F + F / 2 + F / 2 + 1;
     }
-    L->wbf_elems = 2 * nw;
-    L->wbf = take(bfp * b2 * L->wbf_elems);
-    L->nbf = take(bfp * b2 * n9);
-    L->eu_bf = take(bfp * b2 * U * K);
-    L->h1_bf = take(bfp * b2 * U * F);
-    L->h2_bf = take(bfp * b2 * U * 2 * F);
-    L->ga3_bf = take(bfp * b2 * U * 3 * F);
-    L->ga2_bf = take(bfp * b2 * U * 2 * F);
-    L->ga1_bf = take(bfp * b2 * U * F);
-    L->gfu_bf = take(bfp * b2 * U * 3 * F);
+    L->wbf_bytes = prec ? 3 * nw * esz + 128 * 256 : 0;
+    L->wbf = take(L->wbf_bytes);
+    L->nbf = take(esz * n9);
+    L->eu_bf = 0;
+    L->h1_bf = take(esz * U * F);
+    L->h2_bf = take(esz * U * 2 * F);
+    L->ga3_bf = take(esz * U * 3 * F);
+    L->ga2_bf = take(esz * U * 2 * F);
+    L->ga1_bf = 0;
+    L->gfu_bf = 0;
     // MD
     L->md_row_ptr = take(i * (N + 1));
     L->md_col = take(i * E);

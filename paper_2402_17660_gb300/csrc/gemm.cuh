@@ -37,13 +37,18 @@ struct GemmShape {
 // --------------------------------------------------------------- epilogues
 // Each epilogue receives 4 consecutive columns (n..n+3, all < N) of row m by
 // value (a pointer would force the accumulator fragment into local memory).
-// Optional BF16 copies feed the tensor-core GEMMs of the BF16 mode.
-__device__ __forceinline__ void store_bf16x4(__nv_bfloat16 *p, const float o[4]) {
-    __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]), b = __floats2bfloat162_rn(o[2], o[3]);
-    uint2 u;
-    u.x = *reinterpret_cast<uint32_t *>(&a);
-    u.y = *reinterpret_cast<uint32_t *>(&b);
-    *reinterpret_cast<uint2 *>(p) = u;
+// Optional operand copies (bf16 or TF32 residual) feed the tensor-core GEMMs.
+__device__ __forceinline__ void store_copy4(const OpCopy &c, int64_t idx, const float o[4]) {
+    if (c.mode == 1) {
+        __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]), b = __floats2bfloat162_rn(o[2], o[3]);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t *>(&a);
+        u.y = *reinterpret_cast<uint32_t *>(&b);
+        *reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(c.p) + idx) = u;
+    } else if (c.mode == 2) {
+        *reinterpret_cast<float4 *>(static_cast<float *>(c.p) + idx) =
+            make_float4(tf32_residual(o[0]), tf32_residual(o[1]), tf32_residual(o[2]), tf32_residual(o[3]));
+    }
 }
 
 struct EpiStore {  // C = v (+ C when accumulate)
@@ -60,7 +65,7 @@ struct EpiStore {  // C = v (+ C when accumulate)
     }
 };
 
-struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m] (+ bf16 copy)
+struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m] (+ operand copy)
     const float *bias;
     float *pre;
     int64_t ldp;
@@ -68,8 +73,8 @@ struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m] (+ bf1
     int64_t ldo;
     int silu;
     const float *rowscale;
-    __nv_bfloat16 *out_bf;
-    int64_t ldob;
+    OpCopy out_cp;
+    int64_t ldoc;
     __device__ void operator()(int z, int64_t m, int n, float4 vv) const {
         const float v[4] = {vv.x, vv.y, vv.z, vv.w};
         float a[4], o[4];
@@ -83,18 +88,18 @@ struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m] (+ bf1
         }
         if (pre) *reinterpret_cast<float4 *>(pre + m * ldp + n) = make_float4(a[0], a[1], a[2], a[3]);
         if (out) *reinterpret_cast<float4 *>(out + m * ldo + n) = make_float4(o[0], o[1], o[2], o[3]);
-        if (out_bf) store_bf16x4(out_bf + m * ldob + n, o);
+        if (out_cp.mode) store_copy4(out_cp, m * ldoc + n, o);
     }
 };
 
-struct EpiGradAct {  // out = v * silu'(pre)  (+ out when accumulate) (+ bf16 copy)
+struct EpiGradAct {  // out = v * silu'(pre)  (+ out when accumulate) (+ operand copy)
     const float *pre;
     int64_t ldp;
     float *out;
     int64_t ldo;
     int accumulate;
-    __nv_bfloat16 *out_bf;
-    int64_t ldob;
+    OpCopy out_cp;
+    int64_t ldoc;
     __device__ void operator()(int z, int64_t m, int n, float4 vv) const {
         const float v[4] = {vv.x, vv.y, vv.z, vv.w};
         const float4 a = *reinterpret_cast<const float4 *>(pre + m * ldp + n);
@@ -106,7 +111,7 @@ struct EpiGradAct {  // out = v * silu'(pre)  (+ out when accumulate) (+ bf16 co
             o[0] += c.x; o[1] += c.y; o[2] += c.z; o[3] += c.w;
         }
         *p = make_float4(o[0], o[1], o[2], o[3]);
-        if (out_bf) store_bf16x4(out_bf + m * ldob + n, o);
+        if (out_cp.mode) store_copy4(out_cp, m * ldoc + n, o);
     }
 };
 

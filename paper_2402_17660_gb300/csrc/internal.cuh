@@ -81,15 +81,27 @@ __device__ __forceinline__ void store_coords(float *__restrict__ T, int n, int c
     for (int k = 0; k < 5; ++k) pS[(int64_t)k * F] = v[4 + k];
 }
 
-// optional BF16 copy of a node tensor (operand of the BF16 tensor-core mixing)
-__device__ __forceinline__ void store_coords_bf(__nv_bfloat16 *__restrict__ T, int n, int c, int N, int F,
-                                                const float v[9]) {
-    if (!T) return;
-    T[(int64_t)n * F + c] = __float2bfloat16_rn(v[0]);
+// Operand copy written next to an FP32 result for the tensor-core GEMMs:
+// mode 1 = bf16 copy (BF16 mode), mode 2 = its TF32 residual x - tf32(x) in
+// fp32 (3xTF32 mode, where x itself serves as the TF32 high part).
+struct OpCopy {
+    void *p;
+    int mode;
+};
+__device__ __forceinline__ float tf32_residual(float x) {
+    return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+__device__ __forceinline__ void opcopy_store(const OpCopy &c, int64_t idx, float v) {
+    if (c.mode == 1) static_cast<__nv_bfloat16 *>(c.p)[idx] = __float2bfloat16_rn(v);
+    else if (c.mode == 2) static_cast<float *>(c.p)[idx] = tf32_residual(v);
+}
+__device__ __forceinline__ void store_coords_cp(const OpCopy &T, int n, int c, int N, int F, const float v[9]) {
+    if (!T.mode) return;
+    opcopy_store(T, (int64_t)n * F + c, v[0]);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) T[((int64_t)N + 3LL * n + k) * F + c] = __float2bfloat16_rn(v[1 + k]);
+    for (int k = 0; k < 3; ++k) opcopy_store(T, ((int64_t)N + 3LL * n + k) * F + c, v[1 + k]);
 #pragma unroll
-    for (int k = 0; k < 5; ++k) T[(4LL * N + 5LL * n + k) * F + c] = __float2bfloat16_rn(v[4 + k]);
+    for (int k = 0; k < 5; ++k) opcopy_store(T, (4LL * N + 5LL * n + k) * F + c, v[4 + k]);
 }
 
 // coordinates -> row-major 3x3
@@ -253,9 +265,9 @@ struct Layout {
     size_t fu, gfu, ue, edge_g, gp, q0, gEi;
     // weight-gradient scratch
     size_t gA_atom, gB_atom, zpart, wpart;
-    // BF16 mode: operand copies for the tensor-core GEMMs
+    // tensor-core modes: operand copies for the GEMMs
     size_t wbf, nbf, eu_bf, h1_bf, h2_bf, ga3_bf, ga2_bf, ga1_bf, gfu_bf;
-    int64_t wbf_elems;
+    int64_t wbf_bytes;
     int64_t wpart_floats, zsplits;
     // MD
     size_t md_row_ptr, md_col, md_npairs, md_forces, md_energy, md_pos_ref, md_step;

@@ -201,7 +201,7 @@ __global__ void k_lower_assign(const int32_t *__restrict__ row_ptr, const int32_
 __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restrict__ box,
                            const int32_t *__restrict__ batch, const int2 *__restrict__ uij,
                            const int32_t *__restrict__ nu, int maxU, RadialParams rp,
-                           float *__restrict__ eu, float *__restrict__ phiu, __nv_bfloat16 *__restrict__ eu_bf) {
+                           float *__restrict__ eu, float *__restrict__ phiu, OpCopy eu_cp) {
     const int U = *nu;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)U * rp.K;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -214,7 +214,7 @@ __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restric
         float e, de;
         expnorm_k(d, k, rp, phi, 0.f, e, de);
         eu[t] = e;
-        if (eu_bf) eu_bf[t] = __float2bfloat16_rn(e);
+        opcopy_store(eu_cp, t, e);
         if (k == 0) phiu[u] = phi;
     }
 }
@@ -271,7 +271,7 @@ __global__ void k_emb_edges(const float *__restrict__ pos, const float *__restri
                             const int32_t *__restrict__ pair_of, int N, int F, int max_z, RadialParams rp,
                             const float *__restrict__ fu, const float *__restrict__ Ta,
                             const float *__restrict__ Tb, float *__restrict__ Xraw, int32_t *status,
-                            __nv_bfloat16 *__restrict__ Xraw_bf) {
+                            OpCopy Xraw_cp) {
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         int zi = z[i];
@@ -317,7 +317,7 @@ __global__ void k_emb_edges(const float *__restrict__ pos, const float *__restri
             }
         }
         store_coords(Xraw, i, c, N, F, v);
-        store_coords_bf(Xraw_bf, i, c, N, F, v);
+        store_coords_cp(Xraw_cp, i, c, N, F, v);
     }
 }
 
@@ -360,7 +360,7 @@ __global__ void k_emb_scale(const float *__restrict__ U, const float *__restrict
 // ----------------------------------------------------- interaction ---
 // Xn = X / (||X|| + 1)
 __global__ void k_node_norm(const float *__restrict__ X, int N, int F, float *__restrict__ qn,
-                            float *__restrict__ Xn, __nv_bfloat16 *__restrict__ Xn_bf) {
+                            float *__restrict__ Xn, OpCopy Xn_cp) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -372,7 +372,7 @@ __global__ void k_node_norm(const float *__restrict__ X, int N, int F, float *__
 #pragma unroll
         for (int k = 0; k < 9; ++k) v[k] *= r;
         store_coords(Xn, i, c, N, F, v);
-        store_coords_bf(Xn_bf, i, c, N, F, v);
+        store_coords_cp(Xn_cp, i, c, N, F, v);
     }
 }
 
@@ -418,7 +418,7 @@ __global__ void k_message(const int32_t *__restrict__ row_ptr, const int32_t *__
 
 // T = Y M + M Y; Tn = decomp(T) / (||T|| + 1)
 __global__ void k_node_update(const float *__restrict__ Y, const float *__restrict__ M, int N, int F,
-                              float *__restrict__ Tn, __nv_bfloat16 *__restrict__ Tn_bf) {
+                              float *__restrict__ Tn, OpCopy Tn_cp) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -436,7 +436,7 @@ __global__ void k_node_update(const float *__restrict__ Y, const float *__restri
 #pragma unroll
         for (int k = 0; k < 9; ++k) tc[k] *= r;
         store_coords(Tn, i, c, N, F, tc);
-        store_coords_bf(Tn_bf, i, c, N, F, tc);
+        store_coords_cp(Tn_cp, i, c, N, F, tc);
     }
 }
 
@@ -561,7 +561,7 @@ __global__ void k_out_norms_bwd(const float *__restrict__ X, const float *__rest
 
 // X_out = Xn + dX + dX dX:  g_dX = g + expand^T(G Q^T + Q^T G), G = decomp^T(g)
 __global__ void k_residual_bwd(const float *__restrict__ gX, const float *__restrict__ dX, int N, int F,
-                               float *__restrict__ gdX, __nv_bfloat16 *__restrict__ gdX_bf) {
+                               float *__restrict__ gdX, OpCopy gdX_cp) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -578,7 +578,7 @@ __global__ void k_residual_bwd(const float *__restrict__ gX, const float *__rest
 #pragma unroll
         for (int k = 0; k < 9; ++k) g[k] += gq[k];
         store_coords(gdX, i, c, N, F, g);
-        store_coords_bf(gdX_bf, i, c, N, F, g);
+        store_coords_cp(gdX_cp, i, c, N, F, g);
     }
 }
 
@@ -634,7 +634,7 @@ __global__ void k_T_bwd(const float *__restrict__ Y, const float *__restrict__ M
 __global__ void k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                               const int32_t *__restrict__ pair_of, const float *__restrict__ gU,
                               const float *__restrict__ Y, const float *__restrict__ gM, int N, int F,
-                              float *__restrict__ gY, float *__restrict__ gg, __nv_bfloat16 *__restrict__ gY_bf) {
+                              float *__restrict__ gY, float *__restrict__ gg, OpCopy gY_cp) {
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         float yi[9], gmi[9], acc[9];
@@ -681,14 +681,14 @@ __global__ void k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t
             }
         }
         store_coords(gY, i, c, N, F, acc);
-        store_coords_bf(gY_bf, i, c, N, F, acc);
+        store_coords_cp(gY_cp, i, c, N, F, acc);
     }
 }
 
 // g = phi * silu(a3):  ga3 = gg * phi * silu'(a3) (in place), gphi += <gg, silu(a3)>
 __global__ void k_mlp3_bwd(float *__restrict__ gg, const float *__restrict__ a3,
                            const float *__restrict__ phiu, const int32_t *__restrict__ nu, int W,
-                           float *__restrict__ gphi, __nv_bfloat16 *__restrict__ ga3_bf) {
+                           float *__restrict__ gphi, OpCopy ga3_cp) {
     const int U = *nu;
     const int lane = threadIdx.x & 31;
     for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < U;
@@ -701,7 +701,7 @@ __global__ void k_mlp3_bwd(float *__restrict__ gg, const float *__restrict__ a3,
             s = fmaf(gv, silu_f(a), s);
             const float ga = gv * phi * silu_grad_f(a);
             gg[o] = ga;
-            if (ga3_bf) ga3_bf[o] = __float2bfloat16_rn(ga);
+            opcopy_store(ga3_cp, o, ga);
         }
         s = warp_sum(s);
         if (lane == 0) gphi[u] += s;
@@ -732,7 +732,7 @@ __global__ void k_node_norm_bwd(const float *__restrict__ X, const float *__rest
 // X0 = s_p * U:  gU = s_p gX0; gas2 = <gX0, U>_p * silu'(as2)
 __global__ void k_emb_scale_bwd(const float *__restrict__ gX0, const float *__restrict__ U,
                                 const float *__restrict__ s, const float *__restrict__ as2, int N, int F,
-                                float *__restrict__ gU, float *__restrict__ gas2, __nv_bfloat16 *__restrict__ gU_bf) {
+                                float *__restrict__ gU, float *__restrict__ gas2, OpCopy gU_cp) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -751,7 +751,7 @@ __global__ void k_emb_scale_bwd(const float *__restrict__ gX0, const float *__re
 #pragma unroll
         for (int k = 4; k < 9; ++k) g[k] *= si[2];
         store_coords(gU, i, c, N, F, g);
-        store_coords_bf(gU_bf, i, c, N, F, g);
+        store_coords_cp(gU_cp, i, c, N, F, g);
 #pragma unroll
         for (int p = 0; p < 3; ++p) gas2[t * 3 + p] = gs[p] * silu_grad_f(as2[t * 3 + p]);
     }
@@ -794,7 +794,7 @@ __global__ void k_emb_bwd(const float *__restrict__ pos, const float *__restrict
                           const float *__restrict__ fu, const float *__restrict__ Ta,
                           const float *__restrict__ Tb, const float *__restrict__ gXraw, int want_z,
                           float *__restrict__ gfu, float4 *__restrict__ edge_g, float *__restrict__ gA_atom,
-                          float *__restrict__ gB_atom, __nv_bfloat16 *__restrict__ gfu_bf) {
+                          float *__restrict__ gB_atom, OpCopy gfu_cp) {
     constexpr int F = CPL * 32;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -865,12 +865,10 @@ __global__ void k_emb_bwd(const float *__restrict__ pos, const float *__restrict
                         o[0] = o0;
                         o[F] = o1;
                         o[2 * F] = o2;
-                        if (gfu_bf) {
-                            __nv_bfloat16 *ob = gfu_bf + (int64_t)u * 3 * F + c;
-                            ob[0] = __float2bfloat16_rn(o0);
-                            ob[F] = __float2bfloat16_rn(o1);
-                            ob[2 * F] = __float2bfloat16_rn(o2);
-                        }
+                        const int64_t ob = (int64_t)u * 3 * F + c;
+                        opcopy_store(gfu_cp, ob, o0);
+                        opcopy_store(gfu_cp, ob + F, o1);
+                        opcopy_store(gfu_cp, ob + 2 * F, o2);
                     }
                     accB[k] = fmaf(phi, hc0 * f0 + hcA * f1 + hcS * f2, accB[k]);
                 }
@@ -905,7 +903,7 @@ __global__ void k_emb_bwd_pairs(const float *__restrict__ pos, const float *__re
                                 RadialParams rp, const float *__restrict__ fu, const float *__restrict__ Ta,
                                 const float *__restrict__ Tb, const float *__restrict__ gXraw,
                                 float *__restrict__ gfu, float4 *__restrict__ edge_g,
-                                __nv_bfloat16 *__restrict__ gfu_bf) {
+                                OpCopy gfu_cp) {
     constexpr int F = CPL * 32;
     const int lane = threadIdx.x & 31;
     const int U = *nu;
@@ -967,12 +965,10 @@ __global__ void k_emb_bwd_pairs(const float *__restrict__ pos, const float *__re
             o[0] = o0;
             o[F] = o1;
             o[2 * F] = o2;
-            if (gfu_bf) {
-                __nv_bfloat16 *ob = gfu_bf + (int64_t)u * 3 * F + c;
-                ob[0] = __float2bfloat16_rn(o0);
-                ob[F] = __float2bfloat16_rn(o1);
-                ob[2 * F] = __float2bfloat16_rn(o2);
-            }
+            const int64_t ob = (int64_t)u * 3 * F + c;
+            opcopy_store(gfu_cp, ob, o0);
+            opcopy_store(gfu_cp, ob + F, o1);
+            opcopy_store(gfu_cp, ob + 2 * F, o2);
         }
         a_phi = warp_sum(a_phi); ax = warp_sum(ax); ay = warp_sum(ay); az = warp_sum(az);
         b_phi = warp_sum(b_phi); bx = warp_sum(bx); by = warp_sum(by); bz = warp_sum(bz);
@@ -1116,14 +1112,20 @@ __global__ void k_seed_atoms(const float *__restrict__ seed, const int32_t *__re
     if (i < N) gEi[i] = seed ? seed[batch ? batch[i] : 0] : 1.0f;
 }
 
-// BF16 copies of the GEMM weights for the tensor-core mode: job j converts
-// a [rows][cols] float matrix, transposed when tr[j] (backward operands).
+// Weight operands of the tensor-core modes: job j reads a [rows][cols] float
+// matrix (transposed when tr[j], for backward operands) and writes a bf16
+// copy (mode 1) or an fp32 high part (if hi[j]) and TF32 residual (mode 2).
 constexpr int kMaxCvtJobs = 128;
 struct CvtJobs {
     const float *src[kMaxCvtJobs];
-    __nv_bfloat16 *dst[kMaxCvtJobs];
+    void *hi[kMaxCvtJobs];
+    void *lo[kMaxCvtJobs];
     int rows[kMaxCvtJobs], cols[kMaxCvtJobs], tr[kMaxCvtJobs];
-    int n;
+    int n, mode;
+};
+struct WOp {  // a weight operand: bf16 matrix, or fp32 high part + residual
+    const void *b;
+    const void *blo;
 };
 __global__ void k_cvt_weights(const __grid_constant__ CvtJobs J) {
     const int j = blockIdx.y;
@@ -1131,8 +1133,14 @@ __global__ void k_cvt_weights(const __grid_constant__ CvtJobs J) {
     const int R = J.rows[j], C = J.cols[j];
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < R * C; t += gridDim.x * blockDim.x) {
         const int r = t / C, c = t % C;
-        const __nv_bfloat16 v = __float2bfloat16_rn(J.src[j][t]);
-        J.dst[j][J.tr[j] ? (int64_t)c * R + r : (int64_t)t] = v;
+        const float v = J.src[j][t];
+        const int64_t o = J.tr[j] ? (int64_t)c * R + r : (int64_t)t;
+        if (J.mode == 1) {
+            static_cast<__nv_bfloat16 *>(J.hi[j])[o] = __float2bfloat16_rn(v);
+        } else {
+            if (J.hi[j]) static_cast<float *>(J.hi[j])[o] = v;
+            static_cast<float *>(J.lo[j])[o] = tf32_residual(v);
+        }
     }
 }
 
@@ -1219,47 +1227,64 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         return P;
     };
 
-    // ---- BF16 tensor-core mode: operand buffers and weight copies
-    const bool bf = d.precision == 1;
+    // ---- tensor-core modes: operand copies and weight copies
+    //   precision 1 (BF16): bf16 operands, one MMA per k-step
+    //   precision 2 (3xTF32): fp32 operands plus their TF32 residuals
+    const int prec = d.precision;
+    const bool tcm = prec != 0;
     const bool wg = grad_w != nullptr;
-    // FP32 activations h1, h2 are read by the FP32 GEMMs and by the weight
-    // gradients; the BF16 GEMMs read only their bf16 copies
-    const bool keep_h = !bf || wg;
-    auto bfp = [&](size_t off) { return bf ? wsp<__nv_bfloat16>(ctx, off) : (__nv_bfloat16 *)nullptr; };
-    // (the num_rbf-wide operands e(d) and dE/df stay FP32, so no bf16 copies)
-    __nv_bfloat16 *nbf = bfp(Lw.nbf), *eu_bf = nullptr, *h1_bf = bfp(Lw.h1_bf), *h2_bf = bfp(Lw.h2_bf),
-                  *ga3_bf = bfp(Lw.ga3_bf), *ga2_bf = bfp(Lw.ga2_bf), *ga1_bf = nullptr, *gfu_bf = nullptr;
+    // FP32 activations h1, h2 are read by the FP32 and 3xTF32 GEMMs and by the
+    // weight gradients; the BF16 GEMMs read only their bf16 copies
+    const bool keep_h = prec != 1 || wg;
+    auto cp = [&](size_t off) { return OpCopy{tcm ? (void *)(ctx->ws + off) : nullptr, prec}; };
+    // (the num_rbf-wide operands e(d) and dE/df stay FP32, so they get no copy)
+    const OpCopy none{nullptr, 0};
+    const OpCopy nbf = cp(Lw.nbf), eu_cp = none, h1_cp = cp(Lw.h1_bf), h2_cp = cp(Lw.h2_bf),
+                 ga3_cp = cp(Lw.ga3_bf), ga2_cp = cp(Lw.ga2_bf), ga1_cp = none, gfu_cp = none;
     struct LayerB {
-        __nv_bfloat16 *mlp2, *mlp3, *mlp2T, *mlp3T, *mix1, *mix1T, *mix2, *mix2T;
+        WOp mlp2, mlp3, mlp2T, mlp3T, mix1, mix1T, mix2, mix2T;
     } lb[8] = {};
-    __nv_bfloat16 *emix_b16 = nullptr, *emixT_b16 = nullptr;
+    WOp emix{}, emixT{};
 
     // ---- graph prep
     ProfSeq pf(ctx, st);
     pf.mark(P_PREP);
-    if (bf) {
+    if (tcm) {
         CvtJobs J;
         J.n = 0;
-        __nv_bfloat16 *wb = wsp<__nv_bfloat16>(ctx, Lw.wbf);
-        int64_t woff = 0;
+        J.mode = prec;
+        char *wb = ctx->ws + Lw.wbf;
+        const int esz = prec == 1 ? 2 : 4;
+        int64_t woff = 0;  // bytes
+        auto alloc = [&](int64_t elems) {
+            void *p = wb + woff;
+            woff += (elems * esz + 255) & ~(int64_t)255;
+            return p;
+        };
+        // forward operands keep the (out, in) = K-major layout; backward
+        // operands are transposed.  3xTF32 uses the fp32 weights themselves as
+        // the high part of the forward operands.
         auto job = [&](const float *src, int rows, int cols, int tr) {
-            __nv_bfloat16 *dst = wb + woff;
-            woff += (int64_t)rows * cols;
-            woff = (woff + 127) & ~(int64_t)127;
-            J.src[J.n] = src; J.dst[J.n] = dst; J.rows[J.n] = rows; J.cols[J.n] = cols; J.tr[J.n] = tr;
+            WOp w{};
+            void *hi = (prec == 1 || tr) ? alloc((int64_t)rows * cols) : nullptr;
+            void *lo = prec == 2 ? alloc((int64_t)rows * cols) : nullptr;
+            J.src[J.n] = src; J.hi[J.n] = hi; J.lo[J.n] = lo;
+            J.rows[J.n] = rows; J.cols[J.n] = cols; J.tr[J.n] = tr;
             ++J.n;
-            return dst;
+            w.b = hi ? hi : (const void *)src;
+            w.blo = lo;
+            return w;
         };
         auto job_classes_T = [&](const float *src) {  // [3][F][F] -> per-class transposes
-            __nv_bfloat16 *first = nullptr;
+            WOp first{};
             for (int q = 0; q < 3; ++q) {
-                __nv_bfloat16 *p = job(src + (int64_t)q * F * F, F, F, 1);
-                if (!q) first = p;
+                WOp w = job(src + (int64_t)q * F * F, F, F, 1);
+                if (!q) first = w;
             }
             return first;
         };
-        emix_b16 = job(W.emb_mix_w, 3 * F, F, 0);
-        emixT_b16 = job_classes_T(W.emb_mix_w);
+        emix = job(W.emb_mix_w, 3 * F, F, 0);
+        emixT = job_classes_T(W.emb_mix_w);
         for (int l = 0; l < NL; ++l) {
             const LayerW &Lr = W.layer[l];
             lb[l].mlp2 = job(Lr.mlp2_w, 2 * F, F, 0);
@@ -1271,11 +1296,23 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             lb[l].mix2 = job(Lr.mix2_w, 3 * F, F, 0);
             lb[l].mix2T = job_classes_T(Lr.mix2_w);
         }
-        if (woff > Lw.wbf_elems || J.n > kMaxCvtJobs) return TNET_ERR_WORKSPACE;
+        if (woff > Lw.wbf_bytes || J.n > kMaxCvtJobs) return TNET_ERR_WORKSPACE;
         k_cvt_weights<<<dim3(64, J.n), 256, 0, st>>>(J);
         count_launch();
         TNET_LAUNCH_CHECK();
     }
+    // tensor-core GEMM: A (fp32 A32 plus its copy) against weight operand w
+    auto tcg = [&](const tc::TcShape &P, const float *A32, const OpCopy &Acp, int64_t a_rows, int64_t lda,
+                   const WOp &w, int64_t b_rows, int64_t ldb, const auto &epi, int bn = 0) -> int {
+        if (prec == 1)
+            return tc_any(P, (const __nv_bfloat16 *)Acp.p, a_rows, lda, (const __nv_bfloat16 *)w.b, b_rows, ldb,
+                          epi, status, st, bn);
+        const tc::TcOperands o{A32, w.b, Acp.p, w.blo, a_rows, lda, b_rows, ldb};
+        if (P.N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st);
+        if (P.N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st);
+        if (P.N % 192 == 0 && bn != 128) return tc::tc_gemm_ops<192, true>(P, o, epi, status, st);
+        return tc::tc_gemm_ops<128, true>(P, o, epi, status, st);
+    };
     TNET_CUDA_TRY(cudaMemsetAsync(sys_start, 0, sizeof(int32_t) * S, st));
     TNET_CUDA_TRY(cudaMemsetAsync(sys_end, 0, sizeof(int32_t) * S, st));
     TRY(sys_bounds(batch, N, S, sys_start, sys_end, status, st));
@@ -1291,7 +1328,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     float *eu = f32(Lw.eu), *phiu = f32(Lw.phiu), *fu = f32(Lw.fu);
-    k_edge_rbf<<<pair_grid, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu, eu_bf);
+    k_edge_rbf<<<pair_grid, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu, eu_cp);
     count_launch();
     k_elem_tables<<<d.max_z, F, 0, st>>>(W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
     count_launch();
@@ -1323,7 +1360,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
                            EpiBiasAct{W.emb_mlp1_b, as1, 2 * F, hs1, 2 * F, 1, nullptr}, gctas, st));
     TRY(sgemm<false, true>(gshape(N, 3 * F, 2 * F, hs1, 2 * F, W.emb_mlp2_w, 2 * F),
                            EpiBiasAct{W.emb_mlp2_b, as2, 3 * F, s, 3 * F, 1, nullptr}, gctas, st));
-    if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, emix_b16, 3 * F, F, EpiStore{Uemb, F, 0}, status, st));
+    if (tcm) TRY(tcg(tc::tshape_classes(N, F), Xraw, nbf, 9LL * N, F, emix, 3 * F, F, EpiStore{Uemb, F, 0}));
     else TRY(sgemm<false, true>(gshape_classes(N, F, Xraw, W.emb_mix_w), EpiStore{Uemb, F, 0}, gctas, st));
     float *X = f32(Lw.Xin);  // layer 0 input
     k_emb_scale<<<grid_for((int64_t)N * F, 256, sms), 256, 0, st>>>(Uemb, s, N, F, X);
@@ -1335,10 +1372,10 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
           *gbuf = f32(Lw.g);
     auto edge_mlp = [&](int l) -> int {
         const LayerW &Lr = W.layer[l];
-        const EpiBiasAct e1{Lr.mlp1_b, a1, F, keep_h ? h1 : nullptr, F, 1, nullptr, h1_bf, F};
-        const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, keep_h ? h2 : nullptr, 2 * F, 1, nullptr, h2_bf, 2 * F};
+        const EpiBiasAct e1{Lr.mlp1_b, a1, F, keep_h ? h1 : nullptr, F, 1, nullptr, h1_cp, F};
+        const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, keep_h ? h2 : nullptr, 2 * F, 1, nullptr, h2_cp, 2 * F};
         const EpiBiasAct e3{Lr.mlp3_b, a3, 3 * F, gbuf, 3 * F, 1, phiu};
-        if (bf) {
+        if (tcm) {
             tc::TcShape t2 = tc::tshape(maxU, 2 * F, F), t3 = tc::tshape(maxU, 3 * F, 2 * F);
             t2.rows_dev = t3.rows_dev = nu;
             pf.mark(P_MLP1);  // K = num_rbf: FP32 (see the projections above)
@@ -1346,9 +1383,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             p1.rows_dev = nu;
             TRY(sgemm<false, true>(p1, e1, gctas, st));
             pf.mark(P_MLP2);
-            TRY(tc_any(t2, h1_bf, maxU, F, lb[l].mlp2, 2 * F, F, e2, status, st, bn2));
+            TRY(tcg(t2, h1, h1_cp, maxU, F, lb[l].mlp2, 2 * F, F, e2, bn2));
             pf.mark(P_MLP3);
-            TRY(tc_any(t3, h2_bf, maxU, 2 * F, lb[l].mlp3, 3 * F, 2 * F, e3, status, st, bn3));
+            TRY(tcg(t3, h2, h2_cp, maxU, 2 * F, lb[l].mlp3, 3 * F, 2 * F, e3, bn3));
             return TNET_OK;
         }
         pf.mark(P_MLP1);
@@ -1376,7 +1413,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         count_launch();
         TNET_LAUNCH_CHECK();
         pf.mark(P_NODE_MIX);
-        if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix1, 3 * F, F, EpiStore{Y, F, 0}, status, st));
+        if (tcm) TRY(tcg(tc::tshape_classes(N, F), Xn, nbf, 9LL * N, F, lb[l].mix1, 3 * F, F, EpiStore{Y, F, 0}));
         else TRY(sgemm<false, true>(gshape_classes(N, F, Xn, W.layer[l].mix1_w), EpiStore{Y, F, 0}, gctas, st));
         TRY(edge_mlp(l));
         pf.mark(P_MESSAGE);
@@ -1387,7 +1424,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         count_launch();
         TNET_LAUNCH_CHECK();
         pf.mark(P_NODE_MIX);
-        if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix2, 3 * F, F, EpiStore{dX, F, 0}, status, st));
+        if (tcm) TRY(tcg(tc::tshape_classes(N, F), Tn, nbf, 9LL * N, F, lb[l].mix2, 3 * F, F, EpiStore{dX, F, 0}));
         else TRY(sgemm<false, true>(gshape_classes(N, F, Tn, W.layer[l].mix2_w), EpiStore{dX, F, 0}, gctas, st));
         pf.mark(P_NODE_ELEM);
         k_residual<<<ew, 256, 0, st>>>(Xn, dX, N, F, Xnext);
@@ -1454,7 +1491,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         k_residual_bwd<<<ew, 256, 0, st>>>(gX, dX, N, F, gdX, nbf);
         count_launch();
         TNET_LAUNCH_CHECK();
-        if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix2T, 3 * F, F, EpiStore{gTn, F, 0}, status, st));
+        if (tcm) TRY(tcg(tc::tshape_classes(N, F), gdX, nbf, 9LL * N, F, lb[l].mix2T, 3 * F, F, EpiStore{gTn, F, 0}));
         else TRY(sgemm<false, false>(gshape_classes(N, F, gdX, Lr.mix2_w), EpiStore{gTn, F, 0}, gctas, st));
         if (wg) TRY(wgrad_outer(rows3(gdX, Tn), wpart, wcap, gw(Gr.mix2_w), 0, sms, st));
         k_T_bwd<<<ew, 256, 0, st>>>(Y, M, gTn, N, F, gY, gM);
@@ -1465,19 +1502,19 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         k_message_bwd<<<atom_blocks, F, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, gM, N, F, gY, gg, nbf);
         count_launch();
         pf.mark(P_MLP_ELEM_BWD);
-        k_mlp3_bwd<<<pair_grid, 256, 0, st>>>(gg, a3, phiu, nu, 3 * F, gphiu, ga3_bf);
+        k_mlp3_bwd<<<pair_grid, 256, 0, st>>>(gg, a3, phiu, nu, 3 * F, gphiu, ga3_cp);
         count_launch();
         TNET_LAUNCH_CHECK();
-        const EpiGradAct g3{a2, 2 * F, ga2, 2 * F, 0, ga2_bf, 2 * F};
-        const EpiGradAct g2{a1, F, ga1, F, 0, ga1_bf, F};
+        const EpiGradAct g3{a2, 2 * F, ga2, 2 * F, 0, ga2_cp, 2 * F};
+        const EpiGradAct g2{a1, F, ga1, F, 0, ga1_cp, F};
         const EpiStore g1{ge, K, l != NL - 1};
-        if (bf) {
+        if (tcm) {
             tc::TcShape t3 = tc::tshape(maxU, 2 * F, 3 * F), t2 = tc::tshape(maxU, F, 2 * F);
             t2.rows_dev = t3.rows_dev = nu;
             pf.mark(P_MLP3_BWD);
-            TRY(tc_any(t3, ga3_bf, maxU, 3 * F, lb[l].mlp3T, 2 * F, 3 * F, g3, status, st, bn2));
+            TRY(tcg(t3, gg, ga3_cp, maxU, 3 * F, lb[l].mlp3T, 2 * F, 3 * F, g3, bn2));
             pf.mark(P_MLP2_BWD);
-            TRY(tc_any(t2, ga2_bf, maxU, 2 * F, lb[l].mlp2T, F, 2 * F, g2, status, st));
+            TRY(tcg(t2, ga2, ga2_cp, maxU, 2 * F, lb[l].mlp2T, F, 2 * F, g2));
             pf.mark(P_MLP1_BWD);  // N = num_rbf: FP32 SIMT
             GemmShape q1 = gshape(maxU, K, F, ga1, F, Lr.mlp1_w, K);
             q1.rows_dev = nu;
@@ -1509,7 +1546,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             TRY(wgrad_outer(rows3(gY, Xn), wpart, wcap, gw(Gr.mix1_w), 0, sms, st));
         }
         pf.mark(P_NODE_BWD);
-        if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, lb[l].mix1T, 3 * F, F, EpiStore{gX, F, 1}, status, st));
+        if (tcm) TRY(tcg(tc::tshape_classes(N, F), gY, nbf, 9LL * N, F, lb[l].mix1T, 3 * F, F, EpiStore{gX, F, 1}));
         else TRY(sgemm<false, false>(gshape_classes(N, F, gY, Lr.mix1_w), EpiStore{gX, F, 1}, gctas, st));
         k_node_norm_bwd<<<ew, 256, 0, st>>>(Xl, qn, N, F, gX);
         count_launch();
@@ -1525,7 +1562,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     TRY(sgemm<false, false>(gshape(N, 2 * F, 3 * F, gas2, 3 * F, W.emb_mlp2_w, 2 * F),
                             EpiGradAct{as1, 2 * F, gas1, 2 * F, 0}, gctas, st));
     TRY(sgemm<false, false>(gshape(N, F, 2 * F, gas1, 2 * F, W.emb_mlp1_w, F), EpiStore{gn0, F, 0}, gctas, st));
-    if (bf) TRY(tc_any(tc::tshape_classes(N, F), nbf, 9LL * N, F, emixT_b16, 3 * F, F, EpiStore{gXraw, F, 0}, status, st));
+    if (tcm) TRY(tcg(tc::tshape_classes(N, F), gU, nbf, 9LL * N, F, emixT, 3 * F, F, EpiStore{gXraw, F, 0}));
     else TRY(sgemm<false, false>(gshape_classes(N, F, gU, W.emb_mix_w), EpiStore{gXraw, F, 0}, gctas, st));
     k_ln0_bwd<<<N, F, 0, st>>>(Xraw, gn0, ln0, W.emb_ln_g, N, F, gXraw);
     count_launch();
@@ -1550,10 +1587,10 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
 #define EMB_BWD(CPL)                                                                                         \
     if (wg)                                                                                                  \
         k_emb_bwd<CPL><<<bwd_blocks, 256, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, d.max_z, rp, \
-                                                   fu, Ta, Tb, gXraw, 1, gfu, edge_g, gA, gB, gfu_bf);        \
+                                                   fu, Ta, Tb, gXraw, 1, gfu, edge_g, gA, gB, gfu_cp);        \
     else                                                                                                     \
         k_emb_bwd_pairs<CPL><<<pair_grid, 256, 0, st>>>(pos, box, batch, z, uij, ue, rev, nu, N, d.max_z, rp, fu, \
-                                                      Ta, Tb, gXraw, gfu, edge_g, gfu_bf)
+                                                      Ta, Tb, gXraw, gfu, edge_g, gfu_cp)
     switch (F / 32) {
         case 2: EMB_BWD(2); break;
         case 4: EMB_BWD(4); break;

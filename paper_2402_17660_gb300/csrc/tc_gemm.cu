@@ -20,15 +20,16 @@ EncodeFn tensor_map_encoder() {
     return fn;
 }
 
-int make_map_bf16(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+static int make_map(CUtensorMap *m, CUtensorMapDataType dt, int esz, const void *base, int64_t rows, int64_t cols,
+                    int64_t ld, int box_rows) {
     EncodeFn enc = tensor_map_encoder();
     if (!enc) return TNET_ERR_CUDA;
     if (rows < 1 || cols < 1 || box_rows < 1 || box_rows > 256) return TNET_ERR_ARG;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};  // 128-byte rows
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+    CUresult r = enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -38,10 +39,39 @@ int make_map_bf16(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, 
     return TNET_OK;
 }
 
+int make_map_bf16(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+    return make_map(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, rows, cols, ld, box_rows);
+}
+int make_map_f32(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+    return make_map(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, rows, cols, ld, box_rows);
+}
+
 }  // namespace tc
 }  // namespace tnet
 
 using namespace tnet;
+
+// TF32X3 residuals of a float array (for the test entry point)
+__global__ void k_tf32_lo(const float *__restrict__ x, float *__restrict__ lo, int64_t n) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) lo[t] = tc::tf32_lo(x[t]);
+}
+
+extern "C" int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const float *B, float *Alo, float *Blo,
+                                      float *Cout, int32_t *status, tnet_stream_t stream) {
+    if (M < 1 || N < 4 || N > 512 || K < 4 || K % 4 || N % 4 || !A || !B || !Alo || !Blo || !Cout) return TNET_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_tf32_lo<<<(int)(((int64_t)M * K + 255) / 256), 256, 0, st>>>(A, Alo, (int64_t)M * K);
+    k_tf32_lo<<<(int)(((int64_t)N * K + 255) / 256), 256, 0, st>>>(B, Blo, (int64_t)N * K);
+    TNET_LAUNCH_CHECK();
+    tc::TcShape P = tc::tshape(M, N, K);
+    EpiStore epi{Cout, N, 0};
+    const tc::TcOperands o{A, B, Alo, Blo, M, K, N, K};
+    if (N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st);
+    if (N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st);
+    if (N % 192 == 0) return tc::tc_gemm_ops<192, true>(P, o, epi, status, st);
+    return tc::tc_gemm_ops<128, true>(P, o, epi, status, st);
+}
 
 extern "C" int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void *B, float *Cout, int32_t *status,
                                   tnet_stream_t stream) {

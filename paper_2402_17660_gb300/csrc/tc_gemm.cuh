@@ -1,10 +1,18 @@
-// BF16 tensor-core GEMM for sm_103a: TMA tile loads into 128B-swizzled
-// shared memory, tcgen05.mma issued by one thread with the FP32 accumulator
-// in tensor memory (TMEM), and a tcgen05.ld epilogue that applies the same
-// fused epilogue functors as the SIMT path.
+// Tensor-core GEMM for sm_103a: TMA tile loads into 128B-swizzled shared
+// memory, tcgen05.mma issued by one thread with the FP32 accumulator in
+// tensor memory (TMEM), and a tcgen05.ld epilogue that applies the same fused
+// epilogue functors as the SIMT path.
 //
-//   C[m][n] = epi( sum_k A[m][k] B[n][k] ),  A [rows][lda], B [rows][ldb] bf16,
+//   C[m][n] = epi( sum_k A[m][k] B[n][k] ),  A [rows][lda], B [rows][ldb},
 //   both K-major (row-major with K contiguous).
+//
+// Two operand modes:
+//   BF16   A, B bf16; one kind::f16 MMA per k-step.
+//   TF32X3 A, B fp32 plus their TF32 residuals A_lo = A - tf32(A),
+//          B_lo = B - tf32(B) (fp32 arrays); three kind::tf32 MMAs per k-step,
+//          A B + A_lo B + A B_lo, which keeps FP32-level accuracy (the tensor
+//          core reads an fp32 operand as TF32 by dropping its low 13 mantissa
+//          bits, so A itself serves as tf32(A)).
 //
 // Persistent CTAs walk 128 x BN output tiles.  Warp 0 issues TMA loads into a
 // 4-stage shared-memory ring, warp 1 owns TMEM and issues the MMAs (K = 16
@@ -24,7 +32,7 @@
 namespace tnet {
 namespace tc {
 
-constexpr int BM = 128, BK = 64, EPI_WARPS = 16, THREADS = 64 + 32 * EPI_WARPS;
+constexpr int BM = 128, EPI_WARPS = 16, THREADS = 64 + 32 * EPI_WARPS;
 constexpr int STG_LD = 20;  // floats per staged row (16 + pad, keeps float4 alignment)
 constexpr uint32_t kSpinLimit = 1u << 22;
 
@@ -123,19 +131,38 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: D f32, A and B bf16, both K-major, M x N.
+// Instruction descriptor: D f32, A and B bf16 (format 1) or tf32 (format 2),
+// both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// D (TMEM) (+)= A * B^T, kind::tf32 (fp32 containers read as TF32)
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+// TF32 residual of an fp32 value: x - (x with its low 13 mantissa bits cleared)
+__device__ __forceinline__ float tf32_lo(float x) { return tf32_residual(x); }
 
-template <int BN>
+template <int BN, bool X3 = false>
 struct TileCfg {
-    static constexpr int STAGES = BN >= 192 ? 3 : 4;
-    static constexpr uint32_t A_BYTES = BM * BK * 2;
-    static constexpr uint32_t B_BYTES = BN * BK * 2;
+    // one k-block is 128 bytes of K per row: 64 bf16 or 32 fp32 elements
+    static constexpr int BKE = X3 ? 32 : 64;
+    static constexpr uint32_t A_BYTES = BM * 128;
+    static constexpr uint32_t B_BYTES = BN * 128;
+    // bytes per pipeline stage: A, B (+ A_lo, B_lo for TF32X3)
+    static constexpr uint32_t STAGE_TX = (X3 ? 2 : 1) * (A_BYTES + B_BYTES);
+    static constexpr int STAGES = X3 ? 2 : (BN >= 192 ? 3 : 4);
     static constexpr uint32_t TMEM_COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
     static constexpr uint32_t STAGE_BYTES = EPI_WARPS * 32 * STG_LD * 4;  // epilogue transpose buffers
-    static constexpr size_t SMEM = 1024 + STAGES * (size_t)(A_BYTES + B_BYTES) + 256 + STAGE_BYTES;
+    static constexpr size_t SMEM = 1024 + STAGES * (size_t)STAGE_TX + 256 + STAGE_BYTES;
 };
 
 // Tile index -> (class, first row, first column); false past the last tile.
@@ -155,23 +182,28 @@ struct TileIter {
 };
 __device__ __forceinline__ int64_t sel3(int z, int64_t a, int64_t b, int64_t c) { return z == 0 ? a : (z == 1 ? b : c); }
 
-template <int BN, class Epi>
+template <int BN, class Epi, bool X3>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcShape P, Epi epi,
-              int32_t *status) {
-    using C = TileCfg<BN>;
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo, TcShape P,
+              Epi epi, int32_t *status) {
+    using C = TileCfg<BN, X3>;
     constexpr int STAGES = C::STAGES;
+    constexpr int BK = C::BKE;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // stage s: A at sA + s*A_BYTES, B at sB + s*B_BYTES; TF32X3 adds A_lo, B_lo
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * C::A_BYTES;
-    uint64_t *full = (uint64_t *)(sB + STAGES * C::B_BYTES);
+    uint8_t *sAlo = sB + STAGES * C::B_BYTES;
+    uint8_t *sBlo = sAlo + (X3 ? STAGES * C::A_BYTES : 0);
+    uint64_t *full = (uint64_t *)(sBlo + (X3 ? STAGES * C::B_BYTES : 0));
     uint64_t *empty = full + STAGES;
     uint64_t *acc_full = empty + STAGES;
     uint64_t *acc_empty = acc_full + 2;
     uint32_t *tmem_slot = (uint32_t *)(acc_empty + 2);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
-    float *stage_all = (float *)(sB + STAGES * C::B_BYTES + 256);
+    float *stage_all = (float *)((uint8_t *)full + 256);
 
     // rows per class (class 0 may be bounded by a device-side count)
     int M0 = P.M[0];
@@ -219,11 +251,15 @@ __global__ void __launch_bounds__(THREADS, 1)
                         *abort_flag = 1;
                         break;
                     }
-                    mbar_expect_tx(&full[s], C::A_BYTES + C::B_BYTES);
-                    tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * BK, (int)(sel3(z, P.row0[0], P.row0[1], P.row0[2]) + m0),
-                                &full[s]);
-                    tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * BK,
-                                (int)(sel3(z, P.brow0[0], P.brow0[1], P.brow0[2]) + n0), &full[s]);
+                    mbar_expect_tx(&full[s], C::STAGE_TX);
+                    const int ya = (int)(sel3(z, P.row0[0], P.row0[1], P.row0[2]) + m0);
+                    const int yb = (int)(sel3(z, P.brow0[0], P.brow0[1], P.brow0[2]) + n0);
+                    tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * BK, ya, &full[s]);
+                    tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * BK, yb, &full[s]);
+                    if (X3) {
+                        tma_load_2d(sAlo + s * C::A_BYTES, &tmAlo, kb * BK, ya, &full[s]);
+                        tma_load_2d(sBlo + s * C::B_BYTES, &tmBlo, kb * BK, yb, &full[s]);
+                    }
                 }
             }
             for (int k = kg > STAGES ? kg - STAGES : 0; k < kg; ++k)
@@ -231,7 +267,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
-            const uint32_t idesc = idesc_bf16(BM, BN);
+            const uint32_t idesc = X3 ? idesc_tf32(BM, BN) : idesc_bf16(BM, BN);
             int kg = 0, lt = 0;
             int z, m0, n0;
             for (int t = blockIdx.x; it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x, ++lt) {
@@ -252,10 +288,20 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     fence_after();
                     const uint32_t a0 = smem_u32(sA + s * C::A_BYTES), b0 = smem_u32(sB + s * C::B_BYTES);
+                    // four 32-byte k-steps per 128-byte k-block in both modes
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k)
-                        umma_bf16(d, sdesc_sw128(a0 + k * 32), sdesc_sw128(b0 + k * 32), idesc,
-                                  (kb > 0 || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t da = sdesc_sw128(a0 + k * 32), db = sdesc_sw128(b0 + k * 32);
+                        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                        if (X3) {
+                            const uint32_t al = smem_u32(sAlo + s * C::A_BYTES), bl = smem_u32(sBlo + s * C::B_BYTES);
+                            umma_tf32(d, da, db, idesc, acc);
+                            umma_tf32(d, sdesc_sw128(al + k * 32), db, idesc, 1u);
+                            umma_tf32(d, da, sdesc_sw128(bl + k * 32), idesc, 1u);
+                        } else {
+                            umma_bf16(d, da, db, idesc, acc);
+                        }
+                    }
                     umma_commit(&empty[s]);
                 }
                 if (!ok) {
@@ -329,27 +375,43 @@ using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, vo
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeFn tensor_map_encoder();  // resolved once through the runtime (tc_gemm.cu)
 
-// 2-D bf16 tensor map: `rows` rows of `cols` elements, row pitch `ld`
-// elements, box of `box_rows` x 64 elements, 128B swizzle, zero fill.
+// 2-D tensor maps (bf16 or fp32): `rows` rows of `cols` elements, row pitch
+// `ld` elements, box of `box_rows` x 128 bytes, 128B swizzle, zero fill.
 int make_map_bf16(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+int make_map_f32(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
 
-template <int BN, class Epi>
-int tc_gemm(const TcShape &P, const __nv_bfloat16 *A, int64_t a_rows, int64_t lda, const __nv_bfloat16 *B,
-            int64_t b_rows, int64_t ldb, const Epi &epi, int32_t *status, cudaStream_t st) {
-    using C = TileCfg<BN>;
+// Operands of one GEMM: A, B and (TF32X3 only) their residual arrays.
+struct TcOperands {
+    const void *A, *B, *Alo, *Blo;
+    int64_t a_rows, lda, b_rows, ldb;
+};
+
+template <int BN, bool X3, class Epi>
+int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *status, cudaStream_t st) {
+    using C = TileCfg<BN, X3>;
+    const int esz = X3 ? 4 : 2;
     int maxM = 0;
     for (int z = 0; z < P.nclass; ++z) maxM = P.M[z] > maxM ? P.M[z] : maxM;
     if (maxM <= 0 || P.N <= 0) return TNET_OK;
-    if (P.N % 4 || (lda * 2) % 16 || (ldb * 2) % 16 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
+    if (P.N % 4 || (o.lda * esz) % 16 || (o.ldb * esz) % 16 || ((uintptr_t)o.A & 15) || ((uintptr_t)o.B & 15))
         return TNET_ERR_ARG;
-    CUtensorMap ma, mb;
-    int rc = make_map_bf16(&ma, A, a_rows, P.K, lda, BM);
-    if (rc) return rc;
-    rc = make_map_bf16(&mb, B, b_rows, P.K, ldb, BN);
-    if (rc) return rc;
+    if (X3 && (!o.Alo || !o.Blo || ((uintptr_t)o.Alo & 15) || ((uintptr_t)o.Blo & 15))) return TNET_ERR_ARG;
+    CUtensorMap ma, mb, mal, mbl;
+    int rc;
+    if (X3) {
+        if ((rc = make_map_f32(&ma, o.A, o.a_rows, P.K, o.lda, BM))) return rc;
+        if ((rc = make_map_f32(&mb, o.B, o.b_rows, P.K, o.ldb, BN))) return rc;
+        if ((rc = make_map_f32(&mal, o.Alo, o.a_rows, P.K, o.lda, BM))) return rc;
+        if ((rc = make_map_f32(&mbl, o.Blo, o.b_rows, P.K, o.ldb, BN))) return rc;
+    } else {
+        if ((rc = make_map_bf16(&ma, o.A, o.a_rows, P.K, o.lda, BM))) return rc;
+        if ((rc = make_map_bf16(&mb, o.B, o.b_rows, P.K, o.ldb, BN))) return rc;
+        mal = ma;
+        mbl = mb;
+    }
     static bool attr_set = false;
     if (!attr_set) {
-        TNET_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<BN, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        TNET_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<BN, Epi, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)C::SMEM));
         attr_set = true;
     }
@@ -363,10 +425,16 @@ int tc_gemm(const TcShape &P, const __nv_bfloat16 *A, int64_t a_rows, int64_t ld
         if (sms <= 0) sms = 1;
     }
     const int grid = (int)(tiles < sms ? tiles : sms);
-    k_tc_gemm<BN, Epi><<<grid, THREADS, C::SMEM, st>>>(ma, mb, P, epi, status);
+    k_tc_gemm<BN, Epi, X3><<<grid, THREADS, C::SMEM, st>>>(ma, mb, mal, mbl, P, epi, status);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
+}
+
+template <int BN, class Epi>
+int tc_gemm(const TcShape &P, const __nv_bfloat16 *A, int64_t a_rows, int64_t lda, const __nv_bfloat16 *B,
+            int64_t b_rows, int64_t ldb, const Epi &epi, int32_t *status, cudaStream_t st) {
+    return tc_gemm_ops<BN, false>(P, TcOperands{A, B, nullptr, nullptr, a_rows, lda, b_rows, ldb}, epi, status, st);
 }
 
 inline TcShape tshape(int M, int N, int K) {

@@ -310,3 +310,44 @@ def test_autotuner_knobs_change_speed_not_results(tmp_path):
         # the cache is read back
         knobs2, _ = autotune(m, z, pos, nl, None, box, 1, cache=str(tmp_path / "t.json"))
         assert knobs2 == knobs
+
+
+
+# -------------------------------------------------------- 3xTF32 mode ---
+def _make_x3(sys, weights=W, shape=SHAPE):
+    from paper_2402_17660_gb300.tnet import TensorNet
+    m32 = make_model(weights, sys, shape=shape)
+    return TensorNet(weights, F=shape.F, K=shape.K, L=shape.L, max_z=shape.max_z, max_atoms=sys.n_atoms,
+                     max_systems=sys.n_systems, max_pairs=m32.max_pairs, precision=2, device=DEV)
+
+
+@pytest.mark.parametrize("name", ["molecule32", "water3000"])
+def test_tf32x3_mode_meets_fp32_tolerances(name):
+    s = synth.workload(name)
+    m = _make_x3(s)
+    E, F = gpu_energy_forces(m, s)
+    Es, Ei, Fo = oracle_energy_forces(W, s)
+    e_err = energy_errors(E, Es, Ei, s.batch).max()
+    f_err = force_error(F, Fo)
+    print(f"{name} 3xTF32: rel energy err {e_err:.2e}, rel RMS force err {f_err:.2e}")
+    assert e_err <= E_TOL and f_err <= F_TOL
+
+
+def test_tf32x3_mode_batch_and_weight_grads():
+    from oracle.tensornet import TensorNet as Oracle
+    from paper_2402_17660_gb300.tnet import unpack_weights
+    s = synth.molecule_batch(24, seed=6)
+    m = _make_x3(s)
+    z, pos, batch, box = to_dev(s)
+    nl = gpu_pairs(m, s)
+    m.reset_status()
+    E, Fg, G = m.energy_forces(z, pos, nl, batch, box, s.n_systems, grad_weights=True)
+    torch.cuda.synchronize()
+    m.check_status("3xtf32")
+    Es, Ei, Fo, Go = Oracle(W).energy_forces(s.z, s.pos, s.batch, None, n_systems=s.n_systems, want_weights=True)
+    assert np.all(energy_errors(E.cpu().numpy(), Es, Ei, s.batch) <= E_TOL)
+    assert force_error(Fg.cpu().numpy(), Fo) <= F_TOL
+    Gg = unpack_weights(G.cpu().numpy(), 128, 32, 2, 100)
+    for k in Go:
+        rms = np.sqrt(np.mean(Go[k] ** 2))
+        assert np.sqrt(np.mean((Gg[k] - Go[k]) ** 2)) <= F_TOL * max(rms, 1e-30), k

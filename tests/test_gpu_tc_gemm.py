@@ -37,3 +37,26 @@ def test_tc_gemm_matches_matmul(M, N, K):
     err, scale = _run(M, N, K)
     # exact BF16 products, FP32 accumulation over K terms
     assert err <= 1e-5 * scale * max(1.0, (K / 64) ** 0.5), (err, scale)
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 32), (1, 32, 32), (300, 128, 128), (777, 384, 256), (129, 64, 384),
+                                   (4096, 256, 128)])
+def test_tc_gemm_3xtf32_matches_fp64(M, N, K):
+    """3xTF32 (A B + A_lo B + A B_lo on the tensor cores) reaches FP32-level
+    accuracy on fp32 inputs."""
+    g = torch.Generator(device="cpu").manual_seed(1)
+    A = torch.randn(M, K, generator=g).cuda()
+    B = torch.randn(N, K, generator=g).cuda()
+    Alo, Blo = torch.empty_like(A), torch.empty_like(B)
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lib = _lib.load()
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    rc = lib.tnet_debug_tc_gemm_f32(M, N, K, p(A), p(B), p(Alo), p(Blo), p(C), p(st),
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = A.double() @ B.double().T
+    err = (C.double() - ref).abs().max().item()
+    assert err <= 2e-6 * (K ** 0.5) * ref.abs().max().item(), err
