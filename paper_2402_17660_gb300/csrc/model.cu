@@ -1275,13 +1275,19 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             w.blo = lo;
             return w;
         };
-        auto job_classes_T = [&](const float *src) {  // [3][F][F] -> per-class transposes
-            WOp first{};
+        // [3][F][F] -> per-class transposes; the three classes' high parts (and
+        // residuals) must stay stacked contiguously [3F][F] for the GEMM
+        auto job_classes_T = [&](const float *src) {
+            const int64_t ff = (int64_t)F * F;
+            char *hi = (char *)alloc(3 * ff), *lo = prec == 2 ? (char *)alloc(3 * ff) : nullptr;
             for (int q = 0; q < 3; ++q) {
-                WOp w = job(src + (int64_t)q * F * F, F, F, 1);
-                if (!q) first = w;
+                J.src[J.n] = src + q * ff;
+                J.hi[J.n] = hi + q * ff * esz;
+                J.lo[J.n] = lo ? lo + q * ff * esz : nullptr;
+                J.rows[J.n] = F; J.cols[J.n] = F; J.tr[J.n] = 1;
+                ++J.n;
             }
-            return first;
+            return WOp{hi, lo};
         };
         emix = job(W.emb_mix_w, 3 * F, F, 0);
         emixT = job_classes_T(W.emb_mix_w);
