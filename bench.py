@@ -47,6 +47,9 @@ def parse():
                     help="fp32: SIMT FP32 GEMMs; tf32x3: FP32-accurate 3xTF32 tensor-core GEMMs; "
                          "bf16: BF16 tensor-core GEMMs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", default="auto",
+                    help="auto: autotune launch shapes on this input (cached); default: the library's "
+                         "defaults; or a comma-separated knob list")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--md", type=int, default=0,
                     help="also time this many velocity-Verlet steps (0.5 fs, 1 A skin, rebuild every 20)")
@@ -307,7 +310,12 @@ def run_ours(args):
 
     # launch shapes from the autotuner (timed on this input, cached as JSON)
     from paper_2402_17660_gb300.tnet import autotune
-    knobs, tune_ms = autotune(m, z, pos, nl, batch, box, S)
+    if args.tuning == "auto":
+        knobs, tune_ms = autotune(m, z, pos, nl, batch, box, S)
+    else:
+        if args.tuning != "default":
+            m.set_tuning([int(v) for v in args.tuning.split(",")])
+        knobs, tune_ms = m.get_tuning(), {}
 
     def step():
         m.neighbors(pos, batch, box, S, out=nl)

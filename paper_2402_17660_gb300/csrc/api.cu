@@ -129,6 +129,7 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->zpart = take(f * 2 * L->zsplits * Z * F);
     L->wpart_floats = 4LL << 20;
     L->wpart = take(f * L->wpart_floats);
+    L->w3p = take(f * (NL > 0 ? NL : 1) * (6LL * F * F + 3 * F));
     // tensor-core modes: weight operands (bf16 forward + transposed copies, or
     // fp32 residuals + transposed high parts), one node-tensor operand copy and
     // the per-pair radial-MLP operand copies (bf16 or fp32 TF32 residuals)

@@ -111,16 +111,23 @@ __global__ void k_ln_grad(const float *__restrict__ gy, const float *__restrict_
     partial[(int64_t)s * 2 * C + C + c] = ab;
 }
 
-// out[z][i] = sum_s partial[z][s][i]  (fixed order; + out when accumulate)
+// out[z][i] = sum_s partial[z][s][i]  (fixed order; + out when accumulate).
+// With perm_f > 0 the rows m of each [3 perm_f][ncols] class come in
+// plane-major order (m = p perm_f + c) and are written to row c*3 + p.
 __global__ void k_split_reduce(const float *__restrict__ partial, int splits, int64_t per_class, int nclass,
-                               float *__restrict__ out, int accumulate) {
+                               float *__restrict__ out, int accumulate, int ncols, int perm_f) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= per_class * nclass) return;
     const int64_t z = t / per_class, i = t % per_class;
-    float acc = accumulate ? out[t] : 0.f;
+    int64_t o = t;
+    if (perm_f > 0) {
+        const int64_t m = i / ncols, n = i % ncols;
+        o = z * per_class + ((m % perm_f) * 3 + m / perm_f) * ncols + n;
+    }
+    float acc = accumulate ? out[o] : 0.f;
     const float *p = partial + z * splits * per_class + i;
     for (int s = 0; s < splits; ++s) acc += p[(int64_t)s * per_class];
-    out[t] = acc;
+    out[o] = acc;
 }
 
 static int choose_splits(int64_t rows_cap, int64_t tiles, int nclass, int64_t per_split_floats,
@@ -139,7 +146,7 @@ static int choose_splits(int64_t rows_cap, int64_t tiles, int nclass, int64_t pe
 }
 
 int wgrad_outer(const WgradShape &P, float *partial, int64_t partial_cap, float *out, int accumulate, int sms,
-                cudaStream_t st) {
+                cudaStream_t st, int perm_f) {
     int64_t rows_cap = 0;
     for (int z = 0; z < P.nclass; ++z) rows_cap = P.rows[z] > rows_cap ? P.rows[z] : rows_cap;
     if (rows_cap <= 0 || P.M <= 0 || P.N <= 0) return TNET_OK;
@@ -153,14 +160,14 @@ int wgrad_outer(const WgradShape &P, float *partial, int64_t partial_cap, float 
     count_launch();
     const int64_t tot = (int64_t)P.nclass * P.M * P.N;
     k_split_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(partial, splits, (int64_t)P.M * P.N, P.nclass,
-                                                                  out, accumulate);
+                                                                  out, accumulate, P.N, perm_f);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
 }
 
 int wgrad_colsum(const WgradShape &P, const float *roww, float *partial, int64_t partial_cap, float *out,
-                 int accumulate, int sms, cudaStream_t st) {
+                 int accumulate, int sms, cudaStream_t st, int perm_f) {
     int64_t rows_cap = 0;
     for (int z = 0; z < P.nclass; ++z) rows_cap = P.rows[z] > rows_cap ? P.rows[z] : rows_cap;
     if (rows_cap <= 0 || P.M <= 0) return TNET_OK;
@@ -171,7 +178,8 @@ int wgrad_colsum(const WgradShape &P, const float *roww, float *partial, int64_t
     k_colsum<<<g, 256, 0, st>>>(P, splits, chunk, roww, partial);
     count_launch();
     const int64_t tot = (int64_t)P.nclass * P.M;
-    k_split_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(partial, splits, P.M, P.nclass, out, accumulate);
+    k_split_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(partial, splits, P.M, P.nclass, out, accumulate,
+                                                                  1, perm_f);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
@@ -188,7 +196,7 @@ int wgrad_layernorm(const float *gy, const float *x, const float2 *stats, int R,
     dim3 g((unsigned)tiles, splits, 1);
     k_ln_grad<<<g, 256, 0, st>>>(gy, x, stats, R, C, splits, chunk, partial);
     count_launch();
-    k_split_reduce<<<(unsigned)((2 * C + 255) / 256), 256, 0, st>>>(partial, splits, 2LL * C, 1, out_g, 0);
+    k_split_reduce<<<(unsigned)((2 * C + 255) / 256), 256, 0, st>>>(partial, splits, 2LL * C, 1, out_g, 0, 1, 0);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;

@@ -53,6 +53,21 @@ struct SysInfo {
 // S rows [4N,9N) (row 4N+5n+k).  A class-p mixing is one GEMM over a
 // contiguous block of rows.
 // ---------------------------------------------------------------------------
+// Runs CALL(F) with F as a compile-time constant (the channel counts the
+// library accepts: multiples of 64 up to 512); returns TNET_ERR_ARG otherwise.
+#define TNET_F_SWITCH(Fv, CALL)                 \
+    switch (Fv) {                              \
+        case 64: CALL(64); break;              \
+        case 128: CALL(128); break;            \
+        case 192: CALL(192); break;            \
+        case 256: CALL(256); break;            \
+        case 320: CALL(320); break;            \
+        case 384: CALL(384); break;            \
+        case 448: CALL(448); break;            \
+        case 512: CALL(512); break;            \
+        default: return TNET_ERR_ARG;          \
+    }
+
 __device__ __forceinline__ int64_t crow(int n, int k, int N) {
     return k == 0 ? (int64_t)n : (k < 4 ? (int64_t)N + 3LL * n + (k - 1) : 4LL * N + 5LL * n + (k - 4));
 }
@@ -268,6 +283,9 @@ struct Layout {
     // tensor-core modes: operand copies for the GEMMs
     size_t wbf, nbf, eu_bf, h1_bf, h2_bf, ga3_bf, ga2_bf, ga1_bf, gfu_bf;
     int64_t wbf_bytes;
+    // per layer: the last radial-MLP layer's weight [3F][2F] and bias [3F]
+    // with rows in plane-major order p*F + c (the blob keeps c*3 + p)
+    size_t w3p;
     int64_t wpart_floats, zsplits;
     // MD
     size_t md_row_ptr, md_col, md_npairs, md_forces, md_energy, md_pos_ref, md_step;
@@ -345,12 +363,13 @@ struct WgradShape {
     int64_t ldb;
     int nclass;
 };
-// out[z][m][n] (+)= sum_rows A[r][m] B[r][n]
+// out[z][m][n] (+)= sum_rows A[r][m] B[r][n].  perm_f > 0: A's M = 3 perm_f
+// columns are plane-major (m = p perm_f + c); out row c*3 + p receives row m.
 int wgrad_outer(const WgradShape &P, float *partial, int64_t partial_cap, float *out, int accumulate, int sms,
-                cudaStream_t st);
-// out[z][m] (+)= sum_rows A[r][m] * roww[r] (roww may be NULL)
+                cudaStream_t st, int perm_f = 0);
+// out[z][m] (+)= sum_rows A[r][m] * roww[r] (roww may be NULL); perm_f as above
 int wgrad_colsum(const WgradShape &P, const float *roww, float *partial, int64_t partial_cap, float *out,
-                 int accumulate, int sms, cudaStream_t st);
+                 int accumulate, int sms, cudaStream_t st, int perm_f = 0);
 int wgrad_layernorm(const float *gy, const float *x, const float2 *stats, int R, int C, float *partial,
                     int64_t partial_cap, float *out_g, int sms, cudaStream_t st);
 

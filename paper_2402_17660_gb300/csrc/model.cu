@@ -104,9 +104,10 @@ __global__ void k_rev(const int32_t *__restrict__ row_ptr, const int32_t *__rest
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (i >= N) return;
     const int lane = threadIdx.x & 31;
-    for (int e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
+    const int e0 = row_ptr[i];
+    for (int e = e0 + lane; e < row_ptr[i + 1]; e += 32) {
         const int j = col[e];
-        if (j < 0 || j >= N) {
+        if (j < 0 || j >= N || (e > e0 && col[e - 1] >= j)) {  // rows must ascend strictly
             set_status(status, TNET_ERR_ARG);
             rev[e] = e;
             continue;
@@ -193,7 +194,9 @@ __global__ void k_lower_assign(const int32_t *__restrict__ row_ptr, const int32_
     const int lane = threadIdx.x & 31;
     for (int e = row_ptr[i] + lane; e < row_ptr[i + 1]; e += 32) {
         const int j = col[e];
-        if (j <= i) pair_of[e] = (j == i) ? -1 : pair_of[rev[e]];
+        // rev[e] == e marks a column that is out of range or has no reverse
+        // edge (status ARG is set): the edge stays inactive
+        if (j <= i) pair_of[e] = (j == i || rev[e] == e) ? -1 : pair_of[rev[e]];
     }
 }
 
@@ -376,40 +379,51 @@ __global__ void k_node_norm(const float *__restrict__ X, int N, int F, float *__
     }
 }
 
-// M_i = sum_j g^p_ij Y^p_j over the row (block = F threads, one atom per block).
-// Loads for kMU edges are issued before any of them is used (memory-level
-// parallelism); the sums still run in row order.
-__global__ void k_message(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                          const int32_t *__restrict__ pair_of, const float *__restrict__ gU,
-                          const float *__restrict__ Y, int N, int F, float *__restrict__ M) {
+// M_i = sum_j g^p_ij Y^p_j over the row (block = F threads, thread = channel).
+// g of pair u is stored plane-major, g[u][p][c], so each of its three loads is
+// one coalesced F-channel row.  The row's pair and column indices are staged in
+// shared memory (one coalesced load per chunk of F edges), so each group of
+// kMU edges waits for one round of gathers, not for its indices first; the
+// sums still run in row order.  F is a template parameter so the coordinate
+// offsets are immediates.
+template <int F>
+__global__ void __launch_bounds__(F) k_message(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                               const int32_t *__restrict__ pair_of, const float *__restrict__ gU,
+                                               const float *__restrict__ Y, int N, float *__restrict__ M) {
+    __shared__ int32_t s_u[F], s_j[F];
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         float m[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int e1 = row_ptr[i + 1];
-        for (int eb = row_ptr[i]; eb < e1; eb += kMU) {
-            int uu[kMU], jj[kMU];
+        const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
+        for (int cb = e0; cb < e1; cb += F) {
+            const int n = e1 - cb < F ? e1 - cb : F;
+            __syncthreads();  // the previous chunk is consumed
+            if (c < n) { s_u[c] = pair_of[cb + c]; s_j[c] = col[cb + c]; }
+            __syncthreads();
+            for (int k0 = 0; k0 < n; k0 += kMU) {
+                int uu[kMU], jj[kMU];
 #pragma unroll
-            for (int k = 0; k < kMU; ++k) {
-                const int e = eb + k;
-                uu[k] = e < e1 ? pair_of[e] : -1;
-                jj[k] = e < e1 ? col[e] : 0;
-            }
-            float g[kMU][3], y[kMU][9];
+                for (int k = 0; k < kMU; ++k) {
+                    uu[k] = k0 + k < n ? s_u[k0 + k] : -1;
+                    jj[k] = k0 + k < n ? s_j[k0 + k] : 0;
+                }
+                float g[kMU][3], y[kMU][9];
 #pragma unroll
-            for (int k = 0; k < kMU; ++k) {
-                if (uu[k] < 0) continue;
-                const float *gp = gU + (int64_t)uu[k] * 3 * F + 3 * c;
-                g[k][0] = gp[0]; g[k][1] = gp[1]; g[k][2] = gp[2];
-                load_coords(Y, jj[k], c, N, F, y[k]);
-            }
+                for (int k = 0; k < kMU; ++k) {
+                    if (uu[k] < 0) continue;
+                    const float *gp = gU + (int64_t)uu[k] * 3 * F + c;
+                    g[k][0] = gp[0]; g[k][1] = gp[F]; g[k][2] = gp[2 * F];
+                    load_coords(Y, jj[k], c, N, F, y[k]);
+                }
 #pragma unroll
-            for (int k = 0; k < kMU; ++k) {
-                if (uu[k] < 0) continue;
-                m[0] = fmaf(g[k][0], y[k][0], m[0]);
+                for (int k = 0; k < kMU; ++k) {
+                    if (uu[k] < 0) continue;
+                    m[0] = fmaf(g[k][0], y[k][0], m[0]);
 #pragma unroll
-                for (int q = 1; q < 4; ++q) m[q] = fmaf(g[k][1], y[k][q], m[q]);
+                    for (int q = 1; q < 4; ++q) m[q] = fmaf(g[k][1], y[k][q], m[q]);
 #pragma unroll
-                for (int q = 4; q < 9; ++q) m[q] = fmaf(g[k][2], y[k][q], m[q]);
+                    for (int q = 4; q < 9; ++q) m[q] = fmaf(g[k][2], y[k][q], m[q]);
+                }
             }
         }
         store_coords(M, i, c, N, F, m);
@@ -629,54 +643,95 @@ __global__ void k_T_bwd(const float *__restrict__ Y, const float *__restrict__ M
 // Message adjoint.  For atom i (block, thread per channel):
 //   gY_i += sum_j g^p_ij gM_j                       (g_ij = g_ji)
 //   gg[u(i,j)] = <gM_i, Y^p_j> + <gM_j, Y^p_i>       for upper edges j > i
-// Each undirected entry is written once, by its upper edge: no atomics.
-// Loads for kMU edges are in flight together; sums run in row order.
-__global__ void k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                              const int32_t *__restrict__ pair_of, const float *__restrict__ gU,
-                              const float *__restrict__ Y, const float *__restrict__ gM, int N, int F,
-                              float *__restrict__ gY, float *__restrict__ gg, OpCopy gY_cp) {
+// Each undirected entry is written once, by its upper edge: no atomics.  Rows
+// ascend, so the upper edges are the row's suffix: the lower part gathers
+// gM_j alone (kMU edges in flight), the upper part gM_j and Y_j together
+// (kMUU edges).  Indices are staged in shared memory as in k_message; the gY
+// sums run in row order.
+constexpr int kMUU = 2;
+template <int F>
+__global__ void __launch_bounds__(F, 512 / F)
+    k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                  const int32_t *__restrict__ pair_of, const float *__restrict__ gU, const float *__restrict__ Y,
+                  const float *__restrict__ gM, int N, float *__restrict__ gY, float *__restrict__ gg,
+                  OpCopy gY_cp) {
+    __shared__ int32_t s_u[F], s_j[F];
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         float yi[9], gmi[9], acc[9];
         load_coords(Y, i, c, N, F, yi);
         load_coords(gM, i, c, N, F, gmi);
         load_coords(gY, i, c, N, F, acc);
-        const int e1 = row_ptr[i + 1];
-        for (int eb = row_ptr[i]; eb < e1; eb += kMU) {
-            int uu[kMU], jj[kMU];
+        const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
+        int eu = e0, hi = e1;  // eu = first edge with col > i
+        while (eu < hi) {
+            const int mid = (eu + hi) >> 1;
+            if (col[mid] <= i) eu = mid + 1;
+            else hi = mid;
+        }
+        for (int cb = e0; cb < e1; cb += F) {
+            const int n = e1 - cb < F ? e1 - cb : F;
+            __syncthreads();
+            if (c < n) { s_u[c] = pair_of[cb + c]; s_j[c] = col[cb + c]; }
+            __syncthreads();
+            const int nl = eu - cb < 0 ? 0 : (eu - cb < n ? eu - cb : n);  // lower edges of the chunk
+            for (int k0 = 0; k0 < nl; k0 += kMU) {
+                int uu[kMU], jj[kMU];
 #pragma unroll
-            for (int k = 0; k < kMU; ++k) {
-                const int e = eb + k;
-                uu[k] = e < e1 ? pair_of[e] : -1;
-                jj[k] = e < e1 ? col[e] : 0;
+                for (int k = 0; k < kMU; ++k) {
+                    uu[k] = k0 + k < nl ? s_u[k0 + k] : -1;
+                    jj[k] = k0 + k < nl ? s_j[k0 + k] : 0;
+                }
+                float g[kMU][3], gmj[kMU][9];
+#pragma unroll
+                for (int k = 0; k < kMU; ++k) {
+                    if (uu[k] < 0) continue;
+                    const float *gp = gU + (int64_t)uu[k] * 3 * F + c;
+                    g[k][0] = gp[0]; g[k][1] = gp[F]; g[k][2] = gp[2 * F];
+                    load_coords(gM, jj[k], c, N, F, gmj[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < kMU; ++k) {
+                    if (uu[k] < 0) continue;
+                    acc[0] = fmaf(g[k][0], gmj[k][0], acc[0]);
+#pragma unroll
+                    for (int q = 1; q < 4; ++q) acc[q] = fmaf(g[k][1], gmj[k][q], acc[q]);
+#pragma unroll
+                    for (int q = 4; q < 9; ++q) acc[q] = fmaf(g[k][2], gmj[k][q], acc[q]);
+                }
             }
-            float g[kMU][3], gmj[kMU][9];
+            for (int k0 = nl; k0 < n; k0 += kMUU) {
+                int uu[kMUU], jj[kMUU];
 #pragma unroll
-            for (int k = 0; k < kMU; ++k) {
-                if (uu[k] < 0) continue;
-                const float *gp = gU + (int64_t)uu[k] * 3 * F + 3 * c;
-                g[k][0] = gp[0]; g[k][1] = gp[1]; g[k][2] = gp[2];
-                load_coords(gM, jj[k], c, N, F, gmj[k]);
-            }
+                for (int k = 0; k < kMUU; ++k) {
+                    uu[k] = k0 + k < n ? s_u[k0 + k] : -1;
+                    jj[k] = k0 + k < n ? s_j[k0 + k] : 0;
+                }
+                float g[kMUU][3], gmj[kMUU][9], yj[kMUU][9];
 #pragma unroll
-            for (int k = 0; k < kMU; ++k) {
-                if (uu[k] < 0) continue;
-                acc[0] = fmaf(g[k][0], gmj[k][0], acc[0]);
+                for (int k = 0; k < kMUU; ++k) {
+                    if (uu[k] < 0) continue;
+                    const float *gp = gU + (int64_t)uu[k] * 3 * F + c;
+                    g[k][0] = gp[0]; g[k][1] = gp[F]; g[k][2] = gp[2 * F];
+                    load_coords(gM, jj[k], c, N, F, gmj[k]);
+                    load_coords(Y, jj[k], c, N, F, yj[k]);
+                }
 #pragma unroll
-                for (int q = 1; q < 4; ++q) acc[q] = fmaf(g[k][1], gmj[k][q], acc[q]);
+                for (int k = 0; k < kMUU; ++k) {
+                    if (uu[k] < 0) continue;
+                    acc[0] = fmaf(g[k][0], gmj[k][0], acc[0]);
 #pragma unroll
-                for (int q = 4; q < 9; ++q) acc[q] = fmaf(g[k][2], gmj[k][q], acc[q]);
-                if (jj[k] > i) {
-                    float yj[9];
-                    load_coords(Y, jj[k], c, N, F, yj);
-                    float sI = gmi[0] * yj[0] + gmj[k][0] * yi[0];
+                    for (int q = 1; q < 4; ++q) acc[q] = fmaf(g[k][1], gmj[k][q], acc[q]);
+#pragma unroll
+                    for (int q = 4; q < 9; ++q) acc[q] = fmaf(g[k][2], gmj[k][q], acc[q]);
+                    float sI = gmi[0] * yj[k][0] + gmj[k][0] * yi[0];
                     float sA = 0.f, sS = 0.f;
 #pragma unroll
-                    for (int q = 1; q < 4; ++q) sA += gmi[q] * yj[q] + gmj[k][q] * yi[q];
+                    for (int q = 1; q < 4; ++q) sA += gmi[q] * yj[k][q] + gmj[k][q] * yi[q];
 #pragma unroll
-                    for (int q = 4; q < 9; ++q) sS += gmi[q] * yj[q] + gmj[k][q] * yi[q];
-                    float *o = gg + (int64_t)uu[k] * 3 * F + 3 * c;
-                    o[0] = sI; o[1] = sA; o[2] = sS;
+                    for (int q = 4; q < 9; ++q) sS += gmi[q] * yj[k][q] + gmj[k][q] * yi[q];
+                    float *o = gg + (int64_t)uu[k] * 3 * F + c;
+                    o[0] = sI; o[F] = sA; o[2 * F] = sS;
                 }
             }
         }
@@ -1112,6 +1167,29 @@ __global__ void k_seed_atoms(const float *__restrict__ seed, const int32_t *__re
     if (i < N) gEi[i] = seed ? seed[batch ? batch[i] : 0] : 1.0f;
 }
 
+// Plane-major copy of each layer's last radial-MLP layer: row p*F + c of the
+// copy is row c*3 + p of the blob (weight [3F][2F], then bias [3F]), so the
+// per-pair filters g_ij and their adjoints are three contiguous F-channel
+// planes I, A, S and the message kernels read and write them coalesced.
+struct FilterRows {
+    const float *w[8], *b[8];
+};
+__global__ void k_filter_rows(const __grid_constant__ FilterRows R, int F, float *__restrict__ out) {
+    const int l = blockIdx.y;
+    const int64_t nw = 6LL * F * F, per = nw + 3 * F;
+    const int cols = 2 * F;
+    float *o = out + l * per;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per; t += (int64_t)gridDim.x * blockDim.x) {
+        if (t < nw) {
+            const int r = (int)(t / cols), k = (int)(t % cols);
+            o[t] = R.w[l][(int64_t)((r % F) * 3 + r / F) * cols + k];
+        } else {
+            const int r = (int)(t - nw);
+            o[t] = R.b[l][(r % F) * 3 + r / F];
+        }
+    }
+}
+
 // Weight operands of the tensor-core modes: job j reads a [rows][cols] float
 // matrix (transposed when tr[j], for backward operands) and writes a bf16
 // copy (mode 1) or an fp32 high part (if hi[j]) and TF32 residual (mode 2).
@@ -1249,6 +1327,16 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     // ---- graph prep
     ProfSeq pf(ctx, st);
     pf.mark(P_PREP);
+    const int64_t w3_per = 6LL * F * F + 3 * F;
+    auto w3p = [&](int l) { return f32(Lw.w3p) + l * w3_per; };  // plane-major mlp3 weight
+    auto b3p = [&](int l) { return f32(Lw.w3p) + l * w3_per + 6LL * F * F; };
+    if (NL > 0) {
+        FilterRows FR{};
+        for (int l = 0; l < NL; ++l) { FR.w[l] = W.layer[l].mlp3_w; FR.b[l] = W.layer[l].mlp3_b; }
+        k_filter_rows<<<dim3(48, NL), 256, 0, st>>>(FR, F, f32(Lw.w3p));
+        count_launch();
+        TNET_LAUNCH_CHECK();
+    }
     if (tcm) {
         CvtJobs J;
         J.n = 0;
@@ -1294,9 +1382,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         for (int l = 0; l < NL; ++l) {
             const LayerW &Lr = W.layer[l];
             lb[l].mlp2 = job(Lr.mlp2_w, 2 * F, F, 0);
-            lb[l].mlp3 = job(Lr.mlp3_w, 3 * F, 2 * F, 0);
+            lb[l].mlp3 = job(w3p(l), 3 * F, 2 * F, 0);
             lb[l].mlp2T = job(Lr.mlp2_w, 2 * F, F, 1);
-            lb[l].mlp3T = job(Lr.mlp3_w, 3 * F, 2 * F, 1);
+            lb[l].mlp3T = job(w3p(l), 3 * F, 2 * F, 1);
             lb[l].mix1 = job(Lr.mix1_w, 3 * F, F, 0);
             lb[l].mix1T = job_classes_T(Lr.mix1_w);
             lb[l].mix2 = job(Lr.mix2_w, 3 * F, F, 0);
@@ -1380,7 +1468,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         const LayerW &Lr = W.layer[l];
         const EpiBiasAct e1{Lr.mlp1_b, a1, F, keep_h ? h1 : nullptr, F, 1, nullptr, h1_cp, F};
         const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, keep_h ? h2 : nullptr, 2 * F, 1, nullptr, h2_cp, 2 * F};
-        const EpiBiasAct e3{Lr.mlp3_b, a3, 3 * F, gbuf, 3 * F, 1, phiu};
+        const EpiBiasAct e3{b3p(l), a3, 3 * F, gbuf, 3 * F, 1, phiu};
         if (tcm) {
             tc::TcShape t2 = tc::tshape(maxU, 2 * F, F), t3 = tc::tshape(maxU, 3 * F, 2 * F);
             t2.rows_dev = t3.rows_dev = nu;
@@ -1403,7 +1491,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         p2.rows_dev = nu;
         TRY(sgemm<false, true>(p2, e2, gctas, st));
         pf.mark(P_MLP3);
-        GemmShape p3 = gshape(maxU, 3 * F, 2 * F, h2, 2 * F, Lr.mlp3_w, 2 * F);
+        GemmShape p3 = gshape(maxU, 3 * F, 2 * F, h2, 2 * F, w3p(l), 2 * F);
         p3.rows_dev = nu;
         TRY(sgemm<false, true>(p3, e3, gctas, st));
         return TNET_OK;
@@ -1423,7 +1511,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         else TRY(sgemm<false, true>(gshape_classes(N, F, Xn, W.layer[l].mix1_w), EpiStore{Y, F, 0}, gctas, st));
         TRY(edge_mlp(l));
         pf.mark(P_MESSAGE);
-        k_message<<<atom_blocks, F, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, N, F, M);
+#define MSG_FWD(FF) k_message<FF><<<atom_blocks, FF, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, N, M)
+        TNET_F_SWITCH(F, MSG_FWD);
+#undef MSG_FWD
         count_launch();
         pf.mark(P_NODE_ELEM);
         k_node_update<<<ew, 256, 0, st>>>(Y, M, N, F, Tn, nbf);
@@ -1505,7 +1595,10 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         TNET_LAUNCH_CHECK();
         TRY(edge_mlp(l));  // recompute a1, h1, a2, h2, a3, g of this layer
         pf.mark(P_MSG_BWD);
-        k_message_bwd<<<atom_blocks, F, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, gM, N, F, gY, gg, nbf);
+#define MSG_BWD(FF) \
+    k_message_bwd<FF><<<atom_blocks, FF, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, gM, N, gY, gg, nbf)
+        TNET_F_SWITCH(F, MSG_BWD);
+#undef MSG_BWD
         count_launch();
         pf.mark(P_MLP_ELEM_BWD);
         k_mlp3_bwd<<<pair_grid, 256, 0, st>>>(gg, a3, phiu, nu, 3 * F, gphiu, ga3_cp);
@@ -1527,7 +1620,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             TRY(sgemm<false, false>(q1, g1, gctas, st));
         } else {
             pf.mark(P_MLP3_BWD);
-            GemmShape q3 = gshape(maxU, 2 * F, 3 * F, gg, 3 * F, Lr.mlp3_w, 2 * F);
+            GemmShape q3 = gshape(maxU, 2 * F, 3 * F, gg, 3 * F, w3p(l), 2 * F);
             q3.rows_dev = nu;
             TRY(sgemm<false, false>(q3, g3, gctas, st));
             pf.mark(P_MLP2_BWD);
@@ -1540,9 +1633,11 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             TRY(sgemm<false, false>(q1, g1, gctas, st));
         }
         if (wg) {
-            TRY(wgrad_outer(rows1(3 * F, 2 * F, maxU, gg, 3 * F, h2, 2 * F, nu), wpart, wcap, gw(Gr.mlp3_w), 0, sms, st));
+            // gg is plane-major: map its rows back to the blob's c*3 + p order
+            TRY(wgrad_outer(rows1(3 * F, 2 * F, maxU, gg, 3 * F, h2, 2 * F, nu), wpart, wcap, gw(Gr.mlp3_w), 0, sms, st,
+                            F));
             TRY(wgrad_colsum(rows1(3 * F, 1, maxU, gg, 3 * F, nullptr, 0, nu), nullptr, wpart, wcap, gw(Gr.mlp3_b), 0,
-                             sms, st));
+                             sms, st, F));
             TRY(wgrad_outer(rows1(2 * F, F, maxU, ga2, 2 * F, h1, F, nu), wpart, wcap, gw(Gr.mlp2_w), 0, sms, st));
             TRY(wgrad_colsum(rows1(2 * F, 1, maxU, ga2, 2 * F, nullptr, 0, nu), nullptr, wpart, wcap, gw(Gr.mlp2_b), 0,
                              sms, st));

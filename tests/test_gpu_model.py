@@ -8,7 +8,7 @@ import torch
 
 from oracle.neighbors import neighbor_pairs
 from paper_2402_17660_gb300 import synth
-from paper_2402_17660_gb300.tnet import EnergyFn
+from paper_2402_17660_gb300.tnet import EnergyFn, NeighborList
 
 from .gpu_helpers import (DEV, E_TOL, F_TOL, RC, energy_errors, force_error, gpu_energy_forces, gpu_pairs,
                           make_model, margin_ok, oracle_energy_forces, to_dev)
@@ -112,6 +112,25 @@ def test_bad_atomic_number_flagged():
     m.energy_forces(z, pos, nl)
     torch.cuda.synchronize()
     assert int(m.status.item()) == 8
+
+
+def test_unsorted_row_rejected():
+    """Rows must ascend strictly (the reverse-edge search and the upper-edge
+    split rely on it); a swapped pair of columns is reported as ARG."""
+    s = _cluster(16)
+    m = make_model(W, s)
+    z, pos, batch, box = to_dev(s)
+    nl = gpu_pairs(m, s)
+    rp, col = nl.row_ptr.cpu().numpy(), nl.col.cpu().numpy().copy()
+    i = int(np.argmax(np.diff(rp)))
+    assert rp[i + 1] - rp[i] >= 2
+    a = rp[i]
+    col[a], col[a + 1] = col[a + 1], col[a]
+    bad = NeighborList(nl.row_ptr, torch.from_numpy(col).to(DEV), nl.n_pairs, nl.cutoff)
+    m.reset_status()
+    m.energy_forces(z, pos, bad)
+    torch.cuda.synchronize()
+    assert int(m.status.item()) == 1
 
 
 def test_autograd_function_positions():
