@@ -245,10 +245,14 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours ---
-def stage_work(tag, nu, N, E, F, K, bf16):
+def stage_work(tag, nu, N, E, F, K, prec):
     """Algorithmic work of one instance of a timed stage: (FLOP, bytes, engine).
-    Bytes count each operand read once and each result written once."""
+    Bytes count each operand read once and each result written once,
+    including the operand copies the tensor-core modes write beside a result
+    (bf16: 2 B per element; 3xTF32: a 4 B residual)."""
     f = 4.0
+    bf16 = prec == "bf16"
+    cp = {"fp32": 0.0, "bf16": 2.0, "tf32x3": 4.0}[prec]   # operand-copy bytes per element
     hb = 2.0 if bf16 else 4.0            # bytes per element of a GEMM input operand
     if tag == "mlp1":
         return 2.0 * nu * K * F, nu * (K * f + F * f + F * hb), "alu"
@@ -264,15 +268,17 @@ def stage_work(tag, nu, N, E, F, K, bf16):
     if tag == "mlp1_bwd":
         return 2.0 * nu * F * K, nu * (F * f + 2 * K * f), "alu"
     if tag == "emb_edges":   # read the pair projections once, write X_raw once
-        return 2.0 * 12 * F * 2 * nu, f * (3 * F * nu + 9 * N * F) + (2.0 * 9 * N * F if bf16 else 0), "hbm"
+        return 2.0 * 12 * F * 2 * nu, f * (3 * F * nu + 9 * N * F) + cp * 9 * N * F, "hbm"
     if tag == "emb_edges_bwd":  # read gX_raw and the projections, write their adjoint and 16 B per edge
         return 2.0 * 40 * F * 2 * nu, f * (9 * N * F + 6 * F * nu) + 16.0 * E, "hbm"
-    if tag == "mlp_elem_bwd":   # read dE/dg and a3, write dE/da3 (+ bf16 copy)
-        return 6.0 * 3 * F * nu, nu * 3 * F * (3 * f + (2 if bf16 else 0)), "hbm"
     if tag == "message":     # read Y and the pair filters once, write M once, read the CSR
         return 2.0 * 9 * F * 2 * nu, f * (2 * 9 * N * F + 3 * F * nu) + 8.0 * E, "hbm"
     if tag == "message_bwd":
-        return 4.0 * 9 * F * 2 * nu, f * (4 * 9 * N * F + 2 * 3 * F * nu) + 8.0 * E, "hbm"
+        # read Y, gM, gY, the filters g, a3 and phi; write gY (+ copy), dE/da3
+        # (fp32 unless bf16, + copy) and update dE/dphi; read the CSR
+        rd = f * (3 * 9 * N * F + 2 * 3 * F * nu + nu) + 8.0 * E
+        wr = (f + cp) * 9 * N * F + ((0.0 if bf16 else f) + cp) * 3 * F * nu + 2 * f * nu
+        return 4.0 * 9 * F * 2 * nu + 6.0 * 3 * F * nu, rd + wr, "hbm"
     return None
 
 
@@ -389,13 +395,12 @@ def run_ours(args):
     hbm = peaks.get("hbm_gbs", 6800.0)
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s, derived
-    bf = args.precision == "bf16"
     x3 = args.precision == "tf32x3"
     work_tags = [k for k in sorted(stages, key=lambda k: -stages[k]["ms_per_step"])
-                 if stage_work(k, nu, N, n_pairs, F_, shape.K, bf) is not None]
+                 if stage_work(k, nu, N, n_pairs, F_, shape.K, args.precision) is not None]
     if work_tags:
         tag = work_tags[0]
-        flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, bf)
+        flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, args.precision)
         if x3 and tag in ("mlp2", "mlp3", "mlp3_bwd", "mlp2_bwd"):
             # 3xTF32: three TF32 MMAs per product; operands fp32 + fp32 residual
             engine = "tensor_tf32"

@@ -88,12 +88,14 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     // edge MLP
     L->eu = take(f * U * K);
     L->phiu = take(f * U);
-    L->a1 = take(f * U * F);
-    L->h1 = take(f * U * F);
-    L->a2 = take(f * U * 2 * F);
-    L->h2 = take(f * U * 2 * F);
-    L->a3 = take(f * U * 3 * F);
-    L->g = take(f * U * 3 * F);
+    // (one set per layer: the reverse pass reads them instead of recomputing)
+    const int64_t NLm = NL > 0 ? NL : 1;
+    L->a1 = take(f * U * F * NLm);
+    L->h1 = take(f * U * F * NLm);
+    L->a2 = take(f * U * 2 * F * NLm);
+    L->h2 = take(f * U * 2 * F * NLm);
+    L->a3 = take(f * U * 3 * F * NLm);
+    L->g = take(f * U * 3 * F * NLm);
     // reverse pass
     L->gXa = take(f * n9);
     L->gXb = take(f * n9);
@@ -146,8 +148,8 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->wbf = take(L->wbf_bytes);
     L->nbf = take(esz * n9);
     L->eu_bf = 0;
-    L->h1_bf = take(esz * U * F);
-    L->h2_bf = take(esz * U * 2 * F);
+    L->h1_bf = take(esz * U * F * NLm);
+    L->h2_bf = take(esz * U * 2 * F * NLm);
     L->ga3_bf = take(esz * U * 3 * F);
     L->ga2_bf = take(esz * U * 2 * F);
     L->ga1_bf = 0;

@@ -223,6 +223,12 @@ __device__ __forceinline__ float silu_grad_f(float x) {
     const float s = __fdividef(1.0f, 1.0f + __expf(-x));
     return s * (1.0f + x * (1.0f - s));
 }
+// silu(x) and silu'(x) from one sigmoid evaluation
+__device__ __forceinline__ void silu_and_grad_f(float x, float &v, float &d) {
+    const float s = __fdividef(1.0f, 1.0f + __expf(-x));
+    v = x * s;
+    d = s * (1.0f + x * (1.0f - s));
+}
 
 // ------------------------------------------------------------- geometry ---
 // Nearest periodic image of a pair vector for a rectangular box; L = 0 along

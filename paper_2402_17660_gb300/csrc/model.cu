@@ -240,7 +240,6 @@ __global__ void k_elem_tables(const float *__restrict__ emb, const float *__rest
 }
 
 // ------------------------------------------------------- embedding ---
-constexpr int kEG = 4;  // edges processed per group in the embedding kernels
 
 struct EdgeGeo {
     int j, active;
@@ -379,10 +378,12 @@ __global__ void k_node_norm(const float *__restrict__ X, int N, int F, float *__
     }
 }
 
+constexpr int kChunk = 128;  // row edges whose indices are staged in shared memory at a time
+
 // M_i = sum_j g^p_ij Y^p_j over the row (block = F threads, thread = channel).
 // g of pair u is stored plane-major, g[u][p][c], so each of its three loads is
 // one coalesced F-channel row.  The row's pair and column indices are staged in
-// shared memory (one coalesced load per chunk of F edges), so each group of
+// shared memory (one coalesced load per chunk of kChunk edges), so each group of
 // kMU edges waits for one round of gathers, not for its indices first; the
 // sums still run in row order.  F is a template parameter so the coordinate
 // offsets are immediates.
@@ -390,15 +391,15 @@ template <int F>
 __global__ void __launch_bounds__(F) k_message(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                                const int32_t *__restrict__ pair_of, const float *__restrict__ gU,
                                                const float *__restrict__ Y, int N, float *__restrict__ M) {
-    __shared__ int32_t s_u[F], s_j[F];
+    __shared__ int32_t s_u[kChunk], s_j[kChunk];
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         float m[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
-        for (int cb = e0; cb < e1; cb += F) {
-            const int n = e1 - cb < F ? e1 - cb : F;
+        for (int cb = e0; cb < e1; cb += kChunk) {
+            const int n = e1 - cb < kChunk ? e1 - cb : kChunk;
             __syncthreads();  // the previous chunk is consumed
-            if (c < n) { s_u[c] = pair_of[cb + c]; s_j[c] = col[cb + c]; }
+            for (int t = c; t < n; t += F) { s_u[t] = pair_of[cb + t]; s_j[t] = col[cb + t]; }
             __syncthreads();
             for (int k0 = 0; k0 < n; k0 += kMU) {
                 int uu[kMU], jj[kMU];
@@ -640,27 +641,43 @@ __global__ void k_T_bwd(const float *__restrict__ Y, const float *__restrict__ M
     }
 }
 
-// Message adjoint.  For atom i (block, thread per channel):
-//   gY_i += sum_j g^p_ij gM_j                       (g_ij = g_ji)
-//   gg[u(i,j)] = <gM_i, Y^p_j> + <gM_j, Y^p_i>       for upper edges j > i
-// Each undirected entry is written once, by its upper edge: no atomics.  Rows
-// ascend, so the upper edges are the row's suffix: the lower part gathers
-// gM_j alone (kMU edges in flight), the upper part gM_j and Y_j together
-// (kMUU edges).  Indices are staged in shared memory as in k_message; the gY
-// sums run in row order.
+// Message adjoint and the last radial layer's elementwise adjoint.  For atom
+// i (block, thread per channel):
+//   gY_i += sum_j g^p_ij gM_j                          (g_ij = g_ji)
+//   gg^p[u(i,j)] = <gM_i, Y^p_j> + <gM_j, Y^p_i>        for upper edges j > i
+// and, with g = phi silu(a3), for the same upper edge:
+//   ga3 = gg phi silu'(a3)       (fp32 if ga3 != NULL, plus its operand copy)
+//   gphi[u] += sum over the 3F entries of gg silu(a3)
+// Each undirected pair is handled once, by its upper edge: no atomics.  The
+// gphi sum is reduced per warp, then over the warps in a fixed order at the end
+// of each chunk.  Rows ascend, so the upper edges are the row's suffix: the
+// lower part gathers gM_j alone (kMU edges in flight), the upper part gM_j,
+// Y_j and a3 together (kMUU edges).  Indices are staged in shared memory as in
+// k_message; the gY sums run in row order.
 constexpr int kMUU = 2;
 template <int F>
 __global__ void __launch_bounds__(F, 512 / F)
     k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                   const int32_t *__restrict__ pair_of, const float *__restrict__ gU, const float *__restrict__ Y,
-                  const float *__restrict__ gM, int N, float *__restrict__ gY, float *__restrict__ gg,
-                  OpCopy gY_cp) {
-    __shared__ int32_t s_u[F], s_j[F];
-    const int c = threadIdx.x;
+                  const float *__restrict__ gM, const float *__restrict__ a3, const float *__restrict__ phiu,
+                  int N, float *__restrict__ gY, OpCopy gY_cp, float *__restrict__ ga3, OpCopy ga3_cp,
+                  float *__restrict__ gphi) {
+    constexpr int NW = F / 32;
+    __shared__ int32_t s_u[kChunk], s_j[kChunk];
+    __shared__ float s_red[kChunk][NW];
+    __shared__ float s_yi[9][F], s_gmi[9][F];  // row i's Y and gM (per thread's channel)
+    const int c = threadIdx.x, lane = c & 31, warp = c >> 5;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
-        float yi[9], gmi[9], acc[9];
-        load_coords(Y, i, c, N, F, yi);
-        load_coords(gM, i, c, N, F, gmi);
+        float acc[9];
+        {
+            float t[9];
+            load_coords(Y, i, c, N, F, t);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) s_yi[q][c] = t[q];
+            load_coords(gM, i, c, N, F, t);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) s_gmi[q][c] = t[q];
+        }
         load_coords(gY, i, c, N, F, acc);
         const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
         int eu = e0, hi = e1;  // eu = first edge with col > i
@@ -669,10 +686,10 @@ __global__ void __launch_bounds__(F, 512 / F)
             if (col[mid] <= i) eu = mid + 1;
             else hi = mid;
         }
-        for (int cb = e0; cb < e1; cb += F) {
-            const int n = e1 - cb < F ? e1 - cb : F;
+        for (int cb = e0; cb < e1; cb += kChunk) {
+            const int n = e1 - cb < kChunk ? e1 - cb : kChunk;
             __syncthreads();
-            if (c < n) { s_u[c] = pair_of[cb + c]; s_j[c] = col[cb + c]; }
+            for (int t = c; t < n; t += F) { s_u[t] = pair_of[cb + t]; s_j[t] = col[cb + t]; }
             __syncthreads();
             const int nl = eu - cb < 0 ? 0 : (eu - cb < n ? eu - cb : n);  // lower edges of the chunk
             for (int k0 = 0; k0 < nl; k0 += kMU) {
@@ -707,12 +724,14 @@ __global__ void __launch_bounds__(F, 512 / F)
                     uu[k] = k0 + k < n ? s_u[k0 + k] : -1;
                     jj[k] = k0 + k < n ? s_j[k0 + k] : 0;
                 }
-                float g[kMUU][3], gmj[kMUU][9], yj[kMUU][9];
+                float g[kMUU][3], gmj[kMUU][9], yj[kMUU][9], a[kMUU][3], phi[kMUU];
 #pragma unroll
                 for (int k = 0; k < kMUU; ++k) {
                     if (uu[k] < 0) continue;
-                    const float *gp = gU + (int64_t)uu[k] * 3 * F + c;
-                    g[k][0] = gp[0]; g[k][1] = gp[F]; g[k][2] = gp[2 * F];
+                    const int64_t o = (int64_t)uu[k] * 3 * F + c;
+                    g[k][0] = gU[o]; g[k][1] = gU[o + F]; g[k][2] = gU[o + 2 * F];
+                    a[k][0] = a3[o]; a[k][1] = a3[o + F]; a[k][2] = a3[o + 2 * F];
+                    phi[k] = phiu[uu[k]];
                     load_coords(gM, jj[k], c, N, F, gmj[k]);
                     load_coords(Y, jj[k], c, N, F, yj[k]);
                 }
@@ -724,42 +743,40 @@ __global__ void __launch_bounds__(F, 512 / F)
                     for (int q = 1; q < 4; ++q) acc[q] = fmaf(g[k][1], gmj[k][q], acc[q]);
 #pragma unroll
                     for (int q = 4; q < 9; ++q) acc[q] = fmaf(g[k][2], gmj[k][q], acc[q]);
-                    float sI = gmi[0] * yj[k][0] + gmj[k][0] * yi[0];
-                    float sA = 0.f, sS = 0.f;
+                    float sp[3];
+                    sp[0] = s_gmi[0][c] * yj[k][0] + gmj[k][0] * s_yi[0][c];
+                    sp[1] = 0.f; sp[2] = 0.f;
 #pragma unroll
-                    for (int q = 1; q < 4; ++q) sA += gmi[q] * yj[k][q] + gmj[k][q] * yi[q];
+                    for (int q = 1; q < 4; ++q) sp[1] += s_gmi[q][c] * yj[k][q] + gmj[k][q] * s_yi[q][c];
 #pragma unroll
-                    for (int q = 4; q < 9; ++q) sS += gmi[q] * yj[k][q] + gmj[k][q] * yi[q];
-                    float *o = gg + (int64_t)uu[k] * 3 * F + c;
-                    o[0] = sI; o[F] = sA; o[2 * F] = sS;
+                    for (int q = 4; q < 9; ++q) sp[2] += s_gmi[q][c] * yj[k][q] + gmj[k][q] * s_yi[q][c];
+                    const int64_t o = (int64_t)uu[k] * 3 * F + c;
+                    float r = 0.f;
+#pragma unroll
+                    for (int p = 0; p < 3; ++p) {
+                        float sv, sd;
+                        silu_and_grad_f(a[k][p], sv, sd);
+                        r = fmaf(sp[p], sv, r);
+                        const float ga = sp[p] * phi[k] * sd;
+                        if (ga3) ga3[o + p * F] = ga;
+                        opcopy_store(ga3_cp, o + p * F, ga);
+                    }
+                    r = warp_sum(r);
+                    if (lane == 0) s_red[k0 + k - nl][warp] = r;
                 }
+            }
+            __syncthreads();
+            for (int t = c; t < n - nl; t += F) {
+                const int u = s_u[nl + t];
+                if (u < 0) continue;
+                float r = 0.f;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) r += s_red[t][w];
+                gphi[u] += r;
             }
         }
         store_coords(gY, i, c, N, F, acc);
         store_coords_cp(gY_cp, i, c, N, F, acc);
-    }
-}
-
-// g = phi * silu(a3):  ga3 = gg * phi * silu'(a3) (in place), gphi += <gg, silu(a3)>
-__global__ void k_mlp3_bwd(float *__restrict__ gg, const float *__restrict__ a3,
-                           const float *__restrict__ phiu, const int32_t *__restrict__ nu, int W,
-                           float *__restrict__ gphi, OpCopy ga3_cp) {
-    const int U = *nu;
-    const int lane = threadIdx.x & 31;
-    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < U;
-         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const float phi = phiu[u];
-        float s = 0.f;
-        for (int n = lane; n < W; n += 32) {
-            const int64_t o = u * W + n;
-            const float a = a3[o], gv = gg[o];
-            s = fmaf(gv, silu_f(a), s);
-            const float ga = gv * phi * silu_grad_f(a);
-            gg[o] = ga;
-            opcopy_store(ga3_cp, o, ga);
-        }
-        s = warp_sum(s);
-        if (lane == 0) gphi[u] += s;
     }
 }
 
@@ -1317,8 +1334,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     auto cp = [&](size_t off) { return OpCopy{tcm ? (void *)(ctx->ws + off) : nullptr, prec}; };
     // (the num_rbf-wide operands e(d) and dE/df stay FP32, so they get no copy)
     const OpCopy none{nullptr, 0};
-    const OpCopy nbf = cp(Lw.nbf), eu_cp = none, h1_cp = cp(Lw.h1_bf), h2_cp = cp(Lw.h2_bf),
-                 ga3_cp = cp(Lw.ga3_bf), ga2_cp = cp(Lw.ga2_bf), ga1_cp = none, gfu_cp = none;
+    const OpCopy nbf = cp(Lw.nbf), eu_cp = none, ga3_cp = cp(Lw.ga3_bf), ga2_cp = cp(Lw.ga2_bf), ga1_cp = none,
+                 gfu_cp = none;
+    // per-layer radial-MLP activations (and their operand copies)
+    const int64_t esz_cp = prec == 1 ? 2 : 4;
+    auto h1_cp = [&](int l) { return cp(Lw.h1_bf + (size_t)((int64_t)l * maxU * F * esz_cp)); };
+    auto h2_cp = [&](int l) { return cp(Lw.h2_bf + (size_t)((int64_t)l * maxU * 2 * F * esz_cp)); };
     struct LayerB {
         WOp mlp2, mlp3, mlp2T, mlp3T, mix1, mix1T, mix2, mix2T;
     } lb[8] = {};
@@ -1462,12 +1483,14 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     TNET_LAUNCH_CHECK();
 
     // ---- interaction layers
-    float *a1 = f32(Lw.a1), *h1 = f32(Lw.h1), *a2 = f32(Lw.a2), *h2 = f32(Lw.h2), *a3 = f32(Lw.a3),
-          *gbuf = f32(Lw.g);
+    // layer l's radial-MLP activations: [maxU][width] slabs
+    auto act = [&](size_t off, int width, int l) { return f32(off) + (int64_t)l * maxU * width; };
     auto edge_mlp = [&](int l) -> int {
         const LayerW &Lr = W.layer[l];
-        const EpiBiasAct e1{Lr.mlp1_b, a1, F, keep_h ? h1 : nullptr, F, 1, nullptr, h1_cp, F};
-        const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, keep_h ? h2 : nullptr, 2 * F, 1, nullptr, h2_cp, 2 * F};
+        float *a1 = act(Lw.a1, F, l), *h1 = act(Lw.h1, F, l), *a2 = act(Lw.a2, 2 * F, l),
+              *h2 = act(Lw.h2, 2 * F, l), *a3 = act(Lw.a3, 3 * F, l), *gbuf = act(Lw.g, 3 * F, l);
+        const EpiBiasAct e1{Lr.mlp1_b, a1, F, keep_h ? h1 : nullptr, F, 1, nullptr, h1_cp(l), F};
+        const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, keep_h ? h2 : nullptr, 2 * F, 1, nullptr, h2_cp(l), 2 * F};
         const EpiBiasAct e3{b3p(l), a3, 3 * F, gbuf, 3 * F, 1, phiu};
         if (tcm) {
             tc::TcShape t2 = tc::tshape(maxU, 2 * F, F), t3 = tc::tshape(maxU, 3 * F, 2 * F);
@@ -1477,9 +1500,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             p1.rows_dev = nu;
             TRY(sgemm<false, true>(p1, e1, gctas, st));
             pf.mark(P_MLP2);
-            TRY(tcg(t2, h1, h1_cp, maxU, F, lb[l].mlp2, 2 * F, F, e2, bn2));
+            TRY(tcg(t2, h1, h1_cp(l), maxU, F, lb[l].mlp2, 2 * F, F, e2, bn2));
             pf.mark(P_MLP3);
-            TRY(tcg(t3, h2, h2_cp, maxU, 2 * F, lb[l].mlp3, 3 * F, 2 * F, e3, bn3));
+            TRY(tcg(t3, h2, h2_cp(l), maxU, 2 * F, lb[l].mlp3, 3 * F, 2 * F, e3, bn3));
             return TNET_OK;
         }
         pf.mark(P_MLP1);
@@ -1511,6 +1534,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         else TRY(sgemm<false, true>(gshape_classes(N, F, Xn, W.layer[l].mix1_w), EpiStore{Y, F, 0}, gctas, st));
         TRY(edge_mlp(l));
         pf.mark(P_MESSAGE);
+        const float *gbuf = act(Lw.g, 3 * F, l);
 #define MSG_FWD(FF) k_message<FF><<<atom_blocks, FF, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, N, M)
         TNET_F_SWITCH(F, MSG_FWD);
 #undef MSG_FWD
@@ -1593,15 +1617,18 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         k_T_bwd<<<ew, 256, 0, st>>>(Y, M, gTn, N, F, gY, gM);
         count_launch();
         TNET_LAUNCH_CHECK();
-        TRY(edge_mlp(l));  // recompute a1, h1, a2, h2, a3, g of this layer
+        // this layer's radial-MLP activations, kept from the forward pass
+        const float *a1 = act(Lw.a1, F, l), *h1 = act(Lw.h1, F, l), *a2 = act(Lw.a2, 2 * F, l),
+                    *h2 = act(Lw.h2, 2 * F, l), *a3 = act(Lw.a3, 3 * F, l), *gbuf = act(Lw.g, 3 * F, l);
         pf.mark(P_MSG_BWD);
-#define MSG_BWD(FF) \
-    k_message_bwd<FF><<<atom_blocks, FF, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, gM, N, gY, gg, nbf)
+        // (the BF16 GEMMs read only the copy of ga3; the fp32 ga3 feeds the FP32
+        // and 3xTF32 GEMMs and the weight gradients)
+        float *ga3_out = (prec != 1 || wg) ? gg : nullptr;
+#define MSG_BWD(FF)                                                                                          \
+    k_message_bwd<FF><<<atom_blocks, FF, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu, N, gY, nbf, \
+                                                  ga3_out, ga3_cp, gphiu)
         TNET_F_SWITCH(F, MSG_BWD);
 #undef MSG_BWD
-        count_launch();
-        pf.mark(P_MLP_ELEM_BWD);
-        k_mlp3_bwd<<<pair_grid, 256, 0, st>>>(gg, a3, phiu, nu, 3 * F, gphiu, ga3_cp);
         count_launch();
         TNET_LAUNCH_CHECK();
         const EpiGradAct g3{a2, 2 * F, ga2, 2 * F, 0, ga2_cp, 2 * F};
