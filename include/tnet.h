@@ -57,11 +57,17 @@ typedef struct tnet_ctx tnet_ctx;
  * is reduced in FP64 in every mode.
  * Limits: F a multiple of 64 in [64, 512], K a multiple of 8 in [8, 64],
  * (precision 1 and 2 need F <= 256),
- * 0 <= L <= 8, 1 <= max_z <= 128, 0 <= cutoff_lower < cutoff_upper. */
+ * 0 <= L <= 8, 1 <= max_z <= 128, 0 <= cutoff_lower < cutoff_upper.
+ * recompute_edges: 0 = the forward pass keeps every layer's radial-MLP
+ * activations (about 12 F floats per undirected pair and layer, plus operand
+ * copies) for the reverse pass; 1 = the reverse pass recomputes them, so the
+ * workspace holds one layer's worth (for systems whose pair count presses on
+ * memory).  Results are bitwise identical either way. */
 typedef struct {
     int F, K, L, max_z;
     float cutoff_upper, cutoff_lower;
     int precision;
+    int recompute_edges;
 } tnet_model_desc;
 
 typedef enum {

@@ -13,7 +13,7 @@ from . import build as _build
 class ModelDesc(ctypes.Structure):
     _fields_ = [("F", ctypes.c_int), ("K", ctypes.c_int), ("L", ctypes.c_int), ("max_z", ctypes.c_int),
                 ("cutoff_upper", ctypes.c_float), ("cutoff_lower", ctypes.c_float),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("recompute_edges", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p

@@ -17,6 +17,7 @@ int validate_desc(const tnet_model_desc *d) {
     if (d->max_z < 1 || d->max_z > 128) return TNET_ERR_ARG;
     if (!(d->cutoff_upper > d->cutoff_lower) || d->cutoff_lower < 0.f) return TNET_ERR_ARG;
     if (d->precision < 0 || d->precision > 2) return TNET_ERR_ARG;
+    if (d->recompute_edges < 0 || d->recompute_edges > 1) return TNET_ERR_ARG;
     return TNET_OK;
 }
 
@@ -88,8 +89,8 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     // edge MLP
     L->eu = take(f * U * K);
     L->phiu = take(f * U);
-    // (one set per layer: the reverse pass reads them instead of recomputing)
-    const int64_t NLm = NL > 0 ? NL : 1;
+    // (one set per layer, which the reverse pass reads, unless it recomputes them)
+    const int64_t NLm = (NL > 0 && !d->recompute_edges) ? NL : 1;
     L->a1 = take(f * U * F * NLm);
     L->h1 = take(f * U * F * NLm);
     L->a2 = take(f * U * 2 * F * NLm);

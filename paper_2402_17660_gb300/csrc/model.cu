@@ -1338,8 +1338,11 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
                  gfu_cp = none;
     // per-layer radial-MLP activations (and their operand copies)
     const int64_t esz_cp = prec == 1 ? 2 : 4;
-    auto h1_cp = [&](int l) { return cp(Lw.h1_bf + (size_t)((int64_t)l * maxU * F * esz_cp)); };
-    auto h2_cp = [&](int l) { return cp(Lw.h2_bf + (size_t)((int64_t)l * maxU * 2 * F * esz_cp)); };
+    // slab of layer l (one shared slab when the reverse pass recomputes them)
+    const bool keep_act = !d.recompute_edges;
+    auto slab = [&](int l) { return keep_act ? (int64_t)l : 0; };
+    auto h1_cp = [&](int l) { return cp(Lw.h1_bf + (size_t)(slab(l) * maxU * F * esz_cp)); };
+    auto h2_cp = [&](int l) { return cp(Lw.h2_bf + (size_t)(slab(l) * maxU * 2 * F * esz_cp)); };
     struct LayerB {
         WOp mlp2, mlp3, mlp2T, mlp3T, mix1, mix1T, mix2, mix2T;
     } lb[8] = {};
@@ -1484,7 +1487,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
 
     // ---- interaction layers
     // layer l's radial-MLP activations: [maxU][width] slabs
-    auto act = [&](size_t off, int width, int l) { return f32(off) + (int64_t)l * maxU * width; };
+    auto act = [&](size_t off, int width, int l) { return f32(off) + slab(l) * maxU * width; };
     auto edge_mlp = [&](int l) -> int {
         const LayerW &Lr = W.layer[l];
         float *a1 = act(Lw.a1, F, l), *h1 = act(Lw.h1, F, l), *a2 = act(Lw.a2, 2 * F, l),
@@ -1617,7 +1620,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         k_T_bwd<<<ew, 256, 0, st>>>(Y, M, gTn, N, F, gY, gM);
         count_launch();
         TNET_LAUNCH_CHECK();
-        // this layer's radial-MLP activations, kept from the forward pass
+        // this layer's radial-MLP activations: kept from the forward pass, or
+        // recomputed here (same kernels, same inputs: bitwise the same values)
+        if (!keep_act) TRY(edge_mlp(l));
         const float *a1 = act(Lw.a1, F, l), *h1 = act(Lw.h1, F, l), *a2 = act(Lw.a2, 2 * F, l),
                     *h2 = act(Lw.h2, 2 * F, l), *a3 = act(Lw.a3, 3 * F, l), *gbuf = act(Lw.g, 3 * F, l);
         pf.mark(P_MSG_BWD);

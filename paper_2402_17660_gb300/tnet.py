@@ -72,14 +72,15 @@ class TensorNet:
     """One libtnet context: model shape, limits and its device workspace."""
 
     def __init__(self, weights: dict, F=128, K=32, L=2, max_z=100, cutoff_upper=5.0, cutoff_lower=0.0,
-                 max_atoms=1024, max_systems=1, max_pairs=65536, precision=0, device="cuda"):
+                 max_atoms=1024, max_systems=1, max_pairs=65536, precision=0, device="cuda",
+                 recompute_edges=False):
         self.lib = _lib.load()
         self.device = torch.device(device)
         if self.device.type != "cuda":
             raise RuntimeError("libtnet runs on CUDA devices only")
         self.F, self.K, self.L, self.max_z = F, K, L, max_z
         self.cutoff = float(cutoff_upper)
-        self.desc = _lib.ModelDesc(F, K, L, max_z, cutoff_upper, cutoff_lower, precision)
+        self.desc = _lib.ModelDesc(F, K, L, max_z, cutoff_upper, cutoff_lower, precision, int(bool(recompute_edges)))
         self.max_atoms, self.max_systems, self.max_pairs = int(max_atoms), int(max_systems), int(max_pairs)
         nbytes = self.lib.tnet_workspace_bytes(ctypes.byref(self.desc), self.max_atoms, self.max_systems,
                                                self.max_pairs)

@@ -48,6 +48,21 @@ def test_workspace_bytes(lib):
     assert lib.tnet_workspace_bytes(ctypes.byref(d), 0, 1, 10) == -1
 
 
+def test_recompute_edges_shrinks_workspace(lib):
+    keep = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0, 0)
+    rec = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0, 1)
+    a = lib.tnet_workspace_bytes(ctypes.byref(keep), 3000, 1, 160000)
+    b = lib.tnet_workspace_bytes(ctypes.byref(rec), 3000, 1, 160000)
+    # one layer's radial-MLP activations: 12 F floats per undirected pair
+    assert a - b >= 12 * 128 * 4 * 80000
+    one = _lib.ModelDesc(128, 32, 1, 100, 5.0, 0.0, 0, 0)
+    one_r = _lib.ModelDesc(128, 32, 1, 100, 5.0, 0.0, 0, 1)
+    assert lib.tnet_workspace_bytes(ctypes.byref(one), 3000, 1, 160000) == \
+        lib.tnet_workspace_bytes(ctypes.byref(one_r), 3000, 1, 160000)
+    bad = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0, 2)
+    assert lib.tnet_workspace_bytes(ctypes.byref(bad), 3000, 1, 160000) == -1
+
+
 def test_create_rejects_bad_workspace(lib):
     d = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0)
     ctx = ctypes.c_void_p()

@@ -8,7 +8,7 @@ import torch
 
 from oracle.neighbors import neighbor_pairs
 from paper_2402_17660_gb300 import synth
-from paper_2402_17660_gb300.tnet import EnergyFn, NeighborList
+from paper_2402_17660_gb300.tnet import EnergyFn, NeighborList, TensorNet
 
 from .gpu_helpers import (DEV, E_TOL, F_TOL, RC, energy_errors, force_error, gpu_energy_forces, gpu_pairs,
                           make_model, margin_ok, oracle_energy_forces, to_dev)
@@ -112,6 +112,26 @@ def test_bad_atomic_number_flagged():
     m.energy_forces(z, pos, nl)
     torch.cuda.synchronize()
     assert int(m.status.item()) == 8
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_recompute_edges_bitwise_equal(precision):
+    """Keeping the radial-MLP activations and recomputing them in the reverse
+    pass run the same kernels on the same inputs: identical results."""
+    s = synth.workload("water3000")
+    z, pos, batch, box = to_dev(s)
+    out = []
+    for rec in (False, True):
+        m = TensorNet(W, max_atoms=s.n_atoms, max_pairs=200000, precision=precision, device=DEV,
+                      recompute_edges=rec)
+        nl = gpu_pairs(m, s)
+        m.reset_status()
+        E, F, G = m.energy_forces(z, pos, nl, None, box, 1, forces=True, grad_weights=True)
+        torch.cuda.synchronize()
+        m.check_status("recompute_edges")
+        out.append((E.cpu().numpy(), F.cpu().numpy(), G.cpu().numpy()))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
 
 
 def test_unsorted_row_rejected():
