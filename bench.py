@@ -55,7 +55,8 @@ def parse():
                          "defaults; or a comma-separated knob list")
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--md", type=int, default=0,
-                    help="also time this many velocity-Verlet steps (0.5 fs, 1 A skin, rebuild every 20)")
+                    help="also time this many velocity-Verlet steps (0.5 fs, 1 A skin, rebuild every 20 steps "
+                         "and whenever an atom has moved more than skin/2)")
     ap.add_argument("--per-molecule", action="store_true",
                     help="for batched workloads, also time one eager call per molecule")
     return ap.parse_args()
@@ -602,6 +603,8 @@ def run_md(sys_, shape, prec, dev, args):
     et = (ek + ep).cpu().numpy()
     return {"steps": n, "dt_fs": dt, "rebuild_every": R, "skin_A": 1.0, "ns_per_day": n * dt * 1e-6 / sec * 86400,
             "steps_per_s": n / sec, "drift_eV_per_atom_per_ps": float((et[-1] - et[0]) / N / (n * dt * 1e-3)),
+            "neighbor_builds": m.md_rebuilds(),
+            "rebuild_rule": "every 20 steps and in any step where an atom moved > skin/2 (device-side test)",
             "status": status, "weights": "random init, output layer scaled by 0.05"}
 
 

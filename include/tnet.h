@@ -81,7 +81,7 @@ typedef enum {
     TNET_ERR_WORKSPACE = 7,   /* workspace too small or misaligned */
     TNET_ERR_Z = 8,           /* atomic number outside [0, max_z) (device) */
     TNET_ERR_UNSUPPORTED = 9, /* valid request this build does not implement */
-    TNET_ERR_SKIN = 10        /* MD: an atom moved more than skin/2 between rebuilds */
+    TNET_ERR_SKIN = 10        /* reserved (tnet_md_step rebuilds when an atom moves > skin/2) */
 } tnet_status;
 
 const char *tnet_status_string(int status);
@@ -178,8 +178,9 @@ int tnet_energy_forces(tnet_ctx *ctx, const float *weights, int n_atoms, int n_s
 /* Molecular dynamics (the paper's MD use, Sec. 3 "Molecular Simulations";
  * one step = one energy evaluation plus one force backward pass): n_steps
  * velocity-Verlet steps of one system with time step dt_fs:
- *   v += dt/2 F/m; x += dt v; [every rebuild_every steps: neighbor list at
- *   cutoff_upper + skin]; F = forces(x); v += dt/2 F/m.
+ *   v += dt/2 F/m; x += dt v; [neighbor list at cutoff_upper + skin: every
+ *   rebuild_every steps, and in any step where an atom has moved more than
+ *   skin/2 since the last rebuild]; F = forces(x); v += dt/2 F/m.
  * Forces in eV/A and masses in amu are converted with
  * 1 eV/(A amu) = 9.64853321e-3 A/fs^2.
  *   inv_mass [N] float32 1/m in 1/amu; pos, vel [N][3] float32 updated in
@@ -188,13 +189,20 @@ int tnet_energy_forces(tnet_ctx *ctx, const float *weights, int n_atoms, int n_s
  *   after each step
  * The steps run as replays of a CUDA graph of rebuild_every steps that the
  * context captures on first use and re-captures when a pointer, count or
- * parameter changes.  If an atom moves more than skin/2 between rebuilds,
- * status SKIN is set (results of that interval are not trustworthy).
+ * parameter changes.  The displacement test runs on the device in every
+ * step; a step that does not rebuild runs the neighbor kernels as no-ops, so
+ * the list always holds every pair within cutoff_upper and the trajectory
+ * does not depend on skin or rebuild_every.
  * Requires max_pairs >= the pairs within cutoff_upper + skin. */
 int tnet_md_step(tnet_ctx *ctx, const float *weights, int n_atoms, const int32_t *z,
                  const float *inv_mass, float *pos, float *vel, const float *box, float dt_fs,
                  float skin, int rebuild_every, int n_steps, double *e_kin, double *e_pot,
                  int32_t *status_dev, tnet_stream_t stream);
+
+/* Number of neighbor-list builds (periodic and displacement-triggered,
+ * including the initial one) of the last tnet_md_step call on this context.
+ * Synchronous: waits for the device.  count: host pointer. */
+int tnet_md_rebuilds(tnet_ctx *ctx, int64_t *count);
 
 /* ---- allocation-free neighbor search (no counterpart in the paper) -------
  * For callers that cannot allocate device memory (code inside another

@@ -163,6 +163,8 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->md_energy = take(8);
     L->md_pos_ref = take(f * 3 * N);
     L->md_step = take(i * 4);
+    L->md_need = take(i * 4);
+    L->md_rebuilds = take(8);
     L->total = off;
     return TNET_OK;
 }
@@ -220,7 +222,7 @@ const char *tnet_status_string(int s) {
         case TNET_ERR_WORKSPACE: return "workspace too small or misaligned";
         case TNET_ERR_Z: return "atomic number out of range";
         case TNET_ERR_UNSUPPORTED: return "not supported by this build";
-        case TNET_ERR_SKIN: return "an atom moved more than skin/2 between neighbor-list rebuilds";
+        case TNET_ERR_SKIN: return "reserved (skin violations trigger a rebuild)";
         default: return "unknown status";
     }
 }
@@ -392,6 +394,12 @@ int tnet_md_step(tnet_ctx *c, const float *w, int N, const int32_t *z, const flo
     if (!(dt > 0.f) || !(skin >= 0.f) || rebuild_every < 1 || n_steps < 0) return TNET_ERR_ARG;
     return md_impl(c, w, N, z, inv_mass, pos, vel, box, dt, skin, rebuild_every, n_steps, e_kin, e_pot,
                    status, (cudaStream_t)stream);
+}
+
+int tnet_md_rebuilds(tnet_ctx *c, int64_t *count) {
+    if (!c || !count) return TNET_ERR_ARG;
+    TNET_CUDA_TRY(cudaMemcpy(count, wsp<int64_t>(c, c->lay.md_rebuilds), sizeof(int64_t), cudaMemcpyDeviceToHost));
+    return TNET_OK;
 }
 
 }  // extern "C"

@@ -294,7 +294,7 @@ struct Layout {
     size_t w3p;
     int64_t wpart_floats, zsplits;
     // MD
-    size_t md_row_ptr, md_col, md_npairs, md_forces, md_energy, md_pos_ref, md_step;
+    size_t md_row_ptr, md_col, md_npairs, md_forces, md_energy, md_pos_ref, md_step, md_need, md_rebuilds;
     size_t total;
     int64_t node9;  // floats of one [9N][F] buffer
     int64_t cells;  // cell capacity
@@ -385,15 +385,17 @@ template <class T>
 __host__ inline T *wsp(tnet_ctx *c, size_t off) {
     return reinterpret_cast<T *>(c->ws + off);
 }
+// gate: optional device flag; when it reads 0 every kernel of the call
+// returns at once (a rebuild that the graph enqueues but the step skips)
 int scan_exclusive_i32(const int32_t *in, int32_t *out, int n, int32_t *tmp, int32_t *total_dev,
-                       int64_t *total64_dev, cudaStream_t st);
+                       int64_t *total64_dev, cudaStream_t st, const int32_t *gate = nullptr);
 int tnet_kernel_setup(tnet_ctx *c);
 int sys_bounds(const int32_t *batch, int N, int S, int32_t *sys_start, int32_t *sys_end,
                int32_t *status, cudaStream_t st);
 int64_t weight_offsets(const tnet_model_desc *d, const float *base, struct Weights *w);
 int neighbors_impl(tnet_ctx *ctx, int n_atoms, int n_systems, const float *pos, const int32_t *batch,
                    const float *box, float cutoff, int32_t *row_ptr, int32_t *col, int64_t cap,
-                   int64_t *n_pairs_dev, int32_t *status_dev, cudaStream_t st);
+                   int64_t *n_pairs_dev, int32_t *status_dev, cudaStream_t st, const int32_t *gate = nullptr);
 int energy_forces_impl(tnet_ctx *ctx, const float *w, int n_atoms, int n_systems, const int32_t *z,
                        const float *pos, const int32_t *batch, const float *box,
                        const int32_t *row_ptr, const int32_t *col, const float *seed,

@@ -19,9 +19,12 @@ __global__ void k_half_kick(float *__restrict__ vel, const float *__restrict__ F
     vel[t] += hdt * kAccel * F[t] * inv_m[t / 3];
 }
 
+// x += dt v; raise the rebuild flag when an atom is more than skin/2 from
+// where it was at the last rebuild (two atoms closing in from outside
+// cutoff + skin could then be within the cutoff)
 __global__ void k_drift(float *__restrict__ pos, const float *__restrict__ vel, int N, float dt,
                         const float *__restrict__ ref, const float *__restrict__ box, float lim2,
-                        int32_t *status) {
+                        int32_t *__restrict__ need) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float d[3];
@@ -32,12 +35,21 @@ __global__ void k_drift(float *__restrict__ pos, const float *__restrict__ vel, 
         d[k] = x - ref[3LL * i + k];
         if (box) d[k] -= box[4 * k] * rintf(d[k] / box[4 * k]);
     }
-    if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] > lim2) set_status(status, TNET_ERR_SKIN);
+    if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] > lim2) *need = 1;
 }
 
-__global__ void k_copy(float *__restrict__ dst, const float *__restrict__ src, int64_t n) {
+__global__ void k_copy(float *__restrict__ dst, const float *__restrict__ src, int64_t n,
+                       const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t < n) dst[t] = src[t];
+}
+
+// after a rebuild slot: count it (periodic, or triggered by the flag) and
+// clear the flag
+__global__ void k_rebuild_done(int32_t *__restrict__ need, int64_t *__restrict__ count, int periodic) {
+    if (periodic || *need) ++*count;
+    *need = 0;
 }
 
 // single block: kinetic energy (FP64, eV) and the step's records
@@ -77,14 +89,22 @@ struct MdArgs {
     int32_t *status;
 };
 
-int enqueue_rebuild(tnet_ctx *c, const MdArgs &a, cudaStream_t st) {
+// Neighbor list at cutoff + skin and the reference positions.  periodic:
+// always; otherwise only if the drift raised the rebuild flag (the kernels
+// are enqueued either way, so one graph serves every step, and return at
+// once when the flag is clear).
+int enqueue_rebuild(tnet_ctx *c, const MdArgs &a, bool periodic, cudaStream_t st) {
     const Layout &L = c->lay;
     const float rcut = c->d.cutoff_upper + a.skin;
+    int32_t *need = wsp<int32_t>(c, L.md_need);
+    const int32_t *gate = periodic ? nullptr : need;
     int rc = neighbors_impl(c, a.N, 1, a.pos, nullptr, a.box, rcut, wsp<int32_t>(c, L.md_row_ptr),
                             wsp<int32_t>(c, L.md_col), c->max_pairs, wsp<int64_t>(c, L.md_npairs), a.status,
-                            st);
+                            st, gate);
     if (rc) return rc;
-    k_copy<<<(3 * a.N + 255) / 256, 256, 0, st>>>(wsp<float>(c, L.md_pos_ref), a.pos, 3LL * a.N);
+    k_copy<<<(3 * a.N + 255) / 256, 256, 0, st>>>(wsp<float>(c, L.md_pos_ref), a.pos, 3LL * a.N, gate);
+    count_launch();
+    k_rebuild_done<<<1, 1, 0, st>>>(need, wsp<int64_t>(c, L.md_rebuilds), periodic ? 1 : 0);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
@@ -105,11 +125,11 @@ int enqueue_step(tnet_ctx *c, const MdArgs &a, bool rebuild, cudaStream_t st) {
     count_launch();
     const float lim = 0.5f * a.skin;
     k_drift<<<nb, 256, 0, st>>>(a.pos, a.vel, a.N, a.dt, wsp<float>(c, L.md_pos_ref), a.box, lim * lim,
-                                a.status);
+                                wsp<int32_t>(c, L.md_need));
     count_launch();
     TNET_LAUNCH_CHECK();
-    if (rebuild) {
-        int rc = enqueue_rebuild(c, a, st);
+    {
+        int rc = enqueue_rebuild(c, a, rebuild, st);
         if (rc) return rc;
     }
     int rc = enqueue_forces(c, a, st);
@@ -129,8 +149,10 @@ int md_impl(tnet_ctx *c, const float *w, int N, const int32_t *z, const float *i
             double *e_pot, int32_t *status, cudaStream_t st) {
     const MdArgs a{w, N, z, inv_m, pos, vel, box, dt, skin, e_kin, e_pot, status};
     TNET_CUDA_TRY(cudaMemsetAsync(wsp<int32_t>(c, c->lay.md_step), 0, sizeof(int32_t), st));
+    TNET_CUDA_TRY(cudaMemsetAsync(wsp<int32_t>(c, c->lay.md_need), 0, sizeof(int32_t), st));
+    TNET_CUDA_TRY(cudaMemsetAsync(wsp<int64_t>(c, c->lay.md_rebuilds), 0, sizeof(int64_t), st));
     // forces at the starting positions
-    int rc = enqueue_rebuild(c, a, st);
+    int rc = enqueue_rebuild(c, a, true, st);
     if (rc) return rc;
     rc = enqueue_forces(c, a, st);
     if (rc) return rc;

@@ -42,7 +42,8 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *tota
 }
 
 __global__ void k_scan_tiles(const int32_t *__restrict__ in, int32_t *__restrict__ out, int n,
-                             int32_t *__restrict__ tile_sums) {
+                             int32_t *__restrict__ tile_sums, const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     __shared__ int32_t sm[32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     int32_t v[kScanItems];
@@ -63,7 +64,9 @@ __global__ void k_scan_tiles(const int32_t *__restrict__ in, int32_t *__restrict
 }
 
 // single block: exclusive scan of the tile sums (nt <= kScanTile)
-__global__ void k_scan_top(int32_t *__restrict__ tile_sums, int nt, int32_t *__restrict__ grand) {
+__global__ void k_scan_top(int32_t *__restrict__ tile_sums, int nt, int32_t *__restrict__ grand,
+                           const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     __shared__ int32_t sm[32];
     const int base = threadIdx.x * kScanItems;
     int32_t v[kScanItems];
@@ -85,7 +88,8 @@ __global__ void k_scan_top(int32_t *__restrict__ tile_sums, int nt, int32_t *__r
 
 __global__ void k_scan_add(int32_t *__restrict__ out, int n, const int32_t *__restrict__ tile_sums,
                            const int32_t *__restrict__ grand, int32_t *__restrict__ total_dev,
-                           int64_t *__restrict__ total64_dev) {
+                           int64_t *__restrict__ total64_dev, const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] += tile_sums[i / kScanTile];
     if (i == 0) {
@@ -97,19 +101,29 @@ __global__ void k_scan_add(int32_t *__restrict__ out, int n, const int32_t *__re
 
 // out[0..n] = exclusive scan of in[0..n), out[n] = total.  tmp needs
 // ceil(n / 4096) + 1 ints.  n <= 4096 * 4096.
+// dst[0..n) = 0 unless a gate is given and clear (the gated form of a memset)
+__global__ void k_zero_i32(int32_t *__restrict__ dst, int64_t n, const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        dst[t] = 0;
+}
+
 int scan_exclusive_i32(const int32_t *in, int32_t *out, int n, int32_t *tmp, int32_t *total_dev,
-                       int64_t *total64_dev, cudaStream_t st) {
+                       int64_t *total64_dev, cudaStream_t st, const int32_t *gate) {
     const int nt = (n + kScanTile - 1) / kScanTile;
     if (nt > kScanTile) return TNET_ERR_ARG;
     const int ntl = nt > 0 ? nt : 1;
     if (n > 0) {
-        k_scan_tiles<<<nt, kScanThreads, 0, st>>>(in, out, n, tmp);
+        k_scan_tiles<<<nt, kScanThreads, 0, st>>>(in, out, n, tmp, gate);
         count_launch();
     }
-    else TNET_CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(int32_t), st));
-    k_scan_top<<<1, kScanThreads, 0, st>>>(tmp, ntl, tmp + ntl);
+    else if (gate) {
+        k_zero_i32<<<1, 32, 0, st>>>(tmp, 1, gate);
+        count_launch();
+    } else TNET_CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(int32_t), st));
+    k_scan_top<<<1, kScanThreads, 0, st>>>(tmp, ntl, tmp + ntl, gate);
     count_launch();
-    k_scan_add<<<(n + 255) / 256 + 1, 256, 0, st>>>(out, n, tmp, tmp + ntl, total_dev, total64_dev);
+    k_scan_add<<<(n + 255) / 256 + 1, 256, 0, st>>>(out, n, tmp, tmp + ntl, total_dev, total64_dev, gate);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
@@ -118,7 +132,8 @@ int scan_exclusive_i32(const int32_t *in, int32_t *out, int n, int32_t *tmp, int
 // --------------------------------------------------------------- systems ---
 __global__ void k_sys_bounds(const int32_t *__restrict__ batch, int N, int S,
                              int32_t *__restrict__ sys_start, int32_t *__restrict__ sys_end,
-                             int32_t *status) {
+                             int32_t *status, const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int b = batch ? batch[n] : 0;
@@ -135,7 +150,7 @@ __global__ void k_sys_bounds(const int32_t *__restrict__ batch, int N, int S,
 
 int sys_bounds(const int32_t *batch, int N, int S, int32_t *sys_start, int32_t *sys_end,
                int32_t *status, cudaStream_t st) {
-    k_sys_bounds<<<(N + 255) / 256, 256, 0, st>>>(batch, N, S, sys_start, sys_end, status);
+    k_sys_bounds<<<(N + 255) / 256, 256, 0, st>>>(batch, N, S, sys_start, sys_end, status, nullptr);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
@@ -144,7 +159,9 @@ int sys_bounds(const int32_t *batch, int N, int S, int32_t *sys_start, int32_t *
 // One block per system: bounding box, finiteness, box checks and cell grid.
 __global__ void k_sys_setup(const float *__restrict__ pos, const float *__restrict__ box, float cutoff,
                             const int32_t *__restrict__ sys_start, const int32_t *__restrict__ sys_end,
-                            SysInfo *__restrict__ info, int32_t *__restrict__ ncell, int32_t *status) {
+                            SysInfo *__restrict__ info, int32_t *__restrict__ ncell, int32_t *status,
+                            const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int s = blockIdx.x;
     const int a0 = sys_start[s], a1 = sys_end[s];
     float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
@@ -243,7 +260,9 @@ __device__ __forceinline__ int axis_cell(float x, int k, const SysInfo &s) {
 
 __global__ void k_bin(const float *__restrict__ pos, const int32_t *__restrict__ batch, int N,
                       const SysInfo *__restrict__ info, const int32_t *__restrict__ cell_off,
-                      int32_t *__restrict__ cell_of, int32_t *__restrict__ cell_count, int64_t cells) {
+                      int32_t *__restrict__ cell_of, int32_t *__restrict__ cell_count, int64_t cells,
+                      const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int b = batch ? batch[n] : 0;
@@ -258,7 +277,8 @@ __global__ void k_bin(const float *__restrict__ pos, const int32_t *__restrict__
 
 __global__ void k_scatter(const float *__restrict__ pos, int N, const int32_t *__restrict__ cell_of,
                           const int32_t *__restrict__ cell_start, int32_t *__restrict__ cell_fill,
-                          int32_t *__restrict__ sorted, float4 *__restrict__ spos) {
+                          int32_t *__restrict__ sorted, float4 *__restrict__ spos, const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     const int c = cell_of[n];
@@ -326,7 +346,8 @@ __device__ __forceinline__ void for_candidates(int i, const float *__restrict__ 
 __global__ void k_pair_count(const float *__restrict__ pos, const int32_t *__restrict__ batch, int N,
                              const SysInfo *__restrict__ info, const int32_t *__restrict__ cell_off,
                              const int32_t *__restrict__ cell_start, const float4 *__restrict__ spos,
-                             float rc2, int32_t *__restrict__ rowcnt) {
+                             float rc2, int32_t *__restrict__ rowcnt, const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (i >= N) return;
     int cnt = 0;
@@ -336,7 +357,9 @@ __global__ void k_pair_count(const float *__restrict__ pos, const int32_t *__res
     if ((threadIdx.x & 31) == 0) rowcnt[i] = cnt;
 }
 
-__global__ void k_cap_check(const int64_t *__restrict__ n_pairs, int64_t cap, int32_t *status) {
+__global__ void k_cap_check(const int64_t *__restrict__ n_pairs, int64_t cap, int32_t *status,
+                            const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     if (*n_pairs > cap) set_status(status, TNET_ERR_CAPACITY);
 }
 
@@ -346,7 +369,9 @@ __global__ void __launch_bounds__(kFillWarps * 32)
 k_pair_fill(const float *__restrict__ pos, const int32_t *__restrict__ batch, int N,
             const SysInfo *__restrict__ info, const int32_t *__restrict__ cell_off,
             const int32_t *__restrict__ cell_start, const float4 *__restrict__ spos, float rc2,
-            const int32_t *__restrict__ row_ptr, int32_t *__restrict__ col, int64_t cap) {
+            const int32_t *__restrict__ row_ptr, int32_t *__restrict__ col, int64_t cap,
+            const int32_t *__restrict__ gate) {
+    if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     __shared__ int32_t buf[kFillWarps][kMaxRowSorted];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kFillWarps + w;
@@ -405,7 +430,7 @@ k_pair_fill(const float *__restrict__ pos, const int32_t *__restrict__ batch, in
 
 int neighbors_impl(tnet_ctx *ctx, int N, int S, const float *pos, const int32_t *batch,
                    const float *box, float cutoff, int32_t *row_ptr, int32_t *col, int64_t cap,
-                   int64_t *n_pairs_dev, int32_t *status, cudaStream_t st) {
+                   int64_t *n_pairs_dev, int32_t *status, cudaStream_t st, const int32_t *gate) {
     const Layout &L = ctx->lay;
     int32_t *sys_start = wsp<int32_t>(ctx, L.sys_start), *sys_end = wsp<int32_t>(ctx, L.sys_end);
     SysInfo *info = wsp<SysInfo>(ctx, L.sysinfo);
@@ -419,44 +444,54 @@ int neighbors_impl(tnet_ctx *ctx, int N, int S, const float *pos, const int32_t 
     ProfSeq pf(ctx, st);
     pf.mark(P_NBR);
 
-    TNET_CUDA_TRY(cudaMemsetAsync(sys_start, 0, sizeof(int32_t) * S, st));
-    TNET_CUDA_TRY(cudaMemsetAsync(sys_end, 0, sizeof(int32_t) * S, st));
-    TNET_CUDA_TRY(cudaMemsetAsync(cell_count, 0, sizeof(int32_t) * (cells + 1), st));
-    TNET_CUDA_TRY(cudaMemsetAsync(cell_fill, 0, sizeof(int32_t) * cells, st));
+    auto zero = [&](int32_t *p, int64_t n) -> int {
+        if (!gate) {
+            TNET_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof(int32_t) * n, st));
+            return TNET_OK;
+        }
+        k_zero_i32<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(p, n, gate);
+        count_launch();
+        return TNET_OK;
+    };
+    int zrc = zero(sys_start, S);
+    if (!zrc) zrc = zero(sys_end, S);
+    if (!zrc) zrc = zero(cell_count, cells + 1LL);
+    if (!zrc) zrc = zero(cell_fill, cells);
+    if (zrc) return zrc;
     if (N > 0) {
-        k_sys_bounds<<<(N + 255) / 256, 256, 0, st>>>(batch, N, S, sys_start, sys_end, status);
+        k_sys_bounds<<<(N + 255) / 256, 256, 0, st>>>(batch, N, S, sys_start, sys_end, status, gate);
         count_launch();
         TNET_LAUNCH_CHECK();
     }
-    k_sys_setup<<<S, 256, 0, st>>>(pos, box, cutoff, sys_start, sys_end, info, ncell, status);
+    k_sys_setup<<<S, 256, 0, st>>>(pos, box, cutoff, sys_start, sys_end, info, ncell, status, gate);
     count_launch();
     TNET_LAUNCH_CHECK();
-    int rc = scan_exclusive_i32(ncell, ncell, S, tmp, nullptr, nullptr, st);
+    int rc = scan_exclusive_i32(ncell, ncell, S, tmp, nullptr, nullptr, st, gate);
     if (rc) return rc;
     if (N > 0) {
-        k_bin<<<(N + 255) / 256, 256, 0, st>>>(pos, batch, N, info, ncell, cell_of, cell_count, cells);
+        k_bin<<<(N + 255) / 256, 256, 0, st>>>(pos, batch, N, info, ncell, cell_of, cell_count, cells, gate);
         count_launch();
         TNET_LAUNCH_CHECK();
     }
-    rc = scan_exclusive_i32(cell_count, cell_start, cells, tmp, nullptr, nullptr, st);
+    rc = scan_exclusive_i32(cell_count, cell_start, cells, tmp, nullptr, nullptr, st, gate);
     if (rc) return rc;
     if (N > 0) {
-        k_scatter<<<(N + 255) / 256, 256, 0, st>>>(pos, N, cell_of, cell_start, cell_fill, sorted, spos);
+        k_scatter<<<(N + 255) / 256, 256, 0, st>>>(pos, N, cell_of, cell_start, cell_fill, sorted, spos, gate);
         count_launch();
         TNET_LAUNCH_CHECK();
         k_pair_count<<<(int)(((int64_t)N * 32 + 255) / 256), 256, 0, st>>>(
-            pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, rowcnt);
+            pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, rowcnt, gate);
         count_launch();
         TNET_LAUNCH_CHECK();
     }
-    rc = scan_exclusive_i32(rowcnt, row_ptr, N, tmp, nullptr, n_pairs_dev, st);
+    rc = scan_exclusive_i32(rowcnt, row_ptr, N, tmp, nullptr, n_pairs_dev, st, gate);
     if (rc) return rc;
-    k_cap_check<<<1, 1, 0, st>>>(n_pairs_dev, cap, status);
+    k_cap_check<<<1, 1, 0, st>>>(n_pairs_dev, cap, status, gate);
     count_launch();
     TNET_LAUNCH_CHECK();
     if (N > 0) {
         k_pair_fill<<<(N + kFillWarps - 1) / kFillWarps, kFillWarps * 32, 0, st>>>(
-            pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, row_ptr, col, cap);
+            pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, row_ptr, col, cap, gate);
         count_launch();
         TNET_LAUNCH_CHECK();
     }

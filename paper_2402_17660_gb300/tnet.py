@@ -176,6 +176,12 @@ class TensorNet:
                                          _stream(self.device)), "tnet_md_step")
         return e_kin, e_pot
 
+    def md_rebuilds(self) -> int:
+        """Neighbor-list builds of the last md() call (waits for the device)."""
+        n = ctypes.c_int64()
+        _lib.check(self.lib.tnet_md_rebuilds(self.ctx, ctypes.byref(n)), "tnet_md_rebuilds")
+        return int(n.value)
+
 
 class EnergyFn(torch.autograd.Function):
     """E_s(pos, weights) with gradients from libtnet's reverse pass.

@@ -82,3 +82,27 @@ def test_energy_conservation_short_run():
     fluct = np.std(ke) / s.n_atoms
     print(f"E_tot drift per atom over 50 fs: {drift:.3e} eV; KE fluctuation per atom {fluct:.3e} eV")
     assert drift < max(0.05 * np.std(ke), 1e-3 * s.n_atoms) / s.n_atoms
+
+
+def test_triggered_rebuilds_make_the_trajectory_schedule_independent():
+    """A thin skin forces displacement-triggered rebuilds between the
+    periodic ones; every list then holds all pairs within the cutoff, and
+    only active pairs enter the sums, so the trajectory equals the one with
+    a fresh cutoff list in every step, bit for bit."""
+    s = synth.workload("water3000")
+    m = make_model(W, s, max_pairs=300000)
+    z, pos, vel, inv_m, box = _state(s)
+    pa, va = pos.clone(), vel.clone()
+    pb, vb = pos.clone(), vel.clone()
+    m.reset_status()
+    eka, epa = m.md(z, inv_m, pa, va, box, 0.5, 0.2, 20, 40)
+    n_a = m.md_rebuilds()
+    ekb, epb = m.md(z, inv_m, pb, vb, box, 0.5, 0.0, 1, 40)
+    n_b = m.md_rebuilds()
+    torch.cuda.synchronize()
+    m.check_status("md")
+    assert n_b == 41                   # the initial build plus one per step
+    assert 3 < n_a < 41                # periodic (2) + initial + triggered ones
+    assert torch.equal(pa, pb) and torch.equal(va, vb)
+    assert torch.equal(epa, epb) and torch.equal(eka, ekb)
+
