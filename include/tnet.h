@@ -204,6 +204,13 @@ int tnet_md_step(tnet_ctx *ctx, const float *weights, int n_atoms, const int32_t
  * Synchronous: waits for the device.  count: host pointer. */
 int tnet_md_rebuilds(tnet_ctx *ctx, int64_t *count);
 
+/* Copy of the neighbor list tnet_md_step keeps in the context (CSR at
+ * cutoff_upper + skin, built at the last rebuild of the last call), stream-
+ * ordered on `stream`: row_ptr [n_atoms+1] and col [min(n_pairs, cap)] device
+ * buffers of the caller, n_pairs a device int64. */
+int tnet_md_neighbor_list(tnet_ctx *ctx, int n_atoms, int32_t *row_ptr, int32_t *col, int64_t cap,
+                          int64_t *n_pairs, tnet_stream_t stream);
+
 /* ---- allocation-free neighbor search (no counterpart in the paper) -------
  * For callers that cannot allocate device memory (code inside another
  * framework's memory pool or a real-time loop that forbids cudaMalloc after
@@ -231,10 +238,11 @@ int tnet_neighbors_noalloc(int n_atoms, int n_systems, const float *pos, const i
  * <= 512.  Bounded in-kernel waits report TNET_ERR_TIMEOUT in *status_dev. */
 int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void *B, float *C, int32_t *status_dev,
                        tnet_stream_t stream);
-/* The same in 3xTF32: A [M][K], B [N][K] float32; A_lo, B_lo are caller
- * scratch of the same sizes that receive the TF32 residuals; K a multiple of
- * 4, N a multiple of 4 and <= 512. */
-int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const float *B, float *A_lo, float *B_lo, float *C,
+/* The same in 3xTF32: A [M][K], B [N][K] float32; B_split is caller scratch
+ * of 2*N*K floats that receives B's TF32 split (high parts, then the rounded
+ * remainders; A's split is formed inside the kernel); K a multiple of 4, N a
+ * multiple of 4 and <= 512. */
+int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const float *B, float *B_split, float *C,
                            int32_t *status_dev, tnet_stream_t stream);
 
 /* ---- tuning (no counterpart in the paper) ---------------------------------

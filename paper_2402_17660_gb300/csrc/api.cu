@@ -54,6 +54,7 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->rowcnt = take(i * (N + 1));
     L->scan_tmp = take(i * (big / 4096 + 16));
     // graph prep
+    L->rp_safe = take(i * (N + 1));
     L->rev = take(i * E);
     L->pair_of = take(i * E);
     L->uedge = take(8 * U);
@@ -133,11 +134,13 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->wpart_floats = 4LL << 20;
     L->wpart = take(f * L->wpart_floats);
     L->w3p = take(f * (NL > 0 ? NL : 1) * (6LL * F * F + 3 * F));
-    // tensor-core modes: weight operands (bf16 forward + transposed copies, or
-    // fp32 residuals + transposed high parts), one node-tensor operand copy and
-    // the per-pair radial-MLP operand copies (bf16 or fp32 TF32 residuals)
+    // tensor-core modes: weight operands (bf16 forward + transposed copies,
+    // or fp32 TF32 residuals + transposed high parts; the 3xTF32 GEMMs of the
+    // BF16 mode use the latter), and in BF16 mode the bf16 copies of the node
+    // tensor and radial-MLP activations the BF16 GEMMs read (3xTF32 reads the
+    // fp32 activations themselves)
     const int prec = d->precision;
-    const int64_t esz = prec == 1 ? 2 : (prec == 2 ? 4 : 0);
+    const int64_t esz = prec == 1 ? 2 : 0;
     int64_t nw = 0;
     {
         nw += Z * F + F * 2 * F + F + 3 * F * K + 3 * F + 2 * F + 2 * F * F + 2 * F + 3 * F * 2 * F + 3 * F +
@@ -145,7 +148,7 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
         nw += NL * (F * K + F + 2 * F * F + 2 * F + 3 * F * 2 * F + 3 * F + 6 * F * F);
         nw += 6 * F + F * 3 * F + F + F / 2 * F + F / 2 + F / 2 + 1;
     }
-    L->wbf_bytes = prec ? 3 * nw * esz + 128 * 256 : 0;
+    L->wbf_bytes = prec ? 3 * nw * 4 + 128 * 256 : 0;
     L->wbf = take(L->wbf_bytes);
     L->nbf = take(esz * n9);
     L->eu_bf = 0;
@@ -390,10 +393,25 @@ int tnet_md_step(tnet_ctx *c, const float *w, int N, const int32_t *z, const flo
                  double *e_kin, double *e_pot, int32_t *status, tnet_stream_t stream) {
     int rc = check_common(c, N, 1, pos, status);
     if (rc) return rc;
-    if (!w || !z || !inv_mass || !vel || !e_kin || !e_pot) return TNET_ERR_ARG;
+    if (!w || !z || !inv_mass || !vel || (n_steps > 0 && (!e_kin || !e_pot))) return TNET_ERR_ARG;
     if (!(dt > 0.f) || !(skin >= 0.f) || rebuild_every < 1 || n_steps < 0) return TNET_ERR_ARG;
     return md_impl(c, w, N, z, inv_mass, pos, vel, box, dt, skin, rebuild_every, n_steps, e_kin, e_pot,
                    status, (cudaStream_t)stream);
+}
+
+int tnet_md_neighbor_list(tnet_ctx *c, int N, int32_t *row_ptr, int32_t *col, int64_t cap, int64_t *n_pairs,
+                          tnet_stream_t stream) {
+    if (!c || !row_ptr || !n_pairs || N < 1 || N > c->max_atoms || cap < 0 || (cap > 0 && !col)) return TNET_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const Layout &L = c->lay;
+    TNET_CUDA_TRY(cudaMemcpyAsync(row_ptr, wsp<int32_t>(c, L.md_row_ptr), sizeof(int32_t) * (N + 1),
+                                  cudaMemcpyDeviceToDevice, st));
+    TNET_CUDA_TRY(cudaMemcpyAsync(n_pairs, wsp<int64_t>(c, L.md_npairs), sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                                  st));
+    const int64_t n = cap < c->max_pairs ? cap : c->max_pairs;
+    if (n > 0)
+        TNET_CUDA_TRY(cudaMemcpyAsync(col, wsp<int32_t>(c, L.md_col), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+    return TNET_OK;
 }
 
 int tnet_md_rebuilds(tnet_ctx *c, int64_t *count) {

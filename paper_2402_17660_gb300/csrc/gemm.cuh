@@ -37,7 +37,7 @@ struct GemmShape {
 // --------------------------------------------------------------- epilogues
 // Each epilogue receives 4 consecutive columns (n..n+3, all < N) of row m by
 // value (a pointer would force the accumulator fragment into local memory).
-// Optional operand copies (bf16 or TF32 residual) feed the tensor-core GEMMs.
+// Optional bf16 operand copies feed the BF16 tensor-core GEMMs.
 __device__ __forceinline__ void store_copy4(const OpCopy &c, int64_t idx, const float o[4]) {
     if (c.mode == 1) {
         __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]), b = __floats2bfloat162_rn(o[2], o[3]);
@@ -45,9 +45,6 @@ __device__ __forceinline__ void store_copy4(const OpCopy &c, int64_t idx, const 
         u.x = *reinterpret_cast<uint32_t *>(&a);
         u.y = *reinterpret_cast<uint32_t *>(&b);
         *reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(c.p) + idx) = u;
-    } else if (c.mode == 2) {
-        *reinterpret_cast<float4 *>(static_cast<float *>(c.p) + idx) =
-            make_float4(tf32_residual(o[0]), tf32_residual(o[1]), tf32_residual(o[2]), tf32_residual(o[3]));
     }
 }
 

@@ -96,19 +96,29 @@ __device__ __forceinline__ void store_coords(float *__restrict__ T, int n, int c
     for (int k = 0; k < 5; ++k) pS[(int64_t)k * F] = v[4 + k];
 }
 
-// Operand copy written next to an FP32 result for the tensor-core GEMMs:
-// mode 1 = bf16 copy (BF16 mode), mode 2 = its TF32 residual x - tf32(x) in
-// fp32 (3xTF32 mode, where x itself serves as the TF32 high part).
+// Operand copy written next to an FP32 result for the BF16 tensor-core GEMMs
+// (mode 1: a bf16 copy; mode 0: none).  The 3xTF32 GEMMs read the fp32
+// result itself and form its TF32 residual in shared memory.
 struct OpCopy {
     void *p;
     int mode;
 };
-__device__ __forceinline__ float tf32_residual(float x) {
-    return x - __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+// Split of an fp32 value for 3xTF32: hi = x rounded to the nearest TF32
+// value (PTX cvt.rna.tf32.f32: 10 explicit mantissa bits), lo = x - hi
+// (exact in fp32, |lo| <= 2^-11 |x|) rounded to TF32 in turn.  Both halves are
+// TF32-representable, so the tensor core reads them exactly, and
+// hi + lo = x within 2^-22 |x|.
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ void tf32_split(float x, float &hi, float &lo) {
+    hi = tf32_round(x);
+    lo = tf32_round(__fsub_rn(x, hi));
 }
 __device__ __forceinline__ void opcopy_store(const OpCopy &c, int64_t idx, float v) {
     if (c.mode == 1) static_cast<__nv_bfloat16 *>(c.p)[idx] = __float2bfloat16_rn(v);
-    else if (c.mode == 2) static_cast<float *>(c.p)[idx] = tf32_residual(v);
 }
 __device__ __forceinline__ void store_coords_cp(const OpCopy &T, int n, int c, int N, int F, const float v[9]) {
     if (!T.mode) return;
@@ -233,11 +243,22 @@ __device__ __forceinline__ void silu_and_grad_f(float x, float &v, float &d) {
 // ------------------------------------------------------------- geometry ---
 // Nearest periodic image of a pair vector for a rectangular box; L = 0 along
 // an axis means that axis is not periodic.
+// Pair geometry with every rounding fixed (the _rn intrinsics are never
+// contracted into FMAs): kernels that decide the same pair independently (the
+// neighbor count and fill passes, the model's upper-pair count and
+// assignment) then agree even for a pair within an ulp of the cutoff, and
+// r_ji is exactly -r_ij.
+__device__ __forceinline__ float mic1(float x, float L) {
+    return __fsub_rn(x, __fmul_rn(L, rintf(__fdiv_rn(x, L))));
+}
+__device__ __forceinline__ float norm2_rn(float x, float y, float z) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
+}
 __device__ __forceinline__ void mic(float &x, float &y, float &z, const SysInfo &s) {
     if (s.pbc) {
-        x -= s.L[0] * rintf(x / s.L[0]);
-        y -= s.L[1] * rintf(y / s.L[1]);
-        z -= s.L[2] * rintf(z / s.L[2]);
+        x = mic1(x, s.L[0]);
+        y = mic1(y, s.L[1]);
+        z = mic1(z, s.L[2]);
     }
 }
 
@@ -272,7 +293,7 @@ struct Layout {
     size_t sys_start, sys_end, sysinfo, sys_ncell, cell_count, cell_start, cell_fill, cell_of,
         sorted, spos, rowcnt, scan_tmp;
     // energy / forces: graph bookkeeping
-    size_t rev, pair_of, uedge, ucnt, nu;
+    size_t rev, pair_of, uedge, ucnt, nu, rp_safe;
     // node buffers
     size_t Ta, Tb, Xraw, Uemb, n0, as1, hs1, as2, s, ln0;
     size_t Xin, qn, Xn, Y, M, Tn, dX;  // per layer (stride given below)

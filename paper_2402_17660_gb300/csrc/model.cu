@@ -82,18 +82,19 @@ __device__ __forceinline__ float block_sum(float v, float *sm) {
     return t;
 }
 
-// pair vector r_ij = mic(r_i - r_j) for rectangular boxes (box rows diagonal)
+// pair vector r_ij = mic(r_i - r_j) for rectangular boxes (box rows diagonal),
+// with fixed rounding (see mic1)
 __device__ __forceinline__ void pair_vec(const float *__restrict__ pos, const float *__restrict__ box,
                                          const int32_t *__restrict__ batch, int i, int j, float &x,
                                          float &y, float &zz) {
-    x = pos[3LL * i] - pos[3LL * j];
-    y = pos[3LL * i + 1] - pos[3LL * j + 1];
-    zz = pos[3LL * i + 2] - pos[3LL * j + 2];
+    x = __fsub_rn(pos[3LL * i], pos[3LL * j]);
+    y = __fsub_rn(pos[3LL * i + 1], pos[3LL * j + 1]);
+    zz = __fsub_rn(pos[3LL * i + 2], pos[3LL * j + 2]);
     if (box) {
         const float *B = box + 9LL * (batch ? batch[i] : 0);
-        x -= B[0] * rintf(x / B[0]);
-        y -= B[4] * rintf(y / B[4]);
-        zz -= B[8] * rintf(zz / B[8]);
+        x = mic1(x, B[0]);
+        y = mic1(y, B[4]);
+        zz = mic1(zz, B[8]);
     }
 }
 
@@ -143,7 +144,7 @@ __global__ void k_upper_count(const float *__restrict__ pos, const float *__rest
             if (j > i && j < N) {
                 float x, y, zz;
                 pair_vec(pos, box, batch, i, j, x, y, zz);
-                up = sqrtf(x * x + y * y + zz * zz) < rc;
+                up = sqrtf(norm2_rn(x, y, zz)) < rc;
             }
         }
         cnt += __popc(__ballot_sync(0xffffffffu, up));
@@ -169,7 +170,7 @@ __global__ void k_upper_assign(const float *__restrict__ pos, const float *__res
             if (j > i && j < N) {
                 float x, y, zz;
                 pair_vec(pos, box, batch, i, j, x, y, zz);
-                up = sqrtf(x * x + y * y + zz * zz) < rc;
+                up = sqrtf(norm2_rn(x, y, zz)) < rc;
             }
         }
         const unsigned m = __ballot_sync(0xffffffffu, up);
@@ -212,7 +213,7 @@ __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restric
         const int2 p = uij[u];
         float x, y, zz;
         pair_vec(pos, box, batch, p.x, p.y, x, y, zz);
-        const float d = sqrtf(x * x + y * y + zz * zz);
+        const float d = sqrtf(norm2_rn(x, y, zz));
         const float phi = cutoff_phi(d, rp);
         float e, de;
         expnorm_k(d, k, rp, phi, 0.f, e, de);
@@ -253,7 +254,7 @@ __device__ __forceinline__ EdgeGeo edge_geo(const float *__restrict__ pos, const
     g.j = j;
     float x, y, zz;
     pair_vec(pos, box, batch, i, j, x, y, zz);
-    g.d = sqrtf(x * x + y * y + zz * zz);
+    g.d = sqrtf(norm2_rn(x, y, zz));
     g.active = (g.d < rp.rc) && (g.d > 0.f);
     const float inv = g.d > 0.f ? 1.0f / g.d : 0.f;
     g.u[0] = x * inv; g.u[1] = y * inv; g.u[2] = zz * inv;
@@ -893,7 +894,7 @@ __global__ void k_emb_bwd(const float *__restrict__ pos, const float *__restrict
             const int j = col[e];
             float x, y, zz;
             pair_vec(pos, box, batch, i, j, x, y, zz);
-            const float d = sqrtf(x * x + y * y + zz * zz);
+            const float d = sqrtf(norm2_rn(x, y, zz));
             const float inv = 1.0f / d;
             const float ux = x * inv, uy = y * inv, uz = zz * inv;
             const float phi = cutoff_phi(d, rp);
@@ -986,7 +987,7 @@ __global__ void k_emb_bwd_pairs(const float *__restrict__ pos, const float *__re
         const int i = p.x, j = p.y;
         float x, y, zz;
         pair_vec(pos, box, batch, i, j, x, y, zz);
-        const float d = sqrtf(x * x + y * y + zz * zz);
+        const float d = sqrtf(norm2_rn(x, y, zz));
         const float inv = 1.0f / d;
         const float ux = x * inv, uy = y * inv, uz = zz * inv;
         const float phi = cutoff_phi(d, rp);
@@ -1069,7 +1070,7 @@ __global__ void k_pair_vec(const float *__restrict__ pos, const float *__restric
         const int2 p = uij[u];
         float x, y, zz;
         pair_vec(pos, box, batch, p.x, p.y, x, y, zz);
-        const float d = sqrtf(x * x + y * y + zz * zz);
+        const float d = sqrtf(norm2_rn(x, y, zz));
         const float phi = cutoff_phi(d, rp), dphi = cutoff_dphi(d, rp);
         float s = 0.f;
         for (int k = lane; k < rp.K; k += 32) {
@@ -1209,14 +1210,15 @@ __global__ void k_filter_rows(const __grid_constant__ FilterRows R, int F, float
 
 // Weight operands of the tensor-core modes: job j reads a [rows][cols] float
 // matrix (transposed when tr[j], for backward operands) and writes a bf16
-// copy (mode 1) or an fp32 high part (if hi[j]) and TF32 residual (mode 2).
+// copy (mode[j] = 1) or its TF32 split hi + lo (mode[j] = 2, the 3xTF32
+// GEMMs).
 constexpr int kMaxCvtJobs = 128;
 struct CvtJobs {
     const float *src[kMaxCvtJobs];
     void *hi[kMaxCvtJobs];
     void *lo[kMaxCvtJobs];
-    int rows[kMaxCvtJobs], cols[kMaxCvtJobs], tr[kMaxCvtJobs];
-    int n, mode;
+    int rows[kMaxCvtJobs], cols[kMaxCvtJobs], tr[kMaxCvtJobs], mode[kMaxCvtJobs];
+    int n;
 };
 struct WOp {  // a weight operand: bf16 matrix, or fp32 high part + residual
     const void *b;
@@ -1230,11 +1232,13 @@ __global__ void k_cvt_weights(const __grid_constant__ CvtJobs J) {
         const int r = t / C, c = t % C;
         const float v = J.src[j][t];
         const int64_t o = J.tr[j] ? (int64_t)c * R + r : (int64_t)t;
-        if (J.mode == 1) {
+        if (J.mode[j] == 1) {
             static_cast<__nv_bfloat16 *>(J.hi[j])[o] = __float2bfloat16_rn(v);
         } else {
-            if (J.hi[j]) static_cast<float *>(J.hi[j])[o] = v;
-            static_cast<float *>(J.lo[j])[o] = tf32_residual(v);
+            float hi, lo;
+            tf32_split(v, hi, lo);
+            static_cast<float *>(J.hi[j])[o] = hi;
+            static_cast<float *>(J.lo[j])[o] = lo;
         }
     }
 }
@@ -1275,9 +1279,27 @@ static inline int grid_for(int64_t n, int threads, int num_sms) {
         if (rc_) return rc_;        \
     } while (0)
 
+// Row offsets clamped to [0, cap] (cap = the context's pair capacity, which
+// sizes every per-edge buffer): a caller's CSR can then never send a kernel
+// outside those buffers.  Offsets outside the range or decreasing are
+// reported as ARG (or CAPACITY when they pass the capacity).
+__global__ void k_rows_in_range(const int32_t *__restrict__ row_ptr, int N, int64_t cap,
+                                int32_t *__restrict__ safe, int32_t *status) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = row_ptr[t];
+        int32_t w = v < 0 ? 0 : v;
+        if (w > cap) {
+            w = (int32_t)cap;
+            set_status(status, TNET_ERR_CAPACITY);
+        }
+        if (v < 0 || (t == 0 && v != 0) || (t > 0 && row_ptr[t - 1] > v)) set_status(status, TNET_ERR_ARG);
+        safe[t] = w;
+    }
+}
+
 int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const int32_t *z,
                        const float *pos, const int32_t *batch, const float *box,
-                       const int32_t *row_ptr, const int32_t *col, const float *seed,
+                       const int32_t *row_ptr_in, const int32_t *col, const float *seed,
                        double *energy, float *forces, float *grad_w, int32_t *status,
                        cudaStream_t st) {
     const tnet_model_desc &d = ctx->d;
@@ -1300,6 +1322,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     const int64_t wcap = Lw.wpart_floats;
     int32_t *sys_start = i32(Lw.sys_start), *sys_end = i32(Lw.sys_end);
     int32_t *rev = i32(Lw.rev), *pair_of = i32(Lw.pair_of), *ucnt = i32(Lw.ucnt);
+    // every kernel below reads the clamped copy of the row offsets
+    int32_t *row_ptr = i32(Lw.rp_safe);
+    k_rows_in_range<<<(N + 256) / 256 < 1024 ? (N + 256) / 256 : 1024, 256, 0, st>>>(row_ptr_in, N, ctx->max_pairs,
+                                                                                     row_ptr, status);
+    count_launch();
+    TNET_LAUNCH_CHECK();
     int32_t *nu = i32(Lw.nu), *ue = i32(Lw.ue);
     int2 *uij = wsp<int2>(ctx, Lw.uedge);
     float *Ta = f32(Lw.Ta), *Tb = f32(Lw.Tb);
@@ -1331,22 +1359,35 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     // FP32 activations h1, h2 are read by the FP32 and 3xTF32 GEMMs and by the
     // weight gradients; the BF16 GEMMs read only their bf16 copies
     const bool keep_h = prec != 1 || wg;
-    auto cp = [&](size_t off) { return OpCopy{tcm ? (void *)(ctx->ws + off) : nullptr, prec}; };
+    // bf16 operand copies (BF16 mode only: the 3xTF32 GEMMs read the fp32
+    // activations and form their residuals in shared memory)
+    auto cp = [&](size_t off) { return prec == 1 ? OpCopy{(void *)(ctx->ws + off), 1} : OpCopy{nullptr, 0}; };
     // (the num_rbf-wide operands e(d) and dE/df stay FP32, so they get no copy)
     const OpCopy none{nullptr, 0};
     const OpCopy nbf = cp(Lw.nbf), eu_cp = none, ga3_cp = cp(Lw.ga3_bf), ga2_cp = cp(Lw.ga2_bf), ga1_cp = none,
                  gfu_cp = none;
     // per-layer radial-MLP activations (and their operand copies)
-    const int64_t esz_cp = prec == 1 ? 2 : 4;
+    const int64_t esz_cp = 2;
     // slab of layer l (one shared slab when the reverse pass recomputes them)
     const bool keep_act = !d.recompute_edges;
     auto slab = [&](int l) { return keep_act ? (int64_t)l : 0; };
     auto h1_cp = [&](int l) { return cp(Lw.h1_bf + (size_t)(slab(l) * maxU * F * esz_cp)); };
     auto h2_cp = [&](int l) { return cp(Lw.h2_bf + (size_t)(slab(l) * maxU * 2 * F * esz_cp)); };
     struct LayerB {
-        WOp mlp2, mlp3, mlp2T, mlp3T, mix1, mix1T, mix2, mix2T;
+        WOp mlp2, mlp3, mlp2T, mlp3T, mix1, mix1T, mix2, mix2T, mlp1, mlp1T;
     } lb[8] = {};
     WOp emix{}, emixT{};
+    // 3xTF32 weight operands of the num_rbf-wide radial layers, in both
+    // tensor-core modes (rounding the narrow expnorm basis to bf16 costs more
+    // force accuracy than any other operand), and of the per-atom embedding
+    // and output MLPs in BF16 mode.  In the FP32-accurate mode those per-atom
+    // MLPs stay on FP32 FMA: they are cheap, and the energy is the quantity
+    // most sensitive to them (3xTF32 there costs an order of magnitude of
+    // energy accuracy).
+    const bool atom_x3 = prec == 1;
+    struct X3W {
+        WOp dproj, dprojT, emb_mlp1, emb_mlp1T, emb_mlp2, emb_mlp2T, out, outT, head1, head1T;
+    } wx{};
 
     // ---- graph prep
     ProfSeq pf(ctx, st);
@@ -1364,39 +1405,40 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     if (tcm) {
         CvtJobs J;
         J.n = 0;
-        J.mode = prec;
         char *wb = ctx->ws + Lw.wbf;
-        const int esz = prec == 1 ? 2 : 4;
         int64_t woff = 0;  // bytes
-        auto alloc = [&](int64_t elems) {
+        auto alloc = [&](int64_t elems, int esz) {
             void *p = wb + woff;
             woff += (elems * esz + 255) & ~(int64_t)255;
             return p;
         };
         // forward operands keep the (out, in) = K-major layout; backward
-        // operands are transposed.  3xTF32 uses the fp32 weights themselves as
-        // the high part of the forward operands.
-        auto job = [&](const float *src, int rows, int cols, int tr) {
+        // operands are transposed
+        auto job_m = [&](const float *src, int rows, int cols, int tr, int mode) {
             WOp w{};
-            void *hi = (prec == 1 || tr) ? alloc((int64_t)rows * cols) : nullptr;
-            void *lo = prec == 2 ? alloc((int64_t)rows * cols) : nullptr;
+            const int esz = mode == 1 ? 2 : 4;
+            void *hi = alloc((int64_t)rows * cols, esz);
+            void *lo = mode == 2 ? alloc((int64_t)rows * cols, esz) : nullptr;
             J.src[J.n] = src; J.hi[J.n] = hi; J.lo[J.n] = lo;
-            J.rows[J.n] = rows; J.cols[J.n] = cols; J.tr[J.n] = tr;
+            J.rows[J.n] = rows; J.cols[J.n] = cols; J.tr[J.n] = tr; J.mode[J.n] = mode;
             ++J.n;
-            w.b = hi ? hi : (const void *)src;
+            w.b = hi;
             w.blo = lo;
             return w;
         };
+        auto job = [&](const float *src, int rows, int cols, int tr) { return job_m(src, rows, cols, tr, prec); };
+        auto job3 = [&](const float *src, int rows, int cols, int tr) { return job_m(src, rows, cols, tr, 2); };
         // [3][F][F] -> per-class transposes; the three classes' high parts (and
         // residuals) must stay stacked contiguously [3F][F] for the GEMM
         auto job_classes_T = [&](const float *src) {
             const int64_t ff = (int64_t)F * F;
-            char *hi = (char *)alloc(3 * ff), *lo = prec == 2 ? (char *)alloc(3 * ff) : nullptr;
+            const int esz = prec == 1 ? 2 : 4;
+            char *hi = (char *)alloc(3 * ff, esz), *lo = prec == 2 ? (char *)alloc(3 * ff, esz) : nullptr;
             for (int q = 0; q < 3; ++q) {
                 J.src[J.n] = src + q * ff;
                 J.hi[J.n] = hi + q * ff * esz;
                 J.lo[J.n] = lo ? lo + q * ff * esz : nullptr;
-                J.rows[J.n] = F; J.cols[J.n] = F; J.tr[J.n] = 1;
+                J.rows[J.n] = F; J.cols[J.n] = F; J.tr[J.n] = 1; J.mode[J.n] = prec;
                 ++J.n;
             }
             return WOp{hi, lo};
@@ -1413,23 +1455,43 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             lb[l].mix1T = job_classes_T(Lr.mix1_w);
             lb[l].mix2 = job(Lr.mix2_w, 3 * F, F, 0);
             lb[l].mix2T = job_classes_T(Lr.mix2_w);
+            lb[l].mlp1 = job3(Lr.mlp1_w, F, K, 0);
+            lb[l].mlp1T = job3(Lr.mlp1_w, F, K, 1);
+        }
+        wx.dproj = job3(W.dproj_w, 3 * F, K, 0);
+        wx.dprojT = job3(W.dproj_w, 3 * F, K, 1);
+        if (atom_x3) {
+            wx.emb_mlp1 = job3(W.emb_mlp1_w, 2 * F, F, 0);
+            wx.emb_mlp1T = job3(W.emb_mlp1_w, 2 * F, F, 1);
+            wx.emb_mlp2 = job3(W.emb_mlp2_w, 3 * F, 2 * F, 0);
+            wx.emb_mlp2T = job3(W.emb_mlp2_w, 3 * F, 2 * F, 1);
+            wx.out = job3(W.out_w, F, 3 * F, 0);
+            wx.outT = job3(W.out_w, F, 3 * F, 1);
+            wx.head1 = job3(W.head1_w, H, F, 0);
+            wx.head1T = job3(W.head1_w, H, F, 1);
         }
         if (woff > Lw.wbf_bytes || J.n > kMaxCvtJobs) return TNET_ERR_WORKSPACE;
         k_cvt_weights<<<dim3(64, J.n), 256, 0, st>>>(J);
         count_launch();
         TNET_LAUNCH_CHECK();
     }
-    // tensor-core GEMM: A (fp32 A32 plus its copy) against weight operand w
+    // 3xTF32 tensor-core GEMM: fp32 A (split in the kernel) against weight
+    // operand w (its TF32 split)
+    auto tcx3 = [&](const tc::TcShape &P, const float *A32, int64_t a_rows, int64_t lda, const WOp &w,
+                    int64_t b_rows, int64_t ldb, const auto &epi, int bn = 0) -> int {
+        const tc::TcOperands o{A32, w.b, w.blo, a_rows, lda, b_rows, ldb};
+        if (P.N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st);
+        if (P.N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st);
+        if (P.N % 192 == 0 && bn != 128) return tc::tc_gemm_ops<192, true>(P, o, epi, status, st);
+        return tc::tc_gemm_ops<128, true>(P, o, epi, status, st);
+    };
+    // tensor-core GEMM of the mode: BF16 (A's bf16 copy) or 3xTF32 (A itself)
     auto tcg = [&](const tc::TcShape &P, const float *A32, const OpCopy &Acp, int64_t a_rows, int64_t lda,
                    const WOp &w, int64_t b_rows, int64_t ldb, const auto &epi, int bn = 0) -> int {
         if (prec == 1)
             return tc_any(P, (const __nv_bfloat16 *)Acp.p, a_rows, lda, (const __nv_bfloat16 *)w.b, b_rows, ldb,
                           epi, status, st, bn);
-        const tc::TcOperands o{A32, w.b, Acp.p, w.blo, a_rows, lda, b_rows, ldb};
-        if (P.N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st);
-        if (P.N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st);
-        if (P.N % 192 == 0 && bn != 128) return tc::tc_gemm_ops<192, true>(P, o, epi, status, st);
-        return tc::tc_gemm_ops<128, true>(P, o, epi, status, st);
+        return tcx3(P, A32, a_rows, lda, w, b_rows, ldb, epi, bn);
     };
     TNET_CUDA_TRY(cudaMemsetAsync(sys_start, 0, sizeof(int32_t) * S, st));
     TNET_CUDA_TRY(cudaMemsetAsync(sys_end, 0, sizeof(int32_t) * S, st));
@@ -1456,9 +1518,15 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         // expnorm basis values to bf16 costs more force accuracy than any
         // other operand
         const EpiBiasAct ep{W.dproj_b, nullptr, 0, fu, 3 * F, 0, nullptr};
-        GemmShape pp = gshape(maxU, 3 * F, K, eu, K, W.dproj_w, K);
-        pp.rows_dev = nu;
-        TRY(sgemm<false, true>(pp, ep, gctas, st));
+        if (tcm) {
+            tc::TcShape tp = tc::tshape(maxU, 3 * F, K);
+            tp.rows_dev = nu;
+            TRY(tcx3(tp, eu, maxU, K, wx.dproj, 3 * F, K, ep, bn3));
+        } else {
+            GemmShape pp = gshape(maxU, 3 * F, K, eu, K, W.dproj_w, K);
+            pp.rows_dev = nu;
+            TRY(sgemm<false, true>(pp, ep, gctas, st));
+        }
     }
 
     // ---- embedding
@@ -1474,10 +1542,17 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     pf.mark(P_EMB_NODE);
-    TRY(sgemm<false, true>(gshape(N, 2 * F, F, n0, F, W.emb_mlp1_w, F),
-                           EpiBiasAct{W.emb_mlp1_b, as1, 2 * F, hs1, 2 * F, 1, nullptr}, gctas, st));
-    TRY(sgemm<false, true>(gshape(N, 3 * F, 2 * F, hs1, 2 * F, W.emb_mlp2_w, 2 * F),
-                           EpiBiasAct{W.emb_mlp2_b, as2, 3 * F, s, 3 * F, 1, nullptr}, gctas, st));
+    {
+        const EpiBiasAct em1{W.emb_mlp1_b, as1, 2 * F, hs1, 2 * F, 1, nullptr};
+        const EpiBiasAct em2{W.emb_mlp2_b, as2, 3 * F, s, 3 * F, 1, nullptr};
+        if (atom_x3) {
+            TRY(tcx3(tc::tshape(N, 2 * F, F), n0, N, F, wx.emb_mlp1, 2 * F, F, em1, bn2));
+            TRY(tcx3(tc::tshape(N, 3 * F, 2 * F), hs1, N, 2 * F, wx.emb_mlp2, 3 * F, 2 * F, em2, bn3));
+        } else {
+            TRY(sgemm<false, true>(gshape(N, 2 * F, F, n0, F, W.emb_mlp1_w, F), em1, gctas, st));
+            TRY(sgemm<false, true>(gshape(N, 3 * F, 2 * F, hs1, 2 * F, W.emb_mlp2_w, 2 * F), em2, gctas, st));
+        }
+    }
     if (tcm) TRY(tcg(tc::tshape_classes(N, F), Xraw, nbf, 9LL * N, F, emix, 3 * F, F, EpiStore{Uemb, F, 0}));
     else TRY(sgemm<false, true>(gshape_classes(N, F, Xraw, W.emb_mix_w), EpiStore{Uemb, F, 0}, gctas, st));
     float *X = f32(Lw.Xin);  // layer 0 input
@@ -1498,10 +1573,10 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         if (tcm) {
             tc::TcShape t2 = tc::tshape(maxU, 2 * F, F), t3 = tc::tshape(maxU, 3 * F, 2 * F);
             t2.rows_dev = t3.rows_dev = nu;
-            pf.mark(P_MLP1);  // K = num_rbf: FP32 (see the projections above)
-            GemmShape p1 = gshape(maxU, F, K, eu, K, Lr.mlp1_w, K);
-            p1.rows_dev = nu;
-            TRY(sgemm<false, true>(p1, e1, gctas, st));
+            pf.mark(P_MLP1);  // K = num_rbf: 3xTF32 in both modes (see the projections above)
+            tc::TcShape t1 = tc::tshape(maxU, F, K);
+            t1.rows_dev = nu;
+            TRY(tcx3(t1, eu, maxU, K, lb[l].mlp1, F, K, e1));
             pf.mark(P_MLP2);
             TRY(tcg(t2, h1, h1_cp(l), maxU, F, lb[l].mlp2, 2 * F, F, e2, bn2));
             pf.mark(P_MLP3);
@@ -1564,10 +1639,17 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     k_out_norms<<<N, F, 0, st>>>(Xfin, N, F, W.out_ln_g, W.out_ln_b, h, hn, lno);
     count_launch();
     TNET_LAUNCH_CHECK();
-    TRY(sgemm<false, true>(gshape(N, F, 3 * F, hn, 3 * F, W.out_w, 3 * F),
-                           EpiBiasAct{W.out_b, ao, F, o, F, 1, nullptr}, gctas, st));
-    TRY(sgemm<false, true>(gshape(N, H, F, o, F, W.head1_w, F),
-                           EpiBiasAct{W.head1_b, at, H, t, H, 1, nullptr}, gctas, st));
+    {
+        const EpiBiasAct eo{W.out_b, ao, F, o, F, 1, nullptr};
+        const EpiBiasAct eh{W.head1_b, at, H, t, H, 1, nullptr};
+        if (atom_x3) {
+            TRY(tcx3(tc::tshape(N, F, 3 * F), hn, N, 3 * F, wx.out, F, 3 * F, eo));
+            TRY(tcx3(tc::tshape(N, H, F), o, N, F, wx.head1, H, F, eh));
+        } else {
+            TRY(sgemm<false, true>(gshape(N, F, 3 * F, hn, 3 * F, W.out_w, 3 * F), eo, gctas, st));
+            TRY(sgemm<false, true>(gshape(N, H, F, o, F, W.head1_w, F), eh, gctas, st));
+        }
+    }
     k_head<<<warps_grid, 256, 0, st>>>(t, N, H, W.head2_w, W.head2_b, Ei);
     count_launch();
     k_energy<<<S, 256, 0, st>>>(Ei, sys_start, sys_end, energy);
@@ -1583,8 +1665,13 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     k_head_bwd<<<grid_for((int64_t)N * H, 256, sms), 256, 0, st>>>(at, N, H, W.head2_w, seed, batch, gat);
     count_launch();
     TNET_LAUNCH_CHECK();
-    TRY(sgemm<false, false>(gshape(N, F, H, gat, H, W.head1_w, F), EpiGradAct{ao, F, gao, F, 0}, gctas, st));
-    TRY(sgemm<false, false>(gshape(N, 3 * F, F, gao, F, W.out_w, 3 * F), EpiStore{ghn, 3 * F, 0}, gctas, st));
+    if (atom_x3) {
+        TRY(tcx3(tc::tshape(N, F, H), gat, N, H, wx.head1T, F, H, EpiGradAct{ao, F, gao, F, 0}));
+        TRY(tcx3(tc::tshape(N, 3 * F, F), gao, N, F, wx.outT, 3 * F, F, EpiStore{ghn, 3 * F, 0}, bn3));
+    } else {
+        TRY(sgemm<false, false>(gshape(N, F, H, gat, H, W.head1_w, F), EpiGradAct{ao, F, gao, F, 0}, gctas, st));
+        TRY(sgemm<false, false>(gshape(N, 3 * F, F, gao, F, W.out_w, 3 * F), EpiStore{ghn, 3 * F, 0}, gctas, st));
+    }
     k_out_norms_bwd<<<N, F, 0, st>>>(Xfin, h, ghn, lno, W.out_ln_g, N, F, gX);
     count_launch();
     TNET_LAUNCH_CHECK();
@@ -1646,10 +1733,10 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             TRY(tcg(t3, gg, ga3_cp, maxU, 3 * F, lb[l].mlp3T, 2 * F, 3 * F, g3, bn2));
             pf.mark(P_MLP2_BWD);
             TRY(tcg(t2, ga2, ga2_cp, maxU, 2 * F, lb[l].mlp2T, F, 2 * F, g2));
-            pf.mark(P_MLP1_BWD);  // N = num_rbf: FP32 SIMT
-            GemmShape q1 = gshape(maxU, K, F, ga1, F, Lr.mlp1_w, K);
-            q1.rows_dev = nu;
-            TRY(sgemm<false, false>(q1, g1, gctas, st));
+            pf.mark(P_MLP1_BWD);  // N = num_rbf: 3xTF32 in both modes
+            tc::TcShape u1 = tc::tshape(maxU, K, F);
+            u1.rows_dev = nu;
+            TRY(tcx3(u1, ga1, maxU, F, lb[l].mlp1T, K, F, g1));
         } else {
             pf.mark(P_MLP3_BWD);
             GemmShape q3 = gshape(maxU, 2 * F, 3 * F, gg, 3 * F, w3p(l), 2 * F);
@@ -1692,9 +1779,15 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     k_emb_scale_bwd<<<ew, 256, 0, st>>>(gX, Uemb, s, as2, N, F, gU, gas2, nbf);
     count_launch();
     TNET_LAUNCH_CHECK();
-    TRY(sgemm<false, false>(gshape(N, 2 * F, 3 * F, gas2, 3 * F, W.emb_mlp2_w, 2 * F),
-                            EpiGradAct{as1, 2 * F, gas1, 2 * F, 0}, gctas, st));
-    TRY(sgemm<false, false>(gshape(N, F, 2 * F, gas1, 2 * F, W.emb_mlp1_w, F), EpiStore{gn0, F, 0}, gctas, st));
+    if (atom_x3) {
+        TRY(tcx3(tc::tshape(N, 2 * F, 3 * F), gas2, N, 3 * F, wx.emb_mlp2T, 2 * F, 3 * F,
+                 EpiGradAct{as1, 2 * F, gas1, 2 * F, 0}, bn2));
+        TRY(tcx3(tc::tshape(N, F, 2 * F), gas1, N, 2 * F, wx.emb_mlp1T, F, 2 * F, EpiStore{gn0, F, 0}));
+    } else {
+        TRY(sgemm<false, false>(gshape(N, 2 * F, 3 * F, gas2, 3 * F, W.emb_mlp2_w, 2 * F),
+                                EpiGradAct{as1, 2 * F, gas1, 2 * F, 0}, gctas, st));
+        TRY(sgemm<false, false>(gshape(N, F, 2 * F, gas1, 2 * F, W.emb_mlp1_w, F), EpiStore{gn0, F, 0}, gctas, st));
+    }
     if (tcm) TRY(tcg(tc::tshape_classes(N, F), gU, nbf, 9LL * N, F, emixT, 3 * F, F, EpiStore{gXraw, F, 0}));
     else TRY(sgemm<false, false>(gshape_classes(N, F, gU, W.emb_mix_w), EpiStore{gXraw, F, 0}, gctas, st));
     k_ln0_bwd<<<N, F, 0, st>>>(Xraw, gn0, ln0, W.emb_ln_g, N, F, gXraw);
@@ -1739,9 +1832,15 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     {   // dE/de of the pair's radial basis also flows through the projections
-        GemmShape pg = gshape(maxU, K, 3 * F, gfu, 3 * F, W.dproj_w, K);
-        pg.rows_dev = nu;
-        TRY(sgemm<false, false>(pg, EpiStore{ge, K, NL > 0}, gctas, st));
+        if (tcm) {
+            tc::TcShape tg = tc::tshape(maxU, K, 3 * F);
+            tg.rows_dev = nu;
+            TRY(tcx3(tg, gfu, maxU, 3 * F, wx.dprojT, K, 3 * F, EpiStore{ge, K, NL > 0}));
+        } else {
+            GemmShape pg = gshape(maxU, K, 3 * F, gfu, 3 * F, W.dproj_w, K);
+            pg.rows_dev = nu;
+            TRY(sgemm<false, false>(pg, EpiStore{ge, K, NL > 0}, gctas, st));
+        }
     }
     if (wg) {
         TRY(wgrad_outer(rows1(3 * F, K, maxU, gfu, 3 * F, eu, K, nu), wpart, wcap, gw(G.dproj_w), 0, sms, st));

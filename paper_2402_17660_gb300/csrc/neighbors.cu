@@ -333,9 +333,9 @@ __device__ __forceinline__ void for_candidates(int i, const float *__restrict__ 
                     if (p + lane < p1) {
                         const float4 q = spos[p + lane];
                         j = __float_as_int(q.w);
-                        float dx = xi - q.x, dy = yi - q.y, dz = zi - q.z;
+                        float dx = __fsub_rn(xi, q.x), dy = __fsub_rn(yi, q.y), dz = __fsub_rn(zi, q.z);
                         mic(dx, dy, dz, s);
-                        const float d2 = dx * dx + dy * dy + dz * dz;
+                        const float d2 = norm2_rn(dx, dy, dz);
                         ok = (j != i) && (d2 < rc2);
                     }
                     fn(j, ok);
@@ -357,10 +357,16 @@ __global__ void k_pair_count(const float *__restrict__ pos, const int32_t *__res
     if ((threadIdx.x & 31) == 0) rowcnt[i] = cnt;
 }
 
-__global__ void k_cap_check(const int64_t *__restrict__ n_pairs, int64_t cap, int32_t *status,
-                            const int32_t *__restrict__ gate) {
+// More pairs than the capacity: flag it (n_pairs keeps the required count)
+// and clamp the row offsets to the capacity, so that the truncated list
+// never sends a reader past the end of col.
+__global__ void k_cap_check(const int64_t *__restrict__ n_pairs, int64_t cap, int32_t *__restrict__ row_ptr, int N,
+                            int32_t *status, const int32_t *__restrict__ gate) {
     if (gate && *gate == 0) return;  // gated rebuild: nothing to do
-    if (*n_pairs > cap) set_status(status, TNET_ERR_CAPACITY);
+    if (*n_pairs <= cap) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, TNET_ERR_CAPACITY);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= N; t += (int64_t)gridDim.x * blockDim.x)
+        if (row_ptr[t] > cap) row_ptr[t] = (int32_t)cap;
 }
 
 constexpr int kFillWarps = 4;
@@ -381,15 +387,18 @@ k_pair_fill(const float *__restrict__ pos, const int32_t *__restrict__ batch, in
     int32_t *sb = buf[w];
     const bool in_smem = rlen <= kMaxRowSorted;
     int cnt = 0;
+    // rlen is the count pass's result, clamped when the list overflowed the
+    // capacity: write no more than that
     for_candidates(i, pos, batch, info, cell_off, cell_start, spos, rc2, [&](int j, bool ok) {
         const unsigned m = __ballot_sync(0xffffffffu, ok);
         const int slot = cnt + __popc(m & ((1u << lane) - 1u));
-        if (ok) {
+        if (ok && slot < rlen) {
             if (in_smem) sb[slot] = j;
-            else if (r0 + slot < cap) col[r0 + slot] = j;
+            else col[r0 + slot] = j;
         }
         cnt += __popc(m);
     });
+    cnt = cnt < rlen ? cnt : rlen;
     __syncwarp();
     if (in_smem) {
         int P = 1;
@@ -412,9 +421,8 @@ k_pair_fill(const float *__restrict__ pos, const int32_t *__restrict__ batch, in
                 __syncwarp();
             }
         }
-        for (int k = lane; k < cnt; k += 32)
-            if (r0 + k < cap) col[r0 + k] = sb[k];
-    } else if (lane == 0 && r0 + cnt <= cap) {
+        for (int k = lane; k < cnt; k += 32) col[r0 + k] = sb[k];
+    } else if (lane == 0) {
         // pathological row: sort in place in global memory
         for (int a = 1; a < cnt; ++a) {
             const int32_t v = col[r0 + a];
@@ -486,7 +494,8 @@ int neighbors_impl(tnet_ctx *ctx, int N, int S, const float *pos, const int32_t 
     }
     rc = scan_exclusive_i32(rowcnt, row_ptr, N, tmp, nullptr, n_pairs_dev, st, gate);
     if (rc) return rc;
-    k_cap_check<<<1, 1, 0, st>>>(n_pairs_dev, cap, status, gate);
+    k_cap_check<<<(N + 256) / 256 < 1024 ? (N + 256) / 256 : 1024, 256, 0, st>>>(n_pairs_dev, cap, row_ptr, N,
+                                                                                  status, gate);
     count_launch();
     TNET_LAUNCH_CHECK();
     if (N > 0) {

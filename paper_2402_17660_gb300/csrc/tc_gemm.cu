@@ -51,22 +51,22 @@ int make_map_f32(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, i
 
 using namespace tnet;
 
-// TF32X3 residuals of a float array (for the test entry point)
-__global__ void k_tf32_lo(const float *__restrict__ x, float *__restrict__ lo, int64_t n) {
+// TF32 split of the weights (for the test entry point)
+__global__ void k_tf32_split(const float *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo, int64_t n) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t < n) lo[t] = tc::tf32_lo(x[t]);
+    if (t < n) tf32_split(x[t], hi[t], lo[t]);
 }
 
-extern "C" int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const float *B, float *Alo, float *Blo,
-                                      float *Cout, int32_t *status, tnet_stream_t stream) {
-    if (M < 1 || N < 4 || N > 512 || K < 4 || K % 4 || N % 4 || !A || !B || !Alo || !Blo || !Cout) return TNET_ERR_ARG;
+extern "C" int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const float *B, float *Bsplit, float *Cout,
+                                      int32_t *status, tnet_stream_t stream) {
+    if (M < 1 || N < 4 || N > 512 || K < 4 || K % 4 || N % 4 || !A || !B || !Bsplit || !Cout) return TNET_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    k_tf32_lo<<<(int)(((int64_t)M * K + 255) / 256), 256, 0, st>>>(A, Alo, (int64_t)M * K);
-    k_tf32_lo<<<(int)(((int64_t)N * K + 255) / 256), 256, 0, st>>>(B, Blo, (int64_t)N * K);
+    const int64_t nk = (int64_t)N * K;
+    k_tf32_split<<<(int)((nk + 255) / 256), 256, 0, st>>>(B, Bsplit, Bsplit + nk, nk);
     TNET_LAUNCH_CHECK();
     tc::TcShape P = tc::tshape(M, N, K);
     EpiStore epi{Cout, N, 0};
-    const tc::TcOperands o{A, B, Alo, Blo, M, K, N, K};
+    const tc::TcOperands o{A, Bsplit, Bsplit + nk, M, K, N, K};
     if (N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st);
     if (N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st);
     if (N % 192 == 0) return tc::tc_gemm_ops<192, true>(P, o, epi, status, st);

@@ -8,18 +8,23 @@
 //
 // Two operand modes:
 //   BF16   A, B bf16; one kind::f16 MMA per k-step.
-//   TF32X3 A, B fp32 plus their TF32 residuals A_lo = A - tf32(A),
-//          B_lo = B - tf32(B) (fp32 arrays); three kind::tf32 MMAs per k-step,
-//          A B + A_lo B + A B_lo, which keeps FP32-level accuracy (the tensor
-//          core reads an fp32 operand as TF32 by dropping its low 13 mantissa
-//          bits, so A itself serves as tf32(A)).
+//   TF32X3 fp32 A and the weights' TF32 split B = B_hi + B_lo (two fp32
+//          arrays of TF32-representable values, see tf32_split); three
+//          kind::tf32 MMAs per k-step, A_hi B_hi + A_lo B_hi + A_hi B_lo,
+//          within about 3 * 2^-22 |a||b| per product of the fp32 product.
+//          A's split is formed in shared memory: two converter warps rewrite
+//          each landed A tile into A_hi (in place) and A_lo (a second buffer)
+//          at the same byte offsets (an elementwise map, so the 128-byte
+//          swizzle carries over), fence it for the async proxy and release
+//          the stage to the MMA warp.  No split of an activation ever goes
+//          through HBM.
 //
 // Persistent CTAs walk 128 x BN output tiles.  Warp 0 issues TMA loads into a
-// 4-stage shared-memory ring, warp 1 owns TMEM and issues the MMAs (K = 16
-// per instruction, four per 64-wide k-block) into one of two accumulators,
-// so the epilogue of a tile overlaps the MMAs of the next.  Sixteen epilogue
-// warps drain TMEM (warp w reads lanes 32*(w%4) .. +31, a quarter of the
-// tile's columns each) and run the fused epilogue.  Every mbarrier wait is bounded;
+// 2-4 stage shared-memory ring, warp 1 owns TMEM and issues the MMAs (four
+// 32-byte k-steps per 128-byte k-block) into one of two accumulators, so the
+// epilogue of a tile overlaps the MMAs of the next.  Sixteen epilogue warps
+// drain TMEM (warp w reads lanes 32*(w%4) .. +31, a quarter of the tile's
+// columns each) and run the fused epilogue.  Every mbarrier wait is bounded;
 // on expiry the kernel records TNET_ERR_TIMEOUT, the other roles stop, the
 // producer waits (bounded) for its own copies in flight, TMEM is freed and
 // the kernel returns.
@@ -32,7 +37,7 @@
 namespace tnet {
 namespace tc {
 
-constexpr int BM = 128, EPI_WARPS = 16, THREADS = 64 + 32 * EPI_WARPS;
+constexpr int BM = 128, EPI_WARPS = 16, CONV_WARPS = 2, THREADS = 64 + 32 * (EPI_WARPS + CONV_WARPS);
 constexpr int STG_LD = 20;  // floats per staged row (16 + pad, keeps float4 alignment)
 constexpr uint32_t kSpinLimit = 1u << 22;
 
@@ -148,8 +153,6 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accum)
         : "memory");
 }
-// TF32 residual of an fp32 value: x - (x with its low 13 mantissa bits cleared)
-__device__ __forceinline__ float tf32_lo(float x) { return tf32_residual(x); }
 
 template <int BN, bool X3 = false>
 struct TileCfg {
@@ -157,12 +160,13 @@ struct TileCfg {
     static constexpr int BKE = X3 ? 32 : 64;
     static constexpr uint32_t A_BYTES = BM * 128;
     static constexpr uint32_t B_BYTES = BN * 128;
-    // bytes per pipeline stage: A, B (+ A_lo, B_lo for TF32X3)
-    static constexpr uint32_t STAGE_TX = (X3 ? 2 : 1) * (A_BYTES + B_BYTES);
+    // bytes TMA brings per pipeline stage: A, B (+ B_lo for TF32X3; A_lo is
+    // formed in shared memory)
+    static constexpr uint32_t STAGE_TX = A_BYTES + (X3 ? 2 : 1) * B_BYTES;
     static constexpr int STAGES = X3 ? 2 : (BN >= 192 ? 3 : 4);
     static constexpr uint32_t TMEM_COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
     static constexpr uint32_t STAGE_BYTES = EPI_WARPS * 32 * STG_LD * 4;  // epilogue transpose buffers
-    static constexpr size_t SMEM = 1024 + STAGES * (size_t)STAGE_TX + 256 + STAGE_BYTES;
+    static constexpr size_t SMEM = 1024 + STAGES * (size_t)(STAGE_TX + (X3 ? A_BYTES : 0)) + 256 + STAGE_BYTES;
 };
 
 // Tile index -> (class, first row, first column); false past the last tile.
@@ -201,7 +205,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t *empty = full + STAGES;
     uint64_t *acc_full = empty + STAGES;
     uint64_t *acc_empty = acc_full + 2;
-    uint32_t *tmem_slot = (uint32_t *)(acc_empty + 2);
+    uint64_t *conv = acc_empty + 2;  // TF32X3: A_lo of the stage is ready
+    uint32_t *tmem_slot = (uint32_t *)(conv + STAGES);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     float *stage_all = (float *)((uint8_t *)full + 256);
 
@@ -225,6 +230,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
+            mbar_init(&conv[s], CONV_WARPS);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -256,10 +262,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const int yb = (int)(sel3(z, P.brow0[0], P.brow0[1], P.brow0[2]) + n0);
                     tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * BK, ya, &full[s]);
                     tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * BK, yb, &full[s]);
-                    if (X3) {
-                        tma_load_2d(sAlo + s * C::A_BYTES, &tmAlo, kb * BK, ya, &full[s]);
-                        tma_load_2d(sBlo + s * C::B_BYTES, &tmBlo, kb * BK, yb, &full[s]);
-                    }
+                    if (X3) tma_load_2d(sBlo + s * C::B_BYTES, &tmBlo, kb * BK, yb, &full[s]);
                 }
             }
             for (int k = kg > STAGES ? kg - STAGES : 0; k < kg; ++k)
@@ -282,7 +285,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 bool ok = true;
                 for (int kb = 0; kb < nk; ++kb, ++kg) {
                     const int s = kg % STAGES;
-                    if (!mbar_wait(&full[s], (kg / STAGES) & 1, abort_flag)) {
+                    if (!mbar_wait(&full[s], (kg / STAGES) & 1, abort_flag) ||
+                        (X3 && !mbar_wait(&conv[s], (kg / STAGES) & 1, abort_flag))) {
                         ok = false;
                         break;
                     }
@@ -312,7 +316,43 @@ __global__ void __launch_bounds__(THREADS, 1)
                 umma_commit(&acc_full[buf]);
             }
         }
-    } else {  // epilogue warps 2..9
+    } else if (warp >= 2 + EPI_WARPS) {
+        if (X3) {  // converters: A -> (A_hi, A_lo) for every stage, in k order
+            const int ct = threadIdx.x - 32 * (2 + EPI_WARPS);
+            int kg = 0;
+            bool ok = true;
+            int z, m0, n0;
+            for (int t = blockIdx.x; ok && it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x) {
+                for (int kb = 0; kb < nk; ++kb, ++kg) {
+                    const int s = kg % STAGES;
+                    if (!mbar_wait(&full[s], (kg / STAGES) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    float4 *hi = reinterpret_cast<float4 *>(sA + s * C::A_BYTES);
+                    float4 *lo = reinterpret_cast<float4 *>(sAlo + s * C::A_BYTES);
+#pragma unroll 4
+                    for (int i = ct; i < (int)(C::A_BYTES / 16); i += 32 * CONV_WARPS) {
+                        float4 v = hi[i], l;
+                        tf32_split(v.x, v.x, l.x);
+                        tf32_split(v.y, v.y, l.y);
+                        tf32_split(v.z, v.z, l.z);
+                        tf32_split(v.w, v.w, l.w);
+                        hi[i] = v;
+                        lo[i] = l;
+                    }
+                    // make the generic-proxy writes visible to the tensor core
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&conv[s]);
+                }
+            }
+            if (!ok) {
+                set_status(status, TNET_ERR_TIMEOUT);
+                *abort_flag = 1;
+            }
+        }
+    } else {  // epilogue warps 2 .. 2 + EPI_WARPS - 1
         const int q = warp & 3;                  // TMEM lane quadrant this warp may read
         // column slices of at least 16 (one tcgen05.ld.x16); warps past the last
         // slice only take part in the accumulator hand-off
@@ -380,9 +420,9 @@ EncodeFn tensor_map_encoder();  // resolved once through the runtime (tc_gemm.cu
 int make_map_bf16(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
 int make_map_f32(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
 
-// Operands of one GEMM: A, B and (TF32X3 only) their residual arrays.
+// Operands of one GEMM: A, B and (TF32X3 only) B's split: B = B_hi, Blo = B_lo.
 struct TcOperands {
-    const void *A, *B, *Alo, *Blo;
+    const void *A, *B, *Blo;
     int64_t a_rows, lda, b_rows, ldb;
 };
 
@@ -395,14 +435,14 @@ int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *
     if (maxM <= 0 || P.N <= 0) return TNET_OK;
     if (P.N % 4 || (o.lda * esz) % 16 || (o.ldb * esz) % 16 || ((uintptr_t)o.A & 15) || ((uintptr_t)o.B & 15))
         return TNET_ERR_ARG;
-    if (X3 && (!o.Alo || !o.Blo || ((uintptr_t)o.Alo & 15) || ((uintptr_t)o.Blo & 15))) return TNET_ERR_ARG;
+    if (X3 && (!o.Blo || ((uintptr_t)o.Blo & 15))) return TNET_ERR_ARG;
     CUtensorMap ma, mb, mal, mbl;
     int rc;
     if (X3) {
         if ((rc = make_map_f32(&ma, o.A, o.a_rows, P.K, o.lda, BM))) return rc;
         if ((rc = make_map_f32(&mb, o.B, o.b_rows, P.K, o.ldb, BN))) return rc;
-        if ((rc = make_map_f32(&mal, o.Alo, o.a_rows, P.K, o.lda, BM))) return rc;
         if ((rc = make_map_f32(&mbl, o.Blo, o.b_rows, P.K, o.ldb, BN))) return rc;
+        mal = ma;  // unused: A_lo is formed in shared memory
     } else {
         if ((rc = make_map_bf16(&ma, o.A, o.a_rows, P.K, o.lda, BM))) return rc;
         if ((rc = make_map_bf16(&mb, o.B, o.b_rows, P.K, o.ldb, BN))) return rc;
@@ -434,7 +474,7 @@ int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *
 template <int BN, class Epi>
 int tc_gemm(const TcShape &P, const __nv_bfloat16 *A, int64_t a_rows, int64_t lda, const __nv_bfloat16 *B,
             int64_t b_rows, int64_t ldb, const Epi &epi, int32_t *status, cudaStream_t st) {
-    return tc_gemm_ops<BN, false>(P, TcOperands{A, B, nullptr, nullptr, a_rows, lda, b_rows, ldb}, epi, status, st);
+    return tc_gemm_ops<BN, false>(P, TcOperands{A, B, nullptr, a_rows, lda, b_rows, ldb}, epi, status, st);
 }
 
 inline TcShape tshape(int M, int N, int K) {

@@ -176,6 +176,15 @@ class TensorNet:
                                          _stream(self.device)), "tnet_md_step")
         return e_kin, e_pot
 
+    def md_neighbor_list(self, n_atoms: int) -> NeighborList:
+        """A copy of the neighbor list md() keeps (cutoff + skin, last rebuild)."""
+        nl = NeighborList(torch.empty(n_atoms + 1, dtype=torch.int32, device=self.device),
+                          torch.empty(self.max_pairs, dtype=torch.int32, device=self.device),
+                          torch.zeros(1, dtype=torch.int64, device=self.device), float("nan"))
+        _lib.check(self.lib.tnet_md_neighbor_list(self.ctx, int(n_atoms), _p(nl.row_ptr), _p(nl.col), self.max_pairs,
+                                                  _p(nl.n_pairs), _stream(self.device)), "tnet_md_neighbor_list")
+        return nl
+
     def md_rebuilds(self) -> int:
         """Neighbor-list builds of the last md() call (waits for the device)."""
         n = ctypes.c_int64()

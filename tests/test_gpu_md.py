@@ -106,3 +106,21 @@ def test_triggered_rebuilds_make_the_trajectory_schedule_independent():
     assert torch.equal(pa, pb) and torch.equal(va, vb)
     assert torch.equal(epa, epb) and torch.equal(eka, ekb)
 
+
+def test_md_neighbor_list_is_the_list_at_the_last_rebuild():
+    """With a rebuild in every step, the list md() keeps equals a fresh
+    tnet_neighbors call at cutoff + skin on the final positions."""
+    s = synth.workload("water3000")
+    m = make_model(W, s, max_pairs=300000)
+    z, pos, vel, inv_m, box = _state(s)
+    m.reset_status()
+    m.md(z, inv_m, pos, vel, box, 0.5, 1.0, 1, 3)
+    torch.cuda.synchronize()
+    m.check_status("md")
+    a = m.md_neighbor_list(s.n_atoms)
+    b = m.neighbors(pos, None, box, 1, cutoff=6.0)
+    torch.cuda.synchronize()
+    n = int(b.n_pairs.item())
+    assert int(a.n_pairs.item()) == n
+    assert torch.equal(a.row_ptr, b.row_ptr) and torch.equal(a.col[:n], b.col[:n])
+

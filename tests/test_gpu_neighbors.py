@@ -8,7 +8,7 @@ import torch
 from oracle.neighbors import neighbor_pairs, neighbor_rows
 from paper_2402_17660_gb300 import synth
 
-from .gpu_helpers import RC, csr_to_pairs, gpu_pairs, make_model, margin_ok
+from .gpu_helpers import RC, csr_to_pairs, gpu_energy_forces, gpu_pairs, make_model, margin_ok, to_dev
 
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
 
@@ -109,14 +109,42 @@ def test_large_sampled_rows(name):
 
 def test_capacity_overflow_reports_needed_size():
     s = synth.workload("water3000")
-    oi, _ = neighbor_pairs(s.pos, s.batch, s.box, RC)
+    oi, oj = neighbor_pairs(s.pos, s.batch, s.box, RC)
     m = make_model(W, s, max_pairs=len(oi) + 100)
     cap = len(oi) // 2
     nl = gpu_pairs(m, s, cap=cap)
     assert int(m.status.item()) == 2
     assert int(nl.n_pairs.item()) == len(oi)
+    # the row offsets are clamped to the capacity, so readers stay inside col;
+    # the rows that fit are complete
     counts = np.bincount(oi, minlength=s.n_atoms)
-    assert np.array_equal(np.diff(nl.row_ptr.cpu().numpy()), counts)
+    full = np.concatenate([[0], np.cumsum(counts)])
+    rp = nl.row_ptr.cpu().numpy().astype(np.int64)
+    assert np.array_equal(rp, np.minimum(full, cap))
+    last = int(np.searchsorted(full, cap, side="right")) - 1      # rows [0, last) fit whole
+    got_i, got_j = csr_to_pairs(nl)
+    o = np.lexsort((oj, oi))
+    ref_i, ref_j = oi[o], oj[o]
+    keep, sel = got_i < last, ref_i < last
+    assert np.array_equal(got_i[keep], ref_i[sel]) and np.array_equal(got_j[keep], ref_j[sel])
+
+
+def test_energy_forces_on_truncated_list_is_flagged_and_safe():
+    """An overflowed (truncated) list is not symmetric: tnet_energy_forces
+    flags it and treats the unmatched edges as inactive, touching nothing
+    outside its buffers; the context then evaluates a full list correctly."""
+    s = synth.workload("molecule32")
+    oi, _ = neighbor_pairs(s.pos, s.batch, s.box, RC)
+    m = make_model(W, s, max_pairs=len(oi) + 100)
+    nl = gpu_pairs(m, s, cap=len(oi) // 2)
+    assert int(m.status.item()) == 2
+    z, pos, batch, box = to_dev(s)
+    m.reset_status()
+    m.energy_forces(z, pos, nl)
+    torch.cuda.synchronize()
+    assert int(m.status.item()) != 0
+    E, F = gpu_energy_forces(m, s)
+    assert np.isfinite(E).all() and np.isfinite(F).all()
 
 
 def test_box_too_small_and_nan_flagged():

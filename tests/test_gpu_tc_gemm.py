@@ -40,23 +40,33 @@ def test_tc_gemm_matches_matmul(M, N, K):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 32), (1, 32, 32), (300, 128, 128), (777, 384, 256), (129, 64, 384),
-                                   (4096, 256, 128)])
+                                   (4096, 256, 128), (200, 64, 36), (3000, 32, 384), (20000, 128, 256),
+                                   (8192, 384, 384)])
 def test_tc_gemm_3xtf32_matches_fp64(M, N, K):
-    """3xTF32 (A B + A_lo B + A B_lo on the tensor cores) reaches FP32-level
-    accuracy on fp32 inputs."""
+    """3xTF32 (A B + A_lo B + A B_lo on the tensor cores, A_lo formed in
+    shared memory) reaches FP32-level accuracy on fp32 inputs, including a
+    ragged last k-block and persistent CTAs whose stages wrap many times.
+    Each operand is split into its nearest TF32 value and the TF32-rounded
+    remainder (below 2^-11 of the value, rounded to within 2^-22 of it), so
+    the three products miss the exact one by less than 3 * 2^-22 |a||b| (plus
+    FP32 accumulation), elementwise."""
     g = torch.Generator(device="cpu").manual_seed(1)
     A = torch.randn(M, K, generator=g).cuda()
     B = torch.randn(N, K, generator=g).cuda()
-    Alo, Blo = torch.empty_like(A), torch.empty_like(B)
+    Bsplit = torch.empty(2 * N * K, dtype=torch.float32, device="cuda")
     C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     lib = _lib.load()
     p = lambda t: ctypes.c_void_p(t.data_ptr())
-    rc = lib.tnet_debug_tc_gemm_f32(M, N, K, p(A), p(B), p(Alo), p(Blo), p(C), p(st),
+    rc = lib.tnet_debug_tc_gemm_f32(M, N, K, p(A), p(B), p(Bsplit), p(C), p(st),
                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 0
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     ref = A.double() @ B.double().T
-    err = (C.double() - ref).abs().max().item()
-    assert err <= 2e-6 * (K ** 0.5) * ref.abs().max().item(), err
+    scale = A.double().abs() @ B.double().abs().T          # sum_k |a_ik| |b_jk|
+    rel = ((C.double() - ref).abs() / scale)
+    assert rel.max().item() <= 3 * 2.0 ** -22 + K * 2.0 ** -24, rel.max().item()
+    # typical error: at the FP32 accumulation floor (a split that went wrong,
+    # e.g. a residual from another tile, shows up near 1e-4)
+    assert rel.pow(2).mean().sqrt().item() <= 3e-7, rel.pow(2).mean().sqrt().item()
