@@ -14,10 +14,14 @@ Readings (the paper does not state them):
   * self pairs are excluded; the pair is kept when d < cutoff (strict);
   * the pair vector is r_ij = r_i - r_j and atom i is the receiver;
   * boxes are given as rows a, b, c of a lower-triangular matrix
-    (a = (ax,0,0), b = (bx,by,0), c = (cx,cy,cz)); the nearest image is
-    taken by removing c*round(z/cz), then b*round(y/by), then a*round(x/ax),
-    which is the exact nearest image for rectangular boxes and for reduced
-    triclinic boxes whose perpendicular widths are all >= 2*cutoff.
+    (a = (ax,0,0), b = (bx,by,0), c = (cx,cy,cz)), rectangular or triclinic;
+    the nearest image is taken by removing c*round(z/cz), then
+    b*round(y/by), then a*round(x/ax).  That leaves r in the brick
+    |x| <= ax/2, |y| <= by/2, |z| <= cz/2, which holds exactly one image of
+    every vector.  The perpendicular widths obey w_c = cz, w_b <= by and
+    w_a <= ax, so when all of them are >= 2*cutoff an image shorter than
+    the cutoff lies in that brick: the pair set (d < cutoff) and the vectors
+    of those pairs are exact, for any such box, reduced or not.
 
 Pinned by: a second search that enumerates the 27 periodic images
 explicitly, and scipy's k-d tree (tests/test_oracle_neighbors.py).
@@ -113,17 +117,18 @@ def neighbor_pairs(pos, batch, box, cutoff: float, block: int = 2048):
     return i[order], j[order]
 
 
-def neighbor_pairs_images(pos, batch, box, cutoff: float):
+def neighbor_pairs_images(pos, batch, box, cutoff: float, reach: int = 1):
     """Independent check of `neighbor_pairs` for small inputs: for every
-    pair of the same system, enumerate the 27 periodic images n.B with
-    n in {-1,0,1}^3 of r_i - r_j (after wrapping both atoms into the box)
-    and keep the pair when any image is within the cutoff."""
+    pair of the same system, enumerate the periodic images n.B with
+    n in {-reach..reach}^3 of r_i - r_j (after wrapping both atoms into the
+    cell) and keep the pair when any image is within the cutoff.  reach = 1
+    (27 images) covers rectangular boxes; strongly tilted cells need 2."""
     pos = np.asarray(pos, dtype=np.float64)
     batch = np.asarray(batch)
     N = len(pos)
     ii, jj = [], []
-    shifts = np.array([[a, b, c] for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)],
-                      dtype=np.float64)
+    rr = range(-reach, reach + 1)
+    shifts = np.array([[a, b, c] for a in rr for b in rr for c in rr], dtype=np.float64)
     for i in range(N):
         for j in range(N):
             if i == j or batch[i] != batch[j]:

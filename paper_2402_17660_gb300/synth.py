@@ -434,6 +434,57 @@ def perturb(sys: System, seed: int, scale: float = 0.02) -> System:
     return dataclasses.replace(sys, pos=pos)
 
 
+def _lower_image_np(r: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Nearest image for a lower-triangular box with rows a, b, c (remove c,
+    then b, then a; used only to validate generated geometry)."""
+    r = np.array(r, dtype=np.float64, copy=True)
+    for k in (2, 1, 0):
+        r -= np.round(r[:, k] / B[k, k])[:, None] * B[k]
+    return r
+
+
+def triclinic_water(n_side: int = 10, L: float = 31.04, tilt=(0.3, 0.2, -0.25), seed: int = 5,
+                    jitter: float = 0.3, radii=(5.0,), margin=1e-4) -> System:
+    """Rigid waters on a jittered lattice in a triclinic cell with rows
+    a = (L,0,0), b = (tb L, L, 0), c = (tc1 L, tc2 L, L) (tilt = (tb, tc1,
+    tc2); the volume, and so the density, of the cube of side L): lattice
+    sites at fractional coordinates (k + 1/2)/n_side, random orientations,
+    and no pair within `margin` of a radius in `radii` (checked by brute
+    force under the cell's nearest image)."""
+    rng = np.random.default_rng(seed)
+    tb, tc1, tc2 = tilt
+    B = np.array([[L, 0, 0], [tb * L, L, 0], [tc1 * L, tc2 * L, L]], dtype=np.float64)
+    g = (np.arange(n_side) + 0.5) / n_side
+    frac = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    centres = frac @ B
+    xyz = _place_waters(rng, centres, jitter)
+    n = len(xyz)
+    for _ in range(200):
+        x = xyz.astype(np.float32).astype(np.float64)
+        bad = np.zeros(n, dtype=bool)
+        for a0 in range(0, n, 512):
+            r = (x[a0:a0 + 512, None, :] - x[None, :, :]).reshape(-1, 3)
+            d = np.linalg.norm(_lower_image_np(r, B), axis=1).reshape(-1, n)
+            hit = np.zeros_like(d, dtype=bool)
+            for R in radii:
+                hit |= np.abs(d - R) < margin
+            ia, ib = np.nonzero(hit)
+            bad[ia + a0] = True
+            bad[ib] = True
+        if not bad.any():
+            break
+        mols = np.unique(np.nonzero(bad)[0] // 3)
+        xyz = xyz.reshape(-1, 3, 3)
+        xyz[mols] = _place_waters(rng, centres[mols], jitter).reshape(-1, 3, 3)
+        xyz = xyz.reshape(-1, 3)
+    else:
+        raise RuntimeError("could not satisfy the pair-distance margin")
+    nw = len(centres)
+    z = np.tile(np.array([Z_O, Z_H, Z_H], np.int32), nw)
+    return System(f"triclinic_water{3 * nw}", z, xyz.astype(np.float32), np.zeros(3 * nw, np.int32),
+                  B.astype(np.float32)[None], 1, {"L": L, "tilt": tilt})
+
+
 def workload(name: str) -> System:
     """The five named workloads:
     molecule32  - 32-atom molecule in vacuum

@@ -167,6 +167,37 @@ def test_periodic_image_shift_invariance():
     assert np.allclose(F1, F0, atol=1e-12)
 
 
+def test_triclinic_cell_equivalent_to_cube_gives_same_energy_forces():
+    """Same lattice, other basis (a = (L,0,0), b = (L,L,0), c = (0,L,L)):
+    the model sees the same pairs and vectors, so energy and forces agree
+    to rounding; a shift of atoms by lattice vectors of the tilted basis
+    changes nothing either."""
+    W, m = _model()
+    s = synth.water_box(6, 18.6, seed=3)
+    L = 18.6
+    skew = np.array([[[L, 0, 0], [L, L, 0], [0, L, L]]], np.float32)
+    pos = s.pos.astype(np.float64)
+    E0, _, F0, _ = m.energy_forces(s.z, pos, s.batch, s.box)
+    E1, _, F1, _ = m.energy_forces(s.z, pos, s.batch, skew)
+    assert abs(E1[0] - E0[0]) < 1e-11 * max(1.0, abs(E0[0]))
+    assert np.allclose(F1, F0, atol=1e-10 * _rms(F0))
+    shifted = pos.copy()
+    shifted[1::3] += skew[0, 0] - 2 * skew[0, 1] + skew[0, 2]
+    E2, _, F2, _ = m.energy_forces(s.z, shifted, s.batch, skew)
+    assert abs(E2[0] - E0[0]) < 1e-11 * max(1.0, abs(E0[0]))
+    assert np.allclose(F2, F0, atol=1e-10 * _rms(F0))
+
+
+def test_triclinic_forces_match_finite_differences():
+    W, m = _model()
+    s = synth.triclinic_water(4, 12.416, seed=3)
+    pos = s.pos.astype(np.float64)[:24]
+    z, batch = s.z[:24], s.batch[:24]
+    _, _, F, _ = m.energy_forces(z, pos, batch, s.box)
+    fd = _fd_forces(m, z, pos, batch, s.box)
+    assert np.abs(F - fd).max() <= 1e-7 * _rms(F) + 1e-9
+
+
 def test_batch_equals_separate_systems():
     W, m = _model()
     s = synth.molecule_batch(4, nmin=6, nmax=12, seed=5)

@@ -111,3 +111,65 @@ def test_generated_inputs_keep_margin():
         d = np.linalg.norm(r, axis=1)
         for R in radii:
             assert np.all(np.abs(d - R) >= 1e-4)
+
+
+# ---------------------------------------------------------------- triclinic
+TRICLINIC_BOXES = [
+    np.array([[12.0, 0, 0], [3.6, 11.5, 0], [2.4, -2.9, 12.2]]),      # reduced tilts
+    np.array([[20.0, 0, 0], [14.0, 13.0, 0], [-9.0, 8.0, 13.0]]),     # not reduced, widths >= 2 rc
+]
+
+
+def _tri_cloud(seed, B, n=48):
+    rng = np.random.default_rng(seed)
+    frac = rng.uniform(-0.5, 1.5, (n, 3))             # many atoms outside the cell
+    pos = frac @ B
+    pos[0] = 0.0
+    pos[1] = B[0] + B[1] + B[2] - 1e-3                 # across the far corner
+    return pos.astype(np.float32), np.zeros(n, np.int32), B.astype(np.float32)[None]
+
+
+@pytest.mark.parametrize("k", range(len(TRICLINIC_BOXES)))
+@pytest.mark.parametrize("seed", [0, 1])
+def test_triclinic_pbc_matches_image_enumeration(k, seed):
+    """The sequential c, b, a reduction against brute force over 125 images,
+    on a reduced and a strongly tilted (not reduced) cell."""
+    pos, batch, box = _tri_cloud(seed, TRICLINIC_BOXES[k])
+    a = _as_set(*neighbor_pairs(pos, batch, box, RC))
+    b = _as_set(*neighbor_pairs_images(pos, batch, box, RC, reach=2))
+    assert a == b and len(a) > 0
+
+
+def test_triclinic_minimum_image_is_nearest():
+    """For pair vectors whose nearest image is within the cutoff, the
+    reduction returns that image (brute force over 125 images)."""
+    B = TRICLINIC_BOXES[1]
+    rng = np.random.default_rng(5)
+    near = rng.uniform(-1, 1, (2000, 3))
+    near *= (rng.uniform(0, RC, 2000) / np.linalg.norm(near, axis=1))[:, None]
+    n = rng.integers(-3, 4, (2000, 3))
+    r = near + n @ B
+    got = minimum_image(r, B)
+    assert np.allclose(got, near, atol=1e-9)
+
+
+def test_lattice_equivalent_triclinic_cell_gives_the_same_pairs():
+    """The cube of side L and the cell a = (L,0,0), b = (L,L,0), c = (0,L,L)
+    span the same lattice (a unimodular change of basis); with all widths
+    >= 2 rc the pair sets and the nearest-image vectors coincide."""
+    s = synth.water_box(6, 18.6, seed=3)
+    L = 18.6
+    cube = s.box
+    skew = np.array([[[L, 0, 0], [L, L, 0], [0, L, L]]], np.float32)
+    ia, ja = neighbor_pairs(s.pos, s.batch, cube, RC)
+    ib, jb = neighbor_pairs(s.pos, s.batch, skew, RC)
+    assert np.array_equal(ia, ib) and np.array_equal(ja, jb)
+    p = s.pos.astype(np.float64)
+    assert np.allclose(minimum_image(p[ia] - p[ja], cube[0]), minimum_image(p[ib] - p[jb], skew[0]), atol=1e-9)
+
+
+def test_triclinic_box_too_narrow_rejected():
+    L = 17.0                                            # widths L, L/sqrt(2), L/sqrt(3) < 2 rc
+    with pytest.raises(ValueError):
+        check_box(np.array([[L, 0, 0], [L, L, 0], [0, L, L]]), RC)
+
