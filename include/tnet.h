@@ -137,9 +137,12 @@ int tnet_destroy(tnet_ctx *ctx);
  *   batch    [N] int32 system index of each atom, non-decreasing, in
  *            [0, n_systems); NULL means every atom is in system 0
  *   box      [S][3][3] float32, rows a, b, c of each system's box, lower-
- *            triangular (a = (ax,0,0), b = (bx,by,0)); only rectangular
- *            boxes (diagonal) are implemented; NULL means no periodicity.
- *            Each perpendicular width must be >= 2*cutoff (else BOX).
+ *            triangular (a = (ax,0,0), b = (bx,by,0), c = (cx,cy,cz)),
+ *            rectangular or triclinic, reduced or not (Sec. 2.5.1: periodic
+ *            boundary conditions with rectangular and triclinic boxes);
+ *            NULL means no periodicity.  Each perpendicular width must be
+ *            >= 2*cutoff (else BOX); the nearest image (remove c, then b,
+ *            then a) is then exact for every pair within the cutoff.
  *   cutoff   Angstrom (> 0); a pair is kept when d < cutoff
  * Output (receiver-sorted CSR; within a row, columns ascend):
  *   row_ptr  [N+1] int32   row_ptr[0] = 0, row i holds the j of pairs (i, j)

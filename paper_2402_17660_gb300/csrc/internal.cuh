@@ -32,13 +32,14 @@ __device__ __forceinline__ void set_status(int32_t *st, int code) {
 
 // Per-system cell grid (one cell list per system; cells never mix systems).
 struct SysInfo {
-    float origin[3];    // lower corner of the grid
-    float inv_cell[3];  // 1 / cell width along x, y, z
-    float L[3];         // periodic box lengths (rectangular); 0 when not periodic
-    int nc[3];          // cells along x, y, z (>= 1)
+    float origin[3];    // no PBC: lower corner of the grid
+    float inv_cell[3];  // no PBC: 1 / cell width along x, y, z
+    float L[3];         // PBC: box diagonal ax, by, cz; 0 when not periodic
+    float tilt[3];      // PBC: bx, cx, cy of the lower-triangular box (0: rectangular)
+    int nc[3];          // cells along x, y, z (PBC: along a, b, c) (>= 1)
     int cell_off;       // first global cell index of this system
     int pbc;            // 1 if periodic
-    int pad[2];
+    int pad;
 };
 
 // ---------------------------------------------------------------------------
@@ -254,12 +255,30 @@ __device__ __forceinline__ float mic1(float x, float L) {
 __device__ __forceinline__ float norm2_rn(float x, float y, float z) {
     return __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
 }
+// Nearest image for a lower-triangular box with rows a = (ax,0,0),
+// b = (bx,by,0), c = (cx,cy,cz): remove c round(z/cz), then b round(y/by),
+// then a round(x/ax).  The result lies in the brick |x| <= ax/2, |y| <= by/2,
+// |z| <= cz/2, which holds one image of every vector; since the box's
+// perpendicular widths obey w_c = cz, w_b <= by, w_a <= ax, an image shorter
+// than half the smallest width is that one.  Rectangular boxes have zero
+// tilts, and then this is mic1 along each axis.
+__device__ __forceinline__ void mic_lower(float &x, float &y, float &z, float ax, float bx, float by, float cx,
+                                          float cy, float cz) {
+    const float kc = rintf(__fdiv_rn(z, cz));
+    x = __fsub_rn(x, __fmul_rn(kc, cx));
+    y = __fsub_rn(y, __fmul_rn(kc, cy));
+    z = __fsub_rn(z, __fmul_rn(kc, cz));
+    const float kb = rintf(__fdiv_rn(y, by));
+    x = __fsub_rn(x, __fmul_rn(kb, bx));
+    y = __fsub_rn(y, __fmul_rn(kb, by));
+    x = __fsub_rn(x, __fmul_rn(rintf(__fdiv_rn(x, ax)), ax));
+}
+// the same with the box as 9 floats, rows a, b, c
+__device__ __forceinline__ void mic_box(float &x, float &y, float &z, const float *__restrict__ B) {
+    mic_lower(x, y, z, B[0], B[3], B[4], B[6], B[7], B[8]);
+}
 __device__ __forceinline__ void mic(float &x, float &y, float &z, const SysInfo &s) {
-    if (s.pbc) {
-        x = mic1(x, s.L[0]);
-        y = mic1(y, s.L[1]);
-        z = mic1(z, s.L[2]);
-    }
+    if (s.pbc) mic_lower(x, y, z, s.L[0], s.tilt[0], s.L[1], s.tilt[1], s.tilt[2], s.L[2]);
 }
 
 // Radial part of the model: cosine cutoff phi(d), expnorm basis e_k(d) and

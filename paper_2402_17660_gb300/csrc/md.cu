@@ -33,8 +33,8 @@ __global__ void k_drift(float *__restrict__ pos, const float *__restrict__ vel, 
         const float x = pos[3LL * i + k] + dt * vel[3LL * i + k];
         pos[3LL * i + k] = x;
         d[k] = x - ref[3LL * i + k];
-        if (box) d[k] -= box[4 * k] * rintf(d[k] / box[4 * k]);
     }
+    if (box) mic_box(d[0], d[1], d[2], box);
     if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] > lim2) *need = 1;
 }
 

@@ -82,20 +82,15 @@ __device__ __forceinline__ float block_sum(float v, float *sm) {
     return t;
 }
 
-// pair vector r_ij = mic(r_i - r_j) for rectangular boxes (box rows diagonal),
-// with fixed rounding (see mic1)
+// pair vector r_ij = mic(r_i - r_j) for rectangular or triclinic
+// (lower-triangular) boxes, with fixed rounding (see mic_lower)
 __device__ __forceinline__ void pair_vec(const float *__restrict__ pos, const float *__restrict__ box,
                                          const int32_t *__restrict__ batch, int i, int j, float &x,
                                          float &y, float &zz) {
     x = __fsub_rn(pos[3LL * i], pos[3LL * j]);
     y = __fsub_rn(pos[3LL * i + 1], pos[3LL * j + 1]);
     zz = __fsub_rn(pos[3LL * i + 2], pos[3LL * j + 2]);
-    if (box) {
-        const float *B = box + 9LL * (batch ? batch[i] : 0);
-        x = mic1(x, B[0]);
-        y = mic1(y, B[4]);
-        zz = mic1(zz, B[8]);
-    }
+    if (box) mic_box(x, y, zz, box + 9LL * (batch ? batch[i] : 0));
 }
 
 // ------------------------------------------------------- graph prep ---

@@ -206,26 +206,35 @@ __global__ void k_sys_setup(const float *__restrict__ pos, const float *__restri
     const int na = a1 - a0;
     if (sbad) set_status(status, TNET_ERR_NAN);
     if (box) {
+        // rows a = (ax,0,0), b = (bx,by,0), c = (cx,cy,cz): rectangular or
+        // triclinic.  Cells are cut along a, b, c in fractional coordinates,
+        // nc_k = floor(w_k / cutoff) of them, where w_k is the perpendicular
+        // width between the box faces spanned by the other two vectors: the
+        // planes between cells are then >= cutoff apart, so a pair within
+        // the cutoff is in the same or an adjacent cell along every axis
+        // (with a 1e-4 relative slack, so rounding at a cell face never
+        // matters).
         const float *B = box + 9LL * s;
         si.pbc = 1;
-        if (B[1] != 0.f || B[2] != 0.f || B[5] != 0.f || B[3] != 0.f || B[6] != 0.f || B[7] != 0.f) {
-            // only rectangular boxes are implemented (lower-triangular input
-            // with non-zero b_x, c_x or c_y is a triclinic box)
-            set_status(status, (B[1] != 0.f || B[2] != 0.f || B[5] != 0.f) ? TNET_ERR_BOX
-                                                                         : TNET_ERR_UNSUPPORTED);
-        }
+        const double ax = B[0], bx = B[3], by = B[4], cx = B[6], cy = B[7], cz = B[8];
+        if (B[1] != 0.f || B[2] != 0.f || B[5] != 0.f || !(ax > 0.0) || !(by > 0.0) || !(cz > 0.0))
+            set_status(status, TNET_ERR_BOX);
+        const double n0 = by * cz, n1 = -bx * cz, n2 = bx * cy - by * cx;  // b x c
+        const double w[3] = {ax * by * cz / sqrt(n0 * n0 + n1 * n1 + n2 * n2), by * cz / sqrt(cz * cz + cy * cy),
+                             cz};
+        si.L[0] = (float)ax; si.L[1] = (float)by; si.L[2] = (float)cz;
+        si.tilt[0] = (float)bx; si.tilt[1] = (float)cx; si.tilt[2] = (float)cy;
         for (int k = 0; k < 3; ++k) {
-            const float L = B[4 * k];
-            if (!(L >= 2.0f * cutoff)) set_status(status, TNET_ERR_BOX);
-            si.L[k] = L;
+            if (!(w[k] >= 2.0 * cutoff)) set_status(status, TNET_ERR_BOX);
             si.origin[k] = 0.f;
-            int nc = (L > 0.f) ? (int)floorf(L / cutoff) : 1;
+            const int nc = (w[k] > 0.0 && w[k] < 1e30) ? (int)floor(w[k] / (cutoff * 1.0001)) : 1;
             si.nc[k] = nc < 1 ? 1 : nc;
         }
     } else {
         si.pbc = 0;
         for (int k = 0; k < 3; ++k) {
             si.L[k] = 0.f;
+            si.tilt[k] = 0.f;
             const float ext = na > 0 ? (shi[k][0] - slo[k][0]) : 0.f;
             si.origin[k] = na > 0 ? slo[k][0] : 0.f;
             int nc = (ext > 0.f && isfinite(ext)) ? (int)floorf(ext / cutoff) : 1;
@@ -240,22 +249,39 @@ __global__ void k_sys_setup(const float *__restrict__ pos, const float *__restri
         if (si.nc[2] > si.nc[k]) k = 2;
         si.nc[k] = si.nc[k] / 2 > 1 ? si.nc[k] / 2 : 1;
     }
-    for (int k = 0; k < 3; ++k) {
-        const float width = si.pbc ? si.L[k] : (na > 0 ? shi[k][0] - slo[k][0] : 0.f);
+    for (int k = 0; k < 3; ++k) {  // (PBC: cells per unit of fractional coordinate)
+        const float width = si.pbc ? 1.0f : (na > 0 ? shi[k][0] - slo[k][0] : 0.f);
         si.inv_cell[k] = width > 0.f ? si.nc[k] / width : 0.f;
     }
     si.cell_off = 0;
-    si.pad[0] = si.pad[1] = 0;
+    si.pad = 0;
     info[s] = si;
     ncell[s] = na > 0 ? si.nc[0] * si.nc[1] * si.nc[2] : 0;
 }
 
-__device__ __forceinline__ int axis_cell(float x, int k, const SysInfo &s) {
-    float u = x - s.origin[k];
-    if (s.pbc) u -= s.L[k] * floorf(u / s.L[k]);
-    int c = (int)floorf(u * s.inv_cell[k]);
+__device__ __forceinline__ int cell_index(float u, int nc) {
+    int c = (int)floorf(u);
     c = c < 0 ? 0 : c;
-    return c >= s.nc[k] ? s.nc[k] - 1 : c;
+    return c >= nc ? nc - 1 : c;
+}
+// Cell of a point.  Without PBC: along x, y, z from the grid's corner.  With
+// PBC: along a, b, c from the fractional coordinates (back substitution in
+// the lower-triangular box, wrapped into [0, 1)).  Fixed rounding, so the
+// binning pass and the pair passes put an atom in the same cell.
+__device__ __forceinline__ void point_cell(float x, float y, float z, const SysInfo &s, int &ca, int &cb, int &cc) {
+    if (s.pbc) {
+        const float fc = __fdiv_rn(z, s.L[2]);
+        const float fb = __fdiv_rn(__fsub_rn(y, __fmul_rn(fc, s.tilt[2])), s.L[1]);
+        const float fa = __fdiv_rn(__fsub_rn(__fsub_rn(x, __fmul_rn(fc, s.tilt[1])), __fmul_rn(fb, s.tilt[0])),
+                                   s.L[0]);
+        ca = cell_index(__fmul_rn(__fsub_rn(fa, floorf(fa)), s.inv_cell[0]), s.nc[0]);
+        cb = cell_index(__fmul_rn(__fsub_rn(fb, floorf(fb)), s.inv_cell[1]), s.nc[1]);
+        cc = cell_index(__fmul_rn(__fsub_rn(fc, floorf(fc)), s.inv_cell[2]), s.nc[2]);
+    } else {
+        ca = cell_index(__fmul_rn(__fsub_rn(x, s.origin[0]), s.inv_cell[0]), s.nc[0]);
+        cb = cell_index(__fmul_rn(__fsub_rn(y, s.origin[1]), s.inv_cell[1]), s.nc[1]);
+        cc = cell_index(__fmul_rn(__fsub_rn(z, s.origin[2]), s.inv_cell[2]), s.nc[2]);
+    }
 }
 
 __global__ void k_bin(const float *__restrict__ pos, const int32_t *__restrict__ batch, int N,
@@ -267,8 +293,8 @@ __global__ void k_bin(const float *__restrict__ pos, const int32_t *__restrict__
     if (n >= N) return;
     const int b = batch ? batch[n] : 0;
     const SysInfo s = info[b];
-    const int cx = axis_cell(pos[3LL * n], 0, s), cy = axis_cell(pos[3LL * n + 1], 1, s),
-              cz = axis_cell(pos[3LL * n + 2], 2, s);
+    int cx, cy, cz;
+    point_cell(pos[3LL * n], pos[3LL * n + 1], pos[3LL * n + 2], s, cx, cy, cz);
     int64_t c = cell_off[b] + ((int64_t)cx * s.nc[1] + cy) * s.nc[2] + cz;
     if (c >= cells) c = cells - 1;  // unreachable when the budget holds
     cell_of[n] = (int32_t)c;
@@ -316,7 +342,8 @@ __device__ __forceinline__ void for_candidates(int i, const float *__restrict__ 
     const int b = batch ? batch[i] : 0;
     const SysInfo s = info[b];
     const float xi = pos[3LL * i], yi = pos[3LL * i + 1], zi = pos[3LL * i + 2];
-    const int cx = axis_cell(xi, 0, s), cy = axis_cell(yi, 1, s), cz = axis_cell(zi, 2, s);
+    int cx, cy, cz;
+    point_cell(xi, yi, zi, s, cx, cy, cz);
     int nx[3], ny[3], nz[3];
     const int mx = axis_neighbors(cx, s.nc[0], s.pbc, nx);
     const int my = axis_neighbors(cy, s.nc[1], s.pbc, ny);

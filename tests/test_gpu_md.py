@@ -22,8 +22,9 @@ def _state(sys):
     return z, pos, vel, inv_m, box
 
 
-def test_one_step_matches_velocity_verlet():
-    s = synth.workload("water3000")
+@pytest.mark.parametrize("name", ["water3000", "triclinic"])
+def test_one_step_matches_velocity_verlet(name):
+    s = synth.workload(name) if name != "triclinic" else synth.triclinic_water(6, 18.6, seed=5, radii=(5.0, 6.0))
     m = make_model(W, s, max_pairs=300000)
     z, pos, vel, inv_m, box = _state(s)
     dt = 0.5

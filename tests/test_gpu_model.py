@@ -85,6 +85,22 @@ def test_water3000():
     _compare(synth.workload("water3000"))
 
 
+def test_triclinic_water():
+    _compare(synth.triclinic_water(6, 18.6, seed=5))
+
+
+def test_cube_and_equivalent_tilted_cell_agree():
+    """Same lattice, other basis: the pair vectors differ only by rounding."""
+    s = synth.workload("water3000")
+    L = 31.04
+    t = synth.System(s.name, s.z, s.pos, s.batch, np.array([[[L, 0, 0], [L, L, 0], [0, L, L]]], np.float32), 1)
+    m = make_model(W, s)
+    E0, F0 = gpu_energy_forces(m, s)
+    E1, F1 = gpu_energy_forces(m, t)
+    assert abs(E1[0] - E0[0]) <= 1e-6 * abs(E0[0])
+    assert force_error(F1, F0) <= 1e-5
+
+
 def test_skin_list_gives_identical_results():
     s = synth.water_box(10, 31.04, seed=1, radii=(5.0, 6.0))
     m = make_model(W, s, max_pairs=400000)

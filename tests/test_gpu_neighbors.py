@@ -180,3 +180,54 @@ def test_deterministic_and_graph_capturable():
     torch.cuda.synchronize()
     n = int(a.n_pairs.item())
     assert torch.equal(out.col[:n], ga[:n])
+
+
+# ---------------------------------------------------------------- triclinic
+TRICLINIC_BOXES = [
+    np.array([[12.0, 0, 0], [3.6, 11.5, 0], [2.4, -2.9, 12.2]]),      # reduced tilts
+    np.array([[20.0, 0, 0], [14.0, 13.0, 0], [-9.0, 8.0, 13.0]]),     # not reduced, widths >= 2 rc
+]
+
+
+def _tri_case(seed, B, n=60):
+    for s0 in range(seed, seed + 100):
+        rng = np.random.default_rng(s0)
+        frac = rng.uniform(-0.5, 1.5, (n, 3))
+        pos = frac @ B
+        s = synth.System(f"tri{s0}", rng.choice([1, 6, 7, 8], n).astype(np.int32), pos.astype(np.float32),
+                         np.zeros(n, np.int32), B.astype(np.float32)[None], 1)
+        if margin_ok(s):
+            return s
+    raise RuntimeError
+
+
+@pytest.mark.parametrize("k", range(len(TRICLINIC_BOXES)))
+@pytest.mark.parametrize("seed", [0, 100, 200])
+def test_triclinic_pairs_exact(k, seed):
+    _check_exact(_tri_case(seed, TRICLINIC_BOXES[k]))
+
+
+def test_triclinic_water_pairs_exact():
+    _check_exact(synth.triclinic_water(10, 31.04, seed=5))
+
+
+def test_cube_and_equivalent_tilted_cell_give_same_pairs():
+    """Same lattice, two bases: the cube of side L and a = (L,0,0),
+    b = (L,L,0), c = (0,L,L)."""
+    s = synth.workload("water3000")
+    L = 31.04
+    nl_a = _check_exact(s)
+    t = synth.System(s.name, s.z, s.pos, s.batch, np.array([[[L, 0, 0], [L, L, 0], [0, L, L]]], np.float32), 1)
+    nl_b = _check_exact(t)
+    n = int(nl_a.n_pairs.item())
+    assert torch.equal(nl_a.row_ptr, nl_b.row_ptr) and torch.equal(nl_a.col[:n], nl_b.col[:n])
+
+
+def test_narrow_triclinic_box_flagged():
+    L = 17.0   # widths L, L/sqrt(2), L/sqrt(3): the last is below 2 rc
+    s = synth.random_cluster(20, seed=1)
+    s.box = np.array([[[L, 0, 0], [L, L, 0], [0, L, L]]], np.float32)
+    m = make_model(W, s, max_pairs=1000)
+    gpu_pairs(m, s)
+    assert int(m.status.item()) == 3
+
