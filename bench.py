@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import ctypes
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -57,6 +58,12 @@ def parse():
     ap.add_argument("--md", type=int, default=0,
                     help="also time this many velocity-Verlet steps (0.5 fs, 1 A skin, rebuild every 20 steps "
                          "and whenever an atom has moved more than skin/2)")
+    ap.add_argument("--sweep", choices=["paper"], default=None,
+                    help="paper: single random-walk molecules of the paper's five atom counts, cutoff 4.5 A, "
+                         "0/1/2 interaction layers (one JSON line)")
+    ap.add_argument("--neighbor-bench", action="store_true",
+                    help="neighbor search alone: 32,768-particle random cloud (64 neighbors per particle) split "
+                         "into 1..1024 systems (one JSON line)")
     ap.add_argument("--per-molecule", action="store_true",
                     help="for batched workloads, also time one eager call per molecule")
     return ap.parse_args()
@@ -620,10 +627,147 @@ def kernel_revision() -> str:
     return h.hexdigest()[:12]
 
 
+def graph_ms(step, steps, warmup):
+    """Capture step() in a CUDA graph, replay it `warmup` times, then time
+    `steps` replays with CUDA events; ms per replay."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for _ in range(warmup):
+        g.replay()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(steps):
+        g.replay()
+    ev[1].record()
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]) / steps
+
+
+# Table tab:prot of the paper (million E+F steps/day, one RTX 4090, the
+# whole model in one CUDA graph): context only, other GPU and real molecules.
+PAPER_GRAPH_MSTEPS = {22: (172.80, 84.71, 56.47), 49: (154.29, 63.53, 39.82), 166: (77.14, 26.02, 15.57),
+                      2489: (5.65, 1.69, 1.00), 5807: (2.33, 0.70, 0.42)}
+
+
+def run_sweep(args):
+    """Single molecules of the paper's five sizes (synthetic random walks),
+    cutoff 4.5 A, 0/1/2 interaction layers: graph-replayed neighbor search +
+    energy + forces."""
+    import torch
+    from paper_2402_17660_gb300 import synth
+    from paper_2402_17660_gb300.tnet import TensorNet
+    dev = torch.device("cuda:0")
+    prec = {"fp32": 0, "bf16": 1, "tf32x3": 2}[args.precision]
+    rows = []
+    for n in (22, 49, 166, 2489, 5807):
+        s = synth.random_walk_molecule(n, seed=n)
+        z = torch.from_numpy(s.z).to(dev)
+        pos = torch.from_numpy(s.pos).to(dev)
+        for L in (0, 1, 2):
+            shape = synth.ModelShape(L=L, cutoff_upper=4.5)
+            W = synth.init_weights(shape, seed=0)
+            m = TensorNet(W, L=L, cutoff_upper=4.5, max_atoms=n, max_pairs=64 * n + 64, precision=prec,
+                          device=dev)
+            nl = m.neighbors(pos, None, None, 1)
+            E = torch.empty(1, dtype=torch.float64, device=dev)
+            Fo = torch.empty((n, 3), dtype=torch.float32, device=dev)
+            m.energy_forces(z, pos, nl, None, None, 1, out=(E, Fo, None))
+            torch.cuda.synchronize()
+            m.check_status("sweep")
+            npairs = int(nl.n_pairs.item())
+
+            def step():
+                m.neighbors(pos, None, None, 1, out=nl)
+                m.energy_forces(z, pos, nl, None, None, 1, out=(E, Fo, None))
+
+            ms = graph_ms(step, max(args.steps, 50), max(args.warmup, 20))
+            m.check_status("sweep")
+            rate = 1e3 / ms
+            rows.append({"atoms": n, "layers": L, "pairs": npairs, "ms_per_step": ms, "evals_per_s": rate,
+                         "Msteps_per_day": rate * 86400 / 1e6,
+                         "paper_rtx4090_graph_Msteps_per_day": PAPER_GRAPH_MSTEPS[n][L]})
+            del m
+    line = {"metric": "paper-shape sweep: TensorNet E+F steps/day, single molecules in vacuum", "unit": "Msteps/day",
+            "dtype": {0: "f32", 1: "bf16 GEMM / f32", 2: "f32 (GEMMs as 3xTF32 on the tensor cores)"}[prec],
+            "data": "synthetic: self-avoiding random walks (1.5 A steps, H/C/N/O) of the paper's five atom counts, "
+                    "random-init weights",
+            "config": {"cutoff_A": 4.5, "channels": 128, "rbf": 32, "pair_capacity": "64 per atom",
+                       "step": "neighbor search + energy + forces, one CUDA graph", "l2": "not flushed (as the paper)"},
+            "sweep": rows,
+            "note": "paper column: Table tab:prot, RTX 4090, graph variant, real molecules and trained models "
+                    "(context, not a target)"}
+    print(json.dumps(line))
+    return 0
+
+
+def run_neighbor_bench(args):
+    """tnet_neighbors alone on a random cloud of 32,768 particles at a density
+    giving 64 neighbors per particle within the 5 A cutoff, split into 1 to
+    1024 independent systems (each its own cloud of that density): the
+    paper's neighbor benchmark, where one shared cell list degrades with the
+    batch size; here cells are per system."""
+    import torch
+    from paper_2402_17660_gb300 import synth
+    from paper_2402_17660_gb300.tnet import TensorNet
+    dev = torch.device("cuda:0")
+    n_total, rc, nbr = 32768, 5.0, 64
+    rho = nbr / (4.0 / 3.0 * math.pi * rc ** 3)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = json.load(open(peaks_path)).get("hbm_gbs", 6800.0) if os.path.exists(peaks_path) else 6800.0
+    rng = np.random.default_rng(7)
+    rows = []
+    W = synth.init_weights(synth.ModelShape(), seed=0)
+    for B in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024):
+        nb = n_total // B
+        side = (nb / rho) ** (1.0 / 3.0)
+        pos_np = np.concatenate([rng.uniform(0, side, (nb, 3)) for _ in range(B)]).astype(np.float32)
+        batch_np = np.repeat(np.arange(B, dtype=np.int32), nb)
+        cap = int(nbr * 1.3 * n_total) + 1024
+        m = TensorNet(W, max_atoms=n_total, max_systems=B, max_pairs=cap, device=dev)
+        pos = torch.from_numpy(pos_np).to(dev)
+        batch = torch.from_numpy(batch_np).to(dev) if B > 1 else None
+        box = None   # clouds in vacuum: a 32-particle system is far narrower than 2 cutoffs
+        nl = m.neighbors(pos, batch, box, B, cutoff=rc)
+        torch.cuda.synchronize()
+        m.check_status("neighbor bench")
+        npairs = int(nl.n_pairs.item())
+        ms = graph_ms(lambda: m.neighbors(pos, batch, box, B, cutoff=rc, out=nl), max(args.steps, 50),
+                      max(args.warmup, 10))
+        m.check_status("neighbor bench")
+        # algorithmic bytes: positions, batch, row offsets, one int per pair,
+        # and the cell sort (cell index + sorted index + float4 copy per atom)
+        nbytes = n_total * (12 + 4 + 4 + 2 * (4 + 4 + 16)) + 4 * npairs
+        rows.append({"systems": B, "atoms_per_system": nb, "pairs": npairs, "pairs_per_atom": npairs / n_total,
+                     "ms_per_call": ms, "Gpairs_per_s": npairs / ms / 1e6,
+                     "hbm_GBs_algorithmic": nbytes / ms / 1e6, "hbm_frac_of_measured": nbytes / ms / 1e6 / hbm})
+        del m
+    line = {"metric": "tnet_neighbors time vs batch size (32,768 particles, 64 neighbors each)", "unit": "ms",
+            "data": "synthetic uniform random clouds in vacuum, one cube per system at the same density "
+                    "(small systems have fewer neighbors per particle: their surface)",
+            "config": {"cutoff_A": rc, "particles": n_total, "step": "one tnet_neighbors call in a CUDA graph",
+                       "l2": "not flushed"},
+            "rows": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
+    if args.neighbor_bench:
+        return run_neighbor_bench(args)
     return run_ours(args)
 
 

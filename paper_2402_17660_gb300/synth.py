@@ -485,6 +485,55 @@ def triclinic_water(n_side: int = 10, L: float = 31.04, tilt=(0.3, 0.2, -0.25), 
                   B.astype(np.float32)[None], 1, {"L": L, "tilt": tilt})
 
 
+def random_walk_molecule(n: int, seed: int = 0, step: float = 1.5, min_nonbonded: float = 1.2,
+                         radii=(4.5,), margin=1e-4) -> System:
+    """A molecule-like cluster in vacuum: a seeded self-avoiding random walk
+    of n atoms with `step` A bonds, every non-bonded distance >= min_nonbonded,
+    elements H/C/N/O with probabilities .5/.3/.1/.1, and no pair distance
+    within `margin` of a radius in `radii` (the stand-in for the paper's
+    single molecules of the same atom counts)."""
+    rng = np.random.default_rng(seed)
+    cell = max(min_nonbonded, 1.0)
+    grid: dict[tuple[int, int, int], list[int]] = {}
+    walk = np.zeros((n, 3))
+
+    def key(p):
+        return tuple(np.floor(p / cell).astype(int).tolist())
+
+    def ok(p, prev):
+        k = key(p)
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    for idx in grid.get((k[0] + dx, k[1] + dy, k[2] + dz), ()):
+                        if idx != prev and np.sum((walk[idx] - p) ** 2) < min_nonbonded ** 2:
+                            return False
+        return True
+
+    grid.setdefault(key(walk[0]), []).append(0)
+    k = 1
+    while k < n:
+        for _ in range(200):
+            d = rng.standard_normal(3)
+            p = walk[k - 1] + step * d / np.linalg.norm(d)
+            if ok(p, k - 1):
+                break
+        else:
+            raise RuntimeError("random walk stuck")
+        walk[k] = p
+        grid.setdefault(key(p), []).append(k)
+        k += 1
+    for _ in range(100):
+        bad = _near_radius_atoms(walk.astype(np.float32).astype(np.float64), None, radii, margin)
+        if bad.size == 0:
+            break
+        walk[bad] += rng.uniform(-1e-3, 1e-3, (len(bad), 3))
+    else:
+        raise RuntimeError("could not satisfy the pair-distance margin")
+    z = rng.choice(np.array([Z_H, Z_C, Z_N, Z_O], np.int32), n, p=[0.5, 0.3, 0.1, 0.1])
+    return System(f"walk{n}", z, walk.astype(np.float32), np.zeros(n, np.int32), None, 1)
+
+
 def workload(name: str) -> System:
     """The five named workloads:
     molecule32  - 32-atom molecule in vacuum

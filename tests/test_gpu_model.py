@@ -85,6 +85,21 @@ def test_water3000():
     _compare(synth.workload("water3000"))
 
 
+@pytest.mark.parametrize("L", [0, 1, 2])
+def test_paper_shape_molecule_cutoff_4_5(L):
+    """The shapes of the paper's single-molecule table: cutoff 4.5 A, 0, 1 or
+    2 interaction layers, on a 166-atom random-walk molecule."""
+    shape = synth.ModelShape(L=L, cutoff_upper=4.5)
+    Wl = synth.init_weights(shape, seed=0)
+    s = synth.random_walk_molecule(166, seed=166)
+    m = make_model(Wl, s, shape=shape, cutoff=4.5)
+    E, F = gpu_energy_forces(m, s, cutoff=4.5)
+    Es, Ei, Fo = oracle_energy_forces(Wl, s, shape)
+    e_err, f_err = energy_errors(E, Es, Ei, s.batch), force_error(F, Fo)
+    print(f"walk166 L={L}: rel energy err {e_err.max():.2e}, rel RMS force err {f_err:.2e}")
+    assert np.all(e_err <= E_TOL) and f_err <= F_TOL
+
+
 def test_triclinic_water():
     _compare(synth.triclinic_water(6, 18.6, seed=5))
 
