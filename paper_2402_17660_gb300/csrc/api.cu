@@ -90,6 +90,7 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     // edge MLP
     L->eu = take(f * U * K);
     L->phiu = take(f * U);
+    L->geo = take(16 * U);
     // (one set per layer, which the reverse pass reads, unless it recomputes them)
     const int64_t NLm = (NL > 0 && !d->recompute_edges) ? NL : 1;
     L->a1 = take(f * U * F * NLm);

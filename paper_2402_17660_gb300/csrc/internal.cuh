@@ -318,7 +318,7 @@ struct Layout {
     size_t Xin, qn, Xn, Y, M, Tn, dX;  // per layer (stride given below)
     size_t Xfin, h, hn, lno, ao, o, at, t, Ei;
     // edge MLP (undirected active edges)
-    size_t eu, phiu, a1, h1, a2, h2, a3, g;
+    size_t eu, phiu, geo, a1, h1, a2, h2, a3, g;
     // backward
     size_t gXa, gXb, gdX, gTn, gM, gY, gat, gao, ghn, gh, gU, gas2, gas1, gn0, gq0, gg, ga2, ga1, ge,
         gphiu, gvec;

@@ -22,6 +22,7 @@
 namespace tnet {
 
 constexpr int kMU = 4;  // edges whose loads are in flight together in the row kernels
+constexpr int kChunk = 128;  // row edges whose indices are staged in shared memory at a time
 
 // ----------------------------------------------------------- weights ---
 struct LayerW {
@@ -196,11 +197,13 @@ __global__ void k_lower_assign(const int32_t *__restrict__ row_ptr, const int32_
     }
 }
 
-// Radial basis and cutoff of each undirected active edge.
+// Radial basis and cutoff of each undirected active edge, and its geometry
+// (unit vector u_ij for i < j, and phi) for the embedding kernels.
 __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restrict__ box,
                            const int32_t *__restrict__ batch, const int2 *__restrict__ uij,
                            const int32_t *__restrict__ nu, int maxU, RadialParams rp,
-                           float *__restrict__ eu, float *__restrict__ phiu, OpCopy eu_cp) {
+                           float *__restrict__ eu, float *__restrict__ phiu, float4 *__restrict__ geo,
+                           OpCopy eu_cp) {
     const int U = *nu;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)U * rp.K;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -214,7 +217,11 @@ __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restric
         expnorm_k(d, k, rp, phi, 0.f, e, de);
         eu[t] = e;
         opcopy_store(eu_cp, t, e);
-        if (k == 0) phiu[u] = phi;
+        if (k == 0) {
+            phiu[u] = phi;
+            const float inv = 1.0f / d;
+            geo[u] = make_float4(x * inv, y * inv, zz * inv, phi);  // u_ij for i < j, and phi
+        }
     }
 }
 
@@ -260,16 +267,18 @@ __device__ __forceinline__ EdgeGeo edge_geo(const float *__restrict__ pos, const
 
 // X_raw_i = sum_j phi Z_ij (f^I I0 + f^A A0(u) + f^S S0(u)) over the active
 // edges of row i, in row order.  f^p = W^p e(d) + b^p depends only on d, so
-// it is computed once per undirected pair by a GEMM (fu, columns p*F + c).
+// it is computed once per undirected pair by a GEMM (fu, columns p*F + c);
+// so are u and phi (geo, from k_edge_rbf).
 // Block = F threads (thread = channel), persistent over atoms; loads for kMU
 // edges are in flight together.
-__global__ void k_emb_edges(const float *__restrict__ pos, const float *__restrict__ box,
-                            const int32_t *__restrict__ batch, const int32_t *__restrict__ z,
-                            const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                            const int32_t *__restrict__ pair_of, int N, int F, int max_z, RadialParams rp,
-                            const float *__restrict__ fu, const float *__restrict__ Ta,
-                            const float *__restrict__ Tb, float *__restrict__ Xraw, int32_t *status,
-                            OpCopy Xraw_cp) {
+template <int F>
+__global__ void __launch_bounds__(F) k_emb_edges(const float4 *__restrict__ geo, const int32_t *__restrict__ z,
+                                                 const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                                 const int32_t *__restrict__ pair_of, int N, int max_z,
+                                                 const float *__restrict__ fu, const float *__restrict__ Ta,
+                                                 const float *__restrict__ Tb, float *__restrict__ Xraw,
+                                                 int32_t *status, OpCopy Xraw_cp) {
+    __shared__ int32_t s_u[kChunk], s_zs[kChunk];  // pair index; element of the column atom, signed by direction
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         int zi = z[i];
@@ -279,39 +288,52 @@ __global__ void k_emb_edges(const float *__restrict__ pos, const float *__restri
         }
         const float ta = Ta[(int64_t)zi * F + c];
         float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const int e1 = row_ptr[i + 1];
-        for (int eb = row_ptr[i]; eb < e1; eb += kMU) {
-            int uu[kMU], jj[kMU];
-#pragma unroll
-            for (int k = 0; k < kMU; ++k) {
-                const int e = eb + k;
-                uu[k] = e < e1 ? pair_of[e] : -1;
-                jj[k] = e < e1 ? col[e] : 0;
+        const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
+        for (int cb = e0; cb < e1; cb += kChunk) {
+            const int n = e1 - cb < kChunk ? e1 - cb : kChunk;
+            __syncthreads();
+            for (int t = c; t < n; t += F) {
+                const int u = pair_of[cb + t];
+                s_u[t] = u;
+                int zj = 0, j = i;
+                if (u >= 0) {
+                    j = col[cb + t];
+                    zj = z[j];
+                    zj = (zj < 0 || zj >= max_z) ? 0 : zj;
+                }
+                s_zs[t] = j > i ? zj : -1 - zj;   // u_ij = +u of the pair when i is its first atom
             }
-            float f[kMU][3], tb[kMU], r[kMU][3];
+            __syncthreads();
+            for (int k0 = 0; k0 < n; k0 += kMU) {
+                int uu[kMU], zz[kMU];
 #pragma unroll
-            for (int k = 0; k < kMU; ++k) {
-                if (uu[k] < 0) continue;
-                const float *fp = fu + (int64_t)uu[k] * 3 * F + c;
-                f[k][0] = fp[0]; f[k][1] = fp[F]; f[k][2] = fp[2 * F];
-                int zj = z[jj[k]];
-                zj = (zj < 0 || zj >= max_z) ? 0 : zj;
-                tb[k] = Tb[(int64_t)zj * F + c];
-                pair_vec(pos, box, batch, i, jj[k], r[k][0], r[k][1], r[k][2]);
-            }
+                for (int k = 0; k < kMU; ++k) {
+                    uu[k] = k0 + k < n ? s_u[k0 + k] : -1;
+                    zz[k] = k0 + k < n ? s_zs[k0 + k] : 0;
+                }
+                float f[kMU][3], tb[kMU];
+                float4 gk[kMU];
 #pragma unroll
-            for (int k = 0; k < kMU; ++k) {
-                if (uu[k] < 0) continue;
-                const float d = sqrtf(r[k][0] * r[k][0] + r[k][1] * r[k][1] + r[k][2] * r[k][2]);
-                const float inv = 1.0f / d;
-                const float ux = r[k][0] * inv, uy = r[k][1] * inv, uz = r[k][2] * inv;
-                const float pz = cutoff_phi(d, rp) * (ta + tb[k]);
-                const float cI = pz * f[k][0], cA = pz * f[k][1], cS = pz * f[k][2];
-                v[0] += cI;
-                v[1] += cA * ux; v[2] += cA * uy; v[3] += cA * uz;
-                v[4] += cS * (ux * ux - (1.0f / 3.0f));
-                v[5] += cS * (uy * uy - (1.0f / 3.0f));
-                v[6] += cS * ux * uy; v[7] += cS * ux * uz; v[8] += cS * uy * uz;
+                for (int k = 0; k < kMU; ++k) {
+                    if (uu[k] < 0) continue;
+                    const float *fp = fu + (int64_t)uu[k] * 3 * F + c;
+                    f[k][0] = fp[0]; f[k][1] = fp[F]; f[k][2] = fp[2 * F];
+                    tb[k] = Tb[(int64_t)(zz[k] >= 0 ? zz[k] : -1 - zz[k]) * F + c];
+                    gk[k] = geo[uu[k]];
+                }
+#pragma unroll
+                for (int k = 0; k < kMU; ++k) {
+                    if (uu[k] < 0) continue;
+                    const float sg = zz[k] >= 0 ? 1.0f : -1.0f;
+                    const float ux = sg * gk[k].x, uy = sg * gk[k].y, uz = sg * gk[k].z;
+                    const float pz = gk[k].w * (ta + tb[k]);
+                    const float cI = pz * f[k][0], cA = pz * f[k][1], cS = pz * f[k][2];
+                    v[0] += cI;
+                    v[1] += cA * ux; v[2] += cA * uy; v[3] += cA * uz;
+                    v[4] += cS * (ux * ux - (1.0f / 3.0f));
+                    v[5] += cS * (uy * uy - (1.0f / 3.0f));
+                    v[6] += cS * ux * uy; v[7] += cS * ux * uz; v[8] += cS * uy * uz;
+                }
             }
         }
         store_coords(Xraw, i, c, N, F, v);
@@ -373,8 +395,6 @@ __global__ void k_node_norm(const float *__restrict__ X, int N, int F, float *__
         store_coords_cp(Xn_cp, i, c, N, F, v);
     }
 }
-
-constexpr int kChunk = 128;  // row edges whose indices are staged in shared memory at a time
 
 // M_i = sum_j g^p_ij Y^p_j over the row (block = F threads, thread = channel).
 // g of pair u is stored plane-major, g[u][p][c], so each of its three loads is
@@ -1503,7 +1523,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     float *eu = f32(Lw.eu), *phiu = f32(Lw.phiu), *fu = f32(Lw.fu);
-    k_edge_rbf<<<pair_grid, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu, eu_cp);
+    float4 *geo = wsp<float4>(ctx, Lw.geo);
+    k_edge_rbf<<<pair_grid, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu, geo, eu_cp);
     count_launch();
     k_elem_tables<<<d.max_z, F, 0, st>>>(W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
     count_launch();
@@ -1530,8 +1551,11 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
           *hs1 = f32(Lw.hs1), *as2 = f32(Lw.as2), *s = f32(Lw.s), *q0 = f32(Lw.q0);
     float2 *ln0 = wsp<float2>(ctx, Lw.ln0);
     const int atom_blocks = N < sms * ctx->tune[T_ROW_BLOCKS] ? N : sms * ctx->tune[T_ROW_BLOCKS];
-    k_emb_edges<<<atom_blocks, F, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, F, d.max_z, rp, fu, Ta,
-                                           Tb, Xraw, status, nbf);
+#define EMB_FWD(FF)                                                                                           \
+    k_emb_edges<FF><<<atom_blocks, FF, 0, st>>>(geo, z, row_ptr, col, pair_of, N, d.max_z, fu, Ta, Tb, Xraw, status, \
+                                                nbf)
+    TNET_F_SWITCH(F, EMB_FWD);
+#undef EMB_FWD
     count_launch();
     k_norm_ln<<<N, F, 0, st>>>(Xraw, N, F, W.emb_ln_g, W.emb_ln_b, n0, ln0, q0);
     count_launch();
