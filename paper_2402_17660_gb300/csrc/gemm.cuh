@@ -48,23 +48,32 @@ __device__ __forceinline__ void store_copy4(const OpCopy &c, int64_t idx, const 
     }
 }
 
+// Each functor splits into pre() (the loads: issued for several rows before
+// the accumulator values arrive, so their latency overlaps) and post() (the
+// arithmetic and stores); operator() runs both.  pre() may be given a row or
+// column clamped into range, and its result is then unused.
 struct EpiStore {  // C = v (+ C when accumulate)
     float *C;
     int64_t ldc;
     int accumulate;
-    __device__ void operator()(int z, int64_t m, int n, float4 o) const {
-        float4 *p = reinterpret_cast<float4 *>(C + m * ldc + n);
-        if (accumulate) {
-            const float4 c = *p;
-            o.x += c.x; o.y += c.y; o.z += c.z; o.w += c.w;
-        }
-        *p = o;
+    struct Pre {
+        float4 c;
+    };
+    __device__ Pre pre(int, int64_t m, int n) const {
+        return Pre{accumulate ? *reinterpret_cast<const float4 *>(C + m * ldc + n) : make_float4(0.f, 0.f, 0.f, 0.f)};
     }
+    __device__ void post(int, int64_t m, int n, float4 o, const Pre &p) const {
+        if (accumulate) {
+            o.x += p.c.x; o.y += p.c.y; o.z += p.c.z; o.w += p.c.w;
+        }
+        *reinterpret_cast<float4 *>(C + m * ldc + n) = o;
+    }
+    __device__ void operator()(int z, int64_t m, int n, float4 o) const { post(z, m, n, o, pre(z, m, n)); }
 };
 
 struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m] (+ operand copy)
     const float *bias;
-    float *pre;
+    float *pre_out;
     int64_t ldp;
     float *out;
     int64_t ldo;
@@ -72,44 +81,55 @@ struct EpiBiasAct {  // a = v + bias; pre = a; out = act(a) * rowscale[m] (+ ope
     const float *rowscale;
     OpCopy out_cp;
     int64_t ldoc;
-    __device__ void operator()(int z, int64_t m, int n, float4 vv) const {
+    struct Pre {
+        float4 b;
+        float rs;
+    };
+    __device__ Pre pre(int, int64_t m, int n) const {
+        return Pre{bias ? *reinterpret_cast<const float4 *>(bias + n) : make_float4(0.f, 0.f, 0.f, 0.f),
+                   rowscale ? rowscale[m] : 1.0f};
+    }
+    __device__ void post(int, int64_t m, int n, float4 vv, const Pre &p) const {
         const float v[4] = {vv.x, vv.y, vv.z, vv.w};
+        const float bv[4] = {p.b.x, p.b.y, p.b.z, p.b.w};
         float a[4], o[4];
-        const float rs = rowscale ? rowscale[m] : 1.0f;
-        const float4 b4 = bias ? *reinterpret_cast<const float4 *>(bias + n) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             a[q] = v[q] + bv[q];
-            o[q] = (silu ? silu_f(a[q]) : a[q]) * rs;
+            o[q] = (silu ? silu_f(a[q]) : a[q]) * p.rs;
         }
-        if (pre) *reinterpret_cast<float4 *>(pre + m * ldp + n) = make_float4(a[0], a[1], a[2], a[3]);
+        if (pre_out) *reinterpret_cast<float4 *>(pre_out + m * ldp + n) = make_float4(a[0], a[1], a[2], a[3]);
         if (out) *reinterpret_cast<float4 *>(out + m * ldo + n) = make_float4(o[0], o[1], o[2], o[3]);
         if (out_cp.mode) store_copy4(out_cp, m * ldoc + n, o);
     }
+    __device__ void operator()(int z, int64_t m, int n, float4 o) const { post(z, m, n, o, pre(z, m, n)); }
 };
 
 struct EpiGradAct {  // out = v * silu'(pre)  (+ out when accumulate) (+ operand copy)
-    const float *pre;
+    const float *pre_in;
     int64_t ldp;
     float *out;
     int64_t ldo;
     int accumulate;
     OpCopy out_cp;
     int64_t ldoc;
-    __device__ void operator()(int z, int64_t m, int n, float4 vv) const {
-        const float v[4] = {vv.x, vv.y, vv.z, vv.w};
-        const float4 a = *reinterpret_cast<const float4 *>(pre + m * ldp + n);
-        float o[4] = {v[0] * silu_grad_f(a.x), v[1] * silu_grad_f(a.y), v[2] * silu_grad_f(a.z),
-                      v[3] * silu_grad_f(a.w)};
-        float4 *p = reinterpret_cast<float4 *>(out + m * ldo + n);
+    struct Pre {
+        float4 a, c;
+    };
+    __device__ Pre pre(int, int64_t m, int n) const {
+        return Pre{*reinterpret_cast<const float4 *>(pre_in + m * ldp + n),
+                   accumulate ? *reinterpret_cast<const float4 *>(out + m * ldo + n) : make_float4(0.f, 0.f, 0.f, 0.f)};
+    }
+    __device__ void post(int, int64_t m, int n, float4 vv, const Pre &p) const {
+        float o[4] = {vv.x * silu_grad_f(p.a.x), vv.y * silu_grad_f(p.a.y), vv.z * silu_grad_f(p.a.z),
+                      vv.w * silu_grad_f(p.a.w)};
         if (accumulate) {
-            const float4 c = *p;
-            o[0] += c.x; o[1] += c.y; o[2] += c.z; o[3] += c.w;
+            o[0] += p.c.x; o[1] += p.c.y; o[2] += p.c.z; o[3] += p.c.w;
         }
-        *p = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4 *>(out + m * ldo + n) = make_float4(o[0], o[1], o[2], o[3]);
         if (out_cp.mode) store_copy4(out_cp, m * ldoc + n, o);
     }
+    __device__ void operator()(int z, int64_t m, int n, float4 o) const { post(z, m, n, o, pre(z, m, n)); }
 };
 
 // --------------------------------------------------------------- kernel ---

@@ -379,6 +379,15 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int rsub = lane >> 2, csub = (lane & 3) * 4;
 #pragma unroll 1
             for (int c0 = c_begin; c0 < c_end; c0 += 16) {
+                const int n = n0 + c0 + csub;
+                // the epilogue's loads for this lane's 4 rows first (rows and
+                // columns clamped into range), so they overlap the TMEM read
+                typename Epi::Pre pr[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int row = m0 + 32 * q + rsub + 8 * k;
+                    pr[k] = epi.pre(z, rbase + (row < Mrow ? row : Mrow - 1), n < P.N ? n : P.N - 4);
+                }
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * BN + c0), v);
 #pragma unroll
@@ -386,13 +395,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                     *reinterpret_cast<float4 *>(stg + lane * STG_LD + 4 * j) =
                         make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 __syncwarp();
-                const int n = n0 + c0 + csub;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int r = rsub + 8 * k;
                     const int row = m0 + 32 * q + r;
                     const float4 w = *reinterpret_cast<const float4 *>(stg + r * STG_LD + csub);
-                    if (row < Mrow && n < P.N) epi(z, rbase + row, n, w);
+                    if (row < Mrow && n < P.N) epi.post(z, rbase + row, n, w, pr[k]);
                 }
                 __syncwarp();
             }
