@@ -21,17 +21,18 @@ EncodeFn tensor_map_encoder() {
 }
 
 static int make_map(CUtensorMap *m, CUtensorMapDataType dt, int esz, const void *base, int64_t rows, int64_t cols,
-                    int64_t ld, int box_rows) {
+                    int64_t ld, int box_rows, int row_bytes) {
     EncodeFn enc = tensor_map_encoder();
     if (!enc) return TNET_ERR_CUDA;
-    if (rows < 1 || cols < 1 || box_rows < 1 || box_rows > 256) return TNET_ERR_ARG;
+    if (rows < 1 || cols < 1 || box_rows < 1 || box_rows > 256 || (row_bytes != 128 && row_bytes != 64))
+        return TNET_ERR_ARG;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(ld * esz)};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};  // 128-byte rows
+    cuuint32_t box[2] = {(cuuint32_t)(row_bytes / esz), (cuuint32_t)box_rows};  // rows of row_bytes
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         fprintf(stderr, "libtnet: cuTensorMapEncodeTiled failed (%d)\n", (int)r);
         return TNET_ERR_CUDA;
@@ -40,10 +41,11 @@ static int make_map(CUtensorMap *m, CUtensorMapDataType dt, int esz, const void 
 }
 
 int make_map_bf16(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
-    return make_map(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, rows, cols, ld, box_rows);
+    return make_map(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, rows, cols, ld, box_rows, 128);
 }
-int make_map_f32(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
-    return make_map(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, rows, cols, ld, box_rows);
+int make_map_f32(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                 int row_bytes) {
+    return make_map(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, rows, cols, ld, box_rows, row_bytes);
 }
 
 }  // namespace tc

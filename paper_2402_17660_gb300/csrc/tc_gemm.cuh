@@ -20,9 +20,10 @@
 //          through HBM.
 //
 // Persistent CTAs walk 128 x BN output tiles.  Warp 0 issues TMA loads into a
-// 2-4 stage shared-memory ring, warp 1 owns TMEM and issues the MMAs (four
-// 32-byte k-steps per 128-byte k-block) into one of two accumulators, so the
-// epilogue of a tile overlaps the MMAs of the next.  Sixteen epilogue warps
+// 3-4 stage shared-memory ring (k-blocks of 128-byte rows for BF16, 64-byte
+// rows for 3xTF32, whose stage holds four tiles), warp 1 owns TMEM and issues
+// the MMAs (32-byte k-steps) into one of two accumulators, so the epilogue of
+// a tile overlaps the MMAs of the next.  Sixteen epilogue warps
 // drain TMEM (warp w reads lanes 32*(w%4) .. +31, a quarter of the tile's
 // columns each) and run the fused epilogue.  Every mbarrier wait is bounded;
 // on expiry the kernel records TNET_ERR_TIMEOUT, the other roles stop, the
@@ -124,15 +125,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Shared-memory matrix descriptor: K-major tile with 128-byte rows stored in
-// the 128B-swizzle layout TMA writes; 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major tile with ROW-byte rows (128 or
+// 64) stored in the matching swizzle layout TMA writes; 8-row groups 8 * ROW
+// bytes apart.  Swizzle codes: 2 = 128-byte, 4 = 64-byte.
+template <int ROW>
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
+    static_assert(ROW == 128 || ROW == 64, "row bytes");
     uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);  // start address / 16
-    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                   // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);         // start address / 16
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((8 * ROW) >> 4) << 32;           // stride byte offset: 8 rows
+    d |= (uint64_t)1 << 46;                          // descriptor version for tcgen05
+    d |= (uint64_t)(ROW == 128 ? 2 : 4) << 61;       // swizzle mode
     return d;
 }
 
@@ -156,17 +160,22 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint
 
 template <int BN, bool X3 = false>
 struct TileCfg {
-    // one k-block is 128 bytes of K per row: 64 bf16 or 32 fp32 elements
-    static constexpr int BKE = X3 ? 32 : 64;
-    static constexpr uint32_t A_BYTES = BM * 128;
-    static constexpr uint32_t B_BYTES = BN * 128;
+    // one k-block is ROW bytes of K per row: 64 bf16 (128-byte rows), or 16
+    // fp32 (64-byte rows: the 3xTF32 stage holds A, A_lo, B and B_lo, and the
+    // halved rows let four stages fit)
+    static constexpr int ROW = X3 ? 64 : 128;
+    static constexpr int BKE = X3 ? 16 : 64;
+    static constexpr int KSTEPS = ROW / 32;  // MMA k-steps (32 bytes of K) per k-block
+    static constexpr uint32_t A_BYTES = BM * ROW;
+    static constexpr uint32_t B_BYTES = BN * ROW;
     // bytes TMA brings per pipeline stage: A, B (+ B_lo for TF32X3; A_lo is
     // formed in shared memory)
     static constexpr uint32_t STAGE_TX = A_BYTES + (X3 ? 2 : 1) * B_BYTES;
-    static constexpr int STAGES = X3 ? 2 : (BN >= 192 ? 3 : 4);
+    static constexpr int STAGES = X3 ? 4 : (BN >= 192 ? 3 : 4);
     static constexpr uint32_t TMEM_COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
     static constexpr uint32_t STAGE_BYTES = EPI_WARPS * 32 * STG_LD * 4;  // epilogue transpose buffers
     static constexpr size_t SMEM = 1024 + STAGES * (size_t)(STAGE_TX + (X3 ? A_BYTES : 0)) + 256 + STAGE_BYTES;
+    static_assert(SMEM <= 232448, "dynamic shared memory above 227 KB");
 };
 
 // Tile index -> (class, first row, first column); false past the last tile.
@@ -292,16 +301,17 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     fence_after();
                     const uint32_t a0 = smem_u32(sA + s * C::A_BYTES), b0 = smem_u32(sB + s * C::B_BYTES);
-                    // four 32-byte k-steps per 128-byte k-block in both modes
+                    // 32-byte k-steps: four per 128-byte k-block (bf16), two per
+                    // 64-byte k-block (3xTF32)
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint64_t da = sdesc_sw128(a0 + k * 32), db = sdesc_sw128(b0 + k * 32);
+                    for (int k = 0; k < C::KSTEPS; ++k) {
+                        const uint64_t da = sdesc_sw<C::ROW>(a0 + k * 32), db = sdesc_sw<C::ROW>(b0 + k * 32);
                         const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
                         if (X3) {
                             const uint32_t al = smem_u32(sAlo + s * C::A_BYTES), bl = smem_u32(sBlo + s * C::B_BYTES);
                             umma_tf32(d, da, db, idesc, acc);
-                            umma_tf32(d, sdesc_sw128(al + k * 32), db, idesc, 1u);
-                            umma_tf32(d, da, sdesc_sw128(bl + k * 32), idesc, 1u);
+                            umma_tf32(d, sdesc_sw<C::ROW>(al + k * 32), db, idesc, 1u);
+                            umma_tf32(d, da, sdesc_sw<C::ROW>(bl + k * 32), idesc, 1u);
                         } else {
                             umma_bf16(d, da, db, idesc, acc);
                         }
@@ -426,7 +436,8 @@ EncodeFn tensor_map_encoder();  // resolved once through the runtime (tc_gemm.cu
 // 2-D tensor maps (bf16 or fp32): `rows` rows of `cols` elements, row pitch
 // `ld` elements, box of `box_rows` x 128 bytes, 128B swizzle, zero fill.
 int make_map_bf16(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
-int make_map_f32(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows);
+int make_map_f32(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                 int row_bytes);
 
 // Operands of one GEMM: A, B and (TF32X3 only) B's split: B = B_hi, Blo = B_lo.
 struct TcOperands {
@@ -447,9 +458,9 @@ int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *
     CUtensorMap ma, mb, mal, mbl;
     int rc;
     if (X3) {
-        if ((rc = make_map_f32(&ma, o.A, o.a_rows, P.K, o.lda, BM))) return rc;
-        if ((rc = make_map_f32(&mb, o.B, o.b_rows, P.K, o.ldb, BN))) return rc;
-        if ((rc = make_map_f32(&mbl, o.Blo, o.b_rows, P.K, o.ldb, BN))) return rc;
+        if ((rc = make_map_f32(&ma, o.A, o.a_rows, P.K, o.lda, BM, C::ROW))) return rc;
+        if ((rc = make_map_f32(&mb, o.B, o.b_rows, P.K, o.ldb, BN, C::ROW))) return rc;
+        if ((rc = make_map_f32(&mbl, o.Blo, o.b_rows, P.K, o.ldb, BN, C::ROW))) return rc;
         mal = ma;  // unused: A_lo is formed in shared memory
     } else {
         if ((rc = make_map_bf16(&ma, o.A, o.a_rows, P.K, o.lda, BM))) return rc;
