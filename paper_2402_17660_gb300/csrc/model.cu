@@ -204,24 +204,36 @@ __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restric
                            const int32_t *__restrict__ nu, int maxU, RadialParams rp,
                            float *__restrict__ eu, float *__restrict__ phiu, float4 *__restrict__ geo,
                            OpCopy eu_cp) {
-    const int U = *nu;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)U * rp.K;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int u = (int)(t / rp.K), k = (int)(t % rp.K);
-        const int2 p = uij[u];
-        float x, y, zz;
-        pair_vec(pos, box, batch, p.x, p.y, x, y, zz);
-        const float d = sqrtf(norm2_rn(x, y, zz));
-        const float phi = cutoff_phi(d, rp);
-        float e, de;
-        expnorm_k(d, k, rp, phi, 0.f, e, de);
-        eu[t] = e;
-        opcopy_store(eu_cp, t, e);
-        if (k == 0) {
+    // a block takes groups of P pairs: P threads compute the pairs' geometry
+    // once, then all threads evaluate the P x K basis values from it
+    __shared__ float s_d[256], s_phi[256];
+    const int U = *nu, K = rp.K;
+    const int P = blockDim.x / K > 0 ? blockDim.x / K : 1;
+    for (int64_t u0 = (int64_t)blockIdx.x * P; u0 < U; u0 += (int64_t)gridDim.x * P) {
+        const int np = U - u0 < P ? (int)(U - u0) : P;
+        if (threadIdx.x < np) {
+            const int u = (int)u0 + threadIdx.x;
+            const int2 p = uij[u];
+            float x, y, zz;
+            pair_vec(pos, box, batch, p.x, p.y, x, y, zz);
+            const float d = sqrtf(norm2_rn(x, y, zz));
+            const float phi = cutoff_phi(d, rp);
+            s_d[threadIdx.x] = d;
+            s_phi[threadIdx.x] = phi;
             phiu[u] = phi;
             const float inv = 1.0f / d;
             geo[u] = make_float4(x * inv, y * inv, zz * inv, phi);  // u_ij for i < j, and phi
         }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < np * K; idx += blockDim.x) {
+            const int q = idx / K, k = idx % K;
+            float e, de;
+            expnorm_k(s_d[q], k, rp, s_phi[q], 0.f, e, de);
+            const int64_t t = (u0 + q) * K + k;
+            eu[t] = e;
+            opcopy_store(eu_cp, t, e);
+        }
+        __syncthreads();
     }
 }
 
@@ -230,16 +242,23 @@ __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restric
 __global__ void k_elem_tables(const float *__restrict__ emb, const float *__restrict__ W,
                               const float *__restrict__ b, int F, float *__restrict__ Ta,
                               float *__restrict__ Tb) {
-    const int z = blockIdx.x, c = threadIdx.x;
-    const float *e = emb + (int64_t)z * F;
-    const float *w = W + (int64_t)c * 2 * F;
-    float sa = 0.f, sb = 0.f;
-    for (int k = 0; k < F; ++k) {
-        sa = fmaf(w[k], e[k], sa);
-        sb = fmaf(w[F + k], e[k], sb);
+    // block per element z; warp per output row of W (lanes along the row, so
+    // the reads of W are coalesced), a fixed-order warp reduction
+    extern __shared__ float e[];
+    const int z = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = threadIdx.x; k < F; k += blockDim.x) e[k] = emb[(int64_t)z * F + k];
+    __syncthreads();
+    for (int r = warp; r < 2 * F; r += nw) {  // rows c (Ta) and F + c (Tb)
+        const int c = r % F, half = r / F;
+        const float *w = W + (int64_t)c * 2 * F + half * F;
+        float s = 0.f;
+        for (int k = lane; k < F; k += 32) s = fmaf(w[k], e[k], s);
+        s = warp_sum(s);
+        if (lane == 0) {
+            if (half == 0) Ta[(int64_t)z * F + c] = s;
+            else Tb[(int64_t)z * F + c] = s + b[c];
+        }
     }
-    Ta[(int64_t)z * F + c] = sa;
-    Tb[(int64_t)z * F + c] = sb + b[c];
 }
 
 // ------------------------------------------------------- embedding ---
@@ -984,11 +1003,10 @@ __global__ void k_emb_bwd(const float *__restrict__ pos, const float *__restrict
 //   gfu[u]         = dE/df^p summed over both uses (columns p*F + c).
 // Pair-parallel, so small systems still fill the GPU.
 template <int CPL>
-__global__ void k_emb_bwd_pairs(const float *__restrict__ pos, const float *__restrict__ box,
-                                const int32_t *__restrict__ batch, const int32_t *__restrict__ z,
+__global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *__restrict__ z,
                                 const int2 *__restrict__ uij, const int32_t *__restrict__ ue,
                                 const int32_t *__restrict__ rev, const int32_t *__restrict__ nu, int N, int max_z,
-                                RadialParams rp, const float *__restrict__ fu, const float *__restrict__ Ta,
+                                const float *__restrict__ fu, const float *__restrict__ Ta,
                                 const float *__restrict__ Tb, const float *__restrict__ gXraw,
                                 float *__restrict__ gfu, float4 *__restrict__ edge_g,
                                 OpCopy gfu_cp) {
@@ -1000,12 +1018,8 @@ __global__ void k_emb_bwd_pairs(const float *__restrict__ pos, const float *__re
         const int u = (int)uu;
         const int2 p = uij[u];
         const int i = p.x, j = p.y;
-        float x, y, zz;
-        pair_vec(pos, box, batch, i, j, x, y, zz);
-        const float d = sqrtf(norm2_rn(x, y, zz));
-        const float inv = 1.0f / d;
-        const float ux = x * inv, uy = y * inv, uz = zz * inv;
-        const float phi = cutoff_phi(d, rp);
+        const float4 gu = geo[u];  // u_ij and phi of the pair (k_edge_rbf)
+        const float ux = gu.x, uy = gu.y, uz = gu.z, phi = gu.w;
         const float bxx = ux * ux - (1.0f / 3.0f), byy = uy * uy - (1.0f / 3.0f);
         const float bxy = ux * uy, bxz = ux * uz, byz = uy * uz;
         int zi = z[i], zj = z[j];
@@ -1526,7 +1540,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     float4 *geo = wsp<float4>(ctx, Lw.geo);
     k_edge_rbf<<<pair_grid, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu, geo, eu_cp);
     count_launch();
-    k_elem_tables<<<d.max_z, F, 0, st>>>(W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
+    k_elem_tables<<<d.max_z, 256, sizeof(float) * F, st>>>(W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
     count_launch();
     TNET_LAUNCH_CHECK();
     {   // radial projections f^p = W^p e(d) + b^p, once per undirected pair
@@ -1834,8 +1848,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         k_emb_bwd<CPL><<<bwd_blocks, 256, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, d.max_z, rp, \
                                                    fu, Ta, Tb, gXraw, 1, gfu, edge_g, gA, gB, gfu_cp);        \
     else                                                                                                     \
-        k_emb_bwd_pairs<CPL><<<pair_grid, 256, 0, st>>>(pos, box, batch, z, uij, ue, rev, nu, N, d.max_z, rp, fu, \
-                                                      Ta, Tb, gXraw, gfu, edge_g, gfu_cp)
+        k_emb_bwd_pairs<CPL><<<pair_grid, 256, 0, st>>>(geo, z, uij, ue, rev, nu, N, d.max_z, fu, Ta, Tb, gXraw, \
+                                                      gfu, edge_g, gfu_cp)
     switch (F / 32) {
         case 2: EMB_BWD(2); break;
         case 4: EMB_BWD(4); break;
