@@ -249,12 +249,14 @@ int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const float *B, 
                            int32_t *status_dev, tnet_stream_t stream);
 
 /* ---- tuning (no counterpart in the paper) ---------------------------------
- * Launch-shape knobs of a context: grid sizes and GEMM column tiles.  Every
- * value is valid on any input; the choice only changes speed.  Knob k takes
+ * Launch-shape knobs of a context: grid sizes, GEMM column tiles and whether
+ * kernels use programmatic dependent launch (the next kernel is scheduled
+ * while the previous one drains).  Every value is valid on any input; the
+ * choice only changes speed.  Knob k takes
  * one of tnet_tuning_candidates(k, ...) (the count is returned; values are
  * written up to max).  tnet_set_tuning rejects values outside the candidate
- * lists.  An autotuner times the candidates on a real input and sets the
- * fastest (paper_2402_17660_gb300.tnet.autotune). */
+ * lists.  An autotuner times the candidates on a real input (as CUDA-graph
+ * replays) and sets the fastest (paper_2402_17660_gb300.tnet.autotune). */
 int tnet_tuning_knobs(void);
 const char *tnet_tuning_name(int knob);
 int tnet_tuning_candidates(int knob, int32_t *values, int max);

@@ -199,13 +199,15 @@ void ProfSeq::mark(int tag) {
 
 using namespace tnet;
 
+thread_local int tnet::tl_pdl = 1;
+
 // Candidate values of each tuning knob (TuneKnob) and the default's index.
 static const int kTuneCandidates[T_NKNOBS][4] = {{1, 2, 3, 4}, {192, 128, 0, 0}, {256, 128, 0, 0}, {4, 8, 16, 0},
-                                                 {4, 8, 16, 0}};
-static const int kTuneCount[T_NKNOBS] = {4, 2, 2, 3, 3};
-static const int kTuneDefault[T_NKNOBS] = {2, 0, 0, 1, 1};
-static const char *kTuneNames[T_NKNOBS] = {"gemm_ctas_per_sm", "tc_tile_n_3f", "tc_tile_n_2f", "row_blocks_per_sm",
-                                           "pair_blocks_per_sm"};
+                                                 {4, 8, 16, 0}, {1, 0, 0, 0}};
+static const int kTuneCount[T_NKNOBS] = {4, 2, 2, 3, 3, 2};
+static const int kTuneDefault[T_NKNOBS] = {2, 0, 0, 1, 1, 0};
+static const char *kTuneNames[T_NKNOBS] = {"gemm_ctas_per_sm", "tc_tile_n_3f",       "tc_tile_n_2f",
+                                           "row_blocks_per_sm", "pair_blocks_per_sm", "programmatic_launch"};
 
 static const char *kTagNames[P_NTAGS] = {
     "neighbors", "graph_prep", "emb_edges", "emb_node", "mlp1", "mlp2", "mlp3", "message",
@@ -373,6 +375,7 @@ int tnet_neighbors(tnet_ctx *c, int N, int S, const float *pos, const int32_t *b
     if (!row_ptr || !n_pairs_dev || (cap > 0 && !col)) return TNET_ERR_ARG;
     if (cap < 0 || cap > c->max_pairs || !(cutoff > 0.f) || !isfinite(cutoff)) return TNET_ERR_ARG;
     if (S > 1 && !batch) return TNET_ERR_ARG;
+    PdlScope pdl_scope(c->tune[T_PDL]);
     return neighbors_impl(c, N, S, pos, batch, box, cutoff, row_ptr, col, cap, n_pairs_dev, status,
                           (cudaStream_t)stream);
 }
@@ -385,6 +388,7 @@ int tnet_energy_forces(tnet_ctx *c, const float *w, int N, int S, const int32_t 
     if (rc) return rc;
     if (!w || !z || !row_ptr || !col || !energy) return TNET_ERR_ARG;
     if (S > 1 && !batch) return TNET_ERR_ARG;
+    PdlScope pdl_scope(c->tune[T_PDL]);
     return energy_forces_impl(c, w, N, S, z, pos, batch, box, row_ptr, col, seed, energy, forces, grad_w,
                               status, (cudaStream_t)stream);
 }
@@ -396,6 +400,7 @@ int tnet_md_step(tnet_ctx *c, const float *w, int N, const int32_t *z, const flo
     if (rc) return rc;
     if (!w || !z || !inv_mass || !vel || (n_steps > 0 && (!e_kin || !e_pot))) return TNET_ERR_ARG;
     if (!(dt > 0.f) || !(skin >= 0.f) || rebuild_every < 1 || n_steps < 0) return TNET_ERR_ARG;
+    PdlScope pdl_scope(c->tune[T_PDL]);
     return md_impl(c, w, N, z, inv_mass, pos, vel, box, dt, skin, rebuild_every, n_steps, e_kin, e_pot,
                    status, (cudaStream_t)stream);
 }

@@ -135,6 +135,7 @@ struct EpiGradAct {  // out = v * silu'(pre)  (+ out when accumulate) (+ operand
 // --------------------------------------------------------------- kernel ---
 template <bool TA, bool TB, class Epi>
 __global__ void __launch_bounds__(GTHREADS) k_sgemm(GemmShape P, Epi epi) {
+    pdl_entry();
     __shared__ __align__(16) float As[2][GBK][GBM];
     __shared__ __align__(16) float Bs[2][GBK][GBN];
     const int z = blockIdx.z;
@@ -266,7 +267,7 @@ inline int sgemm(const GemmShape &P, const Epi &epi, int max_ctas, cudaStream_t 
     int64_t grid = max_ctas > 0 ? max_ctas : 1;
     if (tiles < grid) grid = tiles;
     dim3 g((unsigned)grid, 1, P.nclass);
-    k_sgemm<TA, TB, Epi><<<g, GTHREADS, 0, st>>>(P, epi);
+    launch(k_sgemm<TA, TB, Epi>, g, GTHREADS, 0, st, P, epi);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;

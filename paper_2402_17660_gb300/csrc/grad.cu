@@ -12,6 +12,7 @@ constexpr int WBM = 64, WBN = 64, WBK = 16, WTHREADS = 256;
 // partial[(z*splits + s)][m][n] = sum over rows r of split s of A[r][m] B[r][n]
 __global__ void __launch_bounds__(WTHREADS) k_wgrad(WgradShape P, int splits, int64_t chunk,
                                                     float *__restrict__ partial) {
+    pdl_entry();
     __shared__ __align__(16) float As[WBK][WBM];
     __shared__ __align__(16) float Bs[WBK][WBN];
     const int z = blockIdx.z, s = blockIdx.y;
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(WTHREADS) k_wgrad(WgradShape P, int splits, in
 // partial[(z*splits + s)][m] = sum over rows of split s of A[r][m] (* w[r])
 __global__ void k_colsum(WgradShape P, int splits, int64_t chunk, const float *__restrict__ roww,
                          float *__restrict__ partial) {
+    pdl_entry();
     const int z = blockIdx.z, s = blockIdx.y;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= P.M) return;
@@ -94,6 +96,7 @@ __global__ void k_colsum(WgradShape P, int splits, int64_t chunk, const float *_
 __global__ void k_ln_grad(const float *__restrict__ gy, const float *__restrict__ x,
                           const float2 *__restrict__ stats, int R, int C, int splits, int64_t chunk,
                           float *__restrict__ partial) {
+    pdl_entry();
     const int s = blockIdx.y;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
@@ -116,6 +119,7 @@ __global__ void k_ln_grad(const float *__restrict__ gy, const float *__restrict_
 // plane-major order (m = p perm_f + c) and are written to row c*3 + p.
 __global__ void k_split_reduce(const float *__restrict__ partial, int splits, int64_t per_class, int nclass,
                                float *__restrict__ out, int accumulate, int ncols, int perm_f) {
+    pdl_entry();
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= per_class * nclass) return;
     const int64_t z = t / per_class, i = t % per_class;
@@ -156,10 +160,10 @@ int wgrad_outer(const WgradShape &P, float *partial, int64_t partial_cap, float 
     const int splits = choose_splits(rows_cap, tiles, P.nclass, (int64_t)P.M * P.N, partial_cap, sms, &chunk);
     if ((int64_t)splits * P.nclass * P.M * P.N > partial_cap) return TNET_ERR_WORKSPACE;
     dim3 g((unsigned)tiles, splits, P.nclass);
-    k_wgrad<<<g, WTHREADS, 0, st>>>(P, splits, chunk, partial);
+    launch(k_wgrad, g, WTHREADS, 0, st, P, splits, chunk, partial);
     count_launch();
     const int64_t tot = (int64_t)P.nclass * P.M * P.N;
-    k_split_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(partial, splits, (int64_t)P.M * P.N, P.nclass,
+    launch(k_split_reduce, (unsigned)((tot + 255) / 256), 256, 0, st, partial, splits, (int64_t)P.M * P.N, P.nclass,
                                                                   out, accumulate, P.N, perm_f);
     count_launch();
     TNET_LAUNCH_CHECK();
@@ -175,10 +179,10 @@ int wgrad_colsum(const WgradShape &P, const float *roww, float *partial, int64_t
     int64_t chunk;
     const int splits = choose_splits(rows_cap, tiles * 4, P.nclass, P.M, partial_cap, sms, &chunk);
     dim3 g((unsigned)tiles, splits, P.nclass);
-    k_colsum<<<g, 256, 0, st>>>(P, splits, chunk, roww, partial);
+    launch(k_colsum, g, 256, 0, st, P, splits, chunk, roww, partial);
     count_launch();
     const int64_t tot = (int64_t)P.nclass * P.M;
-    k_split_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(partial, splits, P.M, P.nclass, out, accumulate,
+    launch(k_split_reduce, (unsigned)((tot + 255) / 256), 256, 0, st, partial, splits, P.M, P.nclass, out, accumulate,
                                                                   1, perm_f);
     count_launch();
     TNET_LAUNCH_CHECK();
@@ -194,9 +198,9 @@ int wgrad_layernorm(const float *gy, const float *x, const float2 *stats, int R,
     int64_t chunk;
     const int splits = choose_splits(R, tiles * 4, 1, 2LL * C, partial_cap, sms, &chunk);
     dim3 g((unsigned)tiles, splits, 1);
-    k_ln_grad<<<g, 256, 0, st>>>(gy, x, stats, R, C, splits, chunk, partial);
+    launch(k_ln_grad, g, 256, 0, st, gy, x, stats, R, C, splits, chunk, partial);
     count_launch();
-    k_split_reduce<<<(unsigned)((2 * C + 255) / 256), 256, 0, st>>>(partial, splits, 2LL * C, 1, out_g, 0, 1, 0);
+    launch(k_split_reduce, (unsigned)((2 * C + 255) / 256), 256, 0, st, partial, splits, 2LL * C, 1, out_g, 0, 1, 0);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;

@@ -1,5 +1,6 @@
 // Internal definitions shared by the libtnet CUDA sources.
 #pragma once
+#include <utility>
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -21,6 +22,41 @@
 #define TNET_LAUNCH_CHECK() TNET_CUDA_TRY(cudaGetLastError())
 
 namespace tnet {
+
+// Programmatic dependent launch.  Kernels of the library are launched (unless
+// the context's pdl knob is 0) with the programmatic-serialization attribute,
+// so the next kernel of a
+// stream (or graph) may be scheduled while the previous one drains; its first
+// statement, pdl_entry(), waits until the previous grid has completed and its
+// writes are visible (griddepcontrol.wait), then lets the following kernel be
+// scheduled once all of this grid's CTAs are running.  Without a programmatic
+// predecessor both instructions are no-ops.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// Whether launches of this host thread carry the attribute: set for the
+// duration of each API call from the context's tuning knob (PdlScope).
+extern thread_local int tl_pdl;
+struct PdlScope {
+    int prev;
+    explicit PdlScope(int on) : prev(tl_pdl) { tl_pdl = on; }
+    ~PdlScope() { tl_pdl = prev; }
+};
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = tl_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);  // errors surface in cudaGetLastError
+}
 
 constexpr int kMaxCellsPerAtom = 2;   // cell budget: 2 cells per atom + 8 per system + 64
 constexpr int kMaxRowSorted = 1024;   // longest CSR row sorted in shared memory
@@ -350,8 +386,8 @@ void count_launch();
 // Stages timed by the optional CUDA-event profiler (tnet_profile).
 // Tuning knobs: 0 SIMT-GEMM CTAs per SM, 1 tcgen05 column tile for N = 3F,
 // 2 tcgen05 column tile for N = 2F, 3 row-kernel blocks per SM, 4 pair-kernel
-// blocks (256 threads) per SM.
-enum TuneKnob { T_GEMM_CTAS = 0, T_TC_BN_3F, T_TC_BN_2F, T_ROW_BLOCKS, T_PAIR_BLOCKS, T_NKNOBS };
+// blocks (256 threads) per SM, 5 programmatic dependent launch on (1) or off.
+enum TuneKnob { T_GEMM_CTAS = 0, T_TC_BN_3F, T_TC_BN_2F, T_ROW_BLOCKS, T_PAIR_BLOCKS, T_PDL, T_NKNOBS };
 
 enum ProfTag {
     P_NBR = 0, P_PREP, P_EMB_EDGE, P_EMB_NODE, P_MLP1, P_MLP2, P_MLP3, P_MESSAGE, P_NODE_MIX,

@@ -14,6 +14,7 @@ constexpr float kAccel = 9.64853321e-3f;  // 1 eV / (A amu) in A / fs^2
 
 __global__ void k_half_kick(float *__restrict__ vel, const float *__restrict__ F,
                             const float *__restrict__ inv_m, int N, float hdt) {
+    pdl_entry();
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= 3LL * N) return;
     vel[t] += hdt * kAccel * F[t] * inv_m[t / 3];
@@ -25,6 +26,7 @@ __global__ void k_half_kick(float *__restrict__ vel, const float *__restrict__ F
 __global__ void k_drift(float *__restrict__ pos, const float *__restrict__ vel, int N, float dt,
                         const float *__restrict__ ref, const float *__restrict__ box, float lim2,
                         int32_t *__restrict__ need) {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float d[3];
@@ -40,6 +42,7 @@ __global__ void k_drift(float *__restrict__ pos, const float *__restrict__ vel, 
 
 __global__ void k_copy(float *__restrict__ dst, const float *__restrict__ src, int64_t n,
                        const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t < n) dst[t] = src[t];
@@ -48,6 +51,7 @@ __global__ void k_copy(float *__restrict__ dst, const float *__restrict__ src, i
 // after a rebuild slot: count it (periodic, or triggered by the flag) and
 // clear the flag
 __global__ void k_rebuild_done(int32_t *__restrict__ need, int64_t *__restrict__ count, int periodic) {
+    pdl_entry();
     if (periodic || *need) ++*count;
     *need = 0;
 }
@@ -56,6 +60,7 @@ __global__ void k_rebuild_done(int32_t *__restrict__ need, int64_t *__restrict__
 __global__ void k_record(const float *__restrict__ vel, const float *__restrict__ inv_m, int N,
                          const double *__restrict__ epot_src, double *__restrict__ e_kin,
                          double *__restrict__ e_pot, int32_t *__restrict__ step) {
+    pdl_entry();
     __shared__ double sm[32];
     double acc = 0.0;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -102,9 +107,9 @@ int enqueue_rebuild(tnet_ctx *c, const MdArgs &a, bool periodic, cudaStream_t st
                             wsp<int32_t>(c, L.md_col), c->max_pairs, wsp<int64_t>(c, L.md_npairs), a.status,
                             st, gate);
     if (rc) return rc;
-    k_copy<<<(3 * a.N + 255) / 256, 256, 0, st>>>(wsp<float>(c, L.md_pos_ref), a.pos, 3LL * a.N, gate);
+    launch(k_copy, (3 * a.N + 255) / 256, 256, 0, st, wsp<float>(c, L.md_pos_ref), a.pos, 3LL * a.N, gate);
     count_launch();
-    k_rebuild_done<<<1, 1, 0, st>>>(need, wsp<int64_t>(c, L.md_rebuilds), periodic ? 1 : 0);
+    launch(k_rebuild_done, 1, 1, 0, st, need, wsp<int64_t>(c, L.md_rebuilds), periodic ? 1 : 0);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
@@ -121,10 +126,10 @@ int enqueue_step(tnet_ctx *c, const MdArgs &a, bool rebuild, cudaStream_t st) {
     const Layout &L = c->lay;
     float *F = wsp<float>(c, L.md_forces);
     const int nb3 = (3 * a.N + 255) / 256, nb = (a.N + 255) / 256;
-    k_half_kick<<<nb3, 256, 0, st>>>(a.vel, F, a.inv_m, a.N, 0.5f * a.dt);
+    launch(k_half_kick, nb3, 256, 0, st, a.vel, F, a.inv_m, a.N, 0.5f * a.dt);
     count_launch();
     const float lim = 0.5f * a.skin;
-    k_drift<<<nb, 256, 0, st>>>(a.pos, a.vel, a.N, a.dt, wsp<float>(c, L.md_pos_ref), a.box, lim * lim,
+    launch(k_drift, nb, 256, 0, st, a.pos, a.vel, a.N, a.dt, wsp<float>(c, L.md_pos_ref), a.box, lim * lim,
                                 wsp<int32_t>(c, L.md_need));
     count_launch();
     TNET_LAUNCH_CHECK();
@@ -134,9 +139,9 @@ int enqueue_step(tnet_ctx *c, const MdArgs &a, bool rebuild, cudaStream_t st) {
     }
     int rc = enqueue_forces(c, a, st);
     if (rc) return rc;
-    k_half_kick<<<nb3, 256, 0, st>>>(a.vel, F, a.inv_m, a.N, 0.5f * a.dt);
+    launch(k_half_kick, nb3, 256, 0, st, a.vel, F, a.inv_m, a.N, 0.5f * a.dt);
     count_launch();
-    k_record<<<1, 1024, 0, st>>>(a.vel, a.inv_m, a.N, wsp<double>(c, L.md_energy), a.e_kin, a.e_pot,
+    launch(k_record, 1, 1024, 0, st, a.vel, a.inv_m, a.N, wsp<double>(c, L.md_energy), a.e_kin, a.e_pot,
                                  wsp<int32_t>(c, L.md_step));
     count_launch();
     TNET_LAUNCH_CHECK();

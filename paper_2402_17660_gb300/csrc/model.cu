@@ -98,6 +98,7 @@ __device__ __forceinline__ void pair_vec(const float *__restrict__ pos, const fl
 // rev[e] = position of (j, i) in row j; one warp per row.
 __global__ void k_rev(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int N,
                       int32_t *__restrict__ rev, int32_t *status) {
+    pdl_entry();
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (i >= N) return;
     const int lane = threadIdx.x & 31;
@@ -128,6 +129,7 @@ __global__ void k_upper_count(const float *__restrict__ pos, const float *__rest
                               const int32_t *__restrict__ batch, const int32_t *__restrict__ row_ptr,
                               const int32_t *__restrict__ col, int N, float rc,
                               int32_t *__restrict__ ucnt) {
+    pdl_entry();
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (i >= N) return;
     const int lane = threadIdx.x & 31;
@@ -153,6 +155,7 @@ __global__ void k_upper_assign(const float *__restrict__ pos, const float *__res
                                const int32_t *__restrict__ col, int N, float rc,
                                const int32_t *__restrict__ uoff, int32_t *__restrict__ pair_of,
                                int2 *__restrict__ uij, int32_t *__restrict__ ue) {
+    pdl_entry();
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (i >= N) return;
     const int lane = threadIdx.x & 31;
@@ -186,6 +189,7 @@ __global__ void k_upper_assign(const float *__restrict__ pos, const float *__res
 
 __global__ void k_lower_assign(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                const int32_t *__restrict__ rev, int N, int32_t *__restrict__ pair_of) {
+    pdl_entry();
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (i >= N) return;
     const int lane = threadIdx.x & 31;
@@ -204,6 +208,7 @@ __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restric
                            const int32_t *__restrict__ nu, int maxU, RadialParams rp,
                            float *__restrict__ eu, float *__restrict__ phiu, float4 *__restrict__ geo,
                            OpCopy eu_cp) {
+    pdl_entry();
     // a block takes groups of P pairs: P threads compute the pairs' geometry
     // once, then all threads evaluate the P x K basis values from it
     __shared__ float s_d[256], s_phi[256];
@@ -242,6 +247,7 @@ __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restric
 __global__ void k_elem_tables(const float *__restrict__ emb, const float *__restrict__ W,
                               const float *__restrict__ b, int F, float *__restrict__ Ta,
                               float *__restrict__ Tb) {
+    pdl_entry();
     // block per element z; warp per output row of W (lanes along the row, so
     // the reads of W are coalesced), a fixed-order warp reduction
     extern __shared__ float e[];
@@ -297,6 +303,7 @@ __global__ void __launch_bounds__(F) k_emb_edges(const float4 *__restrict__ geo,
                                                  const float *__restrict__ fu, const float *__restrict__ Ta,
                                                  const float *__restrict__ Tb, float *__restrict__ Xraw,
                                                  int32_t *status, OpCopy Xraw_cp) {
+    pdl_entry();
     __shared__ int32_t s_u[kChunk], s_zs[kChunk];  // pair index; element of the column atom, signed by direction
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
@@ -364,6 +371,7 @@ __global__ void __launch_bounds__(F) k_emb_edges(const float4 *__restrict__ geo,
 __global__ void k_norm_ln(const float *__restrict__ X, int N, int F, const float *__restrict__ g,
                           const float *__restrict__ b, float *__restrict__ n0, float2 *__restrict__ ln,
                           float *__restrict__ q0) {
+    pdl_entry();
     __shared__ float sm[32];
     const int i = blockIdx.x, c = threadIdx.x;
     float v[9];
@@ -381,6 +389,7 @@ __global__ void k_norm_ln(const float *__restrict__ X, int N, int F, const float
 // X0 = s_p * U (p = class of the coordinate), s channel-major [N][F][3]
 __global__ void k_emb_scale(const float *__restrict__ U, const float *__restrict__ s, int N, int F,
                             float *__restrict__ X0) {
+    pdl_entry();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -400,6 +409,7 @@ __global__ void k_emb_scale(const float *__restrict__ U, const float *__restrict
 // Xn = X / (||X|| + 1)
 __global__ void k_node_norm(const float *__restrict__ X, int N, int F, float *__restrict__ qn,
                             float *__restrict__ Xn, OpCopy Xn_cp) {
+    pdl_entry();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -426,6 +436,7 @@ template <int F>
 __global__ void __launch_bounds__(F) k_message(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                                const int32_t *__restrict__ pair_of, const float *__restrict__ gU,
                                                const float *__restrict__ Y, int N, float *__restrict__ M) {
+    pdl_entry();
     __shared__ int32_t s_u[kChunk], s_j[kChunk];
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
@@ -469,6 +480,7 @@ __global__ void __launch_bounds__(F) k_message(const int32_t *__restrict__ row_p
 // T = Y M + M Y; Tn = decomp(T) / (||T|| + 1)
 __global__ void k_node_update(const float *__restrict__ Y, const float *__restrict__ M, int N, int F,
                               float *__restrict__ Tn, OpCopy Tn_cp) {
+    pdl_entry();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -493,6 +505,7 @@ __global__ void k_node_update(const float *__restrict__ Y, const float *__restri
 // X_out = Xn + dX + dX dX
 __global__ void k_residual(const float *__restrict__ Xn, const float *__restrict__ dX, int N, int F,
                            float *__restrict__ Xout) {
+    pdl_entry();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -513,6 +526,7 @@ __global__ void k_residual(const float *__restrict__ Xn, const float *__restrict
 __global__ void k_out_norms(const float *__restrict__ X, int N, int F, const float *__restrict__ g,
                             const float *__restrict__ b, float *__restrict__ h, float *__restrict__ hn,
                             float2 *__restrict__ ln) {
+    pdl_entry();
     __shared__ float sm[32];
     const int i = blockIdx.x, c = threadIdx.x;
     float v[9];
@@ -536,6 +550,7 @@ __global__ void k_out_norms(const float *__restrict__ X, int N, int F, const flo
 // E_i = w2 . t_i + b2 (one warp per atom)
 __global__ void k_head(const float *__restrict__ t, int N, int H, const float *__restrict__ w2,
                        const float *__restrict__ b2, float *__restrict__ Ei) {
+    pdl_entry();
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (i >= N) return;
     const int lane = threadIdx.x & 31;
@@ -548,6 +563,7 @@ __global__ void k_head(const float *__restrict__ t, int N, int H, const float *_
 // E_s = sum of E_i over the system, in FP64 (one block per system)
 __global__ void k_energy(const float *__restrict__ Ei, const int32_t *__restrict__ sys_start,
                          const int32_t *__restrict__ sys_end, double *__restrict__ energy) {
+    pdl_entry();
     __shared__ double sm[32];
     const int s = blockIdx.x;
     double acc = 0.0;
@@ -567,6 +583,7 @@ __global__ void k_energy(const float *__restrict__ Ei, const int32_t *__restrict
 __global__ void k_head_bwd(const float *__restrict__ at, int N, int H, const float *__restrict__ w2,
                            const float *__restrict__ seed, const int32_t *__restrict__ batch,
                            float *__restrict__ gat) {
+    pdl_entry();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * H;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / H), k = (int)(t % H);
@@ -579,6 +596,7 @@ __global__ void k_head_bwd(const float *__restrict__ at, int N, int H, const flo
 __global__ void k_out_norms_bwd(const float *__restrict__ X, const float *__restrict__ h,
                                 const float *__restrict__ ghn, const float2 *__restrict__ ln,
                                 const float *__restrict__ g, int N, int F, float *__restrict__ gX) {
+    pdl_entry();
     __shared__ float sm[32];
     const int i = blockIdx.x, c = threadIdx.x;
     const float2 mr = ln[i];
@@ -612,6 +630,7 @@ __global__ void k_out_norms_bwd(const float *__restrict__ X, const float *__rest
 // X_out = Xn + dX + dX dX:  g_dX = g + expand^T(G Q^T + Q^T G), G = decomp^T(g)
 __global__ void k_residual_bwd(const float *__restrict__ gX, const float *__restrict__ dX, int N, int F,
                                float *__restrict__ gdX, OpCopy gdX_cp) {
+    pdl_entry();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -636,6 +655,7 @@ __global__ void k_residual_bwd(const float *__restrict__ gX, const float *__rest
 __global__ void k_T_bwd(const float *__restrict__ Y, const float *__restrict__ M,
                         const float *__restrict__ gTn, int N, int F, float *__restrict__ gY,
                         float *__restrict__ gM) {
+    pdl_entry();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -697,6 +717,7 @@ __global__ void __launch_bounds__(F, 512 / F)
                   const float *__restrict__ gM, const float *__restrict__ a3, const float *__restrict__ phiu,
                   int N, float *__restrict__ gY, OpCopy gY_cp, float *__restrict__ ga3, OpCopy ga3_cp,
                   float *__restrict__ gphi) {
+    pdl_entry();
     constexpr int NW = F / 32;
     __shared__ int32_t s_u[kChunk], s_j[kChunk];
     __shared__ float s_red[kChunk][NW];
@@ -818,6 +839,7 @@ __global__ void __launch_bounds__(F, 512 / F)
 // Xn = X / (q + 1):  gX = gXn / (q + 1) - <gXn, X> / (q + 1)^2 * dq/dX (in place)
 __global__ void k_node_norm_bwd(const float *__restrict__ X, const float *__restrict__ qn, int N, int F,
                                 float *__restrict__ gX) {
+    pdl_entry();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -840,6 +862,7 @@ __global__ void k_node_norm_bwd(const float *__restrict__ X, const float *__rest
 __global__ void k_emb_scale_bwd(const float *__restrict__ gX0, const float *__restrict__ U,
                                 const float *__restrict__ s, const float *__restrict__ as2, int N, int F,
                                 float *__restrict__ gU, float *__restrict__ gas2, OpCopy gU_cp) {
+    pdl_entry();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)N * F;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / F), c = (int)(t % F);
@@ -869,6 +892,7 @@ __global__ void k_emb_scale_bwd(const float *__restrict__ gX0, const float *__re
 __global__ void k_ln0_bwd(const float *__restrict__ Xraw, const float *__restrict__ gn0,
                           const float2 *__restrict__ ln, const float *__restrict__ g, int N, int F,
                           float *__restrict__ gXraw) {
+    pdl_entry();
     __shared__ float sm[32];
     const int i = blockIdx.x, c = threadIdx.x;
     float v[9], gv[9], ng[9];
@@ -902,6 +926,7 @@ __global__ void k_emb_bwd(const float *__restrict__ pos, const float *__restrict
                           const float *__restrict__ Tb, const float *__restrict__ gXraw, int want_z,
                           float *__restrict__ gfu, float4 *__restrict__ edge_g, float *__restrict__ gA_atom,
                           float *__restrict__ gB_atom, OpCopy gfu_cp) {
+    pdl_entry();
     constexpr int F = CPL * 32;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -1010,6 +1035,7 @@ __global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *_
                                 const float *__restrict__ Tb, const float *__restrict__ gXraw,
                                 float *__restrict__ gfu, float4 *__restrict__ edge_g,
                                 OpCopy gfu_cp) {
+    pdl_entry();
     constexpr int F = CPL * 32;
     const int lane = threadIdx.x & 31;
     const int U = *nu;
@@ -1092,6 +1118,7 @@ __global__ void k_pair_vec(const float *__restrict__ pos, const float *__restric
                            const int32_t *__restrict__ nu, RadialParams rp, const float *__restrict__ ge,
                            const float *__restrict__ gphi_mlp, const float4 *__restrict__ edge_g,
                            float *__restrict__ Gp) {
+    pdl_entry();
     const int U = *nu;
     const int lane = threadIdx.x & 31;
     for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < U;
@@ -1129,6 +1156,7 @@ __global__ void k_pair_vec(const float *__restrict__ pos, const float *__restric
 __global__ void k_forces(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                          const int32_t *__restrict__ pair_of, const float *__restrict__ Gp, int N,
                          float *__restrict__ forces) {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -1150,6 +1178,7 @@ __global__ void k_forces(const int32_t *__restrict__ row_ptr, const int32_t *__r
 __global__ void k_group_z(const int32_t *__restrict__ z, const float *__restrict__ gA,
                           const float *__restrict__ gB, int N, int F, int max_z, int splits,
                           float *__restrict__ zpart) {
+    pdl_entry();
     const int zz = blockIdx.x, s = blockIdx.y, c = threadIdx.x;
     const int chunk = (N + splits - 1) / splits;
     const int i0 = s * chunk, i1 = min(N, i0 + chunk);
@@ -1166,6 +1195,7 @@ __global__ void k_group_z(const int32_t *__restrict__ z, const float *__restrict
 
 // A[z] = sum over splits of the receiver sums, B[z] likewise for senders.
 __global__ void k_zreduce(const float *__restrict__ zpart, int splits, int F, int max_z, float *__restrict__ AB) {
+    pdl_entry();
     const int zz = blockIdx.x, c = threadIdx.x;
     for (int h = 0; h < 2; ++h) {
         float acc = 0.f;
@@ -1180,6 +1210,7 @@ __global__ void k_zreduce(const float *__restrict__ zpart, int splits, int F, in
 __global__ void k_emb_tables_grad2(const float *__restrict__ AB, int F, int max_z, const float *__restrict__ emb,
                                    const float *__restrict__ We, float *__restrict__ g_emb,
                                    float *__restrict__ g_We, float *__restrict__ g_be) {
+    pdl_entry();
     const int r = blockIdx.x, c = threadIdx.x;
     const float *A = AB, *B = AB + (int64_t)max_z * F;
     if (r < F) {
@@ -1210,6 +1241,7 @@ __global__ void k_emb_tables_grad2(const float *__restrict__ AB, int F, int max_
 // dE/dE_i (seed of the system) and its products for the head gradients
 __global__ void k_seed_atoms(const float *__restrict__ seed, const int32_t *__restrict__ batch, int N,
                              float *__restrict__ gEi) {
+    pdl_entry();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) gEi[i] = seed ? seed[batch ? batch[i] : 0] : 1.0f;
 }
@@ -1222,6 +1254,7 @@ struct FilterRows {
     const float *w[8], *b[8];
 };
 __global__ void k_filter_rows(const __grid_constant__ FilterRows R, int F, float *__restrict__ out) {
+    pdl_entry();
     const int l = blockIdx.y;
     const int64_t nw = 6LL * F * F, per = nw + 3 * F;
     const int cols = 2 * F;
@@ -1254,6 +1287,7 @@ struct WOp {  // a weight operand: bf16 matrix, or fp32 high part + residual
     const void *blo;
 };
 __global__ void k_cvt_weights(const __grid_constant__ CvtJobs J) {
+    pdl_entry();
     const int j = blockIdx.y;
     if (j >= J.n) return;
     const int R = J.rows[j], C = J.cols[j];
@@ -1314,6 +1348,7 @@ static inline int grid_for(int64_t n, int threads, int num_sms) {
 // reported as ARG (or CAPACITY when they pass the capacity).
 __global__ void k_rows_in_range(const int32_t *__restrict__ row_ptr, int N, int64_t cap,
                                 int32_t *__restrict__ safe, int32_t *status) {
+    pdl_entry();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= N; t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = row_ptr[t];
         int32_t w = v < 0 ? 0 : v;
@@ -1353,8 +1388,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     int32_t *rev = i32(Lw.rev), *pair_of = i32(Lw.pair_of), *ucnt = i32(Lw.ucnt);
     // every kernel below reads the clamped copy of the row offsets
     int32_t *row_ptr = i32(Lw.rp_safe);
-    k_rows_in_range<<<(N + 256) / 256 < 1024 ? (N + 256) / 256 : 1024, 256, 0, st>>>(row_ptr_in, N, ctx->max_pairs,
-                                                                                     row_ptr, status);
+    launch(k_rows_in_range, (N + 256) / 256 < 1024 ? (N + 256) / 256 : 1024, 256, 0, st, row_ptr_in, N,
+           ctx->max_pairs, row_ptr, status);
     count_launch();
     TNET_LAUNCH_CHECK();
     int32_t *nu = i32(Lw.nu), *ue = i32(Lw.ue);
@@ -1427,7 +1462,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     if (NL > 0) {
         FilterRows FR{};
         for (int l = 0; l < NL; ++l) { FR.w[l] = W.layer[l].mlp3_w; FR.b[l] = W.layer[l].mlp3_b; }
-        k_filter_rows<<<dim3(48, NL), 256, 0, st>>>(FR, F, f32(Lw.w3p));
+        launch(k_filter_rows, dim3(48, NL), 256, 0, st, FR, F, f32(Lw.w3p));
         count_launch();
         TNET_LAUNCH_CHECK();
     }
@@ -1500,7 +1535,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             wx.head1T = job3(W.head1_w, H, F, 1);
         }
         if (woff > Lw.wbf_bytes || J.n > kMaxCvtJobs) return TNET_ERR_WORKSPACE;
-        k_cvt_weights<<<dim3(64, J.n), 256, 0, st>>>(J);
+        launch(k_cvt_weights, dim3(64, J.n), 256, 0, st, J);
         count_launch();
         TNET_LAUNCH_CHECK();
     }
@@ -1525,22 +1560,22 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     TNET_CUDA_TRY(cudaMemsetAsync(sys_start, 0, sizeof(int32_t) * S, st));
     TNET_CUDA_TRY(cudaMemsetAsync(sys_end, 0, sizeof(int32_t) * S, st));
     TRY(sys_bounds(batch, N, S, sys_start, sys_end, status, st));
-    k_rev<<<warps_grid, 256, 0, st>>>(row_ptr, col, N, rev, status);
+    launch(k_rev, warps_grid, 256, 0, st, row_ptr, col, N, rev, status);
     count_launch();
-    k_upper_count<<<warps_grid, 256, 0, st>>>(pos, box, batch, row_ptr, col, N, rp.rc, ucnt);
+    launch(k_upper_count, warps_grid, 256, 0, st, pos, box, batch, row_ptr, col, N, rp.rc, ucnt);
     count_launch();
     TNET_LAUNCH_CHECK();
     TRY(scan_exclusive_i32(ucnt, ucnt, N, i32(Lw.scan_tmp), nu, nullptr, st));
-    k_upper_assign<<<warps_grid, 256, 0, st>>>(pos, box, batch, row_ptr, col, N, rp.rc, ucnt, pair_of, uij, ue);
+    launch(k_upper_assign, warps_grid, 256, 0, st, pos, box, batch, row_ptr, col, N, rp.rc, ucnt, pair_of, uij, ue);
     count_launch();
-    k_lower_assign<<<warps_grid, 256, 0, st>>>(row_ptr, col, rev, N, pair_of);
+    launch(k_lower_assign, warps_grid, 256, 0, st, row_ptr, col, rev, N, pair_of);
     count_launch();
     TNET_LAUNCH_CHECK();
     float *eu = f32(Lw.eu), *phiu = f32(Lw.phiu), *fu = f32(Lw.fu);
     float4 *geo = wsp<float4>(ctx, Lw.geo);
-    k_edge_rbf<<<pair_grid, 256, 0, st>>>(pos, box, batch, uij, nu, maxU, rp, eu, phiu, geo, eu_cp);
+    launch(k_edge_rbf, pair_grid, 256, 0, st, pos, box, batch, uij, nu, maxU, rp, eu, phiu, geo, eu_cp);
     count_launch();
-    k_elem_tables<<<d.max_z, 256, sizeof(float) * F, st>>>(W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
+    launch(k_elem_tables, d.max_z, 256, sizeof(float) * F, st, W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
     count_launch();
     TNET_LAUNCH_CHECK();
     {   // radial projections f^p = W^p e(d) + b^p, once per undirected pair
@@ -1566,12 +1601,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     float2 *ln0 = wsp<float2>(ctx, Lw.ln0);
     const int atom_blocks = N < sms * ctx->tune[T_ROW_BLOCKS] ? N : sms * ctx->tune[T_ROW_BLOCKS];
 #define EMB_FWD(FF)                                                                                           \
-    k_emb_edges<FF><<<atom_blocks, FF, 0, st>>>(geo, z, row_ptr, col, pair_of, N, d.max_z, fu, Ta, Tb, Xraw, status, \
+    launch(k_emb_edges<FF>, atom_blocks, FF, 0, st, geo, z, row_ptr, col, pair_of, N, d.max_z, fu, Ta, Tb, Xraw, status, \
                                                 nbf)
     TNET_F_SWITCH(F, EMB_FWD);
 #undef EMB_FWD
     count_launch();
-    k_norm_ln<<<N, F, 0, st>>>(Xraw, N, F, W.emb_ln_g, W.emb_ln_b, n0, ln0, q0);
+    launch(k_norm_ln, N, F, 0, st, Xraw, N, F, W.emb_ln_g, W.emb_ln_b, n0, ln0, q0);
     count_launch();
     TNET_LAUNCH_CHECK();
     pf.mark(P_EMB_NODE);
@@ -1589,7 +1624,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     if (tcm) TRY(tcg(tc::tshape_classes(N, F), Xraw, nbf, 9LL * N, F, emix, 3 * F, F, EpiStore{Uemb, F, 0}));
     else TRY(sgemm<false, true>(gshape_classes(N, F, Xraw, W.emb_mix_w), EpiStore{Uemb, F, 0}, gctas, st));
     float *X = f32(Lw.Xin);  // layer 0 input
-    k_emb_scale<<<grid_for((int64_t)N * F, 256, sms), 256, 0, st>>>(Uemb, s, N, F, X);
+    launch(k_emb_scale, grid_for((int64_t)N * F, 256, sms), 256, 0, st, Uemb, s, N, F, X);
     count_launch();
     TNET_LAUNCH_CHECK();
 
@@ -1637,7 +1672,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
               *dX = f32(Lw.dX) + l * n9;
         float *Xnext = (l + 1 < NL) ? X + (l + 1) * n9 : f32(Lw.Xfin);
         pf.mark(P_NODE_ELEM);
-        k_node_norm<<<ew, 256, 0, st>>>(Xl, N, F, qn, Xn, nbf);
+        launch(k_node_norm, ew, 256, 0, st, Xl, N, F, qn, Xn, nbf);
         count_launch();
         TNET_LAUNCH_CHECK();
         pf.mark(P_NODE_MIX);
@@ -1646,19 +1681,19 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         TRY(edge_mlp(l));
         pf.mark(P_MESSAGE);
         const float *gbuf = act(Lw.g, 3 * F, l);
-#define MSG_FWD(FF) k_message<FF><<<atom_blocks, FF, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, N, M)
+#define MSG_FWD(FF) launch(k_message<FF>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, N, M)
         TNET_F_SWITCH(F, MSG_FWD);
 #undef MSG_FWD
         count_launch();
         pf.mark(P_NODE_ELEM);
-        k_node_update<<<ew, 256, 0, st>>>(Y, M, N, F, Tn, nbf);
+        launch(k_node_update, ew, 256, 0, st, Y, M, N, F, Tn, nbf);
         count_launch();
         TNET_LAUNCH_CHECK();
         pf.mark(P_NODE_MIX);
         if (tcm) TRY(tcg(tc::tshape_classes(N, F), Tn, nbf, 9LL * N, F, lb[l].mix2, 3 * F, F, EpiStore{dX, F, 0}));
         else TRY(sgemm<false, true>(gshape_classes(N, F, Tn, W.layer[l].mix2_w), EpiStore{dX, F, 0}, gctas, st));
         pf.mark(P_NODE_ELEM);
-        k_residual<<<ew, 256, 0, st>>>(Xn, dX, N, F, Xnext);
+        launch(k_residual, ew, 256, 0, st, Xn, dX, N, F, Xnext);
         count_launch();
         TNET_LAUNCH_CHECK();
     }
@@ -1669,7 +1704,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     float *h = f32(Lw.h), *hn = f32(Lw.hn), *ao = f32(Lw.ao), *o = f32(Lw.o), *at = f32(Lw.at),
           *t = f32(Lw.t), *Ei = f32(Lw.Ei);
     float2 *lno = wsp<float2>(ctx, Lw.lno);
-    k_out_norms<<<N, F, 0, st>>>(Xfin, N, F, W.out_ln_g, W.out_ln_b, h, hn, lno);
+    launch(k_out_norms, N, F, 0, st, Xfin, N, F, W.out_ln_g, W.out_ln_b, h, hn, lno);
     count_launch();
     TNET_LAUNCH_CHECK();
     {
@@ -1683,9 +1718,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
             TRY(sgemm<false, true>(gshape(N, H, F, o, F, W.head1_w, F), eh, gctas, st));
         }
     }
-    k_head<<<warps_grid, 256, 0, st>>>(t, N, H, W.head2_w, W.head2_b, Ei);
+    launch(k_head, warps_grid, 256, 0, st, t, N, H, W.head2_w, W.head2_b, Ei);
     count_launch();
-    k_energy<<<S, 256, 0, st>>>(Ei, sys_start, sys_end, energy);
+    launch(k_energy, S, 256, 0, st, Ei, sys_start, sys_end, energy);
     count_launch();
     TNET_LAUNCH_CHECK();
     if (!forces && !grad_w) return TNET_OK;
@@ -1695,7 +1730,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     float *gat = f32(Lw.gat), *gao = f32(Lw.gao), *ghn = f32(Lw.ghn), *gEi = f32(Lw.gEi);
     float *gX = f32(Lw.gXa), *gdX = f32(Lw.gdX), *gTn = f32(Lw.gTn), *gM = f32(Lw.gM), *gY = f32(Lw.gY);
     float *gg = f32(Lw.gg), *ga2 = f32(Lw.ga2), *ga1 = f32(Lw.ga1), *ge = f32(Lw.ge), *gphiu = f32(Lw.gphiu);
-    k_head_bwd<<<grid_for((int64_t)N * H, 256, sms), 256, 0, st>>>(at, N, H, W.head2_w, seed, batch, gat);
+    launch(k_head_bwd, grid_for((int64_t)N * H, 256, sms), 256, 0, st, at, N, H, W.head2_w, seed, batch, gat);
     count_launch();
     TNET_LAUNCH_CHECK();
     if (atom_x3) {
@@ -1705,11 +1740,11 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         TRY(sgemm<false, false>(gshape(N, F, H, gat, H, W.head1_w, F), EpiGradAct{ao, F, gao, F, 0}, gctas, st));
         TRY(sgemm<false, false>(gshape(N, 3 * F, F, gao, F, W.out_w, 3 * F), EpiStore{ghn, 3 * F, 0}, gctas, st));
     }
-    k_out_norms_bwd<<<N, F, 0, st>>>(Xfin, h, ghn, lno, W.out_ln_g, N, F, gX);
+    launch(k_out_norms_bwd, N, F, 0, st, Xfin, h, ghn, lno, W.out_ln_g, N, F, gX);
     count_launch();
     TNET_LAUNCH_CHECK();
     if (wg) {
-        k_seed_atoms<<<(N + 255) / 256, 256, 0, st>>>(seed, batch, N, gEi);
+        launch(k_seed_atoms, (N + 255) / 256, 256, 0, st, seed, batch, N, gEi);
         count_launch();
         TNET_LAUNCH_CHECK();
         TRY(wgrad_colsum(rows1(H, 1, N, t, H, nullptr, 0, nullptr), gEi, wpart, wcap, gw(G.head2_w), 0, sms, st));
@@ -1731,13 +1766,13 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         float *Y = f32(Lw.Y) + l * n9, *M = f32(Lw.M) + l * n9, *dX = f32(Lw.dX) + l * n9,
               *Tn = f32(Lw.Tn) + l * n9;
         pf.mark(P_NODE_BWD);
-        k_residual_bwd<<<ew, 256, 0, st>>>(gX, dX, N, F, gdX, nbf);
+        launch(k_residual_bwd, ew, 256, 0, st, gX, dX, N, F, gdX, nbf);
         count_launch();
         TNET_LAUNCH_CHECK();
         if (tcm) TRY(tcg(tc::tshape_classes(N, F), gdX, nbf, 9LL * N, F, lb[l].mix2T, 3 * F, F, EpiStore{gTn, F, 0}));
         else TRY(sgemm<false, false>(gshape_classes(N, F, gdX, Lr.mix2_w), EpiStore{gTn, F, 0}, gctas, st));
         if (wg) TRY(wgrad_outer(rows3(gdX, Tn), wpart, wcap, gw(Gr.mix2_w), 0, sms, st));
-        k_T_bwd<<<ew, 256, 0, st>>>(Y, M, gTn, N, F, gY, gM);
+        launch(k_T_bwd, ew, 256, 0, st, Y, M, gTn, N, F, gY, gM);
         count_launch();
         TNET_LAUNCH_CHECK();
         // this layer's radial-MLP activations: kept from the forward pass, or
@@ -1750,7 +1785,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         // and 3xTF32 GEMMs and the weight gradients)
         float *ga3_out = (prec != 1 || wg) ? gg : nullptr;
 #define MSG_BWD(FF)                                                                                          \
-    k_message_bwd<FF><<<atom_blocks, FF, 0, st>>>(row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu, N, gY, nbf, \
+    launch(k_message_bwd<FF>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu, N, gY, nbf, \
                                                   ga3_out, ga3_cp, gphiu)
         TNET_F_SWITCH(F, MSG_BWD);
 #undef MSG_BWD
@@ -1801,7 +1836,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         pf.mark(P_NODE_BWD);
         if (tcm) TRY(tcg(tc::tshape_classes(N, F), gY, nbf, 9LL * N, F, lb[l].mix1T, 3 * F, F, EpiStore{gX, F, 1}));
         else TRY(sgemm<false, false>(gshape_classes(N, F, gY, Lr.mix1_w), EpiStore{gX, F, 1}, gctas, st));
-        k_node_norm_bwd<<<ew, 256, 0, st>>>(Xl, qn, N, F, gX);
+        launch(k_node_norm_bwd, ew, 256, 0, st, Xl, qn, N, F, gX);
         count_launch();
         TNET_LAUNCH_CHECK();
     }
@@ -1809,7 +1844,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     pf.mark(P_EMB_NODE_BWD);
     float *gU = f32(Lw.gU), *gas2 = f32(Lw.gas2), *gas1 = f32(Lw.gas1), *gn0 = f32(Lw.gn0);
     float *gXraw = gdX;
-    k_emb_scale_bwd<<<ew, 256, 0, st>>>(gX, Uemb, s, as2, N, F, gU, gas2, nbf);
+    launch(k_emb_scale_bwd, ew, 256, 0, st, gX, Uemb, s, as2, N, F, gU, gas2, nbf);
     count_launch();
     TNET_LAUNCH_CHECK();
     if (atom_x3) {
@@ -1823,7 +1858,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     }
     if (tcm) TRY(tcg(tc::tshape_classes(N, F), gU, nbf, 9LL * N, F, emixT, 3 * F, F, EpiStore{gXraw, F, 0}));
     else TRY(sgemm<false, false>(gshape_classes(N, F, gU, W.emb_mix_w), EpiStore{gXraw, F, 0}, gctas, st));
-    k_ln0_bwd<<<N, F, 0, st>>>(Xraw, gn0, ln0, W.emb_ln_g, N, F, gXraw);
+    launch(k_ln0_bwd, N, F, 0, st, Xraw, gn0, ln0, W.emb_ln_g, N, F, gXraw);
     count_launch();
     TNET_LAUNCH_CHECK();
     if (wg) {
@@ -1845,10 +1880,10 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     // (atom-parallel kernel); forces alone use the pair-parallel kernel
 #define EMB_BWD(CPL)                                                                                         \
     if (wg)                                                                                                  \
-        k_emb_bwd<CPL><<<bwd_blocks, 256, 0, st>>>(pos, box, batch, z, row_ptr, col, pair_of, N, d.max_z, rp, \
+        launch(k_emb_bwd<CPL>, bwd_blocks, 256, 0, st, pos, box, batch, z, row_ptr, col, pair_of, N, d.max_z, rp, \
                                                    fu, Ta, Tb, gXraw, 1, gfu, edge_g, gA, gB, gfu_cp);        \
     else                                                                                                     \
-        k_emb_bwd_pairs<CPL><<<pair_grid, 256, 0, st>>>(geo, z, uij, ue, rev, nu, N, d.max_z, fu, Ta, Tb, gXraw, \
+        launch(k_emb_bwd_pairs<CPL>, pair_grid, 256, 0, st, geo, z, uij, ue, rev, nu, N, d.max_z, fu, Ta, Tb, gXraw, \
                                                       gfu, edge_g, gfu_cp)
     switch (F / 32) {
         case 2: EMB_BWD(2); break;
@@ -1881,21 +1916,21 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
                          sms, st));
         const int zs = (int)Lw.zsplits;
         float *zpart = f32(Lw.zpart);
-        k_group_z<<<dim3(d.max_z, zs), F, 0, st>>>(z, gA, gB, N, F, d.max_z, zs, zpart);
+        launch(k_group_z, dim3(d.max_z, zs), F, 0, st, z, gA, gB, N, F, d.max_z, zs, zpart);
         count_launch();
-        k_zreduce<<<d.max_z, F, 0, st>>>(zpart, zs, F, d.max_z, zpart);
+        launch(k_zreduce, d.max_z, F, 0, st, zpart, zs, F, d.max_z, zpart);
         count_launch();
-        k_emb_tables_grad2<<<F + d.max_z, F, 0, st>>>(zpart, F, d.max_z, W.emb, W.emb2_w, gw(G.emb), gw(G.emb2_w),
+        launch(k_emb_tables_grad2, F + d.max_z, F, 0, st, zpart, F, d.max_z, W.emb, W.emb2_w, gw(G.emb), gw(G.emb2_w),
                                                       gw(G.emb2_b));
         count_launch();
         TNET_LAUNCH_CHECK();
     }
     if (!forces) return TNET_OK;
     pf.mark(P_FORCES);
-    k_pair_vec<<<pair_grid, 256, 0, st>>>(pos, box, batch, uij, ue, rev, nu, rp, ge, NL > 0 ? gphiu : nullptr, edge_g,
+    launch(k_pair_vec, pair_grid, 256, 0, st, pos, box, batch, uij, ue, rev, nu, rp, ge, NL > 0 ? gphiu : nullptr, edge_g,
                                         Gp);
     count_launch();
-    k_forces<<<(N + 127) / 128, 128, 0, st>>>(row_ptr, col, pair_of, Gp, N, forces);
+    launch(k_forces, (N + 127) / 128, 128, 0, st, row_ptr, col, pair_of, Gp, N, forces);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;

@@ -43,6 +43,7 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *tota
 
 __global__ void k_scan_tiles(const int32_t *__restrict__ in, int32_t *__restrict__ out, int n,
                              int32_t *__restrict__ tile_sums, const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     __shared__ int32_t sm[32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
@@ -66,6 +67,7 @@ __global__ void k_scan_tiles(const int32_t *__restrict__ in, int32_t *__restrict
 // single block: exclusive scan of the tile sums (nt <= kScanTile)
 __global__ void k_scan_top(int32_t *__restrict__ tile_sums, int nt, int32_t *__restrict__ grand,
                            const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     __shared__ int32_t sm[32];
     const int base = threadIdx.x * kScanItems;
@@ -89,6 +91,7 @@ __global__ void k_scan_top(int32_t *__restrict__ tile_sums, int nt, int32_t *__r
 __global__ void k_scan_add(int32_t *__restrict__ out, int n, const int32_t *__restrict__ tile_sums,
                            const int32_t *__restrict__ grand, int32_t *__restrict__ total_dev,
                            int64_t *__restrict__ total64_dev, const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] += tile_sums[i / kScanTile];
@@ -103,6 +106,7 @@ __global__ void k_scan_add(int32_t *__restrict__ out, int n, const int32_t *__re
 // ceil(n / 4096) + 1 ints.  n <= 4096 * 4096.
 // dst[0..n) = 0 unless a gate is given and clear (the gated form of a memset)
 __global__ void k_zero_i32(int32_t *__restrict__ dst, int64_t n, const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         dst[t] = 0;
@@ -114,16 +118,16 @@ int scan_exclusive_i32(const int32_t *in, int32_t *out, int n, int32_t *tmp, int
     if (nt > kScanTile) return TNET_ERR_ARG;
     const int ntl = nt > 0 ? nt : 1;
     if (n > 0) {
-        k_scan_tiles<<<nt, kScanThreads, 0, st>>>(in, out, n, tmp, gate);
+        launch(k_scan_tiles, nt, kScanThreads, 0, st, in, out, n, tmp, gate);
         count_launch();
     }
     else if (gate) {
-        k_zero_i32<<<1, 32, 0, st>>>(tmp, 1, gate);
+        launch(k_zero_i32, 1, 32, 0, st, tmp, 1, gate);
         count_launch();
     } else TNET_CUDA_TRY(cudaMemsetAsync(tmp, 0, sizeof(int32_t), st));
-    k_scan_top<<<1, kScanThreads, 0, st>>>(tmp, ntl, tmp + ntl, gate);
+    launch(k_scan_top, 1, kScanThreads, 0, st, tmp, ntl, tmp + ntl, gate);
     count_launch();
-    k_scan_add<<<(n + 255) / 256 + 1, 256, 0, st>>>(out, n, tmp, tmp + ntl, total_dev, total64_dev, gate);
+    launch(k_scan_add, (n + 255) / 256 + 1, 256, 0, st, out, n, tmp, tmp + ntl, total_dev, total64_dev, gate);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
@@ -133,6 +137,7 @@ int scan_exclusive_i32(const int32_t *in, int32_t *out, int n, int32_t *tmp, int
 __global__ void k_sys_bounds(const int32_t *__restrict__ batch, int N, int S,
                              int32_t *__restrict__ sys_start, int32_t *__restrict__ sys_end,
                              int32_t *status, const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
@@ -150,7 +155,7 @@ __global__ void k_sys_bounds(const int32_t *__restrict__ batch, int N, int S,
 
 int sys_bounds(const int32_t *batch, int N, int S, int32_t *sys_start, int32_t *sys_end,
                int32_t *status, cudaStream_t st) {
-    k_sys_bounds<<<(N + 255) / 256, 256, 0, st>>>(batch, N, S, sys_start, sys_end, status, nullptr);
+    launch(k_sys_bounds, (N + 255) / 256, 256, 0, st, batch, N, S, sys_start, sys_end, status, nullptr);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
@@ -161,6 +166,7 @@ __global__ void k_sys_setup(const float *__restrict__ pos, const float *__restri
                             const int32_t *__restrict__ sys_start, const int32_t *__restrict__ sys_end,
                             SysInfo *__restrict__ info, int32_t *__restrict__ ncell, int32_t *status,
                             const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int s = blockIdx.x;
     const int a0 = sys_start[s], a1 = sys_end[s];
@@ -288,6 +294,7 @@ __global__ void k_bin(const float *__restrict__ pos, const int32_t *__restrict__
                       const SysInfo *__restrict__ info, const int32_t *__restrict__ cell_off,
                       int32_t *__restrict__ cell_of, int32_t *__restrict__ cell_count, int64_t cells,
                       const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
@@ -304,6 +311,7 @@ __global__ void k_bin(const float *__restrict__ pos, const int32_t *__restrict__
 __global__ void k_scatter(const float *__restrict__ pos, int N, const int32_t *__restrict__ cell_of,
                           const int32_t *__restrict__ cell_start, int32_t *__restrict__ cell_fill,
                           int32_t *__restrict__ sorted, float4 *__restrict__ spos, const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
@@ -374,6 +382,7 @@ __global__ void k_pair_count(const float *__restrict__ pos, const int32_t *__res
                              const SysInfo *__restrict__ info, const int32_t *__restrict__ cell_off,
                              const int32_t *__restrict__ cell_start, const float4 *__restrict__ spos,
                              float rc2, int32_t *__restrict__ rowcnt, const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (i >= N) return;
@@ -389,6 +398,7 @@ __global__ void k_pair_count(const float *__restrict__ pos, const int32_t *__res
 // never sends a reader past the end of col.
 __global__ void k_cap_check(const int64_t *__restrict__ n_pairs, int64_t cap, int32_t *__restrict__ row_ptr, int N,
                             int32_t *status, const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     if (*n_pairs <= cap) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, TNET_ERR_CAPACITY);
@@ -404,6 +414,7 @@ k_pair_fill(const float *__restrict__ pos, const int32_t *__restrict__ batch, in
             const int32_t *__restrict__ cell_start, const float4 *__restrict__ spos, float rc2,
             const int32_t *__restrict__ row_ptr, int32_t *__restrict__ col, int64_t cap,
             const int32_t *__restrict__ gate) {
+    pdl_entry();
     if (gate && *gate == 0) return;  // gated rebuild: nothing to do
     __shared__ int32_t buf[kFillWarps][kMaxRowSorted];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -484,7 +495,7 @@ int neighbors_impl(tnet_ctx *ctx, int N, int S, const float *pos, const int32_t 
             TNET_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof(int32_t) * n, st));
             return TNET_OK;
         }
-        k_zero_i32<<<(unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st>>>(p, n, gate);
+        launch(k_zero_i32, (unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), 256, 0, st, p, n, gate);
         count_launch();
         return TNET_OK;
     };
@@ -494,39 +505,39 @@ int neighbors_impl(tnet_ctx *ctx, int N, int S, const float *pos, const int32_t 
     if (!zrc) zrc = zero(cell_fill, cells);
     if (zrc) return zrc;
     if (N > 0) {
-        k_sys_bounds<<<(N + 255) / 256, 256, 0, st>>>(batch, N, S, sys_start, sys_end, status, gate);
+        launch(k_sys_bounds, (N + 255) / 256, 256, 0, st, batch, N, S, sys_start, sys_end, status, gate);
         count_launch();
         TNET_LAUNCH_CHECK();
     }
-    k_sys_setup<<<S, 256, 0, st>>>(pos, box, cutoff, sys_start, sys_end, info, ncell, status, gate);
+    launch(k_sys_setup, S, 256, 0, st, pos, box, cutoff, sys_start, sys_end, info, ncell, status, gate);
     count_launch();
     TNET_LAUNCH_CHECK();
     int rc = scan_exclusive_i32(ncell, ncell, S, tmp, nullptr, nullptr, st, gate);
     if (rc) return rc;
     if (N > 0) {
-        k_bin<<<(N + 255) / 256, 256, 0, st>>>(pos, batch, N, info, ncell, cell_of, cell_count, cells, gate);
+        launch(k_bin, (N + 255) / 256, 256, 0, st, pos, batch, N, info, ncell, cell_of, cell_count, cells, gate);
         count_launch();
         TNET_LAUNCH_CHECK();
     }
     rc = scan_exclusive_i32(cell_count, cell_start, cells, tmp, nullptr, nullptr, st, gate);
     if (rc) return rc;
     if (N > 0) {
-        k_scatter<<<(N + 255) / 256, 256, 0, st>>>(pos, N, cell_of, cell_start, cell_fill, sorted, spos, gate);
+        launch(k_scatter, (N + 255) / 256, 256, 0, st, pos, N, cell_of, cell_start, cell_fill, sorted, spos, gate);
         count_launch();
         TNET_LAUNCH_CHECK();
-        k_pair_count<<<(int)(((int64_t)N * 32 + 255) / 256), 256, 0, st>>>(
+        launch(k_pair_count, (int)(((int64_t)N * 32 + 255) / 256), 256, 0, st, 
             pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, rowcnt, gate);
         count_launch();
         TNET_LAUNCH_CHECK();
     }
     rc = scan_exclusive_i32(rowcnt, row_ptr, N, tmp, nullptr, n_pairs_dev, st, gate);
     if (rc) return rc;
-    k_cap_check<<<(N + 256) / 256 < 1024 ? (N + 256) / 256 : 1024, 256, 0, st>>>(n_pairs_dev, cap, row_ptr, N,
-                                                                                  status, gate);
+    launch(k_cap_check, (N + 256) / 256 < 1024 ? (N + 256) / 256 : 1024, 256, 0, st, n_pairs_dev, cap, row_ptr, N,
+           status, gate);
     count_launch();
     TNET_LAUNCH_CHECK();
     if (N > 0) {
-        k_pair_fill<<<(N + kFillWarps - 1) / kFillWarps, kFillWarps * 32, 0, st>>>(
+        launch(k_pair_fill, (N + kFillWarps - 1) / kFillWarps, kFillWarps * 32, 0, st, 
             pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, row_ptr, col, cap, gate);
         count_launch();
         TNET_LAUNCH_CHECK();

@@ -55,6 +55,7 @@ using namespace tnet;
 
 // TF32 split of the weights (for the test entry point)
 __global__ void k_tf32_split(const float *__restrict__ x, float *__restrict__ hi, float *__restrict__ lo, int64_t n) {
+    pdl_entry();
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t < n) tf32_split(x[t], hi[t], lo[t]);
 }
@@ -64,7 +65,7 @@ extern "C" int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const
     if (M < 1 || N < 4 || N > 512 || K < 4 || K % 4 || N % 4 || !A || !B || !Bsplit || !Cout) return TNET_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nk = (int64_t)N * K;
-    k_tf32_split<<<(int)((nk + 255) / 256), 256, 0, st>>>(B, Bsplit, Bsplit + nk, nk);
+    launch(k_tf32_split, (int)((nk + 255) / 256), 256, 0, st, B, Bsplit, Bsplit + nk, nk);
     TNET_LAUNCH_CHECK();
     tc::TcShape P = tc::tshape(M, N, K);
     EpiStore epi{Cout, N, 0};

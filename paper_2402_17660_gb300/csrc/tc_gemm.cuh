@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo, TcShape P,
               Epi epi, int32_t *status) {
+    pdl_entry();
     using C = TileCfg<BN, X3>;
     constexpr int STAGES = C::STAGES;
     constexpr int BK = C::BKE;
@@ -484,7 +485,7 @@ int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *
         if (sms <= 0) sms = 1;
     }
     const int grid = (int)(tiles < sms ? tiles : sms);
-    k_tc_gemm<BN, Epi, X3><<<grid, THREADS, C::SMEM, st>>>(ma, mb, mal, mbl, P, epi, status);
+    launch(k_tc_gemm<BN, Epi, X3>, grid, THREADS, C::SMEM, st, ma, mb, mal, mbl, P, epi, status);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;

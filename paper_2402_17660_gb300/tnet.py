@@ -237,14 +237,16 @@ def tuning_knobs(lib=None) -> list[tuple[str, list[int]]]:
     return out
 
 
-def autotune(model: TensorNet, z, pos, nl: NeighborList, batch=None, box=None, n_systems=1, reps=3,
+def autotune(model: TensorNet, z, pos, nl: NeighborList, batch=None, box=None, n_systems=1, reps=5,
              cache: str | None = TUNE_CACHE, force=False):
     """Pick launch shapes by timing them on this input (coordinate descent
-    over the context's knobs, CUDA events around whole energy+force calls),
+    over the context's knobs, CUDA events around CUDA-graph replays of whole
+    energy+force calls),
     set them on the model and cache them as JSON keyed by GPU, precision,
     shape and size.  Returns (knobs, {knob: {candidate: ms}})."""
     dev = model.device
-    key = "|".join([torch.cuda.get_device_name(dev), f"p{model.desc.precision}", f"F{model.F}L{model.L}",
+    key = "|".join([torch.cuda.get_device_name(dev), f"knobs{len(model.get_tuning())}", f"p{model.desc.precision}",
+                    f"F{model.F}L{model.L}",
                     f"N{pos.shape[0]}", f"S{n_systems}", f"E{int(nl.n_pairs.item()) // 1024}k"])
     table = {}
     if cache and os.path.exists(cache):
@@ -259,13 +261,26 @@ def autotune(model: TensorNet, z, pos, nl: NeighborList, batch=None, box=None, n
     Fo = torch.empty((pos.shape[0], 3), dtype=torch.float32, device=dev)
 
     def run_ms():
-        model.energy_forces(z, pos, nl, batch, box, n_systems, out=(E, Fo, None))
+        # as a CUDA-graph replay, the way graph-captured steps run (the knobs
+        # are baked into a graph's launches at capture time)
+        def call():
+            model.energy_forces(z, pos, nl, batch, box, n_systems, out=(E, Fo, None))
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            call()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            call()
+        g.replay()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         ev[0].record()
         for _ in range(reps):
-            model.energy_forces(z, pos, nl, batch, box, n_systems, out=(E, Fo, None))
+            g.replay()
         ev[1].record()
         torch.cuda.synchronize()
+        del g
         return ev[0].elapsed_time(ev[1]) / reps
 
     knobs = model.get_tuning()
