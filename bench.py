@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--neighbor-bench", action="store_true",
                     help="neighbor search alone: 32,768-particle random cloud (64 neighbors per particle) split "
                          "into 1..1024 systems (one JSON line)")
+    ap.add_argument("--radial-table", type=int, default=0,
+                    help="n > 0: tabulate the radial projections and filters at n distances (inference "
+                         "mode; cubic Hermite interpolation per pair)")
     ap.add_argument("--per-molecule", action="store_true",
                     help="for batched workloads, also time one eager call per molecule")
     return ap.parse_args()
@@ -221,6 +224,8 @@ def workload_config(sys_, n_pairs, args, graph=True):
     return {"workload": sys_.name, "n_atoms": sys_.n_atoms, "n_systems": sys_.n_systems,
             "periodic": sys_.box is not None, "directed_pairs": int(n_pairs), "cutoff_A": 5.0,
             "layers": 2, "channels": 128, "rbf": 32, "precision": args.precision,
+            "radial_functions": (f"tabulated at {args.radial_table} distances, cubic Hermite"
+                                 if args.radial_table else "radial MLP per pair"),
             "radial_mlp_activations": "recomputed in the reverse pass" if recompute_edges(args, sys_.n_atoms)
             else "kept from the forward pass",
             "step": "neighbor search + energy + forces", "cuda_graph": graph,
@@ -258,15 +263,26 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours ---
-def stage_work(tag, nu, N, E, F, K, prec):
+def stage_work(tag, nu, N, E, F, K, prec, table=False):
     """Algorithmic work of one instance of a timed stage: (FLOP, bytes, engine).
     Bytes count each operand read once and each result written once,
     including the operand copies the tensor-core modes write beside a result
-    (bf16: 2 B per element; 3xTF32: a 4 B residual)."""
+    (bf16: 2 B per element; 3xTF32: a 4 B residual).  With tabulated radial
+    functions the "mlp1" stage is the per-pair table evaluation (read d, write
+    g and dg/dd; the tables themselves stay in L2)."""
     f = 4.0
     bf16 = prec == "bf16"
     cp = {"fp32": 0.0, "bf16": 2.0, "tf32x3": 4.0}[prec]   # operand-copy bytes per element
     hb = 2.0 if bf16 else 4.0            # bytes per element of a GEMM input operand
+    if table:
+        if tag == "mlp1":
+            return 2.0 * 12 * 3 * F * nu, nu * (f + 2 * 3 * F * f), "hbm"
+        if tag == "emb_edges_bwd":  # reads f and df/dd, updates dE/dd
+            return 2.0 * 43 * F * 2 * nu, f * (9 * N * F + 6 * F * nu + 2 * nu) + 16.0 * E, "hbm"
+        if tag == "message_bwd":    # reads g and dg/dd, no dE/da3
+            rd = f * (3 * 9 * N * F + 2 * 3 * F * nu) + 8.0 * E
+            wr = (f + cp) * 9 * N * F + 2 * f * nu
+            return 4.0 * 9 * F * 2 * nu + 2.0 * 3 * F * nu, rd + wr, "hbm"
     if tag == "mlp1":
         return 2.0 * nu * K * F, nu * (K * f + F * f + F * hb), "alu"
     if tag == "mlp2":
@@ -316,8 +332,17 @@ def run_ours(args):
     prec = {"fp32": 0, "bf16": 1, "tf32x3": 2}[args.precision]
     rec = recompute_edges(args, N)
     m = TensorNet(W, max_atoms=N, max_systems=sys_.n_systems, max_pairs=cap, precision=prec, device=dev,
-                  recompute_edges=rec)
+                  recompute_edges=rec, radial_table=args.radial_table)
     lib = m.lib
+    table_build_ms = None
+    if args.radial_table:   # one-off per weight set: time a rebuild of the tables
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0e.record()
+        m.set_weights(W)
+        t1e.record()
+        torch.cuda.synchronize()
+        table_build_ms = t0e.elapsed_time(t1e)
     z = torch.from_numpy(sys_.z).to(dev)
     pos = torch.from_numpy(sys_.pos).to(dev)
     batch = torch.from_numpy(sys_.batch).to(dev) if sys_.n_systems > 1 else None
@@ -417,12 +442,13 @@ def run_ours(args):
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s, derived
     x3 = args.precision == "tf32x3"
+    tab = args.radial_table > 0
     work_tags = [k for k in sorted(stages, key=lambda k: -stages[k]["ms_per_step"])
-                 if stage_work(k, nu, N, n_pairs, F_, shape.K, args.precision) is not None]
+                 if stage_work(k, nu, N, n_pairs, F_, shape.K, args.precision, tab) is not None]
     if work_tags:
         tag = work_tags[0]
-        flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, args.precision)
-        if x3 and tag in ("mlp2", "mlp3", "mlp3_bwd", "mlp2_bwd"):
+        flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, args.precision, tab)
+        if x3 and not tab and tag in ("mlp2", "mlp3", "mlp3_bwd", "mlp2_bwd"):
             # 3xTF32: three TF32 MMAs per product; operands fp32 + fp32 residual
             engine = "tensor_tf32"
             nbytes = nbytes * 1.5
@@ -430,7 +456,8 @@ def run_ours(args):
         traffic = None
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tpath):
-            tr = json.load(open(tpath)).get(f"{args.workload}:{args.precision}:{tag}")
+            tkey = f"{args.workload}:{args.precision}:{tag}" + (f":table{args.radial_table}" if tab else "")
+            tr = json.load(open(tpath)).get(tkey)
             if tr and tr.get("kernel_rev") == kernel_revision():
                 traffic = tr["bytes_per_launch"]
         if engine == "tensor":
@@ -490,7 +517,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     E_run, F_run = E.cpu().numpy().copy(), Fo.cpu().numpy().astype(np.float64)
     accuracy = {}
-    if prec != 0:
+    if prec != 0 or args.radial_table:
         m32 = TensorNet(W, max_atoms=N, max_systems=S, max_pairs=cap, precision=0, device=dev,
                         recompute_edges=rec)
         nl32 = m32.neighbors(pos, batch, box, S)
@@ -518,6 +545,10 @@ def run_ours(args):
                                    sorted(stages.items(), key=lambda kv: -kv[1]["ms_per_step"])},
             "clocks": ck, "parallelism": f"replicas x{world}", "accuracy": accuracy,
             "tuning": {"knobs": knobs, "candidates_ms": tune_ms}}
+    if args.radial_table:
+        line["radial_table"] = {"points": args.radial_table, "build_ms_per_weight_set": table_build_ms,
+                                "note": "tables built once per weight set (tnet_radial_tables), outside the "
+                                        "timed step; accuracy.vs_fp32_gpu compares with the exact radial MLP"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], ref = cpu_baseline(sys_, W)
         if ref is not None:
@@ -589,7 +620,7 @@ def run_md(sys_, shape, prec, dev, args):
     Wmd = synth.md_weights(shape, seed=0)
     N = sys_.n_atoms
     m = TensorNet(Wmd, max_atoms=N, max_systems=1, max_pairs=int(100 * N) + 1024, precision=prec, device=dev,
-                  recompute_edges=recompute_edges(args, N))
+                  recompute_edges=recompute_edges(args, N), radial_table=args.radial_table)
     z = torch.from_numpy(sys_.z).to(dev)
     pos = torch.from_numpy(sys_.pos).to(dev).clone()
     vel = torch.from_numpy(synth.maxwell_boltzmann(sys_, 300.0, seed=1)).to(dev)

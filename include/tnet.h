@@ -62,12 +62,20 @@ typedef struct tnet_ctx tnet_ctx;
  * activations (about 12 F floats per undirected pair and layer, plus operand
  * copies) for the reverse pass; 1 = the reverse pass recomputes them, so the
  * workspace holds one layer's worth (for systems whose pair count presses on
- * memory).  Results are bitwise identical either way. */
+ * memory).  Results are bitwise identical either way.
+ * radial_table: 0 = the radial MLP and the radial projections run per pair;
+ * n in [256, 65536] = both are functions of the pair distance alone, so each
+ * call tabulates them (values and exact d-derivatives, FP32) at n points on
+ * [0, cutoff_upper] and evaluates them per pair by cubic Hermite
+ * interpolation; forces are the exact derivatives of the interpolated energy.
+ * The tables are built by tnet_radial_tables.  An inference mode: weight
+ * gradients return UNSUPPORTED. */
 typedef struct {
     int F, K, L, max_z;
     float cutoff_upper, cutoff_lower;
     int precision;
     int recompute_edges;
+    int radial_table;
 } tnet_model_desc;
 
 typedef enum {
@@ -177,6 +185,19 @@ int tnet_energy_forces(tnet_ctx *ctx, const float *weights, int n_atoms, int n_s
                        const float *box, const int32_t *row_ptr, const int32_t *col,
                        const float *energy_seed, double *energy, float *forces,
                        float *grad_weights, int32_t *status_dev, tnet_stream_t stream);
+
+/* Radial-function tables (contexts with radial_table = n > 0).  The radial
+ * projections f(d) and every layer's filter g(d) (TensorNet Sec. 2.1.1: the
+ * expnorm basis, the cosine cutoff and the radial MLP) depend on the pair
+ * distance and the weights alone.  This call evaluates them, with their
+ * d-derivatives, from `weights` at the n points d_k = k cutoff_upper/(n-1),
+ * FP32, into the context's workspace; tnet_energy_forces and tnet_md_step
+ * then interpolate them and do not read the radial weights.  Call it again
+ * whenever those weights change.  Before the first call, tnet_energy_forces
+ * and tnet_md_step of a table-mode context return TNET_ERR_ARG.  Stream
+ * ordered (the tables are ready for work enqueued after it on `stream`);
+ * graph-capturable.  Contexts without tables: TNET_ERR_ARG. */
+int tnet_radial_tables(tnet_ctx *ctx, const float *weights, tnet_stream_t stream);
 
 /* Molecular dynamics (the paper's MD use, Sec. 3 "Molecular Simulations";
  * one step = one energy evaluation plus one force backward pass): n_steps

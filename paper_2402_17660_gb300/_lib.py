@@ -13,7 +13,7 @@ from . import build as _build
 class ModelDesc(ctypes.Structure):
     _fields_ = [("F", ctypes.c_int), ("K", ctypes.c_int), ("L", ctypes.c_int), ("max_z", ctypes.c_int),
                 ("cutoff_upper", ctypes.c_float), ("cutoff_lower", ctypes.c_float),
-                ("precision", ctypes.c_int), ("recompute_edges", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("recompute_edges", ctypes.c_int), ("radial_table", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p
@@ -31,6 +31,7 @@ SIGNATURES = {
     "tnet_neighbors": (_i32, [_vp, _i32, _i32, _vp, _vp, _vp, _f32, _vp, _vp, _i64, _vp, _vp, _vp]),
     "tnet_energy_forces": (_i32, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                   _vp, _vp, _vp]),
+    "tnet_radial_tables": (_i32, [_vp, _vp, _vp]),
     "tnet_md_step": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _f32, _f32, _i32, _i32, _vp, _vp,
                             _vp, _vp]),
     "tnet_md_rebuilds": (_i32, [_vp, _vp]),

@@ -18,6 +18,7 @@ int validate_desc(const tnet_model_desc *d) {
     if (!(d->cutoff_upper > d->cutoff_lower) || d->cutoff_lower < 0.f) return TNET_ERR_ARG;
     if (d->precision < 0 || d->precision > 2) return TNET_ERR_ARG;
     if (d->recompute_edges < 0 || d->recompute_edges > 1) return TNET_ERR_ARG;
+    if (d->radial_table != 0 && (d->radial_table < 256 || d->radial_table > 65536)) return TNET_ERR_ARG;
     return TNET_OK;
 }
 
@@ -87,16 +88,18 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->at = take(f * N * F / 2);
     L->t = take(f * N * F / 2);
     L->Ei = take(f * N);
-    // edge MLP
-    L->eu = take(f * U * K);
+    // edge MLP (table mode keeps only g, dg/dd in the a3 slab, and f)
+    const int64_t nt = d->radial_table;
+    const int64_t rm = nt > 0 ? 0 : 1;  // the per-pair radial MLP runs
+    L->eu = take(f * U * K * rm);
     L->phiu = take(f * U);
     L->geo = take(16 * U);
     // (one set per layer, which the reverse pass reads, unless it recomputes them)
     const int64_t NLm = (NL > 0 && !d->recompute_edges) ? NL : 1;
-    L->a1 = take(f * U * F * NLm);
-    L->h1 = take(f * U * F * NLm);
-    L->a2 = take(f * U * 2 * F * NLm);
-    L->h2 = take(f * U * 2 * F * NLm);
+    L->a1 = take(f * U * F * NLm * rm);
+    L->h1 = take(f * U * F * NLm * rm);
+    L->a2 = take(f * U * 2 * F * NLm * rm);
+    L->h2 = take(f * U * 2 * F * NLm * rm);
     L->a3 = take(f * U * 3 * F * NLm);
     L->g = take(f * U * 3 * F * NLm);
     // reverse pass
@@ -115,14 +118,14 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->gas1 = take(f * N * 2 * F);
     L->gn0 = take(f * N * F);
     L->gq0 = take(f * N * F);
-    L->gg = take(f * U * 3 * F);
-    L->ga2 = take(f * U * 2 * F);
-    L->ga1 = take(f * U * F);
-    L->ge = take(f * U * K);
+    L->gg = take(f * U * 3 * F * rm);
+    L->ga2 = take(f * U * 2 * F * rm);
+    L->ga1 = take(f * U * F * rm);
+    L->ge = take(f * U * K * rm);
     L->gphiu = take(f * U);
     L->gvec = take(f * 3 * E);
     L->fu = take(f * U * 3 * F);
-    L->gfu = take(f * U * 3 * F);
+    L->gfu = take(f * U * 3 * F * rm);
     L->ue = take(i * U);
     L->edge_g = take(16 * E);
     L->gp = take(f * 3 * U);
@@ -135,6 +138,13 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->wpart_floats = 4LL << 20;
     L->wpart = take(f * L->wpart_floats);
     L->w3p = take(f * (NL > 0 ? NL : 1) * (6LL * F * F + 3 * F));
+    // tabulated radial functions (radial_table = n > 0): value and derivative
+    // tables [n][3F] of the projections f and of each layer's filter g, the
+    // scratch of their construction, the per-pair distance and df/dd
+    L->tab = take(f * (nt > 0 ? (NL + 1) * 2 * nt * 3 * F : 0));
+    L->tab_tmp = take(f * (nt > 0 ? nt * (2 * K + 2 + 3 * F + 3 * 2 * F + 2 * 3 * F) : 0));
+    L->dist = take(f * (nt > 0 ? U : 0));
+    L->dfu = take(f * (nt > 0 ? U * 3 * F : 0));
     // tensor-core modes: weight operands (bf16 forward + transposed copies,
     // or fp32 TF32 residuals + transposed high parts; the 3xTF32 GEMMs of the
     // BF16 mode use the latter), and in BF16 mode the bf16 copies of the node
@@ -153,10 +163,10 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->wbf = take(L->wbf_bytes);
     L->nbf = take(esz * n9);
     L->eu_bf = 0;
-    L->h1_bf = take(esz * U * F * NLm);
-    L->h2_bf = take(esz * U * 2 * F * NLm);
-    L->ga3_bf = take(esz * U * 3 * F);
-    L->ga2_bf = take(esz * U * 2 * F);
+    L->h1_bf = take(esz * U * F * NLm * rm);
+    L->h2_bf = take(esz * U * 2 * F * NLm * rm);
+    L->ga3_bf = take(esz * U * 3 * F * rm);
+    L->ga2_bf = take(esz * U * 2 * F * rm);
     L->ga1_bf = 0;
     L->gfu_bf = 0;
     // MD
@@ -391,6 +401,12 @@ int tnet_energy_forces(tnet_ctx *c, const float *w, int N, int S, const int32_t 
     PdlScope pdl_scope(c->tune[T_PDL]);
     return energy_forces_impl(c, w, N, S, z, pos, batch, box, row_ptr, col, seed, energy, forces, grad_w,
                               status, (cudaStream_t)stream);
+}
+
+int tnet_radial_tables(tnet_ctx *c, const float *w, tnet_stream_t stream) {
+    if (!c || !w || c->d.radial_table <= 0) return TNET_ERR_ARG;
+    PdlScope pdl_scope(c->tune[T_PDL]);
+    return radial_tables_impl(c, w, (cudaStream_t)stream);
 }
 
 int tnet_md_step(tnet_ctx *c, const float *w, int N, const int32_t *z, const float *inv_mass, float *pos,

@@ -368,6 +368,8 @@ struct Layout {
     // per layer: the last radial-MLP layer's weight [3F][2F] and bias [3F]
     // with rows in plane-major order p*F + c (the blob keeps c*3 + p)
     size_t w3p;
+    // tabulated radial functions (radial_table > 0)
+    size_t tab, tab_tmp, dist, dfu;
     int64_t wpart_floats, zsplits;
     // MD
     size_t md_row_ptr, md_col, md_npairs, md_forces, md_energy, md_pos_ref, md_step, md_need, md_rebuilds;
@@ -411,6 +413,9 @@ struct tnet_ctx {
     int prof_on, prof_n, prof_cap;
     cudaEvent_t *prof_ev;
     int *prof_tag;
+    // radial_table > 0: the tables hold the radial functions of the weights
+    // last passed to tnet_radial_tables
+    int tab_ready;
     // CUDA graph cache for tnet_md_step
     cudaGraphExec_t md_exec;
     const void *md_key[8];
@@ -477,6 +482,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *w, int n_atoms, int n_systems
                        const int32_t *row_ptr, const int32_t *col, const float *seed,
                        double *energy, float *forces, float *grad_w, int32_t *status_dev,
                        cudaStream_t st);
+int radial_tables_impl(tnet_ctx *ctx, const float *w, cudaStream_t st);
 int md_impl(tnet_ctx *ctx, const float *w, int n_atoms, const int32_t *z, const float *inv_mass,
             float *pos, float *vel, const float *box, float dt, float skin, int rebuild_every,
             int n_steps, double *e_kin, double *e_pot, int32_t *status_dev, cudaStream_t st);

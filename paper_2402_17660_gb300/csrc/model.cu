@@ -242,6 +242,92 @@ __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restric
     }
 }
 
+// ------------------------------------------------ tabulated radial functions ---
+// The radial projections f(d) and every layer's filter g(d) depend on the pair
+// distance alone.  In table mode they are evaluated, with their d-derivatives,
+// at the grid d_k = k h (k < n, h = rc/(n - 1)) and interpolated per pair by
+// cubic Hermite polynomials on [d_k, d_k+1].
+
+// basis e_q(d_k), de_q/dd, phi(d_k), dphi/dd at every grid point
+__global__ void k_tab_rbf(int n, float h, RadialParams rp, float *__restrict__ e, float *__restrict__ de,
+                          float *__restrict__ phi, float *__restrict__ dphi) {
+    pdl_entry();
+    const int K = rp.K;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * K;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t / K), q = (int)(t % K);
+        const float d = k * h;
+        const float ph = cutoff_phi(d, rp), dph = cutoff_dphi(d, rp);
+        float ev, dev;
+        expnorm_k(d, q, rp, ph, dph, ev, dev);
+        e[t] = ev;
+        de[t] = dev;
+        if (q == 0) {
+            phi[k] = ph;
+            dphi[k] = dph;
+        }
+    }
+}
+
+// g = phi silu(a3) (already in g); dg/dd = dphi silu(a3) + phi t3, where t3 is
+// the tangent of a3 (forward-mode derivative through the MLP)
+__global__ void k_tab_finish(int n, int W, const float *__restrict__ a3, const float *__restrict__ t3,
+                             const float *__restrict__ phi, const float *__restrict__ dphi, float *__restrict__ dg) {
+    pdl_entry();
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * W;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(t / W);
+        dg[t] = dphi[k] * silu_f(a3[t]) + phi[k] * t3[t];
+    }
+}
+
+// per undirected pair: u_ij, phi (geo), phi alone (phiu) and d (dist)
+__global__ void k_pair_geo(const float *__restrict__ pos, const float *__restrict__ box,
+                           const int32_t *__restrict__ batch, const int2 *__restrict__ uij,
+                           const int32_t *__restrict__ nu, RadialParams rp, float *__restrict__ phiu,
+                           float4 *__restrict__ geo, float *__restrict__ dist) {
+    pdl_entry();
+    const int U = *nu;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < U; u += gridDim.x * blockDim.x) {
+        const int2 p = uij[u];
+        float x, y, zz;
+        pair_vec(pos, box, batch, p.x, p.y, x, y, zz);
+        const float d = sqrtf(norm2_rn(x, y, zz));
+        const float phi = cutoff_phi(d, rp);
+        const float inv = 1.0f / d;
+        phiu[u] = phi;
+        dist[u] = d;
+        geo[u] = make_float4(x * inv, y * inv, zz * inv, phi);
+    }
+}
+
+// out_v[u][w], out_d[u][w]: the cubic Hermite interpolant of a tabulated
+// function (values tv, derivatives td, [n][W] on the grid k h) and its
+// derivative at d_u
+__global__ void k_tab_eval(const float *__restrict__ dist, const int32_t *__restrict__ nu, int n, float h,
+                           int W, const float *__restrict__ tv, const float *__restrict__ td,
+                           float *__restrict__ out_v, float *__restrict__ out_d) {
+    pdl_entry();
+    const int U = *nu;
+    const float inv_h = 1.0f / h;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)U * W;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = t / W;
+        const int w = (int)(t % W);
+        const float x = dist[u] * inv_h;
+        int k = (int)floorf(x);
+        k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
+        const float s = x - (float)k;
+        const int64_t o = (int64_t)k * W + w;
+        const float v0 = tv[o], v1 = tv[o + W], d0 = td[o] * h, d1 = td[o + W] * h;
+        const float s2 = s * s, s3 = s2 * s;
+        out_v[t] = (2.f * s3 - 3.f * s2 + 1.f) * v0 + (s3 - 2.f * s2 + s) * d0 + (3.f * s2 - 2.f * s3) * v1 +
+                   (s3 - s2) * d1;
+        out_d[t] = ((6.f * s2 - 6.f * s) * (v0 - v1) + (3.f * s2 - 4.f * s + 1.f) * d0 + (3.f * s2 - 2.f * s) * d1) *
+                   inv_h;
+    }
+}
+
 // Per-element pair-embedding tables: Ta[z] = W_e[:, :F] emb[z],
 // Tb[z] = W_e[:, F:] emb[z] + b_e, so that Z_ij = Ta[z_i] + Tb[z_j].
 __global__ void k_elem_tables(const float *__restrict__ emb, const float *__restrict__ W,
@@ -709,8 +795,10 @@ __global__ void k_T_bwd(const float *__restrict__ Y, const float *__restrict__ M
 // lower part gathers gM_j alone (kMU edges in flight), the upper part gM_j,
 // Y_j and a3 together (kMUU edges).  Indices are staged in shared memory as in
 // k_message; the gY sums run in row order.
+// With TAB (tabulated radial functions) a3 holds dg/dd instead: the kernel
+// adds sum dE/dg dg/dd to gphi (then dE/dd of the pair) and writes no dE/da3.
 constexpr int kMUU = 2;
-template <int F>
+template <int F, bool TAB>
 __global__ void __launch_bounds__(F, 512 / F)
     k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                   const int32_t *__restrict__ pair_of, const float *__restrict__ gU, const float *__restrict__ Y,
@@ -787,7 +875,7 @@ __global__ void __launch_bounds__(F, 512 / F)
                     const int64_t o = (int64_t)uu[k] * 3 * F + c;
                     g[k][0] = gU[o]; g[k][1] = gU[o + F]; g[k][2] = gU[o + 2 * F];
                     a[k][0] = a3[o]; a[k][1] = a3[o + F]; a[k][2] = a3[o + 2 * F];
-                    phi[k] = phiu[uu[k]];
+                    phi[k] = TAB ? 0.f : phiu[uu[k]];
                     load_coords(gM, jj[k], c, N, F, gmj[k]);
                     load_coords(Y, jj[k], c, N, F, yj[k]);
                 }
@@ -810,12 +898,16 @@ __global__ void __launch_bounds__(F, 512 / F)
                     float r = 0.f;
 #pragma unroll
                     for (int p = 0; p < 3; ++p) {
-                        float sv, sd;
-                        silu_and_grad_f(a[k][p], sv, sd);
-                        r = fmaf(sp[p], sv, r);
-                        const float ga = sp[p] * phi[k] * sd;
-                        if (ga3) ga3[o + p * F] = ga;
-                        opcopy_store(ga3_cp, o + p * F, ga);
+                        if constexpr (TAB) {
+                            r = fmaf(sp[p], a[k][p], r);
+                        } else {
+                            float sv, sd;
+                            silu_and_grad_f(a[k][p], sv, sd);
+                            r = fmaf(sp[p], sv, r);
+                            const float ga = sp[p] * phi[k] * sd;
+                            if (ga3) ga3[o + p * F] = ga;
+                            opcopy_store(ga3_cp, o + p * F, ga);
+                        }
                     }
                     r = warp_sum(r);
                     if (lane == 0) s_red[k0 + k - nl][warp] = r;
@@ -1034,7 +1126,7 @@ __global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *_
                                 const float *__restrict__ fu, const float *__restrict__ Ta,
                                 const float *__restrict__ Tb, const float *__restrict__ gXraw,
                                 float *__restrict__ gfu, float4 *__restrict__ edge_g,
-                                OpCopy gfu_cp) {
+                                OpCopy gfu_cp, const float *__restrict__ dfu, float *__restrict__ dEdd) {
     pdl_entry();
     constexpr int F = CPL * 32;
     const int lane = threadIdx.x & 31;
@@ -1053,6 +1145,7 @@ __global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *_
         zj = (zj < 0 || zj >= max_z) ? 0 : zj;
         float a_phi = 0.f, ax = 0.f, ay = 0.f, az = 0.f;   // use (i, j)
         float b_phi = 0.f, bx = 0.f, by = 0.f, bz = 0.f;   // use (j, i), gradient w.r.t. u_ji
+        float gd = 0.f;                                    // sum dE/df df/dd (table mode)
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
             const int c = lane + 32 * k;
@@ -1089,18 +1182,22 @@ __global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *_
             const float o0 = phi * (Zij * gc0 + Zji * hc0);
             const float o1 = phi * (Zij * gcA + Zji * hcA);
             const float o2 = phi * (Zij * gcS + Zji * hcS);
-            float *o = gfu + (int64_t)u * 3 * F + c;
-            o[0] = o0;
-            o[F] = o1;
-            o[2 * F] = o2;
             const int64_t ob = (int64_t)u * 3 * F + c;
+            if (gfu) {
+                gfu[ob] = o0;
+                gfu[ob + F] = o1;
+                gfu[ob + 2 * F] = o2;
+            }
             opcopy_store(gfu_cp, ob, o0);
             opcopy_store(gfu_cp, ob + F, o1);
             opcopy_store(gfu_cp, ob + 2 * F, o2);
+            if (dfu) gd += o0 * dfu[ob] + o1 * dfu[ob + F] + o2 * dfu[ob + 2 * F];
         }
         a_phi = warp_sum(a_phi); ax = warp_sum(ax); ay = warp_sum(ay); az = warp_sum(az);
         b_phi = warp_sum(b_phi); bx = warp_sum(bx); by = warp_sum(by); bz = warp_sum(bz);
+        if (dfu) gd = warp_sum(gd);
         if (lane == 0) {
+            if (dfu) dEdd[u] += gd;
             const int e = ue[u];
             edge_g[e] = make_float4(a_phi, ax, ay, az);
             edge_g[rev[e]] = make_float4(b_phi, bx, by, bz);
@@ -1110,6 +1207,7 @@ __global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *_
 
 // dE/dr_ij of each undirected pair (i < j): one warp per pair, lane k < K.
 //   dE/dd   = sum_k ge[u][k] de_k/dd + (gphi_mlp[u] + gphi(i,j) + gphi(j,i)) dphi/dd
+//             + dEdd[u]  (the tabulated functions' share, table mode)
 //   dE/du   = gu(i,j) - gu(j,i)                       (u_ji = -u_ij)
 //   Gp[u]   = dE/dd u + (dE/du - (dE/du . u) u) / d
 __global__ void k_pair_vec(const float *__restrict__ pos, const float *__restrict__ box,
@@ -1117,7 +1215,7 @@ __global__ void k_pair_vec(const float *__restrict__ pos, const float *__restric
                            const int32_t *__restrict__ ue, const int32_t *__restrict__ rev,
                            const int32_t *__restrict__ nu, RadialParams rp, const float *__restrict__ ge,
                            const float *__restrict__ gphi_mlp, const float4 *__restrict__ edge_g,
-                           float *__restrict__ Gp) {
+                           const float *__restrict__ dEdd, float *__restrict__ Gp) {
     pdl_entry();
     const int U = *nu;
     const int lane = threadIdx.x & 31;
@@ -1129,17 +1227,19 @@ __global__ void k_pair_vec(const float *__restrict__ pos, const float *__restric
         const float d = sqrtf(norm2_rn(x, y, zz));
         const float phi = cutoff_phi(d, rp), dphi = cutoff_dphi(d, rp);
         float s = 0.f;
-        for (int k = lane; k < rp.K; k += 32) {
-            float e, de;
-            expnorm_k(d, k, rp, phi, dphi, e, de);
-            s = fmaf(ge ? ge[u * rp.K + k] : 0.f, de, s);
+        if (ge) {
+            for (int k = lane; k < rp.K; k += 32) {
+                float e, de;
+                expnorm_k(d, k, rp, phi, dphi, e, de);
+                s = fmaf(ge[u * rp.K + k], de, s);
+            }
+            s = warp_sum(s);
         }
-        s = warp_sum(s);
         if (lane == 0) {
             const int e = ue[u];
             const float4 a = edge_g[e], b = edge_g[rev[e]];
             const float gphi = (gphi_mlp ? gphi_mlp[u] : 0.f) + a.x + b.x;
-            const float gd = s + gphi * dphi;
+            const float gd = s + gphi * dphi + (dEdd ? dEdd[u] : 0.f);
             const float inv = 1.0f / d;
             const float ux = x * inv, uy = y * inv, uz = zz * inv;
             const float gx = a.y - b.y, gy = a.z - b.z, gz = a.w - b.w;
@@ -1361,6 +1461,73 @@ __global__ void k_rows_in_range(const int32_t *__restrict__ row_ptr, int N, int6
     }
 }
 
+// Radial-function tables (radial_table = n > 0): the projections f (table 0)
+// and each layer's filter g (table 1 + l), [n][3F] values followed by [n][3F]
+// d-derivatives on the grid d_k = k h, h = rc/(n - 1).  f, g are functions of
+// the pair distance alone (the expnorm basis, the cosine cutoff and the radial
+// MLP of TensorNet Sec. 2.1.1); their derivatives come from a forward-mode
+// pass through the same layers.
+int radial_tables_impl(tnet_ctx *ctx, const float *wblob, cudaStream_t st) {
+    const tnet_model_desc &d = ctx->d;
+    const Layout &Lw = ctx->lay;
+    const int F = d.F, K = d.K, NL = d.L, nt = d.radial_table;
+    const int sms = ctx->num_sms;
+    const RadialParams rp = ctx->rp;
+    const int gctas = sms * ctx->tune[T_GEMM_CTAS];
+    if (nt <= 0) return TNET_ERR_ARG;
+    Weights W;
+    weight_offsets(&d, wblob, &W);
+    auto f32 = [&](size_t off) { return wsp<float>(ctx, off); };
+    const float th = rp.rc / (float)(nt - 1);
+    auto tabv = [&](int j) { return f32(Lw.tab) + (int64_t)j * 2 * nt * 3 * F; };
+    auto tabd = [&](int j) { return tabv(j) + (int64_t)nt * 3 * F; };
+    const int64_t w3_per = 6LL * F * F + 3 * F;
+    auto w3p = [&](int l) { return f32(Lw.w3p) + l * w3_per; };
+    auto b3p = [&](int l) { return f32(Lw.w3p) + l * w3_per + 6LL * F * F; };
+    if (NL > 0) {
+        FilterRows FR{};
+        for (int l = 0; l < NL; ++l) { FR.w[l] = W.layer[l].mlp3_w; FR.b[l] = W.layer[l].mlp3_b; }
+        launch(k_filter_rows, dim3(48, NL), 256, 0, st, FR, F, f32(Lw.w3p));
+        count_launch();
+        TNET_LAUNCH_CHECK();
+    }
+    {
+        // value and forward-mode derivative of each radial function at the grid
+        // points: the MLP chains run on (e, de/dd), FP32 in every mode
+        float *e_t = f32(Lw.tab_tmp), *de_t = e_t + (int64_t)nt * K, *phi_t = de_t + (int64_t)nt * K,
+              *dphi_t = phi_t + nt, *a1_t = dphi_t + nt, *h1_t = a1_t + (int64_t)nt * F, *t1_t = h1_t + (int64_t)nt * F,
+              *a2_t = t1_t + (int64_t)nt * F, *h2_t = a2_t + (int64_t)nt * 2 * F, *t2_t = h2_t + (int64_t)nt * 2 * F,
+              *a3_t = t2_t + (int64_t)nt * 2 * F, *t3_t = a3_t + (int64_t)nt * 3 * F;
+        launch(k_tab_rbf, grid_for((int64_t)nt * K, 256, sms), 256, 0, st, nt, th, rp, e_t, de_t, phi_t, dphi_t);
+        count_launch();
+        TNET_LAUNCH_CHECK();
+        TRY(sgemm<false, true>(gshape(nt, 3 * F, K, e_t, K, W.dproj_w, K),
+                               EpiBiasAct{W.dproj_b, nullptr, 0, tabv(0), 3 * F, 0, nullptr}, gctas, st));
+        TRY(sgemm<false, true>(gshape(nt, 3 * F, K, de_t, K, W.dproj_w, K), EpiStore{tabd(0), 3 * F, 0}, gctas, st));
+        for (int l = 0; l < NL; ++l) {
+            const LayerW &Lr = W.layer[l];
+            TRY(sgemm<false, true>(gshape(nt, F, K, e_t, K, Lr.mlp1_w, K),
+                                   EpiBiasAct{Lr.mlp1_b, a1_t, F, h1_t, F, 1, nullptr}, gctas, st));
+            TRY(sgemm<false, true>(gshape(nt, F, K, de_t, K, Lr.mlp1_w, K), EpiGradAct{a1_t, F, t1_t, F, 0}, gctas,
+                                   st));
+            TRY(sgemm<false, true>(gshape(nt, 2 * F, F, h1_t, F, Lr.mlp2_w, F),
+                                   EpiBiasAct{Lr.mlp2_b, a2_t, 2 * F, h2_t, 2 * F, 1, nullptr}, gctas, st));
+            TRY(sgemm<false, true>(gshape(nt, 2 * F, F, t1_t, F, Lr.mlp2_w, F), EpiGradAct{a2_t, 2 * F, t2_t, 2 * F, 0},
+                                   gctas, st));
+            TRY(sgemm<false, true>(gshape(nt, 3 * F, 2 * F, h2_t, 2 * F, w3p(l), 2 * F),
+                                   EpiBiasAct{b3p(l), a3_t, 3 * F, tabv(1 + l), 3 * F, 1, phi_t}, gctas, st));
+            TRY(sgemm<false, true>(gshape(nt, 3 * F, 2 * F, t2_t, 2 * F, w3p(l), 2 * F),
+                                   EpiGradAct{a3_t, 3 * F, t3_t, 3 * F, 0}, gctas, st));
+            launch(k_tab_finish, grid_for((int64_t)nt * 3 * F, 256, sms), 256, 0, st, nt, 3 * F, a3_t, t3_t, phi_t,
+                   dphi_t, tabd(1 + l));
+            count_launch();
+            TNET_LAUNCH_CHECK();
+        }
+    }
+    ctx->tab_ready = 1;
+    return TNET_OK;
+}
+
 int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const int32_t *z,
                        const float *pos, const int32_t *batch, const float *box,
                        const int32_t *row_ptr_in, const int32_t *col, const float *seed,
@@ -1369,6 +1536,11 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     const tnet_model_desc &d = ctx->d;
     const Layout &Lw = ctx->lay;
     const int F = d.F, K = d.K, NL = d.L, H = F / 2;
+    // table mode: the radial functions are tabulated, which has no weight adjoint
+    const int nt = d.radial_table;
+    const bool tab = nt > 0;
+    if (tab && grad_w) return TNET_ERR_UNSUPPORTED;
+    const float th = tab ? ctx->rp.rc / (float)(nt - 1) : 0.f;
     const int sms = ctx->num_sms;
     const RadialParams rp = ctx->rp;
     const int gctas = sms * ctx->tune[T_GEMM_CTAS];
@@ -1459,7 +1631,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     const int64_t w3_per = 6LL * F * F + 3 * F;
     auto w3p = [&](int l) { return f32(Lw.w3p) + l * w3_per; };  // plane-major mlp3 weight
     auto b3p = [&](int l) { return f32(Lw.w3p) + l * w3_per + 6LL * F * F; };
-    if (NL > 0) {
+    if (NL > 0 && !tab) {
         FilterRows FR{};
         for (int l = 0; l < NL; ++l) { FR.w[l] = W.layer[l].mlp3_w; FR.b[l] = W.layer[l].mlp3_b; }
         launch(k_filter_rows, dim3(48, NL), 256, 0, st, FR, F, f32(Lw.w3p));
@@ -1511,19 +1683,22 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         emixT = job_classes_T(W.emb_mix_w);
         for (int l = 0; l < NL; ++l) {
             const LayerW &Lr = W.layer[l];
-            lb[l].mlp2 = job(Lr.mlp2_w, 2 * F, F, 0);
-            lb[l].mlp3 = job(w3p(l), 3 * F, 2 * F, 0);
-            lb[l].mlp2T = job(Lr.mlp2_w, 2 * F, F, 1);
-            lb[l].mlp3T = job(w3p(l), 3 * F, 2 * F, 1);
             lb[l].mix1 = job(Lr.mix1_w, 3 * F, F, 0);
             lb[l].mix1T = job_classes_T(Lr.mix1_w);
             lb[l].mix2 = job(Lr.mix2_w, 3 * F, F, 0);
             lb[l].mix2T = job_classes_T(Lr.mix2_w);
+            if (tab) continue;  // no per-pair radial MLP
+            lb[l].mlp2 = job(Lr.mlp2_w, 2 * F, F, 0);
+            lb[l].mlp3 = job(w3p(l), 3 * F, 2 * F, 0);
+            lb[l].mlp2T = job(Lr.mlp2_w, 2 * F, F, 1);
+            lb[l].mlp3T = job(w3p(l), 3 * F, 2 * F, 1);
             lb[l].mlp1 = job3(Lr.mlp1_w, F, K, 0);
             lb[l].mlp1T = job3(Lr.mlp1_w, F, K, 1);
         }
-        wx.dproj = job3(W.dproj_w, 3 * F, K, 0);
-        wx.dprojT = job3(W.dproj_w, 3 * F, K, 1);
+        if (!tab) {
+            wx.dproj = job3(W.dproj_w, 3 * F, K, 0);
+            wx.dprojT = job3(W.dproj_w, 3 * F, K, 1);
+        }
         if (atom_x3) {
             wx.emb_mlp1 = job3(W.emb_mlp1_w, 2 * F, F, 0);
             wx.emb_mlp1T = job3(W.emb_mlp1_w, 2 * F, F, 1);
@@ -1573,12 +1748,28 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     TNET_LAUNCH_CHECK();
     float *eu = f32(Lw.eu), *phiu = f32(Lw.phiu), *fu = f32(Lw.fu);
     float4 *geo = wsp<float4>(ctx, Lw.geo);
-    launch(k_edge_rbf, pair_grid, 256, 0, st, pos, box, batch, uij, nu, maxU, rp, eu, phiu, geo, eu_cp);
-    count_launch();
+    // table mode: function 0 is the projections f, function 1 + l layer l's
+    // filter g; each [n][3F] values followed by [n][3F] d-derivatives
+    auto tabv = [&](int j) { return f32(Lw.tab) + (int64_t)j * 2 * nt * 3 * F; };
+    auto tabd = [&](int j) { return tabv(j) + (int64_t)nt * 3 * F; };
+    float *dist = f32(Lw.dist), *dfu = f32(Lw.dfu);
+    if (tab) {
+        if (!ctx->tab_ready) return TNET_ERR_ARG;  // tnet_radial_tables not called
+        launch(k_pair_geo, grid_for(maxU, 256, sms), 256, 0, st, pos, box, batch, uij, nu, rp, phiu, geo, dist);
+        count_launch();
+    } else {
+        launch(k_edge_rbf, pair_grid, 256, 0, st, pos, box, batch, uij, nu, maxU, rp, eu, phiu, geo, eu_cp);
+        count_launch();
+    }
     launch(k_elem_tables, d.max_z, 256, sizeof(float) * F, st, W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
     count_launch();
     TNET_LAUNCH_CHECK();
-    {   // radial projections f^p = W^p e(d) + b^p, once per undirected pair
+    if (tab) {
+        launch(k_tab_eval, grid_for((int64_t)maxU * 3 * F, 256, sms), 256, 0, st, dist, nu, nt, th, 3 * F, tabv(0),
+               tabd(0), fu, dfu);
+        count_launch();
+        TNET_LAUNCH_CHECK();
+    } else {   // radial projections f^p = W^p e(d) + b^p, once per undirected pair
         // FP32 in both modes: K = num_rbf is small, and rounding the narrow
         // expnorm basis values to bf16 costs more force accuracy than any
         // other operand
@@ -1635,6 +1826,14 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         const LayerW &Lr = W.layer[l];
         float *a1 = act(Lw.a1, F, l), *h1 = act(Lw.h1, F, l), *a2 = act(Lw.a2, 2 * F, l),
               *h2 = act(Lw.h2, 2 * F, l), *a3 = act(Lw.a3, 3 * F, l), *gbuf = act(Lw.g, 3 * F, l);
+        if (tab) {  // g and dg/dd (in the a3 slab) from the table
+            pf.mark(P_MLP1);
+            launch(k_tab_eval, grid_for((int64_t)maxU * 3 * F, 256, sms), 256, 0, st, dist, nu, nt, th, 3 * F,
+                   tabv(1 + l), tabd(1 + l), gbuf, a3);
+            count_launch();
+            TNET_LAUNCH_CHECK();
+            return TNET_OK;
+        }
         const EpiBiasAct e1{Lr.mlp1_b, a1, F, keep_h ? h1 : nullptr, F, 1, nullptr, h1_cp(l), F};
         const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, keep_h ? h2 : nullptr, 2 * F, 1, nullptr, h2_cp(l), 2 * F};
         const EpiBiasAct e3{b3p(l), a3, 3 * F, gbuf, 3 * F, 1, phiu};
@@ -1758,7 +1957,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
                          st));
         TRY(wgrad_layernorm(ghn, h, lno, N, 3 * F, wpart, wcap, gw(G.out_ln_g), sms, st));
     }
-    if (NL > 0) TNET_CUDA_TRY(cudaMemsetAsync(gphiu, 0, sizeof(float) * maxU, st));
+    // gphiu collects dE/dphi per pair (or, in table mode, dE/dd)
+    if (NL > 0 || tab) TNET_CUDA_TRY(cudaMemsetAsync(gphiu, 0, sizeof(float) * maxU, st));
     for (int l = NL - 1; l >= 0; --l) {
         const LayerW &Lr = W.layer[l];
         const LayerW &Gr = G.layer[l];
@@ -1785,12 +1985,30 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         // and 3xTF32 GEMMs and the weight gradients)
         float *ga3_out = (prec != 1 || wg) ? gg : nullptr;
 #define MSG_BWD(FF)                                                                                          \
-    launch(k_message_bwd<FF>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu, N, gY, nbf, \
-                                                  ga3_out, ga3_cp, gphiu)
-        TNET_F_SWITCH(F, MSG_BWD);
+    launch(k_message_bwd<FF, false>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu, N, gY, \
+                                                         nbf, ga3_out, ga3_cp, gphiu)
+#define MSG_BWD_TAB(FF)                                                                                      \
+    launch(k_message_bwd<FF, true>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu, N, gY, \
+                                                        nbf, nullptr, none, gphiu)
+        if (tab) {
+            TNET_F_SWITCH(F, MSG_BWD_TAB);
+        } else {
+            TNET_F_SWITCH(F, MSG_BWD);
+        }
 #undef MSG_BWD
+#undef MSG_BWD_TAB
         count_launch();
         TNET_LAUNCH_CHECK();
+        if (tab) {  // no radial MLP to go back through
+            pf.mark(P_NODE_BWD);
+            if (tcm)
+                TRY(tcg(tc::tshape_classes(N, F), gY, nbf, 9LL * N, F, lb[l].mix1T, 3 * F, F, EpiStore{gX, F, 1}));
+            else TRY(sgemm<false, false>(gshape_classes(N, F, gY, Lr.mix1_w), EpiStore{gX, F, 1}, gctas, st));
+            launch(k_node_norm_bwd, ew, 256, 0, st, Xl, qn, N, F, gX);
+            count_launch();
+            TNET_LAUNCH_CHECK();
+            continue;
+        }
         const EpiGradAct g3{a2, 2 * F, ga2, 2 * F, 0, ga2_cp, 2 * F};
         const EpiGradAct g2{a1, F, ga1, F, 0, ga1_cp, F};
         const EpiStore g1{ge, K, l != NL - 1};
@@ -1884,7 +2102,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
                                                    fu, Ta, Tb, gXraw, 1, gfu, edge_g, gA, gB, gfu_cp);        \
     else                                                                                                     \
         launch(k_emb_bwd_pairs<CPL>, pair_grid, 256, 0, st, geo, z, uij, ue, rev, nu, N, d.max_z, fu, Ta, Tb, gXraw, \
-                                                      gfu, edge_g, gfu_cp)
+                                                      tab ? nullptr : gfu, edge_g, gfu_cp, tab ? dfu : nullptr,     \
+                                                      gphiu)
     switch (F / 32) {
         case 2: EMB_BWD(2); break;
         case 4: EMB_BWD(4); break;
@@ -1899,7 +2118,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
 #undef EMB_BWD
     count_launch();
     TNET_LAUNCH_CHECK();
-    {   // dE/de of the pair's radial basis also flows through the projections
+    if (!tab) {   // dE/de of the pair's radial basis also flows through the projections
         if (tcm) {
             tc::TcShape tg = tc::tshape(maxU, K, 3 * F);
             tg.rows_dev = nu;
@@ -1927,8 +2146,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     }
     if (!forces) return TNET_OK;
     pf.mark(P_FORCES);
-    launch(k_pair_vec, pair_grid, 256, 0, st, pos, box, batch, uij, ue, rev, nu, rp, ge, NL > 0 ? gphiu : nullptr, edge_g,
-                                        Gp);
+    launch(k_pair_vec, pair_grid, 256, 0, st, pos, box, batch, uij, ue, rev, nu, rp, tab ? nullptr : ge,
+           (NL > 0 && !tab) ? gphiu : nullptr, edge_g, tab ? gphiu : nullptr, Gp);
     count_launch();
     launch(k_forces, (N + 127) / 128, 128, 0, st, row_ptr, col, pair_of, Gp, N, forces);
     count_launch();

@@ -73,14 +73,15 @@ class TensorNet:
 
     def __init__(self, weights: dict, F=128, K=32, L=2, max_z=100, cutoff_upper=5.0, cutoff_lower=0.0,
                  max_atoms=1024, max_systems=1, max_pairs=65536, precision=0, device="cuda",
-                 recompute_edges=False):
+                 recompute_edges=False, radial_table=0):
         self.lib = _lib.load()
         self.device = torch.device(device)
         if self.device.type != "cuda":
             raise RuntimeError("libtnet runs on CUDA devices only")
         self.F, self.K, self.L, self.max_z = F, K, L, max_z
         self.cutoff = float(cutoff_upper)
-        self.desc = _lib.ModelDesc(F, K, L, max_z, cutoff_upper, cutoff_lower, precision, int(bool(recompute_edges)))
+        self.desc = _lib.ModelDesc(F, K, L, max_z, cutoff_upper, cutoff_lower, precision, int(bool(recompute_edges)),
+                                   int(radial_table))
         self.max_atoms, self.max_systems, self.max_pairs = int(max_atoms), int(max_systems), int(max_pairs)
         nbytes = self.lib.tnet_workspace_bytes(ctypes.byref(self.desc), self.max_atoms, self.max_systems,
                                                self.max_pairs)
@@ -112,6 +113,9 @@ class TensorNet:
         if w.numel() != self.n_weights:
             raise ValueError("weight blob size mismatch")
         self.weights = w
+        if self.desc.radial_table > 0:   # tabulate the radial functions of these weights
+            _lib.check(self.lib.tnet_radial_tables(self.ctx, _p(self.weights), _stream(self.device)),
+                       "tnet_radial_tables")
 
     # -------------------------------------------------------------- tuning
     def get_tuning(self) -> list[int]:

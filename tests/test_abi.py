@@ -98,3 +98,20 @@ def test_tuning_knobs_exported(lib):
         assert name and len(cands) >= 2 and all(c >= 0 for c in cands) and len(set(cands)) == len(cands)
     assert lib.tnet_tuning_name(99) is None
     assert lib.tnet_set_tuning(None, None, 0) == 1
+
+
+def test_radial_table_workspace(lib):
+    """Table mode keeps the tables (2 (L+1) n 3F floats) and per-pair f, g and
+    their d-derivatives, but none of the per-pair radial-MLP activations."""
+    plain = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0, 0, 0)
+    tab = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0, 0, 4096)
+    a = lib.tnet_workspace_bytes(ctypes.byref(plain), 3000, 1, 160000)
+    b = lib.tnet_workspace_bytes(ctypes.byref(tab), 3000, 1, 160000)
+    assert 0 < b < a
+    for n in (1, 255, 65537, -4):
+        bad = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0, 0, n)
+        assert lib.tnet_workspace_bytes(ctypes.byref(bad), 3000, 1, 160000) == -1
+    for n in (256, 65536):
+        ok = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0, 0, n)
+        assert lib.tnet_workspace_bytes(ctypes.byref(ok), 3000, 1, 160000) > 0
+    assert lib.tnet_radial_tables(None, None, None) == 1
