@@ -64,12 +64,12 @@ typedef struct tnet_ctx tnet_ctx;
  * workspace holds one layer's worth (for systems whose pair count presses on
  * memory).  Results are bitwise identical either way.
  * radial_table: 0 = the radial MLP and the radial projections run per pair;
- * n in [256, 65536] = both are functions of the pair distance alone, so each
- * call tabulates them (values and exact d-derivatives, FP32) at n points on
- * [0, cutoff_upper] and evaluates them per pair by cubic Hermite
- * interpolation; forces are the exact derivatives of the interpolated energy.
- * The tables are built by tnet_radial_tables.  An inference mode: weight
- * gradients return UNSUPPORTED. */
+ * n in [256, 16384] = both are functions of the pair distance alone, so they
+ * are tabulated (FP64 values and d-derivatives, stored as FP32 cubic Hermite
+ * coefficients per interval) at n points on [0, cutoff_upper] and
+ * interpolated per pair; forces are the derivatives of the interpolated
+ * energy.  The tables are built by tnet_radial_tables.  An inference mode:
+ * weight gradients return UNSUPPORTED. */
 typedef struct {
     int F, K, L, max_z;
     float cutoff_upper, cutoff_lower;
@@ -191,8 +191,10 @@ int tnet_energy_forces(tnet_ctx *ctx, const float *weights, int n_atoms, int n_s
  * expnorm basis, the cosine cutoff and the radial MLP) depend on the pair
  * distance and the weights alone.  This call evaluates them, with their
  * d-derivatives, from `weights` at the n points d_k = k cutoff_upper/(n-1),
- * FP32, into the context's workspace; tnet_energy_forces and tnet_md_step
- * then interpolate them and do not read the radial weights.  Call it again
+ * in FP64, and stores each interval's cubic Hermite polynomial (coefficients
+ * formed in FP64, kept as FP32) in the context's workspace;
+ * tnet_energy_forces and tnet_md_step then interpolate them and do not read
+ * the radial weights.  Call it again
  * whenever those weights change.  Before the first call, tnet_energy_forces
  * and tnet_md_step of a table-mode context return TNET_ERR_ARG.  Stream
  * ordered (the tables are ready for work enqueued after it on `stream`);

@@ -18,7 +18,7 @@ int validate_desc(const tnet_model_desc *d) {
     if (!(d->cutoff_upper > d->cutoff_lower) || d->cutoff_lower < 0.f) return TNET_ERR_ARG;
     if (d->precision < 0 || d->precision > 2) return TNET_ERR_ARG;
     if (d->recompute_edges < 0 || d->recompute_edges > 1) return TNET_ERR_ARG;
-    if (d->radial_table != 0 && (d->radial_table < 256 || d->radial_table > 65536)) return TNET_ERR_ARG;
+    if (d->radial_table != 0 && (d->radial_table < 256 || d->radial_table > 16384)) return TNET_ERR_ARG;
     return TNET_OK;
 }
 
@@ -138,11 +138,11 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->wpart_floats = 4LL << 20;
     L->wpart = take(f * L->wpart_floats);
     L->w3p = take(f * (NL > 0 ? NL : 1) * (6LL * F * F + 3 * F));
-    // tabulated radial functions (radial_table = n > 0): value and derivative
-    // tables [n][3F] of the projections f and of each layer's filter g, the
+    // tabulated radial functions (radial_table = n > 0): Hermite coefficients
+    // [n-1][4][3F] of the projections f and of each layer's filter g, the FP64
     // scratch of their construction, the per-pair distance and df/dd
-    L->tab = take(f * (nt > 0 ? (NL + 1) * 2 * nt * 3 * F : 0));
-    L->tab_tmp = take(f * (nt > 0 ? nt * (2 * K + 2 + 3 * F + 3 * 2 * F + 2 * 3 * F) : 0));
+    L->tab = take(f * (nt > 0 ? (NL + 1) * (nt - 1) * 4 * 3 * F : 0));
+    L->tab_tmp = take(8 * (nt > 0 ? nt * (2 * K + 2 + 12 * F) : 0));
     L->dist = take(f * (nt > 0 ? U : 0));
     L->dfu = take(f * (nt > 0 ? U * 3 * F : 0));
     // tensor-core modes: weight operands (bf16 forward + transposed copies,

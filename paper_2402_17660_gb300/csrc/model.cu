@@ -244,24 +244,41 @@ __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restric
 
 // ------------------------------------------------ tabulated radial functions ---
 // The radial projections f(d) and every layer's filter g(d) depend on the pair
-// distance alone.  In table mode they are evaluated, with their d-derivatives,
-// at the grid d_k = k h (k < n, h = rc/(n - 1)) and interpolated per pair by
-// cubic Hermite polynomials on [d_k, d_k+1].
+// distance alone.  In table mode they are evaluated in FP64, with their
+// d-derivatives (forward mode through the same layers), at the grid d_k = k h
+// (k < n, h = rc/(n - 1)).  Each interval [d_k, d_k+1] stores the cubic
+// Hermite polynomial p(s) = c0 + c1 s + c2 s^2 + c3 s^3, s = (d - d_k)/h, whose
+// coefficients are formed in FP64 before rounding to FP32: the derivative
+// p'(s)/h then carries no cancellation between neighbouring table values, and
+// the forces are the derivatives of the interpolated energy.
 
-// basis e_q(d_k), de_q/dd, phi(d_k), dphi/dd at every grid point
-__global__ void k_tab_rbf(int n, float h, RadialParams rp, float *__restrict__ e, float *__restrict__ de,
-                          float *__restrict__ phi, float *__restrict__ dphi) {
+struct RadialParams64 {
+    double rc, rl, alpha, beta, mu0, dmu;
+    int K;
+};
+
+__device__ __forceinline__ void silu64(double a, double &v, double &g) {
+    const double sg = 1.0 / (1.0 + exp(-a));
+    v = a * sg;
+    g = sg * (1.0 + a * (1.0 - sg));
+}
+
+// basis e_q(d_k) (the cosine cutoff included), de_q/dd, phi(d_k), dphi/dd
+__global__ void k_tab_rbf(int n, double h, RadialParams64 rp, double *__restrict__ e, double *__restrict__ de,
+                          double *__restrict__ phi, double *__restrict__ dphi) {
     pdl_entry();
     const int K = rp.K;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * K;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(t / K), q = (int)(t % K);
-        const float d = k * h;
-        const float ph = cutoff_phi(d, rp), dph = cutoff_dphi(d, rp);
-        float ev, dev;
-        expnorm_k(d, q, rp, ph, dph, ev, dev);
-        e[t] = ev;
-        de[t] = dev;
+        const double d = k * h;
+        const double ph = d < rp.rc ? 0.5 * (cospi(d / rp.rc) + 1.0) : 0.0;
+        const double dph = d < rp.rc ? -0.5 * 3.141592653589793 / rp.rc * sinpi(d / rp.rc) : 0.0;
+        const double ex = exp(rp.alpha * (rp.rl - d));
+        const double u = ex - (rp.mu0 + q * rp.dmu);
+        const double rho = exp(-rp.beta * u * u);
+        e[t] = ph * rho;
+        de[t] = dph * rho + ph * rho * (2.0 * rp.beta * u * rp.alpha * ex);
         if (q == 0) {
             phi[k] = ph;
             dphi[k] = dph;
@@ -269,15 +286,100 @@ __global__ void k_tab_rbf(int n, float h, RadialParams rp, float *__restrict__ e
     }
 }
 
-// g = phi silu(a3) (already in g); dg/dd = dphi silu(a3) + phi t3, where t3 is
-// the tangent of a3 (forward-mode derivative through the MLP)
-__global__ void k_tab_finish(int n, int W, const float *__restrict__ a3, const float *__restrict__ t3,
-                             const float *__restrict__ phi, const float *__restrict__ dphi, float *__restrict__ dg) {
+// One dense layer of the radial chain at the grid points, FP64, with its
+// tangent: a = x W^T + b, ta = tx W^T, and
+//   mode 0 (hidden layers): y = silu(a),       ty = silu'(a) ta
+//   mode 1 (projections f): y = a,             ty = ta
+//   mode 2 (filters g):     y = phi silu(a),   ty = dphi silu(a) + phi silu'(a) ta
+// 64 x 64 output tiles, 256 threads with 4 x 4 outputs (and tangents) each.
+__global__ void __launch_bounds__(256)
+    k_tab_layer(int n, int Nout, int Kin, const double *__restrict__ x, const double *__restrict__ tx,
+                const float *__restrict__ Wt, const float *__restrict__ b, int mode, const double *__restrict__ phi,
+                const double *__restrict__ dphi, double *__restrict__ y, double *__restrict__ ty) {
     pdl_entry();
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)n * W;
+    constexpr int T = 64, BK = 16;
+    __shared__ double xs[BK][T], ts[BK][T], ws[BK][T];
+    const int tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
+    const int m0 = blockIdx.y * T, n0 = blockIdx.x * T;
+    double acc[4][4], tac[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = tac[i][j] = 0.0;
+    for (int k0 = 0; k0 < Kin; k0 += BK) {
+        for (int i = tid; i < BK * T; i += blockDim.x) {
+            const int r = i / BK, kk = i % BK, gk = k0 + kk;
+            const int gm = m0 + r, gn = n0 + r;
+            const bool okx = gm < n && gk < Kin, okw = gn < Nout && gk < Kin;
+            xs[kk][r] = okx ? x[(int64_t)gm * Kin + gk] : 0.0;
+            ts[kk][r] = okx ? tx[(int64_t)gm * Kin + gk] : 0.0;
+            ws[kk][r] = okw ? (double)Wt[(int64_t)gn * Kin + gk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < BK; ++kk) {
+            double xv[4], tv[4], wv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                xv[i] = xs[kk][tr * 4 + i];
+                tv[i] = ts[kk][tr * 4 + i];
+                wv[i] = ws[kk][tc * 4 + i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j] = fma(xv[i], wv[j], acc[i][j]);
+                    tac[i][j] = fma(tv[i], wv[j], tac[i][j]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + tr * 4 + i;
+        if (gm >= n) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + tc * 4 + j;
+            if (gn >= Nout) continue;
+            const double a = acc[i][j] + (double)b[gn], ta = tac[i][j];
+            double v, g, out, tout;
+            if (mode == 1) {
+                out = a;
+                tout = ta;
+            } else {
+                silu64(a, v, g);
+                if (mode == 0) {
+                    out = v;
+                    tout = g * ta;
+                } else {
+                    out = phi[gm] * v;
+                    tout = dphi[gm] * v + phi[gm] * g * ta;
+                }
+            }
+            y[(int64_t)gm * Nout + gn] = out;
+            ty[(int64_t)gm * Nout + gn] = tout;
+        }
+    }
+}
+
+// Hermite coefficients of each interval, [n-1][4][W]:
+//   c0 = v0, c1 = h v0', c2 = 3 (v1 - v0) - 2 h v0' - h v1', c3 = 2 (v0 - v1) + h v0' + h v1'
+__global__ void k_tab_coef(int n, int W, double h, const double *__restrict__ v, const double *__restrict__ dv,
+                           float *__restrict__ coef) {
+    pdl_entry();
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)(n - 1) * W;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(t / W);
-        dg[t] = dphi[k] * silu_f(a3[t]) + phi[k] * t3[t];
+        const int64_t k = t / W;
+        const int w = (int)(t % W);
+        const double v0 = v[k * W + w], v1 = v[(k + 1) * W + w];
+        const double d0 = h * dv[k * W + w], d1 = h * dv[(k + 1) * W + w];
+        float *c = coef + k * 4 * W + w;
+        c[0] = (float)v0;
+        c[W] = (float)d0;
+        c[2 * W] = (float)(3.0 * (v1 - v0) - 2.0 * d0 - d1);
+        c[3 * W] = (float)(2.0 * (v0 - v1) + d0 + d1);
     }
 }
 
@@ -301,12 +403,11 @@ __global__ void k_pair_geo(const float *__restrict__ pos, const float *__restric
     }
 }
 
-// out_v[u][w], out_d[u][w]: the cubic Hermite interpolant of a tabulated
-// function (values tv, derivatives td, [n][W] on the grid k h) and its
-// derivative at d_u
+// out_v[u][w] = p(s), out_d[u][w] = p'(s)/h of the interval holding d_u
+// (coefficients [n-1][4][W], grid k h)
 __global__ void k_tab_eval(const float *__restrict__ dist, const int32_t *__restrict__ nu, int n, float h,
-                           int W, const float *__restrict__ tv, const float *__restrict__ td,
-                           float *__restrict__ out_v, float *__restrict__ out_d) {
+                           int W, const float *__restrict__ coef, float *__restrict__ out_v,
+                           float *__restrict__ out_d) {
     pdl_entry();
     const int U = *nu;
     const float inv_h = 1.0f / h;
@@ -318,13 +419,10 @@ __global__ void k_tab_eval(const float *__restrict__ dist, const int32_t *__rest
         int k = (int)floorf(x);
         k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
         const float s = x - (float)k;
-        const int64_t o = (int64_t)k * W + w;
-        const float v0 = tv[o], v1 = tv[o + W], d0 = td[o] * h, d1 = td[o + W] * h;
-        const float s2 = s * s, s3 = s2 * s;
-        out_v[t] = (2.f * s3 - 3.f * s2 + 1.f) * v0 + (s3 - 2.f * s2 + s) * d0 + (3.f * s2 - 2.f * s3) * v1 +
-                   (s3 - s2) * d1;
-        out_d[t] = ((6.f * s2 - 6.f * s) * (v0 - v1) + (3.f * s2 - 4.f * s + 1.f) * d0 + (3.f * s2 - 2.f * s) * d1) *
-                   inv_h;
+        const float *c = coef + (int64_t)k * 4 * W + w;
+        const float c0 = c[0], c1 = c[W], c2 = c[2 * W], c3 = c[3 * W];
+        out_v[t] = fmaf(s, fmaf(s, fmaf(s, c3, c2), c1), c0);
+        out_d[t] = fmaf(s, fmaf(s, 3.f * c3, 2.f * c2), c1) * inv_h;
     }
 }
 
@@ -1462,25 +1560,26 @@ __global__ void k_rows_in_range(const int32_t *__restrict__ row_ptr, int N, int6
 }
 
 // Radial-function tables (radial_table = n > 0): the projections f (table 0)
-// and each layer's filter g (table 1 + l), [n][3F] values followed by [n][3F]
-// d-derivatives on the grid d_k = k h, h = rc/(n - 1).  f, g are functions of
+// and each layer's filter g (table 1 + l) as [n-1][4][3F] Hermite
+// coefficients on the grid d_k = k h, h = rc/(n - 1).  f, g are functions of
 // the pair distance alone (the expnorm basis, the cosine cutoff and the radial
-// MLP of TensorNet Sec. 2.1.1); their derivatives come from a forward-mode
-// pass through the same layers.
+// MLP of TensorNet Sec. 2.1.1); the chain runs in FP64 on the values and
+// their d-derivatives.
 int radial_tables_impl(tnet_ctx *ctx, const float *wblob, cudaStream_t st) {
     const tnet_model_desc &d = ctx->d;
     const Layout &Lw = ctx->lay;
     const int F = d.F, K = d.K, NL = d.L, nt = d.radial_table;
     const int sms = ctx->num_sms;
-    const RadialParams rp = ctx->rp;
-    const int gctas = sms * ctx->tune[T_GEMM_CTAS];
     if (nt <= 0) return TNET_ERR_ARG;
     Weights W;
     weight_offsets(&d, wblob, &W);
     auto f32 = [&](size_t off) { return wsp<float>(ctx, off); };
-    const float th = rp.rc / (float)(nt - 1);
-    auto tabv = [&](int j) { return f32(Lw.tab) + (int64_t)j * 2 * nt * 3 * F; };
-    auto tabd = [&](int j) { return tabv(j) + (int64_t)nt * 3 * F; };
+    const double rc = d.cutoff_upper, rl = d.cutoff_lower;
+    RadialParams64 rp{rc, rl, 5.0 / (rc - rl), pow((2.0 / K) * (1.0 - exp(-(rc - rl))), -2.0), exp(-(rc - rl)),
+                      (1.0 - exp(-(rc - rl))) / (K - 1), K};
+    const double h = rc / (nt - 1);
+    const int64_t per_fn = (int64_t)(nt - 1) * 4 * 3 * F;
+    auto coef = [&](int j) { return f32(Lw.tab) + j * per_fn; };
     const int64_t w3_per = 6LL * F * F + 3 * F;
     auto w3p = [&](int l) { return f32(Lw.w3p) + l * w3_per; };
     auto b3p = [&](int l) { return f32(Lw.w3p) + l * w3_per + 6LL * F * F; };
@@ -1491,39 +1590,33 @@ int radial_tables_impl(tnet_ctx *ctx, const float *wblob, cudaStream_t st) {
         count_launch();
         TNET_LAUNCH_CHECK();
     }
-    {
-        // value and forward-mode derivative of each radial function at the grid
-        // points: the MLP chains run on (e, de/dd), FP32 in every mode
-        float *e_t = f32(Lw.tab_tmp), *de_t = e_t + (int64_t)nt * K, *phi_t = de_t + (int64_t)nt * K,
-              *dphi_t = phi_t + nt, *a1_t = dphi_t + nt, *h1_t = a1_t + (int64_t)nt * F, *t1_t = h1_t + (int64_t)nt * F,
-              *a2_t = t1_t + (int64_t)nt * F, *h2_t = a2_t + (int64_t)nt * 2 * F, *t2_t = h2_t + (int64_t)nt * 2 * F,
-              *a3_t = t2_t + (int64_t)nt * 2 * F, *t3_t = a3_t + (int64_t)nt * 3 * F;
-        launch(k_tab_rbf, grid_for((int64_t)nt * K, 256, sms), 256, 0, st, nt, th, rp, e_t, de_t, phi_t, dphi_t);
+    double *e_t = wsp<double>(ctx, Lw.tab_tmp), *de_t = e_t + (int64_t)nt * K, *phi_t = de_t + (int64_t)nt * K,
+           *dphi_t = phi_t + nt, *h1_t = dphi_t + nt, *t1_t = h1_t + (int64_t)nt * F, *h2_t = t1_t + (int64_t)nt * F,
+           *t2_t = h2_t + (int64_t)nt * 2 * F, *v_t = t2_t + (int64_t)nt * 2 * F, *dv_t = v_t + (int64_t)nt * 3 * F;
+    launch(k_tab_rbf, grid_for((int64_t)nt * K, 256, sms), 256, 0, st, nt, h, rp, e_t, de_t, phi_t, dphi_t);
+    count_launch();
+    TNET_LAUNCH_CHECK();
+    auto layer = [&](int Nout, int Kin, const double *x, const double *tx, const float *w, const float *b, int mode,
+                     double *y, double *ty) {
+        launch(k_tab_layer, dim3((Nout + 63) / 64, (nt + 63) / 64), 256, 0, st, nt, Nout, Kin, x, tx, w, b, mode,
+               phi_t, dphi_t, y, ty);
         count_launch();
-        TNET_LAUNCH_CHECK();
-        TRY(sgemm<false, true>(gshape(nt, 3 * F, K, e_t, K, W.dproj_w, K),
-                               EpiBiasAct{W.dproj_b, nullptr, 0, tabv(0), 3 * F, 0, nullptr}, gctas, st));
-        TRY(sgemm<false, true>(gshape(nt, 3 * F, K, de_t, K, W.dproj_w, K), EpiStore{tabd(0), 3 * F, 0}, gctas, st));
-        for (int l = 0; l < NL; ++l) {
-            const LayerW &Lr = W.layer[l];
-            TRY(sgemm<false, true>(gshape(nt, F, K, e_t, K, Lr.mlp1_w, K),
-                                   EpiBiasAct{Lr.mlp1_b, a1_t, F, h1_t, F, 1, nullptr}, gctas, st));
-            TRY(sgemm<false, true>(gshape(nt, F, K, de_t, K, Lr.mlp1_w, K), EpiGradAct{a1_t, F, t1_t, F, 0}, gctas,
-                                   st));
-            TRY(sgemm<false, true>(gshape(nt, 2 * F, F, h1_t, F, Lr.mlp2_w, F),
-                                   EpiBiasAct{Lr.mlp2_b, a2_t, 2 * F, h2_t, 2 * F, 1, nullptr}, gctas, st));
-            TRY(sgemm<false, true>(gshape(nt, 2 * F, F, t1_t, F, Lr.mlp2_w, F), EpiGradAct{a2_t, 2 * F, t2_t, 2 * F, 0},
-                                   gctas, st));
-            TRY(sgemm<false, true>(gshape(nt, 3 * F, 2 * F, h2_t, 2 * F, w3p(l), 2 * F),
-                                   EpiBiasAct{b3p(l), a3_t, 3 * F, tabv(1 + l), 3 * F, 1, phi_t}, gctas, st));
-            TRY(sgemm<false, true>(gshape(nt, 3 * F, 2 * F, t2_t, 2 * F, w3p(l), 2 * F),
-                                   EpiGradAct{a3_t, 3 * F, t3_t, 3 * F, 0}, gctas, st));
-            launch(k_tab_finish, grid_for((int64_t)nt * 3 * F, 256, sms), 256, 0, st, nt, 3 * F, a3_t, t3_t, phi_t,
-                   dphi_t, tabd(1 + l));
-            count_launch();
-            TNET_LAUNCH_CHECK();
-        }
+    };
+    auto finish = [&](int j) {
+        launch(k_tab_coef, grid_for((int64_t)(nt - 1) * 3 * F, 256, sms), 256, 0, st, nt, 3 * F, h, v_t, dv_t,
+               coef(j));
+        count_launch();
+    };
+    layer(3 * F, K, e_t, de_t, W.dproj_w, W.dproj_b, 1, v_t, dv_t);
+    finish(0);
+    for (int l = 0; l < NL; ++l) {
+        const LayerW &Lr = W.layer[l];
+        layer(F, K, e_t, de_t, Lr.mlp1_w, Lr.mlp1_b, 0, h1_t, t1_t);
+        layer(2 * F, F, h1_t, t1_t, Lr.mlp2_w, Lr.mlp2_b, 0, h2_t, t2_t);
+        layer(3 * F, 2 * F, h2_t, t2_t, w3p(l), b3p(l), 2, v_t, dv_t);
+        finish(1 + l);
     }
+    TNET_LAUNCH_CHECK();
     ctx->tab_ready = 1;
     return TNET_OK;
 }
@@ -1750,8 +1843,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     float4 *geo = wsp<float4>(ctx, Lw.geo);
     // table mode: function 0 is the projections f, function 1 + l layer l's
     // filter g; each [n][3F] values followed by [n][3F] d-derivatives
-    auto tabv = [&](int j) { return f32(Lw.tab) + (int64_t)j * 2 * nt * 3 * F; };
-    auto tabd = [&](int j) { return tabv(j) + (int64_t)nt * 3 * F; };
+    auto coef = [&](int j) { return f32(Lw.tab) + (int64_t)j * (nt - 1) * 4 * 3 * F; };
     float *dist = f32(Lw.dist), *dfu = f32(Lw.dfu);
     if (tab) {
         if (!ctx->tab_ready) return TNET_ERR_ARG;  // tnet_radial_tables not called
@@ -1765,8 +1857,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     count_launch();
     TNET_LAUNCH_CHECK();
     if (tab) {
-        launch(k_tab_eval, grid_for((int64_t)maxU * 3 * F, 256, sms), 256, 0, st, dist, nu, nt, th, 3 * F, tabv(0),
-               tabd(0), fu, dfu);
+        launch(k_tab_eval, grid_for((int64_t)maxU * 3 * F, 256, sms), 256, 0, st, dist, nu, nt, th, 3 * F, coef(0),
+               fu, dfu);
         count_launch();
         TNET_LAUNCH_CHECK();
     } else {   // radial projections f^p = W^p e(d) + b^p, once per undirected pair
@@ -1829,7 +1921,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         if (tab) {  // g and dg/dd (in the a3 slab) from the table
             pf.mark(P_MLP1);
             launch(k_tab_eval, grid_for((int64_t)maxU * 3 * F, 256, sms), 256, 0, st, dist, nu, nt, th, 3 * F,
-                   tabv(1 + l), tabd(1 + l), gbuf, a3);
+                   coef(1 + l), gbuf, a3);
             count_launch();
             TNET_LAUNCH_CHECK();
             return TNET_OK;
