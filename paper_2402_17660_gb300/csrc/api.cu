@@ -88,20 +88,21 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->at = take(f * N * F / 2);
     L->t = take(f * N * F / 2);
     L->Ei = take(f * N);
-    // edge MLP (table mode keeps only g, dg/dd in the a3 slab, and f)
+    // edge MLP (none of it in table mode: the consumers evaluate the tables)
     const int64_t nt = d->radial_table;
     const int64_t rm = nt > 0 ? 0 : 1;  // the per-pair radial MLP runs
     L->eu = take(f * U * K * rm);
     L->phiu = take(f * U);
     L->geo = take(16 * U);
-    // (one set per layer, which the reverse pass reads, unless it recomputes them)
+    // (one set per layer, which the reverse pass reads, unless it recomputes
+    // them; none in table mode, where the message kernels evaluate the tables)
     const int64_t NLm = (NL > 0 && !d->recompute_edges) ? NL : 1;
     L->a1 = take(f * U * F * NLm * rm);
     L->h1 = take(f * U * F * NLm * rm);
     L->a2 = take(f * U * 2 * F * NLm * rm);
     L->h2 = take(f * U * 2 * F * NLm * rm);
-    L->a3 = take(f * U * 3 * F * NLm);
-    L->g = take(f * U * 3 * F * NLm);
+    L->a3 = take(f * U * 3 * F * NLm * rm);
+    L->g = take(f * U * 3 * F * NLm * rm);
     // reverse pass
     L->gXa = take(f * n9);
     L->gXb = take(f * n9);
@@ -124,7 +125,7 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->ge = take(f * U * K * rm);
     L->gphiu = take(f * U);
     L->gvec = take(f * 3 * E);
-    L->fu = take(f * U * 3 * F);
+    L->fu = take(f * U * 3 * F * rm);
     L->gfu = take(f * U * 3 * F * rm);
     L->ue = take(i * U);
     L->edge_g = take(16 * E);
@@ -139,12 +140,11 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->wpart = take(f * L->wpart_floats);
     L->w3p = take(f * (NL > 0 ? NL : 1) * (6LL * F * F + 3 * F));
     // tabulated radial functions (radial_table = n > 0): Hermite coefficients
-    // [n-1][4][3F] of the projections f and of each layer's filter g, the FP64
-    // scratch of their construction, the per-pair distance and df/dd
+    // [n-1][3F] float4 of the projections f and of each layer's filter g, the
+    // FP64 scratch of their construction and the per-pair distance
     L->tab = take(f * (nt > 0 ? (NL + 1) * (nt - 1) * 4 * 3 * F : 0));
     L->tab_tmp = take(8 * (nt > 0 ? nt * (2 * K + 2 + 12 * F) : 0));
     L->dist = take(f * (nt > 0 ? U : 0));
-    L->dfu = take(f * (nt > 0 ? U * 3 * F : 0));
     // tensor-core modes: weight operands (bf16 forward + transposed copies,
     // or fp32 TF32 residuals + transposed high parts; the 3xTF32 GEMMs of the
     // BF16 mode use the latter), and in BF16 mode the bf16 copies of the node

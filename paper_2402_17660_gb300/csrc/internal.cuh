@@ -369,7 +369,7 @@ struct Layout {
     // with rows in plane-major order p*F + c (the blob keeps c*3 + p)
     size_t w3p;
     // tabulated radial functions (radial_table > 0)
-    size_t tab, tab_tmp, dist, dfu;
+    size_t tab, tab_tmp, dist;
     int64_t wpart_floats, zsplits;
     // MD
     size_t md_row_ptr, md_col, md_npairs, md_forces, md_energy, md_pos_ref, md_step, md_need, md_rebuilds;

@@ -364,10 +364,10 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Hermite coefficients of each interval, [n-1][4][W]:
+// Hermite coefficients of each interval, [n-1][W] float4 (c0, c1, c2, c3):
 //   c0 = v0, c1 = h v0', c2 = 3 (v1 - v0) - 2 h v0' - h v1', c3 = 2 (v0 - v1) + h v0' + h v1'
 __global__ void k_tab_coef(int n, int W, double h, const double *__restrict__ v, const double *__restrict__ dv,
-                           float *__restrict__ coef) {
+                           float4 *__restrict__ coef) {
     pdl_entry();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)(n - 1) * W;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -375,12 +375,32 @@ __global__ void k_tab_coef(int n, int W, double h, const double *__restrict__ v,
         const int w = (int)(t % W);
         const double v0 = v[k * W + w], v1 = v[(k + 1) * W + w];
         const double d0 = h * dv[k * W + w], d1 = h * dv[(k + 1) * W + w];
-        float *c = coef + k * 4 * W + w;
-        c[0] = (float)v0;
-        c[W] = (float)d0;
-        c[2 * W] = (float)(3.0 * (v1 - v0) - 2.0 * d0 - d1);
-        c[3 * W] = (float)(2.0 * (v0 - v1) + d0 + d1);
+        coef[k * W + w] = make_float4((float)v0, (float)d0, (float)(3.0 * (v1 - v0) - 2.0 * d0 - d1),
+                                      (float)(2.0 * (v0 - v1) + d0 + d1));
     }
+}
+
+// A table-mode view of one radial function: the consumers (embedding,
+// messages and their adjoints) evaluate p(s) and p'(s)/h of the pair's
+// interval themselves, reading one float4 per channel (L2-resident tables).
+struct TabFn {
+    const float4 *coef;  // [n-1][3F]
+    const float *dist;   // [U] pair distances
+    int n;
+    float inv_h;
+};
+__device__ __forceinline__ void tab_locate(const TabFn &T, int u, int &k, float &s) {
+    const float x = T.dist[u] * T.inv_h;
+    int kk = (int)floorf(x);
+    kk = kk < 0 ? 0 : (kk > T.n - 2 ? T.n - 2 : kk);
+    k = kk;
+    s = x - (float)kk;
+}
+__device__ __forceinline__ float tab_value(const float4 &c, float s) {
+    return fmaf(s, fmaf(s, fmaf(s, c.w, c.z), c.y), c.x);
+}
+__device__ __forceinline__ float tab_slope(const float4 &c, float s, float inv_h) {
+    return fmaf(s, fmaf(s, 3.f * c.w, 2.f * c.z), c.y) * inv_h;
 }
 
 // per undirected pair: u_ij, phi (geo), phi alone (phiu) and d (dist)
@@ -400,29 +420,6 @@ __global__ void k_pair_geo(const float *__restrict__ pos, const float *__restric
         phiu[u] = phi;
         dist[u] = d;
         geo[u] = make_float4(x * inv, y * inv, zz * inv, phi);
-    }
-}
-
-// out_v[u][w] = p(s), out_d[u][w] = p'(s)/h of the interval holding d_u
-// (coefficients [n-1][4][W], grid k h)
-__global__ void k_tab_eval(const float *__restrict__ dist, const int32_t *__restrict__ nu, int n, float h,
-                           int W, const float *__restrict__ coef, float *__restrict__ out_v,
-                           float *__restrict__ out_d) {
-    pdl_entry();
-    const int U = *nu;
-    const float inv_h = 1.0f / h;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)U * W;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t u = t / W;
-        const int w = (int)(t % W);
-        const float x = dist[u] * inv_h;
-        int k = (int)floorf(x);
-        k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
-        const float s = x - (float)k;
-        const float *c = coef + (int64_t)k * 4 * W + w;
-        const float c0 = c[0], c1 = c[W], c2 = c[2 * W], c3 = c[3 * W];
-        out_v[t] = fmaf(s, fmaf(s, fmaf(s, c3, c2), c1), c0);
-        out_d[t] = fmaf(s, fmaf(s, 3.f * c3, 2.f * c2), c1) * inv_h;
     }
 }
 
@@ -480,15 +477,17 @@ __device__ __forceinline__ EdgeGeo edge_geo(const float *__restrict__ pos, const
 // so are u and phi (geo, from k_edge_rbf).
 // Block = F threads (thread = channel), persistent over atoms; loads for kMU
 // edges are in flight together.
-template <int F>
+template <int F, bool TAB>
 __global__ void __launch_bounds__(F) k_emb_edges(const float4 *__restrict__ geo, const int32_t *__restrict__ z,
                                                  const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                                  const int32_t *__restrict__ pair_of, int N, int max_z,
-                                                 const float *__restrict__ fu, const float *__restrict__ Ta,
+                                                 const float *__restrict__ fu, TabFn tf, const float *__restrict__ Ta,
                                                  const float *__restrict__ Tb, float *__restrict__ Xraw,
                                                  int32_t *status, OpCopy Xraw_cp) {
     pdl_entry();
     __shared__ int32_t s_u[kChunk], s_zs[kChunk];  // pair index; element of the column atom, signed by direction
+    __shared__ int32_t s_kt[TAB ? kChunk : 1];      // table mode: interval and offset of the pair distance
+    __shared__ float s_st[TAB ? kChunk : 1];
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         int zi = z[i];
@@ -512,6 +511,13 @@ __global__ void __launch_bounds__(F) k_emb_edges(const float4 *__restrict__ geo,
                     zj = (zj < 0 || zj >= max_z) ? 0 : zj;
                 }
                 s_zs[t] = j > i ? zj : -1 - zj;   // u_ij = +u of the pair when i is its first atom
+                if constexpr (TAB) {
+                    int kt = 0;
+                    float st = 0.f;
+                    if (u >= 0) tab_locate(tf, u, kt, st);
+                    s_kt[t] = kt;
+                    s_st[t] = st;
+                }
             }
             __syncthreads();
             for (int k0 = 0; k0 < n; k0 += kMU) {
@@ -526,8 +532,14 @@ __global__ void __launch_bounds__(F) k_emb_edges(const float4 *__restrict__ geo,
 #pragma unroll
                 for (int k = 0; k < kMU; ++k) {
                     if (uu[k] < 0) continue;
-                    const float *fp = fu + (int64_t)uu[k] * 3 * F + c;
-                    f[k][0] = fp[0]; f[k][1] = fp[F]; f[k][2] = fp[2 * F];
+                    if constexpr (TAB) {
+                        const float4 *cp = tf.coef + (int64_t)s_kt[k0 + k] * 3 * F + c;
+                        const float st = s_st[k0 + k];
+                        f[k][0] = tab_value(cp[0], st); f[k][1] = tab_value(cp[F], st); f[k][2] = tab_value(cp[2 * F], st);
+                    } else {
+                        const float *fp = fu + (int64_t)uu[k] * 3 * F + c;
+                        f[k][0] = fp[0]; f[k][1] = fp[F]; f[k][2] = fp[2 * F];
+                    }
                     tb[k] = Tb[(int64_t)(zz[k] >= 0 ? zz[k] : -1 - zz[k]) * F + c];
                     gk[k] = geo[uu[k]];
                 }
@@ -616,12 +628,14 @@ __global__ void k_node_norm(const float *__restrict__ X, int N, int F, float *__
 // kMU edges waits for one round of gathers, not for its indices first; the
 // sums still run in row order.  F is a template parameter so the coordinate
 // offsets are immediates.
-template <int F>
+template <int F, bool TAB>
 __global__ void __launch_bounds__(F) k_message(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                                                const int32_t *__restrict__ pair_of, const float *__restrict__ gU,
-                                               const float *__restrict__ Y, int N, float *__restrict__ M) {
+                                               TabFn tg, const float *__restrict__ Y, int N, float *__restrict__ M) {
     pdl_entry();
     __shared__ int32_t s_u[kChunk], s_j[kChunk];
+    __shared__ int32_t s_kt[TAB ? kChunk : 1];
+    __shared__ float s_st[TAB ? kChunk : 1];
     const int c = threadIdx.x;
     for (int i = blockIdx.x; i < N; i += gridDim.x) {
         float m[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -629,7 +643,18 @@ __global__ void __launch_bounds__(F) k_message(const int32_t *__restrict__ row_p
         for (int cb = e0; cb < e1; cb += kChunk) {
             const int n = e1 - cb < kChunk ? e1 - cb : kChunk;
             __syncthreads();  // the previous chunk is consumed
-            for (int t = c; t < n; t += F) { s_u[t] = pair_of[cb + t]; s_j[t] = col[cb + t]; }
+            for (int t = c; t < n; t += F) {
+                const int u = pair_of[cb + t];
+                s_u[t] = u;
+                s_j[t] = col[cb + t];
+                if constexpr (TAB) {
+                    int kt = 0;
+                    float st = 0.f;
+                    if (u >= 0) tab_locate(tg, u, kt, st);
+                    s_kt[t] = kt;
+                    s_st[t] = st;
+                }
+            }
             __syncthreads();
             for (int k0 = 0; k0 < n; k0 += kMU) {
                 int uu[kMU], jj[kMU];
@@ -642,8 +667,14 @@ __global__ void __launch_bounds__(F) k_message(const int32_t *__restrict__ row_p
 #pragma unroll
                 for (int k = 0; k < kMU; ++k) {
                     if (uu[k] < 0) continue;
-                    const float *gp = gU + (int64_t)uu[k] * 3 * F + c;
-                    g[k][0] = gp[0]; g[k][1] = gp[F]; g[k][2] = gp[2 * F];
+                    if constexpr (TAB) {
+                        const float4 *cp = tg.coef + (int64_t)s_kt[k0 + k] * 3 * F + c;
+                        const float st = s_st[k0 + k];
+                        g[k][0] = tab_value(cp[0], st); g[k][1] = tab_value(cp[F], st); g[k][2] = tab_value(cp[2 * F], st);
+                    } else {
+                        const float *gp = gU + (int64_t)uu[k] * 3 * F + c;
+                        g[k][0] = gp[0]; g[k][1] = gp[F]; g[k][2] = gp[2 * F];
+                    }
                     load_coords(Y, jj[k], c, N, F, y[k]);
                 }
 #pragma unroll
@@ -893,19 +924,22 @@ __global__ void k_T_bwd(const float *__restrict__ Y, const float *__restrict__ M
 // lower part gathers gM_j alone (kMU edges in flight), the upper part gM_j,
 // Y_j and a3 together (kMUU edges).  Indices are staged in shared memory as in
 // k_message; the gY sums run in row order.
-// With TAB (tabulated radial functions) a3 holds dg/dd instead: the kernel
-// adds sum dE/dg dg/dd to gphi (then dE/dd of the pair) and writes no dE/da3.
+// With TAB (tabulated radial functions) g and dg/dd come from the table: the
+// kernel adds sum dE/dg dg/dd to gphi (then dE/dd of the pair) and writes no
+// dE/da3.
 constexpr int kMUU = 2;
 template <int F, bool TAB>
 __global__ void __launch_bounds__(F, 512 / F)
     k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                   const int32_t *__restrict__ pair_of, const float *__restrict__ gU, const float *__restrict__ Y,
                   const float *__restrict__ gM, const float *__restrict__ a3, const float *__restrict__ phiu,
-                  int N, float *__restrict__ gY, OpCopy gY_cp, float *__restrict__ ga3, OpCopy ga3_cp,
+                  TabFn tg, int N, float *__restrict__ gY, OpCopy gY_cp, float *__restrict__ ga3, OpCopy ga3_cp,
                   float *__restrict__ gphi) {
     pdl_entry();
     constexpr int NW = F / 32;
     __shared__ int32_t s_u[kChunk], s_j[kChunk];
+    __shared__ int32_t s_kt[TAB ? kChunk : 1];
+    __shared__ float s_st[TAB ? kChunk : 1];
     __shared__ float s_red[kChunk][NW];
     __shared__ float s_yi[9][F], s_gmi[9][F];  // row i's Y and gM (per thread's channel)
     const int c = threadIdx.x, lane = c & 31, warp = c >> 5;
@@ -931,7 +965,18 @@ __global__ void __launch_bounds__(F, 512 / F)
         for (int cb = e0; cb < e1; cb += kChunk) {
             const int n = e1 - cb < kChunk ? e1 - cb : kChunk;
             __syncthreads();
-            for (int t = c; t < n; t += F) { s_u[t] = pair_of[cb + t]; s_j[t] = col[cb + t]; }
+            for (int t = c; t < n; t += F) {
+                const int u = pair_of[cb + t];
+                s_u[t] = u;
+                s_j[t] = col[cb + t];
+                if constexpr (TAB) {
+                    int kt = 0;
+                    float st = 0.f;
+                    if (u >= 0) tab_locate(tg, u, kt, st);
+                    s_kt[t] = kt;
+                    s_st[t] = st;
+                }
+            }
             __syncthreads();
             const int nl = eu - cb < 0 ? 0 : (eu - cb < n ? eu - cb : n);  // lower edges of the chunk
             for (int k0 = 0; k0 < nl; k0 += kMU) {
@@ -945,8 +990,14 @@ __global__ void __launch_bounds__(F, 512 / F)
 #pragma unroll
                 for (int k = 0; k < kMU; ++k) {
                     if (uu[k] < 0) continue;
-                    const float *gp = gU + (int64_t)uu[k] * 3 * F + c;
-                    g[k][0] = gp[0]; g[k][1] = gp[F]; g[k][2] = gp[2 * F];
+                    if constexpr (TAB) {
+                        const float4 *cp = tg.coef + (int64_t)s_kt[k0 + k] * 3 * F + c;
+                        const float st = s_st[k0 + k];
+                        g[k][0] = tab_value(cp[0], st); g[k][1] = tab_value(cp[F], st); g[k][2] = tab_value(cp[2 * F], st);
+                    } else {
+                        const float *gp = gU + (int64_t)uu[k] * 3 * F + c;
+                        g[k][0] = gp[0]; g[k][1] = gp[F]; g[k][2] = gp[2 * F];
+                    }
                     load_coords(gM, jj[k], c, N, F, gmj[k]);
                 }
 #pragma unroll
@@ -970,10 +1021,22 @@ __global__ void __launch_bounds__(F, 512 / F)
 #pragma unroll
                 for (int k = 0; k < kMUU; ++k) {
                     if (uu[k] < 0) continue;
-                    const int64_t o = (int64_t)uu[k] * 3 * F + c;
-                    g[k][0] = gU[o]; g[k][1] = gU[o + F]; g[k][2] = gU[o + 2 * F];
-                    a[k][0] = a3[o]; a[k][1] = a3[o + F]; a[k][2] = a3[o + 2 * F];
-                    phi[k] = TAB ? 0.f : phiu[uu[k]];
+                    if constexpr (TAB) {   // g and dg/dd (in a) from the pair's interval
+                        const float4 *cp = tg.coef + (int64_t)s_kt[k0 + k] * 3 * F + c;
+                        const float st = s_st[k0 + k];
+#pragma unroll
+                        for (int p = 0; p < 3; ++p) {
+                            const float4 cq = cp[p * F];
+                            g[k][p] = tab_value(cq, st);
+                            a[k][p] = tab_slope(cq, st, tg.inv_h);
+                        }
+                        phi[k] = 0.f;
+                    } else {
+                        const int64_t o = (int64_t)uu[k] * 3 * F + c;
+                        g[k][0] = gU[o]; g[k][1] = gU[o + F]; g[k][2] = gU[o + 2 * F];
+                        a[k][0] = a3[o]; a[k][1] = a3[o + F]; a[k][2] = a3[o + 2 * F];
+                        phi[k] = phiu[uu[k]];
+                    }
                     load_coords(gM, jj[k], c, N, F, gmj[k]);
                     load_coords(Y, jj[k], c, N, F, yj[k]);
                 }
@@ -1217,14 +1280,14 @@ __global__ void k_emb_bwd(const float *__restrict__ pos, const float *__restrict
 //   edge_g[rev e]  = the same for (j, i), u_ji = -u
 //   gfu[u]         = dE/df^p summed over both uses (columns p*F + c).
 // Pair-parallel, so small systems still fill the GPU.
-template <int CPL>
+template <int CPL, bool TAB>
 __global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *__restrict__ z,
                                 const int2 *__restrict__ uij, const int32_t *__restrict__ ue,
                                 const int32_t *__restrict__ rev, const int32_t *__restrict__ nu, int N, int max_z,
-                                const float *__restrict__ fu, const float *__restrict__ Ta,
+                                const float *__restrict__ fu, TabFn tf, const float *__restrict__ Ta,
                                 const float *__restrict__ Tb, const float *__restrict__ gXraw,
                                 float *__restrict__ gfu, float4 *__restrict__ edge_g,
-                                OpCopy gfu_cp, const float *__restrict__ dfu, float *__restrict__ dEdd) {
+                                OpCopy gfu_cp, float *__restrict__ dEdd) {
     pdl_entry();
     constexpr int F = CPL * 32;
     const int lane = threadIdx.x & 31;
@@ -1244,11 +1307,22 @@ __global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *_
         float a_phi = 0.f, ax = 0.f, ay = 0.f, az = 0.f;   // use (i, j)
         float b_phi = 0.f, bx = 0.f, by = 0.f, bz = 0.f;   // use (j, i), gradient w.r.t. u_ji
         float gd = 0.f;                                    // sum dE/df df/dd (table mode)
+        int kt = 0;
+        float st = 0.f;
+        if constexpr (TAB) tab_locate(tf, u, kt, st);
 #pragma unroll
         for (int k = 0; k < CPL; ++k) {
             const int c = lane + 32 * k;
-            const float *fp = fu + (int64_t)u * 3 * F + c;
-            const float f0 = fp[0], f1 = fp[F], f2 = fp[2 * F];
+            float f0, f1, f2, df0 = 0.f, df1 = 0.f, df2 = 0.f;
+            if constexpr (TAB) {
+                const float4 *cp = tf.coef + (int64_t)kt * 3 * F + c;
+                const float4 q0 = cp[0], q1 = cp[F], q2 = cp[2 * F];
+                f0 = tab_value(q0, st); f1 = tab_value(q1, st); f2 = tab_value(q2, st);
+                df0 = tab_slope(q0, st, tf.inv_h); df1 = tab_slope(q1, st, tf.inv_h); df2 = tab_slope(q2, st, tf.inv_h);
+            } else {
+                const float *fp = fu + (int64_t)u * 3 * F + c;
+                f0 = fp[0]; f1 = fp[F]; f2 = fp[2 * F];
+            }
             float gi[9], gj[9];
             load_coords(gXraw, i, c, N, F, gi);
             load_coords(gXraw, j, c, N, F, gj);
@@ -1289,13 +1363,13 @@ __global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *_
             opcopy_store(gfu_cp, ob, o0);
             opcopy_store(gfu_cp, ob + F, o1);
             opcopy_store(gfu_cp, ob + 2 * F, o2);
-            if (dfu) gd += o0 * dfu[ob] + o1 * dfu[ob + F] + o2 * dfu[ob + 2 * F];
+            if constexpr (TAB) gd += o0 * df0 + o1 * df1 + o2 * df2;
         }
         a_phi = warp_sum(a_phi); ax = warp_sum(ax); ay = warp_sum(ay); az = warp_sum(az);
         b_phi = warp_sum(b_phi); bx = warp_sum(bx); by = warp_sum(by); bz = warp_sum(bz);
-        if (dfu) gd = warp_sum(gd);
+        if constexpr (TAB) gd = warp_sum(gd);
         if (lane == 0) {
-            if (dfu) dEdd[u] += gd;
+            if constexpr (TAB) dEdd[u] += gd;
             const int e = ue[u];
             edge_g[e] = make_float4(a_phi, ax, ay, az);
             edge_g[rev[e]] = make_float4(b_phi, bx, by, bz);
@@ -1579,7 +1653,7 @@ int radial_tables_impl(tnet_ctx *ctx, const float *wblob, cudaStream_t st) {
                       (1.0 - exp(-(rc - rl))) / (K - 1), K};
     const double h = rc / (nt - 1);
     const int64_t per_fn = (int64_t)(nt - 1) * 4 * 3 * F;
-    auto coef = [&](int j) { return f32(Lw.tab) + j * per_fn; };
+    auto coef = [&](int j) { return reinterpret_cast<float4 *>(f32(Lw.tab) + j * per_fn); };
     const int64_t w3_per = 6LL * F * F + 3 * F;
     auto w3p = [&](int l) { return f32(Lw.w3p) + l * w3_per; };
     auto b3p = [&](int l) { return f32(Lw.w3p) + l * w3_per + 6LL * F * F; };
@@ -1842,9 +1916,13 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     float *eu = f32(Lw.eu), *phiu = f32(Lw.phiu), *fu = f32(Lw.fu);
     float4 *geo = wsp<float4>(ctx, Lw.geo);
     // table mode: function 0 is the projections f, function 1 + l layer l's
-    // filter g; each [n][3F] values followed by [n][3F] d-derivatives
-    auto coef = [&](int j) { return f32(Lw.tab) + (int64_t)j * (nt - 1) * 4 * 3 * F; };
-    float *dist = f32(Lw.dist), *dfu = f32(Lw.dfu);
+    // filter g, each [n-1][3F] float4 Hermite coefficients
+    float *dist = f32(Lw.dist);
+    auto tabfn = [&](int j) {
+        return TabFn{reinterpret_cast<const float4 *>(f32(Lw.tab) + (int64_t)j * (nt - 1) * 4 * 3 * F), dist, nt,
+                     tab ? 1.0f / th : 0.f};
+    };
+    const TabFn tf0 = tabfn(0);
     if (tab) {
         if (!ctx->tab_ready) return TNET_ERR_ARG;  // tnet_radial_tables not called
         launch(k_pair_geo, grid_for(maxU, 256, sms), 256, 0, st, pos, box, batch, uij, nu, rp, phiu, geo, dist);
@@ -1856,12 +1934,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     launch(k_elem_tables, d.max_z, 256, sizeof(float) * F, st, W.emb, W.emb2_w, W.emb2_b, F, Ta, Tb);
     count_launch();
     TNET_LAUNCH_CHECK();
-    if (tab) {
-        launch(k_tab_eval, grid_for((int64_t)maxU * 3 * F, 256, sms), 256, 0, st, dist, nu, nt, th, 3 * F, coef(0),
-               fu, dfu);
-        count_launch();
-        TNET_LAUNCH_CHECK();
-    } else {   // radial projections f^p = W^p e(d) + b^p, once per undirected pair
+    if (!tab) {   // radial projections f^p = W^p e(d) + b^p, once per undirected pair
         // FP32 in both modes: K = num_rbf is small, and rounding the narrow
         // expnorm basis values to bf16 costs more force accuracy than any
         // other operand
@@ -1884,8 +1957,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     float2 *ln0 = wsp<float2>(ctx, Lw.ln0);
     const int atom_blocks = N < sms * ctx->tune[T_ROW_BLOCKS] ? N : sms * ctx->tune[T_ROW_BLOCKS];
 #define EMB_FWD(FF)                                                                                           \
-    launch(k_emb_edges<FF>, atom_blocks, FF, 0, st, geo, z, row_ptr, col, pair_of, N, d.max_z, fu, Ta, Tb, Xraw, status, \
-                                                nbf)
+    if (tab)                                                                                                  \
+        launch(k_emb_edges<FF, true>, atom_blocks, FF, 0, st, geo, z, row_ptr, col, pair_of, N, d.max_z, fu, tf0, Ta, \
+                                                          Tb, Xraw, status, nbf);                                   \
+    else                                                                                                      \
+        launch(k_emb_edges<FF, false>, atom_blocks, FF, 0, st, geo, z, row_ptr, col, pair_of, N, d.max_z, fu, tf0, Ta, \
+                                                           Tb, Xraw, status, nbf)
     TNET_F_SWITCH(F, EMB_FWD);
 #undef EMB_FWD
     count_launch();
@@ -1918,14 +1995,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         const LayerW &Lr = W.layer[l];
         float *a1 = act(Lw.a1, F, l), *h1 = act(Lw.h1, F, l), *a2 = act(Lw.a2, 2 * F, l),
               *h2 = act(Lw.h2, 2 * F, l), *a3 = act(Lw.a3, 3 * F, l), *gbuf = act(Lw.g, 3 * F, l);
-        if (tab) {  // g and dg/dd (in the a3 slab) from the table
-            pf.mark(P_MLP1);
-            launch(k_tab_eval, grid_for((int64_t)maxU * 3 * F, 256, sms), 256, 0, st, dist, nu, nt, th, 3 * F,
-                   coef(1 + l), gbuf, a3);
-            count_launch();
-            TNET_LAUNCH_CHECK();
-            return TNET_OK;
-        }
+        if (tab) return TNET_OK;  // the message kernels evaluate g, dg/dd from the table
         const EpiBiasAct e1{Lr.mlp1_b, a1, F, keep_h ? h1 : nullptr, F, 1, nullptr, h1_cp(l), F};
         const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, keep_h ? h2 : nullptr, 2 * F, 1, nullptr, h2_cp(l), 2 * F};
         const EpiBiasAct e3{b3p(l), a3, 3 * F, gbuf, 3 * F, 1, phiu};
@@ -1972,7 +2042,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         TRY(edge_mlp(l));
         pf.mark(P_MESSAGE);
         const float *gbuf = act(Lw.g, 3 * F, l);
-#define MSG_FWD(FF) launch(k_message<FF>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, N, M)
+#define MSG_FWD(FF)                                                                                               \
+    if (tab) launch(k_message<FF, true>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, tabfn(1 + l), Y, N, M); \
+    else launch(k_message<FF, false>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, tabfn(1 + l), Y, N, M)
         TNET_F_SWITCH(F, MSG_FWD);
 #undef MSG_FWD
         count_launch();
@@ -2077,11 +2149,11 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         // and 3xTF32 GEMMs and the weight gradients)
         float *ga3_out = (prec != 1 || wg) ? gg : nullptr;
 #define MSG_BWD(FF)                                                                                          \
-    launch(k_message_bwd<FF, false>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu, N, gY, \
-                                                         nbf, ga3_out, ga3_cp, gphiu)
+    launch(k_message_bwd<FF, false>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu,       \
+                                                         tabfn(1 + l), N, gY, nbf, ga3_out, ga3_cp, gphiu)
 #define MSG_BWD_TAB(FF)                                                                                      \
-    launch(k_message_bwd<FF, true>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu, N, gY, \
-                                                        nbf, nullptr, none, gphiu)
+    launch(k_message_bwd<FF, true>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu,        \
+                                                        tabfn(1 + l), N, gY, nbf, nullptr, none, gphiu)
         if (tab) {
             TNET_F_SWITCH(F, MSG_BWD_TAB);
         } else {
@@ -2192,10 +2264,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     if (wg)                                                                                                  \
         launch(k_emb_bwd<CPL>, bwd_blocks, 256, 0, st, pos, box, batch, z, row_ptr, col, pair_of, N, d.max_z, rp, \
                                                    fu, Ta, Tb, gXraw, 1, gfu, edge_g, gA, gB, gfu_cp);        \
+    else if (tab)                                                                                            \
+        launch(k_emb_bwd_pairs<CPL, true>, pair_grid, 256, 0, st, geo, z, uij, ue, rev, nu, N, d.max_z, fu, tf0, Ta, \
+                                                            Tb, gXraw, nullptr, edge_g, none, gphiu);               \
     else                                                                                                     \
-        launch(k_emb_bwd_pairs<CPL>, pair_grid, 256, 0, st, geo, z, uij, ue, rev, nu, N, d.max_z, fu, Ta, Tb, gXraw, \
-                                                      tab ? nullptr : gfu, edge_g, gfu_cp, tab ? dfu : nullptr,     \
-                                                      gphiu)
+        launch(k_emb_bwd_pairs<CPL, false>, pair_grid, 256, 0, st, geo, z, uij, ue, rev, nu, N, d.max_z, fu, tf0, Ta, \
+                                                             Tb, gXraw, gfu, edge_g, gfu_cp, nullptr)
     switch (F / 32) {
         case 2: EMB_BWD(2); break;
         case 4: EMB_BWD(4); break;
