@@ -1355,15 +1355,16 @@ __global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *_
             const float o1 = phi * (Zij * gcA + Zji * hcA);
             const float o2 = phi * (Zij * gcS + Zji * hcS);
             const int64_t ob = (int64_t)u * 3 * F + c;
-            if (gfu) {
+            if constexpr (TAB) {   // no projection weights to go back through
+                gd += o0 * df0 + o1 * df1 + o2 * df2;
+            } else {
                 gfu[ob] = o0;
                 gfu[ob + F] = o1;
                 gfu[ob + 2 * F] = o2;
+                opcopy_store(gfu_cp, ob, o0);
+                opcopy_store(gfu_cp, ob + F, o1);
+                opcopy_store(gfu_cp, ob + 2 * F, o2);
             }
-            opcopy_store(gfu_cp, ob, o0);
-            opcopy_store(gfu_cp, ob + F, o1);
-            opcopy_store(gfu_cp, ob + 2 * F, o2);
-            if constexpr (TAB) gd += o0 * df0 + o1 * df1 + o2 * df2;
         }
         a_phi = warp_sum(a_phi); ax = warp_sum(ax); ay = warp_sum(ay); az = warp_sum(az);
         b_phi = warp_sum(b_phi); bx = warp_sum(bx); by = warp_sum(by); bz = warp_sum(bz);
