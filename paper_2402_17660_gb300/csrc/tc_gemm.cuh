@@ -171,9 +171,16 @@ struct TileCfg {
     // bytes TMA brings per pipeline stage: A, B (+ B_lo for TF32X3; A_lo is
     // formed in shared memory)
     static constexpr uint32_t STAGE_TX = A_BYTES + (X3 ? 2 : 1) * B_BYTES;
-    static constexpr int STAGES = X3 ? 4 : (BN >= 192 ? 3 : 4);
     static constexpr uint32_t TMEM_COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
     static constexpr uint32_t STAGE_BYTES = EPI_WARPS * 32 * STG_LD * 4;  // epilogue transpose buffers
+    // 3xTF32: 4 stages, 5 at BN = 128 (what fits beside the epilogue buffers):
+    // each stage's split and three MMAs make a long round trip, which the
+    // wide radial layers feel.  The narrow tiles (K-wide outputs) keep 4 and a
+    // smaller footprint, which leaves room on the SM for the CTAs of the next
+    // kernel that programmatic launch brings in early.
+    static constexpr int X3_FIT = (int)((232448 - 1024 - 256 - STAGE_BYTES) / (STAGE_TX + A_BYTES));
+    static constexpr int STAGES = X3 ? (BN == 128 && X3_FIT >= 5 ? 5 : 4) : (BN >= 192 ? 3 : 4);
+    static_assert(STAGES >= 2 && 8 * (3 * STAGES + 4) + 8 <= 256, "pipeline barriers exceed their block");
     static constexpr size_t SMEM = 1024 + STAGES * (size_t)(STAGE_TX + (X3 ? A_BYTES : 0)) + 256 + STAGE_BYTES;
     static_assert(SMEM <= 232448, "dynamic shared memory above 227 KB");
 };
