@@ -458,7 +458,7 @@ def run_ours(args):
         if os.path.exists(tpath):
             tkey = f"{args.workload}:{args.precision}:{tag}" + (f":table{args.radial_table}" if tab else "")
             tr = json.load(open(tpath)).get(tkey)
-            if tr and tr.get("kernel_rev") == kernel_revision():
+            if tr and tr.get("kernel_rev") == kernel_revision(tr.get("rev_files")):
                 traffic = tr["bytes_per_launch"]
         if engine == "tensor":
             cpeak, cname, cnote = bf16_peak, "tensor", "of measured bf16 burst (MEASURED_PEAKS.json)"
@@ -646,13 +646,13 @@ def run_md(sys_, shape, prec, dev, args):
             "status": status, "weights": "random init, output layer scaled by 0.05"}
 
 
-def kernel_revision() -> str:
-    """Hash of the CUDA sources; a stored ncu traffic figure is used only
-    while the kernels it was measured on are unchanged."""
+def kernel_revision(files=None) -> str:
+    """Hash of the CUDA sources a kernel is compiled from (default: all of
+    them); a stored ncu traffic figure is used only while they are unchanged."""
     import hashlib
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_2402_17660_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(files if files else os.listdir(d)):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
