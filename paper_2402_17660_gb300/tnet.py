@@ -242,10 +242,10 @@ def tuning_knobs(lib=None) -> list[tuple[str, list[int]]]:
 
 
 def autotune(model: TensorNet, z, pos, nl: NeighborList, batch=None, box=None, n_systems=1, reps=5,
-             cache: str | None = TUNE_CACHE, force=False):
+             cache: str | None = TUNE_CACHE, force=False, passes=3):
     """Pick launch shapes by timing them on this input (coordinate descent
-    over the context's knobs, CUDA events around CUDA-graph replays of whole
-    energy+force calls),
+    over the context's knobs, repeated while it changes a knob, CUDA events
+    around CUDA-graph replays of whole energy+force calls),
     set them on the model and cache them as JSON keyed by GPU, precision,
     shape and size.  Returns (knobs, {knob: {candidate: ms}})."""
     dev = model.device
@@ -289,15 +289,22 @@ def autotune(model: TensorNet, z, pos, nl: NeighborList, batch=None, box=None, n
 
     knobs = model.get_tuning()
     timings = {}
-    for k, (name, cands) in enumerate(tuning_knobs(model.lib)):
-        res = {}
-        for v in cands:
-            trial = list(knobs)
-            trial[k] = v
-            model.set_tuning(trial)
-            res[v] = run_ms()
-        knobs[k] = min(res, key=res.get)
-        timings[name] = {str(v): round(t, 4) for v, t in res.items()}
+    # knobs interact (programmatic launch changes which grid sizes win), so the
+    # descent sweeps again while a sweep still changes something (at most
+    # `passes` sweeps)
+    for _ in range(passes):
+        before = list(knobs)
+        for k, (name, cands) in enumerate(tuning_knobs(model.lib)):
+            res = {}
+            for v in cands:
+                trial = list(knobs)
+                trial[k] = v
+                model.set_tuning(trial)
+                res[v] = run_ms()
+            knobs[k] = min(res, key=res.get)
+            timings[name] = {str(v): round(t, 4) for v, t in res.items()}
+        if knobs == before:
+            break
     model.set_tuning(knobs)
     if cache:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
