@@ -646,15 +646,35 @@ def run_md(sys_, shape, prec, dev, args):
             "status": status, "weights": "random init, output layer scaled by 0.05"}
 
 
-def kernel_revision(files=None) -> str:
-    """Hash of the CUDA sources a kernel is compiled from (default: all of
-    them); a stored ncu traffic figure is used only while they are unchanged."""
+def _definition(text: str, name: str) -> str:
+    """Source text of the __global__/__device__ function `name`, from its
+    qualifier to its matching closing brace."""
+    import re
+    m = re.search(r"\b(?:__global__|__device__)[^;{}]*?\b" + re.escape(name) + r"\s*\(", text)
+    if m is None:
+        raise KeyError(name)
+    i = text.index("{", m.end())
+    depth = 0
+    for j in range(i, len(text)):
+        depth += {"{": 1, "}": -1}.get(text[j], 0)
+        if depth == 0:
+            return text[m.start():j + 1]
+    raise ValueError(name)
+
+
+def kernel_revision(parts=None) -> str:
+    """Hash of the CUDA source a kernel is compiled from: whole files
+    ("internal.cuh") or single function definitions ("model.cu:k_message_bwd");
+    default: every file.  A stored ncu traffic figure is used only while that
+    source is unchanged."""
     import hashlib
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_2402_17660_gb300", "csrc")
-    for f in sorted(files if files else os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(fh.read())
+    for part in sorted(parts if parts else os.listdir(d)):
+        fname, _, func = part.partition(":")
+        with open(os.path.join(d, fname)) as fh:
+            text = fh.read()
+        h.update((_definition(text, func) if func else text).encode())
     return h.hexdigest()[:12]
 
 

@@ -1920,8 +1920,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     // filter g, each [n-1][3F] float4 Hermite coefficients
     float *dist = f32(Lw.dist);
     auto tabfn = [&](int j) {
+        if (!tab) return TabFn{nullptr, nullptr, 0, 0.f};
         return TabFn{reinterpret_cast<const float4 *>(f32(Lw.tab) + (int64_t)j * (nt - 1) * 4 * 3 * F), dist, nt,
-                     tab ? 1.0f / th : 0.f};
+                     1.0f / th};
     };
     const TabFn tf0 = tabfn(0);
     if (tab) {
