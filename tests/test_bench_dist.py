@@ -1,6 +1,6 @@
 """The benchmark's multi-rank path on CPU: two gloo ranks on 127.0.0.1 run
 independent replicas, and the whole-job rate uses the slowest rank's time
-(units of all ranks / max time), as the driver expects."""
+(units of all ranks / max time)."""
 import os
 import socket
 
