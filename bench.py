@@ -263,26 +263,34 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours ---
-def stage_work(tag, nu, N, E, F, K, prec, table=False):
+def stage_work(tag, nu, N, E, F, K, prec, table=0):
     """Algorithmic work of one instance of a timed stage: (FLOP, bytes, engine).
-    Bytes count each operand read once and each result written once,
-    including the operand copies the tensor-core modes write beside a result
-    (bf16: 2 B per element; 3xTF32: a 4 B residual).  With tabulated radial
-    functions the "mlp1" stage is the per-pair table evaluation (read d, write
-    g and dg/dd; the tables themselves stay in L2)."""
+    Bytes count each unique operand read once and each result written once,
+    including the bf16 operand copies the BF16 mode writes beside a result
+    (2 B per element; the 3xTF32 mode writes none: it splits its operands in
+    shared memory).  table = n > 0: tabulated radial functions, whose
+    [n-1][3F] float4 tables are read once per launch (they stay in L2; at most
+    one interval per pair) in place of the per-pair f, g and a3 arrays, and
+    whose radial-MLP stages do not run."""
     f = 4.0
     bf16 = prec == "bf16"
-    cp = {"fp32": 0.0, "bf16": 2.0, "tf32x3": 4.0}[prec]   # operand-copy bytes per element
+    cp = 2.0 if bf16 else 0.0            # operand-copy bytes per element
     hb = 2.0 if bf16 else 4.0            # bytes per element of a GEMM input operand
     if table:
-        if tag == "mlp1":
-            return 2.0 * 12 * 3 * F * nu, nu * (f + 2 * 3 * F * f), "hbm"
-        if tag == "emb_edges_bwd":  # reads f and df/dd, updates dE/dd
-            return 2.0 * 43 * F * 2 * nu, f * (9 * N * F + 6 * F * nu + 2 * nu) + 16.0 * E, "hbm"
-        if tag == "message_bwd":    # reads g and dg/dd, no dE/da3
-            rd = f * (3 * 9 * N * F + 2 * 3 * F * nu) + 8.0 * E
+        tab = min(table - 1, nu) * 3 * F * 16.0   # each pair reads one interval
+        hermite = 2.0 * 7 * 3 * F * 2 * nu   # value (and slope) of each edge's interval
+        if tag == "emb_edges":
+            return 2.0 * 12 * F * 2 * nu + hermite / 2, (f + cp) * 9 * N * F + tab, "hbm"
+        if tag == "emb_edges_bwd":  # reads gX_raw, writes 16 B per edge, updates dE/dd
+            return 2.0 * 43 * F * 2 * nu + hermite / 2, f * (9 * N * F + 2 * nu) + 16.0 * E + tab, "hbm"
+        if tag == "message":
+            return 2.0 * 9 * F * 2 * nu + hermite / 2, f * 2 * 9 * N * F + 8.0 * E + tab, "hbm"
+        if tag == "message_bwd":    # no dE/da3; dE/dd of each pair updated
+            rd = f * 3 * 9 * N * F + 8.0 * E + tab
             wr = (f + cp) * 9 * N * F + 2 * f * nu
-            return 4.0 * 9 * F * 2 * nu + 2.0 * 3 * F * nu, rd + wr, "hbm"
+            return 4.0 * 9 * F * 2 * nu + 2.0 * 3 * F * nu + hermite, rd + wr, "hbm"
+        if tag.startswith("mlp"):
+            return None
     if tag == "mlp1":
         return 2.0 * nu * K * F, nu * (K * f + F * f + F * hb), "alu"
     if tag == "mlp2":
@@ -298,8 +306,12 @@ def stage_work(tag, nu, N, E, F, K, prec, table=False):
         return 2.0 * nu * F * K, nu * (F * f + 2 * K * f), "alu"
     if tag == "emb_edges":   # read the pair projections once, write X_raw once
         return 2.0 * 12 * F * 2 * nu, f * (3 * F * nu + 9 * N * F) + cp * 9 * N * F, "hbm"
-    if tag == "emb_edges_bwd":  # read gX_raw and the projections, write their adjoint and 16 B per edge
-        return 2.0 * 40 * F * 2 * nu, f * (9 * N * F + 6 * F * nu) + 16.0 * E, "hbm"
+    if tag == "emb_edges_bwd":
+        # read gX_raw and the projections, write their adjoint and 16 B per
+        # edge; then the projections' input-gradient GEMM (read dE/df, update
+        # dE/de)
+        return 2.0 * 40 * F * 2 * nu + 2.0 * nu * 3 * F * K, \
+            f * (9 * N * F + 6 * F * nu) + 16.0 * E + nu * (3 * F * f + 2 * K * f), "hbm"
     if tag == "message":     # read Y and the pair filters once, write M once, read the CSR
         return 2.0 * 9 * F * 2 * nu, f * (2 * 9 * N * F + 3 * F * nu) + 8.0 * E, "hbm"
     if tag == "message_bwd":
@@ -444,14 +456,14 @@ def run_ours(args):
     x3 = args.precision == "tf32x3"
     tab = args.radial_table > 0
     work_tags = [k for k in sorted(stages, key=lambda k: -stages[k]["ms_per_step"])
-                 if stage_work(k, nu, N, n_pairs, F_, shape.K, args.precision, tab) is not None]
+                 if stage_work(k, nu, N, n_pairs, F_, shape.K, args.precision, args.radial_table) is not None]
     if work_tags:
         tag = work_tags[0]
-        flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, args.precision, tab)
+        flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, args.precision, args.radial_table)
         if x3 and not tab and tag in ("mlp2", "mlp3", "mlp3_bwd", "mlp2_bwd"):
-            # 3xTF32: three TF32 MMAs per product; operands fp32 + fp32 residual
+            # 3xTF32: three TF32 MMAs per product (the residuals are formed in
+            # shared memory, so the bytes are those of the fp32 operands)
             engine = "tensor_tf32"
-            nbytes = nbytes * 1.5
         per_launch_ms = stages[tag]["ms_per_step"] * args.profile_steps / stages[tag]["instances"]
         traffic = None
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
