@@ -473,8 +473,9 @@ __device__ __forceinline__ EdgeGeo edge_geo(const float *__restrict__ pos, const
 
 // X_raw_i = sum_j phi Z_ij (f^I I0 + f^A A0(u) + f^S S0(u)) over the active
 // edges of row i, in row order.  f^p = W^p e(d) + b^p depends only on d, so
-// it is computed once per undirected pair by a GEMM (fu, columns p*F + c);
-// so are u and phi (geo, from k_edge_rbf).
+// it is computed once per undirected pair by a GEMM (fu, columns p*F + c),
+// or, with TAB, evaluated here from the Hermite table; u and phi come once
+// per pair from geo (k_edge_rbf or k_pair_geo).
 // Block = F threads (thread = channel), persistent over atoms; loads for kMU
 // edges are in flight together.
 template <int F, bool TAB>
@@ -1297,7 +1298,7 @@ __global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *_
         const int u = (int)uu;
         const int2 p = uij[u];
         const int i = p.x, j = p.y;
-        const float4 gu = geo[u];  // u_ij and phi of the pair (k_edge_rbf)
+        const float4 gu = geo[u];  // u_ij and phi of the pair (k_edge_rbf or k_pair_geo)
         const float ux = gu.x, uy = gu.y, uz = gu.z, phi = gu.w;
         const float bxx = ux * ux - (1.0f / 3.0f), byy = uy * uy - (1.0f / 3.0f);
         const float bxy = ux * uy, bxz = ux * uz, byz = uy * uz;
