@@ -3,6 +3,7 @@ exports every function include/tnet.h declares, reports shapes and workspace
 sizes, and the Python blob layout agrees with the header and the
 generators."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -115,3 +116,40 @@ def test_radial_table_workspace(lib):
         ok = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0, 0, n)
         assert lib.tnet_workspace_bytes(ctypes.byref(ok), 3000, 1, 160000) > 0
     assert lib.tnet_radial_tables(None, None, None) == 1
+
+
+def test_plain_c_client(lib, tmp_path):
+    """include/tnet.h is a C99 header: a C program includes it, links
+    libtnet.so and calls the host-side entry points (no GPU needed)."""
+    import shutil
+    import subprocess
+    from paper_2402_17660_gb300 import build as _build
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "tnet.h"
+int main(void) {
+    tnet_model_desc d = {128, 32, 2, 100, 5.0f, 0.0f, 0, 0, 0};
+    int64_t nw = tnet_weights_count(&d);
+    int64_t ws = tnet_workspace_bytes(&d, 3000, 1, 160000);
+    tnet_model_desc bad = d;
+    bad.radial_table = 100;
+    printf("%lld %lld %lld %d %s\n", (long long)nw, (long long)ws,
+           (long long)tnet_workspace_bytes(&bad, 3000, 1, 160000), tnet_tuning_knobs(),
+           tnet_status_string(TNET_ERR_CAPACITY));
+    return (nw > 0 && ws > 0) ? 0 : 1;
+}
+''')
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(_build.LIB)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(_build.__file__)))
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-pedantic", str(src), "-I", os.path.join(root, "include"),
+                    "-L", libdir, "-ltnet", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    d = _lib.ModelDesc(128, 32, 2, 100, 5.0, 0.0, 0, 0, 0)
+    assert int(out[0]) == lib.tnet_weights_count(ctypes.byref(d))
+    assert int(out[1]) == lib.tnet_workspace_bytes(ctypes.byref(d), 3000, 1, 160000)
+    assert int(out[2]) == -1 and int(out[3]) == lib.tnet_tuning_knobs()
