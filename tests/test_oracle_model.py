@@ -8,6 +8,7 @@ import pytest
 import torch
 
 from oracle.neighbors import neighbor_pairs
+from oracle import tensornet as tn
 from oracle.tensornet import TensorNet
 from paper_2402_17660_gb300 import synth
 
@@ -244,6 +245,29 @@ def test_cutoff_continuity():
         dE.append(m.forward(z, np.array([[0.0, 0, 0], [5.0 - eps, 0, 0]]), b, None)[0][0] - far)
     assert abs(dE[0]) > 0
     assert abs(dE[1] / dE[0] - 1 / 16) < 0.005 and abs(dE[2] / dE[1] - 1 / 16) < 0.005
+
+
+def test_edge_filter_vanishes_with_its_slope_at_the_cutoff():
+    """C8: g(d) = 0 for d >= rc, and g(rc - eps) = O(eps^2) (so dg/dd -> 0):
+    the cutoff factor phi carries the whole d-dependence there, since the
+    expnorm basis (with its own phi factor) stays finite."""
+    W, m = _model()
+    K = SMALL.K
+    for d in (5.0, 5.3, 7.0):
+        e, _ = tn.expnorm(np.array([d]), 5.0, 0.0, K)
+        g, _ = m.edge_filter(0, e, tn.cosine_cutoff(np.array([d]), 5.0))
+        assert np.all(g == 0.0)
+    gs = []
+    for eps in (4e-2, 2e-2, 1e-2):
+        d = np.array([5.0 - eps])
+        e, _ = tn.expnorm(d, 5.0, 0.0, K)
+        g, _ = m.edge_filter(1, e, tn.cosine_cutoff(d, 5.0))
+        gs.append(np.abs(g).max())
+    # phi ~ (pi eps / 2 rc)^2 and the basis itself carries another phi, so the
+    # filter's leading behaviour is eps^2 times a bounded factor: halving eps
+    # divides it by 4 to within the factor's own variation
+    assert gs[0] > 0
+    assert abs(gs[1] / gs[0] - 0.25) < 0.02 and abs(gs[2] / gs[1] - 0.25) < 0.02
 
 
 def test_zero_layer_model_runs_and_is_invariant():
