@@ -218,6 +218,51 @@ class TensorNet:
         g = phi[:, None] * h3
         return g.reshape(-1, self.F, 3), (a1, h1, a2, h2, a3, h3)
 
+    # ----------------------------------------------- interaction layer ---
+    def interaction(self, l, X, e, phi, i, j):
+        """Interaction layer l (Sec. 2.1.1) on node tensors X [N, F, 3, 3]:
+        X <- X / (||X|| + 1) per channel [R1]; (I, A, S) = decomp(X);
+        Y^P = W^P_{l,1} P (one bias-free channel mixing per part P); Y = the
+        sum of the three; messages M (see `messages`); then `node_update`.
+        Returns (X_out, cache of the layer's intermediates)."""
+        qn = tensor_norm(X)
+        Xn = X / (qn + 1.0)[..., None, None]
+        parts = decompose(Xn)
+        Yp = [mix(self.p[f"l{l}_mix1_w"][q], parts[q]) for q in range(3)]
+        Y = Yp[0] + Yp[1] + Yp[2]
+        M = self.messages(l, e, phi, i, j, Yp, X.shape[0])
+        Xout, post = self.node_update(l, Xn, Y, M)
+        return Xout, dict(X=X, qn=qn, Xn=Xn, parts=parts, Yp=Yp, Y=Y, M=M, **post)
+
+    def messages(self, l, e, phi, i, j, Yp, N):
+        """M_i = sum over the edges (i, j) of g^I_ij Y^I_j + g^A_ij Y^A_j +
+        g^S_ij Y^S_j, per channel: the receiver i collects its neighbours'
+        parts weighted by the radial filters of `edge_filter`."""
+        F, E = self.F, len(i)
+        M = np.zeros((N, F, 3, 3))
+        for a in range(0, E, EDGE_CHUNK):
+            sl = slice(a, min(E, a + EDGE_CHUNK))
+            g, _ = self.edge_filter(l, e[sl], phi[sl])
+            js = j[sl]
+            vals = sum(g[:, :, q, None, None] * Yp[q][js] for q in range(3))
+            M += segment_sum(i[sl], vals, N)
+        return M
+
+    def node_update(self, l, Xn, Y, M):
+        """Node part after the messages: T = Y M + M Y (the O(3) product, per
+        channel); (I, A, S) = decomp(T) / (||T|| + 1); dX = sum_P W^P_{l,2} P;
+        X_out = Xn + dX + dX dX, the residual on the normalised X [R5].
+        Returns (X_out, {T: the parts of T, pn: ||T||, Tn: the scaled parts,
+        dX})."""
+        T = np.matmul(Y, M) + np.matmul(M, Y)                         # O(3)
+        TI, TA, TS = decompose(T)
+        pn = tensor_norm(TI + TA + TS)
+        den = (pn + 1.0)[..., None, None]
+        Tn = (TI / den, TA / den, TS / den)
+        dX = sum(mix(self.p[f"l{l}_mix2_w"][q], Tn[q]) for q in range(3))
+        Xout = Xn + dX + np.matmul(dX, dX)                            # [R5]
+        return Xout, dict(T=(TI, TA, TS), pn=pn, Tn=Tn, dX=dX)
+
     # --------------------------------------------------------- forward ---
     def forward(self, z, pos, batch, box, pairs=None, n_systems=None):
         """Returns (E_s [S], E_i [N], cache)."""
@@ -260,28 +305,8 @@ class TensorNet:
 
         layers = []
         for l in range(self.L):
-            qn = tensor_norm(X)
-            Xn = X / (qn + 1.0)[..., None, None]
-            parts = decompose(Xn)
-            Yp = [mix(p[f"l{l}_mix1_w"][q], parts[q]) for q in range(3)]
-            Y = Yp[0] + Yp[1] + Yp[2]
-            M = np.zeros((N, F, 3, 3))
-            for a in range(0, E, EDGE_CHUNK):
-                sl = slice(a, min(E, a + EDGE_CHUNK))
-                g, _ = self.edge_filter(l, e[sl], phi[sl])
-                js = j[sl]
-                vals = sum(g[:, :, q, None, None] * Yp[q][js] for q in range(3))
-                M += segment_sum(i[sl], vals, N)
-            T = np.matmul(Y, M) + np.matmul(M, Y)                     # O(3)
-            TI, TA, TS = decompose(T)
-            pn = tensor_norm(TI + TA + TS)
-            den = (pn + 1.0)[..., None, None]
-            Tn = (TI / den, TA / den, TS / den)
-            dX = sum(mix(p[f"l{l}_mix2_w"][q], Tn[q]) for q in range(3))
-            Xout = Xn + dX + np.matmul(dX, dX)                        # [R5]
-            layers.append(dict(X=X, qn=qn, Xn=Xn, parts=parts, Yp=Yp, Y=Y, M=M,
-                               T=(TI, TA, TS), pn=pn, Tn=Tn, dX=dX))
-            X = Xout
+            X, cache_l = self.interaction(l, X, e, phi, i, j)
+            layers.append(cache_l)
 
         # output model [R6, R7]
         I, A, S = decompose(X)

@@ -3,6 +3,8 @@ central finite differences, an autograd witness, the invariances the model
 fixes (Sec. 2.1.1: O(3) equivariance; translation, permutation and periodic
 image invariance), zero net force, cutoff continuity and the isolated-atom
 closed form."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -283,3 +285,104 @@ def test_zero_layer_model_runs_and_is_invariant():
     assert np.allclose(F1, F0 @ Q.T, atol=1e-12)
     fd = _fd_forces(m, s.z, pos, s.batch, None)
     assert np.max(np.abs(F0 - fd)) <= 1e-7 * max(_rms(F0), 1.0)
+
+
+# ------------------------------------------- interaction node update (C9) ---
+# One-channel toy layers whose outputs are worked out by hand.  The mixing
+# weights are scalars per part: W_{l,1} = (2, 3, 5) and W_{l,2} = (2, 3, 5)
+# for (I, A, S), so a dropped or merged decomposition changes the result.
+
+def _toy(F=1, K=2, mlp3_b=(0.0, 0.0, 0.0)):
+    w = np.array([2.0, 3.0, 5.0]).reshape(3, 1, 1)
+    p = {"l0_mix1_w": w, "l0_mix2_w": w,
+         "l0_mlp1_w": np.zeros((F, K)), "l0_mlp1_b": np.zeros(F),
+         "l0_mlp2_w": np.zeros((2 * F, F)), "l0_mlp2_b": np.zeros(2 * F),
+         "l0_mlp3_w": np.zeros((3 * F, 2 * F)), "l0_mlp3_b": np.asarray(mlp3_b, np.float64)}
+    return TensorNet(p, F=F, K=K, L=1)
+
+
+def _one(A):
+    return np.asarray(A, np.float64)[None, None]        # [N=1, F=1, 3, 3]
+
+
+def test_node_update_commuting_factors():
+    """Y = diag(1, 2, 3) and M = diag(4, 5, 6) commute, so T = YM + MY =
+    2 YM = diag(8, 20, 36), symmetric; ||T|| = 64 + 400 + 1296 = 1760.  The
+    parts of T are I = (64/3) Id and S = T - I, with no A part, so
+    dX = (2 I + 5 S) / 1761 = (5 T - 3 (64/3) Id) / 1761 = diag(-24, 36, 116) / 1761,
+    and X_out = Xn + dX + dX^2 (dX diagonal)."""
+    m = _toy()
+    Xn = _one(np.eye(3) * 0.5)
+    Xout, c = m.node_update(0, Xn, _one(np.diag([1.0, 2, 3])), _one(np.diag([4.0, 5, 6])))
+    TI, TA, TS = c["T"]
+    T = (TI + TA + TS)[0, 0]
+    assert np.allclose(T, np.diag([8.0, 20, 36]), atol=1e-13)
+    assert np.allclose(T, T.T, atol=0)
+    assert np.allclose(TA, 0.0, atol=0)
+    assert np.isclose(c["pn"][0, 0], 1760.0, rtol=1e-15)
+    D = np.diag([-24.0, 36.0, 116.0]) / 1761.0
+    assert np.allclose(c["dX"][0, 0], D, atol=1e-15)
+    assert np.allclose(Xout[0, 0], 0.5 * np.eye(3) + D + D @ D, atol=1e-15)
+
+
+def test_node_update_identity_factor():
+    """Y = Id gives T = 2M for any M.  With M = [[1,2,3],[4,5,6],[7,8,10]]:
+    tr T = 32, ||T|| = 4 * 304 = 1216, A(T) = M - M^T, S(T) = M + M^T - (32/3) Id,
+    so dX = (2 (32/3) Id + 3 (M - M^T) + 5 (M + M^T) - (160/3) Id) / 1217
+          = [[-22, 24, 38], [36, 18, 64], [62, 76, 68]] / 1217."""
+    m = _toy()
+    Mm = np.array([[1.0, 2, 3], [4, 5, 6], [7, 8, 10]])
+    Xn = _one(np.zeros((3, 3)))
+    Xout, c = m.node_update(0, Xn, _one(np.eye(3)), _one(Mm))
+    assert np.allclose(sum(c["T"])[0, 0], 2 * Mm, atol=1e-13)
+    assert np.isclose(c["pn"][0, 0], 1216.0, rtol=1e-15)
+    D = np.array([[-22.0, 24, 38], [36, 18, 64], [62, 76, 68]]) / 1217.0
+    assert np.allclose(c["dX"][0, 0], D, atol=1e-15)
+    assert np.allclose(Xout[0, 0], D + D @ D, atol=1e-15)
+
+
+def test_interaction_normalise_decompose_mix():
+    """X = [[1,2,0],[0,1,0],[0,0,1]]: ||X|| = 7, so Xn = X / 8; its parts are
+    I = Id/8, A = [[0,1,0],[-1,0,0],0]/8, S = [[0,1,0],[1,0,0],0]/8, and with
+    W_{l,1} = (2, 3, 5) Y = (2 Id + 3 A + 5 S) * 8 / 8 = [[2,8,0],[2,2,0],[0,0,2]] / 8.
+    An isolated atom has M = 0, so T = 0, dX = 0 and X_out = Xn."""
+    m = _toy()
+    X = _one([[1.0, 2, 0], [0, 1, 0], [0, 0, 1]])
+    e = np.zeros((0, 2))
+    Xout, c = m.interaction(0, X, e, np.zeros(0), np.zeros(0, np.int64), np.zeros(0, np.int64))
+    assert np.isclose(c["qn"][0, 0], 7.0, rtol=1e-15)
+    assert np.allclose(c["Xn"], X / 8.0, atol=1e-16)
+    assert np.allclose(c["Y"][0, 0], np.array([[2.0, 8, 0], [2, 2, 0], [0, 0, 2]]) / 8.0, atol=1e-15)
+    assert np.allclose(c["M"], 0.0, atol=0) and np.allclose(c["dX"], 0.0, atol=0)
+    assert np.allclose(Xout, X / 8.0, atol=1e-16)
+
+
+def test_interaction_layer_two_atoms_closed_form():
+    """Two atoms d = rc/3 apart (phi = 3/4) with isotropic features X_0 = 2 Id,
+    X_1 = Id.  Radial MLP weights zero and last bias b = ln 3 on the I plane
+    give g^I = phi SiLU(ln 3) = (3/4)(3/4) ln 3 = (9/16) ln 3 on every edge.
+    Then Xn_0 = 2/13 Id (||X_0|| = 12), Xn_1 = 1/4 Id (||X_1|| = 3);
+    Y = 2 Xn (the I weight): Y_0 = 4/13 Id, Y_1 = 1/2 Id; M_0 = g Y_1 =
+    (9/32) ln 3 Id, M_1 = g Y_0 = (9/52) ln 3 Id (each atom receives its
+    neighbour's Y); T_k = 2 Y_k M_k = t Id with t = (9/52) ln 3 for both
+    atoms; dX_k = 2 t / (3 t^2 + 1) Id (I weight 2, ||T|| = 3 t^2);
+    X_out = Xn + dX + dX^2."""
+    rc = 5.0
+    m = _toy(mlp3_b=(math.log(3.0), 0.0, 0.0))
+    m.rc = rc
+    pos = np.array([[0.0, 0, 0], [rc / 3, 0, 0]])
+    i = np.array([0, 1])
+    j = np.array([1, 0])
+    d = np.linalg.norm(pos[i] - pos[j], axis=1)
+    phi = tn.cosine_cutoff(d, rc)
+    assert np.allclose(phi, 0.75, atol=1e-15)
+    e, _ = tn.expnorm(d, rc, 0.0, 2)
+    X = np.stack([_one(2 * np.eye(3))[0], _one(np.eye(3))[0]])
+    Xout, c = m.interaction(0, X, e, phi, i, j)
+    ln3 = math.log(3.0)
+    assert np.allclose(c["M"][0, 0], 9 / 32 * ln3 * np.eye(3), atol=1e-15)
+    assert np.allclose(c["M"][1, 0], 9 / 52 * ln3 * np.eye(3), atol=1e-15)
+    for k, (xn, t) in enumerate(((2 / 13, 9 / 52 * ln3), (1 / 4, 9 / 52 * ln3))):
+        dx = 2 * t / (3 * t * t + 1)
+        assert np.allclose(c["dX"][k, 0], dx * np.eye(3), atol=1e-15)
+        assert np.allclose(Xout[k, 0], (xn + dx + dx * dx) * np.eye(3), atol=1e-15)
