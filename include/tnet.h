@@ -251,7 +251,9 @@ int tnet_md_neighbor_list(tnet_ctx *ctx, int n_atoms, int32_t *row_ptr, int32_t 
  * the array's device address (cudaGetSymbolAddress), so make that first call
  * before any stream capture.  All calls share the array: calls whose GPU
  * work overlaps (different streams or threads) race; calls ordered on one
- * stream are safe. */
+ * stream are safe.  Each call lays the array out for its own n_atoms and
+ * n_systems and zeroes what must start at zero, so its cost follows the
+ * input, not the limits. */
 int tnet_neighbors_noalloc(int n_atoms, int n_systems, const float *pos, const int32_t *batch,
                            const float *box, float cutoff, int32_t *row_ptr, int32_t *col, int64_t cap,
                            int64_t *n_pairs_dev, int32_t *status_dev, tnet_stream_t stream);
@@ -270,6 +272,16 @@ int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void *B, float 
  * multiple of 4 and <= 512. */
 int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const float *B, float *B_split, float *C,
                            int32_t *status_dev, tnet_stream_t stream);
+/* Test of the failure path of the tensor-core kernel (no counterpart in the
+ * paper): the 3xTF32 GEMM above with its MMA issuer told to issue nothing and
+ * every mbarrier wait bounded by spin_limit (>= 1) tries instead of the
+ * library's limit.  The loads land, nothing consumes them, the bounded waits
+ * run out: the kernel records TNET_ERR_TIMEOUT in *status_dev, waits for its
+ * own copies, frees its tensor memory and returns, leaving the context
+ * usable.  C is not written.  Returns TNET_ERR_ARG for spin_limit 0 or the
+ * shape errors of tnet_debug_tc_gemm_f32. */
+int tnet_debug_tc_gemm_timeout(int M, int N, int K, const float *A, const float *B, float *B_split, float *C,
+                               uint32_t spin_limit, int32_t *status_dev, tnet_stream_t stream);
 
 /* ---- tuning (no counterpart in the paper) ---------------------------------
  * Launch-shape knobs of a context: grid sizes, GEMM column tiles and whether

@@ -1589,16 +1589,16 @@ int tnet_kernel_setup(tnet_ctx *c) {
 // Tensor-core GEMM with the column tile chosen from N.
 template <class Epi>
 int tc_any(const tc::TcShape &P, const __nv_bfloat16 *A, int64_t a_rows, int64_t lda, const __nv_bfloat16 *B,
-           int64_t b_rows, int64_t ldb, const Epi &epi, int32_t *status, cudaStream_t st, int bn = 0) {
-    if (bn == 128 && P.N % 128 == 0) return tc::tc_gemm<128>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
-    if (bn == 192 && P.N % 192 == 0) return tc::tc_gemm<192>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
-    if (bn == 256 && P.N % 256 == 0) return tc::tc_gemm<256>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
-    if (P.N <= 32) return tc::tc_gemm<32>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
-    if (P.N <= 64) return tc::tc_gemm<64>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
-    if (P.N <= 128) return tc::tc_gemm<128>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
-    if (P.N % 256 == 0) return tc::tc_gemm<256>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
-    if (P.N % 192 == 0) return tc::tc_gemm<192>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
-    if (P.N % 128 == 0) return tc::tc_gemm<128>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st);
+           int64_t b_rows, int64_t ldb, const Epi &epi, int32_t *status, cudaStream_t st, int sms, int bn = 0) {
+    if (bn == 128 && P.N % 128 == 0) return tc::tc_gemm<128>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st, sms);
+    if (bn == 192 && P.N % 192 == 0) return tc::tc_gemm<192>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st, sms);
+    if (bn == 256 && P.N % 256 == 0) return tc::tc_gemm<256>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st, sms);
+    if (P.N <= 32) return tc::tc_gemm<32>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st, sms);
+    if (P.N <= 64) return tc::tc_gemm<64>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st, sms);
+    if (P.N <= 128) return tc::tc_gemm<128>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st, sms);
+    if (P.N % 256 == 0) return tc::tc_gemm<256>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st, sms);
+    if (P.N % 192 == 0) return tc::tc_gemm<192>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st, sms);
+    if (P.N % 128 == 0) return tc::tc_gemm<128>(P, A, a_rows, lda, B, b_rows, ldb, epi, status, st, sms);
     return TNET_ERR_ARG;
 }
 
@@ -1888,17 +1888,17 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     auto tcx3 = [&](const tc::TcShape &P, const float *A32, int64_t a_rows, int64_t lda, const WOp &w,
                     int64_t b_rows, int64_t ldb, const auto &epi, int bn = 0) -> int {
         const tc::TcOperands o{A32, w.b, w.blo, a_rows, lda, b_rows, ldb};
-        if (P.N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st);
-        if (P.N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st);
-        if (P.N % 192 == 0 && bn != 128) return tc::tc_gemm_ops<192, true>(P, o, epi, status, st);
-        return tc::tc_gemm_ops<128, true>(P, o, epi, status, st);
+        if (P.N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st, sms);
+        if (P.N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st, sms);
+        if (P.N % 192 == 0 && bn != 128) return tc::tc_gemm_ops<192, true>(P, o, epi, status, st, sms);
+        return tc::tc_gemm_ops<128, true>(P, o, epi, status, st, sms);
     };
     // tensor-core GEMM of the mode: BF16 (A's bf16 copy) or 3xTF32 (A itself)
     auto tcg = [&](const tc::TcShape &P, const float *A32, const OpCopy &Acp, int64_t a_rows, int64_t lda,
                    const WOp &w, int64_t b_rows, int64_t ldb, const auto &epi, int bn = 0) -> int {
         if (prec == 1)
             return tc_any(P, (const __nv_bfloat16 *)Acp.p, a_rows, lda, (const __nv_bfloat16 *)w.b, b_rows, ldb,
-                          epi, status, st, bn);
+                          epi, status, st, sms, bn);
         return tcx3(P, A32, a_rows, lda, w, b_rows, ldb, epi, bn);
     };
     TNET_CUDA_TRY(cudaMemsetAsync(sys_start, 0, sizeof(int32_t) * S, st));

@@ -60,20 +60,43 @@ __global__ void k_tf32_split(const float *__restrict__ x, float *__restrict__ hi
     if (t < n) tf32_split(x[t], hi[t], lo[t]);
 }
 
-extern "C" int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const float *B, float *Bsplit, float *Cout,
-                                      int32_t *status, tnet_stream_t stream) {
+// SM count of the current device (the debug entry points have no context)
+static int current_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+static int debug_f32(int M, int N, int K, const float *A, const float *B, float *Bsplit, float *Cout,
+                     int32_t *status, tnet_stream_t stream, uint32_t spin_limit, int skip_mma) {
     if (M < 1 || N < 4 || N > 512 || K < 4 || K % 4 || N % 4 || !A || !B || !Bsplit || !Cout) return TNET_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nk = (int64_t)N * K;
     launch(k_tf32_split, (int)((nk + 255) / 256), 256, 0, st, B, Bsplit, Bsplit + nk, nk);
     TNET_LAUNCH_CHECK();
     tc::TcShape P = tc::tshape(M, N, K);
+    P.spin_limit = spin_limit;
+    P.skip_mma = skip_mma;
     EpiStore epi{Cout, N, 0};
     const tc::TcOperands o{A, Bsplit, Bsplit + nk, M, K, N, K};
-    if (N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st);
-    if (N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st);
-    if (N % 192 == 0) return tc::tc_gemm_ops<192, true>(P, o, epi, status, st);
-    return tc::tc_gemm_ops<128, true>(P, o, epi, status, st);
+    const int sms = current_sms();
+    if (N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st, sms);
+    if (N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st, sms);
+    if (N % 192 == 0) return tc::tc_gemm_ops<192, true>(P, o, epi, status, st, sms);
+    return tc::tc_gemm_ops<128, true>(P, o, epi, status, st, sms);
+}
+
+extern "C" int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const float *B, float *Bsplit, float *Cout,
+                                      int32_t *status, tnet_stream_t stream) {
+    return debug_f32(M, N, K, A, B, Bsplit, Cout, status, stream, 0, 0);
+}
+
+extern "C" int tnet_debug_tc_gemm_timeout(int M, int N, int K, const float *A, const float *B, float *Bsplit,
+                                          float *Cout, uint32_t spin_limit, int32_t *status, tnet_stream_t stream) {
+    if (spin_limit < 1) return TNET_ERR_ARG;
+    return debug_f32(M, N, K, A, B, Bsplit, Cout, status, stream, spin_limit, 1);
 }
 
 extern "C" int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void *B, float *Cout, int32_t *status,
@@ -83,9 +106,10 @@ extern "C" int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void
     EpiStore epi{Cout, N, 0};
     const __nv_bfloat16 *a = (const __nv_bfloat16 *)A, *b = (const __nv_bfloat16 *)B;
     cudaStream_t st = (cudaStream_t)stream;
-    if (N <= 32) return tc::tc_gemm<32>(P, a, M, K, b, N, K, epi, status, st);
-    if (N <= 64) return tc::tc_gemm<64>(P, a, M, K, b, N, K, epi, status, st);
-    if (N <= 128) return tc::tc_gemm<128>(P, a, M, K, b, N, K, epi, status, st);
-    if (N % 192 == 0) return tc::tc_gemm<192>(P, a, M, K, b, N, K, epi, status, st);
-    return tc::tc_gemm<256>(P, a, M, K, b, N, K, epi, status, st);
+    const int sms = current_sms();
+    if (N <= 32) return tc::tc_gemm<32>(P, a, M, K, b, N, K, epi, status, st, sms);
+    if (N <= 64) return tc::tc_gemm<64>(P, a, M, K, b, N, K, epi, status, st, sms);
+    if (N <= 128) return tc::tc_gemm<128>(P, a, M, K, b, N, K, epi, status, st, sms);
+    if (N % 192 == 0) return tc::tc_gemm<192>(P, a, M, K, b, N, K, epi, status, st, sms);
+    return tc::tc_gemm<256>(P, a, M, K, b, N, K, epi, status, st, sms);
 }

@@ -33,6 +33,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace tnet {
@@ -41,6 +43,7 @@ namespace tc {
 constexpr int BM = 128, EPI_WARPS = 16, CONV_WARPS = 2, THREADS = 64 + 32 * (EPI_WARPS + CONV_WARPS);
 constexpr int STG_LD = 20;  // floats per staged row (16 + pad, keeps float4 alignment)
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kMaxDevices = 64;
 
 struct TcShape {
     int M[3];                 // rows per class (capacity when rows_dev is set)
@@ -49,6 +52,11 @@ struct TcShape {
     const int32_t *rows_dev;  // optional device row count (class 0), times rows_mul
     int rows_mul;
     int N, K, nclass;
+    // testing only (zero in every library call): a smaller bound on each
+    // mbarrier wait, and an MMA issuer that issues nothing, so that the
+    // bounded waits run out with no MMA and no unconsumed copy in flight
+    uint32_t spin_limit;
+    int skip_mma;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -64,11 +72,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// bounded wait on the given phase parity; false when the limit ran out or
-// (when given) the CTA's abort flag was raised
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag = nullptr) {
+// bounded wait on the given phase parity; false when the limit (kSpinLimit
+// tries unless `limit` is given) ran out or, when given, the CTA's abort flag
+// was raised
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag = nullptr,
+                                          uint32_t limit = 0) {
     const uint32_t addr = smem_u32(bar);
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    const uint32_t n = limit ? limit : kSpinLimit;
+    for (uint32_t it = 0; it < n; ++it) {
         if (abort_flag && (it & 1023u) == 1023u && *abort_flag) return false;
         uint32_t ok;
         asm volatile(
@@ -180,7 +191,7 @@ struct TileCfg {
     // kernel that programmatic launch brings in early.
     static constexpr int X3_FIT = (int)((232448 - 1024 - 256 - STAGE_BYTES) / (STAGE_TX + A_BYTES));
     static constexpr int STAGES = X3 ? (BN == 128 && X3_FIT >= 5 ? 5 : 4) : (BN >= 192 ? 3 : 4);
-    static_assert(STAGES >= 2 && 8 * (3 * STAGES + 4) + 8 <= 256, "pipeline barriers exceed their block");
+    static_assert(STAGES >= 2 && 8 * (3 * STAGES + 5) + 8 <= 256, "pipeline barriers exceed their block");
     static constexpr size_t SMEM = 1024 + STAGES * (size_t)(STAGE_TX + (X3 ? A_BYTES : 0)) + 256 + STAGE_BYTES;
     static_assert(SMEM <= 232448, "dynamic shared memory above 227 KB");
 };
@@ -223,7 +234,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint64_t *acc_full = empty + STAGES;
     uint64_t *acc_empty = acc_full + 2;
     uint64_t *conv = acc_empty + 2;  // TF32X3: A_lo of the stage is ready
-    uint32_t *tmem_slot = (uint32_t *)(conv + STAGES);
+    uint64_t *drain = conv + STAGES;  // every MMA the issuer started has retired
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     float *stage_all = (float *)((uint8_t *)full + 256);
 
@@ -242,6 +254,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     it.mt2 = (M2 + BM - 1) / BM;
     const int nk = (P.K + BK - 1) / BK;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lim = P.spin_limit;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -253,6 +266,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], EPI_WARPS);
         }
+        mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -269,7 +283,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int t = blockIdx.x; it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x) {
                 for (int kb = 0; kb < nk; ++kb, ++kg) {
                     const int s = kg % STAGES;
-                    if (kg >= STAGES && !mbar_wait(&empty[s], ((kg / STAGES) - 1) & 1, abort_flag)) {
+                    if (kg >= STAGES && !mbar_wait(&empty[s], ((kg / STAGES) - 1) & 1, abort_flag, lim)) {
                         set_status(status, TNET_ERR_TIMEOUT);
                         *abort_flag = 1;
                         break;
@@ -282,17 +296,25 @@ __global__ void __launch_bounds__(THREADS, 1)
                     if (X3) tma_load_2d(sBlo + s * C::B_BYTES, &tmBlo, kb * BK, yb, &full[s]);
                 }
             }
-            for (int k = kg > STAGES ? kg - STAGES : 0; k < kg; ++k)
-                mbar_wait(&full[k % STAGES], (k / STAGES) & 1);  // own copies have landed
+            // own copies must land before the CTA exits: a wait that runs out is
+            // recorded and taken up again (bounded) on the same barrier
+            for (int k = kg > STAGES ? kg - STAGES : 0; k < kg; ++k) {
+                bool landed = false;
+                for (int r = 0; r < 64 && !landed; ++r) {
+                    landed = mbar_wait(&full[k % STAGES], (k / STAGES) & 1, nullptr, lim);
+                    if (!landed) set_status(status, TNET_ERR_TIMEOUT);
+                }
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
             const uint32_t idesc = X3 ? idesc_tf32(BM, BN) : idesc_bf16(BM, BN);
             int kg = 0, lt = 0;
             int z, m0, n0;
-            for (int t = blockIdx.x; it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x, ++lt) {
+            for (int t = blockIdx.x; !P.skip_mma && it.get(t, z, m0, n0, BN) && !*abort_flag;
+                 t += gridDim.x, ++lt) {
                 const int buf = lt & 1;
-                if (lt >= 2 && !mbar_wait(&acc_empty[buf], ((lt >> 1) - 1) & 1, abort_flag)) {
+                if (lt >= 2 && !mbar_wait(&acc_empty[buf], ((lt >> 1) - 1) & 1, abort_flag, lim)) {
                     set_status(status, TNET_ERR_TIMEOUT);
                     *abort_flag = 1;
                     break;
@@ -302,8 +324,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 bool ok = true;
                 for (int kb = 0; kb < nk; ++kb, ++kg) {
                     const int s = kg % STAGES;
-                    if (!mbar_wait(&full[s], (kg / STAGES) & 1, abort_flag) ||
-                        (X3 && !mbar_wait(&conv[s], (kg / STAGES) & 1, abort_flag))) {
+                    if (!mbar_wait(&full[s], (kg / STAGES) & 1, abort_flag, lim) ||
+                        (X3 && !mbar_wait(&conv[s], (kg / STAGES) & 1, abort_flag, lim))) {
                         ok = false;
                         break;
                     }
@@ -333,6 +355,14 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 umma_commit(&acc_full[buf]);
             }
+            // on every path: all MMAs this thread issued retire before the
+            // block frees TMEM (a wait that runs out is taken up again)
+            umma_commit(drain);
+            bool retired = false;
+            for (int r = 0; r < 64 && !retired; ++r) {
+                retired = mbar_wait(drain, 0, nullptr, lim);
+                if (!retired) set_status(status, TNET_ERR_TIMEOUT);
+            }
         }
     } else if (warp >= 2 + EPI_WARPS) {
         if (X3) {  // converters: A -> (A_hi, A_lo) for every stage, in k order
@@ -343,7 +373,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int t = blockIdx.x; ok && it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x) {
                 for (int kb = 0; kb < nk; ++kb, ++kg) {
                     const int s = kg % STAGES;
-                    if (!mbar_wait(&full[s], (kg / STAGES) & 1, abort_flag)) {
+                    if (!mbar_wait(&full[s], (kg / STAGES) & 1, abort_flag, lim)) {
                         ok = false;
                         break;
                     }
@@ -382,7 +412,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         int z, m0, n0;
         for (int t = blockIdx.x; it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x, ++lt) {
             const int buf = lt & 1;
-            if (!mbar_wait(&acc_full[buf], (lt >> 1) & 1, abort_flag)) {
+            if (!mbar_wait(&acc_full[buf], (lt >> 1) & 1, abort_flag, lim)) {
                 set_status(status, TNET_ERR_TIMEOUT);
                 *abort_flag = 1;
                 break;
@@ -453,8 +483,27 @@ struct TcOperands {
     int64_t a_rows, lda, b_rows, ldb;
 };
 
+// cudaFuncSetAttribute(kernel, MaxDynamicSharedMemorySize) once per device
+// and kernel instantiation (the attribute is per device)
+template <class Kern>
+int ensure_smem_attr(Kern kernel, int bytes) {
+    static std::mutex mu;
+    static bool done[kMaxDevices] = {};
+    int dev = 0;
+    TNET_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return TNET_ERR_ARG;
+    std::lock_guard<std::mutex> g(mu);
+    if (!done[dev]) {
+        TNET_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        done[dev] = true;
+    }
+    return TNET_OK;
+}
+
+// Launches one persistent GEMM: min(tiles, sms) CTAs, one per SM (`sms` is
+// the SM count of the device the stream runs on).
 template <int BN, bool X3, class Epi>
-int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *status, cudaStream_t st) {
+int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *status, cudaStream_t st, int sms) {
     using C = TileCfg<BN, X3>;
     const int esz = X3 ? 4 : 2;
     int maxM = 0;
@@ -476,21 +525,10 @@ int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *
         mal = ma;
         mbl = mb;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        TNET_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<BN, Epi, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)C::SMEM));
-        attr_set = true;
-    }
+    if ((rc = ensure_smem_attr(k_tc_gemm<BN, Epi, X3>, (int)C::SMEM))) return rc;
     int64_t tiles = 0;
     for (int z = 0; z < P.nclass; ++z) tiles += (int64_t)((P.M[z] + BM - 1) / BM) * ((P.N + BN - 1) / BN);
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+    if (sms < 1) sms = 1;
     const int grid = (int)(tiles < sms ? tiles : sms);
     launch(k_tc_gemm<BN, Epi, X3>, grid, THREADS, C::SMEM, st, ma, mb, mal, mbl, P, epi, status);
     count_launch();
@@ -500,8 +538,8 @@ int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *
 
 template <int BN, class Epi>
 int tc_gemm(const TcShape &P, const __nv_bfloat16 *A, int64_t a_rows, int64_t lda, const __nv_bfloat16 *B,
-            int64_t b_rows, int64_t ldb, const Epi &epi, int32_t *status, cudaStream_t st) {
-    return tc_gemm_ops<BN, false>(P, TcOperands{A, B, nullptr, a_rows, lda, b_rows, ldb}, epi, status, st);
+            int64_t b_rows, int64_t ldb, const Epi &epi, int32_t *status, cudaStream_t st, int sms) {
+    return tc_gemm_ops<BN, false>(P, TcOperands{A, B, nullptr, a_rows, lda, b_rows, ldb}, epi, status, st, sms);
 }
 
 inline TcShape tshape(int M, int N, int K) {

@@ -70,3 +70,37 @@ def test_tc_gemm_3xtf32_matches_fp64(M, N, K):
     # typical error: at the FP32 accumulation floor (a split that went wrong,
     # e.g. a residual from another tile, shows up near 1e-4)
     assert rel.pow(2).mean().sqrt().item() <= 3e-7, rel.pow(2).mean().sqrt().item()
+
+
+def test_bounded_waits_report_timeout_and_leave_the_context_usable():
+    """The failure path of the tensor-core kernel, made to happen without a
+    fault: the 3xTF32 GEMM runs with its MMA issuer told to issue nothing and
+    every mbarrier wait limited to 4096 tries.  The tile loads land and nobody
+    consumes them, so the waits run out: the kernel records TIMEOUT (6) in the
+    status word, waits for its own copies, frees its tensor memory and
+    returns without writing C.  A normal GEMM on the same stream afterwards
+    runs and is accurate."""
+    M, N, K = 1000, 128, 256
+    g = torch.Generator(device="cpu").manual_seed(2)
+    A = torch.randn(M, K, generator=g).cuda()
+    B = torch.randn(N, K, generator=g).cuda()
+    Bsplit = torch.empty(2 * N * K, dtype=torch.float32, device="cuda")
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lib = _lib.load()
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.tnet_debug_tc_gemm_timeout(M, N, K, p(A), p(B), p(Bsplit), p(C), 0, p(st), stream) == 1
+    rc = lib.tnet_debug_tc_gemm_timeout(M, N, K, p(A), p(B), p(Bsplit), p(C), 4096, p(st), stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 6
+    assert torch.isnan(C).all()
+    st.zero_()
+    rc = lib.tnet_debug_tc_gemm_f32(M, N, K, p(A), p(B), p(Bsplit), p(C), p(st), stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = A.double() @ B.double().T
+    rel = (C.double() - ref).abs() / (A.double().abs() @ B.double().abs().T)
+    assert rel.max().item() <= 3 * 2.0 ** -22 + K * 2.0 ** -24
