@@ -25,7 +25,7 @@ constexpr int kNoAllocMaxAtoms = 16384;
 constexpr int kNoAllocMaxSystems = 1024;
 constexpr size_t kNoAllocScratchBytes = 2u << 20;  // 2 MiB per GPU
 
-__device__ __align__(256) char g_noalloc_scratch[kNoAllocScratchBytes];
+static __device__ __align__(256) char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
@@ -68,15 +68,16 @@ extern "C" int tnet_neighbors_noalloc(int n_atoms, int n_systems, const float *p
     int rc = scratch_address(&scratch);
     if (rc) return rc;
     // a host-side context whose workspace is the static array, laid out for
-    // the fixed maximum sizes; only the neighbor-search part is used
+    // this call's sizes (so the zeroing and scans scale with the input, not
+    // with the limits); only the neighbor-search part is used
     tnet_ctx c;
     memset(&c, 0, sizeof c);
     c.d = tnet_model_desc{64, 8, 0, 1, cutoff, 0.f, 0};
-    rc = build_layout(&c.d, kNoAllocMaxAtoms, kNoAllocMaxSystems, 0, &c.lay);
+    rc = build_layout(&c.d, n_atoms, n_systems, 0, &c.lay);
     if (rc) return rc;
     if (c.lay.rev > kNoAllocScratchBytes) return TNET_ERR_WORKSPACE;
-    c.max_atoms = kNoAllocMaxAtoms;
-    c.max_systems = kNoAllocMaxSystems;
+    c.max_atoms = n_atoms;
+    c.max_systems = n_systems;
     c.max_pairs = cap;
     c.ws = (char *)scratch;
     c.ws_bytes = kNoAllocScratchBytes;

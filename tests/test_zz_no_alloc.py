@@ -72,13 +72,21 @@ def test_noalloc_matches_context_entry_point_twice_in_a_row():
         assert torch.equal(col[:n], ref.col[:n])
 
 
-def test_noalloc_rejects_sizes_beyond_its_limit():
+@pytest.mark.parametrize("n_atoms,n_systems", [(20000, 1), (2000, 1025)])
+def test_noalloc_rejects_sizes_beyond_its_limit(n_atoms, n_systems):
+    """Beyond 16,384 atoms or 1,024 systems the call returns WORKSPACE (7) at
+    once and enqueues nothing: the outputs keep their sentinels."""
     lib = _lib.load()
-    pos = torch.from_numpy(np.random.default_rng(1).uniform(0, 60, (20000, 3)).astype(np.float32)).to(DEV)
-    out = torch.empty(20001, dtype=torch.int32, device=DEV)
-    col = torch.empty(16, dtype=torch.int32, device=DEV)
-    npairs = torch.zeros(1, dtype=torch.int64, device=DEV)
-    status = torch.zeros(1, dtype=torch.int32, device=DEV)
-    rc = lib.tnet_neighbors_noalloc(20000, 1, _p(pos), None, None, ctypes.c_float(5.0), _p(out), _p(col), 16,
-                                    _p(npairs), _p(status), None)
+    rng = np.random.default_rng(1)
+    pos = torch.from_numpy(rng.uniform(0, 60, (n_atoms, 3)).astype(np.float32)).to(DEV)
+    batch = torch.from_numpy(np.sort(rng.integers(0, n_systems, n_atoms)).astype(np.int32)).to(DEV)
+    out = torch.full((n_atoms + 1,), -3, dtype=torch.int32, device=DEV)
+    col = torch.full((16,), -5, dtype=torch.int32, device=DEV)
+    npairs = torch.full((1,), -9, dtype=torch.int64, device=DEV)
+    status = torch.full((1,), -11, dtype=torch.int32, device=DEV)
+    rc = lib.tnet_neighbors_noalloc(n_atoms, n_systems, _p(pos), _p(batch), None, ctypes.c_float(5.0), _p(out),
+                                    _p(col), 16, _p(npairs), _p(status), None)
     assert rc == 7
+    torch.cuda.synchronize()
+    assert bool((out == -3).all()) and bool((col == -5).all())
+    assert int(npairs.item()) == -9 and int(status.item()) == -11
