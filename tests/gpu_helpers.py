@@ -11,6 +11,10 @@ from paper_2402_17660_gb300.tnet import TensorNet
 RC = 5.0
 E_TOL = 1e-5   # |dE_s| <= E_TOL * max(|E_s|, sum_i |E_i|)
 F_TOL = 1e-4   # RMS_i |dF_i| <= F_TOL * RMS_i |F_i|
+F_MAX_TOL = 2e-3   # max_i |dF_i| <= F_MAX_TOL * RMS_i |F_i| (the worst atom)
+BF16_E_TOL = 1e-2
+BF16_F_TOL = 1e-2
+BF16_F_MAX_TOL = 1e-1
 
 DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
 
@@ -82,4 +86,14 @@ def energy_errors(E, Es, Ei, batch):
 
 
 def force_error(F, Fo):
+    """RMS_i |F_i - Fo_i| / RMS_i |Fo_i|."""
     return np.sqrt(np.mean(np.sum((F - Fo) ** 2, 1))) / np.sqrt(np.mean(np.sum(Fo ** 2, 1)))
+
+
+def force_errors(F, Fo):
+    """(RMS_i |dF_i|, max_i |dF_i|), both relative to RMS_i |Fo_i|."""
+    F = np.asarray(F, np.float64)
+    Fo = np.asarray(Fo, np.float64)
+    d = np.sqrt(np.sum((F - Fo) ** 2, 1))
+    rms = np.sqrt(np.mean(np.sum(Fo ** 2, 1)))
+    return float(np.sqrt(np.mean(d * d)) / rms), float(d.max() / rms)

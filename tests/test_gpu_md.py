@@ -1,6 +1,11 @@
-"""GPU checks of tnet_md_step: one step equals a hand-assembled velocity
-Verlet step built from tnet_energy_forces, graph replays equal the eager
-path bit for bit, and the total energy is conserved over a short run."""
+"""GPU checks of tnet_md_step: five steps follow a velocity-Verlet
+trajectory driven by the FP64 oracle's forces (stored in tests/golden by
+make_oracle_refs.py, which calls only the oracle); one step equals a
+hand-assembled velocity Verlet step built from tnet_energy_forces; graph
+replays equal the eager path bit for bit; the total energy is conserved over
+a short run."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -45,6 +50,37 @@ def test_one_step_matches_velocity_verlet(name):
     assert abs(ep[0].item() - E1[0]) <= 1e-5 * abs(E1[0]) + 1e-3
     ke = 0.5 * np.sum(np.sum(v1.cpu().numpy().astype(np.float64) ** 2, 1) / (1.0 / s.masses())) / ACC
     assert abs(ek[0].item() - ke) <= 1e-6 * ke
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_md_follows_the_oracle_trajectory(prec):
+    """Water3000, Maxwell-Boltzmann velocities at 300 K, 0.5 fs steps, list at
+    cutoff + 1 A skin: after five steps of tnet_md_step (FP32 state) every
+    position is within 1e-5 A and every velocity within 1e-4 of the RMS
+    velocity of the FP64 oracle's trajectory; per-step potential energies
+    within 1e-5 relative, kinetic energies within 1e-6."""
+    d = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_md_water3000.npz"))
+    wv = np.concatenate([np.asarray(W[k], np.float64).ravel() for k, _ in synth.param_spec(synth.ModelShape())])
+    assert np.allclose([wv.sum(), (wv * wv).sum()], d["weights_checksum"], rtol=1e-13, atol=0)
+    s = synth.System("water3000", d["z"].astype(np.int32), d["pos0"], np.zeros(len(d["z"]), np.int32), d["box"], 1)
+    from paper_2402_17660_gb300.tnet import TensorNet
+    m = TensorNet(W, max_atoms=s.n_atoms, max_systems=1, max_pairs=300000, precision=prec, device=DEV)
+    z, pos, _, box = to_dev(s)
+    vel = torch.from_numpy(d["vel0"]).to(DEV)
+    inv_m = torch.from_numpy(1.0 / s.masses()).to(DEV)
+    n = int(d["steps"])
+    m.reset_status()
+    ek, ep = m.md(z, inv_m, pos, vel, box, float(d["dt"]), 1.0, 20, n)
+    torch.cuda.synchronize()
+    m.check_status("md")
+    dx = np.abs(pos.cpu().numpy().astype(np.float64) - d["pos"]).max()
+    v_rms = np.sqrt(np.mean(np.sum(d["vel"] ** 2, 1)))
+    dv = np.sqrt(np.sum((vel.cpu().numpy().astype(np.float64) - d["vel"]) ** 2, 1)).max() / v_rms
+    de = np.abs(ep.cpu().numpy() - d["e_pot"]).max() / np.abs(d["e_pot"]).max()
+    dk = np.abs(ek.cpu().numpy() - d["e_kin"]).max() / np.abs(d["e_kin"]).max()
+    print(f"md vs oracle (precision {prec}): max |dx| {dx:.2e} A, max |dv| {dv:.2e} of RMS v, E_pot {de:.2e}, "
+          f"E_kin {dk:.2e}")
+    assert dx <= 1e-5 and dv <= 1e-4 and de <= 1e-5 and dk <= 1e-6
 
 
 def test_graph_replay_equals_eager():

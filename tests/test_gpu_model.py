@@ -10,8 +10,9 @@ from oracle.neighbors import neighbor_pairs
 from paper_2402_17660_gb300 import synth
 from paper_2402_17660_gb300.tnet import EnergyFn, NeighborList, TensorNet
 
-from .gpu_helpers import (DEV, E_TOL, F_TOL, RC, energy_errors, force_error, gpu_energy_forces, gpu_pairs,
-                          make_model, margin_ok, oracle_energy_forces, to_dev)
+from .gpu_helpers import (BF16_F_MAX_TOL, BF16_F_TOL, DEV, E_TOL, F_MAX_TOL, F_TOL, RC, energy_errors,
+                          force_error, force_errors, gpu_energy_forces, gpu_pairs, make_model, margin_ok,
+                          oracle_energy_forces, to_dev)
 
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
 
@@ -24,10 +25,11 @@ def _compare(sys, shape=SHAPE, weights=W, seed=None):
     E, F = gpu_energy_forces(m, sys, seed=seed)
     Es, Ei, Fo = oracle_energy_forces(weights, sys, shape, seed=seed)
     e_err = energy_errors(E, Es, Ei, sys.batch)
-    f_err = force_error(F, Fo)
-    print(f"{sys.name}: N={sys.n_atoms} max rel energy err {e_err.max():.2e}, rel RMS force err {f_err:.2e}")
+    f_err, f_max = force_errors(F, Fo)
+    print(f"{sys.name}: N={sys.n_atoms} max rel energy err {e_err.max():.2e}, rel RMS force err {f_err:.2e}, "
+          f"worst atom {f_max:.2e}")
     assert np.all(e_err <= E_TOL), e_err
-    assert f_err <= F_TOL, f_err
+    assert f_err <= F_TOL and f_max <= F_MAX_TOL, (f_err, f_max)
     return m, E, F
 
 
@@ -95,9 +97,9 @@ def test_paper_shape_molecule_cutoff_4_5(L):
     m = make_model(Wl, s, shape=shape, cutoff=4.5)
     E, F = gpu_energy_forces(m, s, cutoff=4.5)
     Es, Ei, Fo = oracle_energy_forces(Wl, s, shape)
-    e_err, f_err = energy_errors(E, Es, Ei, s.batch), force_error(F, Fo)
-    print(f"walk166 L={L}: rel energy err {e_err.max():.2e}, rel RMS force err {f_err:.2e}")
-    assert np.all(e_err <= E_TOL) and f_err <= F_TOL
+    e_err, (f_err, f_max) = energy_errors(E, Es, Ei, s.batch), force_errors(F, Fo)
+    print(f"walk166 L={L}: rel energy err {e_err.max():.2e}, rel RMS force err {f_err:.2e}, worst atom {f_max:.2e}")
+    assert np.all(e_err <= E_TOL) and f_err <= F_TOL and f_max <= F_MAX_TOL
 
 
 def test_triclinic_water():
@@ -263,7 +265,8 @@ def _compare_weight_grads(sys, shape=SHAPE, weights=W, seed=None):
     o = Oracle(weights, F=shape.F, K=shape.K, L=shape.L)
     _, _, Fo, Go = o.energy_forces(sys.z, sys.pos, sys.batch, sys.box, n_systems=sys.n_systems, want_weights=True,
                                    seed=seed)
-    assert force_error(F.cpu().numpy(), Fo) <= F_TOL
+    f_err, f_max = force_errors(F.cpu().numpy(), Fo)
+    assert f_err <= F_TOL and f_max <= F_MAX_TOL, (f_err, f_max)
     worst = 0.0
     for k in Go:
         ref = Go[k]
@@ -310,7 +313,8 @@ def test_autograd_function_weights():
 
 
 # --------------------------------------------------------------- BF16 mode ---
-BF16_F_TOL = 1e-2   # BF16 tensor-core GEMMs: RMS force error <= 1e-2 of the RMS force
+# BF16 tensor-core GEMMs: RMS force error <= 1e-2 of the RMS force (BF16_F_TOL),
+# worst atom <= 1e-1 of it (BF16_F_MAX_TOL)
 
 
 def _make_bf16(sys, weights=W, shape=SHAPE, max_pairs=None):
@@ -328,10 +332,11 @@ def test_bf16_mode_against_oracle(name):
     E32, F32 = gpu_energy_forces(m32, s)
     Es, Ei, Fo = oracle_energy_forces(W, s)
     e_err = energy_errors(Eb, Es, Ei, s.batch).max()
-    f_err = force_error(Fb, Fo)
+    f_err, f_max = force_errors(Fb, Fo)
     f_err32 = force_error(Fb, F32)
-    print(f"{name} BF16: rel energy err {e_err:.2e}, rel RMS force err vs oracle {f_err:.2e}, vs FP32 {f_err32:.2e}")
-    assert f_err <= BF16_F_TOL and f_err32 <= BF16_F_TOL
+    print(f"{name} BF16: rel energy err {e_err:.2e}, rel RMS force err vs oracle {f_err:.2e} (worst atom "
+          f"{f_max:.2e}), vs FP32 {f_err32:.2e}")
+    assert f_err <= BF16_F_TOL and f_err32 <= BF16_F_TOL and f_max <= BF16_F_MAX_TOL
     assert e_err <= 1e-2
 
 
@@ -398,9 +403,9 @@ def test_tf32x3_mode_meets_fp32_tolerances(name):
     E, F = gpu_energy_forces(m, s)
     Es, Ei, Fo = oracle_energy_forces(W, s)
     e_err = energy_errors(E, Es, Ei, s.batch).max()
-    f_err = force_error(F, Fo)
-    print(f"{name} 3xTF32: rel energy err {e_err:.2e}, rel RMS force err {f_err:.2e}")
-    assert e_err <= E_TOL and f_err <= F_TOL
+    f_err, f_max = force_errors(F, Fo)
+    print(f"{name} 3xTF32: rel energy err {e_err:.2e}, rel RMS force err {f_err:.2e}, worst atom {f_max:.2e}")
+    assert e_err <= E_TOL and f_err <= F_TOL and f_max <= F_MAX_TOL
 
 
 def test_tf32x3_mode_batch_and_weight_grads():
@@ -416,7 +421,8 @@ def test_tf32x3_mode_batch_and_weight_grads():
     m.check_status("3xtf32")
     Es, Ei, Fo, Go = Oracle(W).energy_forces(s.z, s.pos, s.batch, None, n_systems=s.n_systems, want_weights=True)
     assert np.all(energy_errors(E.cpu().numpy(), Es, Ei, s.batch) <= E_TOL)
-    assert force_error(Fg.cpu().numpy(), Fo) <= F_TOL
+    f_err, f_max = force_errors(Fg.cpu().numpy(), Fo)
+    assert f_err <= F_TOL and f_max <= F_MAX_TOL, (f_err, f_max)
     Gg = unpack_weights(G.cpu().numpy(), 128, 32, 2, 100)
     for k in Go:
         rms = np.sqrt(np.mean(Go[k] ** 2))
