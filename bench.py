@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--neighbor-bench", action="store_true",
                     help="neighbor search alone: 32,768-particle random cloud (64 neighbors per particle) split "
                          "into 1..1024 systems (one JSON line)")
+    ap.add_argument("--neighbor-stress", action="store_true",
+                    help="neighbor search alone on the 1,029,000-atom periodic water box at 5 and 6 A "
+                         "(one JSON line)")
     ap.add_argument("--radial-table", type=int, default=0,
                     help="n > 0: tabulate the radial projections and filters at n distances (inference "
                          "mode; cubic Hermite interpolation per pair)")
@@ -290,15 +293,19 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ ours ---
-def stage_work(tag, nu, N, E, F, K, prec, table=0):
+def stage_work(tag, nu, N, E, F, K, prec, table=0, rec=False):
     """Algorithmic work of one instance of a timed stage: (FLOP, bytes, engine).
     Bytes count each unique operand read once and each result written once,
     including the bf16 operand copies the BF16 mode writes beside a result
     (2 B per element; the 3xTF32 mode writes none: it splits its operands in
-    shared memory).  table = n > 0: tabulated radial functions, whose
-    [n-1][3F] float4 tables are read once per launch (they stay in L2; at most
-    one interval per pair) in place of the per-pair f, g and a3 arrays, and
-    whose radial-MLP stages do not run."""
+    shared memory).  The radial filter g = phi SiLU(a3) is never stored: the
+    last radial layer writes a3 alone and the message kernels read a3 and phi.
+    rec (activations recomputed in the reverse pass): the forward instances
+    of radial layers 1 and 2 write no pre-activation, the reverse-pass
+    instances do; the figure is the mean over the two.  table = n > 0:
+    tabulated radial functions, whose [n-1][3F] float4 tables are read once
+    per launch (they stay in L2; at most one interval per pair) in place of
+    the per-pair f and a3 arrays, and whose radial-MLP stages do not run."""
     f = 4.0
     bf16 = prec == "bf16"
     cp = 2.0 if bf16 else 0.0            # operand-copy bytes per element
@@ -318,12 +325,14 @@ def stage_work(tag, nu, N, E, F, K, prec, table=0):
             return 4.0 * 9 * F * 2 * nu + 2.0 * 3 * F * nu + hermite, rd + wr, "hbm"
         if tag.startswith("mlp"):
             return None
+    pre = 0.5 if rec else 1.0            # share of instances that store the pre-activation
+    hw = (f if not bf16 else 0.0) + cp   # bytes stored per activation element (fp32 unless BF16 copies only)
     if tag == "mlp1":
-        return 2.0 * nu * K * F, nu * (K * f + F * f + F * hb), "alu"
+        return 2.0 * nu * K * F, nu * (K * f + pre * F * f + F * hw), "alu"
     if tag == "mlp2":
-        return 2.0 * nu * F * 2 * F, nu * (F * hb + 2 * F * f + 2 * F * hb), "tensor" if bf16 else "alu"
+        return 2.0 * nu * F * 2 * F, nu * (F * hb + pre * 2 * F * f + 2 * F * hw), "tensor" if bf16 else "alu"
     if tag == "mlp3":
-        return 2.0 * nu * 2 * F * 3 * F, nu * (2 * F * hb + 2 * 3 * F * f), "tensor" if bf16 else "alu"
+        return 2.0 * nu * 2 * F * 3 * F, nu * (2 * F * hb + 3 * F * f), "tensor" if bf16 else "alu"
     if tag == "mlp3_bwd":
         return 2.0 * nu * 3 * F * 2 * F, nu * (3 * F * hb + 2 * F * f + 2 * F * f + (2 * F * 2 if bf16 else 0)), \
             "tensor" if bf16 else "alu"
@@ -339,12 +348,12 @@ def stage_work(tag, nu, N, E, F, K, prec, table=0):
         # dE/de)
         return 2.0 * 40 * F * 2 * nu + 2.0 * nu * 3 * F * K, \
             f * (9 * N * F + 6 * F * nu) + 16.0 * E + nu * (3 * F * f + 2 * K * f), "hbm"
-    if tag == "message":     # read Y and the pair filters once, write M once, read the CSR
-        return 2.0 * 9 * F * 2 * nu, f * (2 * 9 * N * F + 3 * F * nu) + 8.0 * E, "hbm"
+    if tag == "message":     # read Y, a3 and phi once, write M once, read the CSR
+        return 2.0 * 9 * F * 2 * nu, f * (2 * 9 * N * F + 3 * F * nu + nu) + 8.0 * E, "hbm"
     if tag == "message_bwd":
-        # read Y, gM, gY, the filters g, a3 and phi; write gY (+ copy), dE/da3
-        # (fp32 unless bf16, + copy) and update dE/dphi; read the CSR
-        rd = f * (3 * 9 * N * F + 2 * 3 * F * nu + nu) + 8.0 * E
+        # read Y, gM, gY, a3 and phi; write gY (+ copy), dE/da3 (fp32 unless
+        # bf16, + copy) and update dE/dphi; read the CSR
+        rd = f * (3 * 9 * N * F + 3 * F * nu + nu) + 8.0 * E
         wr = (f + cp) * 9 * N * F + ((0.0 if bf16 else f) + cp) * 3 * F * nu + 2 * f * nu
         return 4.0 * 9 * F * 2 * nu + 6.0 * 3 * F * nu, rd + wr, "hbm"
     return None
@@ -483,10 +492,11 @@ def run_ours(args):
     x3 = args.precision == "tf32x3"
     tab = args.radial_table > 0
     work_tags = [k for k in sorted(stages, key=lambda k: -stages[k]["ms_per_step"])
-                 if stage_work(k, nu, N, n_pairs, F_, shape.K, args.precision, args.radial_table) is not None]
+                 if stage_work(k, nu, N, n_pairs, F_, shape.K, args.precision, args.radial_table, rec) is not None]
     if work_tags:
         tag = work_tags[0]
-        flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, args.precision, args.radial_table)
+        flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, args.precision, args.radial_table,
+                                           rec)
         if x3 and not tab and tag in ("mlp2", "mlp3", "mlp3_bwd", "mlp2_bwd"):
             # 3xTF32: three TF32 MMAs per product (the residuals are formed in
             # shared memory, so the bytes are those of the fp32 operands)
@@ -850,6 +860,53 @@ def run_neighbor_bench(args):
     return 0
 
 
+def run_neighbor_stress(args):
+    """tnet_neighbors alone on the 1,029,000-atom periodic water box (a 70^3
+    lattice of waters at 1 g/cm^3, 217.28 A cube) at the 5 A cutoff and at
+    5 + 1 A skin: the size at which the search's algorithmic bytes exceed
+    L2, so its HBM fraction can be read."""
+    import torch
+    from paper_2402_17660_gb300 import synth
+    from paper_2402_17660_gb300.tnet import TensorNet
+    dev = torch.device("cuda:0")
+    t0 = time.perf_counter()
+    s = synth.million_water_box()
+    gen_s = time.perf_counter() - t0
+    N = s.n_atoms
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = json.load(open(peaks_path)).get("hbm_gbs", 6800.0) if os.path.exists(peaks_path) else 6800.0
+    # a context whose workspace holds no per-pair radial-MLP activations: the
+    # search does not depend on the model
+    shape = synth.ModelShape(F=64, K=8, L=0)
+    m = TensorNet(synth.init_weights(shape, seed=0), F=64, K=8, L=0, max_atoms=N, max_systems=1,
+                  max_pairs=100 * N, device=dev, radial_table=256)
+    pos = torch.from_numpy(s.pos).to(dev)
+    box = torch.from_numpy(s.box).to(dev)
+    rows = []
+    for rc in (5.0, 6.0):
+        nl = m.neighbors(pos, None, box, 1, cutoff=rc)
+        torch.cuda.synchronize()
+        m.check_status("neighbor stress")
+        npairs = int(nl.n_pairs.item())
+        ms = graph_ms(lambda: m.neighbors(pos, None, box, 1, cutoff=rc, out=nl), max(args.steps, 20),
+                      max(args.warmup, 5))
+        m.check_status("neighbor stress")
+        # algorithmic bytes: positions, row offsets, one int per pair, and the
+        # cell sort (cell index + sorted index + float4 copy per atom)
+        nbytes = N * (12 + 4 + 2 * (4 + 4 + 16)) + 4 * npairs
+        rows.append({"cutoff_A": rc, "pairs": npairs, "pairs_per_atom": npairs / N, "ms_per_call": ms,
+                     "Gpairs_per_s": npairs / ms / 1e6, "algorithmic_bytes": nbytes,
+                     "hbm_GBs_algorithmic": nbytes / ms / 1e6, "hbm_frac_of_measured": nbytes / ms / 1e6 / hbm})
+    line = {"metric": "tnet_neighbors on the 1,029,000-atom periodic water box", "unit": "ms",
+            "data": f"synthetic: 343,000 rigid waters on a jittered 70^3 lattice, 217.28 A cube (generated in "
+                    f"{gen_s:.0f} s on the host)",
+            "config": {"atoms": N, "step": "one tnet_neighbors call in a CUDA graph", "l2": "not flushed",
+                       "hbm_peak_GBs": hbm},
+            "rows": rows}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -858,6 +915,8 @@ def main():
         return run_sweep(args)
     if args.neighbor_bench:
         return run_neighbor_bench(args)
+    if args.neighbor_stress:
+        return run_neighbor_stress(args)
     return run_ours(args)
 
 

@@ -263,6 +263,17 @@ __device__ __forceinline__ void mm3_nt(const float A[9], const float B[9], float
             C[3 * r + c] = A[3 * r] * B[3 * c] + A[3 * r + 1] * B[3 * c + 1] + A[3 * r + 2] * B[3 * c + 2];
 }
 
+// Barrier of the F threads of row group g of a block holding RB groups
+// (named barrier 1 + g; barrier 0 is __syncthreads); the whole block when RB = 1.
+template <int F, int RB>
+__device__ __forceinline__ void group_sync(int g) {
+    if constexpr (RB == 1) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "n"(F) : "memory");
+    }
+}
+
 // SiLU and its derivative (fast-math exp and divide: a few ulp, far inside
 // the FP32 path's error budget)
 __device__ __forceinline__ float silu_f(float x) { return __fdividef(x, 1.0f + __expf(-x)); }
@@ -354,7 +365,7 @@ struct Layout {
     size_t Xin, qn, Xn, Y, M, Tn, dX;  // per layer (stride given below)
     size_t Xfin, h, hn, lno, ao, o, at, t, Ei;
     // edge MLP (undirected active edges)
-    size_t eu, phiu, geo, a1, h1, a2, h2, a3, g;
+    size_t eu, phiu, geo, a1, h1, a2, h2, a3;
     // backward
     size_t gXa, gXb, gdX, gTn, gM, gY, gat, gao, ghn, gh, gU, gas2, gas1, gn0, gq0, gg, ga2, ga1, ge,
         gphiu, gvec;
@@ -389,7 +400,7 @@ void count_launch();
 // Tuning knobs: 0 SIMT-GEMM CTAs per SM, 1 tcgen05 column tile for N = 3F,
 // 2 tcgen05 column tile for N = 2F, 3 row-kernel blocks per SM, 4 pair-kernel
 // blocks (256 threads) per SM, 5 programmatic dependent launch on (1) or off.
-enum TuneKnob { T_GEMM_CTAS = 0, T_TC_BN_3F, T_TC_BN_2F, T_ROW_BLOCKS, T_PAIR_BLOCKS, T_PDL, T_NKNOBS };
+enum TuneKnob { T_GEMM_CTAS = 0, T_TC_BN_3F, T_TC_BN_2F, T_ROW_BLOCKS, T_PAIR_BLOCKS, T_PDL, T_ROWS_PER_BLOCK, T_NKNOBS };
 
 enum ProfTag {
     P_NBR = 0, P_PREP, P_EMB_EDGE, P_EMB_NODE, P_MLP1, P_MLP2, P_MLP3, P_MESSAGE, P_NODE_MIX,

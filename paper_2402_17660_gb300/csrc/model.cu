@@ -623,27 +623,40 @@ __global__ void k_node_norm(const float *__restrict__ X, int N, int F, float *__
 }
 
 // M_i = sum_j g^p_ij Y^p_j over the row (block = F threads, thread = channel).
-// g of pair u is stored plane-major, g[u][p][c], so each of its three loads is
-// one coalesced F-channel row.  The row's pair and column indices are staged in
+// The filter is never stored: g = phi(d) SiLU(a3) is formed here from the last
+// radial layer's pre-activation a3 of pair u, stored plane-major, a3[u][p][c],
+// so each of its three loads is one coalesced F-channel row, and phi of the
+// pair (the same expression as the GEMM epilogue would evaluate).  The row's pair and column indices are staged in
 // shared memory (one coalesced load per chunk of kChunk edges), so each group of
 // kMU edges waits for one round of gathers, not for its indices first; the
 // sums still run in row order.  F is a template parameter so the coordinate
 // offsets are immediates.
-template <int F, bool TAB>
-__global__ void __launch_bounds__(F) k_message(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                                               const int32_t *__restrict__ pair_of, const float *__restrict__ gU,
-                                               TabFn tg, const float *__restrict__ Y, int N, float *__restrict__ M) {
+//
+// RB consecutive rows per block, one group of F threads per row (named
+// barrier 1 + group): consecutive atoms share most of their neighbours (the
+// three atoms of a water, the next molecule of the lattice), so the groups of
+// a block gather mostly the same rows of Y at about the same time (columns
+// ascend in every row) and the repeats hit the SM's L1 instead of L2.
+template <int F, bool TAB, int RB>
+__global__ void __launch_bounds__(F * RB, (768 / (F * RB)) > 0 ? 768 / (F * RB) : 1)
+    k_message(const int32_t *__restrict__ row_ptr,
+                                                    const int32_t *__restrict__ col,
+                                                    const int32_t *__restrict__ pair_of, const float *__restrict__ a3,
+                                                    const float *__restrict__ phiu, TabFn tg,
+                                                    const float *__restrict__ Y, int N, float *__restrict__ M) {
     pdl_entry();
-    __shared__ int32_t s_u[kChunk], s_j[kChunk];
-    __shared__ int32_t s_kt[TAB ? kChunk : 1];
-    __shared__ float s_st[TAB ? kChunk : 1];
-    const int c = threadIdx.x;
-    for (int i = blockIdx.x; i < N; i += gridDim.x) {
+    __shared__ int32_t s_u_all[RB][kChunk], s_j_all[RB][kChunk];
+    __shared__ int32_t s_kt_all[RB][TAB ? kChunk : 1];
+    __shared__ float s_st_all[RB][TAB ? kChunk : 1];
+    const int grp = RB > 1 ? (int)threadIdx.x / F : 0, c = RB > 1 ? (int)threadIdx.x % F : (int)threadIdx.x;
+    int32_t *s_u = s_u_all[grp], *s_j = s_j_all[grp], *s_kt = s_kt_all[grp];
+    float *s_st = s_st_all[grp];
+    for (int i = blockIdx.x * RB + grp; i < N; i += gridDim.x * RB) {
         float m[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
         for (int cb = e0; cb < e1; cb += kChunk) {
             const int n = e1 - cb < kChunk ? e1 - cb : kChunk;
-            __syncthreads();  // the previous chunk is consumed
+            group_sync<F, RB>(grp);  // the previous chunk is consumed
             for (int t = c; t < n; t += F) {
                 const int u = pair_of[cb + t];
                 s_u[t] = u;
@@ -656,7 +669,7 @@ __global__ void __launch_bounds__(F) k_message(const int32_t *__restrict__ row_p
                     s_st[t] = st;
                 }
             }
-            __syncthreads();
+            group_sync<F, RB>(grp);
             for (int k0 = 0; k0 < n; k0 += kMU) {
                 int uu[kMU], jj[kMU];
 #pragma unroll
@@ -664,7 +677,7 @@ __global__ void __launch_bounds__(F) k_message(const int32_t *__restrict__ row_p
                     uu[k] = k0 + k < n ? s_u[k0 + k] : -1;
                     jj[k] = k0 + k < n ? s_j[k0 + k] : 0;
                 }
-                float g[kMU][3], y[kMU][9];
+                float g[kMU][3], y[kMU][9], ph[kMU];
 #pragma unroll
                 for (int k = 0; k < kMU; ++k) {
                     if (uu[k] < 0) continue;
@@ -673,14 +686,19 @@ __global__ void __launch_bounds__(F) k_message(const int32_t *__restrict__ row_p
                         const float st = s_st[k0 + k];
                         g[k][0] = tab_value(cp[0], st); g[k][1] = tab_value(cp[F], st); g[k][2] = tab_value(cp[2 * F], st);
                     } else {
-                        const float *gp = gU + (int64_t)uu[k] * 3 * F + c;
-                        g[k][0] = gp[0]; g[k][1] = gp[F]; g[k][2] = gp[2 * F];
+                        const float *ap = a3 + (int64_t)uu[k] * 3 * F + c;
+                        g[k][0] = ap[0]; g[k][1] = ap[F]; g[k][2] = ap[2 * F];
+                        ph[k] = phiu[uu[k]];
                     }
                     load_coords(Y, jj[k], c, N, F, y[k]);
                 }
 #pragma unroll
                 for (int k = 0; k < kMU; ++k) {
                     if (uu[k] < 0) continue;
+                    if constexpr (!TAB) {
+#pragma unroll
+                        for (int p = 0; p < 3; ++p) g[k][p] = silu_f(g[k][p]) * ph[k];
+                    }
                     m[0] = fmaf(g[k][0], y[k][0], m[0]);
 #pragma unroll
                     for (int q = 1; q < 4; ++q) m[q] = fmaf(g[k][1], y[k][q], m[q]);
@@ -916,7 +934,8 @@ __global__ void k_T_bwd(const float *__restrict__ Y, const float *__restrict__ M
 // i (block, thread per channel):
 //   gY_i += sum_j g^p_ij gM_j                          (g_ij = g_ji)
 //   gg^p[u(i,j)] = <gM_i, Y^p_j> + <gM_j, Y^p_i>        for upper edges j > i
-// and, with g = phi silu(a3), for the same upper edge:
+// with g = phi silu(a3) formed here from the pair's stored a3 and phi (the
+// filter itself is never stored), and, for the same upper edge:
 //   ga3 = gg phi silu'(a3)       (fp32 if ga3 != NULL, plus its operand copy)
 //   gphi[u] += sum over the 3F entries of gg silu(a3)
 // Each undirected pair is handled once, by its upper edge: no atomics.  The
@@ -928,23 +947,32 @@ __global__ void k_T_bwd(const float *__restrict__ Y, const float *__restrict__ M
 // With TAB (tabulated radial functions) g and dg/dd come from the table: the
 // kernel adds sum dE/dg dg/dd to gphi (then dE/dd of the pair) and writes no
 // dE/da3.
+// RB consecutive rows per block, one group of F threads per row, as in
+// k_message (the groups' repeated gathers of gM_j and Y_j hit L1).
 constexpr int kMUU = 2;
-template <int F, bool TAB>
-__global__ void __launch_bounds__(F, 512 / F)
+template <int F, bool TAB, int RB>
+__global__ void __launch_bounds__(F * RB, (512 / (F * RB)) > 0 ? 512 / (F * RB) : 1)
     k_message_bwd(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-                  const int32_t *__restrict__ pair_of, const float *__restrict__ gU, const float *__restrict__ Y,
+                  const int32_t *__restrict__ pair_of, const float *__restrict__ Y,
                   const float *__restrict__ gM, const float *__restrict__ a3, const float *__restrict__ phiu,
                   TabFn tg, int N, float *__restrict__ gY, OpCopy gY_cp, float *__restrict__ ga3, OpCopy ga3_cp,
                   float *__restrict__ gphi) {
     pdl_entry();
     constexpr int NW = F / 32;
-    __shared__ int32_t s_u[kChunk], s_j[kChunk];
-    __shared__ int32_t s_kt[TAB ? kChunk : 1];
-    __shared__ float s_st[TAB ? kChunk : 1];
-    __shared__ float s_red[kChunk][NW];
-    __shared__ float s_yi[9][F], s_gmi[9][F];  // row i's Y and gM (per thread's channel)
-    const int c = threadIdx.x, lane = c & 31, warp = c >> 5;
-    for (int i = blockIdx.x; i < N; i += gridDim.x) {
+    constexpr int CH = RB >= 4 ? kChunk / 2 : kChunk;  // staged edges per chunk (static smem stays below 48 KB)
+    __shared__ int32_t s_u_all[RB][CH], s_j_all[RB][CH];
+    __shared__ int32_t s_kt_all[RB][TAB ? CH : 1];
+    __shared__ float s_st_all[RB][TAB ? CH : 1];
+    __shared__ float s_red_all[RB][CH][NW];
+    __shared__ float s_yi_all[RB][9][F], s_gmi_all[RB][9][F];  // row i's Y and gM (per thread's channel)
+    const int grp = RB > 1 ? (int)threadIdx.x / F : 0, c = RB > 1 ? (int)threadIdx.x % F : (int)threadIdx.x;
+    const int lane = c & 31, warp = c >> 5;
+    int32_t *s_u = s_u_all[grp], *s_j = s_j_all[grp], *s_kt = s_kt_all[grp];
+    float *s_st = s_st_all[grp];
+    float(*s_red)[NW] = s_red_all[grp];
+    float(*s_yi)[F] = s_yi_all[grp];
+    float(*s_gmi)[F] = s_gmi_all[grp];
+    for (int i = blockIdx.x * RB + grp; i < N; i += gridDim.x * RB) {
         float acc[9];
         {
             float t[9];
@@ -963,9 +991,9 @@ __global__ void __launch_bounds__(F, 512 / F)
             if (col[mid] <= i) eu = mid + 1;
             else hi = mid;
         }
-        for (int cb = e0; cb < e1; cb += kChunk) {
-            const int n = e1 - cb < kChunk ? e1 - cb : kChunk;
-            __syncthreads();
+        for (int cb = e0; cb < e1; cb += CH) {
+            const int n = e1 - cb < CH ? e1 - cb : CH;
+            group_sync<F, RB>(grp);
             for (int t = c; t < n; t += F) {
                 const int u = pair_of[cb + t];
                 s_u[t] = u;
@@ -978,7 +1006,7 @@ __global__ void __launch_bounds__(F, 512 / F)
                     s_st[t] = st;
                 }
             }
-            __syncthreads();
+            group_sync<F, RB>(grp);
             const int nl = eu - cb < 0 ? 0 : (eu - cb < n ? eu - cb : n);  // lower edges of the chunk
             for (int k0 = 0; k0 < nl; k0 += kMU) {
                 int uu[kMU], jj[kMU];
@@ -987,7 +1015,7 @@ __global__ void __launch_bounds__(F, 512 / F)
                     uu[k] = k0 + k < nl ? s_u[k0 + k] : -1;
                     jj[k] = k0 + k < nl ? s_j[k0 + k] : 0;
                 }
-                float g[kMU][3], gmj[kMU][9];
+                float g[kMU][3], gmj[kMU][9], ph[kMU];
 #pragma unroll
                 for (int k = 0; k < kMU; ++k) {
                     if (uu[k] < 0) continue;
@@ -996,14 +1024,19 @@ __global__ void __launch_bounds__(F, 512 / F)
                         const float st = s_st[k0 + k];
                         g[k][0] = tab_value(cp[0], st); g[k][1] = tab_value(cp[F], st); g[k][2] = tab_value(cp[2 * F], st);
                     } else {
-                        const float *gp = gU + (int64_t)uu[k] * 3 * F + c;
-                        g[k][0] = gp[0]; g[k][1] = gp[F]; g[k][2] = gp[2 * F];
+                        const float *ap = a3 + (int64_t)uu[k] * 3 * F + c;
+                        g[k][0] = ap[0]; g[k][1] = ap[F]; g[k][2] = ap[2 * F];
+                        ph[k] = phiu[uu[k]];
                     }
                     load_coords(gM, jj[k], c, N, F, gmj[k]);
                 }
 #pragma unroll
                 for (int k = 0; k < kMU; ++k) {
                     if (uu[k] < 0) continue;
+                    if constexpr (!TAB) {
+#pragma unroll
+                        for (int p = 0; p < 3; ++p) g[k][p] = silu_f(g[k][p]) * ph[k];
+                    }
                     acc[0] = fmaf(g[k][0], gmj[k][0], acc[0]);
 #pragma unroll
                     for (int q = 1; q < 4; ++q) acc[q] = fmaf(g[k][1], gmj[k][q], acc[q]);
@@ -1034,9 +1067,10 @@ __global__ void __launch_bounds__(F, 512 / F)
                         phi[k] = 0.f;
                     } else {
                         const int64_t o = (int64_t)uu[k] * 3 * F + c;
-                        g[k][0] = gU[o]; g[k][1] = gU[o + F]; g[k][2] = gU[o + 2 * F];
                         a[k][0] = a3[o]; a[k][1] = a3[o + F]; a[k][2] = a3[o + 2 * F];
                         phi[k] = phiu[uu[k]];
+#pragma unroll
+                        for (int p = 0; p < 3; ++p) g[k][p] = silu_f(a[k][p]) * phi[k];
                     }
                     load_coords(gM, jj[k], c, N, F, gmj[k]);
                     load_coords(Y, jj[k], c, N, F, yj[k]);
@@ -1075,7 +1109,7 @@ __global__ void __launch_bounds__(F, 512 / F)
                     if (lane == 0) s_red[k0 + k - nl][warp] = r;
                 }
             }
-            __syncthreads();
+            group_sync<F, RB>(grp);
             for (int t = c; t < n - nl; t += F) {
                 const int u = s_u[nl + t];
                 if (u < 0) continue;
@@ -1602,6 +1636,43 @@ int tc_any(const tc::TcShape &P, const __nv_bfloat16 *A, int64_t a_rows, int64_t
     return TNET_ERR_ARG;
 }
 
+// Launch the row kernels with rb consecutive rows per block (the largest of
+// 4, 2, 1 not above rb whose block fits: at most 1024 threads for the
+// messages, 512 for their adjoint, whose per-row staging is 37 KB at F = 128).
+// blocks1 is the grid the one-row-per-block launch would use.
+template <int F, bool TAB, class... Args>
+static void launch_message(int rb, int blocks1, cudaStream_t st, Args... args) {
+    if constexpr (F * 4 <= 1024) {
+        if (rb >= 4) {
+            launch(k_message<F, TAB, 4>, (blocks1 + 3) / 4, F * 4, 0, st, args...);
+            return;
+        }
+    }
+    if constexpr (F * 2 <= 1024) {
+        if (rb >= 2) {
+            launch(k_message<F, TAB, 2>, (blocks1 + 1) / 2, F * 2, 0, st, args...);
+            return;
+        }
+    }
+    launch(k_message<F, TAB, 1>, blocks1, F, 0, st, args...);
+}
+template <int F, bool TAB, class... Args>
+static void launch_message_bwd(int rb, int blocks1, cudaStream_t st, Args... args) {
+    if constexpr (F * 4 <= 512) {
+        if (rb >= 4) {
+            launch(k_message_bwd<F, TAB, 4>, (blocks1 + 3) / 4, F * 4, 0, st, args...);
+            return;
+        }
+    }
+    if constexpr (F * 2 <= 512) {
+        if (rb >= 2) {
+            launch(k_message_bwd<F, TAB, 2>, (blocks1 + 1) / 2, F * 2, 0, st, args...);
+            return;
+        }
+    }
+    launch(k_message_bwd<F, TAB, 1>, blocks1, F, 0, st, args...);
+}
+
 // ============================================================ driver ===
 static inline int grid_for(int64_t n, int threads, int num_sms) {
     int64_t g = (n + threads - 1) / threads;
@@ -1959,6 +2030,7 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
           *hs1 = f32(Lw.hs1), *as2 = f32(Lw.as2), *s = f32(Lw.s), *q0 = f32(Lw.q0);
     float2 *ln0 = wsp<float2>(ctx, Lw.ln0);
     const int atom_blocks = N < sms * ctx->tune[T_ROW_BLOCKS] ? N : sms * ctx->tune[T_ROW_BLOCKS];
+    const int rows_pb = ctx->tune[T_ROWS_PER_BLOCK];  // consecutive rows per block of the message kernels
 #define EMB_FWD(FF)                                                                                           \
     if (tab)                                                                                                  \
         launch(k_emb_edges<FF, true>, atom_blocks, FF, 0, st, geo, z, row_ptr, col, pair_of, N, d.max_z, fu, tf0, Ta, \
@@ -1994,14 +2066,20 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     // ---- interaction layers
     // layer l's radial-MLP activations: [maxU][width] slabs
     auto act = [&](size_t off, int width, int l) { return f32(off) + slab(l) * maxU * width; };
-    auto edge_mlp = [&](int l) -> int {
+    // The radial MLP of layer l over the undirected pairs.  Its last layer
+    // stores only the pre-activation a3: the message kernels form the filter
+    // g = phi SiLU(a3) themselves.  fwd_only (the forward pass when the reverse
+    // pass recomputes the activations): a1 and a2 are not stored, since only
+    // the reverse pass reads them.
+    auto edge_mlp = [&](int l, bool fwd_only) -> int {
         const LayerW &Lr = W.layer[l];
         float *a1 = act(Lw.a1, F, l), *h1 = act(Lw.h1, F, l), *a2 = act(Lw.a2, 2 * F, l),
-              *h2 = act(Lw.h2, 2 * F, l), *a3 = act(Lw.a3, 3 * F, l), *gbuf = act(Lw.g, 3 * F, l);
+              *h2 = act(Lw.h2, 2 * F, l), *a3 = act(Lw.a3, 3 * F, l);
         if (tab) return TNET_OK;  // the message kernels evaluate g, dg/dd from the table
-        const EpiBiasAct e1{Lr.mlp1_b, a1, F, keep_h ? h1 : nullptr, F, 1, nullptr, h1_cp(l), F};
-        const EpiBiasAct e2{Lr.mlp2_b, a2, 2 * F, keep_h ? h2 : nullptr, 2 * F, 1, nullptr, h2_cp(l), 2 * F};
-        const EpiBiasAct e3{b3p(l), a3, 3 * F, gbuf, 3 * F, 1, phiu};
+        const EpiBiasAct e1{Lr.mlp1_b, fwd_only ? nullptr : a1, F, keep_h ? h1 : nullptr, F, 1, nullptr, h1_cp(l), F};
+        const EpiBiasAct e2{Lr.mlp2_b, fwd_only ? nullptr : a2, 2 * F, keep_h ? h2 : nullptr, 2 * F, 1, nullptr,
+                            h2_cp(l), 2 * F};
+        const EpiBiasAct e3{b3p(l), a3, 3 * F, nullptr, 3 * F, 0, nullptr};
         if (tcm) {
             tc::TcShape t2 = tc::tshape(maxU, 2 * F, F), t3 = tc::tshape(maxU, 3 * F, 2 * F);
             t2.rows_dev = t3.rows_dev = nu;
@@ -2042,12 +2120,14 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         pf.mark(P_NODE_MIX);
         if (tcm) TRY(tcg(tc::tshape_classes(N, F), Xn, nbf, 9LL * N, F, lb[l].mix1, 3 * F, F, EpiStore{Y, F, 0}));
         else TRY(sgemm<false, true>(gshape_classes(N, F, Xn, W.layer[l].mix1_w), EpiStore{Y, F, 0}, gctas, st));
-        TRY(edge_mlp(l));
+        TRY(edge_mlp(l, !keep_act));
         pf.mark(P_MESSAGE);
-        const float *gbuf = act(Lw.g, 3 * F, l);
-#define MSG_FWD(FF)                                                                                               \
-    if (tab) launch(k_message<FF, true>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, tabfn(1 + l), Y, N, M); \
-    else launch(k_message<FF, false>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, tabfn(1 + l), Y, N, M)
+        const float *a3l = act(Lw.a3, 3 * F, l);
+#define MSG_FWD(FF)                                                                                          \
+    if (tab) launch_message<FF, true>(rows_pb, atom_blocks, st, row_ptr, col, pair_of, a3l, phiu, tabfn(1 + l), Y, \
+                                      N, M);                                                                 \
+    else launch_message<FF, false>(rows_pb, atom_blocks, st, row_ptr, col, pair_of, a3l, phiu, tabfn(1 + l), Y, \
+                                   N, M)
         TNET_F_SWITCH(F, MSG_FWD);
 #undef MSG_FWD
         count_launch();
@@ -2144,19 +2224,19 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         TNET_LAUNCH_CHECK();
         // this layer's radial-MLP activations: kept from the forward pass, or
         // recomputed here (same kernels, same inputs: bitwise the same values)
-        if (!keep_act) TRY(edge_mlp(l));
+        if (!keep_act) TRY(edge_mlp(l, false));
         const float *a1 = act(Lw.a1, F, l), *h1 = act(Lw.h1, F, l), *a2 = act(Lw.a2, 2 * F, l),
-                    *h2 = act(Lw.h2, 2 * F, l), *a3 = act(Lw.a3, 3 * F, l), *gbuf = act(Lw.g, 3 * F, l);
+                    *h2 = act(Lw.h2, 2 * F, l), *a3 = act(Lw.a3, 3 * F, l);
         pf.mark(P_MSG_BWD);
         // (the BF16 GEMMs read only the copy of ga3; the fp32 ga3 feeds the FP32
         // and 3xTF32 GEMMs and the weight gradients)
         float *ga3_out = (prec != 1 || wg) ? gg : nullptr;
 #define MSG_BWD(FF)                                                                                          \
-    launch(k_message_bwd<FF, false>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu,       \
-                                                         tabfn(1 + l), N, gY, nbf, ga3_out, ga3_cp, gphiu)
+    launch_message_bwd<FF, false>(rows_pb, atom_blocks, st, row_ptr, col, pair_of, Y, gM, a3, phiu, tabfn(1 + l), \
+                                  N, gY, nbf, ga3_out, ga3_cp, gphiu)
 #define MSG_BWD_TAB(FF)                                                                                      \
-    launch(k_message_bwd<FF, true>, atom_blocks, FF, 0, st, row_ptr, col, pair_of, gbuf, Y, gM, a3, phiu,        \
-                                                        tabfn(1 + l), N, gY, nbf, nullptr, none, gphiu)
+    launch_message_bwd<FF, true>(rows_pb, atom_blocks, st, row_ptr, col, pair_of, Y, gM, a3, phiu, tabfn(1 + l), \
+                                 N, gY, nbf, (float *)nullptr, none, gphiu)
         if (tab) {
             TNET_F_SWITCH(F, MSG_BWD_TAB);
         } else {
