@@ -213,12 +213,12 @@ thread_local int tnet::tl_pdl = 1;
 
 // Candidate values of each tuning knob (TuneKnob) and the default's index.
 static const int kTuneCandidates[T_NKNOBS][4] = {{1, 2, 3, 4}, {192, 128, 0, 0}, {256, 128, 0, 0}, {4, 8, 16, 0},
-                                                 {4, 8, 16, 0}, {1, 0, 0, 0}, {4, 2, 1, 0}};
+                                                 {4, 8, 16, 0}, {1, 0, 0, 0}, {0, 1, 4, 0}};
 static const int kTuneCount[T_NKNOBS] = {4, 2, 2, 3, 3, 2, 3};
-static const int kTuneDefault[T_NKNOBS] = {2, 0, 0, 1, 1, 0, 2};
+static const int kTuneDefault[T_NKNOBS] = {2, 0, 0, 1, 1, 0, 0};
 static const char *kTuneNames[T_NKNOBS] = {"gemm_ctas_per_sm",   "tc_tile_n_3f",        "tc_tile_n_2f",
                                            "row_blocks_per_sm",  "pair_blocks_per_sm",  "programmatic_launch",
-                                           "message_rows_per_block"};
+                                           "message_kernel"};
 
 static const char *kTagNames[P_NTAGS] = {
     "neighbors", "graph_prep", "emb_edges", "emb_node", "mlp1", "mlp2", "mlp3", "message",

@@ -1124,6 +1124,313 @@ __global__ void __launch_bounds__(F * RB, (512 / (F * RB)) > 0 ? 512 / (F * RB) 
     }
 }
 
+// ------------------------------------------- warp-per-row message kernels ---
+// The same sums as k_message and k_message_bwd (exact mode), with one warp per
+// row and four consecutive channels per lane: every gathered row of F floats
+// is one float4 load per lane (F / 128 of them), so the load, address and
+// index instructions per edge fall by four against a thread per channel, the
+// dE/dphi sum of a pair is one warp reduction (no shared-memory partials or
+// block barriers), and each warp keeps two edges' gathers in flight.  Built
+// for F = 128 (the adjoint's per-warp staging of row i is 9 KB).  Offsets are
+// 32-bit (the host checks 9 N F < 2^31).
+constexpr int kV4Warps = 4;  // warps (rows in flight) per block
+
+__device__ __forceinline__ float4 ld4(const float *__restrict__ p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *__restrict__ p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ void fma4(float4 &a, float s, const float4 &x) {
+    a.x = fmaf(s, x.x, a.x); a.y = fmaf(s, x.y, a.y); a.z = fmaf(s, x.z, a.z); a.w = fmaf(s, x.w, a.w);
+}
+__device__ __forceinline__ void fma4v(float4 &a, const float4 &s, const float4 &x) {
+    a.x = fmaf(s.x, x.x, a.x); a.y = fmaf(s.y, x.y, a.y); a.z = fmaf(s.z, x.z, a.z); a.w = fmaf(s.w, x.w, a.w);
+}
+// first element (in floats) of coordinate row q (0..8) of atom n in a node
+// tensor laid out as I rows [0, N), A rows [N, 4N), S rows [4N, 9N)
+__device__ __forceinline__ uint32_t coord_row(int q, uint32_t n, uint32_t N, uint32_t F) {
+    return (q == 0 ? n : (q < 4 ? N + 3u * n + (uint32_t)(q - 1) : 4u * N + 5u * n + (uint32_t)(q - 4))) * F;
+}
+// plane p (I, A, S) of coordinate q
+__device__ __forceinline__ constexpr int plane_of(int q) { return q == 0 ? 0 : (q < 4 ? 1 : 2); }
+
+template <int F>
+__global__ void __launch_bounds__(32 * kV4Warps, 3) k_message_v4(const int32_t *__restrict__ row_ptr,
+                                                              const int32_t *__restrict__ col,
+                                                              const int32_t *__restrict__ pair_of,
+                                                              const float *__restrict__ a3,
+                                                              const float *__restrict__ phiu,
+                                                              const float *__restrict__ Y, int N,
+                                                              float *__restrict__ M) {
+    pdl_entry();
+    static_assert(F % 128 == 0, "four channels per lane");
+    constexpr int PER = F / 128;  // float4 per lane per row
+    constexpr int KM = 2;         // edges in flight per warp
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * kV4Warps;
+    for (int i = blockIdx.x * kV4Warps + (threadIdx.x >> 5); i < N; i += nw) {
+        float4 m[9][PER];
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+#pragma unroll
+            for (int r = 0; r < PER; ++r) m[q][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
+        for (int eb = e0; eb < e1; eb += 32) {
+            const int n = e1 - eb < 32 ? e1 - eb : 32;
+            int u_l = -1, j_l = 0;
+            float ph_l = 0.f;
+            if (lane < n) {
+                u_l = pair_of[eb + lane];
+                j_l = col[eb + lane];
+                if (u_l >= 0) ph_l = phiu[u_l];
+            }
+            for (int k0 = 0; k0 < n; k0 += KM) {
+                int uu[KM], jj[KM];
+                float ph[KM];
+#pragma unroll
+                for (int k = 0; k < KM; ++k) {
+                    const int src = k0 + k < n ? k0 + k : 0;
+                    uu[k] = __shfl_sync(0xffffffffu, u_l, src);
+                    jj[k] = __shfl_sync(0xffffffffu, j_l, src);
+                    ph[k] = __shfl_sync(0xffffffffu, ph_l, src);
+                    if (k0 + k >= n) uu[k] = -1;
+                }
+                float4 g[KM][3][PER], y[KM][9][PER];
+#pragma unroll
+                for (int k = 0; k < KM; ++k) {
+                    if (uu[k] < 0) continue;
+                    const uint32_t ab = (uint32_t)uu[k] * 3u * F + 4u * lane;
+#pragma unroll
+                    for (int p = 0; p < 3; ++p)
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) g[k][p][r] = ld4(a3 + ab + p * F + 128 * r);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        const uint32_t yb = coord_row(q, (uint32_t)jj[k], (uint32_t)N, F) + 4u * lane;
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) y[k][q][r] = ld4(Y + yb + 128 * r);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < KM; ++k) {
+                    if (uu[k] < 0) continue;
+#pragma unroll
+                    for (int p = 0; p < 3; ++p)
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) {
+                            float4 &v = g[k][p][r];
+                            v.x = silu_f(v.x) * ph[k]; v.y = silu_f(v.y) * ph[k];
+                            v.z = silu_f(v.z) * ph[k]; v.w = silu_f(v.w) * ph[k];
+                        }
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) fma4v(m[q][r], g[k][plane_of(q)][r], y[k][q][r]);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const uint32_t mb = coord_row(q, (uint32_t)i, (uint32_t)N, F) + 4u * lane;
+#pragma unroll
+            for (int r = 0; r < PER; ++r) st4(M + mb + 128 * r, m[q][r]);
+        }
+    }
+}
+
+// Adjoint, warp per row: gY_i += sum_j g_ij gM_j over the row; for the upper
+// edges (j > i) also dE/dg of the pair, dE/da3 = dE/dg phi SiLU'(a3) and
+// dE/dphi += sum dE/dg SiLU(a3) (one warp reduction, in the lane order).
+// Row i's own Y and gM sit in shared memory (per warp) for the upper edges'
+// dot products.  One lower edge's gathers are in flight at a time, and an
+// upper edge gathers gM_j (with a3) and then Y_j, which keeps the kernel
+// within 255 registers without spills (two blocks, eight warps per SM).
+template <int F>
+__global__ void __launch_bounds__(32 * kV4Warps, 2)
+    k_message_bwd_v4(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                     const int32_t *__restrict__ pair_of, const float *__restrict__ Y,
+                     const float *__restrict__ gM, const float *__restrict__ a3, const float *__restrict__ phiu,
+                     int N, float *__restrict__ gY, OpCopy gY_cp, float *__restrict__ ga3, OpCopy ga3_cp,
+                     float *__restrict__ gphi) {
+    pdl_entry();
+    static_assert(F % 128 == 0, "four channels per lane");
+    constexpr int PER = F / 128;
+    constexpr int KM = 1;   // lower edges in flight per warp
+    __shared__ float4 s_own[kV4Warps][2][9][F / 4];  // row i's Y and gM
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float4(*s_y)[F / 4] = s_own[w][0];
+    float4(*s_gm)[F / 4] = s_own[w][1];
+    const int nw = gridDim.x * kV4Warps;
+    for (int i = blockIdx.x * kV4Warps + w; i < N; i += nw) {
+        float4 acc[9][PER];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const uint32_t b = coord_row(q, (uint32_t)i, (uint32_t)N, F) + 4u * lane;
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                acc[q][r] = ld4(gY + b + 128 * r);
+                s_y[q][lane + 32 * r] = ld4(Y + b + 128 * r);
+                s_gm[q][lane + 32 * r] = ld4(gM + b + 128 * r);
+            }
+        }
+        // each lane reads back only what it wrote: no barrier needed
+        const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
+        int eu = e0, hi = e1;  // first edge with col > i
+        while (eu < hi) {
+            const int mid = (eu + hi) >> 1;
+            if (col[mid] <= i) eu = mid + 1;
+            else hi = mid;
+        }
+        for (int eb = e0; eb < e1; eb += 32) {
+            const int n = e1 - eb < 32 ? e1 - eb : 32;
+            int u_l = -1, j_l = 0;
+            float ph_l = 0.f;
+            if (lane < n) {
+                u_l = pair_of[eb + lane];
+                j_l = col[eb + lane];
+                if (u_l >= 0) ph_l = phiu[u_l];
+            }
+            const int nl = eu - eb < 0 ? 0 : (eu - eb < n ? eu - eb : n);  // lower edges of the batch
+            for (int k0 = 0; k0 < nl; k0 += KM) {
+                int uu[KM], jj[KM];
+                float ph[KM];
+#pragma unroll
+                for (int k = 0; k < KM; ++k) {
+                    const int src = k0 + k < nl ? k0 + k : 0;
+                    uu[k] = __shfl_sync(0xffffffffu, u_l, src);
+                    jj[k] = __shfl_sync(0xffffffffu, j_l, src);
+                    ph[k] = __shfl_sync(0xffffffffu, ph_l, src);
+                    if (k0 + k >= nl) uu[k] = -1;
+                }
+                float4 g[KM][3][PER], gm[KM][9][PER];
+#pragma unroll
+                for (int k = 0; k < KM; ++k) {
+                    if (uu[k] < 0) continue;
+                    const uint32_t ab = (uint32_t)uu[k] * 3u * F + 4u * lane;
+#pragma unroll
+                    for (int p = 0; p < 3; ++p)
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) g[k][p][r] = ld4(a3 + ab + p * F + 128 * r);
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        const uint32_t b = coord_row(q, (uint32_t)jj[k], (uint32_t)N, F) + 4u * lane;
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) gm[k][q][r] = ld4(gM + b + 128 * r);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < KM; ++k) {
+                    if (uu[k] < 0) continue;
+#pragma unroll
+                    for (int p = 0; p < 3; ++p)
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) {
+                            float4 &v = g[k][p][r];
+                            v.x = silu_f(v.x) * ph[k]; v.y = silu_f(v.y) * ph[k];
+                            v.z = silu_f(v.z) * ph[k]; v.w = silu_f(v.w) * ph[k];
+                        }
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) fma4v(acc[q][r], g[k][plane_of(q)][r], gm[k][q][r]);
+                }
+            }
+            for (int k = nl; k < n; ++k) {  // upper edges, one at a time
+                const int u = __shfl_sync(0xffffffffu, u_l, k);
+                const int j = __shfl_sync(0xffffffffu, j_l, k);
+                const float ph = __shfl_sync(0xffffffffu, ph_l, k);
+                if (u < 0) continue;
+                // two rounds of gathers (gM_j with a3, then Y_j), so that only
+                // one 9-row block is live at a time
+                const uint32_t ab = (uint32_t)u * 3u * F + 4u * lane;
+                float4 sp[3][PER], a[3][PER];
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int r = 0; r < PER; ++r) {
+                        a[p][r] = ld4(a3 + ab + p * F + 128 * r);
+                        sp[p][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                float4 gv[3][PER];
+                float rsum = 0.f;
+                {
+                    float4 gm[9][PER];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        const uint32_t bq = coord_row(q, (uint32_t)j, (uint32_t)N, F) + 4u * lane;
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) gm[q][r] = ld4(gM + bq + 128 * r);
+                    }
+#pragma unroll
+                    for (int p = 0; p < 3; ++p)
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) {
+                            const float4 v = a[p][r];
+                            gv[p][r] = make_float4(silu_f(v.x) * ph, silu_f(v.y) * ph, silu_f(v.z) * ph,
+                                                   silu_f(v.w) * ph);
+                        }
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) {
+                            fma4v(acc[q][r], gv[plane_of(q)][r], gm[q][r]);
+                            fma4v(sp[plane_of(q)][r], gm[q][r], s_y[q][lane + 32 * r]);
+                        }
+                }
+                {
+                    float4 yj[9][PER];
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) {
+                        const uint32_t bq = coord_row(q, (uint32_t)j, (uint32_t)N, F) + 4u * lane;
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) yj[q][r] = ld4(Y + bq + 128 * r);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 9; ++q)
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) fma4v(sp[plane_of(q)][r], s_gm[q][lane + 32 * r], yj[q][r]);
+                }
+#pragma unroll
+                for (int p = 0; p < 3; ++p)
+#pragma unroll
+                    for (int r = 0; r < PER; ++r) {
+                        const float av[4] = {a[p][r].x, a[p][r].y, a[p][r].z, a[p][r].w};
+                        const float sv4[4] = {sp[p][r].x, sp[p][r].y, sp[p][r].z, sp[p][r].w};
+                        float gav[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            float sv, sd;
+                            silu_and_grad_f(av[c], sv, sd);
+                            rsum = fmaf(sv4[c], sv, rsum);
+                            gav[c] = sv4[c] * ph * sd;
+                        }
+                        const uint32_t o = ab + p * F + 128 * r;
+                        if (ga3) st4(ga3 + o, make_float4(gav[0], gav[1], gav[2], gav[3]));
+                        if (ga3_cp.mode) {
+                            opcopy_store(ga3_cp, o, gav[0]);
+                            opcopy_store(ga3_cp, o + 1, gav[1]);
+                            opcopy_store(ga3_cp, o + 2, gav[2]);
+                            opcopy_store(ga3_cp, o + 3, gav[3]);
+                        }
+                    }
+                rsum = warp_sum(rsum);
+                if (lane == 0) gphi[u] += rsum;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const uint32_t b = coord_row(q, (uint32_t)i, (uint32_t)N, F) + 4u * lane;
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                st4(gY + b + 128 * r, acc[q][r]);
+                if (gY_cp.mode) {
+                    opcopy_store(gY_cp, b + 128 * r, acc[q][r].x);
+                    opcopy_store(gY_cp, b + 128 * r + 1, acc[q][r].y);
+                    opcopy_store(gY_cp, b + 128 * r + 2, acc[q][r].z);
+                    opcopy_store(gY_cp, b + 128 * r + 3, acc[q][r].w);
+                }
+            }
+        }
+    }
+}
+
 // Xn = X / (q + 1):  gX = gXn / (q + 1) - <gXn, X> / (q + 1)^2 * dq/dX (in place)
 __global__ void k_node_norm_bwd(const float *__restrict__ X, const float *__restrict__ qn, int N, int F,
                                 float *__restrict__ gX) {
@@ -1636,21 +1943,15 @@ int tc_any(const tc::TcShape &P, const __nv_bfloat16 *A, int64_t a_rows, int64_t
     return TNET_ERR_ARG;
 }
 
-// Launch the row kernels with rb consecutive rows per block (the largest of
-// 4, 2, 1 not above rb whose block fits: at most 1024 threads for the
-// messages, 512 for their adjoint, whose per-row staging is 37 KB at F = 128).
+// Launch the thread-per-channel row kernels with 4 consecutive rows per block
+// when rb >= 4 and the block fits (at most 1024 threads for the messages, 512
+// for their adjoint, whose per-row staging is 37 KB at F = 128), else one.
 // blocks1 is the grid the one-row-per-block launch would use.
 template <int F, bool TAB, class... Args>
 static void launch_message(int rb, int blocks1, cudaStream_t st, Args... args) {
     if constexpr (F * 4 <= 1024) {
         if (rb >= 4) {
             launch(k_message<F, TAB, 4>, (blocks1 + 3) / 4, F * 4, 0, st, args...);
-            return;
-        }
-    }
-    if constexpr (F * 2 <= 1024) {
-        if (rb >= 2) {
-            launch(k_message<F, TAB, 2>, (blocks1 + 1) / 2, F * 2, 0, st, args...);
             return;
         }
     }
@@ -1661,12 +1962,6 @@ static void launch_message_bwd(int rb, int blocks1, cudaStream_t st, Args... arg
     if constexpr (F * 4 <= 512) {
         if (rb >= 4) {
             launch(k_message_bwd<F, TAB, 4>, (blocks1 + 3) / 4, F * 4, 0, st, args...);
-            return;
-        }
-    }
-    if constexpr (F * 2 <= 512) {
-        if (rb >= 2) {
-            launch(k_message_bwd<F, TAB, 2>, (blocks1 + 1) / 2, F * 2, 0, st, args...);
             return;
         }
     }
@@ -2030,7 +2325,14 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
           *hs1 = f32(Lw.hs1), *as2 = f32(Lw.as2), *s = f32(Lw.s), *q0 = f32(Lw.q0);
     float2 *ln0 = wsp<float2>(ctx, Lw.ln0);
     const int atom_blocks = N < sms * ctx->tune[T_ROW_BLOCKS] ? N : sms * ctx->tune[T_ROW_BLOCKS];
-    const int rows_pb = ctx->tune[T_ROWS_PER_BLOCK];  // consecutive rows per block of the message kernels
+    // message kernels: knob 0 = one warp per row with four channels per lane
+    // (exact mode, F = 128, 32-bit offsets), else that many consecutive rows
+    // per block of F threads (one thread per channel)
+    const int rows_pb = ctx->tune[T_MSG_KERNEL] > 0 ? ctx->tune[T_MSG_KERNEL] : 1;
+    const bool warp_rows = ctx->tune[T_MSG_KERNEL] == 0 && !tab && F == 128 && 9LL * N * F < (1LL << 31) &&
+                           (int64_t)maxU * 3 * F < (1LL << 31);
+    const int v4_blocks = (int)((N + kV4Warps - 1) / kV4Warps < atom_blocks ? (N + kV4Warps - 1) / kV4Warps
+                                                                             : atom_blocks);
 #define EMB_FWD(FF)                                                                                           \
     if (tab)                                                                                                  \
         launch(k_emb_edges<FF, true>, atom_blocks, FF, 0, st, geo, z, row_ptr, col, pair_of, N, d.max_z, fu, tf0, Ta, \
@@ -2128,7 +2430,11 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
                                       N, M);                                                                 \
     else launch_message<FF, false>(rows_pb, atom_blocks, st, row_ptr, col, pair_of, a3l, phiu, tabfn(1 + l), Y, \
                                    N, M)
-        TNET_F_SWITCH(F, MSG_FWD);
+        if (warp_rows) launch(k_message_v4<128>, v4_blocks, 32 * kV4Warps, 0, st, row_ptr, col, pair_of, a3l, phiu, Y,
+                              N, M);
+        else {
+            TNET_F_SWITCH(F, MSG_FWD);
+        }
 #undef MSG_FWD
         count_launch();
         pf.mark(P_NODE_ELEM);
@@ -2239,6 +2545,9 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
                                  N, gY, nbf, (float *)nullptr, none, gphiu)
         if (tab) {
             TNET_F_SWITCH(F, MSG_BWD_TAB);
+        } else if (warp_rows) {
+            launch(k_message_bwd_v4<128>, v4_blocks, 32 * kV4Warps, 0, st, row_ptr, col, pair_of, Y, gM, a3, phiu, N, gY,
+                   nbf, ga3_out, ga3_cp, gphiu);
         } else {
             TNET_F_SWITCH(F, MSG_BWD);
         }

@@ -412,6 +412,14 @@ def big_water_box(seed: int = 4, radii=(5.0, 6.0)) -> System:
     return water_box(n_side=32, L=98.6, seed=seed, n_keep=32000, radii=radii)
 
 
+def million_water_box(seed: int = 5) -> System:
+    """343,000 rigid waters (1,029,000 atoms) on a jittered 70^3 lattice at
+    the 1 g/cm^3 spacing (3.104 A) in a 217.28 A periodic cube: the stress
+    case of the neighbor search; pairs are kept clear of both the 5 A cutoff
+    and the 6 A cutoff-plus-skin."""
+    return water_box(n_side=70, L=217.28, seed=seed, radii=(5.0, 6.0))
+
+
 def maxwell_boltzmann(sys: System, T: float = 300.0, seed: int = 0) -> np.ndarray:
     """Initial velocities (A/fs) at temperature T with zero centre-of-mass
     momentum per system."""

@@ -107,6 +107,36 @@ def test_large_sampled_rows(name):
     assert np.array_equal(rkey, key)
 
 
+def test_million_atom_water_box_sampled_rows():
+    """The neighbor search's stress case, 1,029,000 atoms in a 217 A periodic
+    water box, at the cutoff and at cutoff + skin: 256 sampled rows against
+    the oracle's brute force over all atoms, and the whole-list properties.
+    The context is built with tabulated radial functions and no interaction
+    layer, so its workspace holds no per-pair radial-MLP activations."""
+    from paper_2402_17660_gb300.tnet import TensorNet
+    s = synth.million_water_box()
+    shape = synth.ModelShape(F=64, K=8, L=0)
+    m = TensorNet(synth.init_weights(shape, seed=0), F=64, K=8, L=0, max_atoms=s.n_atoms, max_systems=1,
+                  max_pairs=100 * s.n_atoms, device=torch.device("cuda:0"), radial_table=256)
+    rows = np.random.default_rng(3).choice(s.n_atoms, 256, replace=False)
+    for cutoff in (5.0, 6.0):
+        nl = gpu_pairs(m, s, cutoff=cutoff)
+        assert int(m.status.item()) == 0
+        n = int(nl.n_pairs.item())
+        rp = nl.row_ptr.cpu().numpy().astype(np.int64)
+        col = nl.col[:n].cpu().numpy().astype(np.int64)
+        assert rp[-1] == n
+        ref = neighbor_rows(s.pos, s.batch, s.box, cutoff, rows)
+        for a, r in zip(rows, ref):
+            assert np.array_equal(col[rp[a]:rp[a + 1]], r), (cutoff, a)
+        gi = np.repeat(np.arange(s.n_atoms, dtype=np.int64), np.diff(rp))
+        assert np.all(gi != col)
+        key = gi * s.n_atoms + col
+        assert np.all(np.diff(key) > 0)
+        assert np.array_equal(np.sort(col * s.n_atoms + gi), key)
+        print(f"water1029000 cutoff {cutoff}: {n} pairs ({n / s.n_atoms:.1f} per atom), 256 sampled rows exact")
+
+
 def test_capacity_overflow_reports_needed_size():
     s = synth.workload("water3000")
     oi, oj = neighbor_pairs(s.pos, s.batch, s.box, RC)
