@@ -23,9 +23,9 @@
 // 3-4 stage shared-memory ring (k-blocks of 128-byte rows for BF16, 64-byte
 // rows for 3xTF32, whose stage holds four tiles), warp 1 owns TMEM and issues
 // the MMAs (32-byte k-steps) into one of two accumulators, so the epilogue of
-// a tile overlaps the MMAs of the next.  Sixteen epilogue warps
-// drain TMEM (warp w reads lanes 32*(w%4) .. +31, a quarter of the tile's
-// columns each) and run the fused epilogue.  Every mbarrier wait is bounded;
+// a tile overlaps the MMAs of the next.  Sixteen epilogue warps (eight for
+// the 192-wide 3xTF32 tiles) drain TMEM (warp w reads lanes 32*(w%4) .. +31,
+// a quarter (half) of the tile's columns each) and run the fused epilogue.  Every mbarrier wait is bounded;
 // on expiry the kernel records TNET_ERR_TIMEOUT, the other roles stop, the
 // producer waits (bounded) for its own copies in flight, TMEM is freed and
 // the kernel returns.
@@ -40,7 +40,7 @@
 namespace tnet {
 namespace tc {
 
-constexpr int BM = 128, EPI_WARPS = 16, CONV_WARPS = 2, THREADS = 64 + 32 * (EPI_WARPS + CONV_WARPS);
+constexpr int BM = 128, CONV_WARPS = 2;
 constexpr int STG_LD = 20;  // floats per staged row (16 + pad, keeps float4 alignment)
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kMaxDevices = 64;
@@ -183,14 +183,18 @@ struct TileCfg {
     // formed in shared memory)
     static constexpr uint32_t STAGE_TX = A_BYTES + (X3 ? 2 : 1) * B_BYTES;
     static constexpr uint32_t TMEM_COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
-    static constexpr uint32_t STAGE_BYTES = EPI_WARPS * 32 * STG_LD * 4;  // epilogue transpose buffers
-    // 3xTF32: 4 stages, 5 at BN = 128 (what fits beside the epilogue buffers):
-    // each stage's split and three MMAs make a long round trip, which the
-    // wide radial layers feel.  The narrow tiles (K-wide outputs) keep 4 and a
-    // smaller footprint, which leaves room on the SM for the CTAs of the next
-    // kernel that programmatic launch brings in early.
+    // epilogue warps: 16, or 8 for the 192-wide 3xTF32 tiles, whose freed
+    // transpose buffers make room for a fifth pipeline stage
+    static constexpr int EPI = (X3 && BN == 192) ? 8 : 16;
+    static constexpr int THREADS = 64 + 32 * (EPI + CONV_WARPS);
+    static constexpr uint32_t STAGE_BYTES = EPI * 32 * STG_LD * 4;  // epilogue transpose buffers
+    // 3xTF32: 4 stages, 5 at BN = 128 and 192 (what fits beside the epilogue
+    // buffers): each stage's split and three MMAs make a long round trip,
+    // which the wide radial layers feel.  The narrow tiles (K-wide outputs)
+    // keep 4 and a smaller footprint, which leaves room on the SM for the CTAs
+    // of the next kernel that programmatic launch brings in early.
     static constexpr int X3_FIT = (int)((232448 - 1024 - 256 - STAGE_BYTES) / (STAGE_TX + A_BYTES));
-    static constexpr int STAGES = X3 ? (BN == 128 && X3_FIT >= 5 ? 5 : 4) : (BN >= 192 ? 3 : 4);
+    static constexpr int STAGES = X3 ? ((BN == 128 || BN == 192) && X3_FIT >= 5 ? 5 : 4) : (BN >= 192 ? 3 : 4);
     static_assert(STAGES >= 2 && 8 * (3 * STAGES + 5) + 8 <= 256, "pipeline barriers exceed their block");
     static constexpr size_t SMEM = 1024 + STAGES * (size_t)(STAGE_TX + (X3 ? A_BYTES : 0)) + 256 + STAGE_BYTES;
     static_assert(SMEM <= 232448, "dynamic shared memory above 227 KB");
@@ -214,7 +218,7 @@ struct TileIter {
 __device__ __forceinline__ int64_t sel3(int z, int64_t a, int64_t b, int64_t c) { return z == 0 ? a : (z == 1 ? b : c); }
 
 template <int BN, class Epi, bool X3>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(TileCfg<BN, X3>::THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo, TcShape P,
               Epi epi, int32_t *status) {
@@ -264,7 +268,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], EPI_WARPS);
+            mbar_init(&acc_empty[b], C::EPI);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -364,9 +368,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!retired) set_status(status, TNET_ERR_TIMEOUT);
             }
         }
-    } else if (warp >= 2 + EPI_WARPS) {
+    } else if (warp >= 2 + C::EPI) {
         if (X3) {  // converters: A -> (A_hi, A_lo) for every stage, in k order
-            const int ct = threadIdx.x - 32 * (2 + EPI_WARPS);
+            const int ct = threadIdx.x - 32 * (2 + C::EPI);
             int kg = 0;
             bool ok = true;
             int z, m0, n0;
@@ -400,11 +404,11 @@ __global__ void __launch_bounds__(THREADS, 1)
                 *abort_flag = 1;
             }
         }
-    } else {  // epilogue warps 2 .. 2 + EPI_WARPS - 1
+    } else {  // epilogue warps 2 .. 2 + C::EPI - 1
         const int q = warp & 3;                  // TMEM lane quadrant this warp may read
         // column slices of at least 16 (one tcgen05.ld.x16); warps past the last
         // slice only take part in the accumulator hand-off
-        constexpr int NSLICE = (BN / 16) < (EPI_WARPS / 4) ? (BN / 16) : (EPI_WARPS / 4);
+        constexpr int NSLICE = (BN / 16) < (C::EPI / 4) ? (BN / 16) : (C::EPI / 4);
         constexpr int CW = BN / NSLICE;
         const int part = (warp - 2) >> 2;
         const int c_begin = part < NSLICE ? part * CW : 0, c_end = part < NSLICE ? c_begin + CW : 0;
@@ -483,10 +487,11 @@ struct TcOperands {
     int64_t a_rows, lda, b_rows, ldb;
 };
 
-// cudaFuncSetAttribute(kernel, MaxDynamicSharedMemorySize) once per device
-// and kernel instantiation (the attribute is per device)
-template <class Kern>
-int ensure_smem_attr(Kern kernel, int bytes) {
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) of k_tc_gemm<BN, Epi, X3>
+// once per device (the attribute is per device); the flags are per template
+// instantiation, i.e. per kernel
+template <int BN, bool X3, class Epi>
+int ensure_smem_attr() {
     static std::mutex mu;
     static bool done[kMaxDevices] = {};
     int dev = 0;
@@ -494,7 +499,8 @@ int ensure_smem_attr(Kern kernel, int bytes) {
     if (dev < 0 || dev >= kMaxDevices) return TNET_ERR_ARG;
     std::lock_guard<std::mutex> g(mu);
     if (!done[dev]) {
-        TNET_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        TNET_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<BN, Epi, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)TileCfg<BN, X3>::SMEM));
         done[dev] = true;
     }
     return TNET_OK;
@@ -525,12 +531,12 @@ int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *
         mal = ma;
         mbl = mb;
     }
-    if ((rc = ensure_smem_attr(k_tc_gemm<BN, Epi, X3>, (int)C::SMEM))) return rc;
+    if ((rc = ensure_smem_attr<BN, X3, Epi>())) return rc;
     int64_t tiles = 0;
     for (int z = 0; z < P.nclass; ++z) tiles += (int64_t)((P.M[z] + BM - 1) / BM) * ((P.N + BN - 1) / BN);
     if (sms < 1) sms = 1;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    launch(k_tc_gemm<BN, Epi, X3>, grid, THREADS, C::SMEM, st, ma, mb, mal, mbl, P, epi, status);
+    launch(k_tc_gemm<BN, Epi, X3>, grid, C::THREADS, C::SMEM, st, ma, mb, mal, mbl, P, epi, status);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;

@@ -136,12 +136,17 @@ def test_cluster64_energy_forces_weight_grads_and_fd(prec):
         if rel > worst:
             worst_k, worst = k, rel
     # central differences of the GPU energy: along the forces and along a
-    # seeded random field, both normalised to unit RMS displacement per atom
+    # seeded random field, both normalised to unit RMS displacement per atom.
+    # BF16 energies move in steps as rounded operands cross bf16 boundaries,
+    # which a random direction (whose slope is ~sqrt(N) times smaller than
+    # along the forces) resolves only with a wider step: h = 1e-2 A there
+    # (truncation error ~h^2, still far below the bar), 1e-3 A otherwise.
     rng = np.random.default_rng(11)
     fd_rel = []
+    h_fd = 1e-2 if prec == 1 else 1e-3
     for v in (F.astype(np.float64), rng.standard_normal(F.shape)):
         v = v / np.sqrt(np.mean(np.sum(v * v, 1)))
-        fd, an = _directional_fd(m, s, F, v)
+        fd, an = _directional_fd(m, s, F, v, h=h_fd)
         fd_rel.append(abs(fd - an) / abs(an))
     # and of the oracle energy along the forces (FP64, h = 1e-5 A: truncation
     # error ~h^2, rounding ~1e-16 |E| / h, both far below the bar)
