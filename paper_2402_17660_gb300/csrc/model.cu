@@ -1720,6 +1720,105 @@ __global__ void k_emb_bwd_pairs(const float4 *__restrict__ geo, const int32_t *_
     }
 }
 
+// The same adjoint with four consecutive channels per lane (F = 128, exact
+// mode, forces only): every gathered row of gX_raw, the pair's projections
+// and the element tables are float4 loads, a quarter of the load and address
+// instructions of the strided form above.  Offsets are 32-bit (the host
+// checks the sizes).
+template <int F>
+__global__ void __launch_bounds__(256) k_emb_bwd_pairs_v4(const float4 *__restrict__ geo,
+                                                          const int32_t *__restrict__ z,
+                                                          const int2 *__restrict__ uij, const int32_t *__restrict__ ue,
+                                                          const int32_t *__restrict__ rev,
+                                                          const int32_t *__restrict__ nu, int N, int max_z,
+                                                          const float *__restrict__ fu, const float *__restrict__ Ta,
+                                                          const float *__restrict__ Tb,
+                                                          const float *__restrict__ gXraw, float *__restrict__ gfu,
+                                                          float4 *__restrict__ edge_g, OpCopy gfu_cp) {
+    pdl_entry();
+    static_assert(F == 128, "one float4 per lane and row");
+    const int lane = threadIdx.x & 31;
+    const int U = *nu;
+    const uint32_t c4 = 4u * lane;
+    for (int64_t uu = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; uu < U;
+         uu += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int u = (int)uu;
+        const int2 p = uij[u];
+        const int i = p.x, j = p.y;
+        const float4 gu = geo[u];
+        const float ux = gu.x, uy = gu.y, uz = gu.z, phi = gu.w;
+        const float bxx = ux * ux - (1.0f / 3.0f), byy = uy * uy - (1.0f / 3.0f);
+        const float bxy = ux * uy, bxz = ux * uz, byz = uy * uz;
+        int zi = z[i], zj = z[j];
+        zi = (zi < 0 || zi >= max_z) ? 0 : zi;
+        zj = (zj < 0 || zj >= max_z) ? 0 : zj;
+        const uint32_t fb = (uint32_t)u * 3u * F + c4;
+        const float4 f0 = ld4(fu + fb), f1 = ld4(fu + fb + F), f2 = ld4(fu + fb + 2 * F);
+        float4 gi[9], gj[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            gi[q] = ld4(gXraw + coord_row(q, (uint32_t)i, (uint32_t)N, F) + c4);
+            gj[q] = ld4(gXraw + coord_row(q, (uint32_t)j, (uint32_t)N, F) + c4);
+        }
+        const float4 tai = ld4(Ta + (uint32_t)zi * F + c4), tbj = ld4(Tb + (uint32_t)zj * F + c4);
+        const float4 taj = ld4(Ta + (uint32_t)zj * F + c4), tbi = ld4(Tb + (uint32_t)zi * F + c4);
+        float a_phi = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
+        float b_phi = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+        const float vx = -ux, vy = -uy, vz = -uz;
+        float o[3][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            auto el = [k](const float4 &v) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); };
+            float g[9], h[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                g[q] = el(gi[q]);
+                h[q] = el(gj[q]);
+            }
+            const float F0 = el(f0), F1 = el(f1), F2 = el(f2);
+            const float Zij = el(tai) + el(tbj), Zji = el(taj) + el(tbi);
+            const float gc0 = g[0];
+            const float gcA = g[1] * ux + g[2] * uy + g[3] * uz;
+            const float gcS = g[4] * bxx + g[5] * byy + g[6] * bxy + g[7] * bxz + g[8] * byz;
+            a_phi = fmaf(Zij, gc0 * F0 + gcA * F1 + gcS * F2, a_phi);
+            {
+                const float cA = phi * Zij * F1, cS = phi * Zij * F2;
+                ax += cA * g[1] + cS * (2.f * ux * g[4] + uy * g[6] + uz * g[7]);
+                ay += cA * g[2] + cS * (2.f * uy * g[5] + ux * g[6] + uz * g[8]);
+                az += cA * g[3] + cS * (ux * g[7] + uy * g[8]);
+            }
+            const float hc0 = h[0];
+            const float hcA = h[1] * vx + h[2] * vy + h[3] * vz;
+            const float hcS = h[4] * bxx + h[5] * byy + h[6] * bxy + h[7] * bxz + h[8] * byz;
+            b_phi = fmaf(Zji, hc0 * F0 + hcA * F1 + hcS * F2, b_phi);
+            {
+                const float cA = phi * Zji * F1, cS = phi * Zji * F2;
+                bx += cA * h[1] + cS * (2.f * vx * h[4] + vy * h[6] + vz * h[7]);
+                by += cA * h[2] + cS * (2.f * vy * h[5] + vx * h[6] + vz * h[8]);
+                bz += cA * h[3] + cS * (vx * h[7] + vy * h[8]);
+            }
+            o[0][k] = phi * (Zij * gc0 + Zji * hc0);
+            o[1][k] = phi * (Zij * gcA + Zji * hcA);
+            o[2][k] = phi * (Zij * gcS + Zji * hcS);
+        }
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+            st4(gfu + fb + pl * F, make_float4(o[pl][0], o[pl][1], o[pl][2], o[pl][3]));
+            if (gfu_cp.mode) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) opcopy_store(gfu_cp, fb + pl * F + k, o[pl][k]);
+            }
+        }
+        a_phi = warp_sum(a_phi); ax = warp_sum(ax); ay = warp_sum(ay); az = warp_sum(az);
+        b_phi = warp_sum(b_phi); bx = warp_sum(bx); by = warp_sum(by); bz = warp_sum(bz);
+        if (lane == 0) {
+            const int e = ue[u];
+            edge_g[e] = make_float4(a_phi, ax, ay, az);
+            edge_g[rev[e]] = make_float4(b_phi, bx, by, bz);
+        }
+    }
+}
+
 // dE/dr_ij of each undirected pair (i < j): one warp per pair, lane k < K.
 //   dE/dd   = sum_k ge[u][k] de_k/dd + (gphi_mlp[u] + gphi(i,j) + gphi(j,i)) dphi/dd
 //             + dEdd[u]  (the tabulated functions' share, table mode)
@@ -2256,6 +2355,16 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         const tc::TcOperands o{A32, w.b, w.blo, a_rows, lda, b_rows, ldb};
         if (P.N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st, sms);
         if (P.N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st, sms);
+        // num_rbf-deep GEMMs (radial layer 1, the projections) are bound by
+        // their epilogue, not their MMAs: they keep sixteen epilogue warps
+        if (P.K <= 32) {
+            if (P.N % 192 == 0 && bn != 128) return tc::tc_gemm_ops<192, true, true>(P, o, epi, status, st, sms);
+            return tc::tc_gemm_ops<128, true, true>(P, o, epi, status, st, sms);
+        }
+        // 2F-wide outputs: one 256-wide tile when the knob asks for it (fewer
+        // tile loads per MMA: 40 KB of TMA per 880 MMA cycles against 24 KB per
+        // 440 at 128)
+        if (P.N % 256 == 0 && bn == 256) return tc::tc_gemm_ops<256, true>(P, o, epi, status, st, sms);
         if (P.N % 192 == 0 && bn != 128) return tc::tc_gemm_ops<192, true>(P, o, epi, status, st, sms);
         return tc::tc_gemm_ops<128, true>(P, o, epi, status, st, sms);
     };
@@ -2325,10 +2434,11 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
           *hs1 = f32(Lw.hs1), *as2 = f32(Lw.as2), *s = f32(Lw.s), *q0 = f32(Lw.q0);
     float2 *ln0 = wsp<float2>(ctx, Lw.ln0);
     const int atom_blocks = N < sms * ctx->tune[T_ROW_BLOCKS] ? N : sms * ctx->tune[T_ROW_BLOCKS];
-    // message kernels: knob 0 = one warp per row with four channels per lane
-    // (exact mode, F = 128, 32-bit offsets), else that many consecutive rows
-    // per block of F threads (one thread per channel)
-    const int rows_pb = ctx->tune[T_MSG_KERNEL] > 0 ? ctx->tune[T_MSG_KERNEL] : 1;
+    // message kernels (and the pair-parallel embedding adjoint): knob 0 =
+    // one warp per row (pair) with four channels per lane (exact mode,
+    // F = 128, 32-bit offsets), 1 or 4 = that many consecutive rows per block
+    // of F threads (one thread per channel)
+    const int rows_pb = ctx->tune[T_MSG_KERNEL] == 4 ? 4 : 1;
     const bool warp_rows = ctx->tune[T_MSG_KERNEL] == 0 && !tab && F == 128 && 9LL * N * F < (1LL << 31) &&
                            (int64_t)maxU * 3 * F < (1LL << 31);
     const int v4_blocks = (int)((N + kV4Warps - 1) / kV4Warps < atom_blocks ? (N + kV4Warps - 1) / kV4Warps
@@ -2546,8 +2656,8 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         if (tab) {
             TNET_F_SWITCH(F, MSG_BWD_TAB);
         } else if (warp_rows) {
-            launch(k_message_bwd_v4<128>, v4_blocks, 32 * kV4Warps, 0, st, row_ptr, col, pair_of, Y, gM, a3, phiu, N, gY,
-                   nbf, ga3_out, ga3_cp, gphiu);
+            launch(k_message_bwd_v4<128>, v4_blocks, 32 * kV4Warps, 0, st, row_ptr, col, pair_of, Y, gM, a3, phiu, N,
+                   gY, nbf, ga3_out, ga3_cp, gphiu);
         } else {
             TNET_F_SWITCH(F, MSG_BWD);
         }
@@ -2662,6 +2772,10 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     else                                                                                                     \
         launch(k_emb_bwd_pairs<CPL, false>, pair_grid, 256, 0, st, geo, z, uij, ue, rev, nu, N, d.max_z, fu, tf0, Ta, \
                                                              Tb, gXraw, gfu, edge_g, gfu_cp, nullptr)
+    if (!wg && !tab && warp_rows)
+        launch(k_emb_bwd_pairs_v4<128>, pair_grid, 256, 0, st, geo, z, uij, ue, rev, nu, N, d.max_z, fu, Ta, Tb, gXraw,
+               gfu, edge_g, gfu_cp);
+    else
     switch (F / 32) {
         case 2: EMB_BWD(2); break;
         case 4: EMB_BWD(4); break;

@@ -82,8 +82,15 @@ static int debug_f32(int M, int N, int K, const float *A, const float *B, float 
     EpiStore epi{Cout, N, 0};
     const tc::TcOperands o{A, Bsplit, Bsplit + nk, M, K, N, K};
     const int sms = current_sms();
+    // the library's routing: num_rbf-deep GEMMs (K <= 32) keep the 16-warp
+    // epilogue and four stages
     if (N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st, sms);
     if (N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st, sms);
+    if (K <= 32) {
+        if (N % 192 == 0) return tc::tc_gemm_ops<192, true, true>(P, o, epi, status, st, sms);
+        return tc::tc_gemm_ops<128, true, true>(P, o, epi, status, st, sms);
+    }
+    if (N % 256 == 0) return tc::tc_gemm_ops<256, true>(P, o, epi, status, st, sms);
     if (N % 192 == 0) return tc::tc_gemm_ops<192, true>(P, o, epi, status, st, sms);
     return tc::tc_gemm_ops<128, true>(P, o, epi, status, st, sms);
 }

@@ -24,7 +24,7 @@
 // rows for 3xTF32, whose stage holds four tiles), warp 1 owns TMEM and issues
 // the MMAs (32-byte k-steps) into one of two accumulators, so the epilogue of
 // a tile overlaps the MMAs of the next.  Sixteen epilogue warps (eight for
-// the 192-wide 3xTF32 tiles) drain TMEM (warp w reads lanes 32*(w%4) .. +31,
+// the 128- and 192-wide 3xTF32 tiles) drain TMEM (warp w reads lanes 32*(w%4) .. +31,
 // a quarter (half) of the tile's columns each) and run the fused epilogue.  Every mbarrier wait is bounded;
 // on expiry the kernel records TNET_ERR_TIMEOUT, the other roles stop, the
 // producer waits (bounded) for its own copies in flight, TMEM is freed and
@@ -34,6 +34,8 @@
 #include <cuda_bf16.h>
 
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -43,7 +45,6 @@ namespace tc {
 constexpr int BM = 128, CONV_WARPS = 2;
 constexpr int STG_LD = 20;  // floats per staged row (16 + pad, keeps float4 alignment)
 constexpr uint32_t kSpinLimit = 1u << 22;
-constexpr int kMaxDevices = 64;
 
 struct TcShape {
     int M[3];                 // rows per class (capacity when rows_dev is set)
@@ -169,7 +170,7 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint
         : "memory");
 }
 
-template <int BN, bool X3 = false>
+template <int BN, bool X3 = false, bool NK = false>
 struct TileCfg {
     // one k-block is ROW bytes of K per row: 64 bf16 (128-byte rows), or 16
     // fp32 (64-byte rows: the 3xTF32 stage holds A, A_lo, B and B_lo, and the
@@ -183,18 +184,20 @@ struct TileCfg {
     // formed in shared memory)
     static constexpr uint32_t STAGE_TX = A_BYTES + (X3 ? 2 : 1) * B_BYTES;
     static constexpr uint32_t TMEM_COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
-    // epilogue warps: 16, or 8 for the 192-wide 3xTF32 tiles, whose freed
-    // transpose buffers make room for a fifth pipeline stage
-    static constexpr int EPI = (X3 && BN == 192) ? 8 : 16;
+    // epilogue warps: 16, or 8 for the 128- and 192-wide 3xTF32 tiles, whose
+    // freed transpose buffers make room for a deeper pipeline; NK (a K of at
+    // most two k-blocks, whose epilogue outweighs its MMAs) keeps 16 and 4
+    // stages
+    static constexpr int EPI = (X3 && BN >= 128 && !NK) ? 8 : 16;
     static constexpr int THREADS = 64 + 32 * (EPI + CONV_WARPS);
     static constexpr uint32_t STAGE_BYTES = EPI * 32 * STG_LD * 4;  // epilogue transpose buffers
-    // 3xTF32: 4 stages, 5 at BN = 128 and 192 (what fits beside the epilogue
-    // buffers): each stage's split and three MMAs make a long round trip,
-    // which the wide radial layers feel.  The narrow tiles (K-wide outputs)
+    // 3xTF32: 4 stages, and as many as fit beside the epilogue buffers (6 at
+    // BN = 128, 5 at 192, 4 at 256): each stage's split and three MMAs make a
+    // long round trip, which the wide radial layers feel.  The narrow tiles (K-wide outputs)
     // keep 4 and a smaller footprint, which leaves room on the SM for the CTAs
     // of the next kernel that programmatic launch brings in early.
     static constexpr int X3_FIT = (int)((232448 - 1024 - 256 - STAGE_BYTES) / (STAGE_TX + A_BYTES));
-    static constexpr int STAGES = X3 ? ((BN == 128 || BN == 192) && X3_FIT >= 5 ? 5 : 4) : (BN >= 192 ? 3 : 4);
+    static constexpr int STAGES = X3 ? (BN >= 128 && !NK ? (X3_FIT > 6 ? 6 : X3_FIT) : 4) : (BN >= 192 ? 3 : 4);
     static_assert(STAGES >= 2 && 8 * (3 * STAGES + 5) + 8 <= 256, "pipeline barriers exceed their block");
     static constexpr size_t SMEM = 1024 + STAGES * (size_t)(STAGE_TX + (X3 ? A_BYTES : 0)) + 256 + STAGE_BYTES;
     static_assert(SMEM <= 232448, "dynamic shared memory above 227 KB");
@@ -217,13 +220,13 @@ struct TileIter {
 };
 __device__ __forceinline__ int64_t sel3(int z, int64_t a, int64_t b, int64_t c) { return z == 0 ? a : (z == 1 ? b : c); }
 
-template <int BN, class Epi, bool X3>
-__global__ void __launch_bounds__(TileCfg<BN, X3>::THREADS, 1)
+template <int BN, class Epi, bool X3, bool NK = false>
+__global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo, TcShape P,
               Epi epi, int32_t *status) {
     pdl_entry();
-    using C = TileCfg<BN, X3>;
+    using C = TileCfg<BN, X3, NK>;
     constexpr int STAGES = C::STAGES;
     constexpr int BK = C::BKE;
     extern __shared__ uint8_t smem_raw[];
@@ -487,30 +490,27 @@ struct TcOperands {
     int64_t a_rows, lda, b_rows, ldb;
 };
 
-// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) of k_tc_gemm<BN, Epi, X3>
-// once per device (the attribute is per device); the flags are per template
-// instantiation, i.e. per kernel
-template <int BN, bool X3, class Epi>
-int ensure_smem_attr() {
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per device and kernel.
+// Keyed by the kernel's host-side handle and the device (a template kernel
+// used from two translation units can have a handle in each).
+inline int ensure_smem_attr(const void *kern, int bytes) {
     static std::mutex mu;
-    static bool done[kMaxDevices] = {};
+    static std::vector<std::pair<const void *, int>> done;  // (kernel handle, device)
     int dev = 0;
     TNET_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return TNET_ERR_ARG;
     std::lock_guard<std::mutex> g(mu);
-    if (!done[dev]) {
-        TNET_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<BN, Epi, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)TileCfg<BN, X3>::SMEM));
-        done[dev] = true;
-    }
+    for (const auto &d : done)
+        if (d.first == kern && d.second == dev) return TNET_OK;
+    TNET_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done.emplace_back(kern, dev);
     return TNET_OK;
 }
 
 // Launches one persistent GEMM: min(tiles, sms) CTAs, one per SM (`sms` is
 // the SM count of the device the stream runs on).
-template <int BN, bool X3, class Epi>
+template <int BN, bool X3, bool NK = false, class Epi>
 int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *status, cudaStream_t st, int sms) {
-    using C = TileCfg<BN, X3>;
+    using C = TileCfg<BN, X3, NK>;
     const int esz = X3 ? 4 : 2;
     int maxM = 0;
     for (int z = 0; z < P.nclass; ++z) maxM = P.M[z] > maxM ? P.M[z] : maxM;
@@ -531,12 +531,13 @@ int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *
         mal = ma;
         mbl = mb;
     }
-    if ((rc = ensure_smem_attr<BN, X3, Epi>())) return rc;
+    auto kern = k_tc_gemm<BN, Epi, X3, NK>;
+    if ((rc = ensure_smem_attr((const void *)kern, (int)C::SMEM))) return rc;
     int64_t tiles = 0;
     for (int z = 0; z < P.nclass; ++z) tiles += (int64_t)((P.M[z] + BM - 1) / BM) * ((P.N + BN - 1) / BN);
     if (sms < 1) sms = 1;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    launch(k_tc_gemm<BN, Epi, X3>, grid, C::THREADS, C::SMEM, st, ma, mb, mal, mbl, P, epi, status);
+    launch(kern, grid, C::THREADS, C::SMEM, st, ma, mb, mal, mbl, P, epi, status);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;
