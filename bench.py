@@ -506,6 +506,8 @@ def run_ours(args):
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tpath):
             tkey = f"{args.workload}:{args.precision}:{tag}" + (f":table{args.radial_table}" if tab else "")
+            if tag in ("message", "message_bwd", "emb_edges_bwd") and len(knobs) > 6:
+                tkey += f":kernel{knobs[6]}"   # which form of the row kernels ran (the message_kernel knob)
             tr = json.load(open(tpath)).get(tkey)
             if tr and tr.get("kernel_rev") == kernel_revision(tr.get("rev_files")):
                 traffic = tr["bytes_per_launch"]

@@ -137,14 +137,14 @@ def test_cluster64_energy_forces_weight_grads_and_fd(prec):
             worst_k, worst = k, rel
     # central differences of the GPU energy: along the forces and along a
     # seeded random field, both normalised to unit RMS displacement per atom.
-    # BF16 energies move in steps as rounded operands cross bf16 boundaries,
-    # which a random direction (whose slope is ~sqrt(N) times smaller than
-    # along the forces) resolves only with a wider step: h = 1e-2 A there
-    # (truncation error ~h^2, still far below the bar), 1e-3 A otherwise.
+    # h = 1e-3 A (truncation error ~7e-4 along the forces).  BF16 energies
+    # move in steps as rounded operands cross bf16 boundaries, which a random
+    # direction (whose slope is ~sqrt(N) times smaller than along the forces)
+    # resolves only with a wider step: h = 1e-2 A there in BF16 mode (its
+    # truncation error is smaller along that direction).
     rng = np.random.default_rng(11)
     fd_rel = []
-    h_fd = 1e-2 if prec == 1 else 1e-3
-    for v in (F.astype(np.float64), rng.standard_normal(F.shape)):
+    for v, h_fd in ((F.astype(np.float64), 1e-3), (rng.standard_normal(F.shape), 1e-2 if prec == 1 else 1e-3)):
         v = v / np.sqrt(np.mean(np.sum(v * v, 1)))
         fd, an = _directional_fd(m, s, F, v, h=h_fd)
         fd_rel.append(abs(fd - an) / abs(an))

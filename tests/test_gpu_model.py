@@ -380,8 +380,8 @@ def test_autotuner_knobs_change_speed_not_results(tmp_path):
                 trial[k] = v
                 m.set_tuning(trial)
                 E1, F1 = gpu_energy_forces(m, s, nl=nl)
-                assert abs(E1[0] - E0[0]) <= 1e-6 * abs(E0[0]), (name, v)
-                assert force_error(F1, F0) <= 1e-5, (name, v)
+                assert abs(E1[0] - E0[0]) <= 1e-6 * abs(E0[0]), (prec, name, v)
+                assert force_error(F1, F0) <= 1e-5, (prec, name, v, force_error(F1, F0))
         # the cache is read back
         knobs2, _ = autotune(m, z, pos, nl, None, box, 1, cache=str(tmp_path / "t.json"))
         assert knobs2 == knobs
