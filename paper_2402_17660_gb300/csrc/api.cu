@@ -179,6 +179,11 @@ int build_layout(const tnet_model_desc *d, int N, int S, int64_t E, Layout *L) {
     L->md_step = take(i * 4);
     L->md_need = take(i * 4);
     L->md_rebuilds = take(8);
+    // the single-pass neighbor search's row slab (last, so that the neighbor
+    // part at the front of the layout keeps its size)
+    L->slab_width = kSlabWidth;
+    L->slab = take(i * (int64_t)N * kSlabWidth);
+    L->slab_over = take(i * 4);
     L->total = off;
     return TNET_OK;
 }

@@ -60,6 +60,7 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
 
 constexpr int kMaxCellsPerAtom = 2;   // cell budget: 2 cells per atom + 8 per system + 64
 constexpr int kMaxRowSorted = 1024;   // longest CSR row sorted in shared memory
+constexpr int kSlabWidth = 128;       // columns per atom in the single-pass search's row slab
 
 // First device-detected error wins.
 __device__ __forceinline__ void set_status(int32_t *st, int code) {
@@ -358,6 +359,10 @@ struct Layout {
     // neighbor search
     size_t sys_start, sys_end, sysinfo, sys_ncell, cell_count, cell_start, cell_fill, cell_of,
         sorted, spos, rowcnt, scan_tmp;
+    // single-pass search: each row's sorted columns, kSlabWidth per atom, and
+    // the flag of a row that did not fit (slab_width 0: two passes)
+    size_t slab, slab_over;
+    int slab_width;
     // energy / forces: graph bookkeeping
     size_t rev, pair_of, uedge, ucnt, nu, rp_safe;
     // node buffers

@@ -474,6 +474,75 @@ k_pair_fill(const float *__restrict__ pos, const int32_t *__restrict__ batch, in
     }
 }
 
+// Single candidate pass: one warp per atom collects its neighbours (one walk
+// of the 27 cells), sorts them in shared memory and writes the sorted row to
+// the atom's slot of the slab (kSlabWidth columns), with the row's count.  A
+// row longer than kSlabWidth raises `over`; the two-pass fill then runs
+// instead of the copy (gated on it), so the result never depends on the slab.
+__global__ void __launch_bounds__(kFillWarps * 32)
+k_pair_fill_slab(const float *__restrict__ pos, const int32_t *__restrict__ batch, int N,
+                 const SysInfo *__restrict__ info, const int32_t *__restrict__ cell_off,
+                 const int32_t *__restrict__ cell_start, const float4 *__restrict__ spos, float rc2,
+                 int32_t *__restrict__ rowcnt, int32_t *__restrict__ slab, int32_t *__restrict__ over) {
+    pdl_entry();
+    __shared__ int32_t buf[kFillWarps][kSlabWidth];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kFillWarps + w;
+    if (i >= N) return;
+    int32_t *sb = buf[w];
+    int cnt = 0;
+    for_candidates(i, pos, batch, info, cell_off, cell_start, spos, rc2, [&](int j, bool ok) {
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        const int slot = cnt + __popc(m & ((1u << lane) - 1u));
+        if (ok && slot < kSlabWidth) sb[slot] = j;
+        cnt += __popc(m);
+    });
+    if (lane == 0) rowcnt[i] = cnt;
+    if (cnt > kSlabWidth) {
+        if (lane == 0) *over = 1;
+        return;
+    }
+    __syncwarp();
+    int P = 1;
+    while (P < cnt) P <<= 1;
+    for (int k = cnt + lane; k < P; k += 32) sb[k] = 0x7fffffff;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int t = lane; t < P; t += 32) {
+                const int u = t ^ jj;
+                if (u > t) {
+                    const int32_t a = sb[t], b = sb[u];
+                    const bool up = (t & k) == 0;
+                    if ((a > b) == up) {
+                        sb[t] = b;
+                        sb[u] = a;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    int32_t *dst = slab + (int64_t)i * kSlabWidth;
+    for (int k = lane; k < cnt; k += 32) dst[k] = sb[k];
+}
+
+// Rows of the slab into the CSR (warp per row), each within the row offsets
+// (clamped to the capacity when the list overflowed).  Skipped when a row did
+// not fit the slab: the gated two-pass fill writes the list then.
+__global__ void k_slab_copy(const int32_t *__restrict__ slab, const int32_t *__restrict__ row_ptr, int N,
+                            int32_t *__restrict__ col, const int32_t *__restrict__ over) {
+    pdl_entry();
+    if (*over) return;
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < N;
+         i += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int r0 = row_ptr[i], n = row_ptr[i + 1] - r0;
+        const int32_t *src = slab + i * kSlabWidth;
+        for (int k = lane; k < n; k += 32) col[r0 + k] = src[k];
+    }
+}
+
 int neighbors_impl(tnet_ctx *ctx, int N, int S, const float *pos, const int32_t *batch,
                    const float *box, float cutoff, int32_t *row_ptr, int32_t *col, int64_t cap,
                    int64_t *n_pairs_dev, int32_t *status, cudaStream_t st, const int32_t *gate) {
@@ -521,12 +590,22 @@ int neighbors_impl(tnet_ctx *ctx, int N, int S, const float *pos, const int32_t 
     }
     rc = scan_exclusive_i32(cell_count, cell_start, cells, tmp, nullptr, nullptr, st, gate);
     if (rc) return rc;
+    // one candidate pass into the row slab, unless the context has none or
+    // the call is a gated rebuild (MD): then a count pass and a fill pass
+    const bool one_pass = L.slab_width > 0 && !gate && N > 0;
+    int32_t *over = one_pass ? wsp<int32_t>(ctx, L.slab_over) : nullptr;
     if (N > 0) {
         launch(k_scatter, (N + 255) / 256, 256, 0, st, pos, N, cell_of, cell_start, cell_fill, sorted, spos, gate);
         count_launch();
         TNET_LAUNCH_CHECK();
-        launch(k_pair_count, (int)(((int64_t)N * 32 + 255) / 256), 256, 0, st, 
-            pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, rowcnt, gate);
+        if (one_pass) {
+            TNET_CUDA_TRY(cudaMemsetAsync(over, 0, sizeof(int32_t), st));
+            launch(k_pair_fill_slab, (N + kFillWarps - 1) / kFillWarps, kFillWarps * 32, 0, st, pos, batch, N, info,
+                   ncell, cell_start, spos, cutoff * cutoff, rowcnt, wsp<int32_t>(ctx, L.slab), over);
+        } else {
+            launch(k_pair_count, (int)(((int64_t)N * 32 + 255) / 256), 256, 0, st, pos, batch, N, info, ncell,
+                   cell_start, spos, cutoff * cutoff, rowcnt, gate);
+        }
         count_launch();
         TNET_LAUNCH_CHECK();
     }
@@ -537,8 +616,15 @@ int neighbors_impl(tnet_ctx *ctx, int N, int S, const float *pos, const int32_t 
     count_launch();
     TNET_LAUNCH_CHECK();
     if (N > 0) {
-        launch(k_pair_fill, (N + kFillWarps - 1) / kFillWarps, kFillWarps * 32, 0, st, 
-            pos, batch, N, info, ncell, cell_start, spos, cutoff * cutoff, row_ptr, col, cap, gate);
+        if (one_pass) {
+            const int nb = (int)(((int64_t)N * 32 + 255) / 256);
+            launch(k_slab_copy, nb < 4096 ? nb : 4096, 256, 0, st, wsp<int32_t>(ctx, L.slab), row_ptr, N, col, over);
+            count_launch();
+            TNET_LAUNCH_CHECK();
+        }
+        // the fill pass; in one-pass mode gated on a row that did not fit
+        launch(k_pair_fill, (N + kFillWarps - 1) / kFillWarps, kFillWarps * 32, 0, st, pos, batch, N, info, ncell,
+               cell_start, spos, cutoff * cutoff, row_ptr, col, cap, one_pass ? over : gate);
         count_launch();
         TNET_LAUNCH_CHECK();
     }

@@ -76,6 +76,7 @@ extern "C" int tnet_neighbors_noalloc(int n_atoms, int n_systems, const float *p
     rc = build_layout(&c.d, n_atoms, n_systems, 0, &c.lay);
     if (rc) return rc;
     if (c.lay.rev > kNoAllocScratchBytes) return TNET_ERR_WORKSPACE;
+    c.lay.slab_width = 0;  // two-pass search: no row slab in the static array
     c.max_atoms = n_atoms;
     c.max_systems = n_systems;
     c.max_pairs = cap;
