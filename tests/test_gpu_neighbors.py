@@ -82,6 +82,22 @@ def test_workloads_exact(name):
     _check_exact(synth.workload(name))
 
 
+def test_rows_longer_than_the_row_slab_exact():
+    """A dense cloud whose rows exceed the one-pass search's 128-column row
+    slab at a 6 A cutoff: the search falls back to the count and fill passes
+    and the pair list is still exact."""
+    rng = np.random.default_rng(21)
+    for _ in range(20):
+        pos = rng.uniform(0.0, 12.0, (400, 3)).astype(np.float32)
+        s = synth.System("dense400", rng.choice([1, 6, 7, 8], 400).astype(np.int32), pos, np.zeros(400, np.int32),
+                         None, 1)
+        if margin_ok(s, cutoff=6.0):
+            break
+    oi, _ = neighbor_pairs(s.pos, s.batch, None, 6.0)
+    assert np.bincount(oi).max() > 128
+    _check_exact(s, cutoff=6.0)
+
+
 def test_skin_cutoff_exact():
     s = synth.water_box(10, 31.04, seed=1, radii=(5.0, 6.0))
     _check_exact(s, cutoff=6.0)
