@@ -614,7 +614,7 @@ def run_ours(args):
         del g, m, nl
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        line["md"] = run_md(sys_, shape, prec, dev, args)
+        line["md"] = run_md(sys_, shape, prec, dev, args, knobs)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -660,9 +660,10 @@ def per_molecule(sys_, W, prec, dev, args):
             "note": "eager: one tnet_neighbors + tnet_energy_forces call per molecule, no graph"}
 
 
-def run_md(sys_, shape, prec, dev, args):
+def run_md(sys_, shape, prec, dev, args, knobs=None):
     """Velocity Verlet through tnet_md_step (blocks of 20 steps replayed as
-    one CUDA graph): ns/day and total-energy drift."""
+    one CUDA graph): ns/day and total-energy drift, with the launch shapes
+    the autotuner chose for this workload's energy+force step."""
     import torch
     from paper_2402_17660_gb300 import synth
     from paper_2402_17660_gb300.tnet import TensorNet
@@ -672,6 +673,8 @@ def run_md(sys_, shape, prec, dev, args):
     N = sys_.n_atoms
     m = TensorNet(Wmd, max_atoms=N, max_systems=1, max_pairs=int(100 * N) + 1024, precision=prec, device=dev,
                   recompute_edges=recompute_edges(args, N), radial_table=args.radial_table)
+    if knobs is not None:
+        m.set_tuning(knobs)
     z = torch.from_numpy(sys_.z).to(dev)
     pos = torch.from_numpy(sys_.pos).to(dev).clone()
     vel = torch.from_numpy(synth.maxwell_boltzmann(sys_, 300.0, seed=1)).to(dev)
@@ -694,7 +697,8 @@ def run_md(sys_, shape, prec, dev, args):
             "steps_per_s": n / sec, "drift_eV_per_atom_per_ps": float((et[-1] - et[0]) / N / (n * dt * 1e-3)),
             "neighbor_builds": m.md_rebuilds(),
             "rebuild_rule": "every 20 steps and in any step where an atom moved > skin/2 (device-side test)",
-            "status": status, "weights": "random init, output layer scaled by 0.05"}
+            "status": status, "weights": "random init, output layer scaled by 0.05",
+            "tuning": m.get_tuning()}
 
 
 def _definition(text: str, name: str) -> str:
