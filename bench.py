@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recompute-edges", default="auto", choices=["auto", "0", "1"],
                     help="1: recompute the radial-MLP activations in the reverse pass instead of keeping "
-                         "them (auto: from 50,000 atoms on)")
+                         "them (auto: only when keeping them would take over a quarter of device memory)")
     ap.add_argument("--tuning", default="auto",
                     help="auto: autotune launch shapes on this input (cached); default: the library's "
                          "defaults; or a comma-separated knob list")
@@ -359,10 +359,23 @@ def stage_work(tag, nu, N, E, F, K, prec, table=0, rec=False):
     return None
 
 
+KEPT_BYTES_PER_PAIR_SLOT = 4.5 * 1024   # a1, h1, a2, h2, a3 at F = 128: per undirected pair and layer
+
+
 def recompute_edges(args, n_atoms):
-    if args.recompute_edges == "auto":
-        return n_atoms >= 50000
-    return args.recompute_edges == "1"
+    """auto: keep the radial-MLP activations (no second forward through the
+    radial MLP in the reverse pass) unless, at the bench's pair capacity of
+    75 directed pairs per atom and two layers, they would take more than a
+    quarter of the device's memory (about 200,000 atoms on a GB300)."""
+    if args.recompute_edges != "auto":
+        return args.recompute_edges == "1"
+    try:
+        import torch
+        total = torch.cuda.get_device_properties(0).total_memory
+    except Exception:
+        total = 280e9
+    kept = KEPT_BYTES_PER_PAIR_SLOT * (75 * n_atoms / 2) * 2
+    return kept > 0.25 * total
 
 
 def run_ours(args):

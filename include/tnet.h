@@ -290,8 +290,10 @@ int tnet_debug_tc_gemm_timeout(int M, int N, int K, const float *A, const float 
  * choice only changes speed.  Knob k takes
  * one of tnet_tuning_candidates(k, ...) (the count is returned; values are
  * written up to max).  tnet_set_tuning rejects values outside the candidate
- * lists.  An autotuner times the candidates on a real input (as CUDA-graph
- * replays) and sets the fastest (paper_2402_17660_gb300.tnet.autotune). */
+ * lists.  A new context starts from fixed defaults, with programmatic launch
+ * on only when max_atoms <= 1024.  An autotuner times the candidates on a
+ * real input (as CUDA-graph replays) and sets the fastest
+ * (paper_2402_17660_gb300.tnet.autotune). */
 int tnet_tuning_knobs(void);
 const char *tnet_tuning_name(int knob);
 int tnet_tuning_candidates(int knob, int32_t *values, int max);
