@@ -171,15 +171,16 @@ def _axis_permuted(s, perm):
                         s.box.copy(), s.n_systems)
 
 
+@pytest.mark.parametrize("recompute", [False, True], ids=["kept", "recomputed"])
 @pytest.mark.parametrize("prec", [1, 2])
-def test_water96k_invariances_and_fd_in_tensor_core_modes(prec):
-    """In the benchmark's launch configuration (radial-MLP activations
-    recomputed in the reverse pass): zero net force; a cyclic permutation of
-    the axes of the cubic box permutes the forces and keeps the energy; lattice
-    shifts of a third of the atoms change nothing; a central difference along
-    the force field matches the forces."""
+def test_water96k_invariances_and_fd_in_tensor_core_modes(prec, recompute):
+    """In the benchmark's launch configuration (radial-MLP activations kept
+    from the forward pass) and with them recomputed in the reverse pass: zero
+    net force; a cyclic permutation of the axes of the cubic box permutes the
+    forces and keeps the energy; lattice shifts of a third of the atoms change
+    nothing; a central difference along the force field matches the forces."""
     s = synth.workload("water96k")
-    m = _model(s, prec, 100 * s.n_atoms, recompute=True)   # room for the 6 A lists of the FD
+    m = _model(s, prec, 100 * s.n_atoms, recompute=recompute)   # room for the 6 A lists of the FD
     E0, F0 = gpu_energy_forces(m, s)
     rmsF = np.sqrt(np.mean(np.sum(F0.astype(np.float64) ** 2, 1)))
     e_inv = 1e-3 if prec == 1 else 1e-5
@@ -202,3 +203,26 @@ def test_water96k_invariances_and_fd_in_tensor_core_modes(prec):
     assert abs(E2[0] - E0[0]) <= e_inv * abs(E0[0])
     assert force_errors(F2, F0)[0] <= f_inv
     assert abs(fd - an) <= (3e-2 if prec == 1 else 1e-3) * abs(an)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_water96k_kept_and_recomputed_activations_agree_bitwise(prec):
+    """Recomputing the radial-MLP activations in the reverse pass repeats the
+    forward pass's arithmetic, so energies, forces and weight gradients are
+    bitwise those of the run that keeps them."""
+    s = synth.workload("water96k")
+    z, pos, _, box = to_dev(s)
+    out = []
+    for rec in (False, True):
+        m = _model(s, prec, 75 * s.n_atoms, recompute=rec)
+        nl = gpu_pairs(m, s)
+        m.reset_status()
+        E, F, G = m.energy_forces(z, pos, nl, None, box, 1, forces=True, grad_weights=True)
+        torch.cuda.synchronize()
+        m.check_status("energy_forces")
+        out.append((E.cpu().numpy(), F.cpu().numpy(), G.cpu().numpy()))
+        del m, nl, E, F, G
+        torch.cuda.empty_cache()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
