@@ -404,8 +404,11 @@ void count_launch();
 // Stages timed by the optional CUDA-event profiler (tnet_profile).
 // Tuning knobs: 0 SIMT-GEMM CTAs per SM, 1 tcgen05 column tile for N = 3F,
 // 2 tcgen05 column tile for N = 2F, 3 row-kernel blocks per SM, 4 pair-kernel
-// blocks (256 threads) per SM, 5 programmatic dependent launch on (1) or off.
-enum TuneKnob { T_GEMM_CTAS = 0, T_TC_BN_3F, T_TC_BN_2F, T_ROW_BLOCKS, T_PAIR_BLOCKS, T_PDL, T_MSG_KERNEL, T_NKNOBS };
+// blocks (256 threads) per SM, 5 programmatic dependent launch on (1) or off,
+// 6 message-kernel form.
+enum TuneKnob {
+    T_GEMM_CTAS = 0, T_TC_BN_3F, T_TC_BN_2F, T_ROW_BLOCKS, T_PAIR_BLOCKS, T_PDL, T_MSG_KERNEL, T_NKNOBS
+};
 
 enum ProfTag {
     P_NBR = 0, P_PREP, P_EMB_EDGE, P_EMB_NODE, P_MLP1, P_MLP2, P_MLP3, P_MESSAGE, P_NODE_MIX,

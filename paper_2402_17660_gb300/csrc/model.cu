@@ -1242,8 +1242,8 @@ __global__ void __launch_bounds__(32 * kV4Warps, 3) k_message_v4(const int32_t *
 // dot products.  One lower edge's gathers are in flight at a time, and an
 // upper edge gathers gM_j (with a3) and then Y_j, which keeps the kernel
 // within 255 registers without spills (two blocks, eight warps per SM).
-template <int F>
-__global__ void __launch_bounds__(32 * kV4Warps, 2)
+template <int F, int MINB>
+__global__ void __launch_bounds__(32 * kV4Warps, MINB)
     k_message_bwd_v4(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
                      const int32_t *__restrict__ pair_of, const float *__restrict__ Y,
                      const float *__restrict__ gM, const float *__restrict__ a3, const float *__restrict__ phiu,
@@ -1259,16 +1259,22 @@ __global__ void __launch_bounds__(32 * kV4Warps, 2)
     float4(*s_gm)[F / 4] = s_own[w][1];
     const int nw = gridDim.x * kV4Warps;
     for (int i = blockIdx.x * kV4Warps + w; i < N; i += nw) {
+        // row i's Y and gM into shared memory, one coordinate row at a time
+#pragma unroll 1
+        for (int q = 0; q < 9; ++q) {
+            const uint32_t b = coord_row(q, (uint32_t)i, (uint32_t)N, F) + 4u * lane;
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                s_y[q][lane + 32 * r] = ld4(Y + b + 128 * r);
+                s_gm[q][lane + 32 * r] = ld4(gM + b + 128 * r);
+            }
+        }
         float4 acc[9][PER];
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const uint32_t b = coord_row(q, (uint32_t)i, (uint32_t)N, F) + 4u * lane;
 #pragma unroll
-            for (int r = 0; r < PER; ++r) {
-                acc[q][r] = ld4(gY + b + 128 * r);
-                s_y[q][lane + 32 * r] = ld4(Y + b + 128 * r);
-                s_gm[q][lane + 32 * r] = ld4(gM + b + 128 * r);
-            }
+            for (int r = 0; r < PER; ++r) acc[q][r] = ld4(gY + b + 128 * r);
         }
         // each lane reads back only what it wrote: no barrier needed
         const int e0 = row_ptr[i], e1 = row_ptr[i + 1];
@@ -1340,18 +1346,17 @@ __global__ void __launch_bounds__(32 * kV4Warps, 2)
                 // two rounds of gathers (gM_j with a3, then Y_j), so that only
                 // one 9-row block is live at a time
                 const uint32_t ab = (uint32_t)u * 3u * F + 4u * lane;
-                float4 sp[3][PER], a[3][PER];
-#pragma unroll
-                for (int p = 0; p < 3; ++p)
-#pragma unroll
-                    for (int r = 0; r < PER; ++r) {
-                        a[p][r] = ld4(a3 + ab + p * F + 128 * r);
-                        sp[p][r] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                float4 gv[3][PER];
+                float4 sp[3][PER], gv[3][PER];
                 float rsum = 0.f;
                 {
-                    float4 gm[9][PER];
+                    float4 a[3][PER], gm[9][PER];
+#pragma unroll
+                    for (int p = 0; p < 3; ++p)
+#pragma unroll
+                        for (int r = 0; r < PER; ++r) {
+                            a[p][r] = ld4(a3 + ab + p * F + 128 * r);
+                            sp[p][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
 #pragma unroll
                     for (int q = 0; q < 9; ++q) {
                         const uint32_t bq = coord_row(q, (uint32_t)j, (uint32_t)N, F) + 4u * lane;
@@ -1391,7 +1396,10 @@ __global__ void __launch_bounds__(32 * kV4Warps, 2)
                 for (int p = 0; p < 3; ++p)
 #pragma unroll
                     for (int r = 0; r < PER; ++r) {
-                        const float av[4] = {a[p][r].x, a[p][r].y, a[p][r].z, a[p][r].w};
+                        // a3 again (just read by this warp: an L1 or L2 hit) rather
+                        // than held through both gather rounds
+                        const float4 ar = ld4(a3 + ab + p * F + 128 * r);
+                        const float av[4] = {ar.x, ar.y, ar.z, ar.w};
                         const float sv4[4] = {sp[p][r].x, sp[p][r].y, sp[p][r].z, sp[p][r].w};
                         float gav[4];
 #pragma unroll
@@ -2436,11 +2444,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     const int atom_blocks = N < sms * ctx->tune[T_ROW_BLOCKS] ? N : sms * ctx->tune[T_ROW_BLOCKS];
     // message kernels (and the pair-parallel embedding adjoint): knob 0 =
     // one warp per row (pair) with four channels per lane (exact mode,
-    // F = 128, 32-bit offsets), 1 or 4 = that many consecutive rows per block
-    // of F threads (one thread per channel)
+    // F = 128, 32-bit offsets; the adjoint at two blocks per SM), 3 = the
+    // same with the adjoint at three blocks per SM, 1 or 4 = that many
+    // consecutive rows per block of F threads (one thread per channel)
     const int rows_pb = ctx->tune[T_MSG_KERNEL] == 4 ? 4 : 1;
-    const bool warp_rows = ctx->tune[T_MSG_KERNEL] == 0 && !tab && F == 128 && 9LL * N * F < (1LL << 31) &&
-                           (int64_t)maxU * 3 * F < (1LL << 31);
+    const bool warp_rows = (ctx->tune[T_MSG_KERNEL] == 0 || ctx->tune[T_MSG_KERNEL] == 3) && !tab && F == 128 &&
+                           9LL * N * F < (1LL << 31) && (int64_t)maxU * 3 * F < (1LL << 31);
     const int v4_blocks = (int)((N + kV4Warps - 1) / kV4Warps < atom_blocks ? (N + kV4Warps - 1) / kV4Warps
                                                                              : atom_blocks);
 #define EMB_FWD(FF)                                                                                           \
@@ -2656,8 +2665,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         if (tab) {
             TNET_F_SWITCH(F, MSG_BWD_TAB);
         } else if (warp_rows) {
-            launch(k_message_bwd_v4<128>, v4_blocks, 32 * kV4Warps, 0, st, row_ptr, col, pair_of, Y, gM, a3, phiu, N,
-                   gY, nbf, ga3_out, ga3_cp, gphiu);
+            if (ctx->tune[T_MSG_KERNEL] == 3)
+                launch(k_message_bwd_v4<128, 3>, v4_blocks, 32 * kV4Warps, 0, st, row_ptr, col, pair_of, Y, gM, a3,
+                       phiu, N, gY, nbf, ga3_out, ga3_cp, gphiu);
+            else
+                launch(k_message_bwd_v4<128, 2>, v4_blocks, 32 * kV4Warps, 0, st, row_ptr, col, pair_of, Y, gM, a3,
+                       phiu, N, gY, nbf, ga3_out, ga3_cp, gphiu);
         } else {
             TNET_F_SWITCH(F, MSG_BWD);
         }
