@@ -169,6 +169,28 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accum)
         : "memory");
 }
+// The same with A in TMEM: row m of A in lane m, one TF32 element of K per
+// 32-bit column (8 columns per k-step)
+__device__ __forceinline__ void umma_tf32_at(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                             uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+// this thread's 16 consecutive 32-bit columns of its TMEM lane
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float v[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+        "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+        "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
 
 template <int BN, bool X3 = false, bool NK = false>
 struct TileCfg {
@@ -183,13 +205,25 @@ struct TileCfg {
     // bytes TMA brings per pipeline stage: A, B (+ B_lo for TF32X3; A_lo is
     // formed in shared memory)
     static constexpr uint32_t STAGE_TX = A_BYTES + (X3 ? 2 : 1) * B_BYTES;
-    static constexpr uint32_t TMEM_COLS = 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
+    // 3xTF32 at BN = 128 or 192 (K beyond two k-blocks): A's split goes to
+    // TMEM instead of shared memory.  Four converter warps (one per TMEM lane
+    // quadrant) read each landed A row, split it and store A_hi and A_lo with
+    // tcgen05.st into the stage's 32 columns after the two accumulators; the
+    // MMAs then read only B from shared memory.  Per 16-deep k-block at
+    // BN = 192 that cuts the shared-memory traffic from ~128 KB (MMA operand
+    // reads 60, TMA writes 32, split 24, epilogue 12) to ~88 KB, against the
+    // 660 tensor-core cycles of its six MMAs at 128 bytes per cycle.
+    static constexpr bool A_TMEM = X3 && !NK && (BN == 128 || BN == 192);
+    static constexpr int CONV = A_TMEM ? 4 : CONV_WARPS;
+    static constexpr uint32_t A_COL = 2 * BN;  // TMEM column of stage 0's A_hi (A_TMEM)
+    static constexpr uint32_t TMEM_COLS =
+        A_TMEM ? 512 : (2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512);
     // epilogue warps: 16, or 8 for the 128- and 192-wide 3xTF32 tiles, whose
     // freed transpose buffers make room for a deeper pipeline; NK (a K of at
     // most two k-blocks, whose epilogue outweighs its MMAs) keeps 16 and 4
     // stages
     static constexpr int EPI = (X3 && BN >= 128 && !NK) ? 8 : 16;
-    static constexpr int THREADS = 64 + 32 * (EPI + CONV_WARPS);
+    static constexpr int THREADS = 64 + 32 * (EPI + CONV);
     static constexpr uint32_t STAGE_BYTES = EPI * 32 * STG_LD * 4;  // epilogue transpose buffers
     // 3xTF32: 4 stages, and as many as fit beside the epilogue buffers (6 at
     // BN = 128, 5 at 192, 4 at 256): each stage's split and three MMAs make a
@@ -197,9 +231,13 @@ struct TileCfg {
     // keep 4 and a smaller footprint, which leaves room on the SM for the CTAs
     // of the next kernel that programmatic launch brings in early.
     static constexpr int X3_FIT = (int)((232448 - 1024 - 256 - STAGE_BYTES) / (STAGE_TX + A_BYTES));
-    static constexpr int STAGES = X3 ? (BN >= 128 && !NK ? (X3_FIT > 6 ? 6 : X3_FIT) : 4) : (BN >= 192 ? 3 : 4);
+    // (A_TMEM: four stages, the A slots TMEM holds beside two accumulators)
+    static constexpr int STAGES =
+        A_TMEM ? 4 : X3 ? (BN >= 128 && !NK ? (X3_FIT > 6 ? 6 : X3_FIT) : 4) : (BN >= 192 ? 3 : 4);
+    static_assert(!A_TMEM || A_COL + 32 * STAGES <= 512, "A slots exceed TMEM");
     static_assert(STAGES >= 2 && 8 * (3 * STAGES + 5) + 8 <= 256, "pipeline barriers exceed their block");
-    static constexpr size_t SMEM = 1024 + STAGES * (size_t)(STAGE_TX + (X3 ? A_BYTES : 0)) + 256 + STAGE_BYTES;
+    static constexpr size_t SMEM =
+        1024 + STAGES * (size_t)(STAGE_TX + (X3 && !A_TMEM ? A_BYTES : 0)) + 256 + STAGE_BYTES;
     static_assert(SMEM <= 232448, "dynamic shared memory above 227 KB");
 };
 
@@ -235,7 +273,7 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * C::A_BYTES;
     uint8_t *sAlo = sB + STAGES * C::B_BYTES;
-    uint8_t *sBlo = sAlo + (X3 ? STAGES * C::A_BYTES : 0);
+    uint8_t *sBlo = sAlo + (X3 && !C::A_TMEM ? STAGES * C::A_BYTES : 0);
     uint64_t *full = (uint64_t *)(sBlo + (X3 ? STAGES * C::B_BYTES : 0));
     uint64_t *empty = full + STAGES;
     uint64_t *acc_full = empty + STAGES;
@@ -267,7 +305,7 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
-            mbar_init(&conv[s], CONV_WARPS);
+            mbar_init(&conv[s], C::CONV);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
@@ -344,7 +382,14 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
                     for (int k = 0; k < C::KSTEPS; ++k) {
                         const uint64_t da = sdesc_sw<C::ROW>(a0 + k * 32), db = sdesc_sw<C::ROW>(b0 + k * 32);
                         const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-                        if (X3) {
+                        if constexpr (C::A_TMEM) {
+                            // stage s's A_hi at columns A_COL + 32 s, A_lo 16 further
+                            const uint32_t ah = tmem + C::A_COL + (uint32_t)(32 * s + 8 * k);
+                            const uint32_t bl = smem_u32(sBlo + s * C::B_BYTES);
+                            umma_tf32_at(d, ah, db, idesc, acc);
+                            umma_tf32_at(d, ah + 16, db, idesc, 1u);
+                            umma_tf32_at(d, ah, sdesc_sw<C::ROW>(bl + k * 32), idesc, 1u);
+                        } else if (X3) {
                             const uint32_t al = smem_u32(sAlo + s * C::A_BYTES), bl = smem_u32(sBlo + s * C::B_BYTES);
                             umma_tf32(d, da, db, idesc, acc);
                             umma_tf32(d, sdesc_sw<C::ROW>(al + k * 32), db, idesc, 1u);
@@ -384,20 +429,45 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
                         ok = false;
                         break;
                     }
-                    float4 *hi = reinterpret_cast<float4 *>(sA + s * C::A_BYTES);
-                    float4 *lo = reinterpret_cast<float4 *>(sAlo + s * C::A_BYTES);
+                    if constexpr (C::A_TMEM) {
+                        // this lane's row of the tile (= its TMEM lane): 16 fp32
+                        // in four 16-byte chunks, chunk c stored at c ^ ((r >> 1) & 3)
+                        // (TMA's 64-byte swizzle)
+                        const int q = warp & 3, r = 32 * q + lane;
+                        const float4 *row = reinterpret_cast<const float4 *>(sA + s * C::A_BYTES + r * 64);
+                        float h[16], l[16];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float4 v = row[c ^ ((r >> 1) & 3)];
+                            tf32_split(v.x, h[4 * c], l[4 * c]);
+                            tf32_split(v.y, h[4 * c + 1], l[4 * c + 1]);
+                            tf32_split(v.z, h[4 * c + 2], l[4 * c + 2]);
+                            tf32_split(v.w, h[4 * c + 3], l[4 * c + 3]);
+                        }
+                        // stage s's TMEM columns were last read by the MMAs of
+                        // k-block kg - STAGES, which retired before TMA refilled
+                        // stage s (the producer waited on empty[s])
+                        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + C::A_COL + (uint32_t)(32 * s);
+                        tmem_st16(ta, h);
+                        tmem_st16(ta + 16, l);
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        fence_before();
+                    } else {
+                        float4 *hi = reinterpret_cast<float4 *>(sA + s * C::A_BYTES);
+                        float4 *lo = reinterpret_cast<float4 *>(sAlo + s * C::A_BYTES);
 #pragma unroll 4
-                    for (int i = ct; i < (int)(C::A_BYTES / 16); i += 32 * CONV_WARPS) {
-                        float4 v = hi[i], l;
-                        tf32_split(v.x, v.x, l.x);
-                        tf32_split(v.y, v.y, l.y);
-                        tf32_split(v.z, v.z, l.z);
-                        tf32_split(v.w, v.w, l.w);
-                        hi[i] = v;
-                        lo[i] = l;
+                        for (int i = ct; i < (int)(C::A_BYTES / 16); i += 32 * CONV_WARPS) {
+                            float4 v = hi[i], l;
+                            tf32_split(v.x, v.x, l.x);
+                            tf32_split(v.y, v.y, l.y);
+                            tf32_split(v.z, v.z, l.z);
+                            tf32_split(v.w, v.w, l.w);
+                            hi[i] = v;
+                            lo[i] = l;
+                        }
+                        // make the generic-proxy writes visible to the tensor core
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     }
-                    // make the generic-proxy writes visible to the tensor core
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&conv[s]);
                 }

@@ -41,11 +41,13 @@ def test_tc_gemm_matches_matmul(M, N, K):
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 32), (1, 32, 32), (300, 128, 128), (777, 384, 256), (129, 64, 384),
                                    (4096, 256, 128), (200, 64, 36), (3000, 32, 384), (20000, 128, 256),
-                                   (8192, 384, 384), (5000, 384, 32), (3001, 256, 24)])
+                                   (8192, 384, 384), (5000, 384, 32), (3001, 256, 24), (1500, 384, 100),
+                                   (999, 128, 52)])
 def test_tc_gemm_3xtf32_matches_fp64(M, N, K):
-    """3xTF32 (A B + A_lo B + A B_lo on the tensor cores, A_lo formed in
-    shared memory) reaches FP32-level accuracy on fp32 inputs, including a
-    ragged last k-block and persistent CTAs whose stages wrap many times.
+    """3xTF32 (A B + A_lo B + A B_lo on the tensor cores, A's split formed in
+    shared memory, or in tensor memory for the 128- and 192-wide tiles)
+    reaches FP32-level accuracy on fp32 inputs, including a ragged last
+    k-block and persistent CTAs whose stages wrap many times.
     Each operand is split into its nearest TF32 value and the TF32-rounded
     remainder (below 2^-11 of the value, rounded to within 2^-22 of it), so
     the three products miss the exact one by less than 3 * 2^-22 |a||b| (plus
