@@ -232,8 +232,10 @@ struct TileCfg {
     // of the next kernel that programmatic launch brings in early.
     static constexpr int X3_FIT = (int)((232448 - 1024 - 256 - STAGE_BYTES) / (STAGE_TX + A_BYTES));
     // (A_TMEM: four stages, the A slots TMEM holds beside two accumulators)
+    // BF16: four stages (three at BN = 256, where four do not fit beside the
+    // epilogue buffers)
     static constexpr int STAGES =
-        A_TMEM ? 4 : X3 ? (BN >= 128 && !NK ? (X3_FIT > 6 ? 6 : X3_FIT) : 4) : (BN >= 192 ? 3 : 4);
+        A_TMEM ? 4 : X3 ? (BN >= 128 && !NK ? (X3_FIT > 6 ? 6 : X3_FIT) : 4) : (BN >= 256 ? 3 : 4);
     static_assert(!A_TMEM || A_COL + 32 * STAGES <= 512, "A slots exceed TMEM");
     static_assert(STAGES >= 2 && 8 * (3 * STAGES + 5) + 8 <= 256, "pipeline barriers exceed their block");
     static constexpr size_t SMEM =
