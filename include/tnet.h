@@ -272,6 +272,14 @@ int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void *B, float 
  * multiple of 4 and <= 512. */
 int tnet_debug_tc_gemm_f32(int M, int N, int K, const float *A, const float *B, float *B_split, float *C,
                            int32_t *status_dev, tnet_stream_t stream);
+/* Either of the two above (x3 = 1: 3xTF32, B_split as there; x3 = 0: BF16,
+ * B_split unused) with the CTAs in thread-block clusters of `cluster` (1, 2
+ * or 4) that share each weight stage through TMA multicast, the form the
+ * library uses for one-class GEMMs; TNET_ERR_ARG for another cluster size or
+ * the shape errors above.  A tile whose rows do not split into whole 8-row
+ * groups per CTA runs without clusters. */
+int tnet_debug_tc_gemm_cluster(int M, int N, int K, int x3, int cluster, const void *A, const void *B,
+                               float *B_split, float *C, int32_t *status_dev, tnet_stream_t stream);
 /* Test of the failure path of the tensor-core kernel (no counterpart in the
  * paper): the 3xTF32 GEMM above with its MMA issuer told to issue nothing and
  * every mbarrier wait bounded by spin_limit (>= 1) tries instead of the

@@ -38,6 +38,7 @@ SIGNATURES = {
     "tnet_md_neighbor_list": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _vp]),
     "tnet_neighbors_noalloc": (_i32, [_i32, _i32, _vp, _vp, _vp, _f32, _vp, _vp, _i64, _vp, _vp, _vp]),
     "tnet_debug_tc_gemm": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "tnet_debug_tc_gemm_cluster": (_i32, [_i32, _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tnet_debug_tc_gemm_f32": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "tnet_debug_tc_gemm_timeout": (_i32, [_i32, _i32, _i32, _vp, _vp, _vp, _vp, ctypes.c_uint32, _vp, _vp]),
     "tnet_tuning_knobs": (_i32, []),

@@ -218,17 +218,17 @@ thread_local int tnet::tl_pdl = 1;
 
 // Candidate values of each tuning knob (TuneKnob) and the default's index.
 static const int kTuneCandidates[T_NKNOBS][4] = {{1, 2, 3, 4}, {192, 128, 0, 0}, {256, 128, 0, 0}, {4, 8, 16, 0},
-                                                 {4, 8, 16, 0}, {1, 0, 0, 0}, {0, 1, 4, 3}};
-static const int kTuneCount[T_NKNOBS] = {4, 2, 2, 3, 3, 2, 4};
+                                                 {4, 8, 16, 0}, {1, 0, 0, 0}, {0, 1, 4, 3}, {2, 1, 4, 0}};
+static const int kTuneCount[T_NKNOBS] = {4, 2, 2, 3, 3, 2, 4, 3};
 // Defaults: the shapes the autotuner picks on most measured workloads (24k to
 // 96k atoms, both tensor-core precisions).  Programmatic launch is on only for
 // contexts of at most kPdlMaxAtoms atoms, the launch-bound systems it speeds up;
 // from a few thousand atoms on it was measured to slow the step by 5-15%.
-static const int kTuneDefault[T_NKNOBS] = {2, 0, 0, 2, 2, 1, 3};
+static const int kTuneDefault[T_NKNOBS] = {2, 0, 0, 2, 2, 1, 3, 0};
 static const int64_t kPdlMaxAtoms = 1024;
 static const char *kTuneNames[T_NKNOBS] = {"gemm_ctas_per_sm",   "tc_tile_n_3f",        "tc_tile_n_2f",
                                            "row_blocks_per_sm",  "pair_blocks_per_sm",  "programmatic_launch",
-                                           "message_kernel"};
+                                           "message_kernel",     "tc_cluster"};
 
 static const char *kTagNames[P_NTAGS] = {
     "neighbors", "graph_prep", "emb_edges", "emb_node", "mlp1", "mlp2", "mlp3", "message",

@@ -58,6 +58,34 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);  // errors surface in cudaGetLastError
 }
 
+// The same with a 1-D thread-block cluster of `cluster` CTAs (1: none).
+template <typename... KArgs, typename... Args>
+inline void launch_cluster(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int cluster,
+                           Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    int n = 0;
+    if (cluster > 1) {
+        attr[n].id = cudaLaunchAttributeClusterDimension;
+        attr[n].val.clusterDim.x = (unsigned)cluster;
+        attr[n].val.clusterDim.y = 1;
+        attr[n].val.clusterDim.z = 1;
+        ++n;
+    }
+    if (tl_pdl) {
+        attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[n].val.programmaticStreamSerializationAllowed = 1;
+        ++n;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = n;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);  // errors surface in cudaGetLastError
+}
+
 constexpr int kMaxCellsPerAtom = 2;   // cell budget: 2 cells per atom + 8 per system + 64
 constexpr int kMaxRowSorted = 1024;   // longest CSR row sorted in shared memory
 constexpr int kSlabWidth = 128;       // columns per atom in the single-pass search's row slab
@@ -405,9 +433,9 @@ void count_launch();
 // Tuning knobs: 0 SIMT-GEMM CTAs per SM, 1 tcgen05 column tile for N = 3F,
 // 2 tcgen05 column tile for N = 2F, 3 row-kernel blocks per SM, 4 pair-kernel
 // blocks (256 threads) per SM, 5 programmatic dependent launch on (1) or off,
-// 6 message-kernel form.
+// 6 message-kernel form, 7 CTAs per cluster of the one-class tcgen05 GEMMs.
 enum TuneKnob {
-    T_GEMM_CTAS = 0, T_TC_BN_3F, T_TC_BN_2F, T_ROW_BLOCKS, T_PAIR_BLOCKS, T_PDL, T_MSG_KERNEL, T_NKNOBS
+    T_GEMM_CTAS = 0, T_TC_BN_3F, T_TC_BN_2F, T_ROW_BLOCKS, T_PAIR_BLOCKS, T_PDL, T_MSG_KERNEL, T_TC_CLUSTER, T_NKNOBS
 };
 
 enum ProfTag {

@@ -2358,9 +2358,11 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     }
     // 3xTF32 tensor-core GEMM: fp32 A (split in the kernel) against weight
     // operand w (its TF32 split)
-    auto tcx3 = [&](const tc::TcShape &P, const float *A32, int64_t a_rows, int64_t lda, const WOp &w,
+    auto tcx3 = [&](const tc::TcShape &P0, const float *A32, int64_t a_rows, int64_t lda, const WOp &w,
                     int64_t b_rows, int64_t ldb, const auto &epi, int bn = 0) -> int {
         const tc::TcOperands o{A32, w.b, w.blo, a_rows, lda, b_rows, ldb};
+        tc::TcShape P = P0;
+        P.cl = ctx->tune[T_TC_CLUSTER];
         if (P.N <= 32) return tc::tc_gemm_ops<32, true>(P, o, epi, status, st, sms);
         if (P.N <= 64) return tc::tc_gemm_ops<64, true>(P, o, epi, status, st, sms);
         // num_rbf-deep GEMMs (radial layer 1, the projections) are bound by
@@ -2379,9 +2381,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     // tensor-core GEMM of the mode: BF16 (A's bf16 copy) or 3xTF32 (A itself)
     auto tcg = [&](const tc::TcShape &P, const float *A32, const OpCopy &Acp, int64_t a_rows, int64_t lda,
                    const WOp &w, int64_t b_rows, int64_t ldb, const auto &epi, int bn = 0) -> int {
-        if (prec == 1)
-            return tc_any(P, (const __nv_bfloat16 *)Acp.p, a_rows, lda, (const __nv_bfloat16 *)w.b, b_rows, ldb,
+        if (prec == 1) {
+            tc::TcShape Q = P;
+            Q.cl = ctx->tune[T_TC_CLUSTER];
+            return tc_any(Q, (const __nv_bfloat16 *)Acp.p, a_rows, lda, (const __nv_bfloat16 *)w.b, b_rows, ldb,
                           epi, status, st, sms, bn);
+        }
         return tcx3(P, A32, a_rows, lda, w, b_rows, ldb, epi, bn);
     };
     TNET_CUDA_TRY(cudaMemsetAsync(sys_start, 0, sizeof(int32_t) * S, st));

@@ -70,7 +70,7 @@ static int current_sms() {
 }
 
 static int debug_f32(int M, int N, int K, const float *A, const float *B, float *Bsplit, float *Cout,
-                     int32_t *status, tnet_stream_t stream, uint32_t spin_limit, int skip_mma) {
+                     int32_t *status, tnet_stream_t stream, uint32_t spin_limit, int skip_mma, int cl = 1) {
     if (M < 1 || N < 4 || N > 512 || K < 4 || K % 4 || N % 4 || !A || !B || !Bsplit || !Cout) return TNET_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nk = (int64_t)N * K;
@@ -79,6 +79,7 @@ static int debug_f32(int M, int N, int K, const float *A, const float *B, float 
     tc::TcShape P = tc::tshape(M, N, K);
     P.spin_limit = spin_limit;
     P.skip_mma = skip_mma;
+    P.cl = cl;
     EpiStore epi{Cout, N, 0};
     const tc::TcOperands o{A, Bsplit, Bsplit + nk, M, K, N, K};
     const int sms = current_sms();
@@ -106,10 +107,11 @@ extern "C" int tnet_debug_tc_gemm_timeout(int M, int N, int K, const float *A, c
     return debug_f32(M, N, K, A, B, Bsplit, Cout, status, stream, spin_limit, 1);
 }
 
-extern "C" int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void *B, float *Cout, int32_t *status,
-                                  tnet_stream_t stream) {
+static int debug_bf16(int M, int N, int K, const void *A, const void *B, float *Cout, int32_t *status,
+                      tnet_stream_t stream, int cl) {
     if (M < 1 || N < 4 || N > 512 || K < 8 || K % 8 || N % 4 || !A || !B || !Cout) return TNET_ERR_ARG;
     tc::TcShape P = tc::tshape(M, N, K);
+    P.cl = cl;
     EpiStore epi{Cout, N, 0};
     const __nv_bfloat16 *a = (const __nv_bfloat16 *)A, *b = (const __nv_bfloat16 *)B;
     cudaStream_t st = (cudaStream_t)stream;
@@ -119,4 +121,17 @@ extern "C" int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void
     if (N <= 128) return tc::tc_gemm<128>(P, a, M, K, b, N, K, epi, status, st, sms);
     if (N % 192 == 0) return tc::tc_gemm<192>(P, a, M, K, b, N, K, epi, status, st, sms);
     return tc::tc_gemm<256>(P, a, M, K, b, N, K, epi, status, st, sms);
+}
+
+extern "C" int tnet_debug_tc_gemm(int M, int N, int K, const void *A, const void *B, float *Cout, int32_t *status,
+                                  tnet_stream_t stream) {
+    return debug_bf16(M, N, K, A, B, Cout, status, stream, 1);
+}
+
+extern "C" int tnet_debug_tc_gemm_cluster(int M, int N, int K, int x3, int cluster, const void *A, const void *B,
+                                          float *B_split, float *Cout, int32_t *status, tnet_stream_t stream) {
+    if (cluster != 1 && cluster != 2 && cluster != 4) return TNET_ERR_ARG;
+    if (x3)
+        return debug_f32(M, N, K, (const float *)A, (const float *)B, B_split, Cout, status, stream, 0, 0, cluster);
+    return debug_bf16(M, N, K, A, B, Cout, status, stream, cluster);
 }

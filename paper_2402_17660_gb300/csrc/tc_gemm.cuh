@@ -58,6 +58,12 @@ struct TcShape {
     // bounded waits run out with no MMA and no unconsumed copy in flight
     uint32_t spin_limit;
     int skip_mma;
+    // CTAs per thread-block cluster (0 or 1: none; 2 or 4 for a one-class
+    // GEMM): the cluster's CTAs take consecutive 128-row tiles of the same
+    // column tile, and each loads 1/cl of every B (and B_lo) stage with TMA
+    // multicast into all of them, so the weights stream from L2 once per
+    // cl * 128 rows instead of once per 128
+    int cl;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -99,6 +105,25 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
+// the same into every CTA of the cluster in `mask` (same shared-memory offset;
+// each destination's barrier at the offset of `bar` receives the bytes)
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, "
+        "{%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// every thread of every CTA of the cluster
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
                  : "memory");
@@ -123,6 +148,14 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
+}
+// the same arrival on the barrier at this offset in every CTA of `mask`
+__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     uint32_t r[16];
@@ -194,28 +227,32 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float v[16]) {
 
 template <int BN, bool X3 = false, bool NK = false>
 struct TileCfg {
-    // one k-block is ROW bytes of K per row: 64 bf16 (128-byte rows), or 16
-    // fp32 (64-byte rows: the 3xTF32 stage holds A, A_lo, B and B_lo, and the
-    // halved rows let four stages fit)
-    static constexpr int ROW = X3 ? 64 : 128;
-    static constexpr int BKE = X3 ? 16 : 64;
+    // 3xTF32 at BN = 128 or 192 (K beyond two k-blocks): A's split goes to
+    // TMEM instead of shared memory.  Four converter warps (one per TMEM lane
+    // quadrant) read each landed A row, split it and store A_hi and A_lo with
+    // tcgen05.st into a slot of columns after the two accumulators; the MMAs
+    // then read only B from shared memory, and the stage needs no A_lo buffer.
+    static constexpr bool A_TMEM = X3 && !NK && (BN == 128 || BN == 192);
+    // one k-block is ROW bytes of K per row: 64 bf16 or 32 fp32 (128-byte
+    // rows), or 16 fp32 (64-byte rows) for 3xTF32 with A's split in shared
+    // memory, whose stage holds A, A_lo, B and B_lo.  With A in TMEM the
+    // 128-byte k-block halves the TMA rows, barrier round trips and loads
+    // issued per MMA against 64-byte ones.
+    static constexpr int ROW = (X3 && !A_TMEM) ? 64 : 128;
+    static constexpr int BKE = ROW / (X3 ? 4 : 2);
     static constexpr int KSTEPS = ROW / 32;  // MMA k-steps (32 bytes of K) per k-block
     static constexpr uint32_t A_BYTES = BM * ROW;
     static constexpr uint32_t B_BYTES = BN * ROW;
     // bytes TMA brings per pipeline stage: A, B (+ B_lo for TF32X3; A_lo is
-    // formed in shared memory)
+    // formed in shared memory or TMEM)
     static constexpr uint32_t STAGE_TX = A_BYTES + (X3 ? 2 : 1) * B_BYTES;
-    // 3xTF32 at BN = 128 or 192 (K beyond two k-blocks): A's split goes to
-    // TMEM instead of shared memory.  Four converter warps (one per TMEM lane
-    // quadrant) read each landed A row, split it and store A_hi and A_lo with
-    // tcgen05.st into the stage's 32 columns after the two accumulators; the
-    // MMAs then read only B from shared memory.  Per 16-deep k-block at
-    // BN = 192 that cuts the shared-memory traffic from ~128 KB (MMA operand
-    // reads 60, TMA writes 32, split 24, epilogue 12) to ~88 KB, against the
-    // 660 tensor-core cycles of its six MMAs at 128 bytes per cycle.
-    static constexpr bool A_TMEM = X3 && !NK && (BN == 128 || BN == 192);
     static constexpr int CONV = A_TMEM ? 4 : CONV_WARPS;
-    static constexpr uint32_t A_COL = 2 * BN;  // TMEM column of stage 0's A_hi (A_TMEM)
+    // A_TMEM: slot a holds a k-block's A_hi (ROW / 4 columns) then A_lo at
+    // A_COL + a * A_SLOT_COLS; the slots fill TMEM beside the accumulators
+    // (2 at BN = 192, 4 at 128) and are released by their own commit barriers
+    static constexpr uint32_t A_COL = 2 * BN;
+    static constexpr int A_SLOT_COLS = 2 * (ROW / 4);
+    static constexpr int A_SLOTS = A_TMEM ? ((512 - 2 * BN) / A_SLOT_COLS > 4 ? 4 : (512 - 2 * BN) / A_SLOT_COLS) : 1;
     static constexpr uint32_t TMEM_COLS =
         A_TMEM ? 512 : (2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512);
     // epilogue warps: 16, or 8 for the 128- and 192-wide 3xTF32 tiles, whose
@@ -231,13 +268,15 @@ struct TileCfg {
     // keep 4 and a smaller footprint, which leaves room on the SM for the CTAs
     // of the next kernel that programmatic launch brings in early.
     static constexpr int X3_FIT = (int)((232448 - 1024 - 256 - STAGE_BYTES) / (STAGE_TX + A_BYTES));
-    // (A_TMEM: four stages, the A slots TMEM holds beside two accumulators)
-    // BF16: four stages (three at BN = 256, where four do not fit beside the
-    // epilogue buffers)
-    static constexpr int STAGES =
-        A_TMEM ? 4 : X3 ? (BN >= 128 && !NK ? (X3_FIT > 6 ? 6 : X3_FIT) : 4) : (BN >= 256 ? 3 : 4);
-    static_assert(!A_TMEM || A_COL + 32 * STAGES <= 512, "A slots exceed TMEM");
-    static_assert(STAGES >= 2 && 8 * (3 * STAGES + 5) + 8 <= 256, "pipeline barriers exceed their block");
+    // A_TMEM: as many 128-byte stages as fit, at most four.  BF16: four
+    // stages (three at BN = 256, where four do not fit beside the epilogue
+    // buffers)
+    static constexpr int A_FIT = (int)((232448 - 1024 - 256 - STAGE_BYTES) / STAGE_TX);
+    static constexpr int STAGES = A_TMEM ? (A_FIT > 4 ? 4 : A_FIT)
+                                         : X3 ? (BN >= 128 && !NK ? (X3_FIT > 6 ? 6 : X3_FIT) : 4)
+                                              : (BN >= 256 ? 3 : 4);
+    static_assert(!A_TMEM || (A_SLOTS >= 2 && A_COL + A_SLOT_COLS * A_SLOTS <= 512), "A slots exceed TMEM");
+    static_assert(STAGES >= 2 && 8 * (3 * STAGES + 5 + A_SLOTS) + 8 <= 256, "pipeline barriers exceed their block");
     static constexpr size_t SMEM =
         1024 + STAGES * (size_t)(STAGE_TX + (X3 && !A_TMEM ? A_BYTES : 0)) + 256 + STAGE_BYTES;
     static_assert(SMEM <= 232448, "dynamic shared memory above 227 KB");
@@ -255,6 +294,16 @@ struct TileIter {
         else return false;
         m0 = (t / tilesN) * BM;
         n0 = (t % tilesN) * BN_;
+        return true;
+    }
+    // cl > 1 (one class): cluster tile T -> this CTA's tile, rank r of the
+    // cluster taking row tile cl * (T / tilesN) + r (past the last row tile
+    // its rows are out of range: TMA fills them with zeros and the epilogue
+    // stores nothing, but the CTA still loads its share of B for the others)
+    __device__ __forceinline__ bool get_cl(int T, int cl, int r, int &m0, int &n0, int BN_) const {
+        if (T >= ((mt0 + cl - 1) / cl) * tilesN) return false;
+        m0 = ((T / tilesN) * cl + r) * BM;
+        n0 = (T % tilesN) * BN_;
         return true;
     }
 };
@@ -282,7 +331,8 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
     uint64_t *acc_empty = acc_full + 2;
     uint64_t *conv = acc_empty + 2;  // TF32X3: A_lo of the stage is ready
     uint64_t *drain = conv + STAGES;  // every MMA the issuer started has retired
-    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    uint64_t *aempty = drain + 1;     // A_TMEM: the MMAs that read TMEM A slot a retired
+    uint32_t *tmem_slot = (uint32_t *)(aempty + C::A_SLOTS);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     float *stage_all = (float *)((uint8_t *)full + 256);
 
@@ -302,11 +352,23 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
     const int nk = (P.K + BK - 1) / BK;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lim = P.spin_limit;
+    // tile walk: over this CTA's tiles, or over its cluster's tiles
+    const int cl = P.cl > 1 ? P.cl : 1;
+    const int crank = cl > 1 ? (int)cluster_rank() : 0;
+    const uint16_t cmask = (uint16_t)((1u << cl) - 1u);
+    const int t_first = blockIdx.x / cl, t_step = gridDim.x / cl;
+    auto next_tile = [&](int t, int &z, int &m0, int &n0) -> bool {
+        if (cl > 1) {
+            z = 0;
+            return it.get_cl(t, cl, crank, m0, n0, BN);
+        }
+        return it.get(t, z, m0, n0, BN);
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], cl);  // released by the MMA issuer of every CTA of the cluster
             mbar_init(&conv[s], C::CONV);
         }
         for (int b = 0; b < 2; ++b) {
@@ -314,12 +376,14 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
             mbar_init(&acc_empty[b], C::EPI);
         }
         mbar_init(drain, 1);
+        for (int a = 0; a < C::A_SLOTS; ++a) mbar_init(&aempty[a], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) tmem_alloc(tmem_slot, C::TMEM_COLS);
     fence_before();
-    __syncthreads();
+    if (cl > 1) cluster_sync();  // every CTA's barriers exist before any multicast reaches them
+    else __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -327,7 +391,7 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
         if (lane == 0) {  // TMA producer
             int kg = 0;
             int z, m0, n0;
-            for (int t = blockIdx.x; it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x) {
+            for (int t = t_first; next_tile(t, z, m0, n0) && !*abort_flag; t += t_step) {
                 for (int kb = 0; kb < nk; ++kb, ++kg) {
                     const int s = kg % STAGES;
                     if (kg >= STAGES && !mbar_wait(&empty[s], ((kg / STAGES) - 1) & 1, abort_flag, lim)) {
@@ -339,8 +403,17 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
                     const int ya = (int)(sel3(z, P.row0[0], P.row0[1], P.row0[2]) + m0);
                     const int yb = (int)(sel3(z, P.brow0[0], P.brow0[1], P.brow0[2]) + n0);
                     tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * BK, ya, &full[s]);
-                    tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * BK, yb, &full[s]);
-                    if (X3) tma_load_2d(sBlo + s * C::B_BYTES, &tmBlo, kb * BK, yb, &full[s]);
+                    if (cl > 1) {  // this CTA's 1/cl of the B rows, into every CTA
+                        const int hb = BN / cl;
+                        const uint32_t off = (uint32_t)(crank * hb * C::ROW);
+                        tma_load_2d_mc(sB + s * C::B_BYTES + off, &tmB, kb * BK, yb + crank * hb, &full[s], cmask);
+                        if (X3)
+                            tma_load_2d_mc(sBlo + s * C::B_BYTES + off, &tmBlo, kb * BK, yb + crank * hb, &full[s],
+                                           cmask);
+                    } else {
+                        tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * BK, yb, &full[s]);
+                        if (X3) tma_load_2d(sBlo + s * C::B_BYTES, &tmBlo, kb * BK, yb, &full[s]);
+                    }
                 }
             }
             // own copies must land before the CTA exits: a wait that runs out is
@@ -358,8 +431,7 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
             const uint32_t idesc = X3 ? idesc_tf32(BM, BN) : idesc_bf16(BM, BN);
             int kg = 0, lt = 0;
             int z, m0, n0;
-            for (int t = blockIdx.x; !P.skip_mma && it.get(t, z, m0, n0, BN) && !*abort_flag;
-                 t += gridDim.x, ++lt) {
+            for (int t = t_first; !P.skip_mma && next_tile(t, z, m0, n0) && !*abort_flag; t += t_step, ++lt) {
                 const int buf = lt & 1;
                 if (lt >= 2 && !mbar_wait(&acc_empty[buf], ((lt >> 1) - 1) & 1, abort_flag, lim)) {
                     set_status(status, TNET_ERR_TIMEOUT);
@@ -385,11 +457,12 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
                         const uint64_t da = sdesc_sw<C::ROW>(a0 + k * 32), db = sdesc_sw<C::ROW>(b0 + k * 32);
                         const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
                         if constexpr (C::A_TMEM) {
-                            // stage s's A_hi at columns A_COL + 32 s, A_lo 16 further
-                            const uint32_t ah = tmem + C::A_COL + (uint32_t)(32 * s + 8 * k);
+                            // slot kg mod A_SLOTS: A_hi, then A_lo ROW / 4 columns further
+                            const uint32_t ah =
+                                tmem + C::A_COL + (uint32_t)(C::A_SLOT_COLS * (kg % C::A_SLOTS) + 8 * k);
                             const uint32_t bl = smem_u32(sBlo + s * C::B_BYTES);
                             umma_tf32_at(d, ah, db, idesc, acc);
-                            umma_tf32_at(d, ah + 16, db, idesc, 1u);
+                            umma_tf32_at(d, ah + C::ROW / 4, db, idesc, 1u);
                             umma_tf32_at(d, ah, sdesc_sw<C::ROW>(bl + k * 32), idesc, 1u);
                         } else if (X3) {
                             const uint32_t al = smem_u32(sAlo + s * C::A_BYTES), bl = smem_u32(sBlo + s * C::B_BYTES);
@@ -400,7 +473,9 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
                             umma_bf16(d, da, db, idesc, acc);
                         }
                     }
-                    umma_commit(&empty[s]);
+                    if (cl > 1) umma_commit_mc(&empty[s], cmask);  // the stage is free in every CTA's view
+                    else umma_commit(&empty[s]);
+                    if constexpr (C::A_TMEM) umma_commit(&aempty[kg % C::A_SLOTS]);
                 }
                 if (!ok) {
                     set_status(status, TNET_ERR_TIMEOUT);
@@ -424,7 +499,7 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
             int kg = 0;
             bool ok = true;
             int z, m0, n0;
-            for (int t = blockIdx.x; ok && it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x) {
+            for (int t = t_first; ok && next_tile(t, z, m0, n0) && !*abort_flag; t += t_step) {
                 for (int kb = 0; kb < nk; ++kb, ++kg) {
                     const int s = kg % STAGES;
                     if (!mbar_wait(&full[s], (kg / STAGES) & 1, abort_flag, lim)) {
@@ -432,26 +507,36 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
                         break;
                     }
                     if constexpr (C::A_TMEM) {
-                        // this lane's row of the tile (= its TMEM lane): 16 fp32
-                        // in four 16-byte chunks, chunk c stored at c ^ ((r >> 1) & 3)
-                        // (TMA's 64-byte swizzle)
+                        // this lane's row of the tile (= its TMEM lane): 32 fp32
+                        // in eight 16-byte chunks, chunk c stored at c ^ (r & 7)
+                        // (TMA's 128-byte swizzle)
                         const int q = warp & 3, r = 32 * q + lane;
-                        const float4 *row = reinterpret_cast<const float4 *>(sA + s * C::A_BYTES + r * 64);
-                        float h[16], l[16];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const float4 v = row[c ^ ((r >> 1) & 3)];
-                            tf32_split(v.x, h[4 * c], l[4 * c]);
-                            tf32_split(v.y, h[4 * c + 1], l[4 * c + 1]);
-                            tf32_split(v.z, h[4 * c + 2], l[4 * c + 2]);
-                            tf32_split(v.w, h[4 * c + 3], l[4 * c + 3]);
+                        const float4 *row = reinterpret_cast<const float4 *>(sA + s * C::A_BYTES + r * C::ROW);
+                        // the slot's last readers, the MMAs of k-block kg - A_SLOTS,
+                        // must have retired
+                        const int a = kg % C::A_SLOTS;
+                        if (kg >= C::A_SLOTS &&
+                            !mbar_wait(&aempty[a], ((kg / C::A_SLOTS) - 1) & 1, abort_flag, lim)) {
+                            ok = false;
+                            break;
                         }
-                        // stage s's TMEM columns were last read by the MMAs of
-                        // k-block kg - STAGES, which retired before TMA refilled
-                        // stage s (the producer waited on empty[s])
-                        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + C::A_COL + (uint32_t)(32 * s);
-                        tmem_st16(ta, h);
-                        tmem_st16(ta + 16, l);
+                        fence_after();
+                        const uint32_t ta =
+                            tmem + ((uint32_t)(32 * q) << 16) + C::A_COL + (uint32_t)(C::A_SLOT_COLS * a);
+#pragma unroll
+                        for (int h16 = 0; h16 < C::ROW / 64; ++h16) {  // 16 elements (four chunks) at a time
+                            float h[16], l[16];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const float4 v = row[(4 * h16 + c) ^ (r & 7)];
+                                tf32_split(v.x, h[4 * c], l[4 * c]);
+                                tf32_split(v.y, h[4 * c + 1], l[4 * c + 1]);
+                                tf32_split(v.z, h[4 * c + 2], l[4 * c + 2]);
+                                tf32_split(v.w, h[4 * c + 3], l[4 * c + 3]);
+                            }
+                            tmem_st16(ta + 16 * h16, h);
+                            tmem_st16(ta + C::ROW / 4 + 16 * h16, l);
+                        }
                         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                         fence_before();
                     } else {
@@ -489,7 +574,7 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
         const int c_begin = part < NSLICE ? part * CW : 0, c_end = part < NSLICE ? c_begin + CW : 0;
         int lt = 0;
         int z, m0, n0;
-        for (int t = blockIdx.x; it.get(t, z, m0, n0, BN) && !*abort_flag; t += gridDim.x, ++lt) {
+        for (int t = t_first; next_tile(t, z, m0, n0) && !*abort_flag; t += t_step, ++lt) {
             const int buf = lt & 1;
             if (!mbar_wait(&acc_full[buf], (lt >> 1) & 1, abort_flag, lim)) {
                 set_status(status, TNET_ERR_TIMEOUT);
@@ -538,6 +623,9 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
     }
     fence_before();
     __syncthreads();
+    // no CTA leaves while another may still multicast into its shared memory
+    // or release its stages
+    if (cl > 1) cluster_sync();
     if (warp == 1) {
         fence_after();
         tmem_dealloc(tmem, C::TMEM_COLS);
@@ -578,11 +666,47 @@ inline int ensure_smem_attr(const void *kern, int bytes) {
     return TNET_OK;
 }
 
+// How many clusters of `cl` CTAs of this kernel the device runs at once (0
+// if the query fails); cached per kernel handle, device and cluster size.
+inline int max_active_clusters(const void *kern, int threads, int smem, int cl) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void *, int>, int>> done;  // ((kernel, device * 8 + cl), count)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const int key = dev * 8 + cl;
+    std::lock_guard<std::mutex> g(mu);
+    for (const auto &d : done)
+        if (d.first.first == kern && d.first.second == key) return d.second;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cl, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute a[1];
+    a[0].id = cudaLaunchAttributeClusterDimension;
+    a[0].val.clusterDim.x = (unsigned)cl;
+    a[0].val.clusterDim.y = 1;
+    a[0].val.clusterDim.z = 1;
+    cfg.attrs = a;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        n = 0;
+    }
+    done.push_back({{kern, key}, n});
+    return n;
+}
+
 // Launches one persistent GEMM: min(tiles, sms) CTAs, one per SM (`sms` is
-// the SM count of the device the stream runs on).
+// the SM count of the device the stream runs on), in clusters of P.cl when
+// the GEMM has one class, the tile splits into cl row groups of whole 8-row
+// swizzle atoms, and the device runs such clusters.
 template <int BN, bool X3, bool NK = false, class Epi>
-int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *status, cudaStream_t st, int sms) {
+int tc_gemm_ops(const TcShape &P0, const TcOperands &o, const Epi &epi, int32_t *status, cudaStream_t st, int sms) {
     using C = TileCfg<BN, X3, NK>;
+    TcShape P = P0;
+    int cl = P.cl > 1 ? P.cl : 1;
+    if (P.nclass != 1 || BN % cl || (BN / cl) % 8) cl = 1;
     const int esz = X3 ? 4 : 2;
     int maxM = 0;
     for (int z = 0; z < P.nclass; ++z) maxM = P.M[z] > maxM ? P.M[z] : maxM;
@@ -592,24 +716,38 @@ int tc_gemm_ops(const TcShape &P, const TcOperands &o, const Epi &epi, int32_t *
     if (X3 && (!o.Blo || ((uintptr_t)o.Blo & 15))) return TNET_ERR_ARG;
     CUtensorMap ma, mb, mal, mbl;
     int rc;
+    auto kern = k_tc_gemm<BN, Epi, X3, NK>;
+    if ((rc = ensure_smem_attr((const void *)kern, (int)C::SMEM))) return rc;
+    if (sms < 1) sms = 1;
+    int maxc = 0;
+    if (cl > 1) {
+        maxc = max_active_clusters((const void *)kern, C::THREADS, (int)C::SMEM, cl);
+        if (maxc > sms / cl) maxc = sms / cl;
+        if (maxc < 1) cl = 1;
+    }
+    P.cl = cl;
+    const int bbox = BN / cl;  // B rows each CTA loads per stage
     if (X3) {
         if ((rc = make_map_f32(&ma, o.A, o.a_rows, P.K, o.lda, BM, C::ROW))) return rc;
-        if ((rc = make_map_f32(&mb, o.B, o.b_rows, P.K, o.ldb, BN, C::ROW))) return rc;
-        if ((rc = make_map_f32(&mbl, o.Blo, o.b_rows, P.K, o.ldb, BN, C::ROW))) return rc;
-        mal = ma;  // unused: A_lo is formed in shared memory
+        if ((rc = make_map_f32(&mb, o.B, o.b_rows, P.K, o.ldb, bbox, C::ROW))) return rc;
+        if ((rc = make_map_f32(&mbl, o.Blo, o.b_rows, P.K, o.ldb, bbox, C::ROW))) return rc;
+        mal = ma;  // unused: A_lo is formed in shared memory or TMEM
     } else {
         if ((rc = make_map_bf16(&ma, o.A, o.a_rows, P.K, o.lda, BM))) return rc;
-        if ((rc = make_map_bf16(&mb, o.B, o.b_rows, P.K, o.ldb, BN))) return rc;
+        if ((rc = make_map_bf16(&mb, o.B, o.b_rows, P.K, o.ldb, bbox))) return rc;
         mal = ma;
         mbl = mb;
     }
-    auto kern = k_tc_gemm<BN, Epi, X3, NK>;
-    if ((rc = ensure_smem_attr((const void *)kern, (int)C::SMEM))) return rc;
     int64_t tiles = 0;
     for (int z = 0; z < P.nclass; ++z) tiles += (int64_t)((P.M[z] + BM - 1) / BM) * ((P.N + BN - 1) / BN);
-    if (sms < 1) sms = 1;
-    const int grid = (int)(tiles < sms ? tiles : sms);
-    launch(kern, grid, C::THREADS, C::SMEM, st, ma, mb, mal, mbl, P, epi, status);
+    int grid;
+    if (cl > 1) {  // clusters over cluster tiles (cl row tiles of one column tile)
+        const int64_t ctiles = (int64_t)((P.M[0] + BM * cl - 1) / (BM * cl)) * ((P.N + BN - 1) / BN);
+        grid = (int)(ctiles < maxc ? ctiles : maxc) * cl;
+    } else {
+        grid = (int)(tiles < sms ? tiles : sms);
+    }
+    launch_cluster(kern, grid, C::THREADS, C::SMEM, st, cl, ma, mb, mal, mbl, P, epi, status);
     count_launch();
     TNET_LAUNCH_CHECK();
     return TNET_OK;

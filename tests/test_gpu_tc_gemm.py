@@ -74,6 +74,46 @@ def test_tc_gemm_3xtf32_matches_fp64(M, N, K):
     assert rel.pow(2).mean().sqrt().item() <= 3e-7, rel.pow(2).mean().sqrt().item()
 
 
+@pytest.mark.parametrize("cluster", [2, 4])
+@pytest.mark.parametrize("x3,M,N,K", [(1, 777, 384, 256), (1, 20000, 128, 256), (1, 4096, 256, 128),
+                                      (1, 5000, 384, 32), (1, 129, 64, 384), (1, 1, 32, 32), (1, 1500, 384, 100),
+                                      (0, 1000, 256, 128), (0, 777, 384, 256), (0, 300, 128, 64), (0, 1, 32, 32)])
+def test_tc_gemm_clusters_match_single_ctas_bitwise(x3, M, N, K, cluster):
+    """CTAs in clusters that share each weight stage through TMA multicast
+    (each loads 1/cluster of the B rows into every CTA's shared memory, and
+    every CTA's MMA issuer releases the stage in all of them) compute exactly
+    what lone CTAs do: the same MMAs on the same tiles.  Row counts that leave
+    the last cluster with CTAs past the last row tile, a single row, ragged K
+    and every column-tile form are included."""
+    g = torch.Generator(device="cpu").manual_seed(3)
+    A = torch.randn(M, K, generator=g).cuda()
+    B = torch.randn(N, K, generator=g).cuda()
+    if not x3:
+        A, B = A.bfloat16(), B.bfloat16()
+    Bsplit = torch.empty(2 * N * K, dtype=torch.float32, device="cuda")
+    lib = _lib.load()
+    p = lambda t: ctypes.c_void_p(t.data_ptr())
+    sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    out = []
+    for cl in (1, cluster):
+        C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        assert lib.tnet_debug_tc_gemm_cluster(M, N, K, x3, cl, p(A), p(B), p(Bsplit), p(C), p(st), sp) == 0
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        out.append(C)
+    assert torch.equal(out[0], out[1])
+    ref = A.double() @ B.double().T
+    err = (out[1].double() - ref).abs().max().item() / ref.abs().max().item()
+    assert err <= (1e-5 if x3 else 2e-2), err
+
+
+def test_tc_gemm_cluster_rejects_other_sizes():
+    lib = _lib.load()
+    z = ctypes.c_void_p(0)
+    assert lib.tnet_debug_tc_gemm_cluster(128, 128, 64, 1, 3, z, z, z, z, z, z) != 0
+
+
 def test_bounded_waits_report_timeout_and_leave_the_context_usable():
     """The failure path of the tensor-core kernel, made to happen without a
     fault: the 3xTF32 GEMM runs with its MMA issuer told to issue nothing and
