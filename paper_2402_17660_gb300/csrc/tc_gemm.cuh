@@ -227,12 +227,14 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float v[16]) {
 
 template <int BN, bool X3 = false, bool NK = false>
 struct TileCfg {
-    // 3xTF32 at BN = 128 or 192 (K beyond two k-blocks): A's split goes to
-    // TMEM instead of shared memory.  Four converter warps (one per TMEM lane
+    // 3xTF32 at BN <= 192 (K beyond two k-blocks): A's split goes to TMEM
+    // instead of shared memory.  Four converter warps (one per TMEM lane
     // quadrant) read each landed A row, split it and store A_hi and A_lo with
     // tcgen05.st into a slot of columns after the two accumulators; the MMAs
     // then read only B from shared memory, and the stage needs no A_lo buffer.
-    static constexpr bool A_TMEM = X3 && !NK && (BN == 128 || BN == 192);
+    // The narrow tiles (32 or 64 output columns, whose k-blocks carry little
+    // MMA work) gain most: their pace is set by splitting A.
+    static constexpr bool A_TMEM = X3 && !NK && BN <= 192;
     // one k-block is ROW bytes of K per row: 64 bf16 or 32 fp32 (128-byte
     // rows), or 16 fp32 (64-byte rows) for 3xTF32 with A's split in shared
     // memory, whose stage holds A, A_lo, B and B_lo.  With A in TMEM the
@@ -259,7 +261,7 @@ struct TileCfg {
     // freed transpose buffers make room for a deeper pipeline; NK (a K of at
     // most two k-blocks, whose epilogue outweighs its MMAs) keeps 16 and 4
     // stages
-    static constexpr int EPI = (X3 && BN >= 128 && !NK) ? 8 : 16;
+    static constexpr int EPI = (X3 && !NK && (BN >= 128 || A_TMEM)) ? 8 : 16;
     static constexpr int THREADS = 64 + 32 * (EPI + CONV);
     static constexpr uint32_t STAGE_BYTES = EPI * 32 * STG_LD * 4;  // epilogue transpose buffers
     // 3xTF32: 4 stages, and as many as fit beside the epilogue buffers (6 at
@@ -268,11 +270,12 @@ struct TileCfg {
     // keep 4 and a smaller footprint, which leaves room on the SM for the CTAs
     // of the next kernel that programmatic launch brings in early.
     static constexpr int X3_FIT = (int)((232448 - 1024 - 256 - STAGE_BYTES) / (STAGE_TX + A_BYTES));
-    // A_TMEM: as many 128-byte stages as fit, at most four.  BF16: four
-    // stages (three at BN = 256, where four do not fit beside the epilogue
-    // buffers)
+    // A_TMEM: as many 128-byte stages as fit, at most four (six for the
+    // narrow tiles, which stream A).  BF16: four stages (three at BN = 256,
+    // where four do not fit beside the epilogue buffers)
     static constexpr int A_FIT = (int)((232448 - 1024 - 256 - STAGE_BYTES) / STAGE_TX);
-    static constexpr int STAGES = A_TMEM ? (A_FIT > 4 ? 4 : A_FIT)
+    static constexpr int A_CAP = BN <= 64 ? 6 : 4;
+    static constexpr int STAGES = A_TMEM ? (A_FIT > A_CAP ? A_CAP : A_FIT)
                                          : X3 ? (BN >= 128 && !NK ? (X3_FIT > 6 ? 6 : X3_FIT) : 4)
                                               : (BN >= 256 ? 3 : 4);
     static_assert(!A_TMEM || (A_SLOTS >= 2 && A_COL + A_SLOT_COLS * A_SLOTS <= 512), "A slots exceed TMEM");
