@@ -511,8 +511,8 @@ def run_ours(args):
         flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, args.precision, args.radial_table,
                                            rec)
         if x3 and not tab and tag in ("mlp2", "mlp3", "mlp3_bwd", "mlp2_bwd"):
-            # 3xTF32: three TF32 MMAs per product (the residuals are formed in
-            # shared memory, so the bytes are those of the fp32 operands)
+            # 3xTF32: three TF32 MMAs per product (the residuals are formed on
+            # chip, so the bytes are those of the fp32 operands)
             engine = "tensor_tf32"
         per_launch_ms = stages[tag]["ms_per_step"] * args.profile_steps / stages[tag]["instances"]
         traffic = None
