@@ -209,11 +209,12 @@ __global__ void k_edge_rbf(const float *__restrict__ pos, const float *__restric
                            float *__restrict__ eu, float *__restrict__ phiu, float4 *__restrict__ geo,
                            OpCopy eu_cp) {
     pdl_entry();
-    // a block takes groups of P pairs: P threads compute the pairs' geometry
-    // once, then all threads evaluate the P x K basis values from it
+    // a block takes groups of P = blockDim.x (<= 256) pairs: one thread per
+    // pair computes its geometry, then all threads evaluate the P x K basis
+    // values from it (coalesced writes of eu)
     __shared__ float s_d[256], s_phi[256];
     const int U = *nu, K = rp.K;
-    const int P = blockDim.x / K > 0 ? blockDim.x / K : 1;
+    const int P = blockDim.x < 256 ? blockDim.x : 256;
     for (int64_t u0 = (int64_t)blockIdx.x * P; u0 < U; u0 += (int64_t)gridDim.x * P) {
         const int np = U - u0 < P ? (int)(U - u0) : P;
         if (threadIdx.x < np) {
@@ -1840,9 +1841,9 @@ __global__ void k_pair_vec(const float *__restrict__ pos, const float *__restric
                            const float *__restrict__ dEdd, float *__restrict__ Gp) {
     pdl_entry();
     const int U = *nu;
-    const int lane = threadIdx.x & 31;
-    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < U;
-         u += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    // one thread per pair (a warp keeps 32 pairs' loads in flight); the
+    // pair's row of dE/de is read as float4 when K allows
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U; u += (int64_t)gridDim.x * blockDim.x) {
         const int2 p = uij[u];
         float x, y, zz;
         pair_vec(pos, box, batch, p.x, p.y, x, y, zz);
@@ -1850,14 +1851,27 @@ __global__ void k_pair_vec(const float *__restrict__ pos, const float *__restric
         const float phi = cutoff_phi(d, rp), dphi = cutoff_dphi(d, rp);
         float s = 0.f;
         if (ge) {
-            for (int k = lane; k < rp.K; k += 32) {
-                float e, de;
-                expnorm_k(d, k, rp, phi, dphi, e, de);
-                s = fmaf(ge[u * rp.K + k], de, s);
+            const float *g = ge + u * rp.K;
+            if ((rp.K & 3) == 0) {
+                for (int k = 0; k < rp.K; k += 4) {
+                    const float4 gv = *reinterpret_cast<const float4 *>(g + k);
+                    const float gk[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float e, de;
+                        expnorm_k(d, k + j, rp, phi, dphi, e, de);
+                        s = fmaf(gk[j], de, s);
+                    }
+                }
+            } else {
+                for (int k = 0; k < rp.K; ++k) {
+                    float e, de;
+                    expnorm_k(d, k, rp, phi, dphi, e, de);
+                    s = fmaf(g[k], de, s);
+                }
             }
-            s = warp_sum(s);
         }
-        if (lane == 0) {
+        {
             const int e = ue[u];
             const float4 a = edge_g[e], b = edge_g[rev[e]];
             const float gphi = (gphi_mlp ? gphi_mlp[u] : 0.f) + a.x + b.x;
@@ -2234,11 +2248,12 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
     const int prec = d.precision;
     const bool tcm = prec != 0;
     const bool wg = grad_w != nullptr;
-    // FP32 activations h1, h2 are read by the FP32 and 3xTF32 GEMMs and by the
-    // weight gradients; the BF16 GEMMs read only their bf16 copies
+    // FP32 activations h1, h2 are read by the FP32 GEMMs and by the weight
+    // gradients (the 3xTF32 GEMMs form them from a1, a2 when no weight
+    // gradient is asked for); the BF16 GEMMs read only their bf16 copies
     const bool keep_h = prec != 1 || wg;
     // bf16 operand copies (BF16 mode only: the 3xTF32 GEMMs read the fp32
-    // activations and form their residuals in shared memory)
+    // activations and form their residuals on chip)
     auto cp = [&](size_t off) { return prec == 1 ? OpCopy{(void *)(ctx->ws + off), 1} : OpCopy{nullptr, 0}; };
     // (the num_rbf-wide operands e(d) and dE/df stay FP32, so they get no copy)
     const OpCopy none{nullptr, 0};
@@ -2502,10 +2517,28 @@ int energy_forces_impl(tnet_ctx *ctx, const float *wblob, int N, int S, const in
         float *a1 = act(Lw.a1, F, l), *h1 = act(Lw.h1, F, l), *a2 = act(Lw.a2, 2 * F, l),
               *h2 = act(Lw.h2, 2 * F, l), *a3 = act(Lw.a3, 3 * F, l);
         if (tab) return TNET_OK;  // the message kernels evaluate g, dg/dd from the table
+        const EpiBiasAct e3{b3p(l), a3, 3 * F, nullptr, 3 * F, 0, nullptr};
+        if (tcm && prec == 2 && !wg) {
+            // 3xTF32 without weight gradients: layers 1 and 2 store their
+            // pre-activations alone; the next GEMM's converter warps form
+            // h = silu_f(a) from them (bitwise the value the epilogue would
+            // store), and the reverse pass reads only a1, a2
+            const EpiBiasAct s1{Lr.mlp1_b, a1, F, nullptr, F, 1, nullptr};
+            const EpiBiasAct s2{Lr.mlp2_b, a2, 2 * F, nullptr, 2 * F, 1, nullptr};
+            tc::TcShape t1 = tc::tshape(maxU, F, K), t2 = tc::tshape(maxU, 2 * F, F), t3 = tc::tshape(maxU, 3 * F, 2 * F);
+            t1.rows_dev = t2.rows_dev = t3.rows_dev = nu;
+            t2.a_silu = t3.a_silu = 1;
+            pf.mark(P_MLP1);
+            TRY(tcx3(t1, eu, maxU, K, lb[l].mlp1, F, K, s1));
+            pf.mark(P_MLP2);
+            TRY(tcx3(t2, a1, maxU, F, lb[l].mlp2, 2 * F, F, s2, bn2));
+            pf.mark(P_MLP3);
+            TRY(tcx3(t3, a2, maxU, 2 * F, lb[l].mlp3, 3 * F, 2 * F, e3, bn3));
+            return TNET_OK;
+        }
         const EpiBiasAct e1{Lr.mlp1_b, fwd_only ? nullptr : a1, F, keep_h ? h1 : nullptr, F, 1, nullptr, h1_cp(l), F};
         const EpiBiasAct e2{Lr.mlp2_b, fwd_only ? nullptr : a2, 2 * F, keep_h ? h2 : nullptr, 2 * F, 1, nullptr,
                             h2_cp(l), 2 * F};
-        const EpiBiasAct e3{b3p(l), a3, 3 * F, nullptr, 3 * F, 0, nullptr};
         if (tcm) {
             tc::TcShape t2 = tc::tshape(maxU, 2 * F, F), t3 = tc::tshape(maxU, 3 * F, 2 * F);
             t2.rows_dev = t3.rows_dev = nu;

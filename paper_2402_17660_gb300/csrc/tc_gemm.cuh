@@ -64,6 +64,10 @@ struct TcShape {
     // multicast into all of them, so the weights stream from L2 once per
     // cl * 128 rows instead of once per 128
     int cl;
+    // 3xTF32: the operand is SiLU(A) (the converter warps apply silu_f to each
+    // landed element before the split), so a layer's activation need not be
+    // stored beside its pre-activation
+    int a_silu;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -531,7 +535,10 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
                             float h[16], l[16];
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
-                                const float4 v = row[(4 * h16 + c) ^ (r & 7)];
+                                float4 v = row[(4 * h16 + c) ^ (r & 7)];
+                                if (P.a_silu) {
+                                    v.x = silu_f(v.x); v.y = silu_f(v.y); v.z = silu_f(v.z); v.w = silu_f(v.w);
+                                }
                                 tf32_split(v.x, h[4 * c], l[4 * c]);
                                 tf32_split(v.y, h[4 * c + 1], l[4 * c + 1]);
                                 tf32_split(v.z, h[4 * c + 2], l[4 * c + 2]);
@@ -548,6 +555,9 @@ __global__ void __launch_bounds__(TileCfg<BN, X3, NK>::THREADS, 1)
 #pragma unroll 4
                         for (int i = ct; i < (int)(C::A_BYTES / 16); i += 32 * CONV_WARPS) {
                             float4 v = hi[i], l;
+                            if (P.a_silu) {
+                                v.x = silu_f(v.x); v.y = silu_f(v.y); v.z = silu_f(v.z); v.w = silu_f(v.w);
+                            }
                             tf32_split(v.x, v.x, l.x);
                             tf32_split(v.y, v.y, l.y);
                             tf32_split(v.z, v.z, l.z);
