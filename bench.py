@@ -209,29 +209,65 @@ def oracle_eval_seconds(sys_, W, reps=1, want=False):
     return (t, (Es, Ei, Fr)) if want else t
 
 
-def cpu_baseline(sys_, W):
+ORACLE_THREADS_NOTE = ("the oracle is NumPy: its matrix products run on the BLAS thread pool (up to `cores` "
+                       "threads); its elementwise work runs on one thread")
+
+
+def oracle_eval_seconds_single_thread(sys_, W):
+    """The same evaluation as oracle_eval_seconds in a child process whose
+    BLAS and OpenMP pools hold one thread (a fresh process, so the setting
+    takes effect before NumPy loads its BLAS).  None if the child fails."""
+    import pickle
+    import tempfile
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    code = ("import pickle, sys; sys.path.insert(0, sys.argv[2]); import bench; "
+            "s, W = pickle.load(open(sys.argv[1], 'rb')); print(bench.oracle_eval_seconds(s, W))")
+    with tempfile.TemporaryDirectory() as td:
+        f = os.path.join(td, "sample.pkl")
+        with open(f, "wb") as fh:
+            pickle.dump((sys_, W), fh)
+        try:
+            out = subprocess.run([sys.executable, "-c", code, f, ROOT], env=env, capture_output=True, text=True,
+                                 timeout=900, cwd=ROOT)
+            return float(out.stdout.strip().splitlines()[-1]) if out.returncode == 0 else None
+        except (subprocess.TimeoutExpired, ValueError, IndexError):
+            return None
+
+
+def cpu_baseline(sys_, W, single_thread=True):
     """The oracle as it stands on the host cores, on a bounded sample: the
     whole workload up to 3,000 atoms; above that a 1,500-atom cluster carved
     from it, whose rate is extrapolated to the workload linearly in the atom
-    count (said so in the record, with the sample's own measured rate)."""
+    count (said so in the record, with the sample's own measured rate).  The
+    same sample is timed again on one thread."""
     if sys_.n_atoms <= 3000:
         t, ref = oracle_eval_seconds(sys_, W, want=True)
-        return {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                "sample": f"one full FP64 oracle energy+force evaluation of {sys_.name} "
-                          f"(brute-force pairs + forward + analytic reverse pass), {t:.1f} s",
-                "measured_on_full_workload": True}, ref
-    sample = carve_cluster(sys_, 1500)
-    n = sample.n_atoms
-    t = oracle_eval_seconds(sample, W)
-    scale = n / sys_.n_atoms
-    return {"value": scale / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"one FP64 oracle energy+force evaluation of {sample.name}, a {n}-atom open cluster "
-                      f"carved from {sys_.name} ({t:.1f} s)",
-            "measured_on_full_workload": False,
-            "sample_value": 1.0 / t, "sample_unit": f"evals/s of the {n}-atom sample",
-            "extrapolation": f"value = the sample's rate x {n}/{sys_.n_atoms} atoms (linear in atoms; the "
-                             "oracle's brute-force pair search is quadratic, so the whole workload would "
-                             "take longer than this)"}, None
+        rec = {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one full FP64 oracle energy+force evaluation of {sys_.name} "
+                         f"(brute-force pairs + forward + analytic reverse pass), {t:.1f} s",
+               "measured_on_full_workload": True, "threads": ORACLE_THREADS_NOTE}
+        sample, scale = sys_, 1.0
+    else:
+        sample = carve_cluster(sys_, 1500)
+        n = sample.n_atoms
+        t = oracle_eval_seconds(sample, W)
+        scale = n / sys_.n_atoms
+        ref = None
+        rec = {"value": scale / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one FP64 oracle energy+force evaluation of {sample.name}, a {n}-atom open cluster "
+                         f"carved from {sys_.name} ({t:.1f} s)",
+               "measured_on_full_workload": False,
+               "sample_value": 1.0 / t, "sample_unit": f"evals/s of the {n}-atom sample",
+               "extrapolation": f"value = the sample's rate x {n}/{sys_.n_atoms} atoms (linear in atoms; the "
+                                "oracle's brute-force pair search is quadratic, so the whole workload would "
+                                "take longer than this)", "threads": ORACLE_THREADS_NOTE}
+    if single_thread:
+        t1 = oracle_eval_seconds_single_thread(sample, W)
+        rec["single_thread"] = (None if t1 is None else
+                                {"value": scale / t1, "unit": UNIT, "cores": 1, "seconds_per_sample_eval": t1,
+                                 "how": "the same sample in a child process with one BLAS/OpenMP thread"})
+    return rec, ref
 
 
 def workload_config(sys_, n_pairs, args, graph=True):
