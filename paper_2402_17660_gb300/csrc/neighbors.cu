@@ -338,7 +338,16 @@ __device__ __forceinline__ int axis_neighbors(int c, int nc, int pbc, int out[3]
 }
 
 // Visits every candidate j of atom i (same system, neighbouring cells) with
-// one warp; `fn(j, ok)` is called by all lanes in lock-step.
+// one warp; `fn(j, ok)` is called by all lanes in lock-step, once per chunk of
+// 32 candidates (lanes past the last candidate get j = -1, ok = false).
+// Cells are numbered z-fastest, so the neighbouring cells along z of one
+// (x, y) column form one run of consecutive cells (two when the run wraps
+// around a periodic face), whose atoms are one contiguous range of the
+// cell-sorted order.  Lane r first loads the bounds of range r (at most 27,
+// 9 without wrap), a warp scan lays the ranges end to end, and the warp then
+// walks the concatenated candidates 32 at a time, two chunks' loads in
+// flight: each lane finds the range of its candidate by a five-step search
+// over the scanned offsets (shuffles, the same steps in every lane).
 template <class Fn>
 __device__ __forceinline__ void for_candidates(int i, const float *__restrict__ pos,
                                                const int32_t *__restrict__ batch,
@@ -356,26 +365,83 @@ __device__ __forceinline__ void for_candidates(int i, const float *__restrict__ 
     const int mx = axis_neighbors(cx, s.nc[0], s.pbc, nx);
     const int my = axis_neighbors(cy, s.nc[1], s.pbc, ny);
     const int mz = axis_neighbors(cz, s.nc[2], s.pbc, nz);
+    // the z cells in ascending order, merged into runs of consecutive cells
+    int z0 = nz[0], z1 = mz > 1 ? nz[1] : 0x7fffffff, z2 = mz > 2 ? nz[2] : 0x7fffffff, t;
+    if (z0 > z1) { t = z0; z0 = z1; z1 = t; }
+    if (z1 > z2) { t = z1; z1 = z2; z2 = t; }
+    if (z0 > z1) { t = z0; z0 = z1; z1 = t; }
+    int ra0 = z0, ra1 = z0, rb0 = 0, rb1 = -1, rc0 = 0, rc1 = -1, nrun = 1;
+    auto extend = [&](int z) {  // append z (ascending) to the last run or open a new one
+        if (nrun == 1) {
+            if (z == ra1 + 1) ra1 = z;
+            else { rb0 = rb1 = z; nrun = 2; }
+        } else if (nrun == 2) {
+            if (z == rb1 + 1) rb1 = z;
+            else { rc0 = rc1 = z; nrun = 3; }
+        }
+    };
+    if (mz > 1) extend(z1);
+    if (mz > 2) extend(z2);
+    const int R = mx * my * nrun;  // ranges, <= 27
     const int off = cell_off[b];
-    for (int a = 0; a < mx; ++a)
-        for (int bb = 0; bb < my; ++bb)
-            for (int cc = 0; cc < mz; ++cc) {
-                const int cell = off + (nx[a] * s.nc[1] + ny[bb]) * s.nc[2] + nz[cc];
-                const int p0 = cell_start[cell], p1 = cell_start[cell + 1];
-                for (int p = p0; p < p1; p += 32) {
-                    bool ok = false;
-                    int j = -1;
-                    if (p + lane < p1) {
-                        const float4 q = spos[p + lane];
-                        j = __float_as_int(q.w);
-                        float dx = __fsub_rn(xi, q.x), dy = __fsub_rn(yi, q.y), dz = __fsub_rn(zi, q.z);
-                        mic(dx, dy, dz, s);
-                        const float d2 = norm2_rn(dx, dy, dz);
-                        ok = (j != i) && (d2 < rc2);
-                    }
-                    fn(j, ok);
+    int p0 = 0, len = 0;
+    if (lane < R) {
+        const int run = lane % nrun, rxy = lane / nrun;
+        const int a = rxy / my, bb = rxy % my;
+        const int xa = a == 0 ? nx[0] : (a == 1 ? nx[1] : nx[2]);
+        const int yb = bb == 0 ? ny[0] : (bb == 1 ? ny[1] : ny[2]);
+        const int lo = run == 0 ? ra0 : (run == 1 ? rb0 : rc0);
+        const int hi = run == 0 ? ra1 : (run == 1 ? rb1 : rc1);
+        const int col0 = off + (xa * s.nc[1] + yb) * s.nc[2];
+        p0 = cell_start[col0 + lo];
+        len = cell_start[col0 + hi + 1] - p0;
+    }
+    // exclusive offsets of the ranges laid end to end
+    int incl = len;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const int excl = incl - len;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int c0 = 0; c0 < total; c0 += 64) {
+        float4 q[2];
+        bool has[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int tc = c0 + 32 * u + lane;
+            has[u] = tc < total;
+            if (c0 + 32 * u >= total) continue;  // the same in every lane
+            // last range whose offset is <= tc (it holds tc when tc < total)
+            int r = 0;
+            if (R > 1) {  // the same in every lane
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int cand = r + step;
+                    const int e = __shfl_sync(0xffffffffu, excl, cand & 31);
+                    if (cand < R && e <= tc) r = cand;
                 }
             }
+            const int rp0 = __shfl_sync(0xffffffffu, p0, r);
+            const int rex = __shfl_sync(0xffffffffu, excl, r);
+            if (has[u]) q[u] = spos[rp0 + (tc - rex)];
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (c0 + 32 * u >= total) break;  // the same in every lane
+            bool ok = false;
+            int j = -1;
+            if (has[u]) {
+                j = __float_as_int(q[u].w);
+                float dx = __fsub_rn(xi, q[u].x), dy = __fsub_rn(yi, q[u].y), dz = __fsub_rn(zi, q[u].z);
+                mic(dx, dy, dz, s);
+                const float d2 = norm2_rn(dx, dy, dz);
+                ok = (j != i) && (d2 < rc2);
+            }
+            fn(j, ok);
+        }
+    }
 }
 
 __global__ void k_pair_count(const float *__restrict__ pos, const int32_t *__restrict__ batch, int N,
