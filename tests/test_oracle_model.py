@@ -386,3 +386,73 @@ def test_interaction_layer_two_atoms_closed_form():
         dx = 2 * t / (3 * t * t + 1)
         assert np.allclose(c["dX"][k, 0], dx * np.eye(3), atol=1e-15)
         assert np.allclose(Xout[k, 0], (xn + dx + dx * dx) * np.eye(3), atol=1e-15)
+
+
+def _two_atom_embedding(d=2.0):
+    """Two atoms (H receiver 0 at the origin, C at (0, 0, d)), F = 2, K = 4,
+    no interaction layer.  Radial projections are constants (dproj_w = 0),
+    the pair embedding is asymmetric in its two halves, and the embedding
+    mixing of every class swaps the two channels."""
+    shape = synth.ModelShape(F=2, K=4, L=0, max_z=10)
+    W = synth.init_weights(shape, seed=5)
+    W["emb"][:] = 0.0
+    W["emb"][1] = (1.0, 0.0)
+    W["emb"][6] = (0.0, 1.0)
+    W["emb2_w"] = np.array([[1.0, 2.0, 3.0, 4.0], [0.0, 1.0, 0.0, -1.0]], np.float32)
+    W["emb2_b"] = np.array([0.5, -0.5], np.float32)
+    W["dproj_w"][:] = 0.0
+    W["dproj_b"] = np.array([[1.0, 2.0], [3.0, -1.0], [0.5, 4.0]], np.float32)   # [p][c]: I, A, S
+    W["emb_mix_w"] = np.array([[[0.0, 1.0], [1.0, 0.0]]] * 3, np.float32)
+    m = TensorNet(W, F=2, K=4, L=0)
+    z = np.array([1, 6], np.int32)
+    pos = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, d]])
+    _, _, c = m.forward(z, pos, np.zeros(2, np.int32), None)
+    return W, c
+
+
+def test_embedding_edge_sum_closed_form():
+    """The embedding's edge-to-node sum (Sec. 2.1.1) on two atoms along z.
+    Receiver 0 sees r_01 = r_0 - r_1 = -d z (u = -z), receiver 1 sees u = +z.
+    The pair embeddings, receiver first: Z_01 = W_e (1, 0, 0, 1) + b_e =
+    (5.5, -1.5) and Z_10 = W_e (0, 1, 1, 0) + b_e = (5.5, 0.5).  With constant
+    projections f^p = b^p and phi = (cos(2 pi / 5) + 1) / 2 at d = 2 A, channel c
+    of receiver i is phi Z_i[c] (b^I[c] Id + b^A[c] [u]_x + b^S[c] (u u^T - Id/3)),
+    with [-z]_x = [[0, 1, 0], [-1, 0, 0], [0, 0, 0]] (so that [u]_x v = u x v)
+    and u u^T - Id/3 = diag(-1/3, -1/3, 2/3) for u = +-z.  Its squared norm is
+    (phi Z)^2 (3 (b^I)^2 + 2 (b^A)^2 + (2/3) (b^S)^2), the three parts being
+    orthogonal.  Caught: an edge vector r_j - r_i or a transposed skew part
+    (the A block flips sign), the sender-first pair embedding (channel 1
+    swaps -1.5 and 0.5), an S part without the -Id/3, a dropped cutoff factor,
+    an unsquared norm."""
+    W, c = _two_atom_embedding()
+    phi = 0.5 * (math.cos(math.pi * 2.0 / 5.0) + 1.0)
+    Z = {0: np.array([5.5, -1.5]), 1: np.array([5.5, 0.5])}
+    skew = {0: np.array([[0, 1, 0], [-1, 0, 0], [0, 0, 0]], float), 1: np.array([[0, -1, 0], [1, 0, 0], [0, 0, 0]], float)}
+    S0 = np.diag([-1.0 / 3, -1.0 / 3, 2.0 / 3])
+    bI, bA, bS = (W["dproj_b"][p].astype(np.float64) for p in range(3))
+    for i in (0, 1):
+        for ch in (0, 1):
+            want = phi * Z[i][ch] * (bI[ch] * np.eye(3) + bA[ch] * skew[i] + bS[ch] * S0)
+            assert np.allclose(c["Xraw"][i, ch], want, rtol=1e-12, atol=1e-12), (i, ch)
+            q0 = (phi * Z[i][ch]) ** 2 * (3 * bI[ch] ** 2 + 2 * bA[ch] ** 2 + (2.0 / 3.0) * bS[ch] ** 2)
+            assert math.isclose(tn.tensor_norm(c["Xraw"])[i, ch], q0, rel_tol=1e-12)
+
+
+def test_embedding_mixes_before_scaling():
+    """Reading R4 on the same two atoms: each class's channel mixing (here a
+    swap of the two channels) acts on the summed edge features before the
+    per-channel scale s of the receiver, so X[c] = sum_p s[c, p] P_p[1 - c].
+    Scaling first would give sum_p s[1 - c, p] P_p[1 - c]; the two channels'
+    scales differ, so the test tells them apart."""
+    _, c = _two_atom_embedding()
+    s = c["s"]                      # [N, F, 3]
+    P = c["Praw"]                   # three [N, F, 3, 3]
+    assert np.abs(s[:, 0, :] - s[:, 1, :]).max() > 1e-3
+    I, A, S = c["IAS"]              # no interaction layer: the embedding X, decomposed
+    X = I + A + S
+    for i in (0, 1):
+        for ch in (0, 1):
+            want = sum(s[i, ch, p] * P[p][i, 1 - ch] for p in range(3))
+            assert np.allclose(X[i, ch], want, rtol=1e-12, atol=1e-12), (i, ch)
+            wrong = sum(s[i, 1 - ch, p] * P[p][i, 1 - ch] for p in range(3))
+            assert not np.allclose(X[i, ch], wrong, rtol=1e-6, atol=1e-9)
