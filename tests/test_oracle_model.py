@@ -456,3 +456,22 @@ def test_embedding_mixes_before_scaling():
             assert np.allclose(X[i, ch], want, rtol=1e-12, atol=1e-12), (i, ch)
             wrong = sum(s[i, 1 - ch, p] * P[p][i, 1 - ch] for p in range(3))
             assert not np.allclose(X[i, ch], wrong, rtol=1e-6, atol=1e-9)
+
+
+def test_output_concatenates_class_norms_in_blocks():
+    """Reading R6 on the same two atoms: the output model's input is
+    (||I||, ||A||, ||S||) of the final features in blocks of F channels.  With
+    the channel-swap mixing, the class-p part of X[c] is s[c, p] P_p[1 - c], so
+    its squared norm is s[c, p]^2 (phi Z[1 - c] b^p[1 - c])^2 n_p with
+    n_I = 3, n_A = 2, n_S = 2/3 (the norms of Id, [u]_x and u u^T - Id/3).
+    Caught: another block order, channel-major interleaving, unsquared norms."""
+    W, c = _two_atom_embedding()
+    phi = 0.5 * (math.cos(math.pi * 2.0 / 5.0) + 1.0)
+    Z = {0: np.array([5.5, -1.5]), 1: np.array([5.5, 0.5])}
+    b = [W["dproj_b"][p].astype(np.float64) for p in range(3)]
+    n = (3.0, 2.0, 2.0 / 3.0)
+    s = c["s"]
+    for i in (0, 1):
+        want = np.array([s[i, ch, p] ** 2 * (phi * Z[i][1 - ch] * b[p][1 - ch]) ** 2 * n[p]
+                         for p in range(3) for ch in range(2)])
+        assert np.allclose(c["h"][i], want, rtol=1e-10, atol=1e-14), (i, c["h"][i], want)
