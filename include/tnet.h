@@ -156,9 +156,11 @@ int tnet_destroy(tnet_ctx *ctx);
  *   row_ptr  [N+1] int32   row_ptr[0] = 0, row i holds the j of pairs (i, j)
  *   col      [cap] int32
  *   n_pairs_dev  [1] int64 number of pairs found (also when > cap)
- * If the pairs exceed cap, status CAPACITY is set, row_ptr still holds the
- * exact row offsets, col is filled only below cap, and the caller must
- * enlarge col to *n_pairs_dev and call again.  cap must not exceed the
+ * If the pairs exceed cap, status CAPACITY is set, *n_pairs_dev still holds
+ * the number of pairs found, row_ptr holds the exact row offsets clamped to
+ * cap (so no reader of the truncated list leaves col; the rows that end at
+ * or below cap are complete), col is filled only below cap, and the caller
+ * must enlarge col to *n_pairs_dev and call again.  cap must not exceed the
  * context's max_pairs. */
 int tnet_neighbors(tnet_ctx *ctx, int n_atoms, int n_systems, const float *pos,
                    const int32_t *batch, const float *box, float cutoff, int32_t *row_ptr,
