@@ -68,3 +68,16 @@ def test_operand_copies_only_in_bf16_mode():
     bbf = bench.stage_work("message_bwd", nu, N, E, F, K, "bf16")[1]
     assert b32 == bx3
     assert bbf == b32 + 2.0 * 9 * N * F - 2.0 * 3 * F * nu
+
+
+def test_cpu_baseline_times_the_sample_on_one_thread_too():
+    """The CPU baseline record states how the oracle uses the host cores and
+    times the same sample again in a child process on one thread."""
+    from paper_2402_17660_gb300 import synth
+    W = synth.init_weights(synth.ModelShape(), seed=0)    # the shape the oracle timing assumes
+    s = synth.random_cluster(12, seed=3)
+    rec, ref = bench.cpu_baseline(s, W)
+    assert rec["kind"] == "oracle" and rec["measured_on_full_workload"] and ref is not None
+    assert "threads" in rec
+    st = rec["single_thread"]
+    assert st is not None and st["cores"] == 1 and st["value"] > 0 and st["seconds_per_sample_eval"] > 0
