@@ -102,6 +102,27 @@ def test_edge_basis():
         assert np.allclose(P, Q)
 
 
+@pytest.mark.parametrize("reflect", [False, True])
+def test_edge_basis_transforms_under_o3(reflect):
+    """Covariance of the edge basis under an orthogonal R: R S0(u) R^T =
+    S0(R u), while the skew part is a pseudo-tensor, R A0(u) R^T =
+    det(R) A0(R u) (it flips sign under a reflection, which the O(3) energy
+    sees only through squared norms and products of two skew parts)."""
+    rng = np.random.default_rng(7)
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] = -Q[:, 0]
+    R = Q @ np.diag([1.0, 1.0, -1.0]) if reflect else Q
+    u = rng.standard_normal((20, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    _, A0, S0 = tn.edge_basis(u)
+    _, A1, S1 = tn.edge_basis(u @ R.T)
+    det = np.linalg.det(R)
+    assert math.isclose(abs(det), 1.0, rel_tol=1e-12) and (det < 0) == reflect
+    assert np.allclose(R @ S0 @ R.T, S1, atol=1e-13)
+    assert np.allclose(R @ A0 @ R.T, det * A1, atol=1e-13)
+
+
 def test_layer_norm_silu_match_torch():
     rng = np.random.default_rng(2)
     x = rng.standard_normal((6, 40))
