@@ -1,0 +1,75 @@
+"""Degenerate inputs of the energy-and-force path against the FP64 oracle
+(Sec. 2: per-sample energies as sums over the sample's atoms, forces as their
+negative gradient): one atom, a batch in which no pair is within the cutoff
+(every per-pair kernel and GEMM then runs on zero device-side rows), and
+batches with empty systems, whose energy is an empty sum (exactly 0)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2402_17660_gb300 import synth
+from paper_2402_17660_gb300.tnet import TensorNet
+
+from .gpu_helpers import DEV, E_TOL, F_MAX_TOL, F_TOL, force_errors, gpu_energy_forces, oracle_energy_forces
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
+
+SHAPE = synth.ModelShape()
+W = synth.init_weights(SHAPE, seed=0)
+PRECISIONS = [0, 2, 1]
+
+
+def _model(sys, precision):
+    return TensorNet(W, F=SHAPE.F, K=SHAPE.K, L=SHAPE.L, max_z=SHAPE.max_z, max_atoms=sys.n_atoms,
+                     max_systems=sys.n_systems, max_pairs=64 + 40 * sys.n_atoms, precision=precision, device=DEV)
+
+
+def _system(name, z, pos, batch, n_systems):
+    return synth.System(name, np.asarray(z, np.int32), np.asarray(pos, np.float32),
+                        np.asarray(batch, np.int32), None, n_systems)
+
+
+def _check(sys, precision, zero_forces=False):
+    m = _model(sys, precision)
+    E, F = gpu_energy_forces(m, sys)
+    Es, Ei, Fo = oracle_energy_forces(W, sys, SHAPE)
+    counts = np.bincount(sys.batch, minlength=sys.n_systems)
+    empty = counts == 0
+    # an empty system's energy is an empty sum: exactly zero on both sides
+    assert np.all(E[empty] == 0.0) and np.all(Es[empty] == 0.0)
+    tol = E_TOL if precision != 1 else 1e-2
+    scale = np.maximum(np.abs(Es), np.bincount(sys.batch, weights=np.abs(Ei), minlength=sys.n_systems))
+    err = np.abs(E[~empty] - Es[~empty]) / scale[~empty]
+    assert np.all(err <= tol), (precision, err)
+    if zero_forces:
+        assert np.all(F == 0.0) and np.all(Fo == 0.0)
+    else:
+        f_err, f_max = force_errors(F, Fo)
+        f_tol, fm_tol = (F_TOL, F_MAX_TOL) if precision != 1 else (1e-2, 1e-1)
+        assert f_err <= f_tol and f_max <= fm_tol, (precision, f_err, f_max)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_single_atom(precision):
+    _check(_system("one_atom", [6], [[0.3, -0.2, 1.0]], [0], 1), precision, zero_forces=True)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_batch_without_any_pair(precision):
+    """Three systems of isolated atoms, every distance above the 5 A cutoff."""
+    z = [1, 6, 8, 7, 1]
+    pos = [[0, 0, 0], [6.0, 0, 0], [0, 0, 0], [0, 7.5, 0], [0, 0, 0]]
+    _check(_system("no_pairs", z, pos, [0, 0, 1, 1, 2], 3), precision, zero_forces=True)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_batch_with_empty_systems(precision):
+    """Systems 0, 2, 3 and 5 of six hold no atom (at both ends of the range
+    and in the middle): their energies are exactly zero, and the molecules of
+    systems 1 and 4 match the oracle."""
+    a = synth.random_cluster(20, seed=41)
+    b = synth.random_cluster(14, seed=42)
+    z = np.concatenate([a.z, b.z])
+    pos = np.concatenate([a.pos, b.pos + np.float32(50.0)])
+    batch = np.concatenate([np.full(20, 1), np.full(14, 4)])
+    _check(_system("empty_systems", z, pos, batch, 6), precision)
