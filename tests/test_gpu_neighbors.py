@@ -175,6 +175,31 @@ def test_capacity_overflow_reports_needed_size():
     assert np.array_equal(got_i[keep], ref_i[sel]) and np.array_equal(got_j[keep], ref_j[sel])
 
 
+@pytest.mark.parametrize("slack", [0, -1])
+def test_capacity_at_the_exact_pair_count(slack):
+    """A capacity equal to the pair count holds the whole list with no error;
+    one entry less overflows by one: CAPACITY, the exact count reported, the
+    last row offset clamped, and every row but the last complete."""
+    s = synth.workload("molecule32")
+    oi, oj = neighbor_pairs(s.pos, s.batch, s.box, RC)
+    n = len(oi)
+    m = make_model(W, s, max_pairs=n + 100)
+    nl = gpu_pairs(m, s, cap=n + slack)
+    assert int(nl.n_pairs.item()) == n
+    got_i, got_j = csr_to_pairs(nl)
+    if slack == 0:
+        assert int(m.status.item()) == 0
+        assert np.array_equal(got_i, oi) and np.array_equal(got_j, oj)
+        return
+    assert int(m.status.item()) == 2
+    rp = nl.row_ptr.cpu().numpy().astype(np.int64)
+    full = np.concatenate([[0], np.cumsum(np.bincount(oi, minlength=s.n_atoms))])
+    assert np.array_equal(rp, np.minimum(full, n - 1))
+    last_row = int(oi[-1])
+    keep, sel = got_i < last_row, oi < last_row
+    assert np.array_equal(got_i[keep], oi[sel]) and np.array_equal(got_j[keep], oj[sel])
+
+
 def test_energy_forces_on_truncated_list_is_flagged_and_safe():
     """An overflowed (truncated) list is not symmetric: tnet_energy_forces
     flags it and treats the unmatched edges as inactive, touching nothing
