@@ -395,6 +395,43 @@ def stage_work(tag, nu, N, E, F, K, prec, table=0, rec=False):
     return None
 
 
+def stage_roofline(tag, per_launch_ms, nu, N, E, F, K, prec, table, rec, peaks):
+    """Roofline of one stage instance from its algorithmic work (stage_work)
+    and its measured time per instance: the bound is the tensor or ALU roof
+    when the arithmetic intensity is above that roof's ridge point against
+    HBM, else HBM.  3xTF32 GEMMs count useful FLOP against a third of the TF32
+    rate (three MMAs per product).  Peaks: MEASURED_PEAKS.json, else the
+    fallbacks named in each record."""
+    flops, nbytes, engine = stage_work(tag, nu, N, E, F, K, prec, table, rec)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s, derived
+    if prec == "tf32x3" and not table and tag in ("mlp2", "mlp3", "mlp3_bwd", "mlp2_bwd"):
+        # 3xTF32: three TF32 MMAs per product (the residuals are formed on
+        # chip, so the bytes are those of the fp32 operands)
+        engine = "tensor_tf32"
+    if engine == "tensor":
+        cpeak, cname, cnote = bf16_peak, "tensor", "of measured bf16 burst (MEASURED_PEAKS.json)"
+    elif engine == "tensor_tf32":
+        # useful FLOP against one third of the TF32 rate (nominal TF32 = bf16 / 2)
+        cpeak, cname = bf16_peak / 2 / 3, "tensor"
+        cnote = "measured bf16 burst x nominal TF32/BF16 ratio 1/2, divided by the 3 MMAs of 3xTF32"
+    else:
+        cpeak, cname, cnote = fp32_peak, "alu", "FP32 FFMA peak 152 SM x 128 lanes x 2 x 2070 MHz (derived)"
+    ridge = cpeak * 1e12 / (hbm * 1e9)            # FLOP per byte where the two roofs meet
+    if engine != "hbm" and flops / nbytes >= ridge:
+        ach = flops / (per_launch_ms * 1e-3) / 1e12
+        out = {"bound": cname, "achieved": ach, "peak": cpeak, "unit": "TFLOP/s", "frac": ach / cpeak,
+               "peak_note": cnote}
+    else:
+        ach = nbytes / (per_launch_ms * 1e-3) / 1e9
+        out = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+               "peak_note": "of measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
+    out.update({"kernel": tag, "algorithmic_flop_per_launch": flops, "algorithmic_bytes_per_launch": nbytes,
+                "launch_ms": per_launch_ms, "arithmetic_intensity": flops / nbytes})
+    return out
+
+
 KEPT_BYTES_PER_PAIR_SLOT = 4.5 * 1024   # a1, h1, a2, h2, a3 at F = 128: per undirected pair and layer
 
 
@@ -535,22 +572,22 @@ def run_ours(args):
     roofline = None
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    bf16_peak = peaks.get("bf16_tflops", 1900.0)
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s, derived
-    x3 = args.precision == "tf32x3"
     tab = args.radial_table > 0
     work_tags = [k for k in sorted(stages, key=lambda k: -stages[k]["ms_per_step"])
                  if stage_work(k, nu, N, n_pairs, F_, shape.K, args.precision, args.radial_table, rec) is not None]
+    # every stage with a work model, against its own roof (the same live
+    # CUDA-event stage times as the dominant stage's line)
+    stage_rooflines = {}
+    for tag in work_tags:
+        per_launch_ms = stages[tag]["ms_per_step"] * args.profile_steps / stages[tag]["instances"]
+        r = stage_roofline(tag, per_launch_ms, nu, N, n_pairs, F_, shape.K, args.precision, args.radial_table,
+                           rec, peaks)
+        stage_rooflines[tag] = {k: r[k] for k in ("bound", "achieved", "unit", "frac")}
     if work_tags:
         tag = work_tags[0]
-        flops, nbytes, engine = stage_work(tag, nu, N, n_pairs, F_, shape.K, args.precision, args.radial_table,
-                                           rec)
-        if x3 and not tab and tag in ("mlp2", "mlp3", "mlp3_bwd", "mlp2_bwd"):
-            # 3xTF32: three TF32 MMAs per product (the residuals are formed on
-            # chip, so the bytes are those of the fp32 operands)
-            engine = "tensor_tf32"
         per_launch_ms = stages[tag]["ms_per_step"] * args.profile_steps / stages[tag]["instances"]
+        roofline = stage_roofline(tag, per_launch_ms, nu, N, n_pairs, F_, shape.K, args.precision,
+                                  args.radial_table, rec, peaks)
         traffic = None
         tpath = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tpath):
@@ -560,26 +597,7 @@ def run_ours(args):
             tr = json.load(open(tpath)).get(tkey)
             if tr and tr.get("kernel_rev") == kernel_revision(tr.get("rev_files")):
                 traffic = tr["bytes_per_launch"]
-        if engine == "tensor":
-            cpeak, cname, cnote = bf16_peak, "tensor", "of measured bf16 burst (MEASURED_PEAKS.json)"
-        elif engine == "tensor_tf32":
-            # useful FLOP against one third of the TF32 rate (nominal TF32 = bf16 / 2)
-            cpeak, cname = bf16_peak / 2 / 3, "tensor"
-            cnote = "measured bf16 burst x nominal TF32/BF16 ratio 1/2, divided by the 3 MMAs of 3xTF32"
-        else:
-            cpeak, cname, cnote = fp32_peak, "alu", "FP32 FFMA peak 152 SM x 128 lanes x 2 x 2070 MHz (derived)"
-        ridge = cpeak * 1e12 / (hbm * 1e9)            # FLOP per byte where the two roofs meet
-        if engine != "hbm" and flops / nbytes >= ridge:
-            ach = flops / (per_launch_ms * 1e-3) / 1e12
-            roofline = {"bound": cname, "achieved": ach, "peak": cpeak, "unit": "TFLOP/s", "frac": ach / cpeak,
-                        "peak_note": cnote}
-        else:
-            ach = nbytes / (per_launch_ms * 1e-3) / 1e9
-            roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                        "peak_note": "of measured HBM copy bandwidth (MEASURED_PEAKS.json)"}
-        roofline.update({"traffic": traffic, "kernel": tag, "algorithmic_flop_per_launch": flops,
-                         "algorithmic_bytes_per_launch": nbytes, "launch_ms": per_launch_ms,
-                         "arithmetic_intensity": flops / nbytes})
+        roofline = {**roofline, "traffic": traffic}
 
     # ---- end to end through the public API with host buffers
     pos_h = torch.from_numpy(sys_.pos).pin_memory()
@@ -641,6 +659,7 @@ def run_ours(args):
             "config": workload_config(sys_, n_pairs, args),
             "ns_per_day_at_0.5fs": value / world * 86400 * FS_PER_STEP * 1e-6,
             "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "roofline": roofline,
+            "stage_rooflines": stage_rooflines,
             "stages_ms_per_step": {k: round(v["ms_per_step"], 4) for k, v in
                                    sorted(stages.items(), key=lambda kv: -kv[1]["ms_per_step"])},
             "clocks": ck, "parallelism": f"replicas x{world}", "accuracy": accuracy,

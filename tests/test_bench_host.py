@@ -81,3 +81,18 @@ def test_cpu_baseline_times_the_sample_on_one_thread_too():
     assert "threads" in rec
     st = rec["single_thread"]
     assert st is not None and st["cores"] == 1 and st["value"] > 0 and st["seconds_per_sample_eval"] > 0
+
+
+def test_stage_roofline_reproduces_a_measured_line():
+    """The roofline helper on the numbers of a water96k bench line (message
+    adjoint: 4.1743 ms per launch) gives that line's HBM fraction; a 3xTF32
+    GEMM stage is bound by the tensor roof (a third of the TF32 rate)."""
+    peaks = {"hbm_gbs": 6685.8, "bf16_tflops": 1991.1}
+    nu, N, E = 2585414, 96000, 5170828
+    r = bench.stage_roofline("message_bwd", 4.174331029256185, nu, N, E, 128, 32, "tf32x3", 0, False, peaks)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["algorithmic_bytes_per_launch"] - 9784255400.0) < 1.0
+    assert abs(r["frac"] - 0.3505803042423122) < 1e-12
+    g = bench.stage_roofline("mlp3", 2.18, nu, N, E, 128, 32, "tf32x3", 0, False, peaks)
+    assert g["bound"] == "tensor" and abs(g["peak"] - 1991.1 / 6) < 1e-9
+    assert abs(g["achieved"] - 2.0 * nu * 256 * 384 / 2.18e-3 / 1e12) < 1e-9
