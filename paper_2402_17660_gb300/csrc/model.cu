@@ -2089,7 +2089,7 @@ static void launch_message_bwd(int rb, int blocks1, cudaStream_t st, Args... arg
     launch(k_message_bwd<F, TAB, 1>, blocks1, F, 0, st, args...);
 }
 
-// ============================================================ driver ===
+// ============================================== host-side launch sequence ===
 static inline int grid_for(int64_t n, int threads, int num_sms) {
     int64_t g = (n + threads - 1) / threads;
     const int64_t cap = (int64_t)num_sms * 16;
