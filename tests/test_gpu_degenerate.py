@@ -1,8 +1,9 @@
-"""Degenerate inputs of the energy-and-force path against the FP64 oracle
-(Sec. 2: per-sample energies as sums over the sample's atoms, forces as their
-negative gradient): one atom, a batch in which no pair is within the cutoff
-(every per-pair kernel and GEMM then runs on zero device-side rows), and
-batches with empty systems, whose energy is an empty sum (exactly 0)."""
+"""Degenerate and ragged inputs of the energy-and-force path against the
+FP64 oracle (Sec. 2: per-sample energies as sums over the sample's atoms,
+forces as their negative gradient): one atom, a batch in which no pair is
+within the cutoff (every per-pair kernel and GEMM then runs on zero
+device-side rows), batches with empty systems, whose energy is an empty sum
+(exactly 0), and a periodic batch of unlike boxes."""
 import numpy as np
 import pytest
 import torch
@@ -10,7 +11,8 @@ import torch
 from paper_2402_17660_gb300 import synth
 from paper_2402_17660_gb300.tnet import TensorNet
 
-from .gpu_helpers import DEV, E_TOL, F_MAX_TOL, F_TOL, force_errors, gpu_energy_forces, oracle_energy_forces
+from .gpu_helpers import (DEV, E_TOL, F_MAX_TOL, F_TOL, force_errors, gpu_energy_forces, margin_ok,
+                          oracle_energy_forces)
 
 pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not torch.cuda.is_available(), reason="needs CUDA")]
 
@@ -73,3 +75,23 @@ def test_batch_with_empty_systems(precision):
     pos = np.concatenate([a.pos, b.pos + np.float32(50.0)])
     batch = np.concatenate([np.full(20, 1), np.full(14, 4)])
     _check(_system("empty_systems", z, pos, batch, 6), precision)
+
+
+def _unlike_boxes():
+    """Two periodic systems in one batch with unlike cells: a rectangular
+    10.5 x 11 x 12 A box and a strongly tilted triclinic one (perpendicular
+    widths 10.35, 10.75 and 11.5 A, all above two cutoffs)."""
+    boxes = np.array([np.diag([10.5, 11.0, 12.0]), [[11.0, 0, 0], [3.0, 11.0, 0], [2.0, -2.5, 11.5]]], np.float32)
+    p0 = synth.random_cluster(30, seed=100, side=10.0, min_dist=1.2)
+    p1 = synth.random_cluster(24, seed=1100, side=10.0, min_dist=1.2)
+    s = synth.System("unlike_boxes", np.concatenate([p0.z, p1.z]), np.concatenate([p0.pos, p1.pos]),
+                     np.concatenate([np.zeros(30, np.int32), np.ones(24, np.int32)]), boxes, 2)
+    assert margin_ok(s)
+    return s
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_periodic_batch_of_unlike_boxes(precision):
+    """A ragged periodic batch (Sec. 2.5.1: rectangular and triclinic boxes,
+    one cell list per system): energies and forces against the oracle."""
+    _check(_unlike_boxes(), precision)
