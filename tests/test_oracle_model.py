@@ -475,3 +475,37 @@ def test_output_concatenates_class_norms_in_blocks():
         want = np.array([s[i, ch, p] ** 2 * (phi * Z[i][1 - ch] * b[p][1 - ch]) ** 2 * n[p]
                          for p in range(3) for ch in range(2)])
         assert np.allclose(c["h"][i], want, rtol=1e-10, atol=1e-14), (i, c["h"][i], want)
+
+
+def test_interaction_messages_sum_over_every_neighbour():
+    """Three atoms on a line, 0 at the origin, 1 at rc/3 and 2 at -rc/2, with
+    isotropic features X_k = c_k Id (c = 1, 2, 3).  Every pair is within the
+    cutoff, with phi(rc/3) = 3/4, phi(rc/2) = 1/2 and phi(5 rc/6) =
+    (1 - sqrt(3)/2)/2.  With the radial MLP giving g^I = phi SiLU(ln 3) =
+    (3/4) ln 3 phi, Xn_k = c_k/(3 c_k^2 + 1) Id and Y_k = 2 Xn_k, atom 0
+    receives M_0 = (3/4) ln 3 (phi_01 Y_1 + phi_02 Y_2), the sum over both of
+    its neighbours with their own filters; T_0 = 2 Y_0 M_0 = t Id and
+    dX_0 = 2 t / (3 t^2 + 1) Id.  Caught: a mean over neighbours, a single
+    neighbour, one filter for all edges."""
+    rc = 5.0
+    m = _toy(mlp3_b=(math.log(3.0), 0.0, 0.0))
+    m.rc = rc
+    pos = np.array([[0.0, 0, 0], [rc / 3, 0, 0], [-rc / 2, 0, 0]])
+    i = np.array([0, 0, 1, 1, 2, 2])
+    j = np.array([1, 2, 0, 2, 0, 1])
+    d = np.linalg.norm(pos[i] - pos[j], axis=1)
+    phi = tn.cosine_cutoff(d, rc)
+    e, _ = tn.expnorm(d, rc, 0.0, 2)
+    c_ = np.array([1.0, 2.0, 3.0])
+    X = np.stack([_one(ck * np.eye(3))[0] for ck in c_])
+    Xout, cache = m.interaction(0, X, e, phi, i, j)
+    ln3 = math.log(3.0)
+    phis = {(0, 1): 0.75, (0, 2): 0.5, (1, 2): 0.5 * (1.0 - math.sqrt(3.0) / 2.0)}
+    y = 2.0 * c_ / (3.0 * c_ ** 2 + 1.0)
+    for k in range(3):
+        mk = 0.75 * ln3 * sum(phis[tuple(sorted((k, n)))] * y[n] for n in range(3) if n != k)
+        assert np.allclose(cache["M"][k, 0], mk * np.eye(3), rtol=1e-13, atol=1e-15), k
+        t = 2.0 * y[k] * mk
+        dx = 2.0 * t / (3.0 * t * t + 1.0)
+        xn = c_[k] / (3.0 * c_[k] ** 2 + 1.0)
+        assert np.allclose(Xout[k, 0], (xn + dx + dx * dx) * np.eye(3), rtol=1e-13, atol=1e-15), k
