@@ -509,3 +509,29 @@ def test_interaction_messages_sum_over_every_neighbour():
         dx = 2.0 * t / (3.0 * t * t + 1.0)
         xn = c_[k] / (3.0 * c_[k] ** 2 + 1.0)
         assert np.allclose(Xout[k, 0], (xn + dx + dx * dx) * np.eye(3), rtol=1e-13, atol=1e-15), k
+
+
+def test_per_edge_and_per_atom_splits_are_channel_major():
+    """Reading R3 in the oracle's layout: a 3F vector splits as index c*3 + p
+    (p = I, A, S).  With zero weights before the last bias, the radial filter
+    of an edge is g[c][p] = phi SiLU(b3[c*3 + p]) and the embedding's scales
+    are s[c][p] = SiLU(b2[c*3 + p]), for distinct biases; a plane-major split
+    (index p*F + c) fails both."""
+    F = 2
+    b = np.array([0.1, 0.2, 0.3, 0.4, 0.5, 0.6])
+    m = _toy(F=F, mlp3_b=b)
+    phi = np.array([0.75])
+    g, _ = m.edge_filter(0, np.zeros((1, 2)), phi)
+    for c in range(F):
+        for p in range(3):
+            assert math.isclose(g[0, c, p], 0.75 * tn.silu(b[c * 3 + p]), rel_tol=1e-15)
+    shape = synth.ModelShape(F=F, K=4, L=0, max_z=10)
+    W = synth.init_weights(shape, seed=3)
+    W["emb_mlp2_w"][:] = 0.0
+    W["emb_mlp2_b"] = b.astype(np.float32)
+    _, _, c_ = TensorNet(W, F=F, K=4, L=0).forward(np.array([1, 6], np.int32),
+                                                     np.array([[0.0, 0, 0], [0, 0, 2.0]]), np.zeros(2, np.int32), None)
+    b32 = W["emb_mlp2_b"].astype(np.float64)
+    for c in range(F):
+        for p in range(3):
+            assert np.allclose(c_["s"][:, c, p], tn.silu(b32[c * 3 + p]), rtol=1e-15, atol=0)
