@@ -40,8 +40,9 @@ differences of the energy (forces) and of every weight tensor (weight
 gradients), invariance under rotations, reflections, translations,
 permutations of like atoms and periodic image shifts, zero net force,
 equivariance of forces, cutoff continuity, the isolated-atom closed form,
-closed forms of the embedding's edge-to-node sum and of the interaction
-layer's node update on toy inputs, and an independent float64 autograd
+closed forms on toy inputs of the embedding's edge-to-node sum, of the
+channel-major splits, of the interaction layer's messages and node update
+and of the output model's input, and an independent float64 autograd
 restatement of the reverse pass.
 Absolute energies of the composed network have no printed value in the
 paper: parity unpinned beyond those properties.
