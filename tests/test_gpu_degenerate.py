@@ -3,7 +3,8 @@ FP64 oracle (Sec. 2: per-sample energies as sums over the sample's atoms,
 forces as their negative gradient): one atom, a batch in which no pair is
 within the cutoff (every per-pair kernel and GEMM then runs on zero
 device-side rows), batches with empty systems, whose energy is an empty sum
-(exactly 0), and a periodic batch of unlike boxes."""
+(exactly 0), and a periodic batch of unlike boxes; and the whole step
+captured in a CUDA graph against eager calls, bit for bit."""
 import numpy as np
 import pytest
 import torch
@@ -95,3 +96,47 @@ def test_periodic_batch_of_unlike_boxes(precision):
     """A ragged periodic batch (Sec. 2.5.1: rectangular and triclinic boxes,
     one cell list per system): energies and forces against the oracle."""
     _check(_unlike_boxes(), precision)
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_whole_step_graph_replay_equals_eager(precision):
+    """The whole step (neighbor search, energy and forces) captured once in a
+    CUDA graph and replayed on positions updated in place gives bit for bit
+    what eager calls give on the same positions (the path is deterministic:
+    sorted rows, no atomics in the sums)."""
+    s = synth.workload("water3000")
+    N = s.n_atoms
+    m = TensorNet(W, F=SHAPE.F, K=SHAPE.K, L=SHAPE.L, max_z=SHAPE.max_z, max_atoms=N, max_systems=1,
+                  max_pairs=250000, precision=precision, device=DEV)
+    z = torch.from_numpy(s.z).to(DEV)
+    pos = torch.from_numpy(s.pos).to(DEV)
+    box = torch.from_numpy(s.box).to(DEV)
+    m.reset_status()
+    nl = m.neighbors(pos, None, box, 1)
+    E = torch.empty(1, dtype=torch.float64, device=DEV)
+    F = torch.empty((N, 3), dtype=torch.float32, device=DEV)
+
+    def step():
+        m.neighbors(pos, None, box, 1, out=nl)
+        m.energy_forces(z, pos, nl, None, box, 1, out=(E, F, None))
+
+    side = torch.cuda.Stream(DEV)
+    side.wait_stream(torch.cuda.current_stream(DEV))
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream(DEV).wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    gen = torch.Generator(device="cpu").manual_seed(11)
+    for _ in range(3):
+        pos.add_((torch.rand(pos.shape, generator=gen) - 0.5).to(DEV) * 0.02)
+        g.replay()
+        torch.cuda.synchronize()
+        Eg, Fg = E.clone(), F.clone()
+        m.check_status("graph replay")
+        nl2 = m.neighbors(pos, None, box, 1)
+        E2, F2, _ = m.energy_forces(z, pos, nl2, None, box, 1)
+        torch.cuda.synchronize()
+        assert torch.equal(Eg, E2) and torch.equal(Fg, F2)
