@@ -7,6 +7,7 @@ import os
 
 import numpy as np
 import pytest
+import torch
 
 from paper_2402_17660_gb300 import _lib, synth, tnet
 
@@ -154,3 +155,22 @@ int main(void) {
     assert int(out[0]) == lib.tnet_weights_count(ctypes.byref(d))
     assert int(out[1]) == lib.tnet_workspace_bytes(ctypes.byref(d), 3000, 1, 160000)
     assert int(out[2]) == -1 and int(out[3]) == lib.tnet_tuning_knobs()
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """There is no CPU fallback: asking for a library that is not there (and
+    not building it) raises instead of returning a stand-in."""
+    from paper_2402_17660_gb300 import _lib
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load(str(tmp_path / "libtnet.so"), build_if_missing=False)
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the behaviour without a GPU")
+def test_model_without_a_gpu_raises():
+    """Without a CUDA device the model cannot be built: nothing falls back to
+    the host."""
+    from paper_2402_17660_gb300 import synth
+    from paper_2402_17660_gb300.tnet import TensorNet
+    W = synth.init_weights(synth.ModelShape(), seed=0)
+    with pytest.raises(Exception):
+        TensorNet(W, max_atoms=10, max_systems=1, max_pairs=100)
